@@ -1,0 +1,182 @@
+/*
+ * tdmrg.h -- C ABI of the GB300 hot path of time-step-targeting DMRG with
+ * Krylov time evolution (Alvarez, Dias da Silva, Ponce, Dagotto,
+ * arXiv:1103.5391).
+ *
+ * The library holds one superblock L u R (Sec. II.B): the sector tables of the
+ * left and right blocks, block operators split into sector blocks, and the
+ * Hamiltonian as block terms plus connections across the left/right boundary
+ * (Sec. IV, "Hamiltonian connections").  On that superblock it applies H psi,
+ * applies local excitation operators (Eq. b), advances a targeted state by
+ * Krylov time evolution (Sec. II.A Eq. lanczosevolution, Sec. II.C
+ * Eq. lanczosevolution2), forms the weighted reduced density matrix of the
+ * targets (Eq. rdensitymatrix with the weights of Sec. II.C) and its
+ * eigendecomposition, and measures expectation values (Eq. generalcorrelation
+ * with one local operator per block).
+ *
+ * Conventions used by every call
+ *   - Complex numbers are tdmrg_c64 = {re, im} doubles, the layout of
+ *     cuDoubleComplex and torch.complex128.
+ *   - A quantum number is a pair (n_up, n_dn).  Sector tables must be given in
+ *     strictly ascending lexicographic order of (n_up, n_dn).
+ *   - The wave function of superblock sector Q = (N_up, N_dn) is the
+ *     concatenation, over left sectors q in table order whose partner
+ *     r = Q - q exists on the right, of the blocks Psi_q of shape
+ *     dL(q) x dR(r), row-major (left index slow).  tdmrg_sector_size gives
+ *     its length.
+ *   - Superblock basis |alpha>|beta> = (left creation string)(right creation
+ *     string)|0>.  A term "coeff * A_L B_R" is the fermionic product with the
+ *     left operator written first; the library applies it as
+ *     coeff * (A P_L) (x) B when B is fermion-odd, P_L = (-1)^{N_L}, and as
+ *     coeff * A (x) B otherwise.  On a sector block:
+ *       Psi'_{q_out} += coeff * s(q_in) * A[q_out<-q_in] Psi_{q_in} B[r_out<-r_in]^T.
+ *   - Pointers named *_d are device pointers on the context's device; all
+ *     other pointers are host pointers.  Device work is enqueued on the
+ *     context's stream and is asynchronous unless a call says it synchronises.
+ *     The caller owns every buffer it passes; the library owns copies of the
+ *     operators and its workspace.
+ *   - Every call returns TDMRG_OK (0) or a negative error code and never
+ *     aborts; tdmrg_last_error(ctx) describes the last failure on that ctx.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef TDMRG_H
+#define TDMRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdmrg_ctx tdmrg_ctx;
+typedef struct { double re, im; } tdmrg_c64;
+
+enum tdmrg_status {
+    TDMRG_OK = 0,
+    TDMRG_EINVAL = -1,     /* bad argument (null pointer, size, unknown op id)            */
+    TDMRG_ENOMEM = -2,     /* device allocation failed or the HBM budget would be exceeded */
+    TDMRG_ESECTOR = -3,    /* inconsistent quantum numbers (unknown sector, bad block dims) */
+    TDMRG_ECUDA = -4,      /* a CUDA runtime call failed                                    */
+    TDMRG_ETIMEOUT = -5,   /* a bounded device wait ran out                                 */
+    TDMRG_ESTATE = -6      /* call out of order (e.g. apply_h before set_hamiltonian)       */
+};
+
+enum tdmrg_side { TDMRG_LEFT = 0, TDMRG_RIGHT = 1 };
+
+/* Arithmetic of the superblock products (H psi, excitations, expectation values).
+ * Lanczos orthogonalisation, norms, the tridiagonal exponential and rho_L always run in FP64. */
+enum tdmrg_prec {
+    TDMRG_FP64 = 0,        /* complex FP64 products (DMMA tensor-core path)                          */
+    TDMRG_OZAKI_BF16 = 1   /* FP64 operands split into bf16 slices, exact FP32 tensor-core products,
+                              FP64 recombination; accuracy set by ozaki_slices                       */
+};
+
+typedef struct {
+    int device;            /* CUDA device ordinal                                         */
+    void* stream;          /* cudaStream_t to enqueue on; NULL = legacy default stream     */
+    int prec;              /* enum tdmrg_prec                                               */
+    int ozaki_slices;      /* bf16 slices per operand for TDMRG_OZAKI_BF16 (2..7)           */
+    int nk_max;            /* largest Krylov dimension n_K accepted by tdmrg_evolve (<=32)  */
+    double breakdown_tol;  /* Lanczos stops when beta_{j+1} <= tol * max(1, |alpha_j|)      */
+    size_t hbm_budget;     /* bytes the context may allocate on the device; 0 = unlimited   */
+} tdmrg_opts;
+
+/* Fill *o with defaults: device 0, default stream, FP64, 4 slices, nk_max 16, tol 1e-12, no budget. */
+void tdmrg_default_opts(tdmrg_opts* o);
+
+/* Create a context on o->device.  *out receives an opaque handle owned by the library. */
+int tdmrg_create(tdmrg_ctx** out, const tdmrg_opts* o);
+/* Release the context and all device memory it owns (synchronises its stream). */
+int tdmrg_destroy(tdmrg_ctx* ctx);
+/* Change the stream later calls enqueue on (e.g. torch.cuda.current_stream().cuda_stream). */
+int tdmrg_set_stream(tdmrg_ctx* ctx, void* stream);
+/* Change the arithmetic of superblock products (enum tdmrg_prec) and the number of Ozaki slices. */
+int tdmrg_set_precision(tdmrg_ctx* ctx, int prec, int ozaki_slices);
+/* Text of the last error on ctx (a static string when ctx is NULL). */
+const char* tdmrg_last_error(tdmrg_ctx* ctx);
+
+/* Block basis of one side (Sec. II.B: alpha in L, beta in R).  nsec sectors, qn[2*s] = n_up,
+ * qn[2*s+1] = n_dn in strictly ascending lexicographic order, dim[s] >= 1.
+ * Setting a block drops every operator, Hamiltonian and plan of that side.
+ * Errors: EINVAL (nsec < 1, null), ESECTOR (order, dims). */
+int tdmrg_set_block(tdmrg_ctx* ctx, int side, int nsec, const int32_t* qn, const int32_t* dim);
+
+/* Block operator op_id (>= 0) on one side, given as nblk dense sector blocks.
+ * blk_qn[4*b..4*b+3] = (out n_up, out n_dn, in n_up, in n_dn); the data of all blocks is
+ * concatenated in that order, block b being dim(out) x dim(in) row-major.  fermion_odd = 1 marks an
+ * operator that changes the particle number parity (c, c^dag); for a right operator it makes the
+ * library apply the left parity P_L (Sec. II.B: reordering fermions costs at most a sign).
+ * data may be a host (data_on_device = 0) or device pointer; the library copies it.
+ * Redefining an op_id replaces it and invalidates plans that use it.
+ * Errors: EINVAL, ESECTOR (unknown sector), ENOMEM. */
+int tdmrg_set_op(tdmrg_ctx* ctx, int side, int op_id, int fermion_odd, int nblk, const int32_t* blk_qn,
+                 const tdmrg_c64* data, int data_on_device);
+
+/* H = H_L (x) 1 + 1 (x) H_R + sum_k coeff[k] * opL[k] opR[k]  (Sec. IV; Hubbard H of Sec. III.B).
+ * opHL is a left op id, opHR a right op id (-1 = absent); opL[k] / opR[k] are left / right op ids of
+ * connection k, coeff[k] its complex amplitude.  The caller includes both Hermitian halves
+ * (e.g. -t c^dag_i c_j and +t c_i c^dag_j).  Errors: EINVAL, ESTATE (blocks not set). */
+int tdmrg_set_hamiltonian(tdmrg_ctx* ctx, int opHL, int opHR, int nconn, const int32_t* opL,
+                          const int32_t* opR, const tdmrg_c64* coeff);
+
+/* Length of the sector-Q wave function (number of complex entries; 0 if Q has no pairs). */
+int tdmrg_sector_size(tdmrg_ctx* ctx, int n_up, int n_dn, int64_t* dim_out);
+
+/* out_d = H psi_d in sector Q (Sec. IV).  Both are device vectors of tdmrg_sector_size entries and
+ * must not overlap.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+int tdmrg_apply_h(tdmrg_ctx* ctx, int n_up, int n_dn, const tdmrg_c64* psi_d, tdmrg_c64* out_d);
+
+/* Excitation out_d = (opL P_L^{odd(opR)}) (x) opR  psi_d from sector Q_in to Q_out (Eq. b with a
+ * local operator on each block; -1 = identity on that block, not both).  Errors as apply_h. */
+int tdmrg_apply_op(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdmrg_c64* psi_d,
+                   int n_up_out, int n_dn_out, tdmrg_c64* out_d);
+
+/* Krylov advance (Sec. II.A-II.C).  From phi(t) = phi_d in sector Q, builds nk Lanczos vectors
+ * started at phi (full re-orthogonalisation, two classical Gram-Schmidt passes, FP64), diagonalises
+ * T = S^dag D S and writes targets_d[x] = ||phi|| V^dag S^dag e^{-i D t_x} S e_0 ~ e^{-i H t_x} phi
+ * for x = 0..n_v-1 (t_x host array, t_x >= 0).  targets_d is a host array of n_v device pointers,
+ * each a sector-Q vector; a target may alias phi_d (phi is copied into the Krylov workspace before
+ * any target is written), targets must not alias each other.
+ * Lanczos stops early at breakdown; tdmrg_evolve_info reports the dimension used and the error
+ * estimate.  nk in 1..nk_max.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+int tdmrg_evolve(tdmrg_ctx* ctx, int n_up, int n_dn, const tdmrg_c64* phi_d, int n_v, const double* t_x,
+                 int nk, tdmrg_c64* const* targets_d);
+
+/* Results of the last tdmrg_evolve: Krylov dimension used, a-posteriori error estimate
+ * ||phi|| beta_n |[e^{-i T t_{n_v-1}}]_{n-1,0}| (Saad), and optionally alpha[0..n-1], beta[0..n-1]
+ * (beta[j] couples v_j and v_{j+1}; beta[n-1] is the residual).  Synchronises the stream. */
+int tdmrg_evolve_info(tdmrg_ctx* ctx, int* nk_used, double* err_est, double* alpha, double* beta);
+
+/* Weights of time-step targeting (Sec. II.C): n = n_v + 1 states including the ground state,
+ * Omega = 1/(n+3); 2 Omega for the ground state, the first and the last time target, Omega for the
+ * others.  w_gs (host) gets the ground-state weight, w (host, n_v) the target weights.  n_v >= 2. */
+int tdmrg_tst_weights(int n_v, double* w_gs, double* w);
+
+/* Number of complex entries of rho_L (sum over left sectors of dL^2) and of eigenvalues (sum dL). */
+int tdmrg_rho_size(tdmrg_ctx* ctx, int64_t* rho_entries, int64_t* n_evals);
+
+/* Weighted reduced density matrix (Eq. rdensitymatrix):
+ *   rho_L(q) = sum_l w[l] Psi_l(q) Psi_l(q)^dag / <psi_l|psi_l>
+ * over ntargets states psi_d[l] (host array of device pointers) in sectors Q[2l], Q[2l+1] (host).
+ * rho_d receives every left sector's dL x dL block, row-major, packed in left-table order (zero for
+ * sectors no target reaches).  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+int tdmrg_density_matrix(tdmrg_ctx* ctx, int ntargets, const int32_t* Q, const tdmrg_c64* const* psi_d,
+                         const double* w, tdmrg_c64* rho_d);
+
+/* Eigendecomposition of a packed rho_L (as written by tdmrg_density_matrix), FP64 Jacobi per sector.
+ * evals_d (sum dL doubles) gets each sector's eigenvalues in descending order; evecs_d (packed like
+ * rho) gets U with rho(q) = U diag(evals) U^dag, column k of U the k-th eigenvector.  This feeds the
+ * truncation of Sec. II.B.  Errors: EINVAL, ESTATE, ECUDA. */
+int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg_c64* evecs_d);
+
+/* out_d[0] = <psi| opL opR |psi> / <psi|psi> for a sector-preserving product (Eq. generalcorrelation
+ * with a = 1 local operator per block, Eq. nholondoublon; -1 = identity on that block).  out_d is
+ * one device tdmrg_c64.  Errors as apply_op. */
+int tdmrg_expect(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdmrg_c64* psi_d,
+                 tdmrg_c64* out_d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDMRG_H */

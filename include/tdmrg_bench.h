@@ -1,0 +1,31 @@
+/*
+ * tdmrg_bench.h -- measurement entry points of libtdmrg.  The paper has no counterpart: these calls
+ * exist so that benchmarks can state the rooflines and launch counts the hot path runs against.
+ */
+#ifndef TDMRG_BENCH_H
+#define TDMRG_BENCH_H
+
+#include <stdint.h>
+
+#include "tdmrg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Number of kernels the context has launched since it was created (host counter, no sync). */
+int tdmrg_launch_count(tdmrg_ctx* ctx, int64_t* count);
+
+/* Algorithmic FP64-equivalent flops of one H psi in sector Q as the library computes it: 8 real flops
+ * per complex multiply-add of every sector-pair product it issues (stage 1 + stage 2). */
+int tdmrg_hpsi_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
+
+/* Sustained FP64 throughput of this device, measured by timing (CUDA events) a register-resident
+ * loop of the FP64 tensor MMA (mma.sync m8n8k4 f64) and of scalar DFMA on every SM.  Synchronises
+ * the device; takes well under a second.  Results in TFLOP/s. */
+int tdmrg_fp64_peak(int device, double* dmma_tflops, double* dfma_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDMRG_BENCH_H */

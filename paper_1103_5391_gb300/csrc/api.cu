@@ -1,0 +1,441 @@
+// C ABI entry points of libtdmrg (declared and documented in include/tdmrg.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace tdmrg;
+
+namespace {
+thread_local std::string g_err = "no error";
+}
+
+namespace tdmrg {
+
+int fail(tdmrg_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_err = msg;
+    return code;
+}
+
+int cuda_check(tdmrg_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TDMRG_OK;
+    return fail(c, TDMRG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int dev_alloc(tdmrg_ctx* c, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return TDMRG_OK;
+    if (c->opts.hbm_budget && c->allocated + bytes > c->opts.hbm_budget)
+        return fail(c, TDMRG_ENOMEM, std::string(what) + ": HBM budget exceeded");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, TDMRG_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    c->allocated += bytes;
+    return TDMRG_OK;
+}
+
+void dev_free(tdmrg_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->allocated -= std::min(bytes, c->allocated);
+}
+
+}  // namespace tdmrg
+
+namespace {
+
+struct DeviceGuard {   // makes the context's device current for the duration of a call
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void drop_plans(tdmrg_ctx* c) {
+    for (auto& kv : c->plans) {
+        release(c, kv.second->stage1);
+        release(c, kv.second->stage2);
+    }
+    c->plans.clear();
+}
+
+void drop_krylov(tdmrg_ctx* c) {
+    for (auto& kv : c->krylov) {
+        KrylovWork& k = kv.second;
+        size_t n = (size_t)k.n;
+        dev_free(c, k.V, (k.nk + 1) * n * sizeof(cplx));
+        dev_free(c, k.w, n * sizeof(cplx));
+        dev_free(c, k.partA, 64 * kRedBlocks * sizeof(double2));
+        dev_free(c, k.partB, 64 * kRedBlocks * sizeof(double2));
+        dev_free(c, k.tri, 128 * sizeof(double));
+        dev_free(c, k.flags, 4 * sizeof(int));
+        dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
+    }
+    c->krylov.clear();
+    c->last_krylov = nullptr;
+}
+
+int check_ctx(tdmrg_ctx* c) { return c ? TDMRG_OK : fail(nullptr, TDMRG_EINVAL, "null context"); }
+
+int check_op(tdmrg_ctx* c, int side, int id) {
+    if (id < 0) return TDMRG_OK;
+    if (!c->ops[side].count(id))
+        return fail(c, TDMRG_EINVAL, std::string(side ? "right" : "left") + " op id " + std::to_string(id) + " is not set");
+    return TDMRG_OK;
+}
+
+// Cached plan for (terms id, op ids, Q_in, Q_out); terms id 0 = Hamiltonian, 1 = single product.
+int get_plan(tdmrg_ctx* c, int kind, int opL, int opR, int qa, int qb, int oa, int ob, Plan** out) {
+    auto key = std::make_tuple(kind, opL, opR, qa, qb, oa, ob);
+    auto it = c->plans.find(key);
+    if (it != c->plans.end()) { *out = it->second.get(); return TDMRG_OK; }
+    std::vector<Term> terms;
+    if (kind == 0) terms = c->ham;
+    else terms.push_back({opL, opR, make_double2(1.0, 0.0)});
+    std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+    if (!p) return fail(c, TDMRG_ENOMEM, "host allocation");
+    int rc = build_plan(c, terms, qa, qb, oa, ob, p.get());
+    if (rc) { release(c, p->stage1); release(c, p->stage2); return rc; }
+    *out = p.get();
+    c->plans[key] = std::move(p);
+    return TDMRG_OK;
+}
+
+int ensure_tmp(tdmrg_ctx* c, int64_t n) {
+    if (n <= c->tmp_cap) return TDMRG_OK;
+    dev_free(c, c->tmp, c->tmp_cap * sizeof(cplx));
+    c->tmp = nullptr; c->tmp_cap = 0;
+    int rc = dev_alloc(c, (void**)&c->tmp, n * sizeof(cplx), "expectation workspace");
+    if (!rc) c->tmp_cap = n;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tdmrg_default_opts(tdmrg_opts* o) {
+    if (!o) return;
+    o->device = 0;
+    o->stream = nullptr;
+    o->prec = TDMRG_FP64;
+    o->ozaki_slices = 4;
+    o->nk_max = 16;
+    o->breakdown_tol = 1e-12;
+    o->hbm_budget = 0;
+}
+
+int tdmrg_create(tdmrg_ctx** out, const tdmrg_opts* o) {
+    if (!out || !o) return fail(nullptr, TDMRG_EINVAL, "null argument to tdmrg_create");
+    *out = nullptr;
+    if (o->nk_max < 1 || o->nk_max > 32) return fail(nullptr, TDMRG_EINVAL, "nk_max must be in 1..32");
+    if (o->prec != TDMRG_FP64) return fail(nullptr, TDMRG_EINVAL, "unsupported precision");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o->device < 0 || o->device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, TDMRG_ECUDA, "no CUDA device " + std::to_string(o->device));
+    }
+    tdmrg_ctx* c = new (std::nothrow) tdmrg_ctx();
+    if (!c) return fail(nullptr, TDMRG_ENOMEM, "host allocation");
+    c->opts = *o;
+    c->stream = (cudaStream_t)o->stream;
+    DeviceGuard g(o->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, o->device);
+    int rc = dev_alloc(c, (void**)&c->red, 2 * 64 * kRedBlocks * sizeof(double2), "reduction workspace");
+    if (!rc) rc = dev_alloc(c, (void**)&c->dscale, 64 * sizeof(double), "scale workspace");
+    if (rc) {
+        g_err = c->err;
+        tdmrg_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return TDMRG_OK;
+}
+
+int tdmrg_destroy(tdmrg_ctx* c) {
+    if (!c) return TDMRG_OK;
+    DeviceGuard g(c->opts.device);
+    cudaStreamSynchronize(c->stream);
+    drop_plans(c);
+    drop_krylov(c);
+    dev_free(c, c->pool, c->pool_cap * sizeof(cplx));
+    dev_free(c, c->scratch, c->scratch_cap * sizeof(cplx));
+    dev_free(c, c->tmp, c->tmp_cap * sizeof(cplx));
+    dev_free(c, c->red, 2 * 64 * kRedBlocks * sizeof(double2));
+    dev_free(c, c->dscale, 64 * sizeof(double));
+    delete c;
+    return TDMRG_OK;
+}
+
+int tdmrg_set_stream(tdmrg_ctx* c, void* stream) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    c->opts.stream = stream;
+    return TDMRG_OK;
+}
+
+int tdmrg_set_precision(tdmrg_ctx* c, int prec, int slices) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (prec != TDMRG_FP64) return fail(c, TDMRG_EINVAL, "unsupported precision " + std::to_string(prec));
+    c->opts.prec = prec;
+    c->opts.ozaki_slices = slices;
+    return TDMRG_OK;
+}
+
+const char* tdmrg_last_error(tdmrg_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+int tdmrg_set_block(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const int32_t* dim) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if ((side != 0 && side != 1) || nsec < 1 || !qn || !dim) return fail(c, TDMRG_EINVAL, "set_block: bad argument");
+    Side s;
+    for (int k = 0; k < nsec; ++k) {
+        if (dim[k] < 1) return fail(c, TDMRG_ESECTOR, "set_block: sector dimension < 1");
+        if (k > 0) {
+            bool asc = (qn[2 * k] > qn[2 * k - 2]) || (qn[2 * k] == qn[2 * k - 2] && qn[2 * k + 1] > qn[2 * k - 1]);
+            if (!asc) return fail(c, TDMRG_ESECTOR, "set_block: sectors not strictly ascending");
+        }
+        s.nup.push_back(qn[2 * k]);
+        s.ndn.push_back(qn[2 * k + 1]);
+        s.dim.push_back(dim[k]);
+        s.index[{qn[2 * k], qn[2 * k + 1]}] = k;
+    }
+    s.set = true;
+    DeviceGuard g(c->opts.device);
+    cudaStreamSynchronize(c->stream);
+    c->side[side] = s;
+    c->ops[side].clear();
+    c->ham_set = false;
+    c->ham.clear();
+    drop_plans(c);
+    drop_krylov(c);
+    if (!c->ops[0].size() && !c->ops[1].size()) c->pool_used = 0;
+    return TDMRG_OK;
+}
+
+int tdmrg_set_op(tdmrg_ctx* c, int side, int id, int odd, int nblk, const int32_t* bq, const tdmrg_c64* data,
+                 int on_device) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if ((side != 0 && side != 1) || id < 0 || nblk < 0 || (nblk > 0 && (!bq || !data)))
+        return fail(c, TDMRG_EINVAL, "set_op: bad argument");
+    const Side& S = c->side[side];
+    if (!S.set) return fail(c, TDMRG_ESTATE, "set_op: block not set");
+    BlockOp op;
+    op.side = side;
+    op.odd = odd ? 1 : 0;
+    int64_t total = 0;
+    std::vector<std::pair<int, int>> idx;
+    for (int b = 0; b < nblk; ++b) {
+        int qo = S.find(bq[4 * b], bq[4 * b + 1]), qi = S.find(bq[4 * b + 2], bq[4 * b + 3]);
+        if (qo < 0 || qi < 0) return fail(c, TDMRG_ESECTOR, "set_op: block refers to an unknown sector");
+        int dq = (bq[4 * b] + bq[4 * b + 1]) - (bq[4 * b + 2] + bq[4 * b + 3]);
+        if (((dq & 1) != 0) != (op.odd != 0))
+            return fail(c, TDMRG_ESECTOR, "set_op: block parity change does not match fermion_odd");
+        for (auto& p : idx)
+            if (p.first == qo && p.second == qi) return fail(c, TDMRG_ESECTOR, "set_op: duplicate block");
+        idx.push_back({qo, qi});
+        total += (int64_t)S.dim[qo] * S.dim[qi];
+    }
+    DeviceGuard g(c->opts.device);
+    if (c->pool_used + total > c->pool_cap) {   // grow the pool (offsets stay valid)
+        int64_t cap = std::max<int64_t>(2 * c->pool_cap, c->pool_used + total + 4096);
+        cplx* np = nullptr;
+        int rc = dev_alloc(c, (void**)&np, cap * sizeof(cplx), "operator pool");
+        if (rc) return rc;
+        if (c->pool_used) {
+            rc = cuda_check(c, cudaMemcpyAsync(np, c->pool, c->pool_used * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                                               c->stream), "operator pool copy");
+            if (rc) { dev_free(c, np, cap * sizeof(cplx)); return rc; }
+        }
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, c->pool, c->pool_cap * sizeof(cplx));
+        c->pool = np;
+        c->pool_cap = cap;
+    }
+    int64_t off = c->pool_used;
+    int64_t src = 0;
+    for (int b = 0; b < nblk; ++b) {
+        int64_t n = (int64_t)S.dim[idx[b].first] * S.dim[idx[b].second];
+        op.blocks.push_back(std::make_tuple(idx[b].first, idx[b].second, off + src));
+        src += n;
+    }
+    if (total) {
+        int rc = cuda_check(c, cudaMemcpyAsync(c->pool + off, data, total * sizeof(cplx),
+                                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+                            "set_op copy");
+        if (rc) return rc;
+        if (!on_device) cudaStreamSynchronize(c->stream);   // the caller may free its host buffer on return
+    }
+    c->pool_used += total;
+    auto it = c->ops[side].find(id);
+    op.version = it == c->ops[side].end() ? 0 : it->second.version + 1;
+    c->ops[side][id] = op;
+    drop_plans(c);
+    return TDMRG_OK;
+}
+
+int tdmrg_set_hamiltonian(tdmrg_ctx* c, int hl, int hr, int nconn, const int32_t* opL, const int32_t* opR,
+                          const tdmrg_c64* coeff) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "set_hamiltonian: blocks not set");
+    if (nconn < 0 || (nconn > 0 && (!opL || !opR || !coeff))) return fail(c, TDMRG_EINVAL, "set_hamiltonian: bad argument");
+    if (check_op(c, 0, hl) || check_op(c, 1, hr)) return TDMRG_EINVAL;
+    std::vector<Term> terms;
+    if (hl >= 0) {
+        if (c->ops[0].at(hl).odd) return fail(c, TDMRG_EINVAL, "set_hamiltonian: H_L is fermion-odd");
+        terms.push_back({hl, -1, make_double2(1.0, 0.0)});
+    }
+    if (hr >= 0) {
+        if (c->ops[1].at(hr).odd) return fail(c, TDMRG_EINVAL, "set_hamiltonian: H_R is fermion-odd");
+        terms.push_back({-1, hr, make_double2(1.0, 0.0)});
+    }
+    for (int k = 0; k < nconn; ++k) {
+        if (opL[k] < 0 && opR[k] < 0) return fail(c, TDMRG_EINVAL, "set_hamiltonian: connection without operators");
+        if (check_op(c, 0, opL[k]) || check_op(c, 1, opR[k])) return TDMRG_EINVAL;
+        terms.push_back({opL[k], opR[k], make_double2(coeff[k].re, coeff[k].im)});
+    }
+    c->ham = terms;
+    c->ham_set = true;
+    c->ham_version++;
+    drop_plans(c);
+    return TDMRG_OK;
+}
+
+int tdmrg_sector_size(tdmrg_ctx* c, int a, int b, int64_t* out) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!out) return fail(c, TDMRG_EINVAL, "sector_size: null output");
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "sector_size: blocks not set");
+    *out = sector_size(c, a, b);
+    return TDMRG_OK;
+}
+
+int tdmrg_apply_h(tdmrg_ctx* c, int a, int b, const tdmrg_c64* psi, tdmrg_c64* out) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "apply_h: Hamiltonian not set");
+    if (!psi || !out) return fail(c, TDMRG_EINVAL, "apply_h: null vector");
+    DeviceGuard g(c->opts.device);
+    Plan* p = nullptr;
+    int rc = get_plan(c, 0, -1, -1, a, b, a, b, &p);
+    if (rc) return rc;
+    if (p->n_in == 0) return TDMRG_OK;
+    return run_plan(c, *p, (const cplx*)psi, (cplx*)out, nullptr, 0);
+}
+
+int tdmrg_apply_op(tdmrg_ctx* c, int opL, int opR, int a, int b, const tdmrg_c64* psi, int oa, int ob,
+                   tdmrg_c64* out) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "apply_op: blocks not set");
+    if (!psi || !out) return fail(c, TDMRG_EINVAL, "apply_op: null vector");
+    if (opL < 0 && opR < 0) return fail(c, TDMRG_EINVAL, "apply_op: both operators are the identity");
+    if (check_op(c, 0, opL) || check_op(c, 1, opR)) return TDMRG_EINVAL;
+    DeviceGuard g(c->opts.device);
+    Plan* p = nullptr;
+    int rc = get_plan(c, 1, opL, opR, a, b, oa, ob, &p);
+    if (rc) return rc;
+    if (p->n_out == 0) return TDMRG_OK;
+    return run_plan(c, *p, (const cplx*)psi, (cplx*)out, nullptr, 0);
+}
+
+int tdmrg_evolve(tdmrg_ctx* c, int a, int b, const tdmrg_c64* phi, int n_v, const double* t_x, int nk,
+                 tdmrg_c64* const* targets) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "evolve: Hamiltonian not set");
+    if (!phi || !t_x || !targets || n_v < 1 || n_v > 16 || nk < 1 || nk > c->opts.nk_max)
+        return fail(c, TDMRG_EINVAL, "evolve: bad argument (n_v in 1..16, nk in 1..nk_max)");
+    for (int x = 0; x < n_v; ++x) {
+        if (!targets[x]) return fail(c, TDMRG_EINVAL, "evolve: null target");
+        if (!(t_x[x] >= 0.0) || !std::isfinite(t_x[x])) return fail(c, TDMRG_EINVAL, "evolve: t_x must be finite and >= 0");
+        for (int y = 0; y < x; ++y)
+            if (targets[x] == targets[y]) return fail(c, TDMRG_EINVAL, "evolve: targets alias each other");
+    }
+    DeviceGuard g(c->opts.device);
+    return evolve(c, a, b, (const cplx*)phi, n_v, t_x, nk, (cplx* const*)targets);
+}
+
+int tdmrg_evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->last_krylov) return fail(c, TDMRG_ESTATE, "evolve_info: no evolve yet");
+    DeviceGuard g(c->opts.device);
+    return evolve_info(c, nk_used, err, alpha, beta);
+}
+
+int tdmrg_tst_weights(int n_v, double* w_gs, double* w) {
+    if (n_v < 2 || !w_gs || !w) return fail(nullptr, TDMRG_EINVAL, "tst_weights: n_v >= 2 and non-null outputs");
+    const double omega = 1.0 / (double)(n_v + 1 + 3);
+    *w_gs = 2.0 * omega;
+    for (int x = 0; x < n_v; ++x) w[x] = omega;
+    w[0] = 2.0 * omega;
+    w[n_v - 1] = 2.0 * omega;
+    return TDMRG_OK;
+}
+
+int tdmrg_rho_size(tdmrg_ctx* c, int64_t* rho_entries, int64_t* n_evals) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->side[0].set) return fail(c, TDMRG_ESTATE, "rho_size: left block not set");
+    int64_t r = 0, e = 0;
+    for (int d : c->side[0].dim) { r += (int64_t)d * d; e += d; }
+    if (rho_entries) *rho_entries = r;
+    if (n_evals) *n_evals = e;
+    return TDMRG_OK;
+}
+
+int tdmrg_density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const tdmrg_c64* const* psi, const double* w,
+                         tdmrg_c64* rho) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "density_matrix: blocks not set");
+    if (nt < 1 || nt > kMaxBufs - BUF_EXTRA0 || !Q || !psi || !w || !rho)
+        return fail(c, TDMRG_EINVAL, "density_matrix: bad argument (1..12 targets)");
+    for (int l = 0; l < nt; ++l)
+        if (!psi[l] || !(w[l] >= 0.0)) return fail(c, TDMRG_EINVAL, "density_matrix: null state or negative weight");
+    DeviceGuard g(c->opts.device);
+    return density_matrix(c, nt, Q, (const cplx* const*)psi, w, (cplx*)rho);
+}
+
+int tdmrg_rho_eig(tdmrg_ctx* c, const tdmrg_c64* rho, double* evals, tdmrg_c64* evecs) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->side[0].set) return fail(c, TDMRG_ESTATE, "rho_eig: left block not set");
+    if (!rho || !evals || !evecs) return fail(c, TDMRG_EINVAL, "rho_eig: null pointer");
+    DeviceGuard g(c->opts.device);
+    return rho_eig(c, (const cplx*)rho, evals, (cplx*)evecs);
+}
+
+int tdmrg_hpsi_flops(tdmrg_ctx* c, int a, int b, double* flops) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!flops) return fail(c, TDMRG_EINVAL, "hpsi_flops: null output");
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "hpsi_flops: Hamiltonian not set");
+    DeviceGuard g(c->opts.device);
+    Plan* p = nullptr;
+    int rc = get_plan(c, 0, -1, -1, a, b, a, b, &p);
+    if (rc) return rc;
+    *flops = p->flops;
+    return TDMRG_OK;
+}
+
+int tdmrg_expect(tdmrg_ctx* c, int opL, int opR, int a, int b, const tdmrg_c64* psi, tdmrg_c64* out) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!psi || !out) return fail(c, TDMRG_EINVAL, "expect: null pointer");
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "expect: blocks not set");
+    int64_t n = sector_size(c, a, b);
+    if (n == 0) return fail(c, TDMRG_ESECTOR, "expect: empty sector");
+    DeviceGuard g(c->opts.device);
+    int rc = ensure_tmp(c, n);
+    if (rc) return rc;
+    rc = tdmrg_apply_op(c, opL, opR, a, b, psi, a, b, (tdmrg_c64*)c->tmp);
+    if (rc) return rc;
+    c->launches += 2;
+    return cuda_check(c, launch_dot_final((const cplx*)psi, c->tmp, n, c->red, kRedBlocks, (cplx*)out, 1, c->stream),
+                      "expect reduction");
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Grouped complex FP64 GEMM for the sector-pair products of H psi (Sec. IV, Hamiltonian
+// connections), the excitation operators (Eq. b), and rho_L (Eq. rdensitymatrix).
+//
+// One CTA computes one 16 x 16 output tile of one task over a range of its segments:
+//     C_tile = (beta ? C_tile : 0) + sum_segments scale * A_seg * op(B_seg)
+// On GB300 FP64 runs at about 1 TFLOP/s for the whole chip (scalar DFMA and the FP64 MMA alike),
+// i.e. about 7 GFLOP/s per SM, so the kernel is organised for balance rather than data reuse:
+//   - small (16 x 16) tiles so that every sector pair spreads over many SMs;
+//   - the four warps of a CTA split K (warp w takes k-step w of every 16-wide chunk) and their
+//     partial tiles are summed in shared memory in a fixed order;
+//   - tasks with a long K (many segments) are split across CTAs along segment boundaries; each part
+//     stores its partial tile and the last part to arrive (atomic ticket) sums all parts in index
+//     order, so results do not depend on scheduling.
+// Complex products use the FP64 tensor MMA (mma.sync m8n8k4 f64): four real MMAs per complex MMA.
+#include "internal.h"
+
+namespace tdmrg {
+namespace {
+
+constexpr int TS = kTileF64;     // 16
+constexpr int KC = 16;
+constexpr int PAD = TS + 4;      // row stride of the staged planes (conflict-free fragment loads)
+
+__device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int* skip_flag, int skip_step) {
+    if (skip_flag != nullptr && skip_step >= *skip_flag) return;   // Krylov space already complete
+    __shared__ double Are[TS][PAD], Aim[TS][PAD];
+    __shared__ double Bre[KC][PAD], Bim[KC][PAD];
+    __shared__ double2 red[4][TS * TS];
+    __shared__ int last;
+
+    const Tile tile = args.tiles[blockIdx.x];
+    const Task task = args.tasks[tile.task];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int m0 = tile.m0, n0 = tile.n0;
+    const int Mt = min(TS, task.M - m0), Nt = min(TS, task.N - n0);
+    bool sub[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) sub[i][j] = (8 * i < Mt) && (8 * j < Nt);
+
+    double cre[2][2][2], cim[2][2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            cre[i][j][0] = cre[i][j][1] = 0.0;
+            cim[i][j][0] = cim[i][j][1] = 0.0;
+        }
+
+    for (int s = tile.seg_lo; s < tile.seg_hi; ++s) {
+        const Seg seg = args.segs[s];
+        const cplx* __restrict__ A = args.bufs[seg.a_buf] + seg.a_off;
+        const cplx* __restrict__ B = args.bufs[seg.b_buf] + seg.b_off;
+        double sr = seg.scale.x, si = seg.scale.y;
+        if (seg.dscale >= 0) {
+            const double d = args.dscale[seg.dscale];
+            sr *= d; si *= d;
+        }
+        const bool scaled = !(sr == 1.0 && si == 0.0);
+        const double cs = seg.opb == OPB_C ? -1.0 : 1.0;
+        for (int k0 = 0; k0 < seg.K; k0 += KC) {
+            const int kc = min(KC, seg.K - k0);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {             // A chunk TS x KC: threads along k
+                const int e = tid + 128 * u, r = e / KC, k = e % KC;
+                double2 v = make_double2(0.0, 0.0);
+                if (r < Mt && k < kc) v = A[(int64_t)(m0 + r) * seg.lda + k0 + k];
+                if (scaled) v = make_double2(sr * v.x - si * v.y, sr * v.y + si * v.x);
+                Are[r][k] = v.x;
+                Aim[r][k] = v.y;
+            }
+            if (seg.opb == OPB_N) {                   // B[k][n] at B[k*ldb + n]: threads along n
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = tid + 128 * u, k = e / TS, n = e % TS;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (k < kc && n < Nt) v = B[(int64_t)(k0 + k) * seg.ldb + n0 + n];
+                    Bre[k][n] = v.x;
+                    Bim[k][n] = v.y;
+                }
+            } else {                                  // B[k][n] at B[n*ldb + k] (conjugated for 'C')
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = tid + 128 * u, n = e / KC, k = e % KC;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (k < kc && n < Nt) v = B[(int64_t)(n0 + n) * seg.ldb + k0 + k];
+                    Bre[k][n] = v.x;
+                    Bim[k][n] = cs * v.y;
+                }
+            }
+            __syncthreads();
+            const int kk = 4 * warp;
+            if (kk < kc) {
+                double ar[2], ai[2], br[2], bi[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    ar[i] = Are[8 * i + gid][kk + tig];
+                    ai[i] = Aim[8 * i + gid][kk + tig];
+                    br[i] = Bre[kk + tig][8 * i + gid];
+                    bi[i] = Bim[kk + tig][8 * i + gid];
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        if (!sub[i][j]) continue;
+                        dmma(cre[i][j][0], cre[i][j][1], ar[i], br[j]);
+                        dmma(cre[i][j][0], cre[i][j][1], -ai[i], bi[j]);
+                        dmma(cim[i][j][0], cim[i][j][1], ar[i], bi[j]);
+                        dmma(cim[i][j][0], cim[i][j][1], ai[i], br[j]);
+                    }
+            }
+            __syncthreads();
+        }
+    }
+
+    // sum the four warps' partial tiles in a fixed order
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int r = 8 * i + gid, col = 8 * j + 2 * tig + e;
+                red[warp][r * TS + col] = make_double2(cre[i][j][e], cim[i][j][e]);
+            }
+    __syncthreads();
+    double2 v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int e = tid + 128 * u;
+        double2 s = red[0][e];
+        for (int w = 1; w < 4; ++w) { s.x += red[w][e].x; s.y += red[w][e].y; }
+        v[u] = s;
+    }
+    if (tile.split >= 0) {
+        // split-K: publish this part, the last part to arrive sums all parts in index order
+        cplx* part = args.partials + ((int64_t)tile.split_base + tile.part) * (TS * TS);
+        part[tid] = v[0];
+        part[tid + 128] = v[1];
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last = (atomicAdd(args.counters + tile.split, 1) == tile.nparts - 1);
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        const cplx* base = args.partials + (int64_t)tile.split_base * (TS * TS);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = tid + 128 * u;
+            double2 s = make_double2(0.0, 0.0);
+            for (int p = 0; p < tile.nparts; ++p) {
+                const double2 x = __ldcg(base + (int64_t)p * (TS * TS) + e);
+                s.x += x.x; s.y += x.y;
+            }
+            v[u] = s;
+        }
+        if (tid == 0) args.counters[tile.split] = 0;   // ready for the next launch
+    }
+    cplx* __restrict__ C = args.bufs[task.c_buf] + task.c_off;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int e = tid + 128 * u, r = e / TS, col = e % TS;
+        if (r < Mt && col < Nt) {
+            cplx* p = C + (int64_t)(m0 + r) * task.ldc + n0 + col;
+            double2 x = v[u];
+            if (task.beta) {
+                const double2 o = *p;
+                x.x += o.x;
+                x.y += o.y;
+            }
+            *p = x;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step) {
+    if (a.ntiles <= 0) return cudaSuccess;
+    gemm_f64_kernel<<<a.ntiles, 128, 0, s>>>(a, skip_flag, skip_step);
+    return cudaGetLastError();
+}
+
+}  // namespace tdmrg

@@ -1,0 +1,192 @@
+// Internal types of libtdmrg: the sector-pair task lists that every superblock product is
+// compiled into, the context, and the kernel launchers of each translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tdmrg.h"
+
+namespace tdmrg {
+
+typedef double2 cplx;   // {re, im}, same layout as tdmrg_c64
+
+// Buffer ids a segment or task refers to; the launch passes the base pointers.
+enum BufId : int8_t { BUF_OPS = 0, BUF_IN = 1, BUF_SCRATCH = 2, BUF_OUT = 3, BUF_EXTRA0 = 4 };
+constexpr int kMaxBufs = 16;
+
+// op(B) of a segment: 'N' B[k][n] at b[k*ldb+n]; 'T' at b[n*ldb+k]; 'C' conj of 'T'.
+enum OpB : int8_t { OPB_N = 0, OPB_T = 1, OPB_C = 2 };
+
+// One contribution  scale * dscale * A[M x K] * op(B)[K x N]  to a task's output.
+struct Seg {
+    int64_t a_off, b_off;     // element offsets into buffers a_buf, b_buf
+    int32_t lda, ldb, K;
+    int8_t a_buf, b_buf, opb, pad0;
+    int32_t dscale;           // index into the launch's device real scales, -1 = none
+    cplx scale;               // static complex factor (1 = none)
+};
+
+// C[M x N] (row stride ldc, buffer c_buf) = (beta ? C : 0) + sum of segments [seg_begin, seg_end).
+struct Task {
+    int64_t c_off;
+    int32_t ldc, M, N;
+    int32_t seg_begin, seg_end;
+    int8_t c_buf, beta, pad0, pad1;
+    int32_t pad2;
+};
+
+// One CTA's work: output tile (m0, n0) (element origin) of task `task`, segments [seg_lo, seg_hi).
+// A tile whose task is split along K has split >= 0: part `part` of `nparts`, partial tiles at
+// partials[(split_base + part) * tile area], completion ticket counters[split].
+struct Tile {
+    int32_t task;
+    int32_t m0, n0;
+    int32_t cost;             // complex MACs, for ordering
+    int32_t seg_lo, seg_hi;
+    int32_t split, part, nparts, split_base;
+};
+
+// A compiled group of tasks on the device.
+struct TaskList {
+    std::vector<Task> tasks;
+    std::vector<Seg> segs;
+    std::vector<Tile> tiles;
+    Task* d_tasks = nullptr;
+    Seg* d_segs = nullptr;
+    Tile* d_tiles = nullptr;
+    double flops = 0.0;       // algorithmic real flops (8 per complex MAC)
+    size_t bytes = 0;         // device bytes of the arrays below
+    int nsplit = 0, npartial = 0;
+    cplx* d_partials = nullptr;   // split-K partial tiles
+    int* d_counters = nullptr;    // split-K tickets (zero between launches)
+};
+
+// A superblock product compiled for (terms, Q_in, Q_out): stage 1 right products, stage 2 left
+// products (see plan.cu).
+struct Plan {
+    int qin[2], qout[2];
+    int64_t n_in = 0, n_out = 0, scratch = 0;   // complex entries
+    TaskList stage1, stage2;
+    double flops = 0.0;
+};
+
+struct BlockOp {
+    int side = 0, odd = 0;
+    // (out sector, in sector) -> element offset in the op pool; dims from the sector tables
+    std::vector<std::tuple<int, int, int64_t>> blocks;
+    int version = 0;
+};
+
+struct Side {
+    std::vector<int> nup, ndn, dim;
+    std::map<std::pair<int, int>, int> index;
+    bool set = false;
+    int find(int a, int b) const {
+        auto it = index.find({a, b});
+        return it == index.end() ? -1 : it->second;
+    }
+};
+
+struct Term {           // coeff * (A P_L^{odd B}) (x) B; -1 = identity
+    int opL, opR;
+    cplx coeff;
+};
+
+struct KrylovWork {     // device workspace of tdmrg_evolve for one (Q, nk)
+    int64_t n = 0;
+    int nk = 0;
+    cplx* V = nullptr;          // (nk + 1) x n Lanczos vectors
+    cplx* w = nullptr;          // n
+    double2* partA = nullptr;   // reduction partials
+    double2* partB = nullptr;
+    double* tri = nullptr;      // alpha[32], beta[32], beta0, resid, err
+    int* flags = nullptr;       // n_used
+    cplx* coef = nullptr;       // [x][k] Krylov coefficients
+};
+
+// Launch of a grouped complex GEMM (gemm_f64.cu / gemm_ozaki.cu).
+struct GemmArgs {
+    const Task* tasks;
+    const Seg* segs;
+    const Tile* tiles;
+    int ntiles;
+    cplx* bufs[kMaxBufs];
+    const double* dscale;
+    cplx* partials;
+    int* counters;
+};
+
+}  // namespace tdmrg
+
+struct tdmrg_ctx {
+    tdmrg_opts opts;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    tdmrg::Side side[2];
+    // op pool: one device buffer holding every operator block
+    tdmrg::cplx* pool = nullptr;
+    int64_t pool_cap = 0, pool_used = 0;
+    std::map<int, tdmrg::BlockOp> ops[2];
+    bool ham_set = false;
+    std::vector<tdmrg::Term> ham;
+    int ham_version = 0;
+    std::map<std::tuple<int, int, int, int, int, int, int>, std::unique_ptr<tdmrg::Plan>> plans;
+    // generic workspace
+    tdmrg::cplx* scratch = nullptr;
+    int64_t scratch_cap = 0;
+    std::map<std::pair<int, int>, tdmrg::KrylovWork> krylov;
+    tdmrg::KrylovWork* last_krylov = nullptr;
+    // reduction / misc device buffers
+    double2* red = nullptr;        // partials for norms and dots
+    double* dscale = nullptr;      // device real scales (rho weights)
+    tdmrg::cplx* tmp = nullptr;    // apply_op temporary for expect
+    int64_t tmp_cap = 0;
+    size_t allocated = 0;
+    int num_sms = 0;
+    int64_t launches = 0;          // kernels launched by this context
+};
+
+namespace tdmrg {
+
+// error helpers (api.cu)
+int fail(tdmrg_ctx* c, int code, const std::string& msg);
+int cuda_check(tdmrg_ctx* c, cudaError_t e, const char* what);
+int dev_alloc(tdmrg_ctx* c, void** p, size_t bytes, const char* what);
+void dev_free(tdmrg_ctx* c, void* p, size_t bytes);
+
+// plan.cu
+int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qin0, int qin1, int qout0, int qout1,
+               Plan* out);
+int64_t sector_size(const tdmrg_ctx* c, int n_up, int n_dn);
+void make_tiles(TaskList& tl, int tm, int tn, int ksplit);
+int upload(tdmrg_ctx* c, TaskList& tl);
+void release(tdmrg_ctx* c, TaskList& tl);
+int run_plan(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* skip_flag, int skip_step);
+
+// gemm_f64.cu: grouped complex FP64 GEMM (FP64 MMA), tile 16 x 16, split-K above kSplitK
+constexpr int kTileF64 = 16;
+constexpr int kSplitK = 96;
+cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step);
+
+
+// krylov.cu
+int evolve(tdmrg_ctx* c, int n_up, int n_dn, const cplx* phi, int n_v, const double* t_x, int nk,
+           cplx* const* targets);
+int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta);
+cudaError_t launch_norm2(const cplx* x, int64_t n, double2* partials, int nblk, cudaStream_t s);
+cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* partials, int nblk,
+                             cplx* out, int normalise, cudaStream_t s);
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs: fixed, so reductions are deterministic
+
+// density.cu
+int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho);
+int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs);
+
+}  // namespace tdmrg

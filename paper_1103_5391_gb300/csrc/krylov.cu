@@ -1,0 +1,445 @@
+// Krylov time evolution on the device (Sec. II.A, Eq. lanczosevolution; Sec. II.C,
+// Eq. lanczosevolution2; time targets of Sec. II.B).
+//
+// Lanczos is started from phi itself: v_0 = phi / ||phi||.  Step j: w = H v_j (grouped superblock
+// product), alpha_j = Re <v_j|w>, then two classical Gram-Schmidt passes against v_0..v_j
+// (the first pass also removes the alpha_j v_j and beta_j v_{j-1} components), beta_{j+1} = ||w||,
+// v_{j+1} = w / beta_{j+1}; the recursion stops at n_K vectors or when
+// beta_{j+1} <= tol * max(1, |alpha_j|).  Then T = S^dag D S is diagonalised (one warp, cyclic
+// Jacobi, FP64) and the targets phi(t_x) = ||phi|| sum_k v_k [S^dag e^{-i D t_x} S]_{k,0} are formed
+// in one pass over V.  Everything is FP64 and stays on the device; reductions use a fixed grid and
+// a fixed summation order, so results do not depend on scheduling.
+#include <cmath>
+
+#include "internal.h"
+
+namespace tdmrg {
+namespace {
+
+constexpr int NB = kRedBlocks;   // reduction blocks
+constexpr int NT = 256;          // threads per reduction block
+enum { T_ALPHA = 0, T_BETA = 32, T_BETA0 = 64, T_RESID = 65, T_ERR = 66 };
+
+__device__ __forceinline__ void chunk_of(int64_t n, int64_t& lo, int64_t& hi) {
+    const int64_t ch = (n + NB - 1) / NB;
+    lo = min(n, (int64_t)blockIdx.x * ch);
+    hi = min(n, lo + ch);
+}
+
+// Deterministic block sum of a double2 (fixed butterfly, fixed warp order).
+__device__ double2 block_sum(double2 v) {
+    __shared__ double2 sh[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < NT / 32; ++k) { s.x += sh[k].x; s.y += sh[k].y; }
+    return s;   // every thread holds the block total
+}
+
+// Sum of part[0..NB-1] by one warp in a fixed order (identical in every block that calls it).
+__device__ double2 warp_total(const double2* __restrict__ part) {
+    const int l = threadIdx.x & 31;
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = l; b < NB; b += 32) { s.x += part[b].x; s.y += part[b].y; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    return s;
+}
+
+// h[k] = sum of partials of vector k, for k < nv; every block computes the same values.
+__device__ void reduce_coeffs(const double2* __restrict__ part, int nv, double2* h) {
+    const int w = threadIdx.x >> 5;
+    for (int k = w; k < nv; k += NT / 32) {
+        double2 s = warp_total(part + (int64_t)k * NB);
+        if ((threadIdx.x & 31) == 0) h[k] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdotc(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__global__ void __launch_bounds__(NT) k_norm2(const cplx* __restrict__ x, int64_t n, double2* __restrict__ part) {
+    int64_t lo, hi;
+    chunk_of(n, lo, hi);
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = x[i]; s += v.x * v.x + v.y * v.y; }
+    double2 t = block_sum(make_double2(s, 0.0));
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_init_v0(const cplx* __restrict__ phi, int64_t n, const double2* __restrict__ part,
+                                                 cplx* __restrict__ v0, double* __restrict__ tri, int* __restrict__ flags,
+                                                 int nk) {
+    __shared__ double2 h[1];
+    reduce_coeffs(part, 1, h);
+    const double b0 = sqrt(h[0].x);
+    const double inv = b0 > 0.0 ? 1.0 / b0 : 0.0;
+    int64_t lo, hi;
+    chunk_of(n, lo, hi);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = phi[i]; v0[i] = make_double2(v.x * inv, v.y * inv); }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        tri[T_BETA0] = b0;
+        tri[T_RESID] = 0.0;
+        flags[0] = b0 > 0.0 ? nk : 0;
+    }
+}
+
+// Pass 0: partials of <v_k|w>, k < nv.
+__global__ void __launch_bounds__(NT) k_dots(const cplx* __restrict__ V, int nv, int64_t n, const cplx* __restrict__ w,
+                                              double2* __restrict__ part, const int* __restrict__ flags, int j) {
+    if (j >= flags[0]) return;
+    int64_t lo, hi;
+    chunk_of(n, lo, hi);
+    for (int k = 0; k < nv; ++k) {
+        const cplx* vk = V + (int64_t)k * n;
+        double2 s = make_double2(0.0, 0.0);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
+            const double2 p = cdotc(vk[i], w[i]);
+            s.x += p.x; s.y += p.y;
+        }
+        double2 t = block_sum(s);
+        if (threadIdx.x == 0) part[(int64_t)k * NB + blockIdx.x] = t;
+    }
+}
+
+// w -= sum_k h_k v_k with h from partIn; then partials of <v_k|w> (final = 0) or of ||w||^2 (final = 1).
+__global__ void __launch_bounds__(NT) k_orth(const cplx* __restrict__ V, int nv, int64_t n, cplx* __restrict__ w,
+                                              const double2* __restrict__ partIn, double2* __restrict__ partOut,
+                                              double* __restrict__ tri, const int* __restrict__ flags, int j,
+                                              int record_alpha, int final_norm) {
+    if (j >= flags[0]) return;
+    __shared__ double2 h[33];
+    reduce_coeffs(partIn, nv, h);
+    if (record_alpha && blockIdx.x == 0 && threadIdx.x == 0) tri[T_ALPHA + j] = h[j].x;
+    int64_t lo, hi;
+    chunk_of(n, lo, hi);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
+        double2 x = w[i];
+        for (int k = 0; k < nv; ++k) {
+            const double2 p = cmul(h[k], V[(int64_t)k * n + i]);
+            x.x -= p.x; x.y -= p.y;
+        }
+        w[i] = x;
+    }
+    __syncthreads();
+    if (final_norm) {
+        double s = 0.0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = w[i]; s += v.x * v.x + v.y * v.y; }
+        double2 t = block_sum(make_double2(s, 0.0));
+        if (threadIdx.x == 0) partOut[blockIdx.x] = t;
+    } else {
+        for (int k = 0; k < nv; ++k) {
+            const cplx* vk = V + (int64_t)k * n;
+            double2 s = make_double2(0.0, 0.0);
+            for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
+                const double2 p = cdotc(vk[i], w[i]);
+                s.x += p.x; s.y += p.y;
+            }
+            double2 t = block_sum(s);
+            if (threadIdx.x == 0) partOut[(int64_t)k * NB + blockIdx.x] = t;
+        }
+    }
+}
+
+// beta_{j+1} = ||w||; v_{j+1} = w / beta_{j+1}, or stop (last step or breakdown).
+__global__ void __launch_bounds__(NT) k_normalize(const cplx* __restrict__ w, int64_t n, const double2* __restrict__ part,
+                                                   cplx* __restrict__ vnext, double* __restrict__ tri, int* __restrict__ flags,
+                                                   int j, int nk, double tol) {
+    if (j >= flags[0]) return;
+    __shared__ double2 h[1];
+    reduce_coeffs(part, 1, h);
+    const double beta = sqrt(h[0].x);
+    const double alpha = tri[T_ALPHA + j];
+    const bool stop = (j == nk - 1) || (beta <= tol * fmax(1.0, fabs(alpha)));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        tri[T_BETA + j] = beta;
+        if (stop) {
+            tri[T_RESID] = beta;
+            flags[0] = j + 1;
+        }
+    }
+    if (stop) return;
+    const double inv = 1.0 / beta;
+    int64_t lo, hi;
+    chunk_of(n, lo, hi);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = w[i]; vnext[i] = make_double2(v.x * inv, v.y * inv); }
+}
+
+struct Times { double t[16]; };
+
+// T = S^dag D S by cyclic Jacobi (one warp), then c_x[k] = beta0 [S^dag e^{-i D t_x} S]_{k,0}.
+__global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, const int* __restrict__ flags,
+                                                     Times times, int n_v, cplx* __restrict__ coef) {
+    __shared__ double T[32][33], S[32][33];
+    __shared__ double2 ph[16][32];
+    const int l = threadIdx.x;
+    const int n = flags[0];
+    const double b0 = tri[T_BETA0];
+    for (int x = 0; x < n_v; ++x) coef[x * 32 + l] = make_double2(0.0, 0.0);
+    if (n <= 0) {
+        if (l == 0) tri[T_ERR] = 0.0;
+        return;
+    }
+    for (int r = 0; r < n; ++r) {
+        if (l < n) {
+            double v = 0.0;
+            if (l == r) v = tri[T_ALPHA + r];
+            else if (l == r + 1) v = tri[T_BETA + r];
+            else if (l + 1 == r) v = tri[T_BETA + l];
+            T[r][l] = v;
+            S[r][l] = (l == r) ? 1.0 : 0.0;
+        }
+    }
+    __syncwarp();
+    // threshold Jacobi: rotate only entries above 2 eps ||T||_F (smaller ones are set to zero);
+    // stop after a sweep without rotations (quadratic convergence, a handful of sweeps)
+    double fro = 0.0;
+    for (int r = 0; r < n; ++r)
+        if (l < n) fro += T[r][l] * T[r][l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    const double thr = 2.220446049250313e-16 * sqrt(fro);
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = T[p][q];
+                if (fabs(apq) <= thr) {
+                    __syncwarp();
+                    if (l == 0) { T[p][q] = 0.0; T[q][p] = 0.0; }
+                    __syncwarp();
+                    continue;
+                }
+                rotated = 1;
+                const double theta = (T[q][q] - T[p][p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                __syncwarp();
+                if (l < n) {   // columns: A <- A J
+                    const double akp = T[l][p], akq = T[l][q];
+                    T[l][p] = c * akp - s * akq;
+                    T[l][q] = s * akp + c * akq;
+                }
+                __syncwarp();
+                if (l < n) {   // rows: A <- J^T A
+                    const double apk = T[p][l], aqk = T[q][l];
+                    T[p][l] = c * apk - s * aqk;
+                    T[q][l] = s * apk + c * aqk;
+                    const double vkp = S[l][p], vkq = S[l][q];
+                    S[l][p] = c * vkp - s * vkq;
+                    S[l][q] = s * vkp + c * vkq;
+                }
+                __syncwarp();
+            }
+        if (!rotated) break;
+    }
+    // phases e^{-i d_m t_x}
+    for (int x = 0; x < n_v; ++x)
+        if (l < n) {
+            double sn, cs;
+            sincos(T[l][l] * times.t[x], &sn, &cs);
+            ph[x][l] = make_double2(cs, -sn);
+        }
+    __syncwarp();
+    double tmax = 0.0;
+    int xmax = 0;
+    for (int x = 0; x < n_v; ++x)
+        if (times.t[x] > tmax) { tmax = times.t[x]; xmax = x; }
+    for (int x = 0; x < n_v; ++x) {
+        if (l < n) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int m = 0; m < n; ++m) {
+                const double f = S[l][m] * S[0][m];
+                acc.x += f * ph[x][m].x;
+                acc.y += f * ph[x][m].y;
+            }
+            coef[x * 32 + l] = make_double2(b0 * acc.x, b0 * acc.y);
+            if (x == xmax && l == n - 1) tri[T_ERR] = tri[T_RESID] * b0 * sqrt(acc.x * acc.x + acc.y * acc.y);
+        }
+    }
+}
+
+struct TargetPtrs { cplx* p[16]; };
+
+// targets[x][i] = sum_k coef[x][k] v_k[i]: one pass over V, n_v outputs.
+__global__ void __launch_bounds__(256) k_combine(const cplx* __restrict__ V, int64_t n, const int* __restrict__ flags,
+                                                  const cplx* __restrict__ coef, int n_v, TargetPtrs tg) {
+    __shared__ double2 cf[16][32];
+    const int nu = flags[0];
+    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) cf[e / 32][e % 32] = (e / 32 < n_v) ? coef[e] : make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc[16];
+#pragma unroll
+        for (int x = 0; x < 16; ++x) acc[x] = make_double2(0.0, 0.0);
+        for (int k = 0; k < nu; ++k) {
+            const double2 v = V[(int64_t)k * n + i];
+#pragma unroll
+            for (int x = 0; x < 16; ++x) {
+                if (x < n_v) {
+                    const double2 p = cmul(cf[x][k], v);
+                    acc[x].x += p.x; acc[x].y += p.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 16; ++x)
+            if (x < n_v) tg.p[x][i] = acc[x];
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_dot2(const cplx* __restrict__ x, const cplx* __restrict__ y, int64_t n,
+                                              double2* __restrict__ part) {
+    int64_t lo, hi;
+    chunk_of(n, lo, hi);
+    double2 s = make_double2(0.0, 0.0);
+    double nn = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
+        const double2 a = x[i];
+        const double2 p = cdotc(a, y[i]);
+        s.x += p.x; s.y += p.y;
+        nn += a.x * a.x + a.y * a.y;
+    }
+    double2 t = block_sum(s);
+    double2 u = block_sum(make_double2(nn, 0.0));
+    if (threadIdx.x == 0) { part[blockIdx.x] = t; part[NB + blockIdx.x] = u; }
+}
+
+__global__ void __launch_bounds__(NT) k_dot_final(const double2* __restrict__ part, cplx* __restrict__ out, int normalise) {
+    __shared__ double2 h[2];
+    reduce_coeffs(part, 2, h);
+    if (threadIdx.x == 0) {
+        double2 v = h[0];
+        if (normalise) {
+            const double d = h[1].x > 0.0 ? 1.0 / h[1].x : 0.0;
+            v.x *= d; v.y *= d;
+        }
+        *out = v;
+    }
+}
+
+int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out) {
+    auto key = std::make_pair(a * 4096 + b, nk);
+    auto it = c->krylov.find(key);
+    if (it != c->krylov.end() && it->second.n == n) { *out = &it->second; return TDMRG_OK; }
+    KrylovWork k;
+    k.n = n;
+    k.nk = nk;
+    int rc = dev_alloc(c, (void**)&k.V, (size_t)(nk + 1) * n * sizeof(cplx), "Krylov vectors");
+    if (!rc) rc = dev_alloc(c, (void**)&k.w, (size_t)n * sizeof(cplx), "Krylov residual");
+    if (!rc) rc = dev_alloc(c, (void**)&k.partA, 64 * kRedBlocks * sizeof(double2), "Krylov partials");
+    if (!rc) rc = dev_alloc(c, (void**)&k.partB, 64 * kRedBlocks * sizeof(double2), "Krylov partials");
+    if (!rc) rc = dev_alloc(c, (void**)&k.tri, 128 * sizeof(double), "Krylov tridiagonal");
+    if (!rc) rc = dev_alloc(c, (void**)&k.flags, 4 * sizeof(int), "Krylov flags");
+    if (!rc) rc = dev_alloc(c, (void**)&k.coef, 16 * 32 * sizeof(cplx), "Krylov coefficients");
+    if (rc) {
+        dev_free(c, k.V, (size_t)(nk + 1) * n * sizeof(cplx));
+        dev_free(c, k.w, (size_t)n * sizeof(cplx));
+        dev_free(c, k.partA, 64 * kRedBlocks * sizeof(double2));
+        dev_free(c, k.partB, 64 * kRedBlocks * sizeof(double2));
+        dev_free(c, k.tri, 128 * sizeof(double));
+        dev_free(c, k.flags, 4 * sizeof(int));
+        dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
+        return rc;
+    }
+    c->krylov[key] = k;
+    *out = &c->krylov[key];
+    return TDMRG_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_norm2(const cplx* x, int64_t n, double2* partials, int nblk, cudaStream_t s) {
+    (void)nblk;
+    k_norm2<<<NB, NT, 0, s>>>(x, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* partials, int nblk, cplx* out,
+                             int normalise, cudaStream_t s) {
+    (void)nblk;
+    k_dot2<<<NB, NT, 0, s>>>(x, y, n, partials);
+    k_dot_final<<<1, NT, 0, s>>>(partials, out, normalise);
+    return cudaGetLastError();
+}
+
+int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t_x, int nk, cplx* const* targets) {
+    int64_t n = sector_size(c, a, b);
+    if (n == 0) return fail(c, TDMRG_ESECTOR, "evolve: empty sector");
+    Plan* p = nullptr;
+    {
+        auto key = std::make_tuple(0, -1, -1, a, b, a, b);
+        auto it = c->plans.find(key);
+        if (it == c->plans.end()) {
+            std::unique_ptr<Plan> np(new Plan());
+            int rc = build_plan(c, c->ham, a, b, a, b, np.get());
+            if (rc) { release(c, np->stage1); release(c, np->stage2); return rc; }
+            p = np.get();
+            c->plans[key] = std::move(np);
+        } else {
+            p = it->second.get();
+        }
+    }
+    KrylovWork* k = nullptr;
+    int rc = ensure_work(c, a, b, nk, n, &k);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    Times tt{};
+    for (int x = 0; x < n_v; ++x) tt.t[x] = t_x[x];
+    k_norm2<<<NB, NT, 0, s>>>(phi, n, k->partA);
+    k_init_v0<<<NB, NT, 0, s>>>(phi, n, k->partA, k->V, k->tri, k->flags, nk);
+    c->launches += 2;
+    for (int j = 0; j < nk; ++j) {
+        cplx* vj = k->V + (int64_t)j * n;
+        rc = run_plan(c, *p, vj, k->w, k->flags, j);
+        if (rc) return rc;
+        k_dots<<<NB, NT, 0, s>>>(k->V, j + 1, n, k->w, k->partA, k->flags, j);
+        k_orth<<<NB, NT, 0, s>>>(k->V, j + 1, n, k->w, k->partA, k->partB, k->tri, k->flags, j, 1, 0);
+        k_orth<<<NB, NT, 0, s>>>(k->V, j + 1, n, k->w, k->partB, k->partA, k->tri, k->flags, j, 0, 1);
+        k_normalize<<<NB, NT, 0, s>>>(k->w, n, k->partA, k->V + (int64_t)(j + 1) * n, k->tri, k->flags, j, nk,
+                                      c->opts.breakdown_tol);
+        c->launches += 4;
+    }
+    k_tridiag_exp<<<1, 32, 0, s>>>(k->tri, k->flags, tt, n_v, k->coef);
+    TargetPtrs tg{};
+    for (int x = 0; x < n_v; ++x) tg.p[x] = targets[x];
+    int grid = (int)std::min<int64_t>((n + 255) / 256, 4L * c->num_sms);
+    k_combine<<<grid, 256, 0, s>>>(k->V, n, k->flags, k->coef, n_v, tg);
+    c->launches += 2;
+    c->last_krylov = k;
+    return cuda_check(c, cudaGetLastError(), "evolve launch");
+}
+
+int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta) {
+    KrylovWork* k = c->last_krylov;
+    double tri[128];
+    int flags[4];
+    int rc = cuda_check(c, cudaMemcpyAsync(tri, k->tri, sizeof(tri), cudaMemcpyDeviceToHost, c->stream), "evolve_info");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(flags, k->flags, sizeof(flags), cudaMemcpyDeviceToHost, c->stream), "evolve_info");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "evolve_info sync");
+    if (rc) return rc;
+    if (nk_used) *nk_used = flags[0];
+    if (err) *err = tri[T_ERR];
+    for (int j = 0; j < flags[0]; ++j) {
+        if (alpha) alpha[j] = tri[T_ALPHA + j];
+        if (beta) beta[j] = tri[T_BETA + j];
+    }
+    return TDMRG_OK;
+}
+
+}  // namespace tdmrg

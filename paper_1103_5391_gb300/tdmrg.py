@@ -1,0 +1,247 @@
+"""ctypes binding of libtdmrg (include/tdmrg.h): same names, argument marshalling only.
+
+Vectors are torch.complex128 CUDA tensors (device pointers); every step of the
+path runs in the library's kernels.  Loading fails loudly when libtdmrg.so is
+missing: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdmrg.so")
+
+TDMRG_OK, TDMRG_EINVAL, TDMRG_ENOMEM, TDMRG_ESECTOR, TDMRG_ECUDA, TDMRG_ETIMEOUT, TDMRG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+TDMRG_LEFT, TDMRG_RIGHT = 0, 1
+TDMRG_FP64, TDMRG_OZAKI_BF16 = 0, 1
+
+EXPORTED = [
+    "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
+    "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
+    "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect",
+    "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_fp64_peak",
+]
+
+
+class tdmrg_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("prec", ctypes.c_int),
+                ("ozaki_slices", ctypes.c_int), ("nk_max", ctypes.c_int), ("breakdown_tol", ctypes.c_double),
+                ("hbm_budget", ctypes.c_size_t)]
+
+
+class TdmrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tdmrg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libtdmrg.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    PI32, PD, PI64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "tdmrg_default_opts": (None, [ctypes.POINTER(tdmrg_opts)]),
+        "tdmrg_create": (I, [ctypes.POINTER(P), ctypes.POINTER(tdmrg_opts)]),
+        "tdmrg_destroy": (I, [P]),
+        "tdmrg_set_stream": (I, [P, P]),
+        "tdmrg_set_precision": (I, [P, I, I]),
+        "tdmrg_last_error": (ctypes.c_char_p, [P]),
+        "tdmrg_set_block": (I, [P, I, I, PI32, PI32]),
+        "tdmrg_set_op": (I, [P, I, I, I, I, PI32, P, I]),
+        "tdmrg_set_hamiltonian": (I, [P, I, I, I, PI32, PI32, P]),
+        "tdmrg_sector_size": (I, [P, I, I, PI64]),
+        "tdmrg_apply_h": (I, [P, I, I, P, P]),
+        "tdmrg_apply_op": (I, [P, I, I, I, I, P, I, I, P]),
+        "tdmrg_evolve": (I, [P, I, I, P, I, PD, I, ctypes.POINTER(P)]),
+        "tdmrg_evolve_info": (I, [P, ctypes.POINTER(I), PD, PD, PD]),
+        "tdmrg_tst_weights": (I, [I, PD, PD]),
+        "tdmrg_rho_size": (I, [P, PI64, PI64]),
+        "tdmrg_density_matrix": (I, [P, I, PI32, ctypes.POINTER(P), PD, P]),
+        "tdmrg_rho_eig": (I, [P, P, P, P]),
+        "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
+        "tdmrg_launch_count": (I, [P, PI64]),
+        "tdmrg_hpsi_flops": (I, [P, I, I, PD]),
+        "tdmrg_fp64_peak": (I, [I, PD, PD]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, rc):
+    if rc != TDMRG_OK:
+        msg = load().tdmrg_last_error(ctx)
+        raise TdmrgError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda:
+            raise ValueError("device vectors must be CUDA tensors")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+# ----------------------------------------------------------------------------- calls
+def tdmrg_default_opts():
+    o = tdmrg_opts()
+    load().tdmrg_default_opts(ctypes.byref(o))
+    return o
+
+
+def tdmrg_create(opts=None, **kw):
+    o = opts or tdmrg_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    _check(None, load().tdmrg_create(ctypes.byref(h), ctypes.byref(o)))
+    return h
+
+
+def tdmrg_destroy(ctx):
+    return _check(ctx, load().tdmrg_destroy(ctx))
+
+
+def tdmrg_set_stream(ctx, stream):
+    return _check(ctx, load().tdmrg_set_stream(ctx, ctypes.c_void_p(stream)))
+
+
+def tdmrg_set_precision(ctx, prec, slices=4):
+    return _check(ctx, load().tdmrg_set_precision(ctx, prec, slices))
+
+
+def tdmrg_last_error(ctx):
+    m = load().tdmrg_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def tdmrg_set_block(ctx, side, qn, dims):
+    q, qp = _i32(np.asarray(qn).reshape(-1))
+    d, dp = _i32(dims)
+    return _check(ctx, load().tdmrg_set_block(ctx, side, len(d), qp, dp))
+
+
+def tdmrg_set_op(ctx, side, op_id, odd, blocks):
+    """blocks: list of ((out_up, out_dn), (in_up, in_dn), 2-D complex array)."""
+    qn = []
+    parts = []
+    for qo, qi, blk in blocks:
+        qn.extend([qo[0], qo[1], qi[0], qi[1]])
+        parts.append(np.ascontiguousarray(np.asarray(blk, dtype=np.complex128)).reshape(-1))
+    q, qp = _i32(qn if qn else [0])
+    data = np.concatenate(parts) if parts else np.zeros(1, np.complex128)
+    return _check(ctx, load().tdmrg_set_op(ctx, side, op_id, int(odd), len(blocks), qp,
+                                           data.ctypes.data_as(ctypes.c_void_p), 0))
+
+
+def tdmrg_set_hamiltonian(ctx, opHL, opHR, conns):
+    """conns: list of (opL, opR, complex coeff)."""
+    n = len(conns)
+    oL, pL = _i32([c[0] for c in conns] or [0])
+    oR, pR = _i32([c[1] for c in conns] or [0])
+    co = np.array([complex(c[2]) for c in conns] or [0j], dtype=np.complex128)
+    return _check(ctx, load().tdmrg_set_hamiltonian(ctx, opHL, opHR, n, pL, pR, co.ctypes.data_as(ctypes.c_void_p)))
+
+
+def tdmrg_sector_size(ctx, Q):
+    n = ctypes.c_int64()
+    _check(ctx, load().tdmrg_sector_size(ctx, Q[0], Q[1], ctypes.byref(n)))
+    return n.value
+
+
+def tdmrg_apply_h(ctx, Q, psi, out):
+    return _check(ctx, load().tdmrg_apply_h(ctx, Q[0], Q[1], _ptr(psi), _ptr(out)))
+
+
+def tdmrg_apply_op(ctx, opL, opR, Q_in, psi, Q_out, out):
+    return _check(ctx, load().tdmrg_apply_op(ctx, opL, opR, Q_in[0], Q_in[1], _ptr(psi), Q_out[0], Q_out[1], _ptr(out)))
+
+
+def tdmrg_evolve(ctx, Q, phi, times, nk, targets):
+    t = np.ascontiguousarray(np.asarray(times, dtype=np.float64))
+    arr = (ctypes.c_void_p * len(targets))(*[_ptr(x) for x in targets])
+    return _check(ctx, load().tdmrg_evolve(ctx, Q[0], Q[1], _ptr(phi), len(t),
+                                           t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nk, arr))
+
+
+def tdmrg_evolve_info(ctx, nk_max=32):
+    n = ctypes.c_int()
+    err = ctypes.c_double()
+    a = np.zeros(nk_max)
+    b = np.zeros(nk_max)
+    _check(ctx, load().tdmrg_evolve_info(ctx, ctypes.byref(n), ctypes.byref(err),
+                                         a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return n.value, err.value, a[:n.value], b[:n.value]
+
+
+def tdmrg_tst_weights(n_v):
+    wgs = ctypes.c_double()
+    w = np.zeros(max(n_v, 1))
+    _check(None, load().tdmrg_tst_weights(n_v, ctypes.byref(wgs), w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return wgs.value, w[:n_v].tolist()
+
+
+def tdmrg_rho_size(ctx):
+    r, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load().tdmrg_rho_size(ctx, ctypes.byref(r), ctypes.byref(e)))
+    return r.value, e.value
+
+
+def tdmrg_density_matrix(ctx, states, weights, rho):
+    """states: list of (Q, tensor)."""
+    q, qp = _i32([x for Q, _ in states for x in Q])
+    arr = (ctypes.c_void_p * len(states))(*[_ptr(v) for _, v in states])
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    return _check(ctx, load().tdmrg_density_matrix(ctx, len(states), qp, arr,
+                                                   w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
+
+
+def tdmrg_rho_eig(ctx, rho, evals, evecs):
+    return _check(ctx, load().tdmrg_rho_eig(ctx, _ptr(rho), _ptr(evals), _ptr(evecs)))
+
+
+def tdmrg_expect(ctx, opL, opR, Q, psi, out):
+    return _check(ctx, load().tdmrg_expect(ctx, opL, opR, Q[0], Q[1], _ptr(psi), _ptr(out)))
+
+
+def tdmrg_launch_count(ctx):
+    n = ctypes.c_int64()
+    _check(ctx, load().tdmrg_launch_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def tdmrg_hpsi_flops(ctx, Q):
+    f = ctypes.c_double()
+    _check(ctx, load().tdmrg_hpsi_flops(ctx, Q[0], Q[1], ctypes.byref(f)))
+    return f.value
+
+
+def tdmrg_fp64_peak(device=0):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(None, load().tdmrg_fp64_peak(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

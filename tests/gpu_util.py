@@ -1,0 +1,77 @@
+"""Helpers of the GPU parity tests: load oracle problems into libtdmrg and compare."""
+import numpy as np
+import pytest
+
+from oracle import blocks as oblocks
+from oracle import superblock
+
+
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    return torch
+
+
+def new_ctx(**kw):
+    from paper_1103_5391_gb300 import tdmrg as T
+    torch = torch_cuda()
+    return T.tdmrg_create(device=torch.cuda.current_device(),
+                          stream=torch.cuda.current_stream().cuda_stream, **kw)
+
+
+def dev(x):
+    torch = torch_cuda()
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.complex128)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def oracle_ops_of_synthetic(ss):
+    HL = oblocks.BlockOp(ss.HL, False)
+    HR = oblocks.BlockOp(ss.HR, False)
+    conns = []
+    for b in range(ss.nbonds):
+        for s in range(2):
+            A = oblocks.BlockOp(ss.cdagL[b][s], True)
+            B = oblocks.BlockOp(ss.cR[b][s], True)
+            conns.append((ss.coeff_t, A, B))
+            conns.append((-ss.coeff_t, A.dagger(), B.dagger()))
+    sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
+    return sb, HL, HR, conns
+
+
+class ExactLoader:
+    """Loads an oracle.models.ExactProblem: H and arbitrary local operators by id."""
+
+    def __init__(self, ctx, prob):
+        from paper_1103_5391_gb300 import tdmrg as T
+        self.T, self.ctx, self.p = T, ctx, prob
+        T.tdmrg_set_block(ctx, 0, prob.sb.lsec, prob.sb.ldim)
+        T.tdmrg_set_block(ctx, 1, prob.sb.rsec, prob.sb.rdim)
+        self.next_id = [100, 100]
+        hl = self.add(0, prob.HL)
+        hr = self.add(1, prob.HR)
+        conns = []
+        for coeff, A, B in prob.conns:
+            conns.append((self.add(0, A), self.add(1, B), coeff))
+        T.tdmrg_set_hamiltonian(ctx, hl, hr, conns)
+
+    def add(self, side, op):
+        sec = self.p.sb.lsec if side == 0 else self.p.sb.rsec
+        i = self.next_id[side]
+        self.next_id[side] += 1
+        blks = [(sec[qo], sec[qi], b) for (qo, qi), b in op.blocks.items()]
+        self.T.tdmrg_set_op(self.ctx, side, i, op.odd, blks)
+        return i
+
+    def local(self, kind, site, sigma=0):
+        side, op = self.p.op(kind, site, sigma)
+        i = self.add(side, op)
+        return (i, -1) if side == 0 else (-1, i)
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)

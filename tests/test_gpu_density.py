@@ -1,0 +1,88 @@
+"""GPU parity of the weighted reduced density matrix (Eq. rdensitymatrix, weights of Sec. II.C) and
+of its FP64 Jacobi eigendecomposition against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import density, superblock
+from tests.gpu_util import dev, host, new_ctx
+from workloads import sectors as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1103_5391_gb300 import tdmrg as T
+    return T
+
+
+def _states(ss, nv, seed):
+    rng = np.random.default_rng(seed)
+    sts = [(ss.Q0, ss.psi_gs)]
+    for x in range(nv):
+        n = ss.sector_size(ss.Q1)
+        sts.append((ss.Q1, (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * (x + 1)))
+    return sts
+
+
+@pytest.mark.parametrize("L,m,nb", [(8, 24, 1), (32, 400, 1), (32, 800, 2)])
+def test_rho_and_eig(lib, L, m, nb):
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(L, m, 4.0, nbonds=nb, seed=S.SEED_BASE + 7)
+    sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
+    wgs, w = density.tst_weights(4)
+    sts = _states(ss, 4, 1)
+    weights = [wgs] + w
+    ref = density.rho_left(sb, sts, weights)
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        nr, ne = lib.tdmrg_rho_size(ctx)
+        assert nr == sum(d * d for d in ss.ldim) and ne == sum(ss.ldim)
+        rho = dev(np.full(nr, np.nan + 0j))
+        dsts = [(Q, dev(v)) for Q, v in sts]
+        lib.tdmrg_density_matrix(ctx, dsts, weights, rho)
+        got = host(rho)
+        off = 0
+        tr = 0.0
+        for qi, d in enumerate(ss.ldim):
+            blk = got[off: off + d * d].reshape(d, d)
+            assert np.abs(blk - ref[qi]).max() < 1e-14
+            tr += np.trace(blk).real
+            off += d * d
+        assert abs(tr - 1.0) < 1e-13
+        torch = pytest.importorskip("torch")
+        ev = torch.zeros(ne, dtype=torch.float64, device="cuda")
+        U = dev(np.zeros(nr))
+        lib.tdmrg_rho_eig(ctx, rho, ev, U)
+        ev, U = ev.cpu().numpy(), host(U)
+        off = eo = 0
+        for (lam, V), d, r in zip(density.rho_eig(ref), ss.ldim, ref):
+            g_l = ev[eo: eo + d]
+            g_U = U[off: off + d * d].reshape(d, d)
+            assert np.abs(g_l - lam).max() < 1e-13
+            assert np.abs(g_U @ np.diag(g_l) @ g_U.conj().T - r).max() < 1e-13
+            assert np.abs(g_U.conj().T @ g_U - np.eye(d)).max() < 1e-12
+            off += d * d
+            eo += d
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
+def test_expect(lib):
+    from paper_1103_5391_gb300 import problem
+    from oracle import blocks as oblocks
+    ss = S.make_synthetic(16, 100, 4.0, nbonds=1, seed=31)
+    sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        out = dev(np.zeros(1))
+        for a, b, A, B in ((problem.OP_N, -1, oblocks.BlockOp(ss.nL, False), None),
+                           (-1, problem.OP_N, None, oblocks.BlockOp(ss.nR, False)),
+                           (problem.OP_N, problem.OP_N, oblocks.BlockOp(ss.nL, False), oblocks.BlockOp(ss.nR, False))):
+            lib.tdmrg_expect(ctx, a, b, ss.Q0, dev(ss.psi_gs * 3.0), out)
+            want = superblock.expect(sb, A, B, ss.Q0, ss.psi_gs)
+            assert abs(host(out)[0] - want) < 1e-14
+    finally:
+        lib.tdmrg_destroy(ctx)
