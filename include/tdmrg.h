@@ -176,6 +176,23 @@ int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg
 int tdmrg_expect(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdmrg_c64* psi_d,
                  tdmrg_c64* out_d);
 
+/* H psi that allocates no device memory during the call.  The paper has no counterpart: this exists
+ * for callers that may not allocate once they run -- a real-time loop that forbids allocation after
+ * initialisation, a framework whose own pool owns all device memory, a plugin limited to the buffers
+ * it is handed.  Same arithmetic, kernel and result as tdmrg_apply_h (out_d = H psi_d in sector Q);
+ * the scratch (stage-1 intermediates, split-K partial tiles and tickets) lives in a file-scope
+ * static device array of 32 MiB that every GPU loading the library holds until the process exits.
+ *   - The sector must be prepared during set-up by one tdmrg_apply_h or tdmrg_hpsi_flops call for
+ *     Q (those may allocate); otherwise TDMRG_ESTATE.
+ *   - A sector whose scratch exceeds 32 MiB is rejected with TDMRG_ENOMEM and a message giving the
+ *     bytes it needs.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's contents (the tickets are
+ *     cleared on the stream at every call): calls whose work overlaps on the GPU, from any context
+ *     or stream, race -- serialise them. */
+int tdmrg_apply_h_static(tdmrg_ctx* ctx, int n_up, int n_dn, const tdmrg_c64* psi_d, tdmrg_c64* out_d);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ EXPORTED = [
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect",
-    "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_fp64_peak",
+    "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
 ]
 
 
@@ -73,6 +73,7 @@ def load(path=LIB_PATH):
         "tdmrg_launch_count": (I, [P, PI64]),
         "tdmrg_hpsi_flops": (I, [P, I, I, PD]),
         "tdmrg_fp64_peak": (I, [I, PD, PD]),
+        "tdmrg_apply_h_static": (I, [P, I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -245,3 +246,8 @@ def tdmrg_fp64_peak(device=0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(None, load().tdmrg_fp64_peak(device, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def tdmrg_apply_h_static(ctx, Q, psi, out):
+    """H psi with scratch from the library's static device array (no allocation during the call)."""
+    return _check(ctx, load().tdmrg_apply_h_static(ctx, Q[0], Q[1], _ptr(psi), _ptr(out)))
