@@ -170,6 +170,7 @@ int tdmrg_destroy(tdmrg_ctx* c) {
     cudaStreamSynchronize(c->stream);
     drop_plans(c);
     drop_krylov(c);
+    release_eig(c);
     dev_free(c, c->pool, c->pool_cap * sizeof(cplx));
     dev_free(c, c->scratch, c->scratch_cap * sizeof(cplx));
     dev_free(c, c->tmp, c->tmp_cap * sizeof(cplx));
@@ -214,6 +215,7 @@ int tdmrg_set_block(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const i
     s.set = true;
     DeviceGuard g(c->opts.device);
     cudaStreamSynchronize(c->stream);
+    if (side == 0) release_eig(c);
     c->side[side] = s;
     c->ops[side].clear();
     c->ham_set = false;

@@ -111,6 +111,19 @@ struct KrylovWork {     // device workspace of tdmrg_evolve for one (Q, nk)
     cplx* coef = nullptr;       // [x][k] Krylov coefficients
 };
 
+// Workspace of the rho_L eigensolver (eig.cu), built once per left block.
+struct EigWork {
+    bool ready = false;
+    int64_t nrho = 0, nev = 0;
+    int maxn = 0, ns = 0;
+    void* tables = nullptr;     // per-sector offsets and dims
+    cplx* buf = nullptr;        // 6 packed matrices: X, AX, Xh, S, G, E1
+    double* lam = nullptr;
+    double* fro = nullptr;
+    float2* gwork = nullptr;    // FP32 Jacobi storage for sectors too large for shared memory
+    TaskList tl_ax, tl_sg, tl_y;
+};
+
 // Launch of a grouped complex GEMM (gemm_f64.cu / gemm_ozaki.cu).
 struct GemmArgs {
     const Task* tasks;
@@ -151,6 +164,7 @@ struct tdmrg_ctx {
     size_t allocated = 0;
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
+    tdmrg::EigWork eig;
 };
 
 namespace tdmrg {
@@ -187,6 +201,9 @@ constexpr int kRedBlocks = 304;   // 2 x 152 SMs: fixed, so reductions are deter
 
 // density.cu
 int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho);
+
+// eig.cu
 int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs);
+void release_eig(tdmrg_ctx* c);
 
 }  // namespace tdmrg

@@ -206,47 +206,68 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, co
         }
     }
     __syncwarp();
-    // threshold Jacobi: rotate only entries above 2 eps ||T||_F (smaller ones are set to zero);
-    // stop after a sweep without rotations (quadratic convergence, a handful of sweeps)
+    // threshold Jacobi: rotate only entries above 2 eps ||T||_F (smaller ones are set to zero),
+    // stop after a sweep without rotations.  Disjoint pairs of each round (circle method) are
+    // rotated at once, one lane per pair, so a sweep costs n-1 rotation latencies, not n(n-1)/2.
+    __shared__ int pp[16], qq[16];
+    __shared__ double cs[16], sn[16];
     double fro = 0.0;
     for (int r = 0; r < n; ++r)
         if (l < n) fro += T[r][l] * T[r][l];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     const double thr = 2.220446049250313e-16 * sqrt(fro);
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        int rotated = 0;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = T[p][q];
-                if (fabs(apq) <= thr) {
-                    __syncwarp();
-                    if (l == 0) { T[p][q] = 0.0; T[q][p] = 0.0; }
-                    __syncwarp();
-                    continue;
+    const int P = n + (n & 1), npair = P / 2;
+    for (int sweep = 0; sweep < 30 && n > 1; ++sweep) {
+        bool any = false;
+        for (int round = 0; round < P - 1; ++round) {
+            bool rot = false;
+            if (l < npair) {
+                int p, q;
+                if (l == 0) { p = P - 1; q = round; }
+                else { p = (round + l) % (P - 1); q = (round - l + (P - 1)) % (P - 1); }
+                if (p > q) { const int t = p; p = q; q = t; }
+                double c = 1.0, sv = 0.0;
+                if (q < n) {
+                    const double apq = T[p][q];
+                    if (fabs(apq) <= thr) {
+                        T[p][q] = 0.0;
+                        T[q][p] = 0.0;
+                    } else {
+                        rot = true;
+                        const double theta = (T[q][q] - T[p][p]) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sv = t * c;
+                    }
                 }
-                rotated = 1;
-                const double theta = (T[q][q] - T[p][p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                __syncwarp();
-                if (l < n) {   // columns: A <- A J
-                    const double akp = T[l][p], akq = T[l][q];
-                    T[l][p] = c * akp - s * akq;
-                    T[l][q] = s * akp + c * akq;
-                }
-                __syncwarp();
-                if (l < n) {   // rows: A <- J^T A
-                    const double apk = T[p][l], aqk = T[q][l];
-                    T[p][l] = c * apk - s * aqk;
-                    T[q][l] = s * apk + c * aqk;
-                    const double vkp = S[l][p], vkq = S[l][q];
-                    S[l][p] = c * vkp - s * vkq;
-                    S[l][q] = s * vkp + c * vkq;
-                }
-                __syncwarp();
+                pp[l] = p; qq[l] = q; cs[l] = c; sn[l] = sv;
             }
-        if (!rotated) break;
+            any |= (__any_sync(0xffffffffu, rot) != 0);
+            __syncwarp();
+            for (int e = l; e < npair * n; e += 32) {   // columns: A <- A J
+                const int i = e / n, k = e % n, p = pp[i], q = qq[i];
+                if (q >= n) continue;
+                const double c = cs[i], sv = sn[i];
+                const double akp = T[k][p], akq = T[k][q];
+                T[k][p] = c * akp - sv * akq;
+                T[k][q] = sv * akp + c * akq;
+            }
+            __syncwarp();
+            for (int e = l; e < npair * n; e += 32) {   // rows: A <- J^T A;  S <- S J
+                const int i = e / n, k = e % n, p = pp[i], q = qq[i];
+                if (q >= n) continue;
+                const double c = cs[i], sv = sn[i];
+                const double apk = T[p][k], aqk = T[q][k];
+                T[p][k] = c * apk - sv * aqk;
+                T[q][k] = sv * apk + c * aqk;
+                const double vkp = S[k][p], vkq = S[k][q];
+                S[k][p] = c * vkp - sv * vkq;
+                S[k][q] = sv * vkp + c * vkq;
+            }
+            __syncwarp();
+        }
+        if (!any) break;
     }
     // phases e^{-i d_m t_x}
     for (int x = 0; x < n_v; ++x)
