@@ -9,6 +9,9 @@ One step = one time step of the hot path: the Krylov advance (n_K Lanczos steps,
 H psi + FP64 CGS2), the tridiagonal exponential and target assembly, the weighted rho_L of the
 ground state and the 4 targets, its eigendecomposition, and two expectation values.
 `value` = Krylov steps/s over the whole job (n_K per step); L2 is flushed before every step.
+The default arithmetic of H psi is the tensor-core path (bf16 Ozaki slices, --slices 4); the plain
+FP64 GPU path is timed beside it on the same workload, with the largest difference of the measured
+observables over a 20-step trajectory (vs_fp64_gpu).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,6 +37,7 @@ WL = dict(L=32, m=400, U=4.0, t=1.0, nbonds=1, tau=0.05, n_v=4, nk=10)
 WORKLOAD_NAME = "1D Hubbard chain L=32 U=4 half filling m=400 superblock (synthetic Gaussian-sector twin), " \
                 "c^dag excitation, tau=0.05, n_v=4, n_K=10, complex128"
 FLUSH_BYTES = 256 << 20
+BF16_BURST = 1923.8   # TFLOP/s, dense bf16 burst measured on the GB300s (cuBLAS)
 
 
 def parse():
@@ -43,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", choices=["ozaki", "fp64"], default="ozaki")
+    ap.add_argument("--slices", type=int, default=4)
     return ap.parse_args()
 
 
@@ -212,6 +218,78 @@ def run_reference(args):
     return 0
 
 
+class Runner:
+    """Device buffers and one time step of the hot path through the C ABI."""
+
+    def __init__(self, T, problem, ctx, ss, dev, stream):
+        import torch
+        self.T, self.P, self.ctx, self.ss, self.stream = T, problem, ctx, ss, stream
+        c128 = dict(dtype=torch.complex128, device=dev)
+        self.Q0, self.Q1 = ss.Q0, ss.Q1
+        self.n1 = T.tdmrg_sector_size(ctx, self.Q1)
+        self.psi_gs = torch.as_tensor(ss.psi_gs).to(dev)
+        self.phi = torch.zeros(self.n1, **c128)
+        T.tdmrg_apply_op(ctx, -1, problem.OP_EXC, self.Q0, self.psi_gs, self.Q1, self.phi)   # phi = c^dag_j psi (Eq. b)
+        self.phi0 = self.phi.clone()
+        self.nv, self.nk = WL["n_v"], WL["nk"]
+        self.times = [x * WL["tau"] / (self.nv - 1) for x in range(self.nv)]
+        self.targets = [torch.zeros(self.n1, **c128) for _ in range(self.nv - 1)] + [self.phi]   # advance in place
+        self.wgs, self.w = T.tdmrg_tst_weights(self.nv)
+        self.nr, self.ne = T.tdmrg_rho_size(ctx)
+        self.rho = torch.zeros(self.nr, **c128)
+        self.evals = torch.zeros(self.ne, dtype=torch.float64, device=dev)
+        self.evecs = torch.zeros(self.nr, **c128)
+        self.obs = torch.zeros(2, **c128)
+
+    def reset(self):
+        self.phi.copy_(self.phi0)
+
+    def step(self):
+        T, c, P = self.T, self.ctx, self.P
+        T.tdmrg_evolve(c, self.Q1, self.phi, self.times, self.nk, self.targets)
+        T.tdmrg_density_matrix(c, [(self.Q0, self.psi_gs)] + [(self.Q1, t) for t in self.targets], [self.wgs] + self.w,
+                               self.rho)
+        T.tdmrg_rho_eig(c, self.rho, self.evals, self.evecs)
+        T.tdmrg_expect(c, P.OP_N, -1, self.Q1, self.phi, self.obs[0:1])
+        T.tdmrg_expect(c, -1, P.OP_N, self.Q1, self.phi, self.obs[1:2])
+
+
+def timed_steps(torch, runner, steps, flush, stream, barrier):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    for e0, e1 in ev:
+        flush.fill_(1)
+        e0.record(stream)
+        runner.step()
+        e1.record(stream)
+    barrier()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def time_hpsi(torch, T, ctx, Q, x, out, flush, stream, reps=50):
+    for _ in range(3):
+        T.tdmrg_apply_h(ctx, Q, x, out)
+    hev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in hev:
+        flush.fill_(1)
+        e0.record(stream)
+        T.tdmrg_apply_h(ctx, Q, x, out)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in hev)
+
+
+def trajectory(torch, runner, steps):
+    """Observables <n_L>, <n_R> after each of `steps` time steps from the initial excitation."""
+    runner.reset()
+    out = []
+    for _ in range(steps):
+        runner.step()
+        out.append(runner.obs.clone())
+    torch.cuda.synchronize()
+    return torch.stack(out).cpu().numpy()
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -227,32 +305,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ss = workload()
-    ctx = T.tdmrg_create(device=local, stream=stream.cuda_stream)
+    mixed = args.prec == "ozaki"
+    prec = T.TDMRG_OZAKI_BF16 if mixed else T.TDMRG_FP64
+    ctx = T.tdmrg_create(device=local, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
     problem.load_synthetic(ctx, ss)
-    Q0, Q1 = ss.Q0, ss.Q1
-    n0, n1 = T.tdmrg_sector_size(ctx, Q0), T.tdmrg_sector_size(ctx, Q1)
-    c128 = dict(dtype=torch.complex128, device=dev)
-    psi_gs = torch.as_tensor(ss.psi_gs).to(dev)
-    phi = torch.zeros(n1, **c128)
-    T.tdmrg_apply_op(ctx, -1, problem.OP_EXC, Q0, psi_gs, Q1, phi)      # phi = c^dag_j psi (Eq. b)
-    phi0 = phi.clone()
-    nv, nk = WL["n_v"], WL["nk"]
-    times = [x * WL["tau"] / (nv - 1) for x in range(nv)]
-    targets = [torch.zeros(n1, **c128) for _ in range(nv - 1)] + [phi]      # last target advances phi in place
-    wgs, w = T.tdmrg_tst_weights(nv)
-    nr, ne = T.tdmrg_rho_size(ctx)
-    rho = torch.zeros(nr, **c128)
-    evals = torch.zeros(ne, dtype=torch.float64, device=dev)
-    evecs = torch.zeros(nr, **c128)
-    obs = torch.zeros(2, **c128)
+    run = Runner(T, problem, ctx, ss, dev, stream)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def step():
-        T.tdmrg_evolve(ctx, Q1, phi, times, nk, targets)
-        T.tdmrg_density_matrix(ctx, [(Q0, psi_gs)] + [(Q1, t) for t in targets], [wgs] + w, rho)
-        T.tdmrg_rho_eig(ctx, rho, evals, evecs)
-        T.tdmrg_expect(ctx, problem.OP_N, -1, Q1, phi, obs[0:1])
-        T.tdmrg_expect(ctx, -1, problem.OP_N, Q1, phi, obs[1:2])
 
     def barrier():
         if ws > 1:
@@ -261,62 +319,46 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     for _ in range(args.warmup):
-        step()
+        run.step()
     barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     time.sleep(0.25)
     l0 = T.tdmrg_launch_count(ctx)
-    barrier()
-    for e0, e1 in ev:
-        flush.fill_(1)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-    barrier()
+    step_ms = timed_steps(torch, run, args.steps, flush, stream, barrier)
     launches = T.tdmrg_launch_count(ctx) - l0
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    T.tdmrg_evolve_info(ctx)   # raises if a bounded device wait ran out during the timed steps
     total_ms = sum(step_ms)
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
+    nk = run.nk
     value = ws * nk * args.steps / (total_ms * 1e-3)
 
-    # H psi alone: the grouped sector-pair GEMM (both stages), CUDA events on its stream, L2 flushed
-    hx = torch.zeros(n1, **c128)
-    reps = 50
-    hev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    for _ in range(3):
-        T.tdmrg_apply_h(ctx, Q1, phi0, hx)
-    for e0, e1 in hev:
-        flush.fill_(1)
-        e0.record(stream)
-        T.tdmrg_apply_h(ctx, Q1, phi0, hx)
-        e1.record(stream)
-    torch.cuda.synchronize(dev)
-    h_ms = statistics.mean(a.elapsed_time(b) for a, b in hev)
+    # H psi alone (all launches of one product), CUDA events on its stream, L2 flushed
+    Q1 = run.Q1
+    hx = torch.zeros(run.n1, dtype=torch.complex128, device=dev)
+    h_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
     alg = algorithmic_hpsi_flops(ss, Q1)
-    issued = T.tdmrg_hpsi_flops(ctx, Q1)
+    tensor_fl = T.tdmrg_hpsi_tensor_flops(ctx, Q1)
     dmma_peak, dfma_peak = T.tdmrg_fp64_peak(local)
-    achieved = alg / (h_ms * 1e-3) / 1e12
 
     # end to end through the C ABI with host buffers: H2D phi, step, D2H observables + rho_L spectrum
     e2e_steps = max(3, min(args.steps, 50))
-    phi_h = phi0.cpu().pin_memory()
+    phi_h = run.phi0.cpu().pin_memory()
     obs_h = torch.zeros(2, dtype=torch.complex128).pin_memory()
-    ev_h = torch.zeros(ne, dtype=torch.float64).pin_memory()
+    ev_h = torch.zeros(run.ne, dtype=torch.float64).pin_memory()
     barrier()
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     for e0, e1 in ee:
         flush.fill_(1)
         e0.record(stream)
-        phi.copy_(phi_h, non_blocking=True)
-        step()
-        obs_h.copy_(obs, non_blocking=True)
-        ev_h.copy_(evals, non_blocking=True)
+        run.phi.copy_(phi_h, non_blocking=True)
+        run.step()
+        obs_h.copy_(run.obs, non_blocking=True)
+        ev_h.copy_(run.evals, non_blocking=True)
         e1.record(stream)
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
@@ -327,31 +369,57 @@ def run_ours(args):
         e2e_ms = float(t.item())
     e2e_val = ws * nk * e2e_steps / (e2e_ms * 1e-3)
 
+    # the plain FP64 GPU path on the same workload, and the observable error of this path against it
+    fp64 = None
+    if mixed and rank == 0:
+        traj_steps = 20
+        traj_m = trajectory(torch, run, traj_steps)
+        T.tdmrg_set_precision(ctx, T.TDMRG_FP64, 4)
+        traj_f = trajectory(torch, run, traj_steps)
+        run.reset()
+        for _ in range(2):
+            run.step()
+        f_ms = timed_steps(torch, run, min(args.steps, 40), flush, stream, barrier)
+        hf_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
+        fp64 = {"value": nk * len(f_ms) / (sum(f_ms) * 1e-3), "unit": UNIT, "ms_per_step": statistics.mean(f_ms),
+                "hpsi_ms": hf_ms, "hpsi_tflops": alg / (hf_ms * 1e-3) / 1e12,
+                "obs_err": float(np.abs(traj_m - traj_f).max()), "obs_err_steps": traj_steps}
+    T.tdmrg_destroy(ctx)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ss)
     if rank == 0:
         srt = sorted(step_ms)
+        if mixed:
+            roof = {"bound": "tensor", "achieved": tensor_fl / (h_ms * 1e-3) / 1e12, "peak": BF16_BURST, "unit": "TFLOP/s",
+                    "traffic": None, "kernel": "H psi on the tensor path (bf16 slicing + tcgen05 GEMM, 4 launches)",
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS bf16)",
+                    "alg_fp64_equiv_tflops": alg / (h_ms * 1e-3) / 1e12}
+        else:
+            roof = {"bound": "tensor", "achieved": alg / (h_ms * 1e-3) / 1e12, "peak": dmma_peak, "unit": "TFLOP/s",
+                    "traffic": None, "kernel": "gemm_f64_kernel (H psi, 2 launches)",
+                    "peak_source": f"FP64 tensor MMA loop measured live (tdmrg_fp64_peak); DFMA {dfma_peak:.2f} TFLOP/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, **WL, "D": n1, "prec": "fp64",
+            "config": {"workload": WORKLOAD_NAME, **WL, "D": run.n1,
+                       "prec": f"ozaki-bf16 x{args.slices} slices (tcgen05), FP64 Lanczos/eig" if mixed else "fp64",
                        "l2": f"flushed before every step ({FLUSH_BYTES >> 20} MB write)", "parallelism": "replicas"},
             "step_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
-            "hpsi": {"ms": h_ms, "alg_gflop": alg / 1e9, "issued_gflop": issued / 1e9, "tflops": achieved},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": dmma_peak, "unit": "TFLOP/s",
-                         "frac": achieved / dmma_peak, "traffic": None, "kernel": "gemm_f64_kernel (H psi, 2 launches)",
-                         "peak_source": "FP64 tensor MMA loop measured live (tdmrg_fp64_peak); "
-                                        f"DFMA {dfma_peak:.2f} TFLOP/s"},
+            "hpsi": {"ms": h_ms, "alg_gflop": alg / 1e9, "tensor_gflop": tensor_fl / 1e9,
+                     "alg_tflops": alg / (h_ms * 1e-3) / 1e12},
+            "vs_fp64_gpu": fp64,
+            "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * n1,
-                    "d2h_bytes_per_step": 16 * 2 + 8 * ne},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * run.n1,
+                    "d2h_bytes_per_step": 16 * 2 + 8 * run.ne},
             "gpu_launches": launches,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
-    T.tdmrg_destroy(ctx)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -20,6 +20,10 @@ int tdmrg_launch_count(tdmrg_ctx* ctx, int64_t* count);
  * per complex multiply-add of every sector-pair product it issues (stage 1 + stage 2). */
 int tdmrg_hpsi_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
 
+/* Tensor-core flops one H psi in sector Q issues on the Ozaki path (2 M N K per tcgen05.mma over all
+ * tiles, slice pairs and K chunks, padding included); 0 when the context runs FP64. */
+int tdmrg_hpsi_tensor_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
+
 /* Sustained FP64 throughput of this device, measured by timing (CUDA events) a register-resident
  * loop of the FP64 tensor MMA (mma.sync m8n8k4 f64) and of scalar DFMA on every SM.  Synchronises
  * the device; takes well under a second.  Results in TFLOP/s. */

@@ -67,6 +67,9 @@ void drop_plans(tdmrg_ctx* c) {
     for (auto& kv : c->plans) {
         release(c, kv.second->stage1);
         release(c, kv.second->stage2);
+        release(c, kv.second->thin[0]);
+        release(c, kv.second->thin[1]);
+        release_oz(c, kv.second->oz);
     }
     c->plans.clear();
 }
@@ -107,7 +110,12 @@ int get_plan(tdmrg_ctx* c, int kind, int opL, int opR, int qa, int qb, int oa, i
     std::unique_ptr<Plan> p(new (std::nothrow) Plan());
     if (!p) return fail(c, TDMRG_ENOMEM, "host allocation");
     int rc = build_plan(c, terms, qa, qb, oa, ob, p.get());
-    if (rc) { release(c, p->stage1); release(c, p->stage2); return rc; }
+    if (!rc && kind == 0 && c->opts.prec == TDMRG_OZAKI_BF16) rc = build_oz(c, p.get(), c->opts.ozaki_slices);
+    if (rc) {
+        release(c, p->stage1); release(c, p->stage2); release(c, p->thin[0]); release(c, p->thin[1]);
+        release_oz(c, p->oz);
+        return rc;
+    }
     *out = p.get();
     c->plans[key] = std::move(p);
     return TDMRG_OK;
@@ -123,6 +131,23 @@ int ensure_tmp(tdmrg_ctx* c, int64_t n) {
 }
 
 }  // namespace
+
+namespace tdmrg {
+
+int get_ham_plan(tdmrg_ctx* c, int a, int b, Plan** out) { return get_plan(c, 0, -1, -1, a, b, a, b, out); }
+
+int check_device_status(tdmrg_ctx* c) {
+    int st = 0;
+    int rc = cuda_check(c, cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost), "device status");
+    if (rc) return rc;
+    if (st) {
+        cudaMemset(c->dstatus, 0, sizeof(int));
+        return fail(c, TDMRG_ETIMEOUT, "a bounded device wait in a tensor-core kernel ran out; results are invalid");
+    }
+    return TDMRG_OK;
+}
+
+}  // namespace tdmrg
 
 extern "C" {
 
@@ -141,7 +166,9 @@ int tdmrg_create(tdmrg_ctx** out, const tdmrg_opts* o) {
     if (!out || !o) return fail(nullptr, TDMRG_EINVAL, "null argument to tdmrg_create");
     *out = nullptr;
     if (o->nk_max < 1 || o->nk_max > 32) return fail(nullptr, TDMRG_EINVAL, "nk_max must be in 1..32");
-    if (o->prec != TDMRG_FP64) return fail(nullptr, TDMRG_EINVAL, "unsupported precision");
+    if (o->prec != TDMRG_FP64 && o->prec != TDMRG_OZAKI_BF16) return fail(nullptr, TDMRG_EINVAL, "unsupported precision");
+    if (o->prec == TDMRG_OZAKI_BF16 && (o->ozaki_slices < 2 || o->ozaki_slices > 6))
+        return fail(nullptr, TDMRG_EINVAL, "ozaki_slices must be in 2..6");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || o->device < 0 || o->device >= ndev) {
         cudaGetLastError();
@@ -155,6 +182,8 @@ int tdmrg_create(tdmrg_ctx** out, const tdmrg_opts* o) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, o->device);
     int rc = dev_alloc(c, (void**)&c->red, 2 * 64 * kRedBlocks * sizeof(double2), "reduction workspace");
     if (!rc) rc = dev_alloc(c, (void**)&c->dscale, 64 * sizeof(double), "scale workspace");
+    if (!rc) rc = dev_alloc(c, (void**)&c->dstatus, sizeof(int), "status word");
+    if (!rc) rc = cuda_check(c, cudaMemset(c->dstatus, 0, sizeof(int)), "status word");
     if (rc) {
         g_err = c->err;
         tdmrg_destroy(c);
@@ -176,6 +205,7 @@ int tdmrg_destroy(tdmrg_ctx* c) {
     dev_free(c, c->tmp, c->tmp_cap * sizeof(cplx));
     dev_free(c, c->red, 2 * 64 * kRedBlocks * sizeof(double2));
     dev_free(c, c->dscale, 64 * sizeof(double));
+    dev_free(c, c->dstatus, sizeof(int));
     delete c;
     return TDMRG_OK;
 }
@@ -189,9 +219,13 @@ int tdmrg_set_stream(tdmrg_ctx* c, void* stream) {
 
 int tdmrg_set_precision(tdmrg_ctx* c, int prec, int slices) {
     if (check_ctx(c)) return TDMRG_EINVAL;
-    if (prec != TDMRG_FP64) return fail(c, TDMRG_EINVAL, "unsupported precision " + std::to_string(prec));
+    if (prec != TDMRG_FP64 && prec != TDMRG_OZAKI_BF16) return fail(c, TDMRG_EINVAL, "unsupported precision " + std::to_string(prec));
+    if (prec == TDMRG_OZAKI_BF16 && (slices < 2 || slices > 6)) return fail(c, TDMRG_EINVAL, "ozaki_slices must be in 2..6");
+    DeviceGuard g(c->opts.device);
+    cudaStreamSynchronize(c->stream);
     c->opts.prec = prec;
     c->opts.ozaki_slices = slices;
+    drop_plans(c);   // plans are rebuilt in the new arithmetic
     return TDMRG_OK;
 }
 

@@ -41,10 +41,11 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
     extern __shared__ float2 fsm[];
     const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
     const int64_t off = tb.off[sct];
+    const int ld = n | 1;   // odd row stride: column accesses of a warp hit distinct banks
     float2* A;
     float2* V;
-    if (n <= kSmemMaxN) { A = fsm; V = fsm + n * n; }
-    else { A = gwork + 2 * off; V = A + (int64_t)n * n; }
+    if (n <= kSmemMaxN) { A = fsm; V = fsm + n * ld; }
+    else { A = gwork + 4 * off; V = A + (int64_t)n * ld; }
     __shared__ int pp[256], qq[256];
     __shared__ float cs[256];
     __shared__ float2 sn[256];
@@ -53,12 +54,14 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
     __shared__ int rotated;
     const cplx* R = rho + off;
     for (int e = tid; e < n * n; e += JT) {
+        const int r = e / n, cc = e % n;
         const double2 v = R[e];
-        A[e] = make_float2((float)v.x, (float)v.y);
-        V[e] = make_float2((e / n == e % n) ? 1.f : 0.f, 0.f);
+        A[r * ld + cc] = make_float2((float)v.x, (float)v.y);
+        V[r * ld + cc] = make_float2(r == cc ? 1.f : 0.f, 0.f);
     }
+    __syncthreads();
     float fro = 0.f;
-    for (int e = tid; e < n * n; e += JT) { const float2 a = A[e]; fro += a.x * a.x + a.y * a.y; }
+    for (int e = tid; e < n * n; e += JT) { const float2 a = A[(e / n) * ld + e % n]; fro += a.x * a.x + a.y * a.y; }
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     if ((tid & 31) == 0) red[tid >> 5] = fro;
     __syncthreads();
@@ -83,14 +86,14 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
                 float c = 1.f;
                 float2 s = make_float2(0.f, 0.f);
                 if (q < n) {
-                    const float2 b = A[p * n + q];
+                    const float2 b = A[p * ld + q];
                     const float ab = sqrtf(b.x * b.x + b.y * b.y);
                     if (ab <= thr) {
-                        A[p * n + q] = make_float2(0.f, 0.f);
-                        A[q * n + p] = make_float2(0.f, 0.f);
+                        A[p * ld + q] = make_float2(0.f, 0.f);
+                        A[q * ld + p] = make_float2(0.f, 0.f);
                     } else {
                         rotated = 1;
-                        const float a = A[p * n + p].x, d = A[q * n + q].x;
+                        const float a = A[p * ld + p].x, d = A[q * ld + q].x;
                         const float tau = (d - a) / (2.f * ab);
                         const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
                         c = rsqrtf(1.f + t * t);
@@ -108,10 +111,10 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
                 const float c = cs[i];
                 const float2 s = sn[i], sc = conjf2(s);
                 for (int k = lane; k < n; k += 32) {
-                    const float2 ap = A[p * n + k], aq = A[q * n + k];
+                    const float2 ap = A[p * ld + k], aq = A[q * ld + k];
                     const float2 t1 = cmf(s, aq), t2 = cmf(sc, ap);
-                    A[p * n + k] = make_float2(c * ap.x - t1.x, c * ap.y - t1.y);
-                    A[q * n + k] = make_float2(t2.x + c * aq.x, t2.y + c * aq.y);
+                    A[p * ld + k] = make_float2(c * ap.x - t1.x, c * ap.y - t1.y);
+                    A[q * ld + k] = make_float2(t2.x + c * aq.x, t2.y + c * aq.y);
                 }
             }
             __syncthreads();
@@ -121,14 +124,14 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
                 const float c = cs[i];
                 const float2 s = sn[i], sc = conjf2(s);
                 for (int k = lane; k < n; k += 32) {
-                    float2 xp = A[k * n + p], xq = A[k * n + q];
+                    float2 xp = A[k * ld + p], xq = A[k * ld + q];
                     float2 t1 = cmf(sc, xq), t2 = cmf(s, xp);
-                    A[k * n + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
-                    A[k * n + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
-                    xp = V[k * n + p]; xq = V[k * n + q];
+                    A[k * ld + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
+                    A[k * ld + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
+                    xp = V[k * ld + p]; xq = V[k * ld + q];
                     t1 = cmf(sc, xq); t2 = cmf(s, xp);
-                    V[k * n + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
-                    V[k * n + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
+                    V[k * ld + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
+                    V[k * ld + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
                 }
             }
             __syncthreads();
@@ -137,7 +140,10 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
         if (!rotated) break;
     }
     cplx* Xs = X + off;
-    for (int e = tid; e < n * n; e += JT) Xs[e] = make_double2(V[e].x, V[e].y);
+    for (int e = tid; e < n * n; e += JT) {
+        const float2 v = V[(e / n) * ld + e % n];
+        Xs[e] = make_double2(v.x, v.y);
+    }
 }
 
 // Xh = X^H per sector.
@@ -262,7 +268,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         if (!rc) rc = dev_alloc(c, (void**)&w.buf, (size_t)6 * r * sizeof(cplx), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.lam, (size_t)e * sizeof(double), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.fro, (size_t)ns * sizeof(double), "eig workspace");
-        if (!rc && maxn > kSmemMaxN) rc = dev_alloc(c, (void**)&w.gwork, (size_t)2 * r * sizeof(float2), "eig workspace");
+        if (!rc && maxn > kSmemMaxN) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
         if (rc) return rc;
         std::vector<unsigned char> host((size_t)ns * (2 * sizeof(int64_t) + sizeof(int)));
         memcpy(host.data(), off.data(), ns * sizeof(int64_t));
@@ -306,7 +312,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     cplx* E1 = w.buf + 5 * w.nrho;
     cplx* Y = evecs;   // ping-pong with the caller's output, which receives the sorted result at the end
     const int sm = std::min(w.maxn, kSmemMaxN);
-    const size_t smem = (size_t)2 * sm * sm * sizeof(float2);
+    const size_t smem = (size_t)2 * sm * (sm | 1) * sizeof(float2);
     int rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                         "eig smem");
     if (rc) return rc;
@@ -355,7 +361,7 @@ void release_eig(tdmrg_ctx* c) {
     dev_free(c, w.buf, (size_t)6 * w.nrho * sizeof(cplx));
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
     dev_free(c, w.fro, (size_t)ns * sizeof(double));
-    dev_free(c, w.gwork, (size_t)2 * w.nrho * sizeof(float2));
+    dev_free(c, w.gwork, (size_t)4 * w.nrho * sizeof(float2));
     w = EigWork();
 }
 

@@ -2,6 +2,8 @@
 // compiled into, the context, and the kernel launchers of each translation unit.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,13 +70,72 @@ struct TaskList {
     int* d_counters = nullptr;    // split-K tickets (zero between launches)
 };
 
+// ---- tensor-core (Ozaki-sliced) form of a plan's stages, ozaki.cu
+struct OzTask {            // one complex GEMM C (+)= A op(B), all of its segments K-concatenated
+    int64_t c_off;
+    int32_t ldc, M, N;
+    int32_t arow0, brow0;  // first panel row of A' (rows) and B' (column pairs)
+    int32_t aexp0, bexp0;  // first exponent of the rows / columns
+    int32_t kchunks;       // 64-wide chunks of the real K (2 sum K)
+    int8_t c_buf, beta, pad0, pad1;
+};
+struct OzTile { int32_t task, m0, n0, cost; };
+struct OzSliceJob {        // slices the rows of A' (role 0) or columns of B' (role 1) of one operand
+    int32_t role, nvec, seg_begin, seg_end, row0, exp0, ktot, use_scale, vec_prefix;
+};
+struct OzSliceArgs {
+    const OzSliceJob* jobs;
+    int njobs;
+    const Seg* segs;
+    __nv_bfloat16* panel;
+    int* exps;
+    int rows, kpad, S, nvec_total;
+};
+struct OzGemmArgs {
+    const OzTask* tasks;
+    const OzTile* tiles;
+    const int* expA;
+    const int* expB;
+    int rowsA, rowsB;
+    int* status;
+};
+struct OzStage {
+    std::vector<OzTask> tasks;
+    std::vector<OzTile> tiles;
+    std::vector<OzSliceJob> ajobs, bjobs;
+    std::vector<Seg> asegs, bsegs;
+    OzTask* d_tasks = nullptr;
+    OzTile* d_tiles = nullptr;
+    OzSliceJob* d_ajobs = nullptr;
+    OzSliceJob* d_bjobs = nullptr;
+    Seg* d_asegs = nullptr;
+    Seg* d_bsegs = nullptr;
+    __nv_bfloat16* panelA = nullptr;   // S slice planes of rowsA x kpad bf16
+    __nv_bfloat16* panelB = nullptr;
+    int* expA = nullptr;
+    int* expB = nullptr;
+    size_t panel_bytes_a = 0, panel_bytes_b = 0, exp_bytes_a = 0, exp_bytes_b = 0;
+    int rowsA = 0, rowsB = 0, kpad = 0, ncolsB = 0;
+    CUtensorMap mapA, mapB;
+    OzSliceArgs sliceA{}, sliceB{};
+    OzGemmArgs args{};
+};
+struct OzPlan {
+    bool ready = false;
+    int S = 0;
+    OzStage st[2];
+    int* status = nullptr;   // set by a tensor-core CTA whose bounded wait ran out
+};
+
 // A superblock product compiled for (terms, Q_in, Q_out): stage 1 right products, stage 2 left
-// products (see plan.cu).
+// products (see plan.cu); with TDMRG_OZAKI_BF16 also their tensor-core form and the FP64 remainder.
 struct Plan {
     int qin[2], qout[2];
     int64_t n_in = 0, n_out = 0, scratch = 0;   // complex entries
     TaskList stage1, stage2;
     double flops = 0.0;
+    OzPlan oz;
+    TaskList thin[2];
 };
 
 struct BlockOp {
@@ -164,6 +225,7 @@ struct tdmrg_ctx {
     size_t allocated = 0;
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
+    int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
     tdmrg::EigWork eig;
 };
 
@@ -189,6 +251,16 @@ constexpr int kTileF64 = 16;
 constexpr int kSplitK = 96;
 cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step);
 
+
+// api.cu: cached plan of H psi in sector (a, b), in the context's precision
+int get_ham_plan(tdmrg_ctx* c, int a, int b, Plan** out);
+int check_device_status(tdmrg_ctx* c);
+
+// ozaki.cu: tensor-core superblock products
+int build_oz(tdmrg_ctx* c, Plan* p, int S);
+int run_oz(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* skip_flag, int skip_step);
+void release_oz(tdmrg_ctx* c, OzPlan& oz);
+int oz_status(tdmrg_ctx* c, const Plan& p, int* status);
 
 // krylov.cu
 int evolve(tdmrg_ctx* c, int n_up, int n_dn, const cplx* phi, int n_v, const double* t_x, int nk,

@@ -403,21 +403,10 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
     int64_t n = sector_size(c, a, b);
     if (n == 0) return fail(c, TDMRG_ESECTOR, "evolve: empty sector");
     Plan* p = nullptr;
-    {
-        auto key = std::make_tuple(0, -1, -1, a, b, a, b);
-        auto it = c->plans.find(key);
-        if (it == c->plans.end()) {
-            std::unique_ptr<Plan> np(new Plan());
-            int rc = build_plan(c, c->ham, a, b, a, b, np.get());
-            if (rc) { release(c, np->stage1); release(c, np->stage2); return rc; }
-            p = np.get();
-            c->plans[key] = std::move(np);
-        } else {
-            p = it->second.get();
-        }
-    }
+    int rc = get_ham_plan(c, a, b, &p);
+    if (rc) return rc;
     KrylovWork* k = nullptr;
-    int rc = ensure_work(c, a, b, nk, n, &k);
+    rc = ensure_work(c, a, b, nk, n, &k);
     if (rc) return rc;
     cudaStream_t s = c->stream;
     Times tt{};
@@ -453,6 +442,8 @@ int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* 
     int rc = cuda_check(c, cudaMemcpyAsync(tri, k->tri, sizeof(tri), cudaMemcpyDeviceToHost, c->stream), "evolve_info");
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(flags, k->flags, sizeof(flags), cudaMemcpyDeviceToHost, c->stream), "evolve_info");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "evolve_info sync");
+    if (rc) return rc;
+    rc = check_device_status(c);
     if (rc) return rc;
     if (nk_used) *nk_used = flags[0];
     if (err) *err = tri[T_ERR];

@@ -50,6 +50,28 @@ int tdmrg_launch_count(tdmrg_ctx* c, int64_t* count) {
     return TDMRG_OK;
 }
 
+int tdmrg_hpsi_tensor_flops(tdmrg_ctx* c, int a, int b, double* flops) {
+    if (!c || !flops) return tdmrg::fail(c, TDMRG_EINVAL, "hpsi_tensor_flops: null argument");
+    if (!c->ham_set) return tdmrg::fail(c, TDMRG_ESTATE, "hpsi_tensor_flops: Hamiltonian not set");
+    tdmrg::Plan* p = nullptr;
+    int rc = tdmrg::get_ham_plan(c, a, b, &p);
+    if (rc) return rc;
+    double f = 0.0;
+    if (p->oz.ready) {
+        const int S = p->oz.S;
+        for (const tdmrg::OzStage& st : p->oz.st)
+            for (const tdmrg::OzTile& t : st.tiles) {
+                const tdmrg::OzTask& k = st.tasks[t.task];
+                const int nval = k.N - t.n0 < 32 ? k.N - t.n0 : 32;
+                const int n_t = (nval + 7) & ~7;
+                // per 64-wide K chunk: 4 k-steps x S(S+1)/2 MMAs of 128 x 2n_t x 16
+                f += (double)k.kchunks * 4 * (S * (S + 1) / 2) * 2.0 * 128 * (2 * n_t) * 16;
+            }
+    }
+    *flops = f;
+    return TDMRG_OK;
+}
+
 int tdmrg_fp64_peak(int device, double* dmma, double* dfma) {
     if (!dmma || !dfma) return tdmrg::fail(nullptr, TDMRG_EINVAL, "fp64_peak: null output");
     int prev = 0;

@@ -1,0 +1,598 @@
+// Mixed-precision superblock products on the tcgen05 tensor cores (Sec. IV, Hamiltonian connections).
+//
+// Each complex product C (+)= A op(B) of a task is carried out exactly in integer slices
+// (Ozaki-style splitting), so the only approximation is the truncation of the operands:
+//   real embedding     A' = [Re A | Im A]  (M x 2K),   B'^T rows = [Re b_j | -Im b_j], [Im b_j | Re b_j];
+//   common exponents   E_i over row i of A' (all segments of the task), F_j over column j of B';
+//   fixed point        a = v 2^{-E} in (-1, 1),  N = round(a 2^{7S})  (integer arithmetic only);
+//   balanced digits    N = sum_s d_s 2^{7(S-s)},  |d_1| <= 128, |d_s| <= 64  (exact in bf16);
+//   slice products     X_g = sum_{s+t=g} A^(s) B^(t)^T for g = 2..S+1, one TMEM accumulator per g,
+//                      exact in the FP32 accumulator as long as a readout block spans <= 512 real K;
+//   recombination      C' = sum_g X_g 2^{7(S+1-g)} 2^{E_i + F_j - 7(S+1)} in int64, one conversion.
+// The error is about 2^{-7S} of max|A'_i| max|B'_j| per entry (S = ozaki_slices).
+//
+// Operands are pre-sliced into bf16 panels in global memory ("slice planes": plane s holds digit s of
+// every row, K-major, rows of kpad elements) and staged into shared memory by TMA (2-D tensor maps,
+// 128-byte swizzle); one elected thread issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32, M = 128,
+// N = 2 n_t <= 64) into TMEM, the four warps read the accumulators back with tcgen05.ld.
+// Static operands (operator blocks with the term coefficients and fermion signs folded in) are
+// sliced once per plan; the wave function and the stage-1 intermediates are sliced per product.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace tdmrg {
+namespace {
+
+constexpr int KCH = 64;         // K per TMA box / smem stage (64 bf16 = 128 B rows)
+constexpr int TM = 128;         // MMA M
+constexpr int TNC = 32;         // complex output columns per tile (MMA N = 2 * n_t <= 64)
+constexpr int ABOX = TM * KCH * 2;         // bytes of one A slice box (16 KB)
+constexpr int BBOX = 2 * TNC * KCH * 2;    // bytes of one B slice box (8 KB)
+constexpr int kReadoutChunks = 8;          // 8 x 64 = 512 real K per exact accumulation block
+constexpr long kWaitLimit = 1L << 26;      // bounded mbarrier polls
+
+// ------------------------------------------------------------------------------ slicing
+__device__ __forceinline__ int biased_exp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+
+// round(v * 2^{S7 - E}) with integer arithmetic (|v| < 2^E); zero and subnormals give 0
+__device__ __forceinline__ long long fixed_point(double v, int E, int S7) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) return 0;
+    const long long m = (long long)((b & ((1ull << 52) - 1)) | (1ull << 52));
+    const int sh = (ex - 1075) + S7 - E;
+    long long r;
+    if (sh >= 0) r = m << sh;
+    else if (sh < -62) r = 0;
+    else r = (m + (1ll << (-sh - 1))) >> (-sh);
+    return (b >> 63) ? -r : r;
+}
+
+template <int S>
+__device__ __forceinline__ void digits(long long N, int* d) {
+#pragma unroll
+    for (int s = 1; s < S; ++s) {
+        const int w = 7 * (S - s);
+        const long long q = (N + (1ll << (w - 1))) >> w;
+        N -= q << w;
+        d[s - 1] = (int)q;
+    }
+    d[S - 1] = (int)N;
+}
+
+__device__ __forceinline__ double2 fetch(const Seg& sg, const GemmArgs& g, int role, int vec, int k) {
+    if (role == 0) {   // A role: row vec of A
+        double2 v = g.bufs[sg.a_buf][sg.a_off + (int64_t)vec * sg.lda + k];
+        return v;
+    }
+    const cplx* B = g.bufs[sg.b_buf] + sg.b_off;   // B role: column vec of op(B)
+    if (sg.opb == OPB_N) return B[(int64_t)k * sg.ldb + vec];
+    double2 v = B[(int64_t)vec * sg.ldb + k];
+    if (sg.opb == OPB_C) v.y = -v.y;
+    return v;
+}
+
+__device__ __forceinline__ double2 scaled(double2 v, cplx s) {
+    return make_double2(s.x * v.x - s.y * v.y, s.x * v.y + s.y * v.x);
+}
+
+// One warp per vector (row of A' or complex column of B'); two passes over the task's segments.
+template <int S>
+__global__ void __launch_bounds__(256) k_slice(OzSliceArgs sa, GemmArgs g, const int* skip_flag, int skip_step) {
+    if (skip_flag != nullptr && skip_step >= *skip_flag) return;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (gw >= sa.nvec_total) return;
+    int lo = 0, hi = sa.njobs - 1;   // job with vec_prefix[job] <= gw < vec_prefix[job + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sa.jobs[mid].vec_prefix <= gw) lo = mid; else hi = mid - 1;
+    }
+    const OzSliceJob job = sa.jobs[lo];
+    const int v = gw - job.vec_prefix;
+    constexpr int S7 = 7 * S;
+    int emax = 0;
+    for (int s = job.seg_begin; s < job.seg_end; ++s) {
+        const Seg sg = sa.segs[s];
+        for (int k = lane; k < sg.K; k += 32) {
+            double2 x = fetch(sg, g, job.role, v, k);
+            if (job.use_scale) x = scaled(x, sg.scale);
+            emax = max(emax, max(biased_exp(x.x), biased_exp(x.y)));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    const int E = emax == 0 ? 0 : emax - 1023 + 1;   // every |value| < 2^E
+    int r_re, r_im;                                   // destination panel rows
+    if (job.role == 0) {
+        r_re = r_im = job.row0 + v;
+    } else {
+        const int nt = v / TNC, c = v % TNC;
+        const int nrem = job.nvec - TNC * nt;
+        const int n_t = ((nrem < TNC ? nrem : TNC) + 7) & ~7;
+        r_re = job.row0 + 2 * TNC * nt + c;
+        r_im = r_re + n_t;
+    }
+    if (lane == 0) sa.exps[job.exp0 + v] = E;
+    const int64_t plane = (int64_t)sa.rows * sa.kpad;
+    __nv_bfloat16* P = sa.panel;
+    int kbase = 0;
+    for (int s = job.seg_begin; s < job.seg_end; ++s) {
+        const Seg sg = sa.segs[s];
+        for (int k = lane; k < sg.K; k += 32) {
+            double2 x = fetch(sg, g, job.role, v, k);
+            if (job.use_scale) x = scaled(x, sg.scale);
+            int dr[S], di[S];
+            digits<S>(fixed_point(x.x, E, S7), dr);
+            digits<S>(fixed_point(x.y, E, S7), di);
+            const int p = kbase + k, q = job.ktot + kbase + k;
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                __nv_bfloat16* pl = P + t * plane;
+                if (job.role == 0) {
+                    pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
+                    pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)di[t]);
+                } else {
+                    pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
+                    pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)(-di[t]));
+                    pl[(int64_t)r_im * sa.kpad + p] = __float2bfloat16_rn((float)di[t]);
+                    pl[(int64_t)r_im * sa.kpad + q] = __float2bfloat16_rn((float)dr[t]);
+                }
+            }
+        }
+        kbase += sg.K;
+    }
+}
+
+// ------------------------------------------------------------------------------ tcgen05 GEMM
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// a * 2^e as a double, rounded to nearest even, built with integer operations only (the FP64 units
+// of this GPU are ~60x slower than its integer ones); results below the normal range flush to zero
+__device__ __forceinline__ double scaled_int(long long a, int e) {
+    if (a == 0) return 0.0;
+    const unsigned long long sign = a < 0 ? (1ull << 63) : 0ull;
+    unsigned long long u = a < 0 ? (unsigned long long)(-a) : (unsigned long long)a;
+    const int lz = __clzll(u);
+    u <<= lz;                                             // leading one at bit 63
+    unsigned long long mant = u >> 11;                    // 53 bits
+    const unsigned long long rest = u & 0x7FFull;
+    if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ++mant;
+    int ex = 63 - lz + e;
+    if (mant >> 53) { mant >>= 1; ++ex; }
+    const int biased = ex + 1023;
+    if (biased <= 0) return 0.0;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                     const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa, GemmArgs g,
+                                                     const int* skip_flag, int skip_step) {
+    if (skip_flag != nullptr && skip_step >= *skip_flag) return;
+    constexpr int NCOLS = (S * 64 <= 256) ? 256 : 512;   // TMEM columns: one 64-column accumulator per g
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;                 // S boxes of 16 KB
+    unsigned char* sB = smem + S * ABOX;      // S boxes of 8 KB
+    __shared__ __align__(8) uint64_t bar_tma, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const OzTile tile = oa.tiles[blockIdx.x];
+    const OzTask task = oa.tasks[tile.task];
+    const int nrem = task.N - tile.n0;
+    const int nval = nrem < TNC ? nrem : TNC;          // valid complex columns of this tile
+    const int n_t = (nval + 7) & ~7;                    // MMA N = 2 n_t (multiple of 16)
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * n_t) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_tma)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_mma)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tmem_base)), "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    long long acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0;
+    const int ya = task.arow0 + tile.m0;
+    const int yb = task.brow0 + 2 * tile.n0;   // the tile's rows start 2 * TNC rows per full tile
+    uint32_t phase = 0;
+    for (int c = 0; c < task.kchunks; ++c) {
+        if (tid == 0 && !failed) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&bar_tma)), "r"(S * (ABOX + BBOX)) : "memory");
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                tma_load(smem_u32(sA + s * ABOX), &mapA, c * KCH, s * oa.rowsA + ya, smem_u32(&bar_tma));
+                tma_load(smem_u32(sB + s * BBOX), &mapB, c * KCH, s * oa.rowsB + yb, smem_u32(&bar_tma));
+            }
+        }
+        if (!mbar_wait(smem_u32(&bar_tma), phase)) failed = 1;
+        __syncthreads();
+        const bool first_in_block = (c % kReadoutChunks) == 0;
+        if (tid == 0 && !failed) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int ks = 0; ks < KCH / 16; ++ks) {
+#pragma unroll
+                for (int gg = 2; gg <= S + 1; ++gg) {
+                    const int s_lo = gg - S > 1 ? gg - S : 1, s_hi = gg - 1 < S ? gg - 1 : S;
+#pragma unroll
+                    for (int s = s_lo; s <= s_hi; ++s) {
+                        const int t = gg - s;
+                        const uint64_t da = desc_sw128(smem_u32(sA + (s - 1) * ABOX) + ks * 32);
+                        const uint64_t db = desc_sw128(smem_u32(sB + (t - 1) * BBOX) + ks * 32);
+                        const uint32_t accum = (first_in_block && ks == 0 && s == s_lo) ? 0u : 1u;
+                        umma(tmem + (uint32_t)((gg - 2) * 64), da, db, idesc, accum);
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(&bar_mma)) : "memory");
+        }
+        if (!mbar_wait(smem_u32(&bar_mma), phase)) failed = 1;   // smem stage free, accumulators complete
+        __syncthreads();
+        phase ^= 1;
+        if (failed) break;
+        if ((c % kReadoutChunks) == kReadoutChunks - 1 || c == task.kchunks - 1) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int gg = 2; gg <= S + 1; ++gg) {
+                const int shift = 7 * (S + 1 - gg);
+                uint32_t r[4][16];
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb)   // all loads of the group in flight, one wait
+                    if (cb * 16 < 2 * n_t)
+                        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((gg - 2) * 64 + cb * 16), r[cb]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb)
+                    if (cb * 16 < 2 * n_t) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[cb][j])) << shift;
+                    }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();   // accumulators read before the next block overwrites them
+        }
+    }
+    // epilogue: row = TMEM lane; scale by 2^{E_i + F_j - 7(S+1)} and store FP64 complex
+    const int row = 32 * warp + lane;
+    if (!failed && tile.m0 + row < task.M) {
+        const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
+        double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * task.ldc + tile.n0);
+#pragma unroll
+        for (int jj = 0; jj < 64; ++jj) {       // accumulator column jj: Re of column jj, or Im of column jj - n_t
+            if (jj < 2 * n_t) {
+                const bool im = jj >= n_t;
+                const int j = im ? jj - n_t : jj;
+                if (j < nval) {
+                    const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
+                    double v = scaled_int(acc[jj], e);
+                    double* pc = C + 2 * j + (im ? 1 : 0);
+                    if (task.beta) v += *pc;
+                    *pc = v;
+                }
+            }
+        }
+    }
+    if (failed && tid == 0) atomicOr(oa.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOLS));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_map(tdmrg_ctx* c, CUtensorMap* m, void* base, int64_t rows, int kpad, int box_rows) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            !p) {
+            cudaGetLastError();
+            return fail(c, TDMRG_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        }
+        fn = (EncodeTiledFn)p;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, TDMRG_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return TDMRG_OK;
+}
+
+template <int S>
+cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
+    const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_ozaki_gemm<S><<<(int)st.tiles.size(), 128, smem, s>>>(st.mapA, st.mapB, st.args, g, skip_flag, skip_step);
+    return cudaGetLastError();
+}
+
+cudaError_t slice_launch(const OzSliceArgs& sa, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
+    if (sa.nvec_total <= 0) return cudaSuccess;
+    const int warps = 8, grid = (sa.nvec_total + warps - 1) / warps;
+    switch (sa.S) {
+        case 2: k_slice<2><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
+        case 3: k_slice<3><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
+        case 4: k_slice<4><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
+        case 5: k_slice<5><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
+        case 6: k_slice<6><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+int upload_vec(tdmrg_ctx* c, const std::vector<T>& v, T** d, const char* what) {
+    *d = nullptr;
+    if (v.empty()) return TDMRG_OK;
+    int rc = dev_alloc(c, (void**)d, v.size() * sizeof(T), what);
+    if (rc) return rc;
+    return cuda_check(c, cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+}
+
+}  // namespace
+
+void release_oz(tdmrg_ctx* c, OzPlan& oz) {
+    for (OzStage& st : oz.st) {
+        dev_free(c, st.d_tasks, st.tasks.size() * sizeof(OzTask));
+        dev_free(c, st.d_tiles, st.tiles.size() * sizeof(OzTile));
+        dev_free(c, st.d_ajobs, st.ajobs.size() * sizeof(OzSliceJob));
+        dev_free(c, st.d_bjobs, st.bjobs.size() * sizeof(OzSliceJob));
+        dev_free(c, st.d_asegs, st.asegs.size() * sizeof(Seg));
+        dev_free(c, st.d_bsegs, st.bsegs.size() * sizeof(Seg));
+        dev_free(c, st.panelA, st.panel_bytes_a);
+        dev_free(c, st.panelB, st.panel_bytes_b);
+        dev_free(c, st.expA, st.exp_bytes_a);
+        dev_free(c, st.expB, st.exp_bytes_b);
+        st = OzStage();
+    }
+    oz.status = nullptr;   // owned by the context
+    oz.ready = false;
+}
+
+// Build the tensor-core form of the two stages of a plan.  Tasks that the tensor path does not take
+// (no segments, several stage-1 segments, K above the exact-accumulation limits) stay in p.thin[st]
+// and run on the FP64 kernel.
+int build_oz(tdmrg_ctx* c, Plan* p, int S) {
+    OzPlan& oz = p->oz;
+    release_oz(c, oz);
+    oz.S = S;
+    oz.status = c->dstatus;
+    int rc = TDMRG_OK;
+    for (int stg = 0; stg < 2; ++stg) {
+        const TaskList& tl = stg == 0 ? p->stage1 : p->stage2;
+        TaskList& thin = p->thin[stg];
+        release(c, thin);
+        thin.tasks.clear(); thin.segs.clear();
+        OzStage& st = oz.st[stg];
+        std::map<int64_t, int> pair_row;   // stage 1: Psi block offset -> A panel row
+        int rowsA = 0, rowsB = 0, kmax = 0;
+        for (size_t t = 0; t < tl.tasks.size(); ++t) {
+            const Task& tk = tl.tasks[t];
+            const int nseg = tk.seg_end - tk.seg_begin;
+            int ktot = 0;
+            for (int s = tk.seg_begin; s < tk.seg_end; ++s) ktot += tl.segs[s].K;
+            const bool ok = nseg > 0 && (stg == 1 || nseg == 1) && 2 * ktot <= 4096;
+            if (!ok) {   // FP64 kernel
+                Task nt = tk;
+                nt.seg_begin = (int)thin.segs.size();
+                for (int s = tk.seg_begin; s < tk.seg_end; ++s) thin.segs.push_back(tl.segs[s]);
+                nt.seg_end = (int)thin.segs.size();
+                thin.tasks.push_back(nt);
+                continue;
+            }
+            OzTask ot{};
+            ot.c_off = tk.c_off; ot.c_buf = tk.c_buf; ot.ldc = tk.ldc; ot.M = tk.M; ot.N = tk.N; ot.beta = tk.beta;
+            ot.kchunks = (2 * ktot + KCH - 1) / KCH;
+            kmax = std::max(kmax, 2 * ktot);
+            // A operand
+            if (stg == 0) {   // A = Psi_{q'}: one dynamic row-sliced panel per input pair, shared by its tasks
+                const Seg& sg = tl.segs[tk.seg_begin];
+                auto it = pair_row.find(sg.a_off);
+                if (it == pair_row.end()) {
+                    Seg js = sg;
+                    js.scale = make_double2(1.0, 0.0);
+                    OzSliceJob j{};
+                    j.role = 0; j.nvec = tk.M; j.seg_begin = (int)st.asegs.size(); j.seg_end = j.seg_begin + 1;
+                    j.row0 = rowsA; j.exp0 = rowsA; j.ktot = sg.K; j.use_scale = 0;
+                    st.asegs.push_back(js);
+                    st.ajobs.push_back(j);
+                    it = pair_row.emplace(sg.a_off, rowsA).first;
+                    rowsA += tk.M;
+                }
+                ot.arow0 = it->second; ot.aexp0 = it->second;
+            } else {          // A = [ops of all segments], coefficients folded in: static
+                OzSliceJob j{};
+                j.role = 0; j.nvec = tk.M; j.seg_begin = (int)st.asegs.size();
+                for (int s = tk.seg_begin; s < tk.seg_end; ++s) st.asegs.push_back(tl.segs[s]);
+                j.seg_end = (int)st.asegs.size();
+                j.row0 = rowsA; j.exp0 = rowsA; j.ktot = ktot; j.use_scale = 1;
+                st.ajobs.push_back(j);
+                ot.arow0 = rowsA; ot.aexp0 = rowsA;
+                rowsA += tk.M;
+            }
+            // B operand: columns of op(B), K-concatenated over segments
+            {
+                OzSliceJob j{};
+                j.role = 1; j.nvec = tk.N; j.seg_begin = (int)st.bsegs.size();
+                for (int s = tk.seg_begin; s < tk.seg_end; ++s) st.bsegs.push_back(tl.segs[s]);
+                j.seg_end = (int)st.bsegs.size();
+                j.row0 = rowsB; j.exp0 = st.ncolsB; j.ktot = ktot;
+                j.use_scale = stg == 0 ? 1 : 0;   // stage 1: the segment scale goes on the static B
+                st.bjobs.push_back(j);
+                ot.brow0 = rowsB; ot.bexp0 = st.ncolsB;
+                const int full = tk.N / TNC, rem = tk.N % TNC;
+                rowsB += 2 * TNC * full + 2 * ((rem + 7) & ~7);
+                st.ncolsB += tk.N;
+            }
+            const int ti = (int)st.tasks.size();
+            st.tasks.push_back(ot);
+            for (int m0 = 0; m0 < tk.M; m0 += TM)
+                for (int n0 = 0; n0 < tk.N; n0 += TNC) st.tiles.push_back({ti, m0, n0, (int)(std::min(TM, tk.M - m0) * std::min(TNC, tk.N - n0)) * ot.kchunks});
+        }
+        std::stable_sort(st.tiles.begin(), st.tiles.end(), [](const OzTile& a, const OzTile& b) { return a.cost > b.cost; });
+        // panels: rows padded so that every TMA box (128 rows for A, 64 for B) stays inside the plane
+        st.rowsA = rowsA + TM;
+        st.rowsB = rowsB + 2 * TNC;
+        st.kpad = std::max(KCH, (kmax + KCH - 1) / KCH * KCH);
+        st.panel_bytes_a = (size_t)S * st.rowsA * st.kpad * 2;
+        st.panel_bytes_b = (size_t)S * st.rowsB * st.kpad * 2;
+        st.exp_bytes_a = (size_t)std::max(rowsA, 1) * sizeof(int);
+        st.exp_bytes_b = (size_t)std::max(st.ncolsB, 1) * sizeof(int);
+        for (size_t j = 0, pre = 0; j < st.ajobs.size(); ++j) { st.ajobs[j].vec_prefix = (int)pre; pre += st.ajobs[j].nvec; }
+        for (size_t j = 0, pre = 0; j < st.bjobs.size(); ++j) { st.bjobs[j].vec_prefix = (int)pre; pre += st.bjobs[j].nvec; }
+        if (!st.tasks.empty()) {
+            rc = dev_alloc(c, (void**)&st.panelA, st.panel_bytes_a, "ozaki panels");
+            if (!rc) rc = dev_alloc(c, (void**)&st.panelB, st.panel_bytes_b, "ozaki panels");
+            if (!rc) rc = dev_alloc(c, (void**)&st.expA, st.exp_bytes_a, "ozaki exponents");
+            if (!rc) rc = dev_alloc(c, (void**)&st.expB, st.exp_bytes_b, "ozaki exponents");
+            if (!rc) rc = cuda_check(c, cudaMemset(st.panelA, 0, st.panel_bytes_a), "ozaki panels");
+            if (!rc) rc = cuda_check(c, cudaMemset(st.panelB, 0, st.panel_bytes_b), "ozaki panels");
+            if (!rc) rc = upload_vec(c, st.tasks, &st.d_tasks, "ozaki tasks");
+            if (!rc) rc = upload_vec(c, st.tiles, &st.d_tiles, "ozaki tiles");
+            if (!rc) rc = upload_vec(c, st.ajobs, &st.d_ajobs, "ozaki slice jobs");
+            if (!rc) rc = upload_vec(c, st.bjobs, &st.d_bjobs, "ozaki slice jobs");
+            if (!rc) rc = upload_vec(c, st.asegs, &st.d_asegs, "ozaki slice segments");
+            if (!rc) rc = upload_vec(c, st.bsegs, &st.d_bsegs, "ozaki slice segments");
+            if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, TM);
+            if (!rc) rc = encode_map(c, &st.mapB, st.panelB, (int64_t)S * st.rowsB, st.kpad, 2 * TNC);
+            if (rc) return rc;
+            st.args.tasks = st.d_tasks; st.args.tiles = st.d_tiles;
+            st.args.expA = st.expA; st.args.expB = st.expB;
+            st.args.rowsA = st.rowsA; st.args.rowsB = st.rowsB; st.args.status = oz.status;
+            auto mk = [&](OzSliceArgs& sa, const std::vector<OzSliceJob>& jobs, OzSliceJob* dj, Seg* ds, __nv_bfloat16* panel,
+                          int* exps, int rows) {
+                sa.jobs = dj; sa.njobs = (int)jobs.size(); sa.segs = ds; sa.panel = panel; sa.exps = exps;
+                sa.rows = rows; sa.kpad = st.kpad; sa.S = S;
+                sa.nvec_total = jobs.empty() ? 0 : jobs.back().vec_prefix + jobs.back().nvec;
+            };
+            mk(st.sliceA, st.ajobs, st.d_ajobs, st.d_asegs, st.panelA, st.expA, st.rowsA);
+            mk(st.sliceB, st.bjobs, st.d_bjobs, st.d_bsegs, st.panelB, st.expB, st.rowsB);
+        }
+        if (!thin.tasks.empty()) {
+            make_tiles(thin, kTileF64, kTileF64, kSplitK);
+            rc = upload(c, thin);
+            if (rc) return rc;
+        }
+    }
+    // static operands: stage-1 B (operators, scales folded) and stage-2 A (operators, scales folded)
+    GemmArgs g{};
+    g.bufs[BUF_OPS] = c->pool;
+    if (!oz.st[0].tasks.empty()) {
+        rc = cuda_check(c, slice_launch(oz.st[0].sliceB, g, c->stream, nullptr, 0), "ozaki static slices");
+        if (rc) return rc;
+    }
+    if (!oz.st[1].tasks.empty()) {
+        rc = cuda_check(c, slice_launch(oz.st[1].sliceA, g, c->stream, nullptr, 0), "ozaki static slices");
+        if (rc) return rc;
+    }
+    oz.ready = true;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "ozaki static slices");
+}
+
+int run_oz(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* skip_flag, int skip_step) {
+    const OzPlan& oz = p.oz;
+    GemmArgs g{};
+    g.bufs[BUF_OPS] = c->pool;
+    g.bufs[BUF_IN] = const_cast<cplx*>(in);
+    g.bufs[BUF_SCRATCH] = c->scratch;
+    g.bufs[BUF_OUT] = out;
+    g.dscale = c->dscale;
+    cudaStream_t s = c->stream;
+    for (int stg = 0; stg < 2; ++stg) {
+        const OzStage& st = oz.st[stg];
+        cudaError_t e = cudaSuccess;
+        if (!st.tasks.empty()) {
+            e = slice_launch(stg == 0 ? st.sliceA : st.sliceB, g, s, skip_flag, skip_step);
+            c->launches++;
+            if (e == cudaSuccess) {
+                switch (oz.S) {
+                    case 2: e = gemm_launch<2>(st, g, s, skip_flag, skip_step); break;
+                    case 3: e = gemm_launch<3>(st, g, s, skip_flag, skip_step); break;
+                    case 4: e = gemm_launch<4>(st, g, s, skip_flag, skip_step); break;
+                    case 5: e = gemm_launch<5>(st, g, s, skip_flag, skip_step); break;
+                    case 6: e = gemm_launch<6>(st, g, s, skip_flag, skip_step); break;
+                    default: e = cudaErrorInvalidValue;
+                }
+                c->launches++;
+            }
+        }
+        const TaskList& thin = p.thin[stg];
+        if (e == cudaSuccess && !thin.tiles.empty()) {
+            GemmArgs a = g;
+            a.tasks = thin.d_tasks; a.segs = thin.d_segs; a.tiles = thin.d_tiles; a.ntiles = (int)thin.tiles.size();
+            a.partials = thin.d_partials; a.counters = thin.d_counters;
+            e = launch_gemm_f64(a, s, skip_flag, skip_step);
+            c->launches++;
+        }
+        int rc = cuda_check(c, e, "ozaki superblock product launch");
+        if (rc) return rc;
+    }
+    return TDMRG_OK;
+}
+
+int oz_status(tdmrg_ctx* c, const Plan& p, int* status) {
+    *status = 0;
+    if (!p.oz.status) return TDMRG_OK;
+    return cuda_check(c, cudaMemcpy(status, p.oz.status, sizeof(int), cudaMemcpyDeviceToHost), "ozaki status");
+}
+
+}  // namespace tdmrg

@@ -262,6 +262,7 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
 }
 
 int run_plan(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* skip_flag, int skip_step) {
+    if (p.oz.ready) return run_oz(c, p, in, out, skip_flag, skip_step);
     GemmArgs a{};
     a.bufs[BUF_OPS] = c->pool;
     a.bufs[BUF_IN] = const_cast<cplx*>(in);

@@ -21,7 +21,7 @@ EXPORTED = [
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect",
-    "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
+    "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
 ]
 
 
@@ -72,6 +72,7 @@ def load(path=LIB_PATH):
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_launch_count": (I, [P, PI64]),
         "tdmrg_hpsi_flops": (I, [P, I, I, PD]),
+        "tdmrg_hpsi_tensor_flops": (I, [P, I, I, PD]),
         "tdmrg_fp64_peak": (I, [I, PD, PD]),
         "tdmrg_apply_h_static": (I, [P, I, I, P, P]),
     }
@@ -239,6 +240,12 @@ def tdmrg_launch_count(ctx):
 def tdmrg_hpsi_flops(ctx, Q):
     f = ctypes.c_double()
     _check(ctx, load().tdmrg_hpsi_flops(ctx, Q[0], Q[1], ctypes.byref(f)))
+    return f.value
+
+
+def tdmrg_hpsi_tensor_flops(ctx, Q):
+    f = ctypes.c_double()
+    _check(ctx, load().tdmrg_hpsi_tensor_flops(ctx, Q[0], Q[1], ctypes.byref(f)))
     return f.value
 
 

@@ -1,0 +1,154 @@
+"""GPU parity of the tensor-core (Ozaki-sliced bf16, tcgen05) superblock product against the oracle.
+
+Error model: operands are represented to 2^{-7S} of their row / column maximum, and the slice
+products are exact, so |GPU - oracle| <= c * 2^{-7S} * max|A| max|B| * K per entry; the tests bound
+the relative error max|err| / max|ref| by 40 * 2^{-7S} * sqrt(K_max) (c and sqrt(K) cover the
+accumulation of independent truncation errors).  Observables after a Krylov trajectory must match
+exact diagonalisation to 1e-8 at S >= 5."""
+import numpy as np
+import pytest
+
+from oracle import ed, krylov, models, superblock
+from tests.gpu_util import ExactLoader, dev, host, new_ctx, oracle_ops_of_synthetic, rel_err
+from workloads import sectors as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1103_5391_gb300 import tdmrg as T
+    return T
+
+
+def _rand(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+def _tol(slices, kmax):
+    return 40.0 * 2.0 ** (-7 * slices) * np.sqrt(kmax)
+
+
+@pytest.mark.parametrize("slices", [3, 4, 5, 6])
+@pytest.mark.parametrize("L,m,nb,seed", [(8, 24, 2, 3), (32, 400, 1, S.SEED_BASE + 1), (32, 800, 2, S.SEED_BASE + 2)])
+def test_ozaki_hpsi(lib, slices, L, m, nb, seed):
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(L, m, 4.0, nbonds=nb, seed=seed)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=slices)
+    try:
+        problem.load_synthetic(ctx, ss)
+        for Q in (ss.Q0, ss.Q1):
+            n = lib.tdmrg_sector_size(ctx, Q)
+            x = _rand(n, 2)
+            out = dev(np.full(n, np.nan + 0j))
+            lib.tdmrg_apply_h(ctx, Q, dev(x), out)
+            ref = superblock.apply_h(sb, HL, HR, conns, Q, x)
+            err = rel_err(host(out), ref)
+            kmax = 5 * max(ss.ldim) * (1 + 2 * nb)
+            assert err < _tol(slices, kmax), (slices, err)
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
+def test_ozaki_error_decreases_with_slices(lib):
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(16, 120, 4.0, nbonds=1, seed=17)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    x = _rand(ss.sector_size(ss.Q1), 4)
+    ref = superblock.apply_h(sb, HL, HR, conns, ss.Q1, x)
+    errs = []
+    for slices in (2, 3, 4, 5, 6):
+        ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=slices)
+        try:
+            problem.load_synthetic(ctx, ss)
+            out = dev(np.zeros(len(x)))
+            lib.tdmrg_apply_h(ctx, ss.Q1, dev(x), out)
+            errs.append(rel_err(host(out), ref))
+        finally:
+            lib.tdmrg_destroy(ctx)
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 16, errs                 # each slice adds 7 bits
+    assert errs[-1] < 5e-12, errs           # about 2^-42 times the accumulated operand scale
+
+
+def test_ozaki_switch_precision_and_fp64_parity(lib):
+    """set_precision rebuilds the plans; FP64 after Ozaki is bit-for-bit the FP64 result."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(12, 60, 4.0, nbonds=2, seed=23)
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = lib.tdmrg_sector_size(ctx, ss.Q1)
+        x = dev(_rand(n, 5))
+        a, b, c = dev(np.zeros(n)), dev(np.zeros(n)), dev(np.zeros(n))
+        lib.tdmrg_apply_h(ctx, ss.Q1, x, a)
+        lib.tdmrg_set_precision(ctx, lib.TDMRG_OZAKI_BF16, 5)
+        lib.tdmrg_apply_h(ctx, ss.Q1, x, b)
+        lib.tdmrg_set_precision(ctx, lib.TDMRG_FP64, 4)
+        lib.tdmrg_apply_h(ctx, ss.Q1, x, c)
+        assert np.array_equal(host(a), host(c))
+        assert rel_err(host(b), host(a)) < 1e-9
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("slices", [5, 6])
+def test_ozaki_trajectory_against_ed(lib, c1_problem, c1_ground, slices):
+    """L=8 chain, U=4, c^dag_{4 up}: 20 Krylov steps of tau=0.1 on the tensor path; n_i(t) vs ED <= 1e-8."""
+    p = c1_problem
+    e, psi = c1_ground
+    Q1 = (5, 4)
+    tau, nv, nk, steps = 0.1, 4, 12, 20
+    times = krylov.target_times(tau, nv)
+    sec = ed.Sector(8, *Q1)
+    H = ed.hamiltonian(sec, ed.chain_hopping(8), 4.0)
+    perm = superblock.fock_to_psi(p.cut, sec, np.arange(sec.dim) + 0j).real.astype(int)
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=slices)
+    try:
+        ld = ExactLoader(ctx, p)
+        oL, oR = ld.local("cdag", 4, 0)
+        nops = [[ld.local("n", site, s) for s in (0, 1)] for site in range(8)]
+        n = lib.tdmrg_sector_size(ctx, Q1)
+        phi = dev(np.zeros(n))
+        lib.tdmrg_apply_op(ctx, oL, oR, p.Q, dev(psi), Q1, phi)
+        phif = np.zeros(sec.dim, complex); phif[perm] = host(phi)
+        tg = [dev(np.zeros(n)) for _ in range(nv - 1)] + [phi]
+        out = dev(np.zeros(1))
+        worst = 0.0
+        for s in range(steps):
+            lib.tdmrg_evolve(ctx, Q1, phi, times, nk, tg)
+            if s % 4 == 3:
+                ex = ed.evolve(H, phif, [(s + 1) * tau])[0]
+                for site in range(8):
+                    d = 0.0
+                    for a, b in nops[site]:
+                        lib.tdmrg_expect(ctx, a, b, Q1, phi, out)
+                        d += host(out)[0].real
+                    d_ed = ed.density(ex, sec, site, 0) + ed.density(ex, sec, site, 1)
+                    worst = max(worst, abs(d - d_ed))
+        lib.tdmrg_evolve_info(ctx)          # raises if a bounded device wait ran out
+        assert worst < 1e-8, worst
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
+def test_ozaki_synthetic_evolve(lib):
+    """One advance of the L=32 m=400 chain twin on the tensor path (S=5) against the FP64 oracle."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(32, 400, 4.0, nbonds=1, seed=S.SEED_BASE + 1)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    times = krylov.target_times(0.05, 4)
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=5)
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = lib.tdmrg_sector_size(ctx, ss.Q1)
+        tg = [dev(np.zeros(n)) for _ in times]
+        lib.tdmrg_evolve(ctx, ss.Q1, dev(ss.phi), times, 10, tg)
+        ref, n_used, err = krylov.evolve(lambda v: superblock.apply_h(sb, HL, HR, conns, ss.Q1, v), ss.phi, times, 10)
+        lib.tdmrg_evolve_info(ctx)
+        for x in range(len(times)):
+            assert rel_err(host(tg[x]), ref[x]) < 1e-8
+    finally:
+        lib.tdmrg_destroy(ctx)
