@@ -176,6 +176,51 @@ int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg
 int tdmrg_expect(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdmrg_c64* psi_d,
                  tdmrg_c64* out_d);
 
+/* ---- serving: continuous batching of time-evolution jobs ----------------------------------------
+ * A server drives many independent time evolutions (each the repeated time step of Sec. II.C:
+ * Krylov advance with n_v targets, weighted rho_L of the ground state and the targets with its
+ * eigendecomposition, and observables after the step) on one GPU.  A host thread admits submitted
+ * jobs in arrival order while the summed HBM footprint of the running jobs stays within the budget
+ * and fewer than max_active run; every running job owns a stream, so the steps of different jobs
+ * overlap on the device; a job's first step runs directly and the following steps replay a CUDA
+ * graph captured from it.  Results are bit-for-bit those of the same job run alone (every kernel is
+ * deterministic and a job's work never reads another job's memory). */
+typedef struct tdmrg_server tdmrg_server;
+
+enum tdmrg_job_status { TDMRG_JOB_QUEUED = 0, TDMRG_JOB_RUNNING = 1, TDMRG_JOB_DONE = 2, TDMRG_JOB_CANCELLED = 3,
+                        TDMRG_JOB_FAILED = 4 };
+
+typedef struct {
+    tdmrg_ctx* ctx;              /* blocks, operators and H loaded; used only by the server until the job ends */
+    int q_gs[2];                 /* sector of the ground state                                              */
+    const tdmrg_c64* psi_gs_d;   /* ground state (device); caller-owned, must stay valid until the job ends  */
+    int q[2];                    /* sector of the evolving state                                            */
+    const tdmrg_c64* phi0_d;     /* initial state phi (device); copied when the job is admitted              */
+    double tau;                  /* time step; targets at t_x = x tau / (n_v - 1)                           */
+    int n_v, nk, steps;          /* time targets (2..16), Krylov dimension, number of time steps            */
+    int nobs;                    /* observables measured after every step (0..16)                            */
+    int32_t obs_opL[16], obs_opR[16];   /* left / right op ids of each observable (-1 = identity)         */
+} tdmrg_job;
+
+/* Create a server on `device`: hbm_budget bytes for the footprint of running jobs (0 = no limit),
+ * at most max_active jobs at once.  Starts the server thread.  Errors: EINVAL, ECUDA. */
+int tdmrg_server_create(tdmrg_server** out, int device, size_t hbm_budget, int max_active);
+/* Queue a job (non-blocking); *job_id identifies it.  Errors: EINVAL (bad description). */
+int tdmrg_server_submit(tdmrg_server* srv, const tdmrg_job* job, int64_t* job_id);
+/* Non-blocking state of a job.  obs (host, steps * nobs entries, nullable) receives the observables of
+ * the finished steps in step order; step_ms (host, steps floats, nullable) the device time of each
+ * finished step (CUDA events on the job's stream, queueing behind other jobs included).
+ * Errors: EINVAL (unknown id). */
+int tdmrg_server_poll(tdmrg_server* srv, int64_t job_id, int* status, int* steps_done, tdmrg_c64* obs, float* step_ms);
+/* Stop a job after its step in flight; its slot and memory are released.  Errors: EINVAL. */
+int tdmrg_server_cancel(tdmrg_server* srv, int64_t job_id);
+/* Counts of queued, running and finished (done, cancelled or failed) jobs and the bytes in use. */
+int tdmrg_server_stats(tdmrg_server* srv, int* queued, int* running, int* finished, size_t* bytes_in_use);
+/* Stop the server thread, wait for every stream, release all job buffers (job contexts stay the caller's). */
+int tdmrg_server_destroy(tdmrg_server* srv);
+/* Text of the last server-level error, or of the failure of job_id when job_id >= 0. */
+const char* tdmrg_server_last_error(tdmrg_server* srv, int64_t job_id);
+
 /* H psi that allocates no device memory during the call.  The paper has no counterpart: this exists
  * for callers that may not allocate once they run -- a real-time loop that forbids allocation after
  * initialisation, a framework whose own pool owns all device memory, a plugin limited to the buffers

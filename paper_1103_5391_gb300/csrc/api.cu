@@ -72,6 +72,8 @@ void drop_plans(tdmrg_ctx* c) {
         release_oz(c, kv.second->oz);
     }
     c->plans.clear();
+    for (auto& kv : c->rho_plans) release(c, *kv.second);
+    c->rho_plans.clear();
 }
 
 void drop_krylov(tdmrg_ctx* c) {

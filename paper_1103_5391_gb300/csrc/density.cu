@@ -47,35 +47,40 @@ int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* ps
     for (int l = 0; l < nt; ++l) wl.w[l] = w[l];
     k_weight_scale<<<1, 32 * 12, 0, s>>>(c->red, nt, c->dscale, wl);
     c->launches++;
-    // task list: one task per left sector
-    TaskList tl;
-    int64_t off = 0;
-    for (size_t qi = 0; qi < L.dim.size(); ++qi) {
-        Task tk{};
-        tk.c_off = off; tk.c_buf = BUF_OUT; tk.ldc = L.dim[qi]; tk.M = L.dim[qi]; tk.N = L.dim[qi]; tk.beta = 0;
-        tk.seg_begin = (int)tl.segs.size();
-        for (int l = 0; l < nt; ++l) {
-            int ri = R.find(Q[2 * l] - L.nup[qi], Q[2 * l + 1] - L.ndn[qi]);
-            if (ri < 0) continue;
-            // offset of Psi_l(q) inside target l
-            int64_t po = 0;
-            for (size_t k = 0; k < qi; ++k) {
-                int rk = R.find(Q[2 * l] - L.nup[k], Q[2 * l + 1] - L.ndn[k]);
-                if (rk >= 0) po += (int64_t)L.dim[k] * R.dim[rk];
+    // task list: one task per left sector, compiled once per set of target sectors
+    std::vector<int> key(Q, Q + 2 * nt);
+    auto it = c->rho_plans.find(key);
+    if (it == c->rho_plans.end()) {
+        std::unique_ptr<TaskList> tl(new TaskList());
+        int64_t off = 0;
+        for (size_t qi = 0; qi < L.dim.size(); ++qi) {
+            Task tk{};
+            tk.c_off = off; tk.c_buf = BUF_OUT; tk.ldc = L.dim[qi]; tk.M = L.dim[qi]; tk.N = L.dim[qi]; tk.beta = 0;
+            tk.seg_begin = (int)tl->segs.size();
+            for (int l = 0; l < nt; ++l) {
+                int ri = R.find(Q[2 * l] - L.nup[qi], Q[2 * l + 1] - L.ndn[qi]);
+                if (ri < 0) continue;
+                int64_t po = 0;   // offset of Psi_l(q) inside target l
+                for (size_t k = 0; k < qi; ++k) {
+                    int rk = R.find(Q[2 * l] - L.nup[k], Q[2 * l + 1] - L.ndn[k]);
+                    if (rk >= 0) po += (int64_t)L.dim[k] * R.dim[rk];
+                }
+                Seg sg{};
+                sg.a_off = po; sg.a_buf = (int8_t)(BUF_EXTRA0 + l); sg.lda = R.dim[ri];
+                sg.b_off = po; sg.b_buf = (int8_t)(BUF_EXTRA0 + l); sg.ldb = R.dim[ri]; sg.opb = OPB_C;
+                sg.K = R.dim[ri]; sg.scale = make_double2(1.0, 0.0); sg.dscale = l;
+                tl->segs.push_back(sg);
             }
-            Seg sg{};
-            sg.a_off = po; sg.a_buf = (int8_t)(BUF_EXTRA0 + l); sg.lda = R.dim[ri];
-            sg.b_off = po; sg.b_buf = (int8_t)(BUF_EXTRA0 + l); sg.ldb = R.dim[ri]; sg.opb = OPB_C;
-            sg.K = R.dim[ri]; sg.scale = make_double2(1.0, 0.0); sg.dscale = l;
-            tl.segs.push_back(sg);
+            tk.seg_end = (int)tl->segs.size();
+            tl->tasks.push_back(tk);
+            off += (int64_t)L.dim[qi] * L.dim[qi];
         }
-        tk.seg_end = (int)tl.segs.size();
-        tl.tasks.push_back(tk);
-        off += (int64_t)L.dim[qi] * L.dim[qi];
+        make_tiles(*tl, kTileF64, kTileF64, kSplitK);
+        int rc = upload(c, *tl);
+        if (rc) { release(c, *tl); return rc; }
+        it = c->rho_plans.emplace(key, std::move(tl)).first;
     }
-    make_tiles(tl, kTileF64, kTileF64, kSplitK);
-    int rc = upload(c, tl);
-    if (rc) { release(c, tl); return rc; }
+    const TaskList& tl = *it->second;
     GemmArgs a{};
     a.tasks = tl.d_tasks; a.segs = tl.d_segs; a.tiles = tl.d_tiles; a.ntiles = (int)tl.tiles.size();
     a.partials = tl.d_partials; a.counters = tl.d_counters;
@@ -85,9 +90,6 @@ int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* ps
     a.dscale = c->dscale;
     cudaError_t e = launch_gemm_f64(a, s, nullptr, 0);
     c->launches++;
-    // the task list is freed after the stream reaches this point
-    cudaStreamSynchronize(s);
-    release(c, tl);
     return cuda_check(c, e, "density_matrix launch");
 }
 

@@ -297,7 +297,11 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
             make_tiles(tl, kTileF64, kTileF64, kSplitK);
             return upload(c, tl);
         };
-        rc = one(w.tl_ax, EB_AX, EB_RHO, EB_X, -1, -1, -1);
+        // the opt-in is a property of the kernel on the device, shared by every context: always the maximum
+        rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)((size_t)2 * kSmemMaxN * (kSmemMaxN | 1) * sizeof(float2))),
+                        "eig smem");
+        if (!rc) rc = one(w.tl_ax, EB_AX, EB_RHO, EB_X, -1, -1, -1);
         if (!rc) rc = one(w.tl_sg, EB_S, EB_XH, EB_AX, EB_G, EB_XH, EB_X);
         if (!rc) rc = one(w.tl_y, EB_Y, EB_X, EB_E, -1, -1, -1);
         if (rc) return rc;
@@ -313,9 +317,6 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     cplx* Y = evecs;   // ping-pong with the caller's output, which receives the sorted result at the end
     const int sm = std::min(w.maxn, kSmemMaxN);
     const size_t smem = (size_t)2 * sm * (sm | 1) * sizeof(float2);
-    int rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                        "eig smem");
-    if (rc) return rc;
     k_rho_fro<<<ns, 256, 0, s>>>(rho, w.fro, tb);
     k_jacobi32<<<ns, JT, smem, s>>>(rho, X, tb, w.gwork);
     c->launches += 2;

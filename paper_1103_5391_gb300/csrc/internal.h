@@ -212,6 +212,7 @@ struct tdmrg_ctx {
     std::vector<tdmrg::Term> ham;
     int ham_version = 0;
     std::map<std::tuple<int, int, int, int, int, int, int>, std::unique_ptr<tdmrg::Plan>> plans;
+    std::map<std::vector<int>, std::unique_ptr<tdmrg::TaskList>> rho_plans;   // keyed by the targets' sectors
     // generic workspace
     tdmrg::cplx* scratch = nullptr;
     int64_t scratch_cap = 0;

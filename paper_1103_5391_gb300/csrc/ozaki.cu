@@ -357,10 +357,14 @@ int encode_map(tdmrg_ctx* c, CUtensorMap* m, void* base, int64_t rows, int kpad,
 }
 
 template <int S>
+cudaError_t gemm_attr() {
+    const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
+    return cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int S>
 cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     k_ozaki_gemm<S><<<(int)st.tiles.size(), 128, smem, s>>>(st.mapA, st.mapB, st.args, g, skip_flag, skip_step);
     return cudaGetLastError();
 }
@@ -532,6 +536,12 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             rc = upload(c, thin);
             if (rc) return rc;
         }
+    }
+    {   // shared-memory opt-in of the GEMM for this S (set here, outside any stream capture)
+        cudaError_t e = S == 2 ? gemm_attr<2>() : S == 3 ? gemm_attr<3>() : S == 4 ? gemm_attr<4>()
+                      : S == 5 ? gemm_attr<5>() : gemm_attr<6>();
+        rc = cuda_check(c, e, "ozaki shared memory");
+        if (rc) return rc;
     }
     // static operands: stage-1 B (operators, scales folded) and stage-2 A (operators, scales folded)
     GemmArgs g{};

@@ -22,7 +22,17 @@ EXPORTED = [
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect",
     "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
+    "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
+    "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
+TDMRG_JOB_QUEUED, TDMRG_JOB_RUNNING, TDMRG_JOB_DONE, TDMRG_JOB_CANCELLED, TDMRG_JOB_FAILED = 0, 1, 2, 3, 4
+
+
+class tdmrg_job(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("q_gs", ctypes.c_int * 2), ("psi_gs_d", ctypes.c_void_p),
+                ("q", ctypes.c_int * 2), ("phi0_d", ctypes.c_void_p), ("tau", ctypes.c_double), ("n_v", ctypes.c_int),
+                ("nk", ctypes.c_int), ("steps", ctypes.c_int), ("nobs", ctypes.c_int),
+                ("obs_opL", ctypes.c_int32 * 16), ("obs_opR", ctypes.c_int32 * 16)]
 
 
 class tdmrg_opts(ctypes.Structure):
@@ -75,6 +85,14 @@ def load(path=LIB_PATH):
         "tdmrg_hpsi_tensor_flops": (I, [P, I, I, PD]),
         "tdmrg_fp64_peak": (I, [I, PD, PD]),
         "tdmrg_apply_h_static": (I, [P, I, I, P, P]),
+        "tdmrg_server_create": (I, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
+        "tdmrg_server_submit": (I, [P, ctypes.POINTER(tdmrg_job), PI64]),
+        "tdmrg_server_poll": (I, [P, ctypes.c_int64, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
+        "tdmrg_server_cancel": (I, [P, ctypes.c_int64]),
+        "tdmrg_server_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                   ctypes.POINTER(ctypes.c_size_t)]),
+        "tdmrg_server_destroy": (I, [P]),
+        "tdmrg_server_last_error": (ctypes.c_char_p, [P, ctypes.c_int64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -258,3 +276,65 @@ def tdmrg_fp64_peak(device=0):
 def tdmrg_apply_h_static(ctx, Q, psi, out):
     """H psi with scratch from the library's static device array (no allocation during the call)."""
     return _check(ctx, load().tdmrg_apply_h_static(ctx, Q[0], Q[1], _ptr(psi), _ptr(out)))
+
+
+# ----------------------------------------------------------------------------- serving
+def _scheck(srv, rc, job=-1):
+    if rc != TDMRG_OK:
+        m = load().tdmrg_server_last_error(srv, job)
+        raise TdmrgError(rc, m.decode() if m else "")
+    return rc
+
+
+def tdmrg_server_create(device=0, hbm_budget=0, max_active=8):
+    h = ctypes.c_void_p()
+    _check(None, load().tdmrg_server_create(ctypes.byref(h), device, hbm_budget, max_active))
+    return h
+
+
+def tdmrg_server_submit(srv, ctx, Q_gs, psi_gs, Q, phi0, tau, n_v, nk, steps, observables=()):
+    """observables: list of (opL, opR) measured after every step."""
+    j = tdmrg_job()
+    j.ctx = ctx.value if hasattr(ctx, "value") else ctx
+    j.q_gs[0], j.q_gs[1] = Q_gs
+    j.psi_gs_d = psi_gs.data_ptr()
+    j.q[0], j.q[1] = Q
+    j.phi0_d = phi0.data_ptr()
+    j.tau, j.n_v, j.nk, j.steps = tau, n_v, nk, steps
+    j.nobs = len(observables)
+    for k, (a, b) in enumerate(observables):
+        j.obs_opL[k], j.obs_opR[k] = a, b
+    jid = ctypes.c_int64()
+    _scheck(srv, load().tdmrg_server_submit(srv, ctypes.byref(j), ctypes.byref(jid)))
+    return jid.value
+
+
+def tdmrg_server_poll(srv, job_id, steps=0, nobs=0):
+    """(status, steps_done, observables [steps_done x nobs] complex, step_ms [steps_done])."""
+    st, done = ctypes.c_int(), ctypes.c_int()
+    obs = np.zeros(max(steps * nobs, 1), dtype=np.complex128)
+    ms = np.zeros(max(steps, 1), dtype=np.float32)
+    _scheck(srv, load().tdmrg_server_poll(srv, job_id, ctypes.byref(st), ctypes.byref(done),
+                                          obs.ctypes.data_as(ctypes.c_void_p) if steps * nobs else None,
+                                          ms.ctypes.data_as(ctypes.c_void_p) if steps else None))
+    n = done.value
+    return st.value, n, obs[: n * nobs].reshape(n, nobs) if nobs else None, ms[:n]
+
+
+def tdmrg_server_cancel(srv, job_id):
+    return _scheck(srv, load().tdmrg_server_cancel(srv, job_id))
+
+
+def tdmrg_server_stats(srv):
+    q, r, f, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _scheck(srv, load().tdmrg_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f), ctypes.byref(b)))
+    return q.value, r.value, f.value, b.value
+
+
+def tdmrg_server_destroy(srv):
+    return load().tdmrg_server_destroy(srv)
+
+
+def tdmrg_server_last_error(srv, job_id=-1):
+    m = load().tdmrg_server_last_error(srv, job_id)
+    return m.decode() if m else ""

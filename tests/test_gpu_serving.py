@@ -1,0 +1,118 @@
+"""Serving (continuous batching of time-evolution jobs): every job's observables in the mix equal
+the same job run alone (bit for bit: deterministic kernels, no shared memory between jobs); jobs
+arriving while others run are admitted as slots and budget free up; cancellation frees a slot."""
+import time
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import new_ctx, torch_cuda
+from workloads import sectors as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _job(T, problem, torch, L, m, nb, seed, prec):
+    ss = S.make_synthetic(L, m, 4.0, nbonds=nb, seed=seed)
+    ctx = new_ctx(prec=prec, ozaki_slices=4)
+    problem.load_synthetic(ctx, ss)
+    psi = torch.as_tensor(ss.psi_gs).cuda()
+    phi = torch.zeros(T.tdmrg_sector_size(ctx, ss.Q1), dtype=torch.complex128, device="cuda")
+    T.tdmrg_apply_op(ctx, -1, problem.OP_EXC, ss.Q0, psi, ss.Q1, phi)
+    torch.cuda.synchronize()
+    return ss, ctx, psi, phi
+
+
+def _run(T, srv, jobs, steps, arrivals, problem):
+    ids = []
+    t0 = time.time()
+    for (ss, ctx, psi, phi), at in zip(jobs, arrivals):
+        while time.time() - t0 < at:
+            time.sleep(0.001)
+        ids.append(T.tdmrg_server_submit(srv, ctx, ss.Q0, psi, ss.Q1, phi, 0.05, 4, 8, steps,
+                                         [(problem.OP_N, -1), (-1, problem.OP_N)]))
+    out = {}
+    deadline = time.time() + 300
+    while len(out) < len(ids) and time.time() < deadline:
+        for jid in ids:
+            if jid in out:
+                continue
+            st, n, obs, ms = T.tdmrg_server_poll(srv, jid, steps, 2)
+            if st >= T.TDMRG_JOB_DONE:
+                assert st == T.TDMRG_JOB_DONE, T.tdmrg_server_last_error(srv, jid)
+                out[jid] = (st, obs, ms)
+        time.sleep(0.005)
+    return [out[j] for j in ids]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mix_equals_alone(prec):
+    torch = torch_cuda()
+    from paper_1103_5391_gb300 import problem
+    from paper_1103_5391_gb300 import tdmrg as T
+    specs = [(16, 128, 1, 101), (20, 200, 2, 102), (24, 300, 1, 103), (16, 160, 2, 104), (28, 256, 1, 105)]
+    steps = 6
+    jobs = [_job(T, problem, torch, *sp, prec) for sp in specs]
+    try:
+        alone = []
+        for jb in jobs:   # one at a time
+            srv = T.tdmrg_server_create(0, 0, 1)
+            try:
+                alone.append(_run(T, srv, [jb], steps, [0.0], problem)[0])
+            finally:
+                T.tdmrg_server_destroy(srv)
+        srv = T.tdmrg_server_create(0, 0, 3)   # three slots: later arrivals wait for a free slot
+        try:
+            mixed = _run(T, srv, jobs, steps, [0.0, 0.0, 0.01, 0.02, 0.03], problem)
+            q, r, f, b = T.tdmrg_server_stats(srv)
+            assert (q, r, f) == (0, 0, len(jobs))
+        finally:
+            T.tdmrg_server_destroy(srv)
+        for (sa, oa, ma), (sm, om, mm) in zip(alone, mixed):
+            assert sa == sm == T.TDMRG_JOB_DONE
+            assert oa.shape == (steps, 2) and np.isfinite(oa).all()
+            assert np.array_equal(oa, om)
+            assert len(mm) == steps and (mm > 0).all()
+    finally:
+        for ss, ctx, psi, phi in jobs:
+            T.tdmrg_destroy(ctx)
+
+
+def test_budget_cancel_and_errors():
+    torch = torch_cuda()
+    from paper_1103_5391_gb300 import problem
+    from paper_1103_5391_gb300 import tdmrg as T
+    jobs = [_job(T, problem, torch, 20, 200, 1, 200 + k, 0) for k in range(3)]
+    try:
+        srv = T.tdmrg_server_create(0, 1, 4)   # 1-byte budget: one job at a time, in arrival order
+        try:
+            ids = [T.tdmrg_server_submit(srv, ctx, ss.Q0, psi, ss.Q1, phi, 0.05, 4, 8, 40, [(problem.OP_N, -1)])
+                   for ss, ctx, psi, phi in jobs]
+            seen_running = 0
+            for _ in range(2000):
+                q, r, f, b = T.tdmrg_server_stats(srv)
+                seen_running = max(seen_running, r)
+                if r == 1 and q == 2:
+                    break
+                time.sleep(0.001)
+            assert seen_running <= 1
+            T.tdmrg_server_cancel(srv, ids[0])
+            T.tdmrg_server_cancel(srv, ids[2])
+            for _ in range(20000):
+                st = [T.tdmrg_server_poll(srv, j, 40, 1)[0] for j in ids]
+                if all(x >= T.TDMRG_JOB_DONE for x in st):
+                    break
+                time.sleep(0.002)
+            assert st[0] == T.TDMRG_JOB_CANCELLED and st[2] == T.TDMRG_JOB_CANCELLED
+            assert st[1] == T.TDMRG_JOB_DONE
+            assert T.tdmrg_server_poll(srv, ids[1], 40, 1)[1] == 40
+            with pytest.raises(T.TdmrgError):
+                T.tdmrg_server_poll(srv, 999, 1, 1)
+            ss, ctx, psi, phi = jobs[0]
+            with pytest.raises(T.TdmrgError):   # n_v = 1 is not time-step targeting
+                T.tdmrg_server_submit(srv, ctx, ss.Q0, psi, ss.Q1, phi, 0.05, 1, 8, 4)
+        finally:
+            T.tdmrg_server_destroy(srv)
+    finally:
+        for ss, ctx, psi, phi in jobs:
+            T.tdmrg_destroy(ctx)
