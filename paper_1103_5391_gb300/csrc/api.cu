@@ -87,6 +87,7 @@ void drop_krylov(tdmrg_ctx* c) {
         dev_free(c, k.tri, 128 * sizeof(double));
         dev_free(c, k.flags, 4 * sizeof(int));
         dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
+        dev_free(c, k.bar, 2 * sizeof(unsigned));
     }
     c->krylov.clear();
     c->last_krylov = nullptr;
@@ -144,7 +145,8 @@ int check_device_status(tdmrg_ctx* c) {
     if (rc) return rc;
     if (st) {
         cudaMemset(c->dstatus, 0, sizeof(int));
-        return fail(c, TDMRG_ETIMEOUT, "a bounded device wait in a tensor-core kernel ran out; results are invalid");
+        return fail(c, TDMRG_ETIMEOUT, "a bounded device wait ran out (tensor-core mbarrier or Lanczos grid barrier); "
+                                       "results are invalid");
     }
     return TDMRG_OK;
 }

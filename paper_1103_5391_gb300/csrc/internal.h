@@ -170,6 +170,8 @@ struct KrylovWork {     // device workspace of tdmrg_evolve for one (Q, nk)
     double* tri = nullptr;      // alpha[32], beta[32], beta0, resid, err
     int* flags = nullptr;       // n_used
     cplx* coef = nullptr;       // [x][k] Krylov coefficients
+    unsigned* bar = nullptr;    // grid barrier of the fused orthogonalisation
+    int orth_grid = 0;
 };
 
 // Workspace of the rho_L eigensolver (eig.cu), built once per left block.

@@ -4,11 +4,12 @@
 // Lanczos is started from phi itself: v_0 = phi / ||phi||.  Step j: w = H v_j (grouped superblock
 // product), alpha_j = Re <v_j|w>, then two classical Gram-Schmidt passes against v_0..v_j
 // (the first pass also removes the alpha_j v_j and beta_j v_{j-1} components), beta_{j+1} = ||w||,
-// v_{j+1} = w / beta_{j+1}; the recursion stops at n_K vectors or when
-// beta_{j+1} <= tol * max(1, |alpha_j|).  Then T = S^dag D S is diagonalised (one warp, cyclic
+// v_{j+1} = w / beta_{j+1}, all in one cooperative launch per step; the recursion stops at n_K
+// vectors or when beta_{j+1} <= tol * max(1, |alpha_j|).  Then T = S^dag D S is diagonalised (one warp, cyclic
 // Jacobi, FP64) and the targets phi(t_x) = ||phi|| sum_k v_k [S^dag e^{-i D t_x} S]_{k,0} are formed
 // in one pass over V.  Everything is FP64 and stays on the device; reductions use a fixed grid and
 // a fixed summation order, so results do not depend on scheduling.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -99,85 +100,171 @@ __global__ void __launch_bounds__(NT) k_init_v0(const cplx* __restrict__ phi, in
     }
 }
 
-// Pass 0: partials of <v_k|w>, k < nv.
-__global__ void __launch_bounds__(NT) k_dots(const cplx* __restrict__ V, int nv, int64_t n, const cplx* __restrict__ w,
-                                              double2* __restrict__ part, const int* __restrict__ flags, int j) {
-    if (j >= flags[0]) return;
-    int64_t lo, hi;
-    chunk_of(n, lo, hi);
-    for (int k = 0; k < nv; ++k) {
-        const cplx* vk = V + (int64_t)k * n;
-        double2 s = make_double2(0.0, 0.0);
-        for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
-            const double2 p = cdotc(vk[i], w[i]);
-            s.x += p.x; s.y += p.y;
-        }
-        double2 t = block_sum(s);
-        if (threadIdx.x == 0) part[(int64_t)k * NB + blockIdx.x] = t;
-    }
-}
+// ---- one Lanczos orthogonalisation step in a single cooperative launch -----------------------
+// Three grid barriers separate: (A) dots <v_k|w>; (B) w -= sum h_k v_k and the second-pass dots;
+// (C) w -= sum h2_k v_k and ||w||^2; (D) beta, breakdown test, v_{j+1} = w / beta.  Every block
+// reduces the partials of all blocks in the same fixed order, so results do not depend on scheduling.
+// The barrier spins are bounded: when one runs out the kernel sets a status bit and finishes.
+constexpr int OB = 256;   // threads per block of the fused kernel
+constexpr long kBarrierSpin = 1L << 24;
 
-// w -= sum_k h_k v_k with h from partIn; then partials of <v_k|w> (final = 0) or of ||w||^2 (final = 1).
-__global__ void __launch_bounds__(NT) k_orth(const cplx* __restrict__ V, int nv, int64_t n, cplx* __restrict__ w,
-                                              const double2* __restrict__ partIn, double2* __restrict__ partOut,
-                                              double* __restrict__ tri, const int* __restrict__ flags, int j,
-                                              int record_alpha, int final_norm) {
-    if (j >= flags[0]) return;
-    __shared__ double2 h[33];
-    reduce_coeffs(partIn, nv, h);
-    if (record_alpha && blockIdx.x == 0 && threadIdx.x == 0) tri[T_ALPHA + j] = h[j].x;
-    int64_t lo, hi;
-    chunk_of(n, lo, hi);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
-        double2 x = w[i];
-        for (int k = 0; k < nv; ++k) {
-            const double2 p = cmul(h[k], V[(int64_t)k * n + i]);
-            x.x -= p.x; x.y -= p.y;
+struct OrthArgs {
+    const cplx* V;
+    cplx* w;
+    int64_t n;
+    int nv, j, nk;
+    double tol;
+    double2* partA;
+    double2* partB;
+    double* tri;
+    int* flags;
+    unsigned* bar;     // [0] arrivals, [1] generation
+    int* status;
+};
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long it = 0;
+            while (*gen == g0) {
+                if (++it > kBarrierSpin) { atomicOr(status, 2); break; }
+            }
         }
-        w[i] = x;
+        __threadfence();
     }
     __syncthreads();
-    if (final_norm) {
-        double s = 0.0;
-        for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = w[i]; s += v.x * v.x + v.y * v.y; }
-        double2 t = block_sum(make_double2(s, 0.0));
-        if (threadIdx.x == 0) partOut[blockIdx.x] = t;
-    } else {
-        for (int k = 0; k < nv; ++k) {
-            const cplx* vk = V + (int64_t)k * n;
-            double2 s = make_double2(0.0, 0.0);
-            for (int64_t i = lo + threadIdx.x; i < hi; i += NT) {
-                const double2 p = cdotc(vk[i], w[i]);
-                s.x += p.x; s.y += p.y;
-            }
-            double2 t = block_sum(s);
-            if (threadIdx.x == 0) partOut[(int64_t)k * NB + blockIdx.x] = t;
+}
+
+// block sums of 8 complex values (fixed order); result valid in threads 0..7 as out[t]
+__device__ void block_sum8(double2 (&v)[8], double2* sh /* [OB/32][8] */, double2* out) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[k].x += __shfl_xor_sync(0xffffffffu, v[k].x, o);
+            v[k].y += __shfl_xor_sync(0xffffffffu, v[k].y, o);
         }
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sh[w * 8 + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int ww = 0; ww < OB / 32; ++ww) { s.x += sh[ww * 8 + threadIdx.x].x; s.y += sh[ww * 8 + threadIdx.x].y; }
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// partials[k * gridDim + b] for k < nv  ->  every block's h[k] (same order everywhere)
+__device__ void sum_partials(const double2* __restrict__ part, int nv, double2* h) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int k = w; k < nv; k += OB / 32) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int b = l; b < (int)gridDim.x; b += 32) { s.x += part[(int64_t)k * gridDim.x + b].x; s.y += part[(int64_t)k * gridDim.x + b].y; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (l == 0) h[k] = s;
+    }
+    __syncthreads();
+}
+
+// dots <v_k|w> over this block's chunk for all k < nv, written as partials
+__device__ void chunk_dots(const cplx* __restrict__ V, const cplx* __restrict__ w, int64_t n, int nv, int64_t lo,
+                           int64_t hi, double2* part, double2* sh, double2* red8) {
+    for (int k0 = 0; k0 < nv; k0 += 8) {
+        double2 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = make_double2(0.0, 0.0);
+        for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
+            const double2 x = w[i];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k0 + k < nv) {
+                    const double2 p = cdotc(V[(int64_t)(k0 + k) * n + i], x);
+                    acc[k].x += p.x; acc[k].y += p.y;
+                }
+        }
+        block_sum8(acc, sh, red8);
+        if (threadIdx.x < 8 && k0 + (int)threadIdx.x < nv) part[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = red8[threadIdx.x];
     }
 }
 
-// beta_{j+1} = ||w||; v_{j+1} = w / beta_{j+1}, or stop (last step or breakdown).
-__global__ void __launch_bounds__(NT) k_normalize(const cplx* __restrict__ w, int64_t n, const double2* __restrict__ part,
-                                                   cplx* __restrict__ vnext, double* __restrict__ tri, int* __restrict__ flags,
-                                                   int j, int nk, double tol) {
-    if (j >= flags[0]) return;
-    __shared__ double2 h[1];
-    reduce_coeffs(part, 1, h);
-    const double beta = sqrt(h[0].x);
-    const double alpha = tri[T_ALPHA + j];
-    const bool stop = (j == nk - 1) || (beta <= tol * fmax(1.0, fabs(alpha)));
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        tri[T_BETA + j] = beta;
-        if (stop) {
-            tri[T_RESID] = beta;
-            flags[0] = j + 1;
+__global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
+    if (a.j >= a.flags[0]) return;   // uniform: the flag only changes after the last barrier
+    __shared__ double2 sh[(OB / 32) * 8];
+    __shared__ double2 red8[8];
+    __shared__ double2 h[33];
+    const int64_t ch = (a.n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = min(a.n, (int64_t)blockIdx.x * ch), hi = min(a.n, lo + ch);
+    // (A) first-pass dots
+    chunk_dots(a.V, a.w, a.n, a.nv, lo, hi, a.partA, sh, red8);
+    grid_barrier(a.bar, a.status);
+    // (B) subtract, second-pass dots
+    sum_partials(a.partA, a.nv, h);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.tri[T_ALPHA + a.j] = h[a.j].x;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
+        double2 x = a.w[i];
+        for (int k = 0; k < a.nv; ++k) {
+            const double2 p = cmul(h[k], a.V[(int64_t)k * a.n + i]);
+            x.x -= p.x; x.y -= p.y;
         }
+        a.w[i] = x;
     }
-    if (stop) return;
+    __syncthreads();
+    chunk_dots(a.V, a.w, a.n, a.nv, lo, hi, a.partB, sh, red8);
+    grid_barrier(a.bar, a.status);
+    // (C) subtract again, norm
+    sum_partials(a.partB, a.nv, h);
+    double nn = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
+        double2 x = a.w[i];
+        for (int k = 0; k < a.nv; ++k) {
+            const double2 p = cmul(h[k], a.V[(int64_t)k * a.n + i]);
+            x.x -= p.x; x.y -= p.y;
+        }
+        a.w[i] = x;
+        nn += x.x * x.x + x.y * x.y;
+    }
+    {
+        double2 v8[8];
+        v8[0] = make_double2(nn, 0.0);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) v8[k] = make_double2(0.0, 0.0);
+        block_sum8(v8, sh, red8);
+        if (threadIdx.x == 0) a.partA[blockIdx.x] = red8[0];
+    }
+    grid_barrier(a.bar, a.status);
+    // (D) beta, stop test, v_{j+1}
+    sum_partials(a.partA, 1, h);
+    const double beta = sqrt(h[0].x);
+    const double alpha = a.tri[T_ALPHA + a.j];
+    const bool stop = (a.j == a.nk - 1) || (beta <= a.tol * fmax(1.0, fabs(alpha)));
+    if (stop) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.tri[T_BETA + a.j] = beta;
+            a.tri[T_RESID] = beta;
+            a.flags[0] = a.j + 1;   // read by later kernels only (every block is past its check)
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.tri[T_BETA + a.j] = beta;
     const double inv = 1.0 / beta;
-    int64_t lo, hi;
-    chunk_of(n, lo, hi);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = w[i]; vnext[i] = make_double2(v.x * inv, v.y * inv); }
+    cplx* vnext = const_cast<cplx*>(a.V) + (int64_t)(a.j + 1) * a.n;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) { const double2 x = a.w[i]; vnext[i] = make_double2(x.x * inv, x.y * inv); }
 }
 
 struct Times { double t[16]; };
@@ -368,6 +455,13 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
     if (!rc) rc = dev_alloc(c, (void**)&k.tri, 128 * sizeof(double), "Krylov tridiagonal");
     if (!rc) rc = dev_alloc(c, (void**)&k.flags, 4 * sizeof(int), "Krylov flags");
     if (!rc) rc = dev_alloc(c, (void**)&k.coef, 16 * 32 * sizeof(cplx), "Krylov coefficients");
+    if (!rc) rc = dev_alloc(c, (void**)&k.bar, 2 * sizeof(unsigned), "Krylov grid barrier");
+    if (!rc) rc = cuda_check(c, cudaMemset(k.bar, 0, 2 * sizeof(unsigned)), "Krylov grid barrier");
+    if (!rc) {   // co-resident grid of the fused orthogonalisation: at most one block per SM, at most NB
+        int per_sm = 0;
+        rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_orth, OB, 0), "occupancy");
+        k.orth_grid = std::max(1, std::min({c->num_sms * std::max(per_sm, 1), c->num_sms, NB}));
+    }
     if (rc) {
         dev_free(c, k.V, (size_t)(nk + 1) * n * sizeof(cplx));
         dev_free(c, k.w, (size_t)n * sizeof(cplx));
@@ -376,6 +470,7 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
         dev_free(c, k.tri, 128 * sizeof(double));
         dev_free(c, k.flags, 4 * sizeof(int));
         dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
+        dev_free(c, k.bar, 2 * sizeof(unsigned));
         return rc;
     }
     c->krylov[key] = k;
@@ -418,12 +513,22 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
         cplx* vj = k->V + (int64_t)j * n;
         rc = run_plan(c, *p, vj, k->w, k->flags, j);
         if (rc) return rc;
-        k_dots<<<NB, NT, 0, s>>>(k->V, j + 1, n, k->w, k->partA, k->flags, j);
-        k_orth<<<NB, NT, 0, s>>>(k->V, j + 1, n, k->w, k->partA, k->partB, k->tri, k->flags, j, 1, 0);
-        k_orth<<<NB, NT, 0, s>>>(k->V, j + 1, n, k->w, k->partB, k->partA, k->tri, k->flags, j, 0, 1);
-        k_normalize<<<NB, NT, 0, s>>>(k->w, n, k->partA, k->V + (int64_t)(j + 1) * n, k->tri, k->flags, j, nk,
-                                      c->opts.breakdown_tol);
-        c->launches += 4;
+        OrthArgs oa{k->V, k->w, n, j + 1, j, nk, c->opts.breakdown_tol, k->partA, k->partB, k->tri, k->flags,
+                    k->bar, c->dstatus};
+        void* params[] = {&oa};
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(k->orth_grid);
+        cfg.blockDim = dim3(OB);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t le = cudaLaunchKernelExC(&cfg, (const void*)k_lanczos_orth, params);
+        if (le != cudaSuccess) return cuda_check(c, le, "Lanczos orthogonalisation launch");
+        c->launches += 1;
     }
     k_tridiag_exp<<<1, 32, 0, s>>>(k->tri, k->flags, tt, n_v, k->coef);
     TargetPtrs tg{};
