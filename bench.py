@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", choices=["ozaki", "fp64"], default="ozaki")
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--serving", action="store_true", help="serving mix instead of the single-workload line")
+    ap.add_argument("--jobs", type=int, default=24)
+    ap.add_argument("--job-steps", type=int, default=20)
+    ap.add_argument("--max-active", type=int, default=8)
     return ap.parse_args()
 
 
@@ -244,6 +248,20 @@ class Runner:
     def reset(self):
         self.phi.copy_(self.phi0)
 
+    def capture(self, torch, stream):
+        """One time step as a CUDA graph (after a direct step has compiled plans and workspace)."""
+        side = torch.cuda.Stream(device=stream.device)
+        side.wait_stream(stream)
+        self.T.tdmrg_set_stream(self.ctx, side.cuda_stream)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=side, capture_error_mode="thread_local"):
+            self.step()
+        self.T.tdmrg_set_stream(self.ctx, stream.cuda_stream)
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+
     def step(self):
         T, c, P = self.T, self.ctx, self.P
         T.tdmrg_evolve(c, self.Q1, self.phi, self.times, self.nk, self.targets)
@@ -254,13 +272,16 @@ class Runner:
         T.tdmrg_expect(c, -1, P.OP_N, self.Q1, self.phi, self.obs[1:2])
 
 
-def timed_steps(torch, runner, steps, flush, stream, barrier):
+def timed_steps(torch, runner, steps, flush, stream, barrier, graph=False):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier()
     for e0, e1 in ev:
         flush.fill_(1)
         e0.record(stream)
-        runner.step()
+        if graph:
+            runner.replay()
+        else:
+            runner.step()
         e1.record(stream)
     barrier()
     return [a.elapsed_time(b) for a, b in ev]
@@ -318,14 +339,18 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    run.step()                      # compiles plans, allocates workspace
+    l0 = T.tdmrg_launch_count(ctx)
+    run.step()
+    launches_per_step = T.tdmrg_launch_count(ctx) - l0
+    run.capture(torch, stream)      # the timed step is one CUDA-graph replay of the same launches
     for _ in range(args.warmup):
-        run.step()
+        run.replay()
     barrier()
     sampler = ClockSampler(local)
     time.sleep(0.25)
-    l0 = T.tdmrg_launch_count(ctx)
-    step_ms = timed_steps(torch, run, args.steps, flush, stream, barrier)
-    launches = T.tdmrg_launch_count(ctx) - l0
+    step_ms = timed_steps(torch, run, args.steps, flush, stream, barrier, graph=True)
+    launches = launches_per_step * args.steps
     clocks = sampler.stop()
     T.tdmrg_evolve_info(ctx)   # raises if a bounded device wait ran out during the timed steps
     total_ms = sum(step_ms)
@@ -377,9 +402,11 @@ def run_ours(args):
         T.tdmrg_set_precision(ctx, T.TDMRG_FP64, 4)
         traj_f = trajectory(torch, run, traj_steps)
         run.reset()
+        run.step()
+        run.capture(torch, stream)
         for _ in range(2):
-            run.step()
-        f_ms = timed_steps(torch, run, min(args.steps, 40), flush, stream, barrier)
+            run.replay()
+        f_ms = timed_steps(torch, run, min(args.steps, 40), flush, stream, barrier, graph=True)
         hf_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
         fp64 = {"value": nk * len(f_ms) / (sum(f_ms) * 1e-3), "unit": UNIT, "ms_per_step": statistics.mean(f_ms),
                 "hpsi_ms": hf_ms, "hpsi_tflops": alg / (hf_ms * 1e-3) / 1e12,
@@ -417,6 +444,7 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * run.n1,
                     "d2h_bytes_per_step": 16 * 2 + 8 * run.ne},
             "gpu_launches": launches,
+            "step_mode": "CUDA graph replay of one time step (captured from the direct C-ABI calls)",
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -426,10 +454,80 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args):
+    """Continuous batching: a seeded Poisson stream of time-evolution jobs of mixed geometry and size
+    through tdmrg_server_* (admission by HBM footprint, per-job streams, CUDA-graph steps)."""
+    import torch
+    from paper_1103_5391_gb300 import problem
+    from paper_1103_5391_gb300 import tdmrg as T
+    from workloads import sectors as S
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(S.SEED_BASE + 4)
+    jobs, t_gen = [], time.perf_counter()
+    for k in range(args.jobs):
+        L = int(rng.choice(np.arange(16, 50, 2)))
+        ladder = bool(rng.integers(2))
+        U = float(rng.choice([2.0, 4.0, 8.0]))
+        m = int(round(np.exp(rng.uniform(np.log(128), np.log(768)))))
+        ss = S.make_synthetic(L, m, U, nbonds=2 if ladder else 1, seed=S.SEED_BASE + 100 + k)
+        ctx = T.tdmrg_create(device=0, stream=torch.cuda.current_stream().cuda_stream, prec=T.TDMRG_OZAKI_BF16,
+                             ozaki_slices=args.slices)
+        problem.load_synthetic(ctx, ss)
+        psi = torch.as_tensor(ss.psi_gs).cuda()
+        phi = torch.zeros(T.tdmrg_sector_size(ctx, ss.Q1), dtype=torch.complex128, device="cuda")
+        T.tdmrg_apply_op(ctx, -1, problem.OP_EXC, ss.Q0, psi, ss.Q1, phi)
+        jobs.append(dict(L=L, ladder=ladder, U=U, m=m, ss=ss, ctx=ctx, psi=psi, phi=phi))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    gaps = rng.exponential(0.02, args.jobs)       # mean inter-arrival 20 ms
+    srv = T.tdmrg_server_create(0, 0, args.max_active)
+    nk, steps = WL["nk"], args.job_steps
+    ids, peak_running = [], 0
+    t0 = time.perf_counter()
+    t_next = t0
+    for jb, gap in zip(jobs, gaps):
+        t_next += gap
+        while time.perf_counter() < t_next:
+            peak_running = max(peak_running, T.tdmrg_server_stats(srv)[1])
+            time.sleep(0.0005)
+        ss = jb["ss"]
+        ids.append(T.tdmrg_server_submit(srv, jb["ctx"], ss.Q0, jb["psi"], ss.Q1, jb["phi"], WL["tau"], WL["n_v"], nk, steps,
+                                         [(problem.OP_N, -1), (-1, problem.OP_N)]))
+    done = {}
+    while len(done) < len(ids):
+        peak_running = max(peak_running, T.tdmrg_server_stats(srv)[1])
+        for jid in ids:
+            if jid not in done:
+                st, n, obs, ms = T.tdmrg_server_poll(srv, jid, steps, 2)
+                if st >= T.TDMRG_JOB_DONE:
+                    done[jid] = (st, ms)
+        time.sleep(0.001)
+    makespan = time.perf_counter() - t0
+    T.tdmrg_server_destroy(srv)
+    ms = np.concatenate([done[j][1] for j in ids])
+    ok = sum(1 for j in ids if done[j][0] == T.TDMRG_JOB_DONE)
+    for jb in jobs:
+        T.tdmrg_destroy(jb["ctx"])
+    line = {"metric": "serving mix: Krylov steps/s and per-step latency", "value": ok * steps * nk / makespan,
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"Poisson stream of {args.jobs} jobs (mean inter-arrival 20 ms), chains and 2-leg "
+                                   f"ladders L in [16, 48], U in {{2, 4, 8}}, m log-uniform in [128, 768], tau=0.05, "
+                                   f"n_v=4, n_K=10, {steps} time steps each, ozaki-bf16 x{args.slices}",
+                       "max_active": args.max_active},
+            "jobs_done": ok, "makespan_s": makespan, "peak_running": peak_running,
+            "step_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                                "mean": float(ms.mean())},
+            "host_generation_s": t_gen}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
     return run_ours(args)
 
 
