@@ -272,6 +272,18 @@ class Runner:
         T.tdmrg_expect(c, -1, P.OP_N, self.Q1, self.phi, self.obs[1:2])
 
 
+def replica_value(total_ms, work_units, world_size, device=None):
+    """Whole-job throughput of independent replicas: the units all ranks processed divided by the
+    slowest rank's timed device time (one all-reduce of a scalar; no data-path collective)."""
+    import torch
+    if world_size > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world_size * work_units / (total_ms * 1e-3), total_ms
+
+
 def timed_steps(torch, runner, steps, flush, stream, barrier, graph=False):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier()
@@ -353,14 +365,8 @@ def run_ours(args):
     launches = launches_per_step * args.steps
     clocks = sampler.stop()
     T.tdmrg_evolve_info(ctx)   # raises if a bounded device wait ran out during the timed steps
-    total_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     nk = run.nk
-    value = ws * nk * args.steps / (total_ms * 1e-3)
+    value, total_ms = replica_value(sum(step_ms), nk * args.steps, ws, dev)
 
     # H psi alone (all launches of one product), CUDA events on its stream, L2 flushed
     Q1 = run.Q1
@@ -386,13 +392,7 @@ def run_ours(args):
         ev_h.copy_(run.evals, non_blocking=True)
         e1.record(stream)
     barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = ws * nk * e2e_steps / (e2e_ms * 1e-3)
+    e2e_val, e2e_ms = replica_value(sum(a.elapsed_time(b) for a, b in ee), nk * e2e_steps, ws, dev)
 
     # the plain FP64 GPU path on the same workload, and the observable error of this path against it
     fp64 = None
