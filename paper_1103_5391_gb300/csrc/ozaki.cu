@@ -330,6 +330,193 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOLS));
 }
 
+// ---- warp-specialised persistent variant (S <= 4) -------------------------------------------------
+// One CTA per SM walks the tile list (tile = blockIdx.x, + gridDim.x, ...).  Warp 0 issues the TMA
+// loads into NST shared-memory stages, one thread of warp 1 issues the MMAs, warps 2..5 drain the
+// TMEM accumulators.  Accumulation blocks (<= 8 chunks of one tile) alternate between two TMEM
+// buffers, so the epilogue of one block overlaps the MMAs of the next.  Hand-offs:
+//   full[st]  (TMA -> MMA, transaction bytes)     empty[st] (MMA completion -> TMA)
+//   tfull[b]  (MMA completion -> epilogue)         tempty[b] (epilogue warps -> MMA)
+constexpr int NST = 2;
+constexpr long kWaitWS = 1L << 22;
+
+__device__ __forceinline__ bool mbar_wait_ws(uint32_t bar, uint32_t parity, volatile int* failed) {
+    for (long i = 0; i < kWaitWS; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((i & 1023) == 1023 && *failed) return false;
+    }
+    *failed = 1;
+    return false;
+}
+
+template <int S>
+__global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant__ CUtensorMap mapA,
+                                                          const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa,
+                                                          GemmArgs g, int ntiles, const int* skip_flag, int skip_step) {
+    if (skip_flag != nullptr && skip_step >= *skip_flag) return;
+    static_assert(S <= 4, "two TMEM buffers of S x 64 columns must fit in 512");
+    constexpr uint32_t NCOLS = 512;
+    constexpr uint32_t STAGE = S * (ABOX + BBOX);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        failed = 0;
+        for (int i = 0; i < NST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&tfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(smem_u32(&tempty[i])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tmem_base)), "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ---------------------------------------------------------------- TMA producer
+            uint32_t c = 0;
+            for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                const OzTile tile = oa.tiles[t];
+                const OzTask task = oa.tasks[tile.task];
+                const int ya = task.arow0 + tile.m0, yb = task.brow0 + 2 * tile.n0;
+                for (int k = 0; k < task.kchunks; ++k, ++c) {
+                    const int st = c % NST;
+                    if (!mbar_wait_ws(smem_u32(&empty[st]), ((c / NST) & 1) ^ 1, &failed)) break;
+                    unsigned char* sA = smem + st * STAGE;
+                    unsigned char* sB = sA + S * ABOX;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&full[st])), "r"(STAGE) : "memory");
+#pragma unroll
+                    for (int s = 0; s < S; ++s) {
+                        tma_load(smem_u32(sA + s * ABOX), &mapA, k * KCH, s * oa.rowsA + ya, smem_u32(&full[st]));
+                        tma_load(smem_u32(sB + s * BBOX), &mapB, k * KCH, s * oa.rowsB + yb, smem_u32(&full[st]));
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---------------------------------------------------------------- MMA issuer
+            uint32_t c = 0, b = 0;
+            for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                const OzTile tile = oa.tiles[t];
+                const OzTask task = oa.tasks[tile.task];
+                const int nrem = task.N - tile.n0;
+                const int n_t = ((nrem < TNC ? nrem : TNC) + 7) & ~7;
+                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * n_t) >> 3) << 17) |
+                                       ((uint32_t)(TM >> 4) << 24);
+                for (int k0 = 0; k0 < task.kchunks && !failed; k0 += kReadoutChunks, ++b) {
+                    const int buf = b & 1;
+                    if (!mbar_wait_ws(smem_u32(&tempty[buf]), ((b >> 1) & 1) ^ 1, &failed)) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const int k1 = min(task.kchunks, k0 + kReadoutChunks);
+                    for (int k = k0; k < k1; ++k, ++c) {
+                        const int st = c % NST;
+                        if (!mbar_wait_ws(smem_u32(&full[st]), (c / NST) & 1, &failed)) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        unsigned char* sA = smem + st * STAGE;
+                        unsigned char* sB = sA + S * ABOX;
+#pragma unroll
+                        for (int ks = 0; ks < KCH / 16; ++ks) {
+#pragma unroll
+                            for (int gg = 2; gg <= S + 1; ++gg) {
+                                const int s_lo = gg - S > 1 ? gg - S : 1, s_hi = gg - 1 < S ? gg - 1 : S;
+#pragma unroll
+                                for (int s = s_lo; s <= s_hi; ++s) {
+                                    const uint64_t da = desc_sw128(smem_u32(sA + (s - 1) * ABOX) + ks * 32);
+                                    const uint64_t db = desc_sw128(smem_u32(sB + (gg - s - 1) * BBOX) + ks * 32);
+                                    const uint32_t accum = (k == k0 && ks == 0 && s == s_lo) ? 0u : 1u;
+                                    umma(tmem + (uint32_t)(buf * S * 64 + (gg - 2) * 64), da, db, idesc, accum);
+                                }
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     :: "r"(smem_u32(&empty[st])) : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&tfull[buf])) : "memory");
+                }
+            }
+        }
+    } else {   // ------------------------------------------------------------------------ epilogue warps 2..5
+        const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31
+        const int row = 32 * quad + lane;
+        uint32_t b = 0;
+        for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+            const OzTile tile = oa.tiles[t];
+            const OzTask task = oa.tasks[tile.task];
+            const int nrem = task.N - tile.n0;
+            const int nval = nrem < TNC ? nrem : TNC;
+            const int n_t = (nval + 7) & ~7;
+            long long acc[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) acc[j] = 0;
+            bool ok = true;
+            for (int k0 = 0; k0 < task.kchunks; k0 += kReadoutChunks, ++b) {
+                const int buf = b & 1;
+                if (!mbar_wait_ws(smem_u32(&tfull[buf]), (b >> 1) & 1, &failed)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                for (int gg = 2; gg <= S + 1; ++gg) {
+                    const int shift = 7 * (S + 1 - gg);
+                    uint32_t r[4][16];
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb)
+                        if (cb * 16 < 2 * n_t)
+                            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * S * 64 + (gg - 2) * 64 + cb * 16), r[cb]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb)
+                        if (cb * 16 < 2 * n_t) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[cb][j])) << shift;
+                        }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&tempty[buf])) : "memory");
+            }
+            if (!ok) break;
+            if (tile.m0 + row < task.M) {
+                const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
+                double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * task.ldc + tile.n0);
+#pragma unroll
+                for (int jj = 0; jj < 64; ++jj) {
+                    if (jj < 2 * n_t) {
+                        const bool im = jj >= n_t;
+                        const int j = im ? jj - n_t : jj;
+                        if (j < nval) {
+                            const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
+                            double v = scaled_int(acc[jj], e);
+                            double* pc = C + 2 * j + (im ? 1 : 0);
+                            if (task.beta) v += *pc;
+                            *pc = v;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (failed && tid == 0) atomicOr(oa.status, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOLS));
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -358,12 +545,26 @@ int encode_map(tdmrg_ctx* c, CUtensorMap* m, void* base, int64_t rows, int kpad,
 
 template <int S>
 cudaError_t gemm_attr() {
-    const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
-    return cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (S <= 4) {
+        const size_t smem = (size_t)NST * S * (ABOX + BBOX) + 1024;
+        return cudaFuncSetAttribute(k_ozaki_gemm_ws<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    } else {
+        const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
+        return cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
 }
+
+int g_num_sms = 0;
 
 template <int S>
 cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
+    if constexpr (S <= 4) {
+        const size_t smem = (size_t)NST * S * (ABOX + BBOX) + 1024;
+        const int ntiles = (int)st.tiles.size();
+        const int grid = std::max(1, std::min(ntiles, g_num_sms));
+        k_ozaki_gemm_ws<S><<<grid, 192, smem, s>>>(st.mapA, st.mapB, st.args, g, ntiles, skip_flag, skip_step);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
     k_ozaki_gemm<S><<<(int)st.tiles.size(), 128, smem, s>>>(st.mapA, st.mapB, st.args, g, skip_flag, skip_step);
     return cudaGetLastError();
@@ -537,6 +738,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (rc) return rc;
         }
     }
+    g_num_sms = c->num_sms;
     {   // shared-memory opt-in of the GEMM for this S (set here, outside any stream capture)
         cudaError_t e = S == 2 ? gemm_attr<2>() : S == 3 ? gemm_attr<3>() : S == 4 ? gemm_attr<4>()
                       : S == 5 ? gemm_attr<5>() : gemm_attr<6>();
