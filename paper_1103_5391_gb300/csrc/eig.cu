@@ -11,7 +11,8 @@
 //         E_ij = R_ij / 2 otherwise (and on the diagonal),  delta = 2 (||S - diag(lambda)|| + ||rho|| ||R||),
 //         X <- X (I + E);
 //      convergence is quadratic; three iterations take the FP32 seed to FP64 accuracy, including
-//      near-degenerate pairs that the first iteration treats as a cluster;
+//      near-degenerate pairs that the first iteration treats as a cluster.  The iterate is kept as
+//      W = X^H, so every product is a plain or conjugate-transposed GEMM operand;
 //   3. sort each sector's eigenpairs by descending eigenvalue.
 #include <algorithm>
 #include <cmath>
@@ -24,7 +25,11 @@ namespace {
 
 constexpr int JT = 1024;  // threads of the FP32 Jacobi CTA (warps over rotation pairs, lanes over rows)
 constexpr int kSmemMaxN = 112;
-constexpr int kRefine = 3;       // refinement iterations   // A and V as float2 in shared memory: 2 * 112^2 * 8 B = 196 KB
+constexpr int kMaxEigN = 512;    // largest sector dimension
+constexpr int kKChunk = 16;      // K chunk of the refinement GEMMs
+constexpr int kRefine = 3;       // refinement iterations always run
+constexpr int kMaxRefine = 4;    // one more when the last correction was not yet at rounding level
+constexpr double kTolE = 1e-7;   // |E| above this: the next error (~|E|^2) may exceed ~1e-14       // refinement iterations   // A and V as float2 in shared memory: 2 * 112^2 * 8 B = 196 KB
 
 struct EigTables {
     const int64_t* off;   // per sector: offset of its n x n block
@@ -35,9 +40,10 @@ struct EigTables {
 __device__ __forceinline__ float2 cmf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// FP32 seed: X0 (unsorted columns) of each sector's rho block.
-__global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, cplx* __restrict__ X, EigTables tb,
-                                                 float2* __restrict__ gwork) {
+// FP32 seed: W0 = X0^H (X0: unsorted eigenvector columns) of each sector's rho block, and ||rho||_F.
+__global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, cplx* __restrict__ W,
+                                                 double* __restrict__ rho_fro, int* __restrict__ n_iter,
+                                                 EigTables tb, float2* __restrict__ gwork) {
     extern __shared__ float2 fsm[];
     const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
     const int64_t off = tb.off[sct];
@@ -51,8 +57,8 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
     __shared__ float2 sn[256];
     __shared__ float red[JT / 32];
     __shared__ float thr_s;
-    __shared__ int rotated;
     const cplx* R = rho + off;
+    if (sct == 0 && tid == 0) *n_iter = kRefine;
     for (int e = tid; e < n * n; e += JT) {
         const int r = e / n, cc = e % n;
         const double2 v = R[e];
@@ -69,19 +75,20 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
         float f = 0.f;
         for (int k = 0; k < JT / 32; ++k) f += red[k];
         thr_s = 4.8e-7f * sqrtf(f);   // 4 eps_fp32 ||A||_F: above FP32 rounding noise, so sweeps terminate
+        rho_fro[sct] = sqrtf(f);      // ||rho||_F for the refinement's cluster threshold
     }
     __syncthreads();
     const float thr = thr_s;
     const int P = n + (n & 1), npair = P / 2;
     for (int sweep = 0; sweep < 12 && n > 1; ++sweep) {
-        __syncthreads();
-        if (tid == 0) rotated = 0;
-        __syncthreads();
         for (int round = 0; round < P - 1; ++round) {
             for (int i = tid; i < npair; i += JT) {
                 int p, q;
                 if (i == 0) { p = P - 1; q = round; }
-                else { p = (round + i) % (P - 1); q = (round - i + (P - 1)) % (P - 1); }
+                else {   // (round + i) and (round - i) mod P - 1, with 0 <= round < P - 1 and 0 < i < P / 2
+                    p = round + i; if (p >= P - 1) p -= P - 1;
+                    q = round - i; if (q < 0) q += P - 1;
+                }
                 if (p > q) { int t = p; p = q; q = t; }
                 float c = 1.f;
                 float2 s = make_float2(0.f, 0.f);
@@ -92,13 +99,17 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
                         A[p * ld + q] = make_float2(0.f, 0.f);
                         A[q * ld + p] = make_float2(0.f, 0.f);
                     } else {
-                        rotated = 1;
                         const float a = A[p * ld + p].x, d = A[q * ld + q].x;
                         const float tau = (d - a) / (2.f * ab);
                         const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
                         c = rsqrtf(1.f + t * t);
                         const float sv = t * c / ab;
                         s = make_float2(sv * b.x, sv * b.y);   // s e^{i theta}, b = |b| e^{i theta}
+                        // one Newton step on 1 / sqrt(c^2 + |s|^2): J unitary to about one ulp, so the
+                        // hundreds of rotations accumulated in V keep it orthonormal to ~1e-6
+                        const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s.x, s.x, s.y * s.y)), 1.5f);
+                        c *= f;
+                        s.x *= f; s.y *= f;
                     }
                 }
                 pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
@@ -107,7 +118,7 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
             const int warp = tid >> 5, lane = tid & 31;
             for (int i = warp; i < npair; i += JT / 32) {   // rows: A <- J^H A
                 const int p = pp[i], q = qq[i];
-                if (q >= n) continue;
+                if (q >= n || (sn[i].x == 0.f && sn[i].y == 0.f)) continue;   // identity: nothing to rotate
                 const float c = cs[i];
                 const float2 s = sn[i], sc = conjf2(s);
                 for (int k = lane; k < n; k += 32) {
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
             __syncthreads();
             for (int i = warp; i < npair; i += JT / 32) {   // columns: A <- A J, V <- V J
                 const int p = pp[i], q = qq[i];
-                if (q >= n) continue;
+                if (q >= n || (sn[i].x == 0.f && sn[i].y == 0.f)) continue;   // identity: nothing to rotate
                 const float c = cs[i];
                 const float2 s = sn[i], sc = conjf2(s);
                 for (int k = lane; k < n; k += 32) {
@@ -136,116 +147,164 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
             }
             __syncthreads();
         }
-        __syncthreads();
-        if (!rotated) break;
+        // the next sweep rotates only pairs above the threshold: stop when there are none
+        bool above = false;
+        for (int e = tid; e < n * n; e += JT) {
+            const int r = e / n, cc = e % n;
+            if (r < cc) {
+                const float2 b = A[r * ld + cc];
+                above |= sqrtf(b.x * b.x + b.y * b.y) > thr;
+            }
+        }
+        if (!__syncthreads_or(above)) break;
     }
-    cplx* Xs = X + off;
+    cplx* Ws = W + off;   // W = V^H: row j is the conjugate of eigenvector j
     for (int e = tid; e < n * n; e += JT) {
-        const float2 v = V[(e / n) * ld + e % n];
-        Xs[e] = make_double2(v.x, v.y);
+        const float2 v = V[(e % n) * ld + e / n];
+        Ws[e] = make_double2(v.x, -v.y);
     }
 }
 
-// Xh = X^H per sector.
-__global__ void k_conj_transpose(const cplx* __restrict__ X, cplx* __restrict__ Xh, EigTables tb) {
-    const int sct = blockIdx.x, n = tb.dims[sct];
-    const int64_t off = tb.off[sct];
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        const double2 v = X[off + (int64_t)j * n + i];
-        Xh[off + e] = make_double2(v.x, -v.y);
-    }
+// Refinement on W = X^H, which turns every product into a plain or conjugate-transposed operand of the
+// grouped GEMM: rho X = rho W^H, G = W W^H, S = W (rho X), and X <- X (I + E) is W <- (I + E)^H W.
+// The element-wise steps run on (sector, row chunk) CTAs: FP64 arithmetic is slow per SM, so one CTA
+// per sector would leave the largest sector's elements on one SM.
+constexpr int kRowChunks = 8;
+
+__device__ __forceinline__ void chunk_rows(int n, int ch, int& r0, int& r1) {
+    const int rows = (n + kRowChunks - 1) / kRowChunks;
+    r0 = min(n, ch * rows);
+    r1 = min(n, r0 + rows);
 }
 
-// One refinement step's correction: E1 = I + E from S, G; eigenvalue estimates into lam.
-__global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, const cplx* __restrict__ G,
-                                                   const double* __restrict__ rho_fro, cplx* __restrict__ E1,
-                                                   double* __restrict__ lam, EigTables tb) {
-    const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
-    const int64_t off = tb.off[sct];
-    const int64_t eo = tb.eoff[sct];
-    __shared__ double red[2][8];
-    __shared__ double delta_s;
-    for (int i = tid; i < n; i += blockDim.x) lam[eo + i] = S[off + (int64_t)i * n + i].x / G[off + (int64_t)i * n + i].x;
+__device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[8]) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = a; red[1][threadIdx.x >> 5] = b; }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0.0; b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x / 32); ++k) { a += red[0][k]; b += red[1][k]; }
+    }
+}
+
+// lambda_i = Re S_ii / Re G_ii for the chunk's rows; partial squared Frobenius norms of S - diag(lambda)
+// and R = I - G over the chunk's rows into part[(sector, chunk)].
+__global__ void __launch_bounds__(256) k_oa_norms(const cplx* __restrict__ S, const cplx* __restrict__ G,
+                                                  double* __restrict__ lam, double* __restrict__ part,
+                                                  const int* __restrict__ n_iter, int it, EigTables tb) {
+    if (it >= *n_iter) return;   // refinement already converged
+    const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
+    const int64_t off = tb.off[sct], eo = tb.eoff[sct];
+    __shared__ double red[2][8];
+    int r0, r1;
+    chunk_rows(n, ch, r0, r1);
     double offS = 0.0, rr = 0.0;
-    for (int e = tid; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        double2 s = S[off + e];
-        if (i == j) s.x -= lam[eo + i];
-        offS += s.x * s.x + s.y * s.y;
-        double2 g = G[off + e];
+    for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
+        const int i = r0 + e / n, j = e % n;
+        double2 sv = S[off + (int64_t)i * n + j];
+        const double2 g = G[off + (int64_t)i * n + j];
+        if (i == j) {
+            const double l = sv.x / g.x;
+            lam[eo + i] = l;
+            sv.x -= l;
+        }
+        offS += sv.x * sv.x + sv.y * sv.y;
         const double rx = (i == j ? 1.0 : 0.0) - g.x, ry = -g.y;
         rr += rx * rx + ry * ry;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        offS += __shfl_xor_sync(0xffffffffu, offS, o);
-        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    block_sum2(offS, rr, red);
+    if (threadIdx.x == 0) {
+        part[2 * ((int64_t)sct * kRowChunks + ch)] = offS;
+        part[2 * ((int64_t)sct * kRowChunks + ch) + 1] = rr;
     }
-    if ((tid & 31) == 0) { red[0][tid >> 5] = offS; red[1][tid >> 5] = rr; }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < (int)(blockDim.x / 32); ++k) { a += red[0][k]; b += red[1][k]; }
-        delta_s = 2.0 * (sqrt(a) + rho_fro[sct] * sqrt(b));
+}
+
+// Rows of E1^H = (I + E)^H for the chunk.  With S and R = I - G Hermitian and lambda real, the
+// conjugate of E_ji = (S_ji + lambda_i R_ji) / (lambda_i - lambda_j) is
+// (S_ij + lambda_i R_ij) / (lambda_i - lambda_j), and that of the cluster value R_ji / 2 is R_ij / 2.
+// delta = 2 (||S - diag(lambda)||_F + ||rho||_F ||R||_F), partial sums added in a fixed order.
+__global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, const cplx* __restrict__ G,
+                                                   const double* __restrict__ lam, const double* __restrict__ part,
+                                                   const double* __restrict__ rho_fro, cplx* __restrict__ E1h,
+                                                   int* __restrict__ n_iter, int it, EigTables tb) {
+    if (it >= *n_iter) return;   // refinement already converged
+    const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
+    const int64_t off = tb.off[sct], eo = tb.eoff[sct];
+    int r0, r1;
+    chunk_rows(n, ch, r0, r1);
+    if (r0 >= r1) return;
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < kRowChunks; ++k) {
+        a += part[2 * ((int64_t)sct * kRowChunks + k)];
+        b += part[2 * ((int64_t)sct * kRowChunks + k) + 1];
     }
-    __syncthreads();
-    const double delta = delta_s;
-    for (int e = tid; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        const double2 g = G[off + e];
+    const double delta = 2.0 * (sqrt(a) + rho_fro[sct] * sqrt(b));
+    bool big = false;
+    for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
+        const int i = r0 + e / n, j = e % n;
+        const int64_t x = off + (int64_t)i * n + j;
+        const double2 g = G[x];
         const double2 r = make_double2((i == j ? 1.0 : 0.0) - g.x, -g.y);
         double2 ev;
         const double li = lam[eo + i], lj = lam[eo + j];
         if (i != j && fabs(li - lj) > delta) {
-            const double2 s = S[off + e];
-            const double inv = 1.0 / (lj - li);
-            ev = make_double2((s.x + lj * r.x) * inv, (s.y + lj * r.y) * inv);
+            const double2 sv = S[x];
+            const double inv = 1.0 / (li - lj);
+            ev = make_double2((sv.x + li * r.x) * inv, (sv.y + li * r.y) * inv);
         } else {
             ev = make_double2(0.5 * r.x, 0.5 * r.y);
         }
+        big |= fmax(fabs(ev.x), fabs(ev.y)) > kTolE;
         if (i == j) ev.x += 1.0;
-        E1[off + e] = ev;
+        E1h[x] = ev;
     }
+    // the last iteration that always runs asks for one more if its correction was still large
+    if (it == kRefine - 1 && __syncthreads_or(big) && threadIdx.x == 0) atomicMax(n_iter, kMaxRefine);
 }
 
-__global__ void k_rho_fro(const cplx* __restrict__ rho, double* __restrict__ fro, EigTables tb) {
-    const int sct = blockIdx.x, n = tb.dims[sct];
-    const int64_t off = tb.off[sct];
-    double s = 0.0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) { const double2 v = rho[off + e]; s += v.x * v.x + v.y * v.y; }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double red[8];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int k = 0; k < (int)(blockDim.x / 32); ++k) a += red[k];
-        fro[sct] = sqrt(a);
-    }
+// Order key of a double: unsigned comparison of keys is numeric comparison (-0 taken as +0).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v == 0.0 ? 0.0 : v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
 
-// Descending order (ties by index); permute columns of X into U.
-__global__ void k_eig_sort(const cplx* __restrict__ X, const double* __restrict__ lam, cplx* __restrict__ U,
-                           double* __restrict__ evals, EigTables tb) {
-    const int sct = blockIdx.x, n = tb.dims[sct];
+// Descending eigenvalue order (ties by index); rows of the chunk of U = X sorted, X = W^H (W after an even
+// number of refinements is in W_even).
+__global__ void __launch_bounds__(256) k_eig_sort(const cplx* __restrict__ W_even, const cplx* __restrict__ W_odd,
+                                                  const int* __restrict__ n_iter, const double* __restrict__ lam,
+                                                  cplx* __restrict__ U, double* __restrict__ evals, EigTables tb) {
+    const cplx* __restrict__ W = (*n_iter & 1) ? W_odd : W_even;   // the iterate after the last refinement
+    const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
     const int64_t off = tb.off[sct], eo = tb.eoff[sct];
+    __shared__ unsigned long long key[kMaxEigN];
+    __shared__ int src[kMaxEigN];
+    int r0, r1;
+    chunk_rows(n, ch, r0, r1);
+    if (r0 >= r1) return;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) key[j] = order_key(lam[eo + j]);
+    __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double lj = lam[eo + j];
+        const unsigned long long kj = key[j];
         int rank = 0;
-        for (int m = 0; m < n; ++m) {
-            const double lm = lam[eo + m];
-            rank += (lm > lj) || (lm == lj && m < j);
-        }
-        evals[eo + rank] = lj;
-        for (int r = 0; r < n; ++r) U[off + (int64_t)r * n + rank] = X[off + (int64_t)r * n + j];
+        for (int m = 0; m < n; ++m) rank += (key[m] > kj) || (key[m] == kj && m < j);
+        src[rank] = j;
+        if (ch == 0) evals[eo + rank] = lam[eo + j];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
+        const int r = r0 + e / n, k = e % n;
+        const double2 v = W[off + (int64_t)src[k] * n + r];
+        U[off + (int64_t)r * n + k] = make_double2(v.x, -v.y);
     }
 }
 
 }  // namespace
 
 // Buffer ids of the refinement GEMMs (all packed like rho).
-enum { EB_RHO = BUF_EXTRA0, EB_X, EB_AX, EB_XH, EB_S, EB_G, EB_E, EB_Y };
+enum { EB_RHO = BUF_EXTRA0, EB_W, EB_AX, EB_S, EB_G, EB_E, EB_WN };
 
 int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     const Side& L = c->side[0];
@@ -262,12 +321,12 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
             e += L.dim[k];
             maxn = std::max(maxn, L.dim[k]);
         }
-        if (maxn > 2 * 256) return fail(c, TDMRG_EINVAL, "rho_eig: sector dimension above 512");
+        if (maxn > kMaxEigN) return fail(c, TDMRG_EINVAL, "rho_eig: sector dimension above 512");
         w.nrho = r; w.nev = e; w.maxn = maxn; w.ns = ns;
         int rc = dev_alloc(c, (void**)&w.tables, (size_t)ns * (2 * sizeof(int64_t) + sizeof(int)), "eig tables");
         if (!rc) rc = dev_alloc(c, (void**)&w.buf, (size_t)6 * r * sizeof(cplx), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.lam, (size_t)e * sizeof(double), "eig workspace");
-        if (!rc) rc = dev_alloc(c, (void**)&w.fro, (size_t)ns * sizeof(double), "eig workspace");
+        if (!rc) rc = dev_alloc(c, (void**)&w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double), "eig workspace");
         if (!rc && maxn > kSmemMaxN) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
         if (rc) return rc;
         std::vector<unsigned char> host((size_t)ns * (2 * sizeof(int64_t) + sizeof(int)));
@@ -276,78 +335,84 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         memcpy(host.data() + 2 * ns * sizeof(int64_t), L.dim.data(), ns * sizeof(int));
         rc = cuda_check(c, cudaMemcpy(w.tables, host.data(), host.size(), cudaMemcpyHostToDevice), "eig tables");
         if (rc) return rc;
-        // task lists: AX = rho X; S = Xh AX and G = Xh X; Y = X E1
-        auto one = [&](TaskList& tl, int cbuf, int abuf, int bbuf, int cbuf2, int abuf2, int bbuf2) {
+        // task lists: AX = rho W^H; S = W AX and G = W W^H; W' = E1h W
+        struct Prod { int cbuf, abuf, bbuf; int8_t opb; };
+        auto one = [&](TaskList& tl, std::initializer_list<Prod> prods) {
             tl.tasks.clear(); tl.segs.clear();
             for (int k = 0; k < ns; ++k) {
                 const int n = L.dim[k];
-                for (int rep = 0; rep < (cbuf2 >= 0 ? 2 : 1); ++rep) {
+                for (const Prod& pr : prods) {
                     Task t{};
-                    t.c_off = off[k]; t.c_buf = (int8_t)(rep ? cbuf2 : cbuf); t.ldc = n; t.M = n; t.N = n; t.beta = 0;
+                    t.c_off = off[k]; t.c_buf = (int8_t)pr.cbuf; t.ldc = n; t.M = n; t.N = n; t.beta = 0;
                     t.seg_begin = (int)tl.segs.size();
-                    Seg sg{};
-                    sg.a_off = off[k]; sg.a_buf = (int8_t)(rep ? abuf2 : abuf); sg.lda = n;
-                    sg.b_off = off[k]; sg.b_buf = (int8_t)(rep ? bbuf2 : bbuf); sg.ldb = n; sg.opb = OPB_N;
-                    sg.K = n; sg.scale = make_double2(1.0, 0.0); sg.dscale = -1;
-                    tl.segs.push_back(sg);
+                    // K in chunks of kKChunk: split-K over the chunks spreads a sector's FP64 work over
+                    // several SMs (the per-SM FP64 rate is the limit, not the tile count)
+                    for (int k0 = 0; k0 < n; k0 += kKChunk) {
+                        Seg sg{};
+                        sg.a_off = off[k] + k0; sg.a_buf = (int8_t)pr.abuf; sg.lda = n;
+                        sg.b_off = off[k] + (pr.opb == OPB_N ? (int64_t)k0 * n : (int64_t)k0);
+                        sg.b_buf = (int8_t)pr.bbuf; sg.ldb = n; sg.opb = pr.opb;
+                        sg.K = std::min(kKChunk, n - k0); sg.scale = make_double2(1.0, 0.0); sg.dscale = -1;
+                        tl.segs.push_back(sg);
+                    }
                     t.seg_end = (int)tl.segs.size();
                     tl.tasks.push_back(t);
                 }
             }
-            make_tiles(tl, kTileF64, kTileF64, kSplitK);
+            make_tiles(tl, kTileF64, kTileF64, kKChunk);
             return upload(c, tl);
         };
         // the opt-in is a property of the kernel on the device, shared by every context: always the maximum
         rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)((size_t)2 * kSmemMaxN * (kSmemMaxN | 1) * sizeof(float2))),
                         "eig smem");
-        if (!rc) rc = one(w.tl_ax, EB_AX, EB_RHO, EB_X, -1, -1, -1);
-        if (!rc) rc = one(w.tl_sg, EB_S, EB_XH, EB_AX, EB_G, EB_XH, EB_X);
-        if (!rc) rc = one(w.tl_y, EB_Y, EB_X, EB_E, -1, -1, -1);
+        if (!rc) rc = one(w.tl_ax, {{EB_AX, EB_RHO, EB_W, OPB_C}});
+        if (!rc) rc = one(w.tl_sg, {{EB_S, EB_W, EB_AX, OPB_N}, {EB_G, EB_W, EB_W, OPB_C}});
+        if (!rc) rc = one(w.tl_y, {{EB_WN, EB_E, EB_W, OPB_N}});
         if (rc) return rc;
         w.ready = true;
     }
     EigTables tb{(const int64_t*)w.tables, (const int64_t*)w.tables + ns, (const int*)((const int64_t*)w.tables + 2 * ns)};
-    cplx* X = w.buf;
-    cplx* AX = w.buf + w.nrho;
-    cplx* Xh = w.buf + 2 * w.nrho;
+    cplx* W = w.buf;
+    cplx* Wn = w.buf + w.nrho;
+    cplx* AX = w.buf + 2 * w.nrho;
     cplx* S = w.buf + 3 * w.nrho;
     cplx* G = w.buf + 4 * w.nrho;
-    cplx* E1 = w.buf + 5 * w.nrho;
-    cplx* Y = evecs;   // ping-pong with the caller's output, which receives the sorted result at the end
+    cplx* E1h = w.buf + 5 * w.nrho;
+    double* part = w.fro + ns;
+    int* n_iter = reinterpret_cast<int*>(part + 2 * (size_t)ns * kRowChunks);
     const int sm = std::min(w.maxn, kSmemMaxN);
     const size_t smem = (size_t)2 * sm * (sm | 1) * sizeof(float2);
-    k_rho_fro<<<ns, 256, 0, s>>>(rho, w.fro, tb);
-    k_jacobi32<<<ns, JT, smem, s>>>(rho, X, tb, w.gwork);
-    c->launches += 2;
+    k_jacobi32<<<ns, JT, smem, s>>>(rho, W, w.fro, n_iter, tb, w.gwork);
+    c->launches += 1;
     GemmArgs a{};
     a.dscale = c->dscale;
     a.bufs[EB_RHO] = const_cast<cplx*>(rho);
-    a.bufs[EB_AX] = AX; a.bufs[EB_XH] = Xh; a.bufs[EB_S] = S; a.bufs[EB_G] = G; a.bufs[EB_E] = E1;
+    a.bufs[EB_AX] = AX; a.bufs[EB_S] = S; a.bufs[EB_G] = G; a.bufs[EB_E] = E1h;
+    const cplx* W_even = W;
+    const cplx* W_odd = Wn;
+    int it = 0;
+    // iterations past kRefine run on the device only when the previous correction asked for them
     auto gemm = [&](TaskList& tl) {
         a.tasks = tl.d_tasks; a.segs = tl.d_segs; a.tiles = tl.d_tiles; a.ntiles = (int)tl.tiles.size();
         a.partials = tl.d_partials; a.counters = tl.d_counters;
         c->launches++;
-        return launch_gemm_f64(a, s, nullptr, 0);
+        return launch_gemm_f64(a, s, it < kRefine ? nullptr : n_iter, it);
     };
-    cudaError_t e = cudaSuccess;
-    for (int it = 0; it < kRefine && e == cudaSuccess; ++it) {
-        a.bufs[EB_X] = X; a.bufs[EB_Y] = Y;
+    const dim3 chunks(ns, kRowChunks);
+    cudaError_t e = cudaGetLastError();
+    for (; it < kMaxRefine && e == cudaSuccess; ++it) {
+        a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
         e = gemm(w.tl_ax);
-        k_conj_transpose<<<ns, 256, 0, s>>>(X, Xh, tb);
         if (e == cudaSuccess) e = gemm(w.tl_sg);
-        k_oa_update<<<ns, 256, 0, s>>>(S, G, w.fro, E1, w.lam, tb);
+        k_oa_norms<<<chunks, 256, 0, s>>>(S, G, w.lam, part, n_iter, it, tb);
+        k_oa_update<<<chunks, 256, 0, s>>>(S, G, w.lam, part, w.fro, E1h, n_iter, it, tb);
         if (e == cudaSuccess) e = gemm(w.tl_y);
         c->launches += 2;
-        std::swap(X, Y);
-    }
-    // X holds the refined vectors; with an odd number of swaps X == evecs, so sort from a copy
-    if (X == evecs) {
-        e = cudaMemcpyAsync(w.buf + 5 * w.nrho, evecs, (size_t)w.nrho * sizeof(cplx), cudaMemcpyDeviceToDevice, s);
-        X = w.buf + 5 * w.nrho;
+        std::swap(W, Wn);
     }
     if (e == cudaSuccess) {
-        k_eig_sort<<<ns, 128, 0, s>>>(X, w.lam, evecs, evals, tb);
+        k_eig_sort<<<chunks, 256, 0, s>>>(W_even, W_odd, n_iter, w.lam, evecs, evals, tb);
         c->launches++;
         e = cudaGetLastError();
     }
@@ -361,7 +426,7 @@ void release_eig(tdmrg_ctx* c) {
     dev_free(c, w.tables, (size_t)ns * (2 * sizeof(int64_t) + sizeof(int)));
     dev_free(c, w.buf, (size_t)6 * w.nrho * sizeof(cplx));
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
-    dev_free(c, w.fro, (size_t)ns * sizeof(double));
+    dev_free(c, w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double));
     dev_free(c, w.gwork, (size_t)4 * w.nrho * sizeof(float2));
     w = EigWork();
 }
