@@ -40,45 +40,30 @@ struct EigTables {
 __device__ __forceinline__ float2 cmf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// FP32 seed: W0 = X0^H (X0: unsorted eigenvector columns) of each sector's rho block, and ||rho||_F.
-__global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, cplx* __restrict__ W,
-                                                 double* __restrict__ rho_fro, int* __restrict__ n_iter,
-                                                 EigTables tb, float2* __restrict__ gwork) {
-    extern __shared__ float2 fsm[];
-    const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
-    const int64_t off = tb.off[sct];
-    const int ld = n | 1;   // odd row stride: column accesses of a warp hit distinct banks
-    float2* A;
-    float2* V;
-    if (n <= kSmemMaxN) { A = fsm; V = fsm + n * ld; }
-    else { A = gwork + 4 * off; V = A + (int64_t)n * ld; }
-    __shared__ int pp[256], qq[256];
-    __shared__ float cs[256];
-    __shared__ float2 sn[256];
-    __shared__ float red[JT / 32];
-    __shared__ float thr_s;
-    const cplx* R = rho + off;
-    if (sct == 0 && tid == 0) *n_iter = kRefine;
-    for (int e = tid; e < n * n; e += JT) {
-        const int r = e / n, cc = e % n;
-        const double2 v = R[e];
-        A[r * ld + cc] = make_float2((float)v.x, (float)v.y);
-        V[r * ld + cc] = make_float2(r == cc ? 1.f : 0.f, 0.f);
-    }
-    __syncthreads();
-    float fro = 0.f;
-    for (int e = tid; e < n * n; e += JT) { const float2 a = A[(e / n) * ld + e % n]; fro += a.x * a.x + a.y * a.y; }
-    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
-    if ((tid & 31) == 0) red[tid >> 5] = fro;
-    __syncthreads();
-    if (tid == 0) {
-        float f = 0.f;
-        for (int k = 0; k < JT / 32; ++k) f += red[k];
-        thr_s = 4.8e-7f * sqrtf(f);   // 4 eps_fp32 ||A||_F: above FP32 rounding noise, so sweeps terminate
-        rho_fro[sct] = sqrtf(f);      // ||rho||_F for the refinement's cluster threshold
-    }
-    __syncthreads();
-    const float thr = thr_s;
+// Rotation J = [[c, s], [-conj(s), c]] on (p, q) annihilating b = A_pq of the Hermitian 2x2 block
+// [[a, b], [conj(b), d]], written without divisions: with x = d - a and r = sqrt(x^2 + 4|b|^2),
+// tan = sign(x) 2|b| / (|x| + r) gives c = (|x| + r) w and s = sign(x) 2 b w, w = 1 / sqrt(2 r (|x| + r)).
+// A Newton step on 1 / sqrt(c^2 + |s|^2) then makes J unitary to about one ulp, so the hundreds of
+// rotations accumulated in V keep it orthonormal to ~1e-6.
+__device__ __forceinline__ void rotation32(float a, float d, float2 b, float& c, float2& s) {
+    const float x = d - a, ax = fabsf(x);
+    const float v = fmaf(x, x, 4.f * fmaf(b.x, b.x, b.y * b.y));
+    const float r = v * rsqrtf(v);
+    const float w = rsqrtf(2.f * r * (ax + r));
+    const float sg = x < 0.f ? -2.f * w : 2.f * w;
+    c = (ax + r) * w;
+    s = make_float2(sg * b.x, sg * b.y);
+    const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s.x, s.x, s.y * s.y)), 1.5f);
+    c *= f;
+    s.x *= f; s.y *= f;
+}
+
+// Cyclic Jacobi sweeps on A (n x n, row stride ld) accumulating V; A and V are either in shared memory
+// or in global memory, and this body is inlined once for each so that shared accesses compile as such.
+__device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, float thr, int* pp, int* qq,
+                                              float* cs, float2* sn) {
+    const int tid = threadIdx.x;
+    const float thr2 = thr * thr;
     const int P = n + (n & 1), npair = P / 2;
     for (int sweep = 0; sweep < 12 && n > 1; ++sweep) {
         for (int round = 0; round < P - 1; ++round) {
@@ -94,22 +79,11 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
                 float2 s = make_float2(0.f, 0.f);
                 if (q < n) {
                     const float2 b = A[p * ld + q];
-                    const float ab = sqrtf(b.x * b.x + b.y * b.y);
-                    if (ab <= thr) {
+                    if (fmaf(b.x, b.x, b.y * b.y) <= thr2) {
                         A[p * ld + q] = make_float2(0.f, 0.f);
                         A[q * ld + p] = make_float2(0.f, 0.f);
                     } else {
-                        const float a = A[p * ld + p].x, d = A[q * ld + q].x;
-                        const float tau = (d - a) / (2.f * ab);
-                        const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-                        c = rsqrtf(1.f + t * t);
-                        const float sv = t * c / ab;
-                        s = make_float2(sv * b.x, sv * b.y);   // s e^{i theta}, b = |b| e^{i theta}
-                        // one Newton step on 1 / sqrt(c^2 + |s|^2): J unitary to about one ulp, so the
-                        // hundreds of rotations accumulated in V keep it orthonormal to ~1e-6
-                        const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s.x, s.x, s.y * s.y)), 1.5f);
-                        c *= f;
-                        s.x *= f; s.y *= f;
+                        rotation32(A[p * ld + p].x, A[q * ld + q].x, b, c, s);
                     }
                 }
                 pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
@@ -136,10 +110,11 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
                 const float2 s = sn[i], sc = conjf2(s);
                 for (int k = lane; k < n; k += 32) {
                     float2 xp = A[k * ld + p], xq = A[k * ld + q];
+                    const float2 vp = V[k * ld + p], vq = V[k * ld + q];
                     float2 t1 = cmf(sc, xq), t2 = cmf(s, xp);
                     A[k * ld + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
                     A[k * ld + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
-                    xp = V[k * ld + p]; xq = V[k * ld + q];
+                    xp = vp; xq = vq;
                     t1 = cmf(sc, xq); t2 = cmf(s, xp);
                     V[k * ld + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
                     V[k * ld + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
@@ -153,15 +128,72 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, c
             const int r = e / n, cc = e % n;
             if (r < cc) {
                 const float2 b = A[r * ld + cc];
-                above |= sqrtf(b.x * b.x + b.y * b.y) > thr;
+                above |= fmaf(b.x, b.x, b.y * b.y) > thr2;
             }
         }
         if (!__syncthreads_or(above)) break;
     }
-    cplx* Ws = W + off;   // W = V^H: row j is the conjugate of eigenvector j
-    for (int e = tid; e < n * n; e += JT) {
+}
+
+__device__ __forceinline__ void jacobi_load(const cplx* R, float2* A, float2* V, int n, int ld) {
+    for (int e = threadIdx.x; e < n * n; e += JT) {
+        const int r = e / n, cc = e % n;
+        const double2 v = R[e];
+        A[r * ld + cc] = make_float2((float)v.x, (float)v.y);
+        V[r * ld + cc] = make_float2(r == cc ? 1.f : 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ float jacobi_fro2(const float2* A, int n, int ld) {
+    float f = 0.f;
+    for (int e = threadIdx.x; e < n * n; e += JT) { const float2 a = A[(e / n) * ld + e % n]; f += a.x * a.x + a.y * a.y; }
+    return f;
+}
+
+__device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, int ld) {
+    for (int e = threadIdx.x; e < n * n; e += JT) {   // W = V^H: row j is the conjugate of eigenvector j
         const float2 v = V[(e % n) * ld + e / n];
         Ws[e] = make_double2(v.x, -v.y);
+    }
+}
+
+// FP32 seed: W0 = X0^H (X0: unsorted eigenvector columns) of each sector's rho block, and ||rho||_F.
+__global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, cplx* __restrict__ W,
+                                                 double* __restrict__ rho_fro, int* __restrict__ n_iter,
+                                                 EigTables tb, float2* __restrict__ gwork) {
+    extern __shared__ float2 fsm[];
+    const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
+    const int64_t off = tb.off[sct];
+    const int ld = n | 1;   // odd row stride: column accesses of a warp hit distinct banks
+    const bool in_smem = n <= kSmemMaxN;
+    float2* gA = gwork + 4 * off;
+    float2* gV = gA + (int64_t)n * ld;
+    __shared__ int pp[256], qq[256];
+    __shared__ float cs[256];
+    __shared__ float2 sn[256];
+    __shared__ float red[JT / 32];
+    __shared__ float thr_s;
+    if (sct == 0 && tid == 0) *n_iter = kRefine;
+    float fro;
+    if (in_smem) { jacobi_load(rho + off, fsm, fsm + n * ld, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
+    else { jacobi_load(rho + off, gA, gV, n, ld); __syncthreads(); fro = jacobi_fro2(gA, n, ld); }
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    if ((tid & 31) == 0) red[tid >> 5] = fro;
+    __syncthreads();
+    if (tid == 0) {
+        float f = 0.f;
+        for (int k = 0; k < JT / 32; ++k) f += red[k];
+        thr_s = 4.8e-7f * sqrtf(f);   // 4 eps_fp32 ||A||_F: above FP32 rounding noise, so sweeps terminate
+        rho_fro[sct] = sqrtf(f);      // ||rho||_F for the refinement's cluster threshold
+    }
+    __syncthreads();
+    const float thr = thr_s;
+    if (in_smem) {
+        jacobi_sweeps(fsm, fsm + n * ld, n, ld, thr, pp, qq, cs, sn);
+        jacobi_store(fsm + n * ld, W + off, n, ld);
+    } else {
+        jacobi_sweeps(gA, gV, n, ld, thr, pp, qq, cs, sn);
+        jacobi_store(gV, W + off, n, ld);
     }
 }
 

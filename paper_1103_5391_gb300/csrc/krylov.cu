@@ -4,7 +4,7 @@
 // Lanczos is started from phi itself: v_0 = phi / ||phi||.  Step j: w = H v_j (grouped superblock
 // product), alpha_j = Re <v_j|w>, then two classical Gram-Schmidt passes against v_0..v_j
 // (the first pass also removes the alpha_j v_j and beta_j v_{j-1} components), beta_{j+1} = ||w||,
-// v_{j+1} = w / beta_{j+1}, all in one cooperative launch per step; the recursion stops at n_K
+// v_{j+1} = w / beta_{j+1}, all in one cooperative launch per step with two grid barriers; the recursion stops at n_K
 // vectors or when beta_{j+1} <= tol * max(1, |alpha_j|).  Then T = S^dag D S is diagonalised (one warp, cyclic
 // Jacobi, FP64) and the targets phi(t_x) = ||phi|| sum_k v_k [S^dag e^{-i D t_x} S]_{k,0} are formed
 // in one pass over V.  Everything is FP64 and stays on the device; reductions use a fixed grid and
@@ -101,10 +101,15 @@ __global__ void __launch_bounds__(NT) k_init_v0(const cplx* __restrict__ phi, in
 }
 
 // ---- one Lanczos orthogonalisation step in a single cooperative launch -----------------------
-// Three grid barriers separate: (A) dots <v_k|w>; (B) w -= sum h_k v_k and the second-pass dots;
-// (C) w -= sum h2_k v_k and ||w||^2; (D) beta, breakdown test, v_{j+1} = w / beta.  Every block
-// reduces the partials of all blocks in the same fixed order, so results do not depend on scheduling.
-// The barrier spins are bounded: when one runs out the kernel sets a status bit and finishes.
+// Two grid barriers separate: (A) the first-pass dots h1_k = <v_k|w>; (B) w' = w - sum h1_k v_k, the
+// second-pass dots h2_k = <v_k|w'> and ||w'||^2; (C) beta = ||w' - sum h2_k v_k|| and
+// v_{j+1} = (w' - sum h2_k v_k) / beta.  Since h2 holds the projections of w' on orthonormal v_k,
+// ||w' - sum h2_k v_k||^2 = ||w'||^2 - sum |h2_k|^2 (h2 is at rounding level after the first pass, so
+// the difference loses nothing), which saves the barrier of a separate norm pass.  Every block
+// reduces the partials of all blocks in the same fixed order, so results do not depend on
+// scheduling.  FP64 throughput per SM is low on this GPU, so the warp reductions are
+// reduce-scatter (16 FP64 adds for 16 values instead of 80).  The barrier spins are bounded: when one
+// runs out the kernel sets a status bit and finishes.
 constexpr int OB = 256;   // threads per block of the fused kernel
 constexpr long kBarrierSpin = 1L << 24;
 
@@ -143,27 +148,46 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
     __syncthreads();
 }
 
-// block sums of 8 complex values (fixed order); result valid in threads 0..7 as out[t]
-__device__ void block_sum8(double2 (&v)[8], double2* sh /* [OB/32][8] */, double2* out) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+// Block sums of 8 complex values (16 doubles) in a fixed order; the result is in out[0..7].
+// Warp level: reduce-scatter, after which lanes 2m and 2m+1 hold the warp total of double m.
+__device__ void block_sum8(double2 (&v)[8], double* sh /* [OB/32][16] */, double2* out) {
+    double d[16];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 8; ++k) { d[2 * k] = v[k].x; d[2 * k + 1] = v[k].y; }
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            v[k].x += __shfl_xor_sync(0xffffffffu, v[k].x, o);
-            v[k].y += __shfl_xor_sync(0xffffffffu, v[k].y, o);
+    for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (l & o) != 0;   // keep the upper half of the remaining values
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double lo_v = d[i], hi_v = d[i + half];
+            const double send = up ? lo_v : hi_v;
+            d[i] = (up ? hi_v : lo_v) + __shfl_xor_sync(0xffffffffu, send, o);
         }
+    }
+    d[0] += __shfl_xor_sync(0xffffffffu, d[0], 1);   // lanes 2m, 2m+1: total of double m = l >> 1
     __syncthreads();
-    if (l == 0)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sh[w * 8 + k] = v[k];
+    if ((l & 1) == 0) sh[w * 16 + (l >> 1)] = d[0];
     __syncthreads();
-    if (threadIdx.x < 8) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int ww = 0; ww < OB / 32; ++ww) { s.x += sh[ww * 8 + threadIdx.x].x; s.y += sh[ww * 8 + threadIdx.x].y; }
-        out[threadIdx.x] = s;
+    if (threadIdx.x < 16) {
+        double s = 0.0;
+        for (int ww = 0; ww < OB / 32; ++ww) s += sh[ww * 16 + threadIdx.x];
+        reinterpret_cast<double*>(out)[threadIdx.x] = s;
     }
     __syncthreads();
+}
+
+// Deterministic block sum of one double (result in every thread).
+__device__ double block_sum1(double x, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int k = 0; k < OB / 32; ++k) s += sh[k];
+    __syncthreads();
+    return s;
 }
 
 // partials[k * gridDim + b] for k < nv  ->  every block's h[k] (same order everywhere)
@@ -182,75 +206,63 @@ __device__ void sum_partials(const double2* __restrict__ part, int nv, double2* 
     __syncthreads();
 }
 
-// dots <v_k|w> over this block's chunk for all k < nv, written as partials
-__device__ void chunk_dots(const cplx* __restrict__ V, const cplx* __restrict__ w, int64_t n, int nv, int64_t lo,
-                           int64_t hi, double2* part, double2* sh, double2* red8) {
-    for (int k0 = 0; k0 < nv; k0 += 8) {
-        double2 acc[8];
+// Dots <v_k|x> over this block's chunk for k in [k0, k0 + 8) (k < nv), written as partials.  With
+// h != nullptr the chunk is first updated in place, x <- x - sum_k h_k v_k over all nv vectors, and
+// ||x||^2 of the updated chunk is returned (this happens in the group k0 = 0 only).
+__device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
+                             int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
+    double2 acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = make_double2(0.0, 0.0);
-        for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
-            const double2 x = w[i];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (k0 + k < nv) {
-                    const double2 p = cdotc(V[(int64_t)(k0 + k) * n + i], x);
-                    acc[k].x += p.x; acc[k].y += p.y;
-                }
+    for (int k = 0; k < 8; ++k) acc[k] = make_double2(0.0, 0.0);
+    double nn = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
+        double2 x = w[i];
+        if (h != nullptr && k0 == 0) {
+            for (int k = 0; k < nv; ++k) {
+                const double2 p = cmul(h[k], V[(int64_t)k * n + i]);
+                x.x -= p.x; x.y -= p.y;
+            }
+            w[i] = x;
+            nn += x.x * x.x + x.y * x.y;
         }
-        block_sum8(acc, sh, red8);
-        if (threadIdx.x < 8 && k0 + (int)threadIdx.x < nv) part[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = red8[threadIdx.x];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k0 + k < nv) {
+                const double2 p = cdotc(V[(int64_t)(k0 + k) * n + i], x);
+                acc[k].x += p.x; acc[k].y += p.y;
+            }
     }
+    block_sum8(acc, sh, red8);
+    if (threadIdx.x < 8 && k0 + (int)threadIdx.x < nv) part[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = red8[threadIdx.x];
+    return nn;
 }
 
 __global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
     if (a.j >= a.flags[0]) return;   // uniform: the flag only changes after the last barrier
-    __shared__ double2 sh[(OB / 32) * 8];
+    __shared__ double sh[(OB / 32) * 16];
     __shared__ double2 red8[8];
     __shared__ double2 h[33];
     const int64_t ch = (a.n + gridDim.x - 1) / gridDim.x;
     const int64_t lo = min(a.n, (int64_t)blockIdx.x * ch), hi = min(a.n, lo + ch);
     // (A) first-pass dots
-    chunk_dots(a.V, a.w, a.n, a.nv, lo, hi, a.partA, sh, red8);
+    for (int k0 = 0; k0 < a.nv; k0 += 8) chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, nullptr, a.partA, sh, red8);
     grid_barrier(a.bar, a.status);
-    // (B) subtract, second-pass dots
+    // (B) w' = w - sum h1_k v_k, second-pass dots, ||w'||^2
     sum_partials(a.partA, a.nv, h);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.tri[T_ALPHA + a.j] = h[a.j].x;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
-        double2 x = a.w[i];
-        for (int k = 0; k < a.nv; ++k) {
-            const double2 p = cmul(h[k], a.V[(int64_t)k * a.n + i]);
-            x.x -= p.x; x.y -= p.y;
-        }
-        a.w[i] = x;
-    }
-    __syncthreads();
-    chunk_dots(a.V, a.w, a.n, a.nv, lo, hi, a.partB, sh, red8);
-    grid_barrier(a.bar, a.status);
-    // (C) subtract again, norm
-    sum_partials(a.partB, a.nv, h);
     double nn = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
-        double2 x = a.w[i];
-        for (int k = 0; k < a.nv; ++k) {
-            const double2 p = cmul(h[k], a.V[(int64_t)k * a.n + i]);
-            x.x -= p.x; x.y -= p.y;
-        }
-        a.w[i] = x;
-        nn += x.x * x.x + x.y * x.y;
+    for (int k0 = 0; k0 < a.nv; k0 += 8) {
+        nn += chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, h, a.partB, sh, red8);
+        __syncthreads();   // h is read by every thread of the first group
     }
-    {
-        double2 v8[8];
-        v8[0] = make_double2(nn, 0.0);
-#pragma unroll
-        for (int k = 1; k < 8; ++k) v8[k] = make_double2(0.0, 0.0);
-        block_sum8(v8, sh, red8);
-        if (threadIdx.x == 0) a.partA[blockIdx.x] = red8[0];
-    }
+    nn = block_sum1(nn, sh);
+    if (threadIdx.x == 0) a.partB[(int64_t)a.nv * gridDim.x + blockIdx.x] = make_double2(nn, 0.0);
     grid_barrier(a.bar, a.status);
-    // (D) beta, stop test, v_{j+1}
-    sum_partials(a.partA, 1, h);
-    const double beta = sqrt(h[0].x);
+    // (C) beta, stop test, v_{j+1} = (w' - sum h2_k v_k) / beta
+    sum_partials(a.partB, a.nv + 1, h);
+    double b2 = h[a.nv].x;
+    for (int k = 0; k < a.nv; ++k) b2 -= h[k].x * h[k].x + h[k].y * h[k].y;
+    const double beta = sqrt(fmax(b2, 0.0));
     const double alpha = a.tri[T_ALPHA + a.j];
     const bool stop = (a.j == a.nk - 1) || (beta <= a.tol * fmax(1.0, fabs(alpha)));
     if (stop) {
@@ -264,7 +276,14 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.tri[T_BETA + a.j] = beta;
     const double inv = 1.0 / beta;
     cplx* vnext = const_cast<cplx*>(a.V) + (int64_t)(a.j + 1) * a.n;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) { const double2 x = a.w[i]; vnext[i] = make_double2(x.x * inv, x.y * inv); }
+    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
+        double2 x = a.w[i];
+        for (int k = 0; k < a.nv; ++k) {
+            const double2 p = cmul(h[k], a.V[(int64_t)k * a.n + i]);
+            x.x -= p.x; x.y -= p.y;
+        }
+        vnext[i] = make_double2(x.x * inv, x.y * inv);
+    }
 }
 
 struct Times { double t[16]; };
