@@ -120,3 +120,29 @@ def test_breakdown_and_alias(lib):
             assert rel_err(host(got), want) < 1e-10
     finally:
         lib.tdmrg_destroy(ctx)
+
+
+def test_unordered_times(lib):
+    """Targets at unsorted, repeated and zero times, one of them far enough for several
+    substeps of the propagation on the tridiagonal: same targets and error estimate as the oracle's
+    e^{-iTt} from the eigendecomposition of T (Eq. lanczosevolution)."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(16, 150, 4.0, nbonds=2, seed=S.SEED_BASE + 1)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    times = [0.3, 0.2, 0.0, 0.3, 1.5, 0.05]
+    nk = 12
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = lib.tdmrg_sector_size(ctx, ss.Q1)
+        tg = [dev(np.zeros(n)) for _ in times]
+        lib.tdmrg_evolve(ctx, ss.Q1, dev(ss.phi), times, nk, tg)
+        hf = lambda v: superblock.apply_h(sb, HL, HR, conns, ss.Q1, v)
+        ref, n_used, err = krylov.evolve(hf, ss.phi, times, nk)
+        n_gpu, err_gpu, a_g, b_g = lib.tdmrg_evolve_info(ctx)
+        assert n_gpu == n_used
+        for x in range(len(times)):
+            assert rel_err(host(tg[x]), ref[x]) < 1e-10, times[x]
+        assert abs(err_gpu - err) <= 1e-8 * err + 1e-300
+    finally:
+        lib.tdmrg_destroy(ctx)
