@@ -149,15 +149,23 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
     __syncthreads();
 }
 
-// Block sums of 8 complex values (16 doubles) in a fixed order; the result is in out[0..7].
-// Warp level: reduce-scatter, after which lanes 2m and 2m+1 hold the warp total of double m.
-__device__ void block_sum8(double2 (&v)[8], double* sh /* [OB/32][16] */, double2* out) {
-    double d[16];
+// Block sums of NK complex values in a fixed order; the result is in out[0..NK-1].  Warp level:
+// reduce-scatter over ND = 2 * pow2ceil(NK) doubles (log2 ND halving levels, then a butterfly over the
+// remaining lane bits), after which lane l holds the warp total of double l >> (5 - log2 ND).
+template <int NK>
+__device__ void block_sum(double2 (&v)[NK], double* sh /* [OB/32][16] */, double2* out) {
+    constexpr int ND = NK <= 1 ? 2 : NK <= 2 ? 4 : NK <= 4 ? 8 : 16;
+    constexpr int LV = ND == 2 ? 1 : ND == 4 ? 2 : ND == 8 ? 3 : 4;
+    double d[ND];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) { d[2 * k] = v[k].x; d[2 * k + 1] = v[k].y; }
+    for (int k = 0; k < ND / 2; ++k) {
+        d[2 * k] = k < NK ? v[k < NK ? k : 0].x : 0.0;
+        d[2 * k + 1] = k < NK ? v[k < NK ? k : 0].y : 0.0;
+    }
     const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    for (int lv = 0; lv < LV; ++lv) {
+        const int half = ND >> (lv + 1), o = 16 >> lv;
         const bool up = (l & o) != 0;   // keep the upper half of the remaining values
 #pragma unroll
         for (int i = 0; i < half; ++i) {
@@ -166,11 +174,12 @@ __device__ void block_sum8(double2 (&v)[8], double* sh /* [OB/32][16] */, double
             d[i] = (up ? hi_v : lo_v) + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
-    d[0] += __shfl_xor_sync(0xffffffffu, d[0], 1);   // lanes 2m, 2m+1: total of double m = l >> 1
+#pragma unroll
+    for (int o = 16 >> LV; o > 0; o >>= 1) d[0] += __shfl_xor_sync(0xffffffffu, d[0], o);
     __syncthreads();
-    if ((l & 1) == 0) sh[w * 16 + (l >> 1)] = d[0];
+    if ((l & ((32 >> LV) - 1)) == 0) sh[w * 16 + (l >> (5 - LV))] = d[0];
     __syncthreads();
-    if (threadIdx.x < 16) {
+    if (threadIdx.x < 2 * NK) {
         double s = 0.0;
         for (int ww = 0; ww < OB / 32; ++ww) s += sh[ww * 16 + threadIdx.x];
         reinterpret_cast<double*>(out)[threadIdx.x] = s;
@@ -207,35 +216,53 @@ __device__ void sum_partials(const double2* __restrict__ part, int nv, double2* 
     __syncthreads();
 }
 
-// Dots <v_k|x> over this block's chunk for k in [k0, k0 + 8) (k < nv), written as partials.  With
+// Dots <v_k|x> over this block's chunk for k in [k0, k0 + NK), written as partials.  With
 // h != nullptr the chunk is first updated in place, x <- x - sum_k h_k v_k over all nv vectors, and
-// ||x||^2 of the updated chunk is returned (this happens in the group k0 = 0 only).
-__device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
-                             int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
-    double2 acc[8];
+// ||x||^2 of the updated chunk is returned (this happens in the group k0 = 0 only).  NK is the exact
+// count: predicated-off FP64 instructions would still take issue slots of the slow FP64 pipe.
+template <int NK>
+__device__ double chunk_dots_n(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
+                               int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
+    double2 acc[NK];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < NK; ++k) acc[k] = make_double2(0.0, 0.0);
     double nn = 0.0;
+    const cplx* __restrict__ Vk = V + (int64_t)k0 * n;
     for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
         double2 x = w[i];
         if (h != nullptr && k0 == 0) {
             for (int k = 0; k < nv; ++k) {
-                const double2 p = cmul(h[k], V[(int64_t)k * n + i]);
-                x.x -= p.x; x.y -= p.y;
+                const double2 v = V[(int64_t)k * n + i];
+                x.x = fma(-h[k].x, v.x, fma(h[k].y, v.y, x.x));
+                x.y = fma(-h[k].x, v.y, fma(-h[k].y, v.x, x.y));
             }
             w[i] = x;
-            nn += x.x * x.x + x.y * x.y;
+            nn = fma(x.x, x.x, fma(x.y, x.y, nn));
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (k0 + k < nv) {
-                const double2 p = cdotc(V[(int64_t)(k0 + k) * n + i], x);
-                acc[k].x += p.x; acc[k].y += p.y;
-            }
+        for (int k = 0; k < NK; ++k) {
+            const double2 v = Vk[(int64_t)k * n + i];   // acc += conj(v) x
+            acc[k].x = fma(v.x, x.x, fma(v.y, x.y, acc[k].x));
+            acc[k].y = fma(v.x, x.y, fma(-v.y, x.x, acc[k].y));
+        }
     }
-    block_sum8(acc, sh, red8);
-    if (threadIdx.x < 8 && k0 + (int)threadIdx.x < nv) part[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = red8[threadIdx.x];
+    block_sum<NK>(acc, sh, red8);
+    if (threadIdx.x < NK) part[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = red8[threadIdx.x];
     return nn;
+}
+
+__device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
+                             int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
+    switch (min(8, nv - k0)) {
+        case 1: return chunk_dots_n<1>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 2: return chunk_dots_n<2>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 3: return chunk_dots_n<3>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 4: return chunk_dots_n<4>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 5: return chunk_dots_n<5>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 6: return chunk_dots_n<6>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 7: return chunk_dots_n<7>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        default: return chunk_dots_n<8>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+    }
 }
 
 __global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
@@ -280,8 +307,9 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
     for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
         double2 x = a.w[i];
         for (int k = 0; k < a.nv; ++k) {
-            const double2 p = cmul(h[k], a.V[(int64_t)k * a.n + i]);
-            x.x -= p.x; x.y -= p.y;
+            const double2 v = a.V[(int64_t)k * a.n + i];
+            x.x = fma(-h[k].x, v.x, fma(h[k].y, v.y, x.x));
+            x.y = fma(-h[k].x, v.y, fma(-h[k].y, v.x, x.y));
         }
         vnext[i] = make_double2(x.x * inv, x.y * inv);
     }
@@ -369,31 +397,50 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, co
 
 struct TargetPtrs { cplx* p[16]; };
 
-// targets[x][i] = sum_k coef[x][k] v_k[i]: one pass over V, n_v outputs.
+// targets[x][i] = sum_k coef[x][k] v_k[i] for x in [x0, x0 + NX): one pass over V.  NX is exact (no
+// predicated FP64 work for absent targets).
+template <int NX>
 __global__ void __launch_bounds__(256) k_combine(const cplx* __restrict__ V, int64_t n, const int* __restrict__ flags,
-                                                  const cplx* __restrict__ coef, int n_v, TargetPtrs tg) {
-    __shared__ double2 cf[16][32];
+                                                  const cplx* __restrict__ coef, int x0, TargetPtrs tg) {
+    __shared__ double2 cf[NX][32];
     const int nu = flags[0];
-    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) cf[e / 32][e % 32] = (e / 32 < n_v) ? coef[e] : make_double2(0.0, 0.0);
+    for (int e = threadIdx.x; e < NX * 32; e += blockDim.x) cf[e / 32][e % 32] = coef[(x0 + e / 32) * 32 + e % 32];
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 acc[16];
+        double2 acc[NX];
 #pragma unroll
-        for (int x = 0; x < 16; ++x) acc[x] = make_double2(0.0, 0.0);
+        for (int x = 0; x < NX; ++x) acc[x] = make_double2(0.0, 0.0);
         for (int k = 0; k < nu; ++k) {
             const double2 v = V[(int64_t)k * n + i];
 #pragma unroll
-            for (int x = 0; x < 16; ++x) {
-                if (x < n_v) {
-                    const double2 p = cmul(cf[x][k], v);
-                    acc[x].x += p.x; acc[x].y += p.y;
-                }
+            for (int x = 0; x < NX; ++x) {
+                const double2 c = cf[x][k];
+                acc[x].x = fma(c.x, v.x, fma(-c.y, v.y, acc[x].x));
+                acc[x].y = fma(c.x, v.y, fma(c.y, v.x, acc[x].y));
             }
         }
 #pragma unroll
-        for (int x = 0; x < 16; ++x)
-            if (x < n_v) tg.p[x][i] = acc[x];
+        for (int x = 0; x < NX; ++x) tg.p[x][i] = acc[x];   // tg holds the pointers from target x0 on
     }
+}
+
+cudaError_t launch_combine(const cplx* V, int64_t n, const int* flags, const cplx* coef, int n_v, const TargetPtrs& tg,
+                           int grid, cudaStream_t s) {
+    for (int x0 = 0; x0 < n_v; x0 += 8) {
+        TargetPtrs t{};
+        for (int x = x0; x < n_v; ++x) t.p[x - x0] = tg.p[x];
+        switch (std::min(8, n_v - x0)) {
+            case 1: k_combine<1><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 2: k_combine<2><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 3: k_combine<3><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 4: k_combine<4><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 5: k_combine<5><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 6: k_combine<6><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 7: k_combine<7><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            default: k_combine<8><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+        }
+    }
+    return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(NT) k_dot2(const cplx* __restrict__ x, const cplx* __restrict__ y, int64_t n,
@@ -519,8 +566,8 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
     TargetPtrs tg{};
     for (int x = 0; x < n_v; ++x) tg.p[x] = targets[x];
     int grid = (int)std::min<int64_t>((n + 255) / 256, 4L * c->num_sms);
-    k_combine<<<grid, 256, 0, s>>>(k->V, n, k->flags, k->coef, n_v, tg);
-    c->launches += 2;
+    launch_combine(k->V, n, k->flags, k->coef, n_v, tg, grid, s);
+    c->launches += 1 + (n_v + 7) / 8;
     c->last_krylov = k;
     return cuda_check(c, cudaGetLastError(), "evolve launch");
 }
