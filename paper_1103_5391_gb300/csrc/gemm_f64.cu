@@ -6,8 +6,9 @@
 // On GB300 FP64 runs at about 1 TFLOP/s for the whole chip (scalar DFMA and the FP64 MMA alike),
 // i.e. about 7 GFLOP/s per SM, so the kernel is organised for balance rather than data reuse:
 //   - small (16 x 16) tiles so that every sector pair spreads over many SMs;
-//   - the four warps of a CTA split K (warp w takes k-step w of every 16-wide chunk) and their
-//     partial tiles are summed in shared memory in a fixed order;
+//   - each of the four warps owns one 8 x 8 sub-block over the whole K range (no cross-warp sums),
+//     and negated or conjugated operands are staged by integer sign flips, so that the FP64 pipe
+//     runs the MMAs and little else;
 //   - tasks with a long K (many segments) are split across CTAs along segment boundaries; each part
 //     stores its partial tile and the last part to arrive (atomic ticket) sums all parts in index
 //     order, so results do not depend on scheduling.
@@ -27,11 +28,14 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                  : "d"(a), "d"(b));
 }
 
+// Sign flip of a double on the integer pipe: FP64 arithmetic is scarce on this GPU, so negated and
+// conjugated operands are formed while staging instead of by FP64 instructions.
+__device__ __forceinline__ double neg(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (1ll << 63)); }
+
 __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int* skip_flag, int skip_step) {
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;   // Krylov space already complete
-    __shared__ double Are[TS][PAD], Aim[TS][PAD];
+    __shared__ double Are[TS][PAD], Aim[TS][PAD], Ain[TS][PAD];   // Ain = -Aim
     __shared__ double Bre[KC][PAD], Bim[KC][PAD];
-    __shared__ double2 red[4][TS * TS];
     __shared__ int last;
 
     const Tile tile = args.tiles[blockIdx.x];
@@ -40,20 +44,10 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
     const int gid = lane >> 2, tig = lane & 3;
     const int m0 = tile.m0, n0 = tile.n0;
     const int Mt = min(TS, task.M - m0), Nt = min(TS, task.N - n0);
-    bool sub[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) sub[i][j] = (8 * i < Mt) && (8 * j < Nt);
-
-    double cre[2][2][2], cim[2][2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            cre[i][j][0] = cre[i][j][1] = 0.0;
-            cim[i][j][0] = cim[i][j][1] = 0.0;
-        }
+    // warp w owns the 8 x 8 sub-block (w / 2, w % 2) over the whole K range: no cross-warp sums
+    const int bi = warp >> 1, bj = warp & 1;
+    const bool active = (8 * bi < Mt) && (8 * bj < Nt);
+    double cre[2] = {0.0, 0.0}, cim[2] = {0.0, 0.0};
 
     for (int s = tile.seg_lo; s < tile.seg_hi; ++s) {
         const Seg seg = args.segs[s];
@@ -65,7 +59,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
             sr *= d; si *= d;
         }
         const bool scaled = !(sr == 1.0 && si == 0.0);
-        const double cs = seg.opb == OPB_C ? -1.0 : 1.0;
+        const bool conj = seg.opb == OPB_C;
         for (int k0 = 0; k0 < seg.K; k0 += KC) {
             const int kc = min(KC, seg.K - k0);
 #pragma unroll
@@ -76,6 +70,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                 if (scaled) v = make_double2(sr * v.x - si * v.y, sr * v.y + si * v.x);
                 Are[r][k] = v.x;
                 Aim[r][k] = v.y;
+                Ain[r][k] = neg(v.y);
             }
             if (seg.opb == OPB_N) {                   // B[k][n] at B[k*ldb + n]: threads along n
 #pragma unroll
@@ -93,85 +88,63 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     double2 v = make_double2(0.0, 0.0);
                     if (k < kc && n < Nt) v = B[(int64_t)(n0 + n) * seg.ldb + k0 + k];
                     Bre[k][n] = v.x;
-                    Bim[k][n] = cs * v.y;
+                    Bim[k][n] = conj ? neg(v.y) : v.y;
                 }
             }
             __syncthreads();
-            const int kk = 4 * warp;
-            if (kk < kc) {
-                double ar[2], ai[2], br[2], bi[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    ar[i] = Are[8 * i + gid][kk + tig];
-                    ai[i] = Aim[8 * i + gid][kk + tig];
-                    br[i] = Bre[kk + tig][8 * i + gid];
-                    bi[i] = Bim[kk + tig][8 * i + gid];
+            if (active) {
+                for (int kk = 0; kk < kc; kk += 4) {   // zero-padded beyond kc
+                    const double ar = Are[8 * bi + gid][kk + tig], ai = Aim[8 * bi + gid][kk + tig];
+                    const double an = Ain[8 * bi + gid][kk + tig];
+                    const double br = Bre[kk + tig][8 * bj + gid], bm = Bim[kk + tig][8 * bj + gid];
+                    dmma(cre[0], cre[1], ar, br);
+                    dmma(cre[0], cre[1], an, bm);
+                    dmma(cim[0], cim[1], ar, bm);
+                    dmma(cim[0], cim[1], ai, br);
                 }
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        if (!sub[i][j]) continue;
-                        dmma(cre[i][j][0], cre[i][j][1], ar[i], br[j]);
-                        dmma(cre[i][j][0], cre[i][j][1], -ai[i], bi[j]);
-                        dmma(cim[i][j][0], cim[i][j][1], ar[i], bi[j]);
-                        dmma(cim[i][j][0], cim[i][j][1], ai[i], br[j]);
-                    }
             }
             __syncthreads();
         }
     }
 
-    // sum the four warps' partial tiles in a fixed order
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int r = 8 * i + gid, col = 8 * j + 2 * tig + e;
-                red[warp][r * TS + col] = make_double2(cre[i][j][e], cim[i][j][e]);
-            }
-    __syncthreads();
-    double2 v[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int e = tid + 128 * u;
-        double2 s = red[0][e];
-        for (int w = 1; w < 4; ++w) { s.x += red[w][e].x; s.y += red[w][e].y; }
-        v[u] = s;
-    }
+    // this thread's two outputs: row 8 bi + gid, columns 8 bj + 2 tig + e
+    const int r = 8 * bi + gid, col0 = 8 * bj + 2 * tig;
+    double2 v[2] = {make_double2(cre[0], cim[0]), make_double2(cre[1], cim[1])};
     if (tile.split >= 0) {
         // split-K: publish this part, the last part to arrive sums all parts in index order
         cplx* part = args.partials + ((int64_t)tile.split_base + tile.part) * (TS * TS);
-        part[tid] = v[0];
-        part[tid + 128] = v[1];
+        if (active) {
+            part[r * TS + col0] = v[0];
+            part[r * TS + col0 + 1] = v[1];
+        }
         __threadfence();
         __syncthreads();
         if (tid == 0) last = (atomicAdd(args.counters + tile.split, 1) == tile.nparts - 1);
         __syncthreads();
         if (!last) return;
         __threadfence();
-        const cplx* base = args.partials + (int64_t)tile.split_base * (TS * TS);
+        if (active) {
+            const cplx* base = args.partials + (int64_t)tile.split_base * (TS * TS);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int e = tid + 128 * u;
-            double2 s = make_double2(0.0, 0.0);
-            for (int p = 0; p < tile.nparts; ++p) {
-                const double2 x = __ldcg(base + (int64_t)p * (TS * TS) + e);
-                s.x += x.x; s.y += x.y;
+            for (int e = 0; e < 2; ++e) {
+                double2 t = make_double2(0.0, 0.0);
+                for (int p = 0; p < tile.nparts; ++p) {
+                    const double2 x = __ldcg(base + (int64_t)p * (TS * TS) + r * TS + col0 + e);
+                    t.x += x.x; t.y += x.y;
+                }
+                v[e] = t;
             }
-            v[u] = s;
         }
         if (tid == 0) args.counters[tile.split] = 0;   // ready for the next launch
     }
+    if (!active) return;
     cplx* __restrict__ C = args.bufs[task.c_buf] + task.c_off;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int e = tid + 128 * u, r = e / TS, col = e % TS;
+    for (int e = 0; e < 2; ++e) {
+        const int col = col0 + e;
         if (r < Mt && col < Nt) {
             cplx* p = C + (int64_t)(m0 + r) * task.ldc + n0 + col;
-            double2 x = v[u];
+            double2 x = v[e];
             if (task.beta) {
                 const double2 o = *p;
                 x.x += o.x;
