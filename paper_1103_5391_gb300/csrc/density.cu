@@ -56,6 +56,7 @@ int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* ps
         for (size_t qi = 0; qi < L.dim.size(); ++qi) {
             Task tk{};
             tk.c_off = off; tk.c_buf = BUF_OUT; tk.ldc = L.dim[qi]; tk.M = L.dim[qi]; tk.N = L.dim[qi]; tk.beta = 0;
+            tk.herm = 1;   // rho_L(q) is Hermitian: lower tiles plus mirror (a batched HERK)
             tk.seg_begin = (int)tl->segs.size();
             for (int l = 0; l < nt; ++l) {
                 int ri = R.find(Q[2 * l] - L.nup[qi], Q[2 * l + 1] - L.ndn[qi]);

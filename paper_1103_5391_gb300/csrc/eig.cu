@@ -368,7 +368,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         rc = cuda_check(c, cudaMemcpy(w.tables, host.data(), host.size(), cudaMemcpyHostToDevice), "eig tables");
         if (rc) return rc;
         // task lists: AX = rho W^H; S = W AX and G = W W^H; W' = E1h W
-        struct Prod { int cbuf, abuf, bbuf; int8_t opb; };
+        struct Prod { int cbuf, abuf, bbuf; int8_t opb, herm; };
         auto one = [&](TaskList& tl, std::initializer_list<Prod> prods) {
             tl.tasks.clear(); tl.segs.clear();
             for (int k = 0; k < ns; ++k) {
@@ -376,6 +376,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
                 for (const Prod& pr : prods) {
                     Task t{};
                     t.c_off = off[k]; t.c_buf = (int8_t)pr.cbuf; t.ldc = n; t.M = n; t.N = n; t.beta = 0;
+                    t.herm = pr.herm;
                     t.seg_begin = (int)tl.segs.size();
                     // K in chunks of kKChunk: split-K over the chunks spreads a sector's FP64 work over
                     // several SMs (the per-SM FP64 rate is the limit, not the tile count)
@@ -398,9 +399,10 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)((size_t)2 * kSmemMaxN * (kSmemMaxN | 1) * sizeof(float2))),
                         "eig smem");
-        if (!rc) rc = one(w.tl_ax, {{EB_AX, EB_RHO, EB_W, OPB_C}});
-        if (!rc) rc = one(w.tl_sg, {{EB_S, EB_W, EB_AX, OPB_N}, {EB_G, EB_W, EB_W, OPB_C}});
-        if (!rc) rc = one(w.tl_y, {{EB_WN, EB_E, EB_W, OPB_N}});
+        // S = W rho W^H and G = W W^H are Hermitian: lower tiles plus mirror
+        if (!rc) rc = one(w.tl_ax, {{EB_AX, EB_RHO, EB_W, OPB_C, 0}});
+        if (!rc) rc = one(w.tl_sg, {{EB_S, EB_W, EB_AX, OPB_N, 1}, {EB_G, EB_W, EB_W, OPB_C, 1}});
+        if (!rc) rc = one(w.tl_y, {{EB_WN, EB_E, EB_W, OPB_N, 0}});
         if (rc) return rc;
         w.ready = true;
     }

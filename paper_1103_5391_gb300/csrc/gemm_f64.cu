@@ -3,6 +3,8 @@
 //
 // One CTA computes one 16 x 16 output tile of one task over a range of its segments:
 //     C_tile = (beta ? C_tile : 0) + sum_segments scale * A_seg * op(B_seg)
+// For a Hermitian result (rho_L and the Gram matrices of the eigen-refinement) only the tiles on and
+// below the diagonal are computed and each off-diagonal tile is also stored conjugate-transposed.
 // On GB300 FP64 runs at about 1 TFLOP/s for the whole chip (scalar DFMA and the FP64 MMA alike),
 // i.e. about 7 GFLOP/s per SM, so the kernel is organised for balance rather than data reuse:
 //   - small (16 x 16) tiles so that every sector pair spreads over many SMs;
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                 x.y += o.y;
             }
             *p = x;
+            if (task.herm && m0 != n0) C[(int64_t)(n0 + col) * task.ldc + m0 + r] = make_double2(x.x, neg(x.y));
         }
     }
 }

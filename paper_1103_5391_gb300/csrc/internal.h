@@ -40,7 +40,9 @@ struct Task {
     int64_t c_off;
     int32_t ldc, M, N;
     int32_t seg_begin, seg_end;
-    int8_t c_buf, beta, pad0, pad1;
+    int8_t c_buf, beta;
+    int8_t herm;              // C Hermitian (M == N, beta == 0): tiles below the diagonal only, mirrored
+    int8_t pad1;
     int32_t pad2;
 };
 

@@ -95,6 +95,7 @@ void make_tiles(TaskList& tl, int tm, int tn, int ksplit) {
         for (int m0 = 0; m0 < std::max(k.M, 1); m0 += tm)
             for (int n0 = 0; n0 < std::max(k.N, 1); n0 += tn) {
                 if (m0 >= k.M || n0 >= k.N) continue;
+                if (k.herm && n0 > m0) continue;   // upper tiles are written as mirrors of the lower ones
                 int mm = std::min(tm, k.M - m0), nn = std::min(tn, k.N - n0);
                 const int np = (int)parts.size();
                 const int split = np > 1 ? tl.nsplit++ : -1;
