@@ -332,12 +332,17 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
 
 // ---- warp-specialised persistent variant (S <= 4) -------------------------------------------------
 // One CTA per SM walks the tile list (tile = blockIdx.x, + gridDim.x, ...).  Warp 0 issues the TMA
-// loads into NST shared-memory stages, one thread of warp 1 issues the MMAs, warps 2..5 drain the
-// TMEM accumulators.  Accumulation blocks (<= 8 chunks of one tile) alternate between two TMEM
+// loads into NST shared-memory stages, one thread of warp 1 issues the MMAs (M = 64: the M = 64 data
+// path puts row i in TMEM lane 32 (i / 16) + i % 16), warps 2..9 drain the TMEM accumulators, two warps
+// per lane quarter each taking half of the columns.  Accumulation blocks (<= 8 chunks of one tile) alternate between two TMEM
 // buffers, so the epilogue of one block overlaps the MMAs of the next.  Hand-offs:
 //   full[st]  (TMA -> MMA, transaction bytes)     empty[st] (MMA completion -> TMA)
 //   tfull[b]  (MMA completion -> epilogue)         tempty[b] (epilogue warps -> MMA)
-constexpr int NST = 2;
+constexpr int TMW = 64;                    // MMA M of this variant: sector blocks are mostly <= 64 rows
+constexpr int ABOXW = TMW * KCH * 2;       // bytes of one A slice box (8 KB)
+constexpr int NST = 3;                     // shared-memory stages of S x (8 + 8) KB
+constexpr int EPIW = 8;                    // epilogue warps: two per TMEM lane quarter, splitting the columns
+constexpr int WS_THREADS = 64 + 32 * EPIW;
 constexpr long kWaitWS = 1L << 22;
 
 __device__ __forceinline__ bool mbar_wait_ws(uint32_t bar, uint32_t parity, volatile int* failed) {
@@ -353,13 +358,13 @@ __device__ __forceinline__ bool mbar_wait_ws(uint32_t bar, uint32_t parity, vola
 }
 
 template <int S>
-__global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa,
                                                           GemmArgs g, int ntiles, const int* skip_flag, int skip_step) {
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     static_assert(S <= 4, "two TMEM buffers of S x 64 columns must fit in 512");
     constexpr uint32_t NCOLS = 512;
-    constexpr uint32_t STAGE = S * (ABOX + BBOX);
+    constexpr uint32_t STAGE = S * (ABOXW + BBOX);
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2];
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
         }
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&tfull[i])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(smem_u32(&tempty[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&tempty[i])), "r"(EPIW));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -398,11 +403,11 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
                     const int st = c % NST;
                     if (!mbar_wait_ws(smem_u32(&empty[st]), ((c / NST) & 1) ^ 1, &failed)) break;
                     unsigned char* sA = smem + st * STAGE;
-                    unsigned char* sB = sA + S * ABOX;
+                    unsigned char* sB = sA + S * ABOXW;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(&full[st])), "r"(STAGE) : "memory");
 #pragma unroll
                     for (int s = 0; s < S; ++s) {
-                        tma_load(smem_u32(sA + s * ABOX), &mapA, k * KCH, s * oa.rowsA + ya, smem_u32(&full[st]));
+                        tma_load(smem_u32(sA + s * ABOXW), &mapA, k * KCH, s * oa.rowsA + ya, smem_u32(&full[st]));
                         tma_load(smem_u32(sB + s * BBOX), &mapB, k * KCH, s * oa.rowsB + yb, smem_u32(&full[st]));
                     }
                 }
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
                 const int nrem = task.N - tile.n0;
                 const int n_t = ((nrem < TNC ? nrem : TNC) + 7) & ~7;
                 const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * n_t) >> 3) << 17) |
-                                       ((uint32_t)(TM >> 4) << 24);
+                                       ((uint32_t)(TMW >> 4) << 24);
                 for (int k0 = 0; k0 < task.kchunks && !failed; k0 += kReadoutChunks, ++b) {
                     const int buf = b & 1;
                     if (!mbar_wait_ws(smem_u32(&tempty[buf]), ((b >> 1) & 1) ^ 1, &failed)) break;
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
                         if (!mbar_wait_ws(smem_u32(&full[st]), (c / NST) & 1, &failed)) break;
                         asm volatile("tcgen05.fence::after_thread_sync;");
                         unsigned char* sA = smem + st * STAGE;
-                        unsigned char* sB = sA + S * ABOX;
+                        unsigned char* sB = sA + S * ABOXW;
 #pragma unroll
                         for (int ks = 0; ks < KCH / 16; ++ks) {
 #pragma unroll
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
                                 const int s_lo = gg - S > 1 ? gg - S : 1, s_hi = gg - 1 < S ? gg - 1 : S;
 #pragma unroll
                                 for (int s = s_lo; s <= s_hi; ++s) {
-                                    const uint64_t da = desc_sw128(smem_u32(sA + (s - 1) * ABOX) + ks * 32);
+                                    const uint64_t da = desc_sw128(smem_u32(sA + (s - 1) * ABOXW) + ks * 32);
                                     const uint64_t db = desc_sw128(smem_u32(sB + (gg - s - 1) * BBOX) + ks * 32);
                                     const uint32_t accum = (k == k0 && ks == 0 && s == s_lo) ? 0u : 1u;
                                     umma(tmem + (uint32_t)(buf * S * 64 + (gg - 2) * 64), da, db, idesc, accum);
@@ -451,9 +456,10 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
                 }
             }
         }
-    } else {   // ------------------------------------------------------------------------ epilogue warps 2..5
-        const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31
-        const int row = 32 * quad + lane;
+    } else {   // ------------------------------------------------------------------------ epilogue warps 2..9
+        const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31 (16 of them hold rows)
+        const int half = (warp - 2) >> 2;     // accumulator columns 32 * half .. 32 * half + 31
+        const int row = 16 * quad + lane;     // valid for lane < 16
         uint32_t b = 0;
         for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
             const OzTile tile = oa.tiles[t];
@@ -461,9 +467,9 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
             const int nrem = task.N - tile.n0;
             const int nval = nrem < TNC ? nrem : TNC;
             const int n_t = (nval + 7) & ~7;
-            long long acc[64];
+            long long acc[32];
 #pragma unroll
-            for (int j = 0; j < 64; ++j) acc[j] = 0;
+            for (int j = 0; j < 32; ++j) acc[j] = 0;
             bool ok = true;
             for (int k0 = 0; k0 < task.kchunks; k0 += kReadoutChunks, ++b) {
                 const int buf = b & 1;
@@ -472,15 +478,15 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
 #pragma unroll
                 for (int gg = 2; gg <= S + 1; ++gg) {
                     const int shift = 7 * (S + 1 - gg);
-                    uint32_t r[4][16];
+                    uint32_t r[2][16];
 #pragma unroll
-                    for (int cb = 0; cb < 4; ++cb)
-                        if (cb * 16 < 2 * n_t)
-                            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * S * 64 + (gg - 2) * 64 + cb * 16), r[cb]);
+                    for (int cb = 0; cb < 2; ++cb)
+                        if ((2 * half + cb) * 16 < 2 * n_t)
+                            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * S * 64 + (gg - 2) * 64 + (2 * half + cb) * 16), r[cb]);
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                    for (int cb = 0; cb < 4; ++cb)
-                        if (cb * 16 < 2 * n_t) {
+                    for (int cb = 0; cb < 2; ++cb)
+                        if ((2 * half + cb) * 16 < 2 * n_t) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j)
                                 acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[cb][j])) << shift;
@@ -491,17 +497,18 @@ __global__ void __launch_bounds__(192, 1) k_ozaki_gemm_ws(const __grid_constant_
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&tempty[buf])) : "memory");
             }
             if (!ok) break;
-            if (tile.m0 + row < task.M) {
+            if (lane < 16 && tile.m0 + row < task.M) {
                 const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
                 double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * task.ldc + tile.n0);
 #pragma unroll
-                for (int jj = 0; jj < 64; ++jj) {
+                for (int jl = 0; jl < 32; ++jl) {
+                    const int jj = 32 * half + jl;
                     if (jj < 2 * n_t) {
                         const bool im = jj >= n_t;
                         const int j = im ? jj - n_t : jj;
                         if (j < nval) {
                             const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
-                            double v = scaled_int(acc[jj], e);
+                            double v = scaled_int(acc[jl], e);
                             double* pc = C + 2 * j + (im ? 1 : 0);
                             if (task.beta) v += *pc;
                             *pc = v;
@@ -546,7 +553,7 @@ int encode_map(tdmrg_ctx* c, CUtensorMap* m, void* base, int64_t rows, int kpad,
 template <int S>
 cudaError_t gemm_attr() {
     if constexpr (S <= 4) {
-        const size_t smem = (size_t)NST * S * (ABOX + BBOX) + 1024;
+        const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
         return cudaFuncSetAttribute(k_ozaki_gemm_ws<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     } else {
         const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
@@ -559,10 +566,10 @@ int g_num_sms = 0;
 template <int S>
 cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
     if constexpr (S <= 4) {
-        const size_t smem = (size_t)NST * S * (ABOX + BBOX) + 1024;
+        const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
         const int ntiles = (int)st.tiles.size();
         const int grid = std::max(1, std::min(ntiles, g_num_sms));
-        k_ozaki_gemm_ws<S><<<grid, 192, smem, s>>>(st.mapA, st.mapB, st.args, g, ntiles, skip_flag, skip_step);
+        k_ozaki_gemm_ws<S><<<grid, WS_THREADS, smem, s>>>(st.mapA, st.mapB, st.args, g, ntiles, skip_flag, skip_step);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
@@ -621,6 +628,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
     release_oz(c, oz);
     oz.S = S;
     oz.status = c->dstatus;
+    const int tm = S <= 4 ? TMW : TM;   // MMA M of the kernel that runs this precision
     int rc = TDMRG_OK;
     for (int stg = 0; stg < 2; ++stg) {
         const TaskList& tl = stg == 0 ? p->stage1 : p->stage2;
@@ -690,12 +698,12 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             }
             const int ti = (int)st.tasks.size();
             st.tasks.push_back(ot);
-            for (int m0 = 0; m0 < tk.M; m0 += TM)
-                for (int n0 = 0; n0 < tk.N; n0 += TNC) st.tiles.push_back({ti, m0, n0, (int)(std::min(TM, tk.M - m0) * std::min(TNC, tk.N - n0)) * ot.kchunks});
+            for (int m0 = 0; m0 < tk.M; m0 += tm)
+                for (int n0 = 0; n0 < tk.N; n0 += TNC) st.tiles.push_back({ti, m0, n0, (int)(std::min(tm, tk.M - m0) * std::min(TNC, tk.N - n0)) * ot.kchunks});
         }
         std::stable_sort(st.tiles.begin(), st.tiles.end(), [](const OzTile& a, const OzTile& b) { return a.cost > b.cost; });
-        // panels: rows padded so that every TMA box (128 rows for A, 64 for B) stays inside the plane
-        st.rowsA = rowsA + TM;
+        // panels: rows padded so that every TMA box (tm rows for A, 64 for B) stays inside the plane
+        st.rowsA = rowsA + tm;
         st.rowsB = rowsB + 2 * TNC;
         st.kpad = std::max(KCH, (kmax + KCH - 1) / KCH * KCH);
         st.panel_bytes_a = (size_t)S * st.rowsA * st.kpad * 2;
@@ -717,7 +725,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (!rc) rc = upload_vec(c, st.bjobs, &st.d_bjobs, "ozaki slice jobs");
             if (!rc) rc = upload_vec(c, st.asegs, &st.d_asegs, "ozaki slice segments");
             if (!rc) rc = upload_vec(c, st.bsegs, &st.d_bsegs, "ozaki slice segments");
-            if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, TM);
+            if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, tm);
             if (!rc) rc = encode_map(c, &st.mapB, st.panelB, (int64_t)S * st.rowsB, st.kpad, 2 * TNC);
             if (rc) return rc;
             st.args.tasks = st.d_tasks; st.args.tiles = st.d_tiles;
