@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
     for (int e = 0; e < 2; ++e) {
         const int col = col0 + e;
         if (r < Mt && col < Nt) {
-            cplx* p = C + (int64_t)(m0 + r) * task.ldc + n0 + col;
+            cplx* p = task.trans ? C + (int64_t)(n0 + col) * task.ldc + m0 + r : C + (int64_t)(m0 + r) * task.ldc + n0 + col;
             double2 x = v[e];
             if (task.beta) {
                 const double2 o = *p;

@@ -42,7 +42,7 @@ struct Task {
     int32_t seg_begin, seg_end;
     int8_t c_buf, beta;
     int8_t herm;              // C Hermitian (M == N, beta == 0): tiles below the diagonal only, mirrored
-    int8_t pad1;
+    int8_t trans;             // C stored transposed: element (m, n) at c_off + n * ldc + m
     int32_t pad2;
 };
 
@@ -79,7 +79,7 @@ struct OzTask {            // one complex GEMM C (+)= A op(B), all of its segmen
     int32_t arow0, brow0;  // first panel row of A' (rows) and B' (column pairs)
     int32_t aexp0, bexp0;  // first exponent of the rows / columns
     int32_t kchunks;       // 64-wide chunks of the real K (2 sum K)
-    int8_t c_buf, beta, pad0, pad1;
+    int8_t c_buf, beta, trans, pad1;
 };
 struct OzTile { int32_t task, m0, n0, cost; };
 struct OzSliceJob {        // slices the rows of A' (role 0) or columns of B' (role 1) of one operand

@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
     const int row = 32 * warp + lane;
     if (!failed && tile.m0 + row < task.M) {
         const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
-        double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * task.ldc + tile.n0);
+        const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
+        double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
 #pragma unroll
         for (int jj = 0; jj < 64; ++jj) {       // accumulator column jj: Re of column jj, or Im of column jj - n_t
             if (jj < 2 * n_t) {
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
                 if (j < nval) {
                     const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
                     double v = scaled_int(acc[jj], e);
-                    double* pc = C + 2 * j + (im ? 1 : 0);
+                    double* pc = C + 2 * (int64_t)j * cs + (im ? 1 : 0);
                     if (task.beta) v += *pc;
                     *pc = v;
                 }
@@ -499,7 +500,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
             if (!ok) break;
             if (lane < 16 && tile.m0 + row < task.M) {
                 const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
-                double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * task.ldc + tile.n0);
+                const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
+        double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
 #pragma unroll
                 for (int jl = 0; jl < 32; ++jl) {
                     const int jj = 32 * half + jl;
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                         if (j < nval) {
                             const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
                             double v = scaled_int(acc[jl], e);
-                            double* pc = C + 2 * j + (im ? 1 : 0);
+                            double* pc = C + 2 * (int64_t)j * cs + (im ? 1 : 0);
                             if (task.beta) v += *pc;
                             *pc = v;
                         }
@@ -654,6 +656,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             }
             OzTask ot{};
             ot.c_off = tk.c_off; ot.c_buf = tk.c_buf; ot.ldc = tk.ldc; ot.M = tk.M; ot.N = tk.N; ot.beta = tk.beta;
+            ot.trans = tk.trans;
             ot.kchunks = (2 * ktot + KCH - 1) / KCH;
             kmax = std::max(kmax, 2 * ktot);
             // A operand

@@ -189,10 +189,12 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
                         s.b_off = pi.off; s.b_buf = BUF_IN; s.ldb = pi.dr; s.opb = OPB_N;
                         s.K = pi.dl; s.scale = sc; s.dscale = -1;
                         left[ko].push_back(s);
-                    } else {           // T = Psi_{q'} B^T (scratch), then Psi'_q += sc * A T
+                    } else {           // T = Psi_{q'} B^T (scratch, stored as T^T), then Psi'_q += sc * A T
+                        // T^T rows are the columns of T: the stage-1 stores and the stage-2 operand
+                        // reads (slicing of the columns of T) run along contiguous memory
                         Task tk{};
-                        tk.c_off = scr; tk.c_buf = BUF_SCRATCH; tk.ldc = po.dr; tk.M = pi.dl; tk.N = po.dr;
-                        tk.beta = 0;
+                        tk.c_off = scr; tk.c_buf = BUF_SCRATCH; tk.ldc = pi.dl; tk.M = pi.dl; tk.N = po.dr;
+                        tk.beta = 0; tk.trans = 1;
                         Seg s{};
                         s.a_off = pi.off; s.a_buf = BUF_IN; s.lda = pi.dr;
                         s.b_off = b.second; s.b_buf = BUF_OPS; s.ldb = pi.dr; s.opb = OPB_T;
@@ -201,7 +203,7 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
                         s1_inter_seg.push_back(s);
                         Seg s2{};
                         s2.a_off = a.second; s2.a_buf = BUF_OPS; s2.lda = pi.dl;
-                        s2.b_off = scr; s2.b_buf = BUF_SCRATCH; s2.ldb = po.dr; s2.opb = OPB_N;
+                        s2.b_off = scr; s2.b_buf = BUF_SCRATCH; s2.ldb = pi.dl; s2.opb = OPB_T;
                         s2.K = pi.dl; s2.scale = sc; s2.dscale = -1;
                         left[ko].push_back(s2);
                         scr += (int64_t)pi.dl * po.dr;
