@@ -65,28 +65,38 @@ __device__ __forceinline__ void digits(long long N, int* d) {
     d[S - 1] = (int)N;
 }
 
-__device__ __forceinline__ double2 fetch(const Seg& sg, const GemmArgs& g, int role, int vec, int k) {
-    if (role == 0) {   // A role: row vec of A
-        double2 v = g.bufs[sg.a_buf][sg.a_off + (int64_t)vec * sg.lda + k];
-        return v;
-    }
-    const cplx* B = g.bufs[sg.b_buf] + sg.b_off;   // B role: column vec of op(B)
-    if (sg.opb == OPB_N) return B[(int64_t)k * sg.ldb + vec];
-    double2 v = B[(int64_t)vec * sg.ldb + k];
-    if (sg.opb == OPB_C) v.y = -v.y;
-    return v;
-}
-
 __device__ __forceinline__ double2 scaled(double2 v, cplx s) {
     return make_double2(s.x * v.x - s.y * v.y, s.x * v.y + s.y * v.x);
 }
 
-// One warp per vector (row of A' or complex column of B'); two passes over the task's segments.
+// One warp per vector (row of A' or complex column of B'); two passes over the task's segments
+// (exponent, then digits).  The segments are flattened into one element index (their views cached in
+// shared memory, kSegCache at a time) and each lane issues kSliceU independent loads per batch, so a
+// vector costs a few memory latencies instead of one per segment and pass; a vector of at most
+// 32 kSliceU elements keeps its values in registers between the passes.
+constexpr int kSliceU = 8;
+constexpr int kSegCache = 16;
+constexpr int kSliceWarps = 8;
+
+struct SegView {          // element k of the vector at base[k * sk], conjugated and scaled as asked
+    const double2* base;
+    int64_t sk;
+    double2 scale;
+    int conj;
+};
+
+__device__ __forceinline__ double2 view_load(const SegView& w, int k, bool use_scale) {
+    double2 x = w.base[(int64_t)k * w.sk];
+    if (w.conj) x.y = -x.y;
+    if (use_scale) x = scaled(x, w.scale);
+    return x;
+}
+
 template <int S>
-__global__ void __launch_bounds__(256) k_slice(OzSliceArgs sa, GemmArgs g, const int* skip_flag, int skip_step) {
+__global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, GemmArgs g, const int* skip_flag, int skip_step) {
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (gw >= sa.nvec_total) return;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    if (gw >= sa.nvec_total) return;   // warp-uniform
     int lo = 0, hi = sa.njobs - 1;   // job with vec_prefix[job] <= gw < vec_prefix[job + 1]
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -95,15 +105,68 @@ __global__ void __launch_bounds__(256) k_slice(OzSliceArgs sa, GemmArgs g, const
     const OzSliceJob job = sa.jobs[lo];
     const int v = gw - job.vec_prefix;
     constexpr int S7 = 7 * S;
-    int emax = 0;
-    for (int s = job.seg_begin; s < job.seg_end; ++s) {
-        const Seg sg = sa.segs[s];
-        for (int k = lane; k < sg.K; k += 32) {
-            double2 x = fetch(sg, g, job.role, v, k);
-            if (job.use_scale) x = scaled(x, sg.scale);
-            emax = max(emax, max(biased_exp(x.x), biased_exp(x.y)));
+    __shared__ SegView sv[kSliceWarps][kSegCache];
+    __shared__ int spre[kSliceWarps][kSegCache + 1];
+    const int nseg = job.seg_end - job.seg_begin;
+    const bool use_scale = job.use_scale != 0;
+    // views of segments [w0, w0 + nw) for this vector; prefix offsets of their K in spre
+    auto build = [&](int w0, int nw) {
+        __syncwarp();
+        if (lane < nw) {
+            const Seg sg = sa.segs[job.seg_begin + w0 + lane];
+            SegView w;
+            w.scale = sg.scale;
+            w.conj = 0;
+            if (job.role == 0) {
+                w.base = g.bufs[sg.a_buf] + sg.a_off + (int64_t)v * sg.lda;
+                w.sk = 1;
+            } else {
+                const cplx* B = g.bufs[sg.b_buf] + sg.b_off;
+                if (sg.opb == OPB_N) { w.base = B + v; w.sk = sg.ldb; }
+                else { w.base = B + (int64_t)v * sg.ldb; w.sk = 1; w.conj = sg.opb == OPB_C; }
+            }
+            sv[wi][lane] = w;
+            spre[wi][lane + 1] = sg.K;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            spre[wi][0] = 0;
+            for (int i = 0; i < nw; ++i) spre[wi][i + 1] += spre[wi][i];
+        }
+        __syncwarp();
+        return spre[wi][nw];
+    };
+    auto seg_of = [&](int e, int nw) {
+        int sgi = 0;
+        while (sgi + 1 < nw && e >= spre[wi][sgi + 1]) ++sgi;
+        return sgi;
+    };
+    double2 cache[kSliceU];
+    const bool one_batch = nseg <= kSegCache;
+    int emax = 0, kw_first = 0;
+    for (int w0 = 0; w0 < nseg; w0 += kSegCache) {   // pass 1: largest exponent
+        const int nw = min(kSegCache, nseg - w0);
+        const int kw = build(w0, nw);
+        if (w0 == 0) kw_first = kw;
+        for (int e0 = 0; e0 < kw; e0 += 32 * kSliceU) {
+            double2 x[kSliceU];
+#pragma unroll
+            for (int u = 0; u < kSliceU; ++u) {
+                const int e = e0 + lane + 32 * u;
+                x[u] = make_double2(0.0, 0.0);
+                if (e < kw) {
+                    const int sgi = seg_of(e, nw);
+                    x[u] = view_load(sv[wi][sgi], e - spre[wi][sgi], use_scale);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSliceU; ++u) {
+                emax = max(emax, max(biased_exp(x[u].x), biased_exp(x[u].y)));
+                cache[u] = x[u];
+            }
         }
     }
+    const bool cached = one_batch && kw_first <= 32 * kSliceU;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     const int E = emax == 0 ? 0 : emax - 1023 + 1;   // every |value| < 2^E
@@ -121,30 +184,45 @@ __global__ void __launch_bounds__(256) k_slice(OzSliceArgs sa, GemmArgs g, const
     const int64_t plane = (int64_t)sa.rows * sa.kpad;
     __nv_bfloat16* P = sa.panel;
     int kbase = 0;
-    for (int s = job.seg_begin; s < job.seg_end; ++s) {
-        const Seg sg = sa.segs[s];
-        for (int k = lane; k < sg.K; k += 32) {
-            double2 x = fetch(sg, g, job.role, v, k);
-            if (job.use_scale) x = scaled(x, sg.scale);
-            int dr[S], di[S];
-            digits<S>(fixed_point(x.x, E, S7), dr);
-            digits<S>(fixed_point(x.y, E, S7), di);
-            const int p = kbase + k, q = job.ktot + kbase + k;
+    for (int w0 = 0; w0 < nseg; w0 += kSegCache) {   // pass 2: digits
+        const int nw = min(kSegCache, nseg - w0);
+        const int kw = (w0 == 0 && one_batch) ? kw_first : build(w0, nw);
+        for (int e0 = 0; e0 < kw; e0 += 32 * kSliceU) {
+            double2 x[kSliceU];
 #pragma unroll
-            for (int t = 0; t < S; ++t) {
-                __nv_bfloat16* pl = P + t * plane;
-                if (job.role == 0) {
-                    pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
-                    pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)di[t]);
-                } else {
-                    pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
-                    pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)(-di[t]));
-                    pl[(int64_t)r_im * sa.kpad + p] = __float2bfloat16_rn((float)di[t]);
-                    pl[(int64_t)r_im * sa.kpad + q] = __float2bfloat16_rn((float)dr[t]);
+            for (int u = 0; u < kSliceU; ++u) {
+                const int e = e0 + lane + 32 * u;
+                x[u] = make_double2(0.0, 0.0);
+                if (cached) x[u] = cache[u];
+                else if (e < kw) {
+                    const int sgi = seg_of(e, nw);
+                    x[u] = view_load(sv[wi][sgi], e - spre[wi][sgi], use_scale);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kSliceU; ++u) {
+                const int e = e0 + lane + 32 * u;
+                if (e >= kw) continue;
+                int dr[S], di[S];
+                digits<S>(fixed_point(x[u].x, E, S7), dr);
+                digits<S>(fixed_point(x[u].y, E, S7), di);
+                const int p = kbase + e, q = job.ktot + kbase + e;
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+                    __nv_bfloat16* pl = P + t * plane;
+                    if (job.role == 0) {
+                        pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
+                        pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)di[t]);
+                    } else {
+                        pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
+                        pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)(-di[t]));
+                        pl[(int64_t)r_im * sa.kpad + p] = __float2bfloat16_rn((float)di[t]);
+                        pl[(int64_t)r_im * sa.kpad + q] = __float2bfloat16_rn((float)dr[t]);
+                    }
                 }
             }
         }
-        kbase += sg.K;
+        kbase += kw;
     }
 }
 
@@ -581,7 +659,7 @@ cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, co
 
 cudaError_t slice_launch(const OzSliceArgs& sa, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
     if (sa.nvec_total <= 0) return cudaSuccess;
-    const int warps = 8, grid = (sa.nvec_total + warps - 1) / warps;
+    const int warps = kSliceWarps, grid = (sa.nvec_total + warps - 1) / warps;
     switch (sa.S) {
         case 2: k_slice<2><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
         case 3: k_slice<3><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
