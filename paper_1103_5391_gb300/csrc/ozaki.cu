@@ -388,13 +388,20 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
         const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
         const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
         double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
+        int eB[64];   // loads ahead of the stores (see the warp-specialised kernel)
+#pragma unroll
+        for (int jj = 0; jj < 64; ++jj) {
+            const bool im = jj >= n_t;
+            const int j = im ? jj - n_t : jj;
+            eB[jj] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
+        }
 #pragma unroll
         for (int jj = 0; jj < 64; ++jj) {       // accumulator column jj: Re of column jj, or Im of column jj - n_t
             if (jj < 2 * n_t) {
                 const bool im = jj >= n_t;
                 const int j = im ? jj - n_t : jj;
                 if (j < nval) {
-                    const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
+                    const int e = Ei + eB[jj] - 7 * (S + 1);
                     double v = scaled_int(acc[jj], e);
                     double* pc = C + 2 * (int64_t)j * cs + (im ? 1 : 0);
                     if (task.beta) v += *pc;
@@ -447,6 +454,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2];
+    __shared__ int sExp[EPIW][32];   // column exponents of the epilogue warps' current tile
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -552,7 +560,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
             bool ok = true;
             for (int k0 = 0; k0 < task.kchunks; k0 += kReadoutChunks, ++b) {
                 const int buf = b & 1;
-                if (!mbar_wait_ws(smem_u32(&tfull[buf]), (b >> 1) & 1, &failed)) { ok = false; break; }
+                // warp-uniform outcome: the warp synchronises below
+                if (!__all_sync(0xffffffffu, mbar_wait_ws(smem_u32(&tfull[buf]), (b >> 1) & 1, &failed))) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                 for (int gg = 2; gg <= S + 1; ++gg) {
@@ -576,26 +585,41 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&tempty[buf])) : "memory");
             }
             if (!ok) break;
+            // loads ahead of the stores (a load behind a store to C may not be reordered above it, so
+            // loads inside the store loop would cost one memory latency each): the column exponents
+            // through a per-warp row of shared memory, the beta operands eight at a time
+            {
+                const int jj = 32 * half + lane;
+                const bool im = jj >= n_t;
+                const int j = im ? jj - n_t : jj;
+                sExp[warp - 2][lane] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
+            }
+            __syncwarp();
             if (lane < 16 && tile.m0 + row < task.M) {
-                const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
+                const int Ei = oa.expA[task.aexp0 + tile.m0 + row] - 7 * (S + 1);
                 const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
-        double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
+                double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
 #pragma unroll
-                for (int jl = 0; jl < 32; ++jl) {
-                    const int jj = 32 * half + jl;
-                    if (jj < 2 * n_t) {
+                for (int c8 = 0; c8 < 32; c8 += 8) {
+                    double old[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int jj = 32 * half + c8 + u;
                         const bool im = jj >= n_t;
                         const int j = im ? jj - n_t : jj;
-                        if (j < nval) {
-                            const int e = Ei + oa.expB[task.bexp0 + tile.n0 + j] - 7 * (S + 1);
-                            double v = scaled_int(acc[jl], e);
-                            double* pc = C + 2 * (int64_t)j * cs + (im ? 1 : 0);
-                            if (task.beta) v += *pc;
-                            *pc = v;
-                        }
+                        old[u] = (task.beta && jj < 2 * n_t && j < nval) ? C[2 * (int64_t)j * cs + (im ? 1 : 0)] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int jj = 32 * half + c8 + u;
+                        const bool im = jj >= n_t;
+                        const int j = im ? jj - n_t : jj;
+                        if (jj < 2 * n_t && j < nval)
+                            C[2 * (int64_t)j * cs + (im ? 1 : 0)] = scaled_int(acc[c8 + u], Ei + sExp[warp - 2][c8 + u]) + old[u];
                     }
                 }
             }
+            __syncwarp();   // sExp is rewritten for the next tile
         }
     }
     __syncthreads();
