@@ -419,15 +419,15 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
 // ---- warp-specialised persistent variant (S <= 4) -------------------------------------------------
 // One CTA per SM walks the tile list (tile = blockIdx.x, + gridDim.x, ...).  Warp 0 issues the TMA
 // loads into NST shared-memory stages, one thread of warp 1 issues the MMAs (M = 64: the M = 64 data
-// path puts row i in TMEM lane 32 (i / 16) + i % 16), warps 2..9 drain the TMEM accumulators, two warps
-// per lane quarter each taking half of the columns.  Accumulation blocks (<= 8 chunks of one tile) alternate between two TMEM
+// path puts row i in TMEM lane 32 (i / 16) + i % 16), warps 2..17 drain the TMEM accumulators, four
+// warps per lane quarter each taking 16 of the 64 accumulator columns.  Accumulation blocks (<= 8 chunks of one tile) alternate between two TMEM
 // buffers, so the epilogue of one block overlaps the MMAs of the next.  Hand-offs:
 //   full[st]  (TMA -> MMA, transaction bytes)     empty[st] (MMA completion -> TMA)
 //   tfull[b]  (MMA completion -> epilogue)         tempty[b] (epilogue warps -> MMA)
 constexpr int TMW = 64;                    // MMA M of this variant: sector blocks are mostly <= 64 rows
 constexpr int ABOXW = TMW * KCH * 2;       // bytes of one A slice box (8 KB)
 constexpr int NST = 3;                     // shared-memory stages of S x (8 + 8) KB
-constexpr int EPIW = 8;                    // epilogue warps: two per TMEM lane quarter, splitting the columns
+constexpr int EPIW = 16;                   // epilogue warps: four per TMEM lane quarter, 16 accumulator columns each
 constexpr int WS_THREADS = 64 + 32 * EPIW;
 constexpr long kWaitWS = 1L << 22;
 
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2];
-    __shared__ int sExp[EPIW][32];   // column exponents of the epilogue warps' current tile
+    __shared__ int sExp[EPIW][16];   // column exponents of the epilogue warps' current tile
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -543,9 +543,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 }
             }
         }
-    } else {   // ------------------------------------------------------------------------ epilogue warps 2..9
+    } else {   // ------------------------------------------------------------------------ epilogue warps 2..17
         const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31 (16 of them hold rows)
-        const int half = (warp - 2) >> 2;     // accumulator columns 32 * half .. 32 * half + 31
+        const int part = (warp - 2) >> 2;     // accumulator columns 16 * part .. 16 * part + 15
         const int row = 16 * quad + lane;     // valid for lane < 16
         uint32_t b = 0;
         for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
@@ -554,9 +554,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
             const int nrem = task.N - tile.n0;
             const int nval = nrem < TNC ? nrem : TNC;
             const int n_t = (nval + 7) & ~7;
-            long long acc[32];
+            long long acc[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = 0;
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
             bool ok = true;
             for (int k0 = 0; k0 < task.kchunks; k0 += kReadoutChunks, ++b) {
                 const int buf = b & 1;
@@ -566,19 +566,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
 #pragma unroll
                 for (int gg = 2; gg <= S + 1; ++gg) {
                     const int shift = 7 * (S + 1 - gg);
-                    uint32_t r[2][16];
-#pragma unroll
-                    for (int cb = 0; cb < 2; ++cb)
-                        if ((2 * half + cb) * 16 < 2 * n_t)
-                            tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * S * 64 + (gg - 2) * 64 + (2 * half + cb) * 16), r[cb]);
+                    uint32_t r[16];
+                    if (part * 16 < 2 * n_t)
+                        tmem_ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * S * 64 + (gg - 2) * 64 + part * 16), r);
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (part * 16 < 2 * n_t) {
 #pragma unroll
-                    for (int cb = 0; cb < 2; ++cb)
-                        if ((2 * half + cb) * 16 < 2 * n_t) {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                acc[cb * 16 + j] += (long long)__float2int_rn(__uint_as_float(r[cb][j])) << shift;
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << shift;
+                    }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
@@ -589,10 +585,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
             // loads inside the store loop would cost one memory latency each): the column exponents
             // through a per-warp row of shared memory, the beta operands eight at a time
             {
-                const int jj = 32 * half + lane;
+                const int jj = 16 * part + lane;
                 const bool im = jj >= n_t;
                 const int j = im ? jj - n_t : jj;
-                sExp[warp - 2][lane] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
+                if (lane < 16) sExp[warp - 2][lane] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
             }
             __syncwarp();
             if (lane < 16 && tile.m0 + row < task.M) {
@@ -600,18 +596,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
                 double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
 #pragma unroll
-                for (int c8 = 0; c8 < 32; c8 += 8) {
+                for (int c8 = 0; c8 < 16; c8 += 8) {
                     double old[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const int jj = 32 * half + c8 + u;
+                        const int jj = 16 * part + c8 + u;
                         const bool im = jj >= n_t;
                         const int j = im ? jj - n_t : jj;
                         old[u] = (task.beta && jj < 2 * n_t && j < nval) ? C[2 * (int64_t)j * cs + (im ? 1 : 0)] : 0.0;
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const int jj = 32 * half + c8 + u;
+                        const int jj = 16 * part + c8 + u;
                         const bool im = jj >= n_t;
                         const int j = im ? jj - n_t : jj;
                         if (jj < 2 * n_t && j < nval)
