@@ -87,6 +87,7 @@ struct OzSliceJob {        // slices the rows of A' (role 0) or columns of B' (r
 };
 struct OzSliceArgs {
     const OzSliceJob* jobs;
+    const int* vjob;       // job of each vector
     int njobs;
     const Seg* segs;
     __nv_bfloat16* panel;
@@ -106,6 +107,9 @@ struct OzStage {
     std::vector<OzTile> tiles;
     std::vector<OzSliceJob> ajobs, bjobs;
     std::vector<Seg> asegs, bsegs;
+    std::vector<int> avjob, bvjob;   // job index of every vector
+    int* d_avjob = nullptr;
+    int* d_bvjob = nullptr;
     OzTask* d_tasks = nullptr;
     OzTile* d_tiles = nullptr;
     OzSliceJob* d_ajobs = nullptr;

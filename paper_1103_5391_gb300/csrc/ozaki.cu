@@ -97,12 +97,7 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, Gemm
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     if (gw >= sa.nvec_total) return;   // warp-uniform
-    int lo = 0, hi = sa.njobs - 1;   // job with vec_prefix[job] <= gw < vec_prefix[job + 1]
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sa.jobs[mid].vec_prefix <= gw) lo = mid; else hi = mid - 1;
-    }
-    const OzSliceJob job = sa.jobs[lo];
+    const OzSliceJob job = sa.jobs[sa.vjob[gw]];
     const int v = gw - job.vec_prefix;
     constexpr int S7 = 7 * S;
     __shared__ SegView sv[kSliceWarps][kSegCache];
@@ -708,6 +703,8 @@ void release_oz(tdmrg_ctx* c, OzPlan& oz) {
         dev_free(c, st.d_tiles, st.tiles.size() * sizeof(OzTile));
         dev_free(c, st.d_ajobs, st.ajobs.size() * sizeof(OzSliceJob));
         dev_free(c, st.d_bjobs, st.bjobs.size() * sizeof(OzSliceJob));
+        dev_free(c, st.d_avjob, st.avjob.size() * sizeof(int));
+        dev_free(c, st.d_bvjob, st.bvjob.size() * sizeof(int));
         dev_free(c, st.d_asegs, st.asegs.size() * sizeof(Seg));
         dev_free(c, st.d_bsegs, st.bsegs.size() * sizeof(Seg));
         dev_free(c, st.panelA, st.panel_bytes_a);
@@ -811,8 +808,15 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
         st.panel_bytes_b = (size_t)S * st.rowsB * st.kpad * 2;
         st.exp_bytes_a = (size_t)std::max(rowsA, 1) * sizeof(int);
         st.exp_bytes_b = (size_t)std::max(st.ncolsB, 1) * sizeof(int);
-        for (size_t j = 0, pre = 0; j < st.ajobs.size(); ++j) { st.ajobs[j].vec_prefix = (int)pre; pre += st.ajobs[j].nvec; }
-        for (size_t j = 0, pre = 0; j < st.bjobs.size(); ++j) { st.bjobs[j].vec_prefix = (int)pre; pre += st.bjobs[j].nvec; }
+        st.avjob.clear(); st.bvjob.clear();
+        for (size_t j = 0, pre = 0; j < st.ajobs.size(); ++j) {
+            st.ajobs[j].vec_prefix = (int)pre; pre += st.ajobs[j].nvec;
+            st.avjob.insert(st.avjob.end(), st.ajobs[j].nvec, (int)j);
+        }
+        for (size_t j = 0, pre = 0; j < st.bjobs.size(); ++j) {
+            st.bjobs[j].vec_prefix = (int)pre; pre += st.bjobs[j].nvec;
+            st.bvjob.insert(st.bvjob.end(), st.bjobs[j].nvec, (int)j);
+        }
         if (!st.tasks.empty()) {
             rc = dev_alloc(c, (void**)&st.panelA, st.panel_bytes_a, "ozaki panels");
             if (!rc) rc = dev_alloc(c, (void**)&st.panelB, st.panel_bytes_b, "ozaki panels");
@@ -824,6 +828,8 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (!rc) rc = upload_vec(c, st.tiles, &st.d_tiles, "ozaki tiles");
             if (!rc) rc = upload_vec(c, st.ajobs, &st.d_ajobs, "ozaki slice jobs");
             if (!rc) rc = upload_vec(c, st.bjobs, &st.d_bjobs, "ozaki slice jobs");
+            if (!rc && !st.avjob.empty()) rc = upload_vec(c, st.avjob, &st.d_avjob, "ozaki slice jobs");
+            if (!rc && !st.bvjob.empty()) rc = upload_vec(c, st.bvjob, &st.d_bvjob, "ozaki slice jobs");
             if (!rc) rc = upload_vec(c, st.asegs, &st.d_asegs, "ozaki slice segments");
             if (!rc) rc = upload_vec(c, st.bsegs, &st.d_bsegs, "ozaki slice segments");
             if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, tm);
@@ -832,14 +838,14 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             st.args.tasks = st.d_tasks; st.args.tiles = st.d_tiles;
             st.args.expA = st.expA; st.args.expB = st.expB;
             st.args.rowsA = st.rowsA; st.args.rowsB = st.rowsB; st.args.status = oz.status;
-            auto mk = [&](OzSliceArgs& sa, const std::vector<OzSliceJob>& jobs, OzSliceJob* dj, Seg* ds, __nv_bfloat16* panel,
-                          int* exps, int rows) {
-                sa.jobs = dj; sa.njobs = (int)jobs.size(); sa.segs = ds; sa.panel = panel; sa.exps = exps;
+            auto mk = [&](OzSliceArgs& sa, const std::vector<OzSliceJob>& jobs, OzSliceJob* dj, const int* dv, Seg* ds,
+                          __nv_bfloat16* panel, int* exps, int rows) {
+                sa.jobs = dj; sa.vjob = dv; sa.njobs = (int)jobs.size(); sa.segs = ds; sa.panel = panel; sa.exps = exps;
                 sa.rows = rows; sa.kpad = st.kpad; sa.S = S;
                 sa.nvec_total = jobs.empty() ? 0 : jobs.back().vec_prefix + jobs.back().nvec;
             };
-            mk(st.sliceA, st.ajobs, st.d_ajobs, st.d_asegs, st.panelA, st.expA, st.rowsA);
-            mk(st.sliceB, st.bjobs, st.d_bjobs, st.d_bsegs, st.panelB, st.expB, st.rowsB);
+            mk(st.sliceA, st.ajobs, st.d_ajobs, st.d_avjob, st.d_asegs, st.panelA, st.expA, st.rowsA);
+            mk(st.sliceB, st.bjobs, st.d_bjobs, st.d_bvjob, st.d_bsegs, st.panelB, st.expB, st.rowsB);
         }
         if (!thin.tasks.empty()) {
             make_tiles(thin, kTileF64, kTileF64, kSplitK);
