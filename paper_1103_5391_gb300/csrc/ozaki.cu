@@ -514,8 +514,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                         const int st = c % NST;
                         if (!mbar_wait_ws(smem_u32(&full[st]), (c / NST) & 1, &failed)) break;
                         asm volatile("tcgen05.fence::after_thread_sync;");
-                        unsigned char* sA = smem + st * STAGE;
-                        unsigned char* sB = sA + S * ABOXW;
+                        // descriptors of the stage's first A and B boxes; every other operand is a constant
+                        // offset (16-byte units) in the 14-bit start-address field, which does not overflow
+                        const uint64_t da0 = desc_sw128(smem_u32(smem + st * STAGE));
+                        const uint64_t db0 = desc_sw128(smem_u32(smem + st * STAGE + S * ABOXW));
+                        const uint32_t tacc = tmem + (uint32_t)(buf * S * 64);
+                        const bool first = k == k0;
 #pragma unroll
                         for (int ks = 0; ks < KCH / 16; ++ks) {
 #pragma unroll
@@ -523,10 +527,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                                 const int s_lo = gg - S > 1 ? gg - S : 1, s_hi = gg - 1 < S ? gg - 1 : S;
 #pragma unroll
                                 for (int s = s_lo; s <= s_hi; ++s) {
-                                    const uint64_t da = desc_sw128(smem_u32(sA + (s - 1) * ABOXW) + ks * 32);
-                                    const uint64_t db = desc_sw128(smem_u32(sB + (gg - s - 1) * BBOX) + ks * 32);
-                                    const uint32_t accum = (k == k0 && ks == 0 && s == s_lo) ? 0u : 1u;
-                                    umma(tmem + (uint32_t)(buf * S * 64 + (gg - 2) * 64), da, db, idesc, accum);
+                                    const uint64_t da = da0 + (uint64_t)(((s - 1) * ABOXW + ks * 32) >> 4);
+                                    const uint64_t db = db0 + (uint64_t)(((gg - s - 1) * BBOX + ks * 32) >> 4);
+                                    const uint32_t accum = (first && ks == 0 && s == s_lo) ? 0u : 1u;
+                                    umma(tacc + (uint32_t)((gg - 2) * 64), da, db, idesc, accum);
                                 }
                             }
                         }
