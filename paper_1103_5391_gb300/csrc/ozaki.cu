@@ -503,8 +503,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 const OzTask task = oa.tasks[tile.task];
                 const int nrem = task.N - tile.n0;
                 const int n_t = ((nrem < TNC ? nrem : TNC) + 7) & ~7;
-                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * n_t) >> 3) << 17) |
-                                       ((uint32_t)(TMW >> 4) << 24);
+                uint32_t idesc_s[S];   // N = (S + 1 - s) 64 for A slice s (64-row B boxes; rows past 2 n_t unused)
+#pragma unroll
+                for (int s = 1; s <= S; ++s)
+                    idesc_s[s - 1] = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(((S + 1 - s) * 64) >> 3) << 17) |
+                                     ((uint32_t)(TMW >> 4) << 24);
                 for (int k0 = 0; k0 < task.kchunks && !failed; k0 += kReadoutChunks, ++b) {
                     const int buf = b & 1;
                     if (!mbar_wait_ws(smem_u32(&tempty[buf]), ((b >> 1) & 1) ^ 1, &failed)) break;
@@ -520,18 +523,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                         const uint64_t db0 = desc_sw128(smem_u32(smem + st * STAGE + S * ABOXW));
                         const uint32_t tacc = tmem + (uint32_t)(buf * S * 64);
                         const bool first = k == k0;
+                        // A slice s times the adjacent B slices t = 1 .. S + 1 - s in one MMA of
+                        // N = (S + 1 - s) 64: box t lands in columns (s - 1 + t - 1) 64 .., the region of
+                        // group g = s + t; the s = 1 MMA spans every group, so it alone starts a block
 #pragma unroll
                         for (int ks = 0; ks < KCH / 16; ++ks) {
 #pragma unroll
-                            for (int gg = 2; gg <= S + 1; ++gg) {
-                                const int s_lo = gg - S > 1 ? gg - S : 1, s_hi = gg - 1 < S ? gg - 1 : S;
-#pragma unroll
-                                for (int s = s_lo; s <= s_hi; ++s) {
-                                    const uint64_t da = da0 + (uint64_t)(((s - 1) * ABOXW + ks * 32) >> 4);
-                                    const uint64_t db = db0 + (uint64_t)(((gg - s - 1) * BBOX + ks * 32) >> 4);
-                                    const uint32_t accum = (first && ks == 0 && s == s_lo) ? 0u : 1u;
-                                    umma(tacc + (uint32_t)((gg - 2) * 64), da, db, idesc, accum);
-                                }
+                            for (int s = 1; s <= S; ++s) {
+                                const uint64_t da = da0 + (uint64_t)(((s - 1) * ABOXW + ks * 32) >> 4);
+                                const uint64_t db = db0 + (uint64_t)((ks * 32) >> 4);
+                                const uint32_t accum = (first && ks == 0 && s == 1) ? 0u : 1u;
+                                umma(tacc + (uint32_t)((s - 1) * 64), da, db, idesc_s[s - 1], accum);
                             }
                         }
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
