@@ -101,6 +101,7 @@ struct OzGemmArgs {
     const int* expB;
     int rowsA, rowsB;
     int* status;
+    unsigned* sched;   // work queue of the persistent kernel: [0] next tile, [1] finished CTAs (zero between launches)
 };
 struct OzStage {
     std::vector<OzTask> tasks;
@@ -122,6 +123,8 @@ struct OzStage {
     int* expB = nullptr;
     size_t panel_bytes_a = 0, panel_bytes_b = 0, exp_bytes_a = 0, exp_bytes_b = 0;
     int rowsA = 0, rowsB = 0, kpad = 0, ncolsB = 0;
+    unsigned* d_sched = nullptr;
+    int queue = 0;   // tile schedule of the persistent kernel: 0 static, 1 work queue (chosen by timing)
     CUtensorMap mapA, mapB;
     OzSliceArgs sliceA{}, sliceB{};
     OzGemmArgs args{};

@@ -412,8 +412,11 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
 }
 
 // ---- warp-specialised persistent variant (S <= 4) -------------------------------------------------
-// One CTA per SM walks the tile list (tile = blockIdx.x, + gridDim.x, ...).  Warp 0 issues the TMA
-// loads into NST shared-memory stages, one thread of warp 1 issues the MMAs (M = 64: the M = 64 data
+// One CTA per SM walks the tile list (sorted longest first) in one of two schedules, chosen per stage
+// by timing when the plan is built (both give bit-identical results: the accumulation is exact):
+// static (tile blockIdx.x + i gridDim.x) or a device work queue (the producer thread claims the next
+// index with an atomic, one tile ahead, and passes it to the MMA thread and the epilogue warps through
+// a small ring in shared memory).  Warp 0 issues the TMA loads into NST shared-memory stages, one thread of warp 1 issues the MMAs (M = 64: the M = 64 data
 // path puts row i in TMEM lane 32 (i / 16) + i % 16), warps 2..17 drain the TMEM accumulators, four
 // warps per lane quarter each taking 16 of the 64 accumulator columns.  Accumulation blocks (<= 8 chunks of one tile) alternate between two TMEM
 // buffers, so the epilogue of one block overlaps the MMAs of the next.  Hand-offs:
@@ -424,6 +427,7 @@ constexpr int ABOXW = TMW * KCH * 2;       // bytes of one A slice box (8 KB)
 constexpr int NST = 3;                     // shared-memory stages of S x (8 + 8) KB
 constexpr int EPIW = 16;                   // epilogue warps: four per TMEM lane quarter, 16 accumulator columns each
 constexpr int WS_THREADS = 64 + 32 * EPIW;
+constexpr int RT = 4;                      // tile-index ring between the producer and the consumers
 constexpr long kWaitWS = 1L << 22;
 
 __device__ __forceinline__ bool mbar_wait_ws(uint32_t bar, uint32_t parity, volatile int* failed) {
@@ -438,17 +442,25 @@ __device__ __forceinline__ bool mbar_wait_ws(uint32_t bar, uint32_t parity, vola
     return false;
 }
 
+// i-th tile of this CTA under static scheduling: blockIdx.x + i gridDim.x over the longest-first list
+__device__ __forceinline__ int static_tile(uint32_t i, int ntiles, volatile int& failed) {
+    const int64_t t = (int64_t)blockIdx.x + (int64_t)i * gridDim.x;
+    return (t < ntiles && !failed) ? (int)t : -1;
+}
+
 template <int S>
 __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa,
-                                                          GemmArgs g, int ntiles, const int* skip_flag, int skip_step) {
+                                                          GemmArgs g, int ntiles, int queue, const int* skip_flag,
+                                                          int skip_step) {
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     static_assert(S <= 4, "two TMEM buffers of S x 64 columns must fit in 512");
     constexpr uint32_t NCOLS = 512;
     constexpr uint32_t STAGE = S * (ABOXW + BBOX);
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2], rfull[RT], rempty[RT];
+    __shared__ volatile int ring[RT];
     __shared__ int sExp[EPIW][16];   // column exponents of the epilogue warps' current tile
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
@@ -462,6 +474,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&tfull[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&tempty[i])), "r"(EPIW));
+        }
+        for (int i = 0; i < RT; ++i) {   // ring slot: written by the producer, read by the MMA thread and EPIW warps
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&rfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&rempty[i])), "r"(1 + EPIW));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -477,7 +493,20 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
     if (warp == 0) {
         if (lane == 0) {   // ---------------------------------------------------------------- TMA producer
             uint32_t c = 0;
-            for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+            int next = queue ? (int)atomicAdd(oa.sched, 1u) : 0;   // claimed one tile ahead
+            for (uint32_t i = 0;; ++i) {
+                int t;
+                if (queue) {
+                    const int slot = i % RT;
+                    if (!mbar_wait_ws(smem_u32(&rempty[slot]), ((i / RT) & 1) ^ 1, &failed)) break;
+                    t = (next < ntiles && !failed) ? next : -1;
+                    ring[slot] = t;
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&rfull[slot])) : "memory");
+                    if (t >= 0) next = (int)atomicAdd(oa.sched, 1u);
+                } else {
+                    t = static_tile(i, ntiles, failed);
+                }
+                if (t < 0) break;
                 const OzTile tile = oa.tiles[t];
                 const OzTask task = oa.tasks[tile.task];
                 const int ya = task.arow0 + tile.m0, yb = task.brow0 + 2 * tile.n0;
@@ -498,11 +527,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
     } else if (warp == 1) {
         if (lane == 0) {   // ---------------------------------------------------------------- MMA issuer
             uint32_t c = 0, b = 0;
-            for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+            for (uint32_t i = 0;; ++i) {
+                int t;
+                if (queue) {
+                    const int slot = i % RT;
+                    if (!mbar_wait_ws(smem_u32(&rfull[slot]), (i / RT) & 1, &failed)) break;
+                    t = ring[slot];
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&rempty[slot])) : "memory");
+                } else {
+                    t = static_tile(i, ntiles, failed);
+                }
+                if (t < 0) break;
                 const OzTile tile = oa.tiles[t];
                 const OzTask task = oa.tasks[tile.task];
-                const int nrem = task.N - tile.n0;
-                const int n_t = ((nrem < TNC ? nrem : TNC) + 7) & ~7;
                 uint32_t idesc_s[S];   // N = (S + 1 - s) 64 for A slice s (64-row B boxes; rows past 2 n_t unused)
 #pragma unroll
                 for (int s = 1; s <= S; ++s)
@@ -549,7 +586,18 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
         const int part = (warp - 2) >> 2;     // accumulator columns 16 * part .. 16 * part + 15
         const int row = 16 * quad + lane;     // valid for lane < 16
         uint32_t b = 0;
-        for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+        for (uint32_t i = 0;; ++i) {
+            int t;
+            if (queue) {
+                const int slot = i % RT;
+                if (!__all_sync(0xffffffffu, mbar_wait_ws(smem_u32(&rfull[slot]), (i / RT) & 1, &failed))) break;
+                t = ring[slot];
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&rempty[slot])) : "memory");
+            } else {
+                t = __shfl_sync(0xffffffffu, static_tile(i, ntiles, failed), 0);
+            }
+            if (t < 0) break;
             const OzTile tile = oa.tiles[t];
             const OzTask task = oa.tasks[tile.task];
             const int nrem = task.N - tile.n0;
@@ -621,6 +669,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
     }
     __syncthreads();
     if (failed && tid == 0) atomicOr(oa.status, 1);
+    if (queue && tid == 0 && atomicAdd(oa.sched + 1, 1u) == gridDim.x - 1) {   // every CTA has stopped claiming tiles
+        oa.sched[0] = 0;
+        oa.sched[1] = 0;
+    }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOLS));
 }
@@ -670,7 +722,8 @@ cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, co
         const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
         const int ntiles = (int)st.tiles.size();
         const int grid = std::max(1, std::min(ntiles, g_num_sms));
-        k_ozaki_gemm_ws<S><<<grid, WS_THREADS, smem, s>>>(st.mapA, st.mapB, st.args, g, ntiles, skip_flag, skip_step);
+        k_ozaki_gemm_ws<S><<<grid, WS_THREADS, smem, s>>>(st.mapA, st.mapB, st.args, g, ntiles, st.queue, skip_flag,
+                                                           skip_step);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
@@ -717,10 +770,61 @@ void release_oz(tdmrg_ctx* c, OzPlan& oz) {
         dev_free(c, st.panelB, st.panel_bytes_b);
         dev_free(c, st.expA, st.exp_bytes_a);
         dev_free(c, st.expB, st.exp_bytes_b);
+        dev_free(c, st.d_sched, 2 * sizeof(unsigned));
         st = OzStage();
     }
     oz.status = nullptr;   // owned by the context
     oz.ready = false;
+}
+
+// Tile schedule of each stage by timing (the autotuner of the grouped launch): the persistent kernel
+// runs once per candidate on temporary input and output buffers (its time does not depend on the
+// values), and the static schedule is kept unless the work queue is at least 3% faster.  Every
+// schedule computes the same exact integer sums, so the choice never changes a result.
+static int autotune_oz(tdmrg_ctx* c, Plan* p) {
+    OzPlan& oz = p->oz;
+    if (oz.S > 4) return TDMRG_OK;   // only the persistent kernel has schedules
+    cplx *tin = nullptr, *tout = nullptr;
+    const size_t bin = (size_t)std::max<int64_t>(p->n_in, 1) * sizeof(cplx), bout = (size_t)std::max<int64_t>(p->n_out, 1) * sizeof(cplx);
+    int rc = dev_alloc(c, (void**)&tin, bin, "autotuning buffers");
+    if (!rc) rc = dev_alloc(c, (void**)&tout, bout, "autotuning buffers");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc) rc = cuda_check(c, cudaEventCreate(&e0), "autotuning events");
+    if (!rc) rc = cuda_check(c, cudaEventCreate(&e1), "autotuning events");
+    GemmArgs g{};
+    g.bufs[BUF_OPS] = c->pool;
+    g.bufs[BUF_IN] = tin;
+    g.bufs[BUF_SCRATCH] = c->scratch;
+    g.bufs[BUF_OUT] = tout;
+    g.dscale = c->dscale;
+    auto launch = [&](const OzStage& st) {
+        switch (oz.S) {
+            case 2: return gemm_launch<2>(st, g, c->stream, nullptr, 0);
+            case 3: return gemm_launch<3>(st, g, c->stream, nullptr, 0);
+            default: return gemm_launch<4>(st, g, c->stream, nullptr, 0);
+        }
+    };
+    for (int stg = 0; stg < 2 && !rc; ++stg) {
+        OzStage& st = oz.st[stg];
+        if (st.tasks.empty()) continue;
+        float ms[2] = {0.f, 0.f};
+        for (int q = 0; q < 2 && !rc; ++q) {
+            st.queue = q;
+            cudaError_t e = launch(st);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch(st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[q], e0, e1);
+            rc = cuda_check(c, e, "autotuning");
+        }
+        st.queue = (!rc && ms[1] < 0.97f * ms[0]) ? 1 : 0;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(c, tin, bin);
+    dev_free(c, tout, bout);
+    return rc;
 }
 
 // Build the tensor-core form of the two stages of a plan.  Tasks that the tensor path does not take
@@ -836,6 +940,8 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (!rc) rc = upload_vec(c, st.bjobs, &st.d_bjobs, "ozaki slice jobs");
             if (!rc && !st.avjob.empty()) rc = upload_vec(c, st.avjob, &st.d_avjob, "ozaki slice jobs");
             if (!rc && !st.bvjob.empty()) rc = upload_vec(c, st.bvjob, &st.d_bvjob, "ozaki slice jobs");
+            if (!rc) rc = dev_alloc(c, (void**)&st.d_sched, 2 * sizeof(unsigned), "ozaki work queue");
+            if (!rc) rc = cuda_check(c, cudaMemset(st.d_sched, 0, 2 * sizeof(unsigned)), "ozaki work queue");
             if (!rc) rc = upload_vec(c, st.asegs, &st.d_asegs, "ozaki slice segments");
             if (!rc) rc = upload_vec(c, st.bsegs, &st.d_bsegs, "ozaki slice segments");
             if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, tm);
@@ -844,6 +950,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             st.args.tasks = st.d_tasks; st.args.tiles = st.d_tiles;
             st.args.expA = st.expA; st.args.expB = st.expB;
             st.args.rowsA = st.rowsA; st.args.rowsB = st.rowsB; st.args.status = oz.status;
+            st.args.sched = st.d_sched;
             auto mk = [&](OzSliceArgs& sa, const std::vector<OzSliceJob>& jobs, OzSliceJob* dj, const int* dv, Seg* ds,
                           __nv_bfloat16* panel, int* exps, int rows) {
                 sa.jobs = dj; sa.vjob = dv; sa.njobs = (int)jobs.size(); sa.segs = ds; sa.panel = panel; sa.exps = exps;
@@ -877,8 +984,11 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
         rc = cuda_check(c, slice_launch(oz.st[1].sliceA, g, c->stream, nullptr, 0), "ozaki static slices");
         if (rc) return rc;
     }
+    rc = cuda_check(c, cudaStreamSynchronize(c->stream), "ozaki static slices");
+    if (!rc) rc = autotune_oz(c, p);
+    if (rc) return rc;
     oz.ready = true;
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "ozaki static slices");
+    return TDMRG_OK;
 }
 
 int run_oz(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* skip_flag, int skip_step) {
