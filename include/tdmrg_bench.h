@@ -24,6 +24,13 @@ int tdmrg_hpsi_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
  * tiles, slice pairs and K chunks, padding included); 0 when the context runs FP64. */
 int tdmrg_hpsi_tensor_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
 
+/* Tile schedule of the persistent tensor-core kernel for plans built from now on (existing plans are
+ * dropped and rebuilt on their next use): -1 chosen per GEMM stage by timing when the plan is built
+ * (the default), 0 static (CTA b takes tiles b, b + grid, ... of the longest-first list), 1 a device
+ * work queue.  Every schedule computes the same exact integer sums, so results are bit-identical.
+ * Errors: EINVAL (mode outside -1..1). */
+int tdmrg_set_schedule(tdmrg_ctx* ctx, int mode);
+
 /* Sustained FP64 throughput of this device, measured by timing (CUDA events) a register-resident
  * loop of the FP64 tensor MMA (mma.sync m8n8k4 f64) and of scalar DFMA on every SM.  Synchronises
  * the device; takes well under a second.  Results in TFLOP/s. */

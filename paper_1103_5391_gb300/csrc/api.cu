@@ -5,6 +5,7 @@
 #include <new>
 
 #include "internal.h"
+#include "tdmrg_bench.h"
 
 using namespace tdmrg;
 
@@ -459,6 +460,15 @@ int tdmrg_hpsi_flops(tdmrg_ctx* c, int a, int b, double* flops) {
     int rc = get_plan(c, 0, -1, -1, a, b, a, b, &p);
     if (rc) return rc;
     *flops = p->flops;
+    return TDMRG_OK;
+}
+
+int tdmrg_set_schedule(tdmrg_ctx* c, int mode) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (mode < -1 || mode > 1) return fail(c, TDMRG_EINVAL, "set_schedule: mode must be -1, 0 or 1");
+    DeviceGuard g(c->opts.device);
+    c->schedule = mode;
+    drop_plans(c);   // plans are rebuilt with the new schedule on their next use
     return TDMRG_OK;
 }
 

@@ -237,6 +237,7 @@ struct tdmrg_ctx {
     size_t allocated = 0;
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
+    int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue
     int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
     tdmrg::EigWork eig;
 };

@@ -784,6 +784,10 @@ void release_oz(tdmrg_ctx* c, OzPlan& oz) {
 static int autotune_oz(tdmrg_ctx* c, Plan* p) {
     OzPlan& oz = p->oz;
     if (oz.S > 4) return TDMRG_OK;   // only the persistent kernel has schedules
+    if (c->schedule >= 0) {          // fixed by tdmrg_set_schedule
+        for (OzStage& st : oz.st) st.queue = c->schedule;
+        return TDMRG_OK;
+    }
     cplx *tin = nullptr, *tout = nullptr;
     const size_t bin = (size_t)std::max<int64_t>(p->n_in, 1) * sizeof(cplx), bout = (size_t)std::max<int64_t>(p->n_out, 1) * sizeof(cplx);
     int rc = dev_alloc(c, (void**)&tin, bin, "autotuning buffers");

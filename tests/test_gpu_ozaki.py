@@ -52,6 +52,37 @@ def test_ozaki_hpsi(lib, slices, L, m, nb, seed):
         lib.tdmrg_destroy(ctx)
 
 
+@pytest.mark.parametrize("L,m,nb,seed", [(8, 24, 2, 3), (32, 400, 1, S.SEED_BASE + 1)])
+def test_ozaki_schedules_bit_identical(lib, L, m, nb, seed):
+    """The persistent tensor kernel (S <= 4) gives the same bits under the static tile schedule,
+    the device work queue (run three times, so the queue counters must have been reset by each
+    launch) and the autotuned choice, and that result meets the oracle bound."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(L, m, 4.0, nbonds=nb, seed=seed)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=4)
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = lib.tdmrg_sector_size(ctx, ss.Q1)
+        x = _rand(n, 6)
+        xd = dev(x)
+        outs = []
+        for mode, reps in ((0, 1), (1, 3), (-1, 1)):
+            lib.tdmrg_set_schedule(ctx, mode)
+            for _ in range(reps):
+                out = dev(np.full(n, np.nan + 0j))
+                lib.tdmrg_apply_h(ctx, ss.Q1, xd, out)
+                outs.append(host(out))
+        for o in outs[1:]:
+            assert np.array_equal(o.view(np.float64), outs[0].view(np.float64))
+        ref = superblock.apply_h(sb, HL, HR, conns, ss.Q1, x)
+        assert rel_err(outs[0], ref) < _tol(4, 5 * max(ss.ldim) * (1 + 2 * nb))
+        with pytest.raises(lib.TdmrgError):
+            lib.tdmrg_set_schedule(ctx, 2)
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
 def test_ozaki_error_decreases_with_slices(lib):
     from paper_1103_5391_gb300 import problem
     ss = S.make_synthetic(16, 120, 4.0, nbonds=1, seed=17)
