@@ -10,9 +10,10 @@
 //         E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta,
 //         E_ij = R_ij / 2 otherwise (and on the diagonal),  delta = 2 (||S - diag(lambda)|| + ||rho|| ||R||),
 //         X <- X (I + E);
-//      convergence is quadratic; three iterations take the FP32 seed to FP64 accuracy, including
-//      near-degenerate pairs that the first iteration treats as a cluster.  The iterate is kept as
-//      W = X^H, so every product is a plain or conjugate-transposed GEMM operand;
+//      convergence is quadratic: from the FP32 seed (error ~1e-5) two iterations reach rounding level;
+//      a third and a fourth run (decided on the device, launched regardless) while the last correction
+//      is above 1e-7, as for near-degenerate pairs that the first iteration treats as a cluster.  The
+//      iterate is kept as W = X^H, so every product is a plain or conjugate-transposed GEMM operand;
 //   3. sort each sector's eigenpairs by descending eigenvalue.
 #include <algorithm>
 #include <cmath>
@@ -24,12 +25,17 @@ namespace tdmrg {
 namespace {
 
 constexpr int JT = 1024;  // threads of the FP32 Jacobi CTA (warps over rotation pairs, lanes over rows)
-constexpr int kSmemMaxN = 112;
+constexpr int kSmemMaxN = 112;   // A and V as float2 in shared memory: 2 * 112 * 113 * 8 B = 198 KB
+constexpr int kJacSmemCap = 225 * 1024;   // dynamic shared memory of the Jacobi CTA at most
 constexpr int kMaxEigN = 512;    // largest sector dimension
 constexpr int kKChunk = 16;      // K chunk of the refinement GEMMs
-constexpr int kRefine = 3;       // refinement iterations always run
-constexpr int kMaxRefine = 4;    // one more when the last correction was not yet at rounding level
-constexpr double kTolE = 1e-7;   // |E| above this: the next error (~|E|^2) may exceed ~1e-14       // refinement iterations   // A and V as float2 in shared memory: 2 * 112^2 * 8 B = 196 KB
+constexpr int kRefine = 2;       // refinement iterations always run
+constexpr int kMaxRefine = 6;    // more, each only when the previous correction was not yet small
+constexpr float kReseedTol = 1e-7f;    // re-seed rotates (p, q) while |S_pq| > kReseedTol sqrt|S_pp S_qq| ...
+constexpr float kReseedFloor = 1e-14f; // ... and |S_pq| > kReseedFloor ||rho||_F
+// Refinement iterations that may re-seed a sector instead of updating it.
+__host__ __device__ constexpr bool reseed_iter(int it) { return it == 1 || it == 3; }
+constexpr double kTolE = 1e-7;   // |E| above this: the next error (~|E|^2) may exceed ~1e-14
 
 struct EigTables {
     const int64_t* off;   // per sector: offset of its n x n block
@@ -58,88 +64,181 @@ __device__ __forceinline__ void rotation32(float a, float d, float2 b, float& c,
     s.x *= f; s.y *= f;
 }
 
-// Cyclic Jacobi sweeps on A (n x n, row stride ld) accumulating V; A and V are either in shared memory
-// or in global memory, and this body is inlined once for each so that shared accesses compile as such.
-__device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, float thr, int* pp, int* qq,
-                                              float* cs, float2* sn) {
-    const int tid = threadIdx.x;
-    const float thr2 = thr * thr;
+// Round-robin pairing of round `round`: pair i of P / 2 disjoint index pairs (p < q); index P - 1 = n
+// is a dummy when n is odd.
+__device__ __forceinline__ void rr_pair(int round, int i, int P, int& p, int& q) {
+    if (i == 0) { p = P - 1; q = round; }
+    else {   // (round + i) and (round - i) mod P - 1, with 0 <= round < P - 1 and 0 < i < P / 2
+        p = round + i; if (p >= P - 1) p -= P - 1;
+        q = round - i; if (q < 0) q += P - 1;
+    }
+    if (p > q) { int t = p; p = q; q = t; }
+}
+
+// A is Hermitian and only its lower triangle (i >= j) is stored.
+__device__ __forceinline__ float2 lget(const float2* A, int ld, int i, int j) {
+    const bool lo = i >= j;
+    const float2 v = A[lo ? i * ld + j : j * ld + i];
+    return lo ? v : conjf2(v);
+}
+__device__ __forceinline__ void lput(float2* A, int ld, int i, int j, float2 v) {
+    if (i >= j) A[i * ld + j] = v;
+    else A[j * ld + i] = conjf2(v);
+}
+__device__ __forceinline__ float2 rot_l(float c, float2 s, float2 x, float2 y) {   // c x - s y
+    const float2 t = cmf(s, y);
+    return make_float2(c * x.x - t.x, c * x.y - t.y);
+}
+__device__ __forceinline__ float2 rot_r(float c, float2 s, float2 x, float2 y) {   // s x + c y
+    const float2 t = cmf(s, x);
+    return make_float2(t.x + c * y.x, t.y + c * y.y);
+}
+
+constexpr int JA = 512;   // threads that rotate A (warps 0-15); the other 16 warps accumulate V
+
+// Rounds of the rotation record that fit in `smem` bytes beside A and V (two buffers of float4 per pair).
+__host__ __device__ inline int jac_base_bytes(int n) { return n <= kSmemMaxN ? 16 * n * (n | 1) : 0; }
+__host__ __device__ inline int jac_chunk(int n, int smem) {
+    const int P = n + (n & 1), R = P - 1, npair = P / 2;
+    if (npair == 0) return 1;
+    const int c = (smem - jac_base_bytes(n)) / (32 * npair);
+    return c < R ? c : R;
+}
+
+// V <- V J_r for the recorded rounds r0 .. r0 + nr - 1 (V group: warps over pairs, lanes over rows, so a
+// warp's accesses to a column of V fall in distinct banks; a V-group barrier separates the rounds).
+__device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int ld, const float4* rec, int nr, int r0) {
     const int P = n + (n & 1), npair = P / 2;
-    for (int sweep = 0; sweep < 12 && n > 1; ++sweep) {
-        for (int round = 0; round < P - 1; ++round) {
-            for (int i = tid; i < npair; i += JT) {
-                int p, q;
-                if (i == 0) { p = P - 1; q = round; }
-                else {   // (round + i) and (round - i) mod P - 1, with 0 <= round < P - 1 and 0 < i < P / 2
-                    p = round + i; if (p >= P - 1) p -= P - 1;
-                    q = round - i; if (q < 0) q += P - 1;
-                }
-                if (p > q) { int t = p; p = q; q = t; }
-                float c = 1.f;
-                float2 s = make_float2(0.f, 0.f);
-                if (q < n) {
-                    const float2 b = A[p * ld + q];
-                    if (fmaf(b.x, b.x, b.y * b.y) <= thr2) {
-                        A[p * ld + q] = make_float2(0.f, 0.f);
-                        A[q * ld + p] = make_float2(0.f, 0.f);
-                    } else {
-                        rotation32(A[p * ld + p].x, A[q * ld + q].x, b, c, s);
-                    }
-                }
-                pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
-            }
-            __syncthreads();
-            const int warp = tid >> 5, lane = tid & 31;
-            for (int i = warp; i < npair; i += JT / 32) {   // rows: A <- J^H A
-                const int p = pp[i], q = qq[i];
-                if (q >= n || (sn[i].x == 0.f && sn[i].y == 0.f)) continue;   // identity: nothing to rotate
-                const float c = cs[i];
-                const float2 s = sn[i], sc = conjf2(s);
-                for (int k = lane; k < n; k += 32) {
-                    const float2 ap = A[p * ld + k], aq = A[q * ld + k];
-                    const float2 t1 = cmf(s, aq), t2 = cmf(sc, ap);
-                    A[p * ld + k] = make_float2(c * ap.x - t1.x, c * ap.y - t1.y);
-                    A[q * ld + k] = make_float2(t2.x + c * aq.x, t2.y + c * aq.y);
-                }
-            }
-            __syncthreads();
-            for (int i = warp; i < npair; i += JT / 32) {   // columns: A <- A J, V <- V J
-                const int p = pp[i], q = qq[i];
-                if (q >= n || (sn[i].x == 0.f && sn[i].y == 0.f)) continue;   // identity: nothing to rotate
-                const float c = cs[i];
-                const float2 s = sn[i], sc = conjf2(s);
-                for (int k = lane; k < n; k += 32) {
-                    float2 xp = A[k * ld + p], xq = A[k * ld + q];
-                    const float2 vp = V[k * ld + p], vq = V[k * ld + q];
-                    float2 t1 = cmf(sc, xq), t2 = cmf(s, xp);
-                    A[k * ld + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
-                    A[k * ld + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
-                    xp = vp; xq = vq;
-                    t1 = cmf(sc, xq); t2 = cmf(s, xp);
-                    V[k * ld + p] = make_float2(c * xp.x - t1.x, c * xp.y - t1.y);
-                    V[k * ld + q] = make_float2(t2.x + c * xq.x, t2.y + c * xq.y);
-                }
-            }
-            __syncthreads();
-        }
-        // the next sweep rotates only pairs above the threshold: stop when there are none
-        bool above = false;
-        for (int e = tid; e < n * n; e += JT) {
-            const int r = e / n, cc = e % n;
-            if (r < cc) {
-                const float2 b = A[r * ld + cc];
-                above |= fmaf(b.x, b.x, b.y * b.y) > thr2;
+    const int lane = threadIdx.x & 31, vw = (threadIdx.x - JA) >> 5;
+    constexpr int NVW = (JT - JA) / 32;
+    for (int r = 0; r < nr; ++r) {
+        for (int i = vw; i < npair; i += NVW) {
+            const float4 ro = rec[r * npair + i];
+            if (ro.y == 0.f && ro.z == 0.f) continue;   // identity
+            int p, q;
+            rr_pair(r0 + r, i, P, p, q);
+            const float c = ro.x;
+            const float2 s = make_float2(ro.y, ro.z), sc = conjf2(s);
+            for (int k = lane; k < n; k += 32) {
+                const float2 vp = V[k * ld + p], vq = V[k * ld + q];
+                V[k * ld + p] = rot_l(c, sc, vp, vq);
+                V[k * ld + q] = rot_r(c, s, vp, vq);
             }
         }
-        if (!__syncthreads_or(above)) break;
+        asm volatile("bar.sync 2, %0;" ::"r"(JT - JA) : "memory");
     }
 }
 
-__device__ __forceinline__ void jacobi_load(const cplx* R, float2* A, float2* V, int n, int ld) {
+// Cyclic two-sided Jacobi on the lower triangle of A (n x n, row stride ld), eigenvectors accumulated in
+// V, both either in shared or in global memory (the body is inlined once for each so that shared
+// accesses compile as such).  Each round: threads of the A group compute the rotations of the round's
+// disjoint pairs and record them; after a barrier of the A group, each 2 x 2 block (pair a, pair b <= a)
+// of A is rotated on both sides at once, A <- J^H A J, and written back to the lower triangle.  The V
+// group replays the record of the previous chunk of rounds on V meanwhile; record buffers swap at a
+// barrier of all threads every `C` rounds.
+//
+// Criterion: (p, q) is rotated while |A_pq|^2 > lim, lim = thr^2 for the seed, and for the re-seed
+// (`rel`) lim = max(kReseedTol^2 |A_pp A_qq|, floor^2), relative to the pair's own diagonal.
+__device__ __forceinline__ float jac_lim(bool rel, float thr2, float a, float d) {
+    return rel ? fmaxf(kReseedTol * kReseedTol * fabsf(a * d), thr2) : thr2;
+}
+__device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, float thr, bool rel, float4* rec, int C) {
+    const int tid = threadIdx.x;
+    const bool agroup = tid < JA;
+    const float thr2 = thr * thr;
+    const int P = n + (n & 1), npair = P / 2, R = P - 1;
+    const int warp = tid >> 5, lane = tid & 31;
+    int pend = 0, pend_r0 = 0, buf = 0;
+    bool done = n <= 1;
+    for (int sweep = 0; sweep < 12 && !done; ++sweep) {
+        for (int r0 = 0; r0 < R; r0 += C) {
+            const int nr = min(C, R - r0);
+            const bool last = r0 + nr >= R;
+            float4* cur = rec + (size_t)buf * C * npair;
+            bool above = false;
+            if (agroup) {
+                for (int r = 0; r < nr; ++r) {
+                    const int round = r0 + r;
+                    float4* rr = cur + r * npair;
+                    for (int i = tid; i < npair; i += JA) {
+                        int p, q;
+                        rr_pair(round, i, P, p, q);
+                        float c = 1.f;
+                        float2 s = make_float2(0.f, 0.f);
+                        if (q < n) {
+                            const float2 b = conjf2(A[q * ld + p]);
+                            const float ap = A[p * ld + p].x, aq = A[q * ld + q].x;
+                            if (fmaf(b.x, b.x, b.y * b.y) <= jac_lim(rel, thr2, ap, aq)) A[q * ld + p] = make_float2(0.f, 0.f);
+                            else rotation32(ap, aq, b, c, s);
+                        }
+                        rr[i] = make_float4(c, s.x, s.y, 0.f);
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"r"(JA) : "memory");
+                    // warp task j: block row a = j (blocks b = 0 .. a) followed by block row npair - 1 - j
+                    // (blocks 0 .. npair - 1 - j): npair + 1 blocks, lanes over them
+                    for (int j = warp; j < (npair + 1) / 2; j += JA / 32) {
+                        for (int l = lane; l < npair + 1; l += 32) {
+                            int a = j, b = l;
+                            if (l > j) { a = npair - 1 - j; b = l - j - 1; }
+                            if (a == j && l > j) continue;   // odd npair: the middle row is taken once
+                            const float4 ra = rr[a], rb = rr[b];
+                            if (ra.y == 0.f && ra.z == 0.f && rb.y == 0.f && rb.z == 0.f) continue;   // both identity
+                            int pa, qa, pb, qb;
+                            rr_pair(round, a, P, pa, qa);
+                            rr_pair(round, b, P, pb, qb);
+                            const bool va = qa < n, vb = qb < n;
+                            const float2 z2 = make_float2(0.f, 0.f);
+                            const float2 x00 = lget(A, ld, pa, pb);
+                            const float2 x01 = vb ? lget(A, ld, pa, qb) : z2;
+                            const float2 x10 = va ? lget(A, ld, qa, pb) : z2;
+                            const float2 x11 = va && vb ? lget(A, ld, qa, qb) : z2;
+                            const float ca = ra.x, cb = rb.x;
+                            const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
+                            const float2 sac = conjf2(sa), sbc = conjf2(sb);
+                            // rows: J_a^H X;  columns: (J_a^H X) J_b
+                            const float2 y00 = rot_l(ca, sa, x00, x10), y01 = rot_l(ca, sa, x01, x11);
+                            const float2 y10 = rot_r(ca, sac, x00, x10), y11 = rot_r(ca, sac, x01, x11);
+                            const float2 z00 = rot_l(cb, sbc, y00, y01), z01 = rot_r(cb, sb, y00, y01);
+                            const float2 z10 = rot_l(cb, sbc, y10, y11), z11 = rot_r(cb, sb, y10, y11);
+                            if (a != b) {
+                                lput(A, ld, pa, pb, z00);
+                                if (vb) lput(A, ld, pa, qb, z01);
+                                if (va) lput(A, ld, qa, pb, z10);
+                                if (va && vb) lput(A, ld, qa, qb, z11);
+                            } else {
+                                A[pa * ld + pa] = z00;
+                                if (va) { A[qa * ld + pa] = z10; A[qa * ld + qa] = z11; }
+                            }
+                        }
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"r"(JA) : "memory");
+                }
+                if (last) {   // the next sweep rotates only pairs above the threshold: stop when there are none
+                    for (int e = tid; e < n * n; e += JA) {
+                        const int r = e / n, cc = e % n;
+                        if (r > cc) {
+                            const float2 b = A[r * ld + cc];
+                            above |= fmaf(b.x, b.x, b.y * b.y) > jac_lim(rel, thr2, A[r * ld + r].x, A[cc * ld + cc].x);
+                        }
+                    }
+                }
+            } else if (pend) {
+                jacobi_apply_v(V, n, ld, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
+            }
+            const int any = __syncthreads_or(above);
+            pend = nr; pend_r0 = r0; buf ^= 1;
+            if (last && !any) done = true;
+        }
+    }
+    if (!agroup && pend) jacobi_apply_v(V, n, ld, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void jacobi_load(const cplx* R, double scale, float2* A, float2* V, int n, int ld) {
     for (int e = threadIdx.x; e < n * n; e += JT) {
         const int r = e / n, cc = e % n;
         const double2 v = R[e];
-        A[r * ld + cc] = make_float2((float)v.x, (float)v.y);
+        A[r * ld + cc] = make_float2((float)(v.x * scale), (float)(v.y * scale));
         V[r * ld + cc] = make_float2(r == cc ? 1.f : 0.f, 0.f);
     }
 }
@@ -157,43 +256,60 @@ __device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, i
     }
 }
 
-// FP32 seed: W0 = X0^H (X0: unsorted eigenvector columns) of each sector's rho block, and ||rho||_F.
-__global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ rho, cplx* __restrict__ W,
+// FP32 Jacobi per sector.  Dynamic shared memory (`smem` bytes): A and V of sectors with n <= kSmemMaxN,
+// then the rotation record; larger sectors keep A and V in `gwork`.
+//  - seed (rel = false): src = rho; writes W0 = X0^H (X0: unsorted eigenvector columns), ||rho||_F, the
+//    initial iteration count, and clears the sector's re-seed flag;
+//  - re-seed (rel = true) in refinement iteration `it`, for sectors whose flag is set: src = S = X^H rho X
+//    scaled by 1 / ||rho||_F, so that eigenvalues far below FP32's resolution of rho are resolved relative
+//    to their own size; writes V^H (V: eigenvectors of S) over the correction dst = E1h, so that the
+//    iteration's update is W <- V^H W, and asks for two more refinements.
+__global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, cplx* __restrict__ dst,
                                                  double* __restrict__ rho_fro, int* __restrict__ n_iter,
-                                                 EigTables tb, float2* __restrict__ gwork) {
-    extern __shared__ float2 fsm[];
+                                                 int* __restrict__ flags, EigTables tb, float2* __restrict__ gwork,
+                                                 int smem, bool rel, int it) {
+    extern __shared__ float4 fsm4[];
+    float2* fsm = reinterpret_cast<float2*>(fsm4);
     const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
+    if (rel && (it >= *n_iter || flags[sct] == 0)) return;   // iteration skipped, or nothing to re-seed
     const int64_t off = tb.off[sct];
     const int ld = n | 1;   // odd row stride: column accesses of a warp hit distinct banks
     const bool in_smem = n <= kSmemMaxN;
     float2* gA = gwork + 4 * off;
     float2* gV = gA + (int64_t)n * ld;
-    __shared__ int pp[256], qq[256];
-    __shared__ float cs[256];
-    __shared__ float2 sn[256];
+    float4* rec = fsm4 + jac_base_bytes(n) / 16;
+    const int C = jac_chunk(n, smem);
     __shared__ float red[JT / 32];
     __shared__ float thr_s;
-    if (sct == 0 && tid == 0) *n_iter = kRefine;
+    const double scale = rel ? 1.0 / rho_fro[sct] : 1.0;
+    if (!rel && sct == 0 && tid == 0) *n_iter = kRefine;
     float fro;
-    if (in_smem) { jacobi_load(rho + off, fsm, fsm + n * ld, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
-    else { jacobi_load(rho + off, gA, gV, n, ld); __syncthreads(); fro = jacobi_fro2(gA, n, ld); }
+    if (in_smem) { jacobi_load(src + off, scale, fsm, fsm + n * ld, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
+    else { jacobi_load(src + off, scale, gA, gV, n, ld); __syncthreads(); fro = jacobi_fro2(gA, n, ld); }
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     if ((tid & 31) == 0) red[tid >> 5] = fro;
     __syncthreads();
     if (tid == 0) {
         float f = 0.f;
         for (int k = 0; k < JT / 32; ++k) f += red[k];
-        thr_s = 4.8e-7f * sqrtf(f);   // 4 eps_fp32 ||A||_F: above FP32 rounding noise, so sweeps terminate
-        rho_fro[sct] = sqrtf(f);      // ||rho||_F for the refinement's cluster threshold
+        if (rel) {
+            thr_s = kReseedFloor;          // S is in units of ||rho||_F
+            flags[sct] = 0;
+            atomicMax(n_iter, min(kMaxRefine, it + 3));
+        } else {
+            thr_s = 4.8e-7f * sqrtf(f);    // 4 eps_fp32 ||A||_F: above FP32 rounding noise, so sweeps terminate
+            rho_fro[sct] = sqrtf(f);       // ||rho||_F for the refinement's cluster threshold
+            flags[sct] = 0;
+        }
     }
     __syncthreads();
     const float thr = thr_s;
     if (in_smem) {
-        jacobi_sweeps(fsm, fsm + n * ld, n, ld, thr, pp, qq, cs, sn);
-        jacobi_store(fsm + n * ld, W + off, n, ld);
+        jacobi_sweeps(fsm, fsm + n * ld, n, ld, thr, rel, rec, C);
+        jacobi_store(fsm + n * ld, dst + off, n, ld);
     } else {
-        jacobi_sweeps(gA, gV, n, ld, thr, pp, qq, cs, sn);
-        jacobi_store(gV, W + off, n, ld);
+        jacobi_sweeps(gA, gV, n, ld, thr, rel, rec, C);
+        jacobi_store(gV, dst + off, n, ld);
     }
 }
 
@@ -261,7 +377,7 @@ __global__ void __launch_bounds__(256) k_oa_norms(const cplx* __restrict__ S, co
 __global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, const cplx* __restrict__ G,
                                                    const double* __restrict__ lam, const double* __restrict__ part,
                                                    const double* __restrict__ rho_fro, cplx* __restrict__ E1h,
-                                                   int* __restrict__ n_iter, int it, EigTables tb) {
+                                                   int* __restrict__ n_iter, int* __restrict__ flags, int it, EigTables tb) {
     if (it >= *n_iter) return;   // refinement already converged
     const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
     const int64_t off = tb.off[sct], eo = tb.eoff[sct];
@@ -274,7 +390,8 @@ __global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, c
         b += part[2 * ((int64_t)sct * kRowChunks + k) + 1];
     }
     const double delta = 2.0 * (sqrt(a) + rho_fro[sct] * sqrt(b));
-    bool big = false;
+    bool big = false, clus = false;
+    const double floor_s = (double)kReseedFloor * rho_fro[sct];
     for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
         const int i = r0 + e / n, j = e % n;
         const int64_t x = off + (int64_t)i * n + j;
@@ -288,13 +405,19 @@ __global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, c
             ev = make_double2((sv.x + li * r.x) * inv, (sv.y + li * r.y) * inv);
         } else {
             ev = make_double2(0.5 * r.x, 0.5 * r.y);
+            if (i != j) {   // clustered pair still coupled: the cluster is not diagonalised by this update
+                const double2 sv = S[x];
+                clus |= fmax(fabs(sv.x), fabs(sv.y)) > floor_s;
+            }
         }
         big |= fmax(fabs(ev.x), fabs(ev.y)) > kTolE;
         if (i == j) ev.x += 1.0;
         E1h[x] = ev;
     }
-    // the last iteration that always runs asks for one more if its correction was still large
-    if (it == kRefine - 1 && __syncthreads_or(big) && threadIdx.x == 0) atomicMax(n_iter, kMaxRefine);
+    // from the last iteration that always runs on, a correction still above kTolE asks for one more
+    if (it >= kRefine - 1 && it + 1 < kMaxRefine && __syncthreads_or(big) && threadIdx.x == 0) atomicMax(n_iter, it + 2);
+    // at a re-seed iteration, a cluster with coupling above the floor sends the sector to the re-seed
+    if (reseed_iter(it) && __syncthreads_or(clus) && threadIdx.x == 0) flags[sct] = 1;
 }
 
 // Order key of a double: unsigned comparison of keys is numeric comparison (-0 taken as +0).
@@ -396,9 +519,19 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
             return upload(c, tl);
         };
         // the opt-in is a property of the kernel on the device, shared by every context: always the maximum
-        rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)((size_t)2 * kSmemMaxN * (kSmemMaxN | 1) * sizeof(float2))),
-                        "eig smem");
+        if (!rc) rc = dev_alloc(c, (void**)&w.flags, (size_t)ns * sizeof(int), "eig workspace");
+        if (!rc) rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacSmemCap),
+                                 "eig smem");
+        // shared memory of the Jacobi launch: the most any sector asks for (A, V and a whole sweep of
+        // rotation records), capped; every sector then holds at least one round of records
+        int smem = 0;
+        for (int k = 0; k < ns; ++k) {
+            const int n = L.dim[k], P = n + (n & 1);
+            smem = std::max(smem, jac_base_bytes(n) + 32 * (P / 2) * (P - 1));
+        }
+        w.jac_smem = std::min(smem, kJacSmemCap);
+        for (int k = 0; k < ns && !rc; ++k)
+            if (L.dim[k] > 1 && jac_chunk(L.dim[k], w.jac_smem) < 1) rc = fail(c, TDMRG_EINVAL, "rho_eig: Jacobi shared memory");
         // S = W rho W^H and G = W W^H are Hermitian: lower tiles plus mirror
         if (!rc) rc = one(w.tl_ax, {{EB_AX, EB_RHO, EB_W, OPB_C, 0}});
         if (!rc) rc = one(w.tl_sg, {{EB_S, EB_W, EB_AX, OPB_N, 1}, {EB_G, EB_W, EB_W, OPB_C, 1}});
@@ -415,9 +548,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     cplx* E1h = w.buf + 5 * w.nrho;
     double* part = w.fro + ns;
     int* n_iter = reinterpret_cast<int*>(part + 2 * (size_t)ns * kRowChunks);
-    const int sm = std::min(w.maxn, kSmemMaxN);
-    const size_t smem = (size_t)2 * sm * (sm | 1) * sizeof(float2);
-    k_jacobi32<<<ns, JT, smem, s>>>(rho, W, w.fro, n_iter, tb, w.gwork);
+    k_jacobi32<<<ns, JT, w.jac_smem, s>>>(rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, false, 0);
     c->launches += 1;
     GemmArgs a{};
     a.dscale = c->dscale;
@@ -440,7 +571,11 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         e = gemm(w.tl_ax);
         if (e == cudaSuccess) e = gemm(w.tl_sg);
         k_oa_norms<<<chunks, 256, 0, s>>>(S, G, w.lam, part, n_iter, it, tb);
-        k_oa_update<<<chunks, 256, 0, s>>>(S, G, w.lam, part, w.fro, E1h, n_iter, it, tb);
+        k_oa_update<<<chunks, 256, 0, s>>>(S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
+        if (reseed_iter(it)) {
+            k_jacobi32<<<ns, JT, w.jac_smem, s>>>(S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, true, it);
+            c->launches++;
+        }
         if (e == cudaSuccess) e = gemm(w.tl_y);
         c->launches += 2;
         std::swap(W, Wn);
@@ -462,6 +597,7 @@ void release_eig(tdmrg_ctx* c) {
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
     dev_free(c, w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double));
     dev_free(c, w.gwork, (size_t)4 * w.nrho * sizeof(float2));
+    dev_free(c, w.flags, (size_t)ns * sizeof(int));
     w = EigWork();
 }
 

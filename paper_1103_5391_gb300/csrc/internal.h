@@ -193,6 +193,8 @@ struct EigWork {
     double* lam = nullptr;
     double* fro = nullptr;
     float2* gwork = nullptr;    // FP32 Jacobi storage for sectors too large for shared memory
+    int jac_smem = 0;           // dynamic shared memory of the Jacobi launch
+    int* flags = nullptr;       // per sector: re-seed requested by the refinement
     TaskList tl_ax, tl_sg, tl_y;
 };
 

@@ -69,6 +69,54 @@ def test_rho_and_eig(lib, L, m, nb):
         lib.tdmrg_destroy(ctx)
 
 
+@pytest.mark.parametrize("kind,orth_tol", [("mixed", 1e-11), ("graded", 1e-10)])
+def test_rho_eig_hard_spectra(lib, kind, orth_tol):
+    """rho blocks U diag(lambda) U^dag with prescribed spectra on the L=32 m=400 sector layout:
+    'mixed' has exactly degenerate pairs, pairs 1e-4 apart and a rank-deficient tail of zeros (lambda_k
+    = 0.9^k otherwise); 'graded' decays as 0.8^k, so that the smallest eigenvalues and their gaps lie
+    below FP32's resolution of rho and are found by the re-seed in the refined basis.  Eigenvalues and
+    U diag(lambda) U^dag to 1e-12 of the largest eigenvalue, U^dag U to orth_tol."""
+    from paper_1103_5391_gb300 import problem
+    torch = pytest.importorskip("torch")
+    ss = S.make_synthetic(32, 400, 4.0, nbonds=1, seed=S.SEED_BASE + 9)
+    rng = np.random.default_rng(12)
+    blocks, lams = [], []
+    for d in ss.ldim:
+        lam = (0.9 if kind == "mixed" else 0.8) ** np.arange(d)
+        if kind == "mixed":
+            lam[1::4] = lam[0::4][: len(lam[1::4])]                   # exact pairs
+            lam[3::4] = lam[2::4][: len(lam[3::4])] * (1 - 1e-4)      # pairs 1e-4 apart
+            lam[(d + 1) // 2:] = 0.0                                  # rank deficient
+        lams.append(np.sort(lam)[::-1])
+    tr = sum(l.sum() for l in lams)
+    for d, lam in zip(ss.ldim, lams):
+        lam /= tr                                                     # trace 1 over all sectors
+        q, _ = np.linalg.qr(rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d)))
+        blocks.append((q * lam) @ q.conj().T)
+    scale = max(l.max() for l in lams)
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        nr, ne = lib.tdmrg_rho_size(ctx)
+        rho = dev(np.concatenate([b.ravel() for b in blocks]))
+        ev = torch.zeros(ne, dtype=torch.float64, device="cuda")
+        U = dev(np.zeros(nr))
+        lib.tdmrg_rho_eig(ctx, rho, ev, U)
+        ev, U = ev.cpu().numpy(), host(U)
+        off = eo = 0
+        for d, lam, r in zip(ss.ldim, lams, blocks):
+            g_l = ev[eo: eo + d]
+            g_U = U[off: off + d * d].reshape(d, d)
+            assert np.all(np.diff(g_l) <= 0)
+            assert np.abs(g_l - lam).max() < 1e-12 * scale, d
+            assert np.abs(g_U @ np.diag(g_l) @ g_U.conj().T - r).max() < 1e-12 * scale, d
+            assert np.abs(g_U.conj().T @ g_U - np.eye(d)).max() < orth_tol, d
+            off += d * d
+            eo += d
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
 def test_expect(lib):
     from paper_1103_5391_gb300 import problem
     from oracle import blocks as oblocks
