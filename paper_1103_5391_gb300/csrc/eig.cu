@@ -75,16 +75,6 @@ __device__ __forceinline__ void rr_pair(int round, int i, int P, int& p, int& q)
     if (p > q) { int t = p; p = q; q = t; }
 }
 
-// A is Hermitian and only its lower triangle (i >= j) is stored.
-__device__ __forceinline__ float2 lget(const float2* A, int ld, int i, int j) {
-    const bool lo = i >= j;
-    const float2 v = A[lo ? i * ld + j : j * ld + i];
-    return lo ? v : conjf2(v);
-}
-__device__ __forceinline__ void lput(float2* A, int ld, int i, int j, float2 v) {
-    if (i >= j) A[i * ld + j] = v;
-    else A[j * ld + i] = conjf2(v);
-}
 __device__ __forceinline__ float2 rot_l(float c, float2 s, float2 x, float2 y) {   // c x - s y
     const float2 t = cmf(s, y);
     return make_float2(c * x.x - t.x, c * x.y - t.y);
@@ -115,8 +105,7 @@ __device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int ld, const f
         for (int i = vw; i < npair; i += NVW) {
             const float4 ro = rec[r * npair + i];
             if (ro.y == 0.f && ro.z == 0.f) continue;   // identity
-            int p, q;
-            rr_pair(r0 + r, i, P, p, q);
+            const int p = __float_as_int(ro.w) & 0xffff, q = __float_as_int(ro.w) >> 16;
             const float c = ro.x;
             const float2 s = make_float2(ro.y, ro.z), sc = conjf2(s);
             for (int k = lane; k < n; k += 32) {
@@ -129,11 +118,12 @@ __device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int ld, const f
     }
 }
 
-// Cyclic two-sided Jacobi on the lower triangle of A (n x n, row stride ld), eigenvectors accumulated in
+// Cyclic two-sided Jacobi on the Hermitian A (n x n, row stride ld), eigenvectors accumulated in
 // V, both either in shared or in global memory (the body is inlined once for each so that shared
 // accesses compile as such).  Each round: threads of the A group compute the rotations of the round's
-// disjoint pairs and record them; after a barrier of the A group, each 2 x 2 block (pair a, pair b <= a)
-// of A is rotated on both sides at once, A <- J^H A J, and written back to the lower triangle.  The V
+// disjoint pairs and record them (with the pair's indices); after a barrier of the A group, each 2 x 2
+// block (pair a, pair b <= a) of A is rotated on both sides at once, A <- J^H A J, and written back
+// together with its mirror image (plain loads, no triangle addressing).  The V
 // group replays the record of the previous chunk of rounds on V meanwhile; record buffers swap at a
 // barrier of all threads every `C` rounds.
 //
@@ -166,12 +156,16 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                         float c = 1.f;
                         float2 s = make_float2(0.f, 0.f);
                         if (q < n) {
-                            const float2 b = conjf2(A[q * ld + p]);
+                            const float2 b = A[p * ld + q];
                             const float ap = A[p * ld + p].x, aq = A[q * ld + q].x;
-                            if (fmaf(b.x, b.x, b.y * b.y) <= jac_lim(rel, thr2, ap, aq)) A[q * ld + p] = make_float2(0.f, 0.f);
-                            else rotation32(ap, aq, b, c, s);
+                            if (fmaf(b.x, b.x, b.y * b.y) <= jac_lim(rel, thr2, ap, aq)) {
+                                A[p * ld + q] = make_float2(0.f, 0.f);
+                                A[q * ld + p] = make_float2(0.f, 0.f);
+                            } else {
+                                rotation32(ap, aq, b, c, s);
+                            }
                         }
-                        rr[i] = make_float4(c, s.x, s.y, 0.f);
+                        rr[i] = make_float4(c, s.x, s.y, __int_as_float(p | (q << 16)));
                     }
                     asm volatile("bar.sync 1, %0;" ::"r"(JA) : "memory");
                     // warp task j: block row a = j (blocks b = 0 .. a) followed by block row npair - 1 - j
@@ -183,15 +177,16 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                             if (a == j && l > j) continue;   // odd npair: the middle row is taken once
                             const float4 ra = rr[a], rb = rr[b];
                             if (ra.y == 0.f && ra.z == 0.f && rb.y == 0.f && rb.z == 0.f) continue;   // both identity
-                            int pa, qa, pb, qb;
-                            rr_pair(round, a, P, pa, qa);
-                            rr_pair(round, b, P, pb, qb);
+                            const int pqa = __float_as_int(ra.w), pqb = __float_as_int(rb.w);
+                            const int pa = pqa & 0xffff, qa = pqa >> 16, pb = pqb & 0xffff, qb = pqb >> 16;
                             const bool va = qa < n, vb = qb < n;
+                            float2* Ap = A + pa * ld;
+                            float2* Aq = A + qa * ld;   // row qa = n (the dummy) is never accessed
                             const float2 z2 = make_float2(0.f, 0.f);
-                            const float2 x00 = lget(A, ld, pa, pb);
-                            const float2 x01 = vb ? lget(A, ld, pa, qb) : z2;
-                            const float2 x10 = va ? lget(A, ld, qa, pb) : z2;
-                            const float2 x11 = va && vb ? lget(A, ld, qa, qb) : z2;
+                            const float2 x00 = Ap[pb];
+                            const float2 x01 = vb ? Ap[qb] : z2;
+                            const float2 x10 = va ? Aq[pb] : z2;
+                            const float2 x11 = va && vb ? Aq[qb] : z2;
                             const float ca = ra.x, cb = rb.x;
                             const float2 sa = make_float2(ra.y, ra.z), sb = make_float2(rb.y, rb.z);
                             const float2 sac = conjf2(sa), sbc = conjf2(sb);
@@ -200,14 +195,14 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                             const float2 y10 = rot_r(ca, sac, x00, x10), y11 = rot_r(ca, sac, x01, x11);
                             const float2 z00 = rot_l(cb, sbc, y00, y01), z01 = rot_r(cb, sb, y00, y01);
                             const float2 z10 = rot_l(cb, sbc, y10, y11), z11 = rot_r(cb, sb, y10, y11);
-                            if (a != b) {
-                                lput(A, ld, pa, pb, z00);
-                                if (vb) lput(A, ld, pa, qb, z01);
-                                if (va) lput(A, ld, qa, pb, z10);
-                                if (va && vb) lput(A, ld, qa, qb, z11);
+                            if (a != b) {   // the block and its mirror image
+                                Ap[pb] = z00; A[pb * ld + pa] = conjf2(z00);
+                                if (vb) { Ap[qb] = z01; A[qb * ld + pa] = conjf2(z01); }
+                                if (va) { Aq[pb] = z10; A[pb * ld + qa] = conjf2(z10); }
+                                if (va && vb) { Aq[qb] = z11; A[qb * ld + qa] = conjf2(z11); }
                             } else {
-                                A[pa * ld + pa] = z00;
-                                if (va) { A[qa * ld + pa] = z10; A[qa * ld + qa] = z11; }
+                                Ap[pa] = z00;
+                                if (va) { Aq[pa] = z10; Ap[qa] = conjf2(z10); Aq[qa] = z11; }
                             }
                         }
                     }
