@@ -244,10 +244,11 @@ __device__ __forceinline__ float jacobi_fro2(const float2* A, int n, int ld) {
     return f;
 }
 
-__device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, int ld) {
-    for (int e = threadIdx.x; e < n * n; e += JT) {   // W = V^H: row j is the conjugate of eigenvector j
+// W = V^H - dsub I: row j is the conjugate of eigenvector j (dsub = 1 stores the re-seed as a correction)
+__device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, int ld, double dsub) {
+    for (int e = threadIdx.x; e < n * n; e += JT) {
         const float2 v = V[(e % n) * ld + e / n];
-        Ws[e] = make_double2(v.x, -v.y);
+        Ws[e] = make_double2((double)v.x - (e % n == e / n ? dsub : 0.0), -v.y);
     }
 }
 
@@ -257,7 +258,7 @@ __device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, i
 //    initial iteration count, and clears the sector's re-seed flag;
 //  - re-seed (rel = true) in refinement iteration `it`, for sectors whose flag is set: src = S = X^H rho X
 //    scaled by 1 / ||rho||_F, so that eigenvalues far below FP32's resolution of rho are resolved relative
-//    to their own size; writes V^H (V: eigenvectors of S) over the correction dst = E1h, so that the
+//    to their own size; writes V^H - I (V: eigenvectors of S) over the correction dst = E1h, so that the
 //    iteration's update is W <- V^H W, and asks for two more refinements.
 __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, cplx* __restrict__ dst,
                                                  double* __restrict__ rho_fro, int* __restrict__ n_iter,
@@ -301,15 +302,16 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     const float thr = thr_s;
     if (in_smem) {
         jacobi_sweeps(fsm, fsm + n * ld, n, ld, thr, rel, rec, C);
-        jacobi_store(fsm + n * ld, dst + off, n, ld);
+        jacobi_store(fsm + n * ld, dst + off, n, ld, rel ? 1.0 : 0.0);
     } else {
         jacobi_sweeps(gA, gV, n, ld, thr, rel, rec, C);
-        jacobi_store(gV, dst + off, n, ld);
+        jacobi_store(gV, dst + off, n, ld, rel ? 1.0 : 0.0);
     }
 }
 
 // Refinement on W = X^H, which turns every product into a plain or conjugate-transposed operand of the
-// grouped GEMM: rho X = rho W^H, G = W W^H, S = W (rho X), and X <- X (I + E) is W <- (I + E)^H W.
+// grouped GEMM: rho X = rho W^H, G = W W^H, S = W (rho X), and X <- X (I + E) is W <- (I + E)^H W, the
+// last one in the GEMM's correction mode (E^H W in split FP32, W added in FP64).
 // The element-wise steps run on (sector, row chunk) CTAs: FP64 arithmetic is slow per SM, so one CTA
 // per sector would leave the largest sector's elements on one SM.
 constexpr int kRowChunks = 8;
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(256) k_oa_norms(const cplx* __restrict__ S, co
     }
 }
 
-// Rows of E1^H = (I + E)^H for the chunk.  With S and R = I - G Hermitian and lambda real, the
+// Rows of E^H for the chunk (the update adds the identity).  With S and R = I - G Hermitian and lambda real, the
 // conjugate of E_ji = (S_ji + lambda_i R_ji) / (lambda_i - lambda_j) is
 // (S_ij + lambda_i R_ij) / (lambda_i - lambda_j), and that of the cluster value R_ji / 2 is R_ij / 2.
 // delta = 2 (||S - diag(lambda)||_F + ||rho||_F ||R||_F), partial sums added in a fixed order.
@@ -406,8 +408,7 @@ __global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, c
             }
         }
         big |= fmax(fabs(ev.x), fabs(ev.y)) > kTolE;
-        if (i == j) ev.x += 1.0;
-        E1h[x] = ev;
+        E1h[x] = ev;   // the update adds the identity: W' = (I + E1h) W
     }
     // from the last iteration that always runs on, a correction still above kTolE asks for one more
     if (it >= kRefine - 1 && it + 1 < kMaxRefine && __syncthreads_or(big) && threadIdx.x == 0) atomicMax(n_iter, it + 2);
@@ -553,25 +554,25 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     const cplx* W_odd = Wn;
     int it = 0;
     // iterations past kRefine run on the device only when the previous correction asked for them
-    auto gemm = [&](TaskList& tl) {
+    auto gemm = [&](TaskList& tl, bool corr) {
         a.tasks = tl.d_tasks; a.segs = tl.d_segs; a.tiles = tl.d_tiles; a.ntiles = (int)tl.tiles.size();
         a.partials = tl.d_partials; a.counters = tl.d_counters;
         c->launches++;
-        return launch_gemm_f64(a, s, it < kRefine ? nullptr : n_iter, it);
+        return launch_gemm_f64(a, s, it < kRefine ? nullptr : n_iter, it, corr);
     };
     const dim3 chunks(ns, kRowChunks);
     cudaError_t e = cudaGetLastError();
     for (; it < kMaxRefine && e == cudaSuccess; ++it) {
         a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
-        e = gemm(w.tl_ax);
-        if (e == cudaSuccess) e = gemm(w.tl_sg);
+        e = gemm(w.tl_ax, false);
+        if (e == cudaSuccess) e = gemm(w.tl_sg, false);
         k_oa_norms<<<chunks, 256, 0, s>>>(S, G, w.lam, part, n_iter, it, tb);
         k_oa_update<<<chunks, 256, 0, s>>>(S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
         if (reseed_iter(it)) {
             k_jacobi32<<<ns, JT, w.jac_smem, s>>>(S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, true, it);
             c->launches++;
         }
-        if (e == cudaSuccess) e = gemm(w.tl_y);
+        if (e == cudaSuccess) e = gemm(w.tl_y, true);
         c->launches += 2;
         std::swap(W, Wn);
     }

@@ -15,6 +15,11 @@
 //     stores its partial tile and the last part to arrive (atomic ticket) sums all parts in index
 //     order, so results do not depend on scheduling.
 // Complex products use the FP64 tensor MMA (mma.sync m8n8k4 f64): four real MMAs per complex MMA.
+//
+// The correction mode (kCorr) serves the update W' = (I + D) W of the eigen-refinement, where D is small
+// (|D| <= 1e-3, ~1e-7 in the last iteration): D W runs in FP32 as a three-term split product
+// D_hi W_hi + D_hi W_lo + D_lo W_hi (x_hi = fl32(x), x_lo = fl32(x - x_hi); relative error ~1e-14 of
+// |D| |W|), and the epilogue adds W itself in FP64.  W is the B operand of the task's first segment.
 #include "internal.h"
 
 namespace tdmrg {
@@ -34,10 +39,24 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
 // conjugated operands are formed while staging instead of by FP64 instructions.
 __device__ __forceinline__ double neg(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (1ll << 63)); }
 
+__device__ __forceinline__ void split32(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// acc += a * b for complex a = (ar, ai), b = (br, bi) in FP32
+__device__ __forceinline__ void cfma32(float& cr, float& ci, float ar, float ai, float br, float bi) {
+    cr = fmaf(ar, br, fmaf(-ai, bi, cr));
+    ci = fmaf(ar, bi, fmaf(ai, br, ci));
+}
+
+template <bool kCorr>
 __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int* skip_flag, int skip_step) {
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;   // Krylov space already complete
-    __shared__ double Are[TS][PAD], Aim[TS][PAD], Ain[TS][PAD];   // Ain = -Aim
-    __shared__ double Bre[KC][PAD], Bim[KC][PAD];
+    __shared__ double Are[kCorr ? 1 : TS][PAD], Aim[kCorr ? 1 : TS][PAD], Ain[kCorr ? 1 : TS][PAD];   // Ain = -Aim
+    __shared__ double Bre[kCorr ? 1 : KC][PAD], Bim[kCorr ? 1 : KC][PAD];
+    // correction mode: hi / lo FP32 parts, [0] real and [1] imaginary
+    __shared__ float fA[kCorr ? 2 : 1][2][TS][PAD], fB[kCorr ? 2 : 1][2][KC][PAD];
     __shared__ int last;
 
     const Tile tile = args.tiles[blockIdx.x];
@@ -50,6 +69,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
     const int bi = warp >> 1, bj = warp & 1;
     const bool active = (8 * bi < Mt) && (8 * bj < Nt);
     double cre[2] = {0.0, 0.0}, cim[2] = {0.0, 0.0};
+    float fre[2] = {0.f, 0.f}, fim[2] = {0.f, 0.f};
 
     for (int s = tile.seg_lo; s < tile.seg_hi; ++s) {
         const Seg seg = args.segs[s];
@@ -70,9 +90,14 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                 double2 v = make_double2(0.0, 0.0);
                 if (r < Mt && k < kc) v = A[(int64_t)(m0 + r) * seg.lda + k0 + k];
                 if (scaled) v = make_double2(sr * v.x - si * v.y, sr * v.y + si * v.x);
-                Are[r][k] = v.x;
-                Aim[r][k] = v.y;
-                Ain[r][k] = neg(v.y);
+                if constexpr (kCorr) {
+                    split32(v.x, fA[0][0][r][k], fA[1][0][r][k]);
+                    split32(v.y, fA[0][1][r][k], fA[1][1][r][k]);
+                } else {
+                    Are[r][k] = v.x;
+                    Aim[r][k] = v.y;
+                    Ain[r][k] = neg(v.y);
+                }
             }
             if (seg.opb == OPB_N) {                   // B[k][n] at B[k*ldb + n]: threads along n
 #pragma unroll
@@ -80,8 +105,13 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     const int e = tid + 128 * u, k = e / TS, n = e % TS;
                     double2 v = make_double2(0.0, 0.0);
                     if (k < kc && n < Nt) v = B[(int64_t)(k0 + k) * seg.ldb + n0 + n];
-                    Bre[k][n] = v.x;
-                    Bim[k][n] = v.y;
+                    if constexpr (kCorr) {
+                        split32(v.x, fB[0][0][k][n], fB[1][0][k][n]);
+                        split32(v.y, fB[0][1][k][n], fB[1][1][k][n]);
+                    } else {
+                        Bre[k][n] = v.x;
+                        Bim[k][n] = v.y;
+                    }
                 }
             } else {                                  // B[k][n] at B[n*ldb + k] (conjugated for 'C')
 #pragma unroll
@@ -89,12 +119,35 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     const int e = tid + 128 * u, n = e / KC, k = e % KC;
                     double2 v = make_double2(0.0, 0.0);
                     if (k < kc && n < Nt) v = B[(int64_t)(n0 + n) * seg.ldb + k0 + k];
-                    Bre[k][n] = v.x;
-                    Bim[k][n] = conj ? neg(v.y) : v.y;
+                    if (conj) v.y = neg(v.y);
+                    if constexpr (kCorr) {
+                        split32(v.x, fB[0][0][k][n], fB[1][0][k][n]);
+                        split32(v.y, fB[0][1][k][n], fB[1][1][k][n]);
+                    } else {
+                        Bre[k][n] = v.x;
+                        Bim[k][n] = v.y;
+                    }
                 }
             }
             __syncthreads();
-            if (active) {
+            if constexpr (kCorr) {
+                if (active) {
+                    const int rr = 8 * bi + gid;
+                    for (int kk = 0; kk < kc; ++kk) {
+                        const float ahr = fA[0][0][rr][kk], ahi = fA[0][1][rr][kk];
+                        const float alr = fA[1][0][rr][kk], ali = fA[1][1][rr][kk];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int cc = 8 * bj + 2 * tig + e;
+                            const float bhr = fB[0][0][kk][cc], bhi = fB[0][1][kk][cc];
+                            const float blr = fB[1][0][kk][cc], bli = fB[1][1][kk][cc];
+                            cfma32(fre[e], fim[e], alr, ali, bhr, bhi);   // small terms first
+                            cfma32(fre[e], fim[e], ahr, ahi, blr, bli);
+                            cfma32(fre[e], fim[e], ahr, ahi, bhr, bhi);
+                        }
+                    }
+                }
+            } else if (active) {
                 for (int kk = 0; kk < kc; kk += 4) {   // zero-padded beyond kc
                     const double ar = Are[8 * bi + gid][kk + tig], ai = Aim[8 * bi + gid][kk + tig];
                     const double an = Ain[8 * bi + gid][kk + tig];
@@ -112,6 +165,10 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
     // this thread's two outputs: row 8 bi + gid, columns 8 bj + 2 tig + e
     const int r = 8 * bi + gid, col0 = 8 * bj + 2 * tig;
     double2 v[2] = {make_double2(cre[0], cim[0]), make_double2(cre[1], cim[1])};
+    if constexpr (kCorr) {
+        v[0] = make_double2((double)fre[0], (double)fim[0]);
+        v[1] = make_double2((double)fre[1], (double)fim[1]);
+    }
     if (tile.split >= 0) {
         // split-K: publish this part, the last part to arrive sums all parts in index order
         cplx* part = args.partials + ((int64_t)tile.split_base + tile.part) * (TS * TS);
@@ -147,6 +204,12 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
         if (r < Mt && col < Nt) {
             cplx* p = task.trans ? C + (int64_t)(n0 + col) * task.ldc + m0 + r : C + (int64_t)(m0 + r) * task.ldc + n0 + col;
             double2 x = v[e];
+            if constexpr (kCorr) {   // (I + D) W: add W in FP64
+                const Seg s0 = args.segs[task.seg_begin];
+                const double2 w = args.bufs[s0.b_buf][s0.b_off + (int64_t)(m0 + r) * s0.ldb + n0 + col];
+                x.x += w.x;
+                x.y += w.y;
+            }
             if (task.beta) {
                 const double2 o = *p;
                 x.x += o.x;
@@ -160,9 +223,10 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
 
 }  // namespace
 
-cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step) {
+cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step, bool corr) {
     if (a.ntiles <= 0) return cudaSuccess;
-    gemm_f64_kernel<<<a.ntiles, 128, 0, s>>>(a, skip_flag, skip_step);
+    if (corr) gemm_f64_kernel<true><<<a.ntiles, 128, 0, s>>>(a, skip_flag, skip_step);
+    else gemm_f64_kernel<false><<<a.ntiles, 128, 0, s>>>(a, skip_flag, skip_step);
     return cudaGetLastError();
 }
 
