@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
 
 // Refinement on W = X^H, which turns every product into a plain or conjugate-transposed operand of the
 // grouped GEMM: rho X = rho W^H, G = W W^H, S = W (rho X), and X <- X (I + E) is W <- (I + E)^H W, the
-// last one in the GEMM's correction mode (E^H W in split FP32, W added in FP64).
+// last one in the GEMM's correction mode (E^H W in FP32, W added in FP64).
 // The element-wise steps run on (sector, row chunk) CTAs: FP64 arithmetic is slow per SM, so one CTA
 // per sector would leave the largest sector's elements on one SM.
 constexpr int kRowChunks = 8;

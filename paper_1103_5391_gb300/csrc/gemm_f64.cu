@@ -17,9 +17,10 @@
 // Complex products use the FP64 tensor MMA (mma.sync m8n8k4 f64): four real MMAs per complex MMA.
 //
 // The correction mode (kCorr) serves the update W' = (I + D) W of the eigen-refinement, where D is small
-// (|D| <= 1e-3, ~1e-7 in the last iteration): D W runs in FP32 as a three-term split product
-// D_hi W_hi + D_hi W_lo + D_lo W_hi (x_hi = fl32(x), x_lo = fl32(x - x_hi); relative error ~1e-14 of
-// |D| |W|), and the epilogue adds W itself in FP64.  W is the B operand of the task's first segment.
+// (|D| <= 1e-3, ~1e-7 in the last iteration): D W runs in FP32 (each CTA accumulates one K part of at
+// most a few dozen terms; parts are summed in FP64), so its rounding is ~1e-7 of |D| |W|, and the
+// epilogue adds W itself in FP64.  W is the B operand of the task's first segment.  FP32 accumulation
+// is what limits the accuracy, so this mode suits small corrections only, not full products.
 #include "internal.h"
 
 namespace tdmrg {
@@ -39,11 +40,6 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
 // conjugated operands are formed while staging instead of by FP64 instructions.
 __device__ __forceinline__ double neg(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (1ll << 63)); }
 
-__device__ __forceinline__ void split32(double x, float& hi, float& lo) {
-    hi = (float)x;
-    lo = (float)(x - (double)hi);
-}
-
 // acc += a * b for complex a = (ar, ai), b = (br, bi) in FP32
 __device__ __forceinline__ void cfma32(float& cr, float& ci, float ar, float ai, float br, float bi) {
     cr = fmaf(ar, br, fmaf(-ai, bi, cr));
@@ -55,8 +51,8 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;   // Krylov space already complete
     __shared__ double Are[kCorr ? 1 : TS][PAD], Aim[kCorr ? 1 : TS][PAD], Ain[kCorr ? 1 : TS][PAD];   // Ain = -Aim
     __shared__ double Bre[kCorr ? 1 : KC][PAD], Bim[kCorr ? 1 : KC][PAD];
-    // correction mode: hi / lo FP32 parts, [0] real and [1] imaginary
-    __shared__ float fA[kCorr ? 2 : 1][2][TS][PAD], fB[kCorr ? 2 : 1][2][KC][PAD];
+    // correction mode: FP32 operands, [0] real and [1] imaginary
+    __shared__ float fA[2][kCorr ? TS : 1][PAD], fB[2][kCorr ? KC : 1][PAD];
     __shared__ int last;
 
     const Tile tile = args.tiles[blockIdx.x];
@@ -91,8 +87,8 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                 if (r < Mt && k < kc) v = A[(int64_t)(m0 + r) * seg.lda + k0 + k];
                 if (scaled) v = make_double2(sr * v.x - si * v.y, sr * v.y + si * v.x);
                 if constexpr (kCorr) {
-                    split32(v.x, fA[0][0][r][k], fA[1][0][r][k]);
-                    split32(v.y, fA[0][1][r][k], fA[1][1][r][k]);
+                    fA[0][r][k] = (float)v.x;
+                    fA[1][r][k] = (float)v.y;
                 } else {
                     Are[r][k] = v.x;
                     Aim[r][k] = v.y;
@@ -106,8 +102,8 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     double2 v = make_double2(0.0, 0.0);
                     if (k < kc && n < Nt) v = B[(int64_t)(k0 + k) * seg.ldb + n0 + n];
                     if constexpr (kCorr) {
-                        split32(v.x, fB[0][0][k][n], fB[1][0][k][n]);
-                        split32(v.y, fB[0][1][k][n], fB[1][1][k][n]);
+                        fB[0][k][n] = (float)v.x;
+                        fB[1][k][n] = (float)v.y;
                     } else {
                         Bre[k][n] = v.x;
                         Bim[k][n] = v.y;
@@ -121,8 +117,8 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     if (k < kc && n < Nt) v = B[(int64_t)(n0 + n) * seg.ldb + k0 + k];
                     if (conj) v.y = neg(v.y);
                     if constexpr (kCorr) {
-                        split32(v.x, fB[0][0][k][n], fB[1][0][k][n]);
-                        split32(v.y, fB[0][1][k][n], fB[1][1][k][n]);
+                        fB[0][k][n] = (float)v.x;
+                        fB[1][k][n] = (float)v.y;
                     } else {
                         Bre[k][n] = v.x;
                         Bim[k][n] = v.y;
@@ -134,16 +130,11 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                 if (active) {
                     const int rr = 8 * bi + gid;
                     for (int kk = 0; kk < kc; ++kk) {
-                        const float ahr = fA[0][0][rr][kk], ahi = fA[0][1][rr][kk];
-                        const float alr = fA[1][0][rr][kk], ali = fA[1][1][rr][kk];
+                        const float ar = fA[0][rr][kk], ai = fA[1][rr][kk];
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             const int cc = 8 * bj + 2 * tig + e;
-                            const float bhr = fB[0][0][kk][cc], bhi = fB[0][1][kk][cc];
-                            const float blr = fB[1][0][kk][cc], bli = fB[1][1][kk][cc];
-                            cfma32(fre[e], fim[e], alr, ali, bhr, bhi);   // small terms first
-                            cfma32(fre[e], fim[e], ahr, ahi, blr, bli);
-                            cfma32(fre[e], fim[e], ahr, ahi, bhr, bhi);
+                            cfma32(fre[e], fim[e], ar, ai, fB[0][kk][cc], fB[1][kk][cc]);
                         }
                     }
                 }

@@ -264,7 +264,7 @@ int run_plan(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* 
 // gemm_f64.cu: grouped complex FP64 GEMM (FP64 MMA), tile 16 x 16, split-K above kSplitK
 constexpr int kTileF64 = 16;
 constexpr int kSplitK = 96;
-// corr: the correction mode of the eigen-refinement update, C = (I + A) B with A B in split FP32
+// corr: the correction mode of the eigen-refinement update, C = (I + A) B with A B in FP32
 cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step, bool corr = false);
 
 

@@ -25,8 +25,11 @@ def _states(ss, nv, seed):
     return sts
 
 
+@pytest.mark.parametrize("mixed", [False, True])
 @pytest.mark.parametrize("L,m,nb", [(8, 24, 1), (32, 400, 1), (32, 800, 2)])
-def test_rho_and_eig(lib, L, m, nb):
+def test_rho_and_eig(lib, L, m, nb, mixed):
+    """rho_L (an FP64 HERK in either precision of the context) within 1e-14 of the oracle's, and its
+    eigendecomposition to FP64 accuracy."""
     from paper_1103_5391_gb300 import problem
     ss = S.make_synthetic(L, m, 4.0, nbonds=nb, seed=S.SEED_BASE + 7)
     sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
@@ -34,7 +37,7 @@ def test_rho_and_eig(lib, L, m, nb):
     sts = _states(ss, 4, 1)
     weights = [wgs] + w
     ref = density.rho_left(sb, sts, weights)
-    ctx = new_ctx()
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=4) if mixed else new_ctx()
     try:
         problem.load_synthetic(ctx, ss)
         nr, ne = lib.tdmrg_rho_size(ctx)
