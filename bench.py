@@ -18,8 +18,10 @@ observables over a 20-step trajectory (vs_fp64_gpu).
 --impl reference times the CPU oracle (FP64 NumPy) on the same workload on the host cores.
 """
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -38,6 +40,36 @@ WORKLOAD_NAME = "1D Hubbard chain L=32 U=4 half filling m=400 superblock (synthe
                 "c^dag excitation, tau=0.05, n_v=4, n_K=10, complex128"
 FLUSH_BYTES = 256 << 20
 BF16_BURST = 1923.8   # TFLOP/s, dense bf16 burst measured on the GB300s (cuBLAS)
+# DRAM bytes of one tensor-path H psi, from an ncu capture summarised in this file; valid only while the
+# kernels, plans and workload generator are byte-identical to those captured (digest below)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_hpsi_ozaki_L32_m400_chain.md")
+TRAFFIC_SOURCES = ("paper_1103_5391_gb300/csrc/ozaki.cu", "paper_1103_5391_gb300/csrc/plan.cu",
+                   "paper_1103_5391_gb300/csrc/internal.h", "workloads/sectors.py")
+
+
+def sources_digest():
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def hpsi_traffic():
+    """(bytes per H psi, note) from the committed capture, or (None, why not)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            text = f.read()
+    except OSError:
+        return None, "no DRAM capture committed"
+    b = re.search(r"^traffic_bytes_per_hpsi: (\d+)$", text, re.M)
+    d = re.search(r"^sources_sha256: ([0-9a-f]{64})$", text, re.M)
+    if not b or not d:
+        return None, "DRAM capture summary unreadable"
+    if d.group(1) != sources_digest():
+        return None, "kernel or workload sources changed since the DRAM capture"
+    return int(b.group(1)), "dram__bytes_read.sum + dram__bytes_write.sum of the 4 launches of one H psi (ncu, " \
+                            + os.path.relpath(TRAFFIC_FILE, ROOT) + ")"
 
 
 def parse():
@@ -53,6 +85,8 @@ def parse():
     ap.add_argument("--jobs", type=int, default=24)
     ap.add_argument("--job-steps", type=int, default=20)
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
+                    help="only apply H psi N times on the workload (a short run for ncu captures)")
     return ap.parse_args()
 
 
@@ -135,7 +169,7 @@ class OracleStep:
         return n_used
 
 
-def cpu_baseline(ss, budget_s=15.0, max_steps=3):
+def cpu_baseline(ss, budget_s=12.0, max_steps=1000):
     st = OracleStep(ss)
     t0 = time.perf_counter()
     ks, n = 0, 0
@@ -434,8 +468,10 @@ def run_ours(args):
     if rank == 0:
         srt = sorted(step_ms)
         if mixed:
+            traffic, traffic_note = hpsi_traffic()
             roof = {"bound": "tensor", "achieved": tensor_fl / (h_ms * 1e-3) / 1e12, "peak": BF16_BURST, "unit": "TFLOP/s",
-                    "traffic": None, "kernel": "H psi on the tensor path (bf16 slicing + tcgen05 GEMM, 4 launches)",
+                    "traffic": traffic, "traffic_source": traffic_note,
+                    "kernel": "H psi on the tensor path (bf16 slicing + tcgen05 GEMM, 4 launches)",
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS bf16)",
                     "alg_fp64_equiv_tflops": alg / (h_ms * 1e-3) / 1e12}
         else:
@@ -537,10 +573,37 @@ def run_serving(args):
     return 0
 
 
+def run_profile_hpsi(args):
+    """N applications of H psi on the bench workload, nothing else: after the plan build (which times
+    both tile schedules of each stage) every application is slice rows, stage-1 GEMM, slice columns,
+    stage-2 GEMM."""
+    import torch
+    from paper_1103_5391_gb300 import problem, tdmrg as T
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ss = workload()
+    prec = T.TDMRG_OZAKI_BF16 if args.prec == "ozaki" else T.TDMRG_FP64
+    ctx = T.tdmrg_create(device=0, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = T.tdmrg_sector_size(ctx, ss.Q1)
+        x = torch.randn(n, dtype=torch.complex128, device="cuda")
+        y = torch.zeros_like(x)
+        for _ in range(args.profile_hpsi):
+            T.tdmrg_apply_h(ctx, ss.Q1, x, y)
+        torch.cuda.synchronize()
+    finally:
+        T.tdmrg_destroy(ctx)
+    print(json.dumps({"profile_hpsi": args.profile_hpsi, "D": n, "prec": args.prec}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_hpsi > 0:
+        return run_profile_hpsi(args)
     if args.serving:
         return run_serving(args)
     return run_ours(args)
