@@ -18,6 +18,7 @@ constexpr int NB = kRedBlocks;
 struct Weights { double w[12]; };
 
 __global__ void k_weight_scale(const double2* __restrict__ part, int nt, double* __restrict__ dscale, Weights ws) {
+    pdl_enter();
     // one warp per target: dscale[l] = w_l / ||psi_l||^2 (0 for a zero state)
     const int l = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (l >= nt) return;
@@ -45,7 +46,7 @@ int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* ps
     }
     Weights wl{};
     for (int l = 0; l < nt; ++l) wl.w[l] = w[l];
-    k_weight_scale<<<1, 32 * 12, 0, s>>>(c->red, nt, c->dscale, wl);
+    launch_pdl(k_weight_scale, 1, 32 * 12, 0, s, c->red, nt, c->dscale, wl);
     c->launches++;
     // task list: one task per left sector, compiled once per set of target sectors
     std::vector<int> key(Q, Q + 2 * nt);

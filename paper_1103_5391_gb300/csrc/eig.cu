@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
                                                  double* __restrict__ rho_fro, int* __restrict__ n_iter,
                                                  int* __restrict__ flags, EigTables tb, float2* __restrict__ gwork,
                                                  int smem, bool rel, int it) {
+    pdl_enter();
     extern __shared__ float4 fsm4[];
     float2* fsm = reinterpret_cast<float2*>(fsm4);
     const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
@@ -340,6 +341,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[8
 __global__ void __launch_bounds__(256) k_oa_norms(const cplx* __restrict__ S, const cplx* __restrict__ G,
                                                   double* __restrict__ lam, double* __restrict__ part,
                                                   const int* __restrict__ n_iter, int it, EigTables tb) {
+    pdl_enter();
     if (it >= *n_iter) return;   // refinement already converged
     const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
     const int64_t off = tb.off[sct], eo = tb.eoff[sct];
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, c
                                                    const double* __restrict__ lam, const double* __restrict__ part,
                                                    const double* __restrict__ rho_fro, cplx* __restrict__ E1h,
                                                    int* __restrict__ n_iter, int* __restrict__ flags, int it, EigTables tb) {
+    pdl_enter();
     if (it >= *n_iter) return;   // refinement already converged
     const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
     const int64_t off = tb.off[sct], eo = tb.eoff[sct];
@@ -427,6 +430,7 @@ __device__ __forceinline__ unsigned long long order_key(double v) {
 __global__ void __launch_bounds__(256) k_eig_sort(const cplx* __restrict__ W_even, const cplx* __restrict__ W_odd,
                                                   const int* __restrict__ n_iter, const double* __restrict__ lam,
                                                   cplx* __restrict__ U, double* __restrict__ evals, EigTables tb) {
+    pdl_enter();
     const cplx* __restrict__ W = (*n_iter & 1) ? W_odd : W_even;   // the iterate after the last refinement
     const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
     const int64_t off = tb.off[sct], eo = tb.eoff[sct];
@@ -544,7 +548,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     cplx* E1h = w.buf + 5 * w.nrho;
     double* part = w.fro + ns;
     int* n_iter = reinterpret_cast<int*>(part + 2 * (size_t)ns * kRowChunks);
-    k_jacobi32<<<ns, JT, w.jac_smem, s>>>(rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, false, 0);
+    launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, false, 0);
     c->launches += 1;
     GemmArgs a{};
     a.dscale = c->dscale;
@@ -566,10 +570,10 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
         e = gemm(w.tl_ax, false);
         if (e == cudaSuccess) e = gemm(w.tl_sg, false);
-        k_oa_norms<<<chunks, 256, 0, s>>>(S, G, w.lam, part, n_iter, it, tb);
-        k_oa_update<<<chunks, 256, 0, s>>>(S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
+        launch_pdl(k_oa_norms, chunks, 256, 0, s, S, G, w.lam, part, n_iter, it, tb);
+        launch_pdl(k_oa_update, chunks, 256, 0, s, S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
         if (reseed_iter(it)) {
-            k_jacobi32<<<ns, JT, w.jac_smem, s>>>(S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, true, it);
+            launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, true, it);
             c->launches++;
         }
         if (e == cudaSuccess) e = gemm(w.tl_y, true);
@@ -577,7 +581,7 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         std::swap(W, Wn);
     }
     if (e == cudaSuccess) {
-        k_eig_sort<<<chunks, 256, 0, s>>>(W_even, W_odd, n_iter, w.lam, evecs, evals, tb);
+        launch_pdl(k_eig_sort, chunks, 256, 0, s, W_even, W_odd, n_iter, w.lam, evecs, evals, tb);
         c->launches++;
         e = cudaGetLastError();
     }

@@ -48,6 +48,7 @@ __device__ __forceinline__ void cfma32(float& cr, float& ci, float ar, float ai,
 
 template <bool kCorr>
 __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int* skip_flag, int skip_step) {
+    pdl_enter();
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;   // Krylov space already complete
     __shared__ double Are[kCorr ? 1 : TS][PAD], Aim[kCorr ? 1 : TS][PAD], Ain[kCorr ? 1 : TS][PAD];   // Ain = -Aim
     __shared__ double Bre[kCorr ? 1 : KC][PAD], Bim[kCorr ? 1 : KC][PAD];
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
 
 cudaError_t launch_gemm_f64(const GemmArgs& a, cudaStream_t s, const int* skip_flag, int skip_step, bool corr) {
     if (a.ntiles <= 0) return cudaSuccess;
-    if (corr) gemm_f64_kernel<true><<<a.ntiles, 128, 0, s>>>(a, skip_flag, skip_step);
-    else gemm_f64_kernel<false><<<a.ntiles, 128, 0, s>>>(a, skip_flag, skip_step);
+    if (corr) launch_pdl(gemm_f64_kernel<true>, a.ntiles, 128, 0, s, a, skip_flag, skip_step);
+    else launch_pdl(gemm_f64_kernel<false>, a.ntiles, 128, 0, s, a, skip_flag, skip_step);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 #include <memory>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/tdmrg.h"
@@ -18,6 +19,33 @@
 namespace tdmrg {
 
 typedef double2 cplx;   // {re, im}, same layout as tdmrg_c64
+
+// Programmatic dependent launch.  Kernels are launched with the programmatic-serialisation attribute and
+// every kernel of the library starts with pdl_enter(), which waits until the previous grid of the stream
+// has completed and its memory is visible: the launch of a kernel overlaps the end of the previous one,
+// while every global memory access still follows the previous kernel's completion.  No kernel signals
+// its dependents early (measured: blocks parked in the wait beside a running kernel slow it down).
+// Without the launch attribute the wait returns at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// <<<grid, block, smem, s>>> with the programmatic-serialisation attribute
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+#endif
 
 // Buffer ids a segment or task refers to; the launch passes the base pointers.
 enum BufId : int8_t { BUF_OPS = 0, BUF_IN = 1, BUF_SCRATCH = 2, BUF_OUT = 3, BUF_EXTRA0 = 4 };

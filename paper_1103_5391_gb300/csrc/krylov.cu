@@ -73,6 +73,7 @@ __device__ __forceinline__ double2 cdotc(double2 a, double2 b) {   // conj(a) * 
 }
 
 __global__ void __launch_bounds__(NT) k_norm2(const cplx* __restrict__ x, int64_t n, double2* __restrict__ part) {
+    pdl_enter();
     int64_t lo, hi;
     chunk_of(n, lo, hi);
     double s = 0.0;
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(NT) k_norm2(const cplx* __restrict__ x, int64_
 __global__ void __launch_bounds__(NT) k_init_v0(const cplx* __restrict__ phi, int64_t n, const double2* __restrict__ part,
                                                  cplx* __restrict__ v0, double* __restrict__ tri, int* __restrict__ flags,
                                                  int nk) {
+    pdl_enter();
     __shared__ double2 h[1];
     reduce_coeffs(part, 1, h);
     const double b0 = sqrt(h[0].x);
@@ -263,6 +265,7 @@ __device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, i
 }
 
 __global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
+    pdl_enter();
     if (a.j >= a.flags[0]) return;   // uniform: the flag only changes after the last barrier
     __shared__ double sh[(OB / 32) * 16];
     __shared__ double2 red8[8];
@@ -334,6 +337,7 @@ __constant__ double kInvK[25] = {0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 
 // beta_n beta0 |[e^{-i T t_max} e_0]_{n-1}| (t_max the largest target time).
 __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, const int* __restrict__ flags,
                                                      Times times, int n_v, cplx* __restrict__ coef) {
+    pdl_enter();
     __shared__ int order[16];
     const int l = threadIdx.x;
     const int n = flags[0];
@@ -399,6 +403,7 @@ struct TargetPtrs { cplx* p[16]; };
 template <int NX>
 __global__ void __launch_bounds__(256) k_combine(const cplx* __restrict__ V, int64_t n, const int* __restrict__ flags,
                                                   const cplx* __restrict__ coef, int x0, TargetPtrs tg) {
+    pdl_enter();
     __shared__ double2 cf[NX][32];
     const int nu = flags[0];
     for (int e = threadIdx.x; e < NX * 32; e += blockDim.x) cf[e / 32][e % 32] = coef[(x0 + e / 32) * 32 + e % 32];
@@ -427,14 +432,14 @@ cudaError_t launch_combine(const cplx* V, int64_t n, const int* flags, const cpl
         TargetPtrs t{};
         for (int x = x0; x < n_v; ++x) t.p[x - x0] = tg.p[x];
         switch (std::min(8, n_v - x0)) {
-            case 1: k_combine<1><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            case 2: k_combine<2><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            case 3: k_combine<3><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            case 4: k_combine<4><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            case 5: k_combine<5><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            case 6: k_combine<6><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            case 7: k_combine<7><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
-            default: k_combine<8><<<grid, 256, 0, s>>>(V, n, flags, coef, x0, t); break;
+            case 1: launch_pdl(k_combine<1>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            case 2: launch_pdl(k_combine<2>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            case 3: launch_pdl(k_combine<3>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            case 4: launch_pdl(k_combine<4>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            case 5: launch_pdl(k_combine<5>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            case 6: launch_pdl(k_combine<6>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            case 7: launch_pdl(k_combine<7>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+            default: launch_pdl(k_combine<8>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
         }
     }
     return cudaGetLastError();
@@ -442,6 +447,7 @@ cudaError_t launch_combine(const cplx* V, int64_t n, const int* flags, const cpl
 
 __global__ void __launch_bounds__(NT) k_dot2(const cplx* __restrict__ x, const cplx* __restrict__ y, int64_t n,
                                               double2* __restrict__ part) {
+    pdl_enter();
     int64_t lo, hi;
     chunk_of(n, lo, hi);
     double2 s = make_double2(0.0, 0.0);
@@ -458,6 +464,7 @@ __global__ void __launch_bounds__(NT) k_dot2(const cplx* __restrict__ x, const c
 }
 
 __global__ void __launch_bounds__(NT) k_dot_final(const double2* __restrict__ part, cplx* __restrict__ out, int normalise) {
+    pdl_enter();
     __shared__ double2 h[2];
     reduce_coeffs(part, 2, h);
     if (threadIdx.x == 0) {
@@ -511,15 +518,15 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
 
 cudaError_t launch_norm2(const cplx* x, int64_t n, double2* partials, int nblk, cudaStream_t s) {
     (void)nblk;
-    k_norm2<<<NB, NT, 0, s>>>(x, n, partials);
+    launch_pdl(k_norm2, NB, NT, 0, s, x, n, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* partials, int nblk, cplx* out,
                              int normalise, cudaStream_t s) {
     (void)nblk;
-    k_dot2<<<NB, NT, 0, s>>>(x, y, n, partials);
-    k_dot_final<<<1, NT, 0, s>>>(partials, out, normalise);
+    launch_pdl(k_dot2, NB, NT, 0, s, x, y, n, partials);
+    launch_pdl(k_dot_final, 1, NT, 0, s, partials, out, normalise);
     return cudaGetLastError();
 }
 
@@ -535,8 +542,8 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
     cudaStream_t s = c->stream;
     Times tt{};
     for (int x = 0; x < n_v; ++x) tt.t[x] = t_x[x];
-    k_norm2<<<NB, NT, 0, s>>>(phi, n, k->partA);
-    k_init_v0<<<NB, NT, 0, s>>>(phi, n, k->partA, k->V, k->tri, k->flags, nk);
+    launch_pdl(k_norm2, NB, NT, 0, s, phi, n, k->partA);
+    launch_pdl(k_init_v0, NB, NT, 0, s, phi, n, k->partA, k->V, k->tri, k->flags, nk);
     c->launches += 2;
     for (int j = 0; j < nk; ++j) {
         cplx* vj = k->V + (int64_t)j * n;
@@ -559,7 +566,7 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
         if (le != cudaSuccess) return cuda_check(c, le, "Lanczos orthogonalisation launch");
         c->launches += 1;
     }
-    k_tridiag_exp<<<1, 32, 0, s>>>(k->tri, k->flags, tt, n_v, k->coef);
+    launch_pdl(k_tridiag_exp, 1, 32, 0, s, k->tri, k->flags, tt, n_v, k->coef);
     TargetPtrs tg{};
     for (int x = 0; x < n_v; ++x) tg.p[x] = targets[x];
     int grid = (int)std::min<int64_t>((n + 255) / 256, 4L * c->num_sms);

@@ -94,6 +94,7 @@ __device__ __forceinline__ double2 view_load(const SegView& w, int k, bool use_s
 
 template <int S>
 __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, GemmArgs g, const int* skip_flag, int skip_step) {
+    pdl_enter();
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     if (gw >= sa.nvec_total) return;   // warp-uniform
@@ -283,6 +284,7 @@ template <int S>
 __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUtensorMap mapA,
                                                      const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa, GemmArgs g,
                                                      const int* skip_flag, int skip_step) {
+    pdl_enter();
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     constexpr int NCOLS = (S * 64 <= 256) ? 256 : 512;   // TMEM columns: one 64-column accumulator per g
     extern __shared__ unsigned char smem_raw[];
@@ -453,6 +455,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                                                           const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa,
                                                           GemmArgs g, int ntiles, int queue, const int* skip_flag,
                                                           int skip_step) {
+    pdl_enter();
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     static_assert(S <= 4, "two TMEM buffers of S x 64 columns must fit in 512");
     constexpr uint32_t NCOLS = 512;
@@ -722,12 +725,12 @@ cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, co
         const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
         const int ntiles = (int)st.tiles.size();
         const int grid = std::max(1, std::min(ntiles, g_num_sms));
-        k_ozaki_gemm_ws<S><<<grid, WS_THREADS, smem, s>>>(st.mapA, st.mapB, st.args, g, ntiles, st.queue, skip_flag,
+        launch_pdl(k_ozaki_gemm_ws<S>, grid, WS_THREADS, smem, s, st.mapA, st.mapB, st.args, g, ntiles, st.queue, skip_flag,
                                                            skip_step);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
-    k_ozaki_gemm<S><<<(int)st.tiles.size(), 128, smem, s>>>(st.mapA, st.mapB, st.args, g, skip_flag, skip_step);
+    launch_pdl(k_ozaki_gemm<S>, (int)st.tiles.size(), 128, smem, s, st.mapA, st.mapB, st.args, g, skip_flag, skip_step);
     return cudaGetLastError();
 }
 
@@ -735,11 +738,11 @@ cudaError_t slice_launch(const OzSliceArgs& sa, const GemmArgs& g, cudaStream_t 
     if (sa.nvec_total <= 0) return cudaSuccess;
     const int warps = kSliceWarps, grid = (sa.nvec_total + warps - 1) / warps;
     switch (sa.S) {
-        case 2: k_slice<2><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
-        case 3: k_slice<3><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
-        case 4: k_slice<4><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
-        case 5: k_slice<5><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
-        case 6: k_slice<6><<<grid, 32 * warps, 0, s>>>(sa, g, skip_flag, skip_step); break;
+        case 2: launch_pdl(k_slice<2>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
+        case 3: launch_pdl(k_slice<3>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
+        case 4: launch_pdl(k_slice<4>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
+        case 5: launch_pdl(k_slice<5>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
+        case 6: launch_pdl(k_slice<6>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
