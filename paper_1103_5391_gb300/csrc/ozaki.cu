@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, Gemm
         while (sgi + 1 < nw && e >= spre[wi][sgi + 1]) ++sgi;
         return sgi;
     };
-    double2 cache[kSliceU];
+    // the first batch of a vector (up to 32 kSliceU elements) is kept in shared memory between the
+    // passes; each lane reads back only what it wrote, so no barrier is needed
+    __shared__ double2 scache[kSliceWarps][32 * kSliceU];
+    double2* cache = scache[wi];
     const bool one_batch = nseg <= kSegCache;
     int emax = 0, kw_first = 0;
     for (int w0 = 0; w0 < nseg; w0 += kSegCache) {   // pass 1: largest exponent
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, Gemm
 #pragma unroll
             for (int u = 0; u < kSliceU; ++u) {
                 emax = max(emax, max(biased_exp(x[u].x), biased_exp(x[u].y)));
-                cache[u] = x[u];
+                if (w0 == 0 && e0 == 0) cache[lane + 32 * u] = x[u];
             }
         }
     }
@@ -178,42 +181,41 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, Gemm
     }
     if (lane == 0) sa.exps[job.exp0 + v] = E;
     const int64_t plane = (int64_t)sa.rows * sa.kpad;
-    __nv_bfloat16* P = sa.panel;
+    __nv_bfloat16* const row_re = sa.panel + (int64_t)r_re * sa.kpad;   // plane 0 rows; plane t at + t plane
+    __nv_bfloat16* const row_im = sa.panel + (int64_t)r_im * sa.kpad;
+    const bool role0 = job.role == 0;
     int kbase = 0;
     for (int w0 = 0; w0 < nseg; w0 += kSegCache) {   // pass 2: digits
         const int nw = min(kSegCache, nseg - w0);
         const int kw = (w0 == 0 && one_batch) ? kw_first : build(w0, nw);
         for (int e0 = 0; e0 < kw; e0 += 32 * kSliceU) {
-            double2 x[kSliceU];
-#pragma unroll
+#pragma unroll 1
             for (int u = 0; u < kSliceU; ++u) {
                 const int e = e0 + lane + 32 * u;
-                x[u] = make_double2(0.0, 0.0);
-                if (cached) x[u] = cache[u];
-                else if (e < kw) {
+                if (e >= kw) break;   // e grows with u
+                double2 x;
+                if (cached) {
+                    x = cache[lane + 32 * u];
+                } else {
                     const int sgi = seg_of(e, nw);
-                    x[u] = view_load(sv[wi][sgi], e - spre[wi][sgi], use_scale);
+                    x = view_load(sv[wi][sgi], e - spre[wi][sgi], use_scale);
                 }
-            }
-#pragma unroll
-            for (int u = 0; u < kSliceU; ++u) {
-                const int e = e0 + lane + 32 * u;
-                if (e >= kw) continue;
                 int dr[S], di[S];
-                digits<S>(fixed_point(x[u].x, E, S7), dr);
-                digits<S>(fixed_point(x[u].y, E, S7), di);
-                const int p = kbase + e, q = job.ktot + kbase + e;
+                digits<S>(fixed_point(x.x, E, S7), dr);
+                digits<S>(fixed_point(x.y, E, S7), di);
+                __nv_bfloat16* pr = row_re + kbase + e;
+                __nv_bfloat16* pi = row_im + kbase + e;
+                const int q = job.ktot;   // the imaginary half of a row starts at ktot
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    __nv_bfloat16* pl = P + t * plane;
-                    if (job.role == 0) {
-                        pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
-                        pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)di[t]);
+                    if (role0) {
+                        pr[t * plane] = __float2bfloat16_rn((float)dr[t]);
+                        pr[t * plane + q] = __float2bfloat16_rn((float)di[t]);
                     } else {
-                        pl[(int64_t)r_re * sa.kpad + p] = __float2bfloat16_rn((float)dr[t]);
-                        pl[(int64_t)r_re * sa.kpad + q] = __float2bfloat16_rn((float)(-di[t]));
-                        pl[(int64_t)r_im * sa.kpad + p] = __float2bfloat16_rn((float)di[t]);
-                        pl[(int64_t)r_im * sa.kpad + q] = __float2bfloat16_rn((float)dr[t]);
+                        pr[t * plane] = __float2bfloat16_rn((float)dr[t]);
+                        pr[t * plane + q] = __float2bfloat16_rn((float)(-di[t]));
+                        pi[t * plane] = __float2bfloat16_rn((float)di[t]);
+                        pi[t * plane + q] = __float2bfloat16_rn((float)dr[t]);
                     }
                 }
             }
