@@ -158,13 +158,15 @@ int tdmrg_rho_size(tdmrg_ctx* ctx, int64_t* rho_entries, int64_t* n_evals);
 
 /* Weighted reduced density matrix (Eq. rdensitymatrix):
  *   rho_L(q) = sum_l w[l] Psi_l(q) Psi_l(q)^dag / <psi_l|psi_l>
- * over ntargets states psi_d[l] (host array of device pointers) in sectors Q[2l], Q[2l+1] (host).
+ * over ntargets (1..12) states psi_d[l] (host array of device pointers) in sectors Q[2l], Q[2l+1] (host).
  * rho_d receives every left sector's dL x dL block, row-major, packed in left-table order (zero for
  * sectors no target reaches).  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
 int tdmrg_density_matrix(tdmrg_ctx* ctx, int ntargets, const int32_t* Q, const tdmrg_c64* const* psi_d,
                          const double* w, tdmrg_c64* rho_d);
 
-/* Eigendecomposition of a packed rho_L (as written by tdmrg_density_matrix), FP64 Jacobi per sector.
+/* Eigendecomposition of a packed rho_L (as written by tdmrg_density_matrix) to FP64 accuracy per sector
+ * (dL <= 512): FP32 Jacobi seed, FP64 iterative refinement (Ogita-Aishima) with re-seeding of coupled
+ * clusters.
  * evals_d (sum dL doubles) gets each sector's eigenvalues in descending order; evecs_d (packed like
  * rho) gets U with rho(q) = U diag(evals) U^dag, column k of U the k-th eigenvector.  This feeds the
  * truncation of Sec. II.B.  Errors: EINVAL, ESTATE, ECUDA. */
@@ -197,7 +199,7 @@ typedef struct {
     int q[2];                    /* sector of the evolving state                                            */
     const tdmrg_c64* phi0_d;     /* initial state phi (device); copied when the job is admitted              */
     double tau;                  /* time step; targets at t_x = x tau / (n_v - 1)                           */
-    int n_v, nk, steps;          /* time targets (2..16), Krylov dimension, number of time steps            */
+    int n_v, nk, steps;          /* time targets (2..11), Krylov dimension, number of time steps            */
     int nobs;                    /* observables measured after every step (0..16)                            */
     int32_t obs_opL[16], obs_opR[16];   /* left / right op ids of each observable (-1 = identity)         */
 } tdmrg_job;

@@ -306,7 +306,8 @@ int tdmrg_server_create(tdmrg_server** out, int device, size_t budget, int max_a
 int tdmrg_server_submit(tdmrg_server* s, const tdmrg_job* job, int64_t* id) {
     if (!s || !job || !id) return sfail(s, TDMRG_EINVAL, "server_submit: null argument");
     const tdmrg_job& d = *job;
-    if (!d.ctx || !d.psi_gs_d || !d.phi0_d || d.n_v < 2 || d.n_v > 16 || d.nk < 1 || d.nk > d.ctx->opts.nk_max ||
+    // rho_L takes the ground state and the n_v targets: at most 12 states
+    if (!d.ctx || !d.psi_gs_d || !d.phi0_d || d.n_v < 2 || d.n_v > 11 || d.nk < 1 || d.nk > d.ctx->opts.nk_max ||
         d.steps < 1 || d.nobs < 0 || d.nobs > 16 || !(d.tau > 0.0))
         return sfail(s, TDMRG_EINVAL, "server_submit: bad job description");
     if (d.ctx->opts.device != s->device) return sfail(s, TDMRG_EINVAL, "server_submit: context on another device");

@@ -111,6 +111,8 @@ def test_budget_cancel_and_errors():
             ss, ctx, psi, phi = jobs[0]
             with pytest.raises(T.TdmrgError):   # n_v = 1 is not time-step targeting
                 T.tdmrg_server_submit(srv, ctx, ss.Q0, psi, ss.Q1, phi, 0.05, 1, 8, 4)
+            with pytest.raises(T.TdmrgError):   # rho_L would take 13 states
+                T.tdmrg_server_submit(srv, ctx, ss.Q0, psi, ss.Q1, phi, 0.05, 12, 8, 4)
         finally:
             T.tdmrg_server_destroy(srv)
     finally:
