@@ -36,6 +36,13 @@ int tdmrg_set_schedule(tdmrg_ctx* ctx, int mode);
  * the device; takes well under a second.  Results in TFLOP/s. */
 int tdmrg_fp64_peak(int device, double* dmma_tflops, double* dfma_tflops);
 
+/* Failure-path check of the bounded device waits: one block on the context's stream polls a device
+ * word that nothing sets, at most `spins` times, then records a timeout in the context's status word
+ * the way the library's mbarrier and grid-barrier waits do, and returns.  The call synchronises the
+ * stream and returns TDMRG_ETIMEOUT (the status is consumed, so the context stays usable).
+ * Errors: EINVAL (spins outside 1..2^26), ENOMEM, ECUDA. */
+int tdmrg_probe_wait(tdmrg_ctx* ctx, int64_t spins);
+
 #ifdef __cplusplus
 }
 #endif

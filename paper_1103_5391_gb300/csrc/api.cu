@@ -146,8 +146,8 @@ int check_device_status(tdmrg_ctx* c) {
     if (rc) return rc;
     if (st) {
         cudaMemset(c->dstatus, 0, sizeof(int));
-        return fail(c, TDMRG_ETIMEOUT, "a bounded device wait ran out (tensor-core mbarrier or Lanczos grid barrier); "
-                                       "results are invalid");
+        return fail(c, TDMRG_ETIMEOUT, "a bounded device wait ran out (tensor-core mbarrier, Lanczos grid barrier or "
+                                       "the wait probe); results are invalid");
     }
     return TDMRG_OK;
 }
@@ -461,6 +461,38 @@ int tdmrg_hpsi_flops(tdmrg_ctx* c, int a, int b, double* flops) {
     if (rc) return rc;
     *flops = p->flops;
     return TDMRG_OK;
+}
+
+namespace {
+// polls a word that nothing sets; gives up after `spins` polls like every bounded wait of the library
+__global__ void k_wait_probe(const volatile int* flag, int* status, long long spins) {
+    if (threadIdx.x != 0) return;
+    long long it = 0;
+    while (*flag == 0) {
+        if (++it > spins) {
+            atomicOr(status, 4);
+            break;
+        }
+    }
+}
+}  // namespace
+
+int tdmrg_probe_wait(tdmrg_ctx* c, int64_t spins) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (spins < 1 || spins > (int64_t(1) << 26)) return fail(c, TDMRG_EINVAL, "probe_wait: spins must be in 1..2^26");
+    DeviceGuard g(c->opts.device);
+    int* flag = nullptr;
+    int rc = dev_alloc(c, (void**)&flag, sizeof(int), "probe flag");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream), "probe flag");
+    if (!rc) {
+        k_wait_probe<<<1, 32, 0, c->stream>>>(flag, c->dstatus, (long long)spins);
+        c->launches++;
+        rc = cuda_check(c, cudaGetLastError(), "probe launch");
+    }
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "probe wait");
+    dev_free(c, flag, sizeof(int));
+    return rc ? rc : check_device_status(c);
 }
 
 int tdmrg_set_schedule(tdmrg_ctx* c, int mode) {

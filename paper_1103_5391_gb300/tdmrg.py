@@ -22,7 +22,7 @@ EXPORTED = [
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect",
     "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
-    "tdmrg_set_schedule",
+    "tdmrg_set_schedule", "tdmrg_probe_wait",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
@@ -83,6 +83,7 @@ def load(path=LIB_PATH):
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_launch_count": (I, [P, PI64]),
         "tdmrg_set_schedule": (I, [P, I]),
+        "tdmrg_probe_wait": (I, [P, I64]),
         "tdmrg_hpsi_flops": (I, [P, I, I, PD]),
         "tdmrg_hpsi_tensor_flops": (I, [P, I, I, PD]),
         "tdmrg_fp64_peak": (I, [I, PD, PD]),
@@ -249,6 +250,10 @@ def tdmrg_rho_eig(ctx, rho, evals, evecs):
 
 def tdmrg_expect(ctx, opL, opR, Q, psi, out):
     return _check(ctx, load().tdmrg_expect(ctx, opL, opR, Q[0], Q[1], _ptr(psi), _ptr(out)))
+
+
+def tdmrg_probe_wait(ctx, spins):
+    return _check(ctx, load().tdmrg_probe_wait(ctx, spins))
 
 
 def tdmrg_set_schedule(ctx, mode):

@@ -49,3 +49,31 @@ def test_error_codes():
         assert e.value.code == T.TDMRG_ENOMEM
     finally:
         T.tdmrg_destroy(small)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait on a word that nothing sets gives up after its bound and reports TDMRG_ETIMEOUT
+    through the context's status word; the context keeps working and its results are unchanged."""
+    from paper_1103_5391_gb300 import problem
+    from paper_1103_5391_gb300 import tdmrg as T
+    ss = S.make_synthetic(12, 60, 4.0, nbonds=1, seed=5)
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = T.tdmrg_sector_size(ctx, ss.Q1)
+        x = dev(np.random.default_rng(4).standard_normal(n) + 0j)
+        y0, y1 = dev(np.zeros(n)), dev(np.zeros(n))
+        T.tdmrg_apply_h(ctx, ss.Q1, x, y0)
+        with pytest.raises(T.TdmrgError) as e:
+            T.tdmrg_probe_wait(ctx, 100000)
+        assert e.value.code == T.TDMRG_ETIMEOUT
+        assert "bounded device wait" in T.tdmrg_last_error(ctx)
+        with pytest.raises(T.TdmrgError) as e:
+            T.tdmrg_probe_wait(ctx, 0)
+        assert e.value.code == T.TDMRG_EINVAL
+        T.tdmrg_apply_h(ctx, ss.Q1, x, y1)
+        assert np.array_equal(y0.cpu().numpy(), y1.cpu().numpy())
+        T.tdmrg_evolve(ctx, ss.Q1, dev(ss.phi), [0.0, 0.05], 8, [dev(np.zeros(n)), dev(np.zeros(n))])
+        T.tdmrg_evolve_info(ctx)   # the status word was consumed: no stale timeout
+    finally:
+        T.tdmrg_destroy(ctx)
