@@ -178,6 +178,14 @@ int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg
 int tdmrg_expect(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdmrg_c64* psi_d,
                  tdmrg_c64* out_d);
 
+/* out_d[0] = <phi1| opL opR |phi2>, not normalised: the two-state form of Eq. generalcorrelation with
+ * one local operator per block (-1 = identity on that block), e.g. one entry of a Green's function
+ * <phi(t)| c_i c^dag_j |psi(t)> (Sec. I).  phi2_d lives in sector Q2 = (n_up2, n_dn2); opL opR (with
+ * the fermion sign of tdmrg_apply_op) maps it to Q1 = (n_up1, n_dn1), the sector of phi1_d.  The
+ * product uses a library-owned scratch vector and a fixed-order FP64 reduction.  Errors as apply_op. */
+int tdmrg_overlap_op(tdmrg_ctx* ctx, int opL, int opR, int n_up1, int n_dn1, const tdmrg_c64* phi1_d,
+                     int n_up2, int n_dn2, const tdmrg_c64* phi2_d, tdmrg_c64* out_d);
+
 /* ---- serving: continuous batching of time-evolution jobs ----------------------------------------
  * A server drives many independent time evolutions (each the repeated time step of Sec. II.C:
  * Krylov advance with n_v targets, weighted rho_L of the ground state and the targets with its

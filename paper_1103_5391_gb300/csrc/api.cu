@@ -520,4 +520,21 @@ int tdmrg_expect(tdmrg_ctx* c, int opL, int opR, int a, int b, const tdmrg_c64* 
                       "expect reduction");
 }
 
+int tdmrg_overlap_op(tdmrg_ctx* c, int opL, int opR, int a1, int b1, const tdmrg_c64* phi1, int a2, int b2,
+                     const tdmrg_c64* phi2, tdmrg_c64* out) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!phi1 || !phi2 || !out) return fail(c, TDMRG_EINVAL, "overlap_op: null pointer");
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "overlap_op: blocks not set");
+    const int64_t n1 = sector_size(c, a1, b1);
+    if (n1 == 0 || sector_size(c, a2, b2) == 0) return fail(c, TDMRG_ESECTOR, "overlap_op: empty sector");
+    DeviceGuard g(c->opts.device);
+    int rc = ensure_tmp(c, n1);
+    if (rc) return rc;
+    rc = tdmrg_apply_op(c, opL, opR, a2, b2, phi2, a1, b1, (tdmrg_c64*)c->tmp);   // opL opR phi2, in Q1
+    if (rc) return rc;
+    c->launches += 2;
+    return cuda_check(c, launch_dot_final((const cplx*)phi1, c->tmp, n1, c->red, kRedBlocks, (cplx*)out, 0, c->stream),
+                      "overlap_op reduction");
+}
+
 }  // extern "C"

@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect", "tdmrg_overlap_op",
     "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -81,6 +81,7 @@ def load(path=LIB_PATH):
         "tdmrg_density_matrix": (I, [P, I, PI32, ctypes.POINTER(P), PD, P]),
         "tdmrg_rho_eig": (I, [P, P, P, P]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
+        "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
         "tdmrg_launch_count": (I, [P, PI64]),
         "tdmrg_set_schedule": (I, [P, I]),
         "tdmrg_probe_wait": (I, [P, I64]),
@@ -250,6 +251,12 @@ def tdmrg_rho_eig(ctx, rho, evals, evecs):
 
 def tdmrg_expect(ctx, opL, opR, Q, psi, out):
     return _check(ctx, load().tdmrg_expect(ctx, opL, opR, Q[0], Q[1], _ptr(psi), _ptr(out)))
+
+
+def tdmrg_overlap_op(ctx, opL, opR, Q1, phi1, Q2, phi2, out):
+    """out[0] = <phi1| opL opR |phi2> (phi2 in sector Q2, phi1 in the sector Q1 the operators lead to)."""
+    return _check(ctx, load().tdmrg_overlap_op(ctx, opL, opR, Q1[0], Q1[1], _ptr(phi1), Q2[0], Q2[1], _ptr(phi2),
+                                               _ptr(out)))
 
 
 def tdmrg_probe_wait(ctx, spins):

@@ -137,3 +137,38 @@ def test_expect(lib):
             assert abs(host(out)[0] - want) < 1e-14
     finally:
         lib.tdmrg_destroy(ctx)
+
+
+def test_overlap_op(lib):
+    """<phi1| A (x) B |phi2> between different states and sectors (the two-state form of
+    Eq. generalcorrelation): a left creation operator, the right excitation operator and a hopping
+    across the cut, against the oracle's operator application and inner product."""
+    from paper_1103_5391_gb300 import problem
+    from oracle import blocks as oblocks
+    ss = S.make_synthetic(16, 120, 4.0, nbonds=1, seed=37)
+    sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
+    assert tuple(ss.Q1) == (ss.Q0[0] + 1, ss.Q0[1])   # the excited sector has one more up electron
+    rng = np.random.default_rng(9)
+    n0, n1 = ss.sector_size(ss.Q0), ss.sector_size(ss.Q1)
+    phi_q1 = rng.standard_normal(n1) + 1j * rng.standard_normal(n1)
+    phi_q0 = rng.standard_normal(n0) + 1j * rng.standard_normal(n0)
+    cdagL = oblocks.BlockOp(ss.cdagL[0][0], True)
+    cR = oblocks.BlockOp(ss.cR[0][0], True)
+    exc = oblocks.BlockOp(ss.cdag_exc, True)
+    cases = [  # (opL, opR, oracle A, oracle B, Q of phi1, phi1)
+        (problem.OP_CDAG, -1, cdagL, None, ss.Q1, phi_q1),
+        (-1, problem.OP_EXC, None, exc, ss.Q1, phi_q1),
+        (problem.OP_CDAG, problem.OP_CDAG, cdagL, cR, ss.Q0, phi_q0),   # c^dag_L c_R: hop across the cut
+    ]
+    ctx = new_ctx()
+    try:
+        problem.load_synthetic(ctx, ss)
+        out = dev(np.zeros(1))
+        for opL, opR, A, B, Qo, phi1 in cases:
+            lib.tdmrg_overlap_op(ctx, opL, opR, Qo, dev(phi1), ss.Q0, dev(ss.psi_gs), out)
+            want = np.vdot(phi1, superblock.apply_op(sb, A, B, ss.Q0, ss.psi_gs, Qo))
+            assert abs(host(out)[0] - want) < 1e-12 * np.linalg.norm(phi1), (opL, opR)
+        with pytest.raises(lib.TdmrgError):   # phi1 sector does not match where the operator leads
+            lib.tdmrg_overlap_op(ctx, 123, -1, ss.Q1, dev(phi_q1), ss.Q0, dev(ss.psi_gs), out)
+    finally:
+        lib.tdmrg_destroy(ctx)
