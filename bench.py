@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="only apply H psi N times on the workload (a short run for ncu captures)")
+    ap.add_argument("--precision-errors", action="store_true",
+                    help="errors of the tensor path (S = 2..6 slices) against the FP64 path on the L=48 m=1000 chain")
     return ap.parse_args()
 
 
@@ -598,12 +600,54 @@ def run_profile_hpsi(args):
     return 0
 
 
+def run_precision_errors(args):
+    """Relative errors of H psi and of one time step's targets on the tensor path with S = 2..6 slices,
+    against the FP64 GPU path (itself checked against the oracle in the tests), on the L=48 U=10 m=1000
+    chain twin (tau = 0.02, n_v = 4, n_K = 10)."""
+    import torch
+    from paper_1103_5391_gb300 import problem, tdmrg as T
+    from workloads import sectors
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ss = sectors.make_synthetic(48, 1000, 10.0, nbonds=1, seed=sectors.SEED_BASE + 4)
+    times = [x * 0.02 / 3 for x in range(4)]
+    g = torch.Generator(device="cpu").manual_seed(11)
+    res = {}
+    for S in (0, 2, 3, 4, 5, 6):   # 0: the FP64 path
+        prec = T.TDMRG_FP64 if S == 0 else T.TDMRG_OZAKI_BF16
+        ctx = T.tdmrg_create(device=0, stream=stream.cuda_stream, prec=prec, ozaki_slices=S if S else 4)
+        try:
+            problem.load_synthetic(ctx, ss)
+            n = T.tdmrg_sector_size(ctx, ss.Q1)
+            if S == 0:
+                x = torch.complex(torch.randn(n, generator=g, dtype=torch.float64),
+                                  torch.randn(n, generator=g, dtype=torch.float64)).cuda()
+                phi = torch.as_tensor(ss.phi).cuda()
+            y = torch.zeros_like(x)
+            T.tdmrg_apply_h(ctx, ss.Q1, x, y)
+            tg = [torch.zeros_like(phi) for _ in times]
+            T.tdmrg_evolve(ctx, ss.Q1, phi, times, 10, tg)
+            torch.cuda.synchronize()
+            if S == 0:
+                y0, t0 = y, tg[-1]
+            else:
+                res[S] = {"hpsi": float((y - y0).abs().max() / y0.abs().max()),
+                          "target": float((tg[-1] - t0).abs().max() / t0.abs().max())}
+        finally:
+            T.tdmrg_destroy(ctx)
+    print(json.dumps({"precision_errors": res, "workload": "L=48 U=10 m=1000 chain twin, D = %d" % n,
+                      "reference": "FP64 GPU path", "step": "tau = 0.02, n_v = 4, n_K = 10"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_hpsi > 0:
         return run_profile_hpsi(args)
+    if args.precision_errors:
+        return run_precision_errors(args)
     if args.serving:
         return run_serving(args)
     return run_ours(args)
