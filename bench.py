@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--jobs", type=int, default=24)
     ap.add_argument("--job-steps", type=int, default=20)
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--job-lmax", type=int, default=48, help="serving: largest L of a job (even, >= 16)")
+    ap.add_argument("--job-mmax", type=int, default=768, help="serving: largest m of a job (>= 128)")
+    ap.add_argument("--gap-ms", type=float, default=20.0, help="serving: mean inter-arrival time")
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="only apply H psi N times on the workload (a short run for ncu captures)")
     ap.add_argument("--precision-errors", action="store_true",
@@ -518,10 +521,10 @@ def run_serving(args):
     rng = np.random.default_rng(S.SEED_BASE + 4)
     jobs, t_gen = [], time.perf_counter()
     for k in range(args.jobs):
-        L = int(rng.choice(np.arange(16, 50, 2)))
+        L = int(rng.choice(np.arange(16, args.job_lmax + 2, 2)))
         ladder = bool(rng.integers(2))
         U = float(rng.choice([2.0, 4.0, 8.0]))
-        m = int(round(np.exp(rng.uniform(np.log(128), np.log(768)))))
+        m = int(round(np.exp(rng.uniform(np.log(128), np.log(args.job_mmax)))))
         ss = S.make_synthetic(L, m, U, nbonds=2 if ladder else 1, seed=S.SEED_BASE + 100 + k)
         ctx = T.tdmrg_create(device=0, stream=torch.cuda.current_stream().cuda_stream, prec=T.TDMRG_OZAKI_BF16,
                              ozaki_slices=args.slices)
@@ -532,7 +535,7 @@ def run_serving(args):
         jobs.append(dict(L=L, ladder=ladder, U=U, m=m, ss=ss, ctx=ctx, psi=psi, phi=phi))
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    gaps = rng.exponential(0.02, args.jobs)       # mean inter-arrival 20 ms
+    gaps = rng.exponential(args.gap_ms * 1e-3, args.jobs)
     srv = T.tdmrg_server_create(0, 0, args.max_active)
     nk, steps = WL["nk"], args.job_steps
     ids, peak_running = [], 0
@@ -563,8 +566,9 @@ def run_serving(args):
         T.tdmrg_destroy(jb["ctx"])
     line = {"metric": "serving mix: Krylov steps/s and per-step latency", "value": ok * steps * nk / makespan,
             "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": f"Poisson stream of {args.jobs} jobs (mean inter-arrival 20 ms), chains and 2-leg "
-                                   f"ladders L in [16, 48], U in {{2, 4, 8}}, m log-uniform in [128, 768], tau=0.05, "
+            "config": {"workload": f"Poisson stream of {args.jobs} jobs (mean inter-arrival {args.gap_ms:g} ms), chains and "
+                                   f"2-leg ladders L in [16, {args.job_lmax}], U in {{2, 4, 8}}, m log-uniform in "
+                                   f"[128, {args.job_mmax}], tau=0.05, "
                                    f"n_v=4, n_K=10, {steps} time steps each, ozaki-bf16 x{args.slices}",
                        "max_active": args.max_active},
             "jobs_done": ok, "makespan_s": makespan, "peak_running": peak_running,
