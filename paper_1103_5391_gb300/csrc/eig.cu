@@ -4,16 +4,18 @@
 // sector would take milliseconds for the largest sectors.  Instead:
 //   1. seed: a cyclic two-sided Jacobi in FP32 per sector (one CTA per sector, parallel round-robin
 //      ordering of disjoint rotations), giving eigenvectors X0 accurate to about 1e-6;
-//   2. refine: iterative refinement for Hermitian eigenproblems (Ogita & Aishima, 2018), whose FP64
-//      work is three grouped GEMMs per iteration spread over every SM:
+//   2. refine: iterative refinement for Hermitian eigenproblems (Ogita & Aishima, 2018), whose work is
+//      grouped GEMMs spread over every SM (FP64, except the small correction E^H W in FP32):
 //         G = X^H X,  S = X^H (rho X),  lambda_i = Re S_ii / Re G_ii,  R = I - G,
 //         E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta,
 //         E_ij = R_ij / 2 otherwise (and on the diagonal),  delta = 2 (||S - diag(lambda)|| + ||rho|| ||R||),
 //         X <- X (I + E);
 //      convergence is quadratic: from the FP32 seed (error ~1e-5) two iterations reach rounding level;
-//      a third and a fourth run (decided on the device, launched regardless) while the last correction
-//      is above 1e-7, as for near-degenerate pairs that the first iteration treats as a cluster.  The
-//      iterate is kept as W = X^H, so every product is a plain or conjugate-transposed GEMM operand;
+//      up to four more run (decided on the device, launched regardless) while the last correction is
+//      above 1e-7, as for near-degenerate pairs that the first iteration treats as a cluster.  At
+//      iterations 1 and 3 a sector whose clustered pairs stay coupled is re-seeded instead (FP32 Jacobi
+//      on S with a relative criterion, k_jacobi32).  The iterate is kept as W = X^H, so every product
+//      is a plain or conjugate-transposed GEMM operand;
 //   3. sort each sector's eigenpairs by descending eigenvalue.
 #include <algorithm>
 #include <cmath>
