@@ -146,3 +146,41 @@ def test_unordered_times(lib):
         assert abs(err_gpu - err) <= 1e-8 * err + 1e-300
     finally:
         lib.tdmrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_time_dependent_hamiltonian(lib, mixed):
+    """H(t) driven from the host: one time step under H, then the boundary hopping is changed to a
+    weaker, Peierls-phased amplitude a = 0.5 t e^{0.7 i} (its Hermitian partner -conj(a)) by setting
+    the Hamiltonian again, and a second step follows.  Both steps against the oracle with the same
+    coefficients (the plans are rebuilt for the new terms)."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(16, 120, 4.0, nbonds=1, seed=S.SEED_BASE + 8)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    a = 0.5 * ss.coeff_t * np.exp(0.7j)
+    conns2 = [((a if i % 2 == 0 else -np.conj(a)), A, B) for i, (_, A, B) in enumerate(conns)]
+    times = krylov.target_times(0.05, 4)
+    h1 = lambda v: superblock.apply_h(sb, HL, HR, conns, ss.Q1, v)
+    h2 = lambda v: superblock.apply_h(sb, HL, HR, conns2, ss.Q1, v)
+    ref1, _, _ = krylov.evolve(h1, ss.phi, times, 10)
+    ref2, _, _ = krylov.evolve(h2, ref1[-1], times, 10)
+    kw = dict(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=5) if mixed else {}
+    ctx = new_ctx(**kw)
+    try:
+        gconns = problem.load_synthetic(ctx, ss)
+        n = lib.tdmrg_sector_size(ctx, ss.Q1)
+        phi = dev(ss.phi)
+        tg = [dev(np.zeros(n)) for _ in times]
+        lib.tdmrg_evolve(ctx, ss.Q1, phi, times, 10, tg)
+        assert rel_err(host(tg[-1]), ref1[-1]) < (1e-8 if mixed else 1e-10)
+        lib.tdmrg_set_hamiltonian(ctx, problem.OP_H, problem.OP_H,
+                                  [(l, r, (a if i % 2 == 0 else -np.conj(a))) for i, (l, r, _) in enumerate(gconns)])
+        tg2 = [dev(np.zeros(n)) for _ in times]
+        lib.tdmrg_evolve(ctx, ss.Q1, tg[-1], times, 10, tg2)
+        for x in range(len(times)):
+            assert rel_err(host(tg2[x]), ref2[x]) < (1e-8 if mixed else 1e-10), x
+        # the pulse changed the dynamics: the second step differs from evolving under the old H
+        ref_old, _, _ = krylov.evolve(h1, ref1[-1], times, 10)
+        assert rel_err(ref2[-1], ref_old[-1]) > 1e-4
+    finally:
+        lib.tdmrg_destroy(ctx)
