@@ -79,3 +79,21 @@ def test_c1_trajectory_against_ed(c1_problem, c1_ground):
         assert abs(np.vdot(last, last).real - n0) < 1e-12
         assert abs(np.vdot(last, hphi(last)).real - e0) < 1e-10 * max(1, abs(e0))
         assert err < 1e-8
+
+
+def test_error_estimate_bounds_the_true_error():
+    """The a-posteriori estimate ||phi|| beta_n |[e^{-iT t}]_{n-1,0}| (Saad) against the exact error
+    from expm on a random Hermitian matrix with spectrum in about [-1, 1]: it stays above the true
+    error and within a factor 30 of it, for several times and Krylov dimensions."""
+    import scipy.linalg as sl
+    rng = np.random.default_rng(2)
+    n = 300
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = (A + A.conj().T) / np.sqrt(8 * n)
+    phi = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for t in (0.5, 1.0, 2.0):
+        exact = sl.expm(-1j * H * t) @ phi
+        for nk in (6, 8, 10, 12):
+            targets, n_used, err = krylov.evolve(lambda v: H @ v, phi, [0.0, t], nk)
+            true = np.linalg.norm(targets[-1] - exact)
+            assert true <= err <= 30.0 * true, (t, nk, err, true)
