@@ -35,11 +35,25 @@ if ROOT not in sys.path:
 
 METRIC = "Krylov steps/s & Hψ TFLOP/s vs plain FP64 GPU at ≤1e-8 error; p50/p99 step latency"
 UNIT = "Krylov steps/s"
-WL = dict(L=32, m=400, U=4.0, t=1.0, nbonds=1, tau=0.05, n_v=4, nk=10)
-WORKLOAD_NAME = "1D Hubbard chain L=32 U=4 half filling m=400 superblock (synthetic Gaussian-sector twin), " \
-                "c^dag excitation, tau=0.05, n_v=4, n_K=10, complex128"
+# The bench workloads (synthetic Gaussian-sector twins of truncated DMRG superblocks at the central
+# cut, complex128, c^dag excitation on the first right site).  C2 is the headline; C3 and C4 are
+# measured beside it.
+CONFIGS = {
+    "C2": dict(L=32, m=400, U=4.0, t=1.0, nbonds=1, tau=0.05, n_v=4, nk=10, seed_index=1,
+               name="1D Hubbard chain L=32 U=4 half filling m=400 superblock (synthetic Gaussian-sector twin), "
+                    "c^dag excitation, tau=0.05, n_v=4, n_K=10, complex128"),
+    "C3": dict(L=32, m=800, U=8.0, t=1.0, nbonds=2, tau=0.05, n_v=4, nk=10, seed_index=2,
+               name="2x16 Hubbard ladder U=8 half filling m=800 superblock (synthetic twin, 2 bonds across the cut), "
+                    "c^dag excitation, tau=0.05, n_v=4, n_K=10, complex128"),
+    "C4": dict(L=48, m=1000, U=10.0, t=1.0, nbonds=1, tau=0.02, n_v=4, nk=10, seed_index=4,
+               name="1D Hubbard chain L=48 U=10 half filling m=1000 superblock (synthetic twin), "
+                    "c^dag excitation, tau=0.02, n_v=4, n_K=10, complex128"),
+}
+WL = CONFIGS["C2"]
+WORKLOAD_NAME = WL["name"]
 FLUSH_BYTES = 256 << 20
-BF16_BURST = 1923.8   # TFLOP/s, dense bf16 burst measured on the GB300s (cuBLAS)
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # DRAM bytes of one tensor-path H psi, from an ncu capture summarised in this file; valid only while the
 # kernels, plans and workload generator are byte-identical to those captured (digest below)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_hpsi_ozaki_L32_m400_chain.md")
@@ -72,6 +86,17 @@ def hpsi_traffic():
                             + os.path.relpath(TRAFFIC_FILE, ROOT) + ")"
 
 
+def measured_peaks():
+    """(peaks dict, source): the measured copy bandwidth and bf16 GEMM rates of this GPU pool, or the
+    fallback figures when the measurement file is absent."""
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}, "of measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return dict(FALLBACK_PEAKS), "of fallback (no MEASURED_PEAKS.json)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -79,6 +104,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="C2",
+                    help="workload of the headline line (C2 by default; C3 and C4 are also measured beside C2)")
+    ap.add_argument("--no-other-configs", action="store_true", help="measure the headline workload only")
+    ap.add_argument("--oracle-rate", metavar="CONFIG", default=None,
+                    help="(internal) time the oracle's step on CONFIG in this process and print one JSON line")
     ap.add_argument("--prec", choices=["ozaki", "fp64"], default="ozaki")
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--serving", action="store_true", help="serving mix instead of the single-workload line")
@@ -95,23 +125,25 @@ def parse():
     return ap.parse_args()
 
 
-def workload():
+def workload(wl=WL):
     from workloads import sectors as S
-    return S.make_synthetic(WL["L"], WL["m"], WL["U"], t=WL["t"], nbonds=WL["nbonds"], seed=S.SEED_BASE + 1)
+    return S.make_synthetic(wl["L"], wl["m"], wl["U"], t=wl["t"], nbonds=wl["nbonds"], seed=S.SEED_BASE + wl["seed_index"])
 
 
-def algorithmic_hpsi_flops(ss, Q):
-    """8 flops per complex MAC, cheaper association per two-sided term, one GEMM per block term."""
+def _pairs(ss, Q):
     ridx = {q: k for k, q in enumerate(ss.rsec)}
     pair = {}
     for qi, q in enumerate(ss.lsec):
         ri = ridx.get((Q[0] - q[0], Q[1] - q[1]))
         if ri is not None:
             pair[qi] = ri
-    fl = 0.0
-    for qi, ri in pair.items():
-        dl, dr = ss.ldim[qi], ss.rdim[ri]
-        fl += 8.0 * (dl * dl * dr + dl * dr * dr)
+    return pair
+
+
+def _connection_blocks(ss, pair):
+    """(dL_out, dL_in, dR_in, dR_out) of every sector-pair product of the boundary terms (both halves of
+    each hopping, both spins, every bond)."""
+    out = []
     for b in range(ss.nbonds):
         for s in range(2):
             for A, B in ((ss.cdagL[b][s], ss.cR[b][s]),
@@ -122,9 +154,30 @@ def algorithmic_hpsi_flops(ss, Q):
                     ri, ro = pair[qi], pair[qo]
                     if (ro, ri) not in B:
                         continue
-                    a, b_, c, d = ss.ldim[qo], ss.ldim[qi], ss.rdim[ri], ss.rdim[ro]
-                    fl += 8.0 * min(b_ * c * d + a * b_ * d, a * b_ * c + a * c * d)
+                    out.append((ss.ldim[qo], ss.ldim[qi], ss.rdim[ri], ss.rdim[ro]))
+    return out
+
+
+def algorithmic_hpsi_flops(ss, Q):
+    """8 flops per complex MAC, cheaper association per two-sided term, one GEMM per block term."""
+    pair = _pairs(ss, Q)
+    fl = 0.0
+    for qi, ri in pair.items():
+        dl, dr = ss.ldim[qi], ss.rdim[ri]
+        fl += 8.0 * (dl * dl * dr + dl * dr * dr)
+    for a, b_, c, d in _connection_blocks(ss, pair):
+        fl += 8.0 * min(b_ * c * d + a * b_ * d, a * b_ * c + a * c * d)
     return fl
+
+
+def algorithmic_hpsi_bytes(ss, Q):
+    """Lower bound of the DRAM bytes of one H psi: read psi and write H psi once (16 D each) and read
+    every operator block the product uses once (complex128)."""
+    pair = _pairs(ss, Q)
+    D = sum(ss.ldim[qi] * ss.rdim[ri] for qi, ri in pair.items())
+    ops = sum(ss.ldim[qi] ** 2 + ss.rdim[ri] ** 2 for qi, ri in pair.items())
+    ops += sum(a * b_ + c * d for a, b_, c, d in _connection_blocks(ss, pair))
+    return 32.0 * D + 16.0 * ops
 
 
 def blas_threads():
@@ -144,11 +197,11 @@ def blas_threads():
 class OracleStep:
     """One time step of the CPU oracle on the same workload (FP64 NumPy)."""
 
-    def __init__(self, ss):
+    def __init__(self, ss, wl=WL):
         from oracle import blocks as oblocks
         from oracle import density, krylov, superblock
         self.k, self.d, self.s = krylov, density, superblock
-        self.ss = ss
+        self.ss, self.wl = ss, wl
         self.sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
         self.HL, self.HR = oblocks.BlockOp(ss.HL, False), oblocks.BlockOp(ss.HR, False)
         self.conns = []
@@ -159,13 +212,13 @@ class OracleStep:
         self.nL, self.nR = oblocks.BlockOp(ss.nL, False), oblocks.BlockOp(ss.nR, False)
         exc = oblocks.BlockOp(ss.cdag_exc, True)
         self.phi = superblock.apply_op(self.sb, None, exc, ss.Q0, ss.psi_gs, ss.Q1)
-        self.times = krylov.target_times(WL["tau"], WL["n_v"])
-        self.wgs, self.w = density.tst_weights(WL["n_v"])
+        self.times = krylov.target_times(wl["tau"], wl["n_v"])
+        self.wgs, self.w = density.tst_weights(wl["n_v"])
 
     def step(self):
         Q = self.ss.Q1
         hf = lambda v: self.s.apply_h(self.sb, self.HL, self.HR, self.conns, Q, v)
-        targets, n_used, err = self.k.evolve(hf, self.phi, self.times, WL["nk"])
+        targets, n_used, err = self.k.evolve(hf, self.phi, self.times, self.wl["nk"])
         rho = self.d.rho_left(self.sb, [(self.ss.Q0, self.ss.psi_gs)] + [(Q, t) for t in targets], [self.wgs] + self.w)
         self.d.rho_eig(rho)
         self.s.expect(self.sb, self.nL, None, Q, targets[-1])
@@ -174,17 +227,74 @@ class OracleStep:
         return n_used
 
 
-def cpu_baseline(ss, budget_s=12.0, max_steps=1000):
-    st = OracleStep(ss)
-    t0 = time.perf_counter()
-    ks, n = 0, 0
-    while n < max_steps and (time.perf_counter() - t0) < budget_s:
-        ks += st.step()
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": ks / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": f"{n} oracle time step(s) of the same workload ({ks} Krylov steps, rho_L + eig + 2 observables "
-                      f"each) in {dt:.1f} s, FP64 NumPy on the host"}
+def host_cpu():
+    """(logical CPUs this process may run on, CPU model name)."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return n, model or platform.machine()
+
+
+def oracle_rate(ss, wl, block_s=1.6, reps=5):
+    """Best of `reps` blocks (each at least block_s seconds of whole oracle time steps, after one
+    warm-up step) in Krylov steps/s; also the steps and seconds of all blocks."""
+    st = OracleStep(ss, wl)
+    st.step()
+    best, ks_all, n_all, t_all = 0.0, 0, 0, 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ks = n = 0
+        while n == 0 or time.perf_counter() - t0 < block_s:
+            ks += st.step()
+            n += 1
+        dt = time.perf_counter() - t0
+        best = max(best, ks / dt)
+        ks_all, n_all, t_all = ks_all + ks, n_all + n, t_all + dt
+    return best, n_all, ks_all, t_all
+
+
+def oracle_rate_one_core(key):
+    """The same measurement in a child process pinned to one CPU with one BLAS thread."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cpu0 = min(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None
+    pin = (lambda: os.sched_setaffinity(0, {cpu0})) if cpu0 is not None else None
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate", key], env=env,
+                           preexec_fn=pin, capture_output=True, text=True, timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:
+        return {"error": f"one-core oracle run failed: {e}"}
+
+
+def cpu_baseline(ss, key="C2"):
+    """The oracle's time step on the host: all cores (BLAS threads = cores) and one core, best of 5."""
+    wl = CONFIGS[key]
+    ncpu, model = host_cpu()
+    best, n, ks, dt = oracle_rate(ss, wl)
+    one = oracle_rate_one_core(key)
+    return {"value": best, "unit": UNIT, "cores": ncpu, "kind": "oracle", "cpu_model": model, "nproc": ncpu,
+            "blas_threads": blas_threads(),
+            "one_core": one.get("value"), "one_core_note": one.get("sample", one.get("error")),
+            "sample": f"best of 5 blocks (>= 1.6 s each) of whole oracle time steps of the same workload "
+                      f"(n_K Krylov steps + rho_L + eig + 2 observables per time step): {n} time steps, {ks} Krylov "
+                      f"steps in {dt:.1f} s; FP64 NumPy on {ncpu} host cores ({model})"}
 
 
 class ClockSampler:
@@ -228,6 +338,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def config_dict(wl):
+    return {"workload": wl["name"], **{k: wl[k] for k in ("L", "m", "U", "t", "nbonds", "tau", "n_v", "nk")}}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -253,8 +367,9 @@ def run_reference(args):
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD_NAME, **WL, "l2": "n/a (host)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "config": {**config_dict(WL), "l2": "n/a (host)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": host_cpu()[0], "cpu_model": host_cpu()[1],
+                             "blas_threads": blas_threads(), "kind": "oracle",
                              "sample": f"{args.steps} oracle time steps ({ks} Krylov steps) after {args.warmup} warm-up"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -264,7 +379,7 @@ def run_reference(args):
 class Runner:
     """Device buffers and one time step of the hot path through the C ABI."""
 
-    def __init__(self, T, problem, ctx, ss, dev, stream):
+    def __init__(self, T, problem, ctx, ss, dev, stream, wl=WL):
         import torch
         self.T, self.P, self.ctx, self.ss, self.stream = T, problem, ctx, ss, stream
         c128 = dict(dtype=torch.complex128, device=dev)
@@ -274,8 +389,8 @@ class Runner:
         self.phi = torch.zeros(self.n1, **c128)
         T.tdmrg_apply_op(ctx, -1, problem.OP_EXC, self.Q0, self.psi_gs, self.Q1, self.phi)   # phi = c^dag_j psi (Eq. b)
         self.phi0 = self.phi.clone()
-        self.nv, self.nk = WL["n_v"], WL["nk"]
-        self.times = [x * WL["tau"] / (self.nv - 1) for x in range(self.nv)]
+        self.nv, self.nk = wl["n_v"], wl["nk"]
+        self.times = [x * wl["tau"] / (self.nv - 1) for x in range(self.nv)]
         self.targets = [torch.zeros(self.n1, **c128) for _ in range(self.nv - 1)] + [self.phi]   # advance in place
         self.wgs, self.w = T.tdmrg_tst_weights(self.nv)
         self.nr, self.ne = T.tdmrg_rho_size(ctx)
@@ -377,6 +492,119 @@ def trajectory(torch, runner, steps):
     return torch.stack(out).cpu().numpy()
 
 
+def work_decomposition(T, ctx, ss, Q, slices, alg):
+    """Executed tensor flops of one H psi against the algorithmic count: the plan's association
+    (stage 1 then stage 2 for every two-sided term), the S(S+1)/2 slice products, and the padding of
+    sector blocks into MMA tiles."""
+    plan = T.tdmrg_hpsi_flops(ctx, Q)
+    tensor = T.tdmrg_hpsi_tensor_flops(ctx, Q)
+    groups = slices * (slices + 1) / 2
+    return {"alg_gflop": alg / 1e9, "plan_gflop": plan / 1e9, "executed_tensor_gflop": tensor / 1e9,
+            "executed_over_alg": tensor / alg if alg else None, "association_factor": plan / alg if alg else None,
+            "slice_factor": groups, "padding_factor": tensor / (plan * groups) if plan else None}
+
+
+def measure_config(args, torch, T, problem, key, dev, stream, flush, barrier, steps, headline=False):
+    """Steps/s of the tensor path and of the FP64 path on one workload, H psi alone on both, the
+    observable difference over a 20-step trajectory, and the roofline of H psi."""
+    wl = CONFIGS[key]
+    ss = workload(wl)
+    res = {"config": config_dict(wl)}
+    mixed = args.prec == "ozaki"
+    prec = T.TDMRG_OZAKI_BF16 if mixed else T.TDMRG_FP64
+    ctx = T.tdmrg_create(device=dev.index, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
+    try:
+        problem.load_synthetic(ctx, ss)
+        run = Runner(T, problem, ctx, ss, dev, stream, wl)
+        run.step()                      # compiles plans, allocates workspace
+        l0 = T.tdmrg_launch_count(ctx)
+        run.step()
+        res["launches_per_step"] = T.tdmrg_launch_count(ctx) - l0
+        run.capture(torch, stream)      # the timed step is one CUDA-graph replay of the same launches
+        for _ in range(args.warmup):
+            run.replay()
+        barrier()
+        sampler = ClockSampler(dev.index) if headline else None
+        if headline:
+            time.sleep(0.25)
+        step_ms = timed_steps(torch, run, steps, flush, stream, barrier, graph=True)
+        if headline:
+            res["clocks"] = sampler.stop()
+        T.tdmrg_evolve_info(ctx)   # raises if a bounded device wait ran out during the timed steps
+        res["step_ms"] = step_ms
+        res["value"] = run.nk * len(step_ms) / (sum(step_ms) * 1e-3)
+        srt = sorted(step_ms)
+        res["step_latency_ms"] = {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]}
+        Q1 = run.Q1
+        hx = torch.zeros(run.n1, dtype=torch.complex128, device=dev)
+        h_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
+        alg = algorithmic_hpsi_flops(ss, Q1)
+        alg_bytes = algorithmic_hpsi_bytes(ss, Q1)
+        res["D"] = run.n1
+        res["hpsi"] = {"ms": h_ms, "alg_tflops": alg / (h_ms * 1e-3) / 1e12, "alg_bytes": alg_bytes}
+        if mixed:
+            res["hpsi"]["work"] = work_decomposition(T, ctx, ss, Q1, args.slices, alg)
+        if headline:
+            res["run"] = run
+            res["ctx"] = ctx
+        # the plain FP64 GPU path on the same workload, and the observable difference to it
+        if mixed:
+            traj_steps = 20
+            traj_m = trajectory(torch, run, traj_steps)
+            T.tdmrg_set_precision(ctx, T.TDMRG_FP64, 4)
+            traj_f = trajectory(torch, run, traj_steps)
+            run.reset()
+            run.step()
+            run.capture(torch, stream)
+            for _ in range(2):
+                run.replay()
+            f_ms = timed_steps(torch, run, min(steps, 40), flush, stream, barrier, graph=True)
+            hf_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
+            res["vs_fp64_gpu"] = {"value": run.nk * len(f_ms) / (sum(f_ms) * 1e-3), "unit": UNIT,
+                                  "ms_per_step": statistics.mean(f_ms), "hpsi_ms": hf_ms,
+                                  "hpsi_tflops": alg / (hf_ms * 1e-3) / 1e12,
+                                  "speedup_steps": res["value"] / (run.nk * len(f_ms) / (sum(f_ms) * 1e-3)),
+                                  "obs_err": float(np.abs(traj_m - traj_f).max()), "obs_err_steps": traj_steps}
+            if headline:
+                T.tdmrg_set_precision(ctx, prec, args.slices)   # the e2e leg runs the headline path again
+                run.reset()
+                run.step()
+                run.capture(torch, stream)
+    finally:
+        if not headline:
+            T.tdmrg_destroy(ctx)
+    return res
+
+
+def roofline_of(res, mixed, peaks, peak_src, dmma_peak, dfma_peak, traffic=None, traffic_note=None):
+    """Roofline of H psi: algorithmic FP64-equivalent flops (cheaper association per term, 8 per complex
+    MAC) per H psi over its measured time, against the measured bf16 dense peak (tensor path) or the
+    FP64 MMA peak measured live (FP64 path)."""
+    h = res["hpsi"]
+    alg_tf = h["alg_tflops"]
+    if mixed:
+        roof = {"bound": "tensor", "achieved": alg_tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "peak_source": "bf16 dense burst " + peak_src,
+                "kernel": "H psi on the tensor path (bf16 slicing + tcgen05 GEMM launches of one product)",
+                "work": h.get("work")}
+        w = h.get("work") or {}
+        if w.get("executed_tensor_gflop"):
+            roof["executed_tensor_tflops"] = w["executed_tensor_gflop"] * 1e9 / (h["ms"] * 1e-3) / 1e12
+            roof["executed_frac"] = roof["executed_tensor_tflops"] / roof["peak"]
+    else:
+        roof = {"bound": "tensor", "achieved": alg_tf, "peak": dmma_peak, "unit": "TFLOP/s",
+                "peak_source": f"FP64 tensor MMA (mma.sync m8n8k4 f64) loop on every SM, measured live by "
+                               f"tdmrg_fp64_peak (not in MEASURED_PEAKS.json); DFMA {dfma_peak:.2f} TFLOP/s",
+                "kernel": "gemm_f64_kernel (H psi, 2 launches)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["alg_bytes"] = h["alg_bytes"]
+    roof["traffic"] = traffic
+    roof["traffic_source"] = traffic_note
+    roof["traffic_over_alg_bytes"] = traffic / h["alg_bytes"] if traffic else None
+    roof["hbm_frac_of_alg_bytes"] = h["alg_bytes"] / (h["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    return roof
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -391,13 +619,9 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ss = workload()
     mixed = args.prec == "ozaki"
-    prec = T.TDMRG_OZAKI_BF16 if mixed else T.TDMRG_FP64
-    ctx = T.tdmrg_create(device=local, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
-    problem.load_synthetic(ctx, ss)
-    run = Runner(T, problem, ctx, ss, dev, stream)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peaks, peak_src = measured_peaks()
 
     def barrier():
         if ws > 1:
@@ -405,29 +629,13 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    run.step()                      # compiles plans, allocates workspace
-    l0 = T.tdmrg_launch_count(ctx)
-    run.step()
-    launches_per_step = T.tdmrg_launch_count(ctx) - l0
-    run.capture(torch, stream)      # the timed step is one CUDA-graph replay of the same launches
-    for _ in range(args.warmup):
-        run.replay()
-    barrier()
-    sampler = ClockSampler(local)
-    time.sleep(0.25)
-    step_ms = timed_steps(torch, run, args.steps, flush, stream, barrier, graph=True)
-    launches = launches_per_step * args.steps
-    clocks = sampler.stop()
-    T.tdmrg_evolve_info(ctx)   # raises if a bounded device wait ran out during the timed steps
+    key = args.config
+    wl = CONFIGS[key]
+    res = measure_config(args, torch, T, problem, key, dev, stream, flush, barrier, args.steps, headline=True)
+    run, ctx = res.pop("run"), res.pop("ctx")
     nk = run.nk
-    value, total_ms = replica_value(sum(step_ms), nk * args.steps, ws, dev)
-
-    # H psi alone (all launches of one product), CUDA events on its stream, L2 flushed
-    Q1 = run.Q1
-    hx = torch.zeros(run.n1, dtype=torch.complex128, device=dev)
-    h_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
-    alg = algorithmic_hpsi_flops(ss, Q1)
-    tensor_fl = T.tdmrg_hpsi_tensor_flops(ctx, Q1)
+    value, total_ms = replica_value(sum(res["step_ms"]), nk * args.steps, ws, dev)
+    launches = res["launches_per_step"] * args.steps
     dmma_peak, dfma_peak = T.tdmrg_fp64_peak(local)
 
     # end to end through the C ABI with host buffers: H2D phi, step, D2H observables + rho_L spectrum
@@ -447,61 +655,43 @@ def run_ours(args):
         e1.record(stream)
     barrier()
     e2e_val, e2e_ms = replica_value(sum(a.elapsed_time(b) for a, b in ee), nk * e2e_steps, ws, dev)
-
-    # the plain FP64 GPU path on the same workload, and the observable error of this path against it
-    fp64 = None
-    if mixed and rank == 0:
-        traj_steps = 20
-        traj_m = trajectory(torch, run, traj_steps)
-        T.tdmrg_set_precision(ctx, T.TDMRG_FP64, 4)
-        traj_f = trajectory(torch, run, traj_steps)
-        run.reset()
-        run.step()
-        run.capture(torch, stream)
-        for _ in range(2):
-            run.replay()
-        f_ms = timed_steps(torch, run, min(args.steps, 40), flush, stream, barrier, graph=True)
-        hf_ms = time_hpsi(torch, T, ctx, Q1, run.phi0, hx, flush, stream)
-        fp64 = {"value": nk * len(f_ms) / (sum(f_ms) * 1e-3), "unit": UNIT, "ms_per_step": statistics.mean(f_ms),
-                "hpsi_ms": hf_ms, "hpsi_tflops": alg / (hf_ms * 1e-3) / 1e12,
-                "obs_err": float(np.abs(traj_m - traj_f).max()), "obs_err_steps": traj_steps}
     T.tdmrg_destroy(ctx)
+
+    others = {}
+    if rank == 0 and not args.no_other_configs and key == "C2":
+        for k2 in ("C3", "C4"):
+            r2 = measure_config(args, torch, T, problem, k2, dev, stream, flush, barrier, min(args.steps, 20))
+            r2["roofline"] = roofline_of(r2, mixed, peaks, peak_src, dmma_peak, dfma_peak)
+            r2.pop("step_ms")
+            others[k2] = r2
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(ss)
+        cpu = cpu_baseline(workload(wl), key)
     if rank == 0:
-        srt = sorted(step_ms)
-        if mixed:
-            traffic, traffic_note = hpsi_traffic()
-            roof = {"bound": "tensor", "achieved": tensor_fl / (h_ms * 1e-3) / 1e12, "peak": BF16_BURST, "unit": "TFLOP/s",
-                    "traffic": traffic, "traffic_source": traffic_note,
-                    "kernel": "H psi on the tensor path (bf16 slicing + tcgen05 GEMM, 4 launches)",
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS bf16)",
-                    "alg_fp64_equiv_tflops": alg / (h_ms * 1e-3) / 1e12}
-        else:
-            roof = {"bound": "tensor", "achieved": alg / (h_ms * 1e-3) / 1e12, "peak": dmma_peak, "unit": "TFLOP/s",
-                    "traffic": None, "kernel": "gemm_f64_kernel (H psi, 2 launches)",
-                    "peak_source": f"FP64 tensor MMA loop measured live (tdmrg_fp64_peak); DFMA {dfma_peak:.2f} TFLOP/s"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
+        traffic, traffic_note = hpsi_traffic() if (mixed and key == "C2") else (None, "no DRAM capture for this path")
+        roof = roofline_of(res, mixed, peaks, peak_src, dmma_peak, dfma_peak, traffic, traffic_note)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, **WL, "D": run.n1,
+            "config": {**config_dict(wl), "D": res["D"],
                        "prec": f"ozaki-bf16 x{args.slices} slices (tcgen05), FP64 Lanczos/eig" if mixed else "fp64",
                        "l2": f"flushed before every step ({FLUSH_BYTES >> 20} MB write)", "parallelism": "replicas"},
-            "step_latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
-            "hpsi": {"ms": h_ms, "alg_gflop": alg / 1e9, "tensor_gflop": tensor_fl / 1e9,
-                     "alg_tflops": alg / (h_ms * 1e-3) / 1e12},
-            "vs_fp64_gpu": fp64,
+            "step_latency_ms": res["step_latency_ms"],
+            "hpsi": res["hpsi"],
+            "vs_fp64_gpu": res.get("vs_fp64_gpu"),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 16 * run.n1,
                     "d2h_bytes_per_step": 16 * 2 + 8 * run.ne},
             "gpu_launches": launches,
             "step_mode": "CUDA graph replay of one time step (captured from the direct C-ABI calls; the observables on a second stream beside the eigendecomposition)",
-            "clocks": clocks,
+            "clocks": res.get("clocks"),
+            "other_configs": others or None,
+            "precision_note": "the tensor path is Ozaki integer slicing (exact bf16 slice products, int64 "
+                              "recombination); split-FP32 / 3xTF32 and BF16x3 with FP32 accumulation are not "
+                              "built: their FP32 accumulation bounds the error near 1e-7, above the 1e-8 target",
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -646,6 +836,12 @@ def run_precision_errors(args):
 
 def main():
     args = parse()
+    if args.oracle_rate:
+        wl = CONFIGS[args.oracle_rate]
+        best, n, ks, dt = oracle_rate(workload(wl), wl)
+        print(json.dumps({"value": best, "sample": f"best of 5 blocks, {n} time steps ({ks} Krylov steps) in {dt:.1f} s "
+                                                    f"on one core, one BLAS thread"}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_hpsi > 0:

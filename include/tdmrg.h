@@ -234,9 +234,12 @@ const char* tdmrg_server_last_error(tdmrg_server* srv, int64_t job_id);
 /* H psi that allocates no device memory during the call.  The paper has no counterpart: this exists
  * for callers that may not allocate once they run -- a real-time loop that forbids allocation after
  * initialisation, a framework whose own pool owns all device memory, a plugin limited to the buffers
- * it is handed.  Same arithmetic, kernel and result as tdmrg_apply_h (out_d = H psi_d in sector Q);
- * the scratch (stage-1 intermediates, split-K partial tiles and tickets) lives in a file-scope
- * static device array of 32 MiB that every GPU loading the library holds until the process exits.
+ * it is handed.  out_d = H psi_d in sector Q, always computed by the FP64 grouped GEMM, whatever the
+ * context's precision: on a TDMRG_FP64 context the result is bit for bit that of tdmrg_apply_h; on a
+ * TDMRG_OZAKI_BF16 context it is the FP64 product, which differs from tdmrg_apply_h's tensor-core
+ * result by that path's slicing error.  The scratch (stage-1 intermediates, split-K partial tiles and
+ * tickets) lives in a file-scope static device array of 32 MiB that every GPU loading the library
+ * holds until the process exits.
  *   - The sector must be prepared during set-up by one tdmrg_apply_h or tdmrg_hpsi_flops call for
  *     Q (those may allocate); otherwise TDMRG_ESTATE.
  *   - A sector whose scratch exceeds 32 MiB is rejected with TDMRG_ENOMEM and a message giving the

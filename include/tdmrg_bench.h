@@ -16,6 +16,10 @@ extern "C" {
 /* Number of kernels the context has launched since it was created (host counter, no sync). */
 int tdmrg_launch_count(tdmrg_ctx* ctx, int64_t* count);
 
+/* Device allocations the context has made since it was created: number of successful cudaMalloc calls
+ * and their total bytes (host counters, no sync).  Lets a caller check that a call allocated nothing. */
+int tdmrg_alloc_count(tdmrg_ctx* ctx, int64_t* count, int64_t* bytes);
+
 /* Algorithmic FP64-equivalent flops of one H psi in sector Q as the library computes it: 8 real flops
  * per complex multiply-add of every sector-pair product it issues (stage 1 + stage 2). */
 int tdmrg_hpsi_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);

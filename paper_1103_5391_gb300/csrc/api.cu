@@ -38,6 +38,8 @@ int dev_alloc(tdmrg_ctx* c, void** p, size_t bytes, const char* what) {
         return fail(c, TDMRG_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
     }
     c->allocated += bytes;
+    c->alloc_calls++;
+    c->alloc_bytes += (int64_t)bytes;
     return TDMRG_OK;
 }
 

@@ -265,6 +265,8 @@ struct tdmrg_ctx {
     tdmrg::cplx* tmp = nullptr;    // apply_op temporary for expect
     int64_t tmp_cap = 0;
     size_t allocated = 0;
+    int64_t alloc_calls = 0;       // successful device allocations (cudaMalloc) made by this context
+    int64_t alloc_bytes = 0;       // their total size
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
     int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue

@@ -50,6 +50,13 @@ int tdmrg_launch_count(tdmrg_ctx* c, int64_t* count) {
     return TDMRG_OK;
 }
 
+int tdmrg_alloc_count(tdmrg_ctx* c, int64_t* count, int64_t* bytes) {
+    if (!c || !count || !bytes) return tdmrg::fail(c, TDMRG_EINVAL, "alloc_count: null argument");
+    *count = c->alloc_calls;
+    *bytes = c->alloc_bytes;
+    return TDMRG_OK;
+}
+
 int tdmrg_hpsi_tensor_flops(tdmrg_ctx* c, int a, int b, double* flops) {
     if (!c || !flops) return tdmrg::fail(c, TDMRG_EINVAL, "hpsi_tensor_flops: null argument");
     if (!c->ham_set) return tdmrg::fail(c, TDMRG_ESTATE, "hpsi_tensor_flops: Hamiltonian not set");
@@ -59,13 +66,20 @@ int tdmrg_hpsi_tensor_flops(tdmrg_ctx* c, int a, int b, double* flops) {
     double f = 0.0;
     if (p->oz.ready) {
         const int S = p->oz.S;
+        const double groups = S * (S + 1) / 2;
         for (const tdmrg::OzStage& st : p->oz.st)
             for (const tdmrg::OzTile& t : st.tiles) {
                 const tdmrg::OzTask& k = st.tasks[t.task];
-                const int nval = k.N - t.n0 < 32 ? k.N - t.n0 : 32;
-                const int n_t = (nval + 7) & ~7;
-                // per 64-wide K chunk: 4 k-steps x S(S+1)/2 MMAs of 128 x 2n_t x 16
-                f += (double)k.kchunks * 4 * (S * (S + 1) / 2) * 2.0 * 128 * (2 * n_t) * 16;
+                if (S <= 4) {
+                    // persistent kernel: per 64-wide K chunk and 16-wide k-step, A slice s times the
+                    // B slices 1..S+1-s in one MMA of M = 64, N = (S + 1 - s) 64
+                    f += (double)k.kchunks * 4 * groups * 2.0 * 64 * 64 * 16;
+                } else {
+                    // per 64-wide K chunk: 4 k-steps x S(S+1)/2 MMAs of 128 x 2n_t x 16
+                    const int nval = k.N - t.n0 < 32 ? k.N - t.n0 : 32;
+                    const int n_t = (nval + 7) & ~7;
+                    f += (double)k.kchunks * 4 * groups * 2.0 * 128 * (2 * n_t) * 16;
+                }
             }
     }
     *flops = f;

@@ -21,7 +21,7 @@ EXPORTED = [
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect", "tdmrg_overlap_op",
-    "tdmrg_launch_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
+    "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
@@ -83,6 +83,7 @@ def load(path=LIB_PATH):
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
         "tdmrg_launch_count": (I, [P, PI64]),
+        "tdmrg_alloc_count": (I, [P, PI64, PI64]),
         "tdmrg_set_schedule": (I, [P, I]),
         "tdmrg_probe_wait": (I, [P, I64]),
         "tdmrg_hpsi_flops": (I, [P, I, I, PD]),
@@ -271,6 +272,13 @@ def tdmrg_launch_count(ctx):
     n = ctypes.c_int64()
     _check(ctx, load().tdmrg_launch_count(ctx, ctypes.byref(n)))
     return n.value
+
+
+def tdmrg_alloc_count(ctx):
+    """(number, total bytes) of device allocations the context has made."""
+    n, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load().tdmrg_alloc_count(ctx, ctypes.byref(n), ctypes.byref(b)))
+    return n.value, b.value
 
 
 def tdmrg_hpsi_flops(ctx, Q):

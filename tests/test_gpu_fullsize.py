@@ -6,8 +6,9 @@ are element by element: H psi on both paths, one time step of the Krylov advance
 resulting targets and its eigendecomposition, and an observable.
 
 Bounds: FP64 path 1e-12 (H psi) and 1e-10 (targets, the per-step bound for the FP64 path); tensor
-path with S = 4 slices the error model of the slicing, 40 2^{-7S} sqrt(K_max) for H psi, and 2e-6
-relative for the targets of one step (measured errors are printed by the bench, not here)."""
+path with S = 4 slices 140 2^{-28} = 5.2e-7 relative for H psi (10x the largest error measured over
+the tensor-path tests, see test_gpu_ozaki) and 6e-7 relative for the targets of one step (10x the
+measured 3.0e-8 on the chain and 5.7e-8 on the ladder)."""
 import numpy as np
 import pytest
 
@@ -41,8 +42,7 @@ def test_fullsize_hpsi(lib, L, m, U, nb, tau):
     rng = np.random.default_rng(8)
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     ref = superblock.apply_h(sb, HL, HR, conns, ss.Q1, x)
-    kmax = 5 * max(ss.ldim) * (1 + 2 * nb)
-    for prec, bound in (("fp64", 1e-12), ("ozaki", 40.0 * 2.0 ** -28 * np.sqrt(kmax))):
+    for prec, bound in (("fp64", 1e-12), ("ozaki", 140.0 * 2.0 ** -28)):
         kw = dict(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=4) if prec == "ozaki" else {}
         ctx = new_ctx(**kw)
         try:
@@ -77,7 +77,7 @@ def test_fullsize_time_step(lib, L, m, U, nb, tau, mixed):
         lib.tdmrg_evolve(ctx, ss.Q1, dev(ss.phi), times, nk, tg)
         n_gpu, err_gpu, a_g, b_g = lib.tdmrg_evolve_info(ctx)
         assert n_gpu == n_used
-        bound = 2e-6 if mixed else 1e-10
+        bound = 6e-7 if mixed else 1e-10
         got = [host(t) for t in tg]
         for x in range(nv):
             assert _rel(got[x], ref[x]) < bound, x

@@ -1,10 +1,14 @@
 """GPU parity of the tensor-core (Ozaki-sliced bf16, tcgen05) superblock product against the oracle.
 
-Error model: operands are represented to 2^{-7S} of their row / column maximum, and the slice
-products are exact, so |GPU - oracle| <= c * 2^{-7S} * max|A| max|B| * K per entry; the tests bound
-the relative error max|err| / max|ref| by 40 * 2^{-7S} * sqrt(K_max) (c and sqrt(K) cover the
-accumulation of independent truncation errors).  Observables after a Krylov trajectory must match
-exact diagonalisation to 1e-8 at S >= 5."""
+Error model: each operand entry is rounded to 7S bits below its row (A) or column (B) exponent, and
+the slice products and their recombination are exact, so the only error is that rounding.  Measured
+over every workload of these tests (chains and ladders, L = 8 ... 48, m = 24 ... 1000, both sectors),
+the relative error max|GPU - oracle| / max|oracle| of H psi is c 2^{-7S} with c at most 9.9, 12.5,
+13.8, 21.7 and 19.3 for S = 2 ... 6 (c grows slowly with the sector sizes, like the square root of the
+number of accumulated terms).  The bounds below are 10x those largest measured values, rounded up:
+an error twice or four times the slicing error of a correct implementation still passes only where
+the measured error sat well below the maximum, and anything larger fails.  Observables after a Krylov
+trajectory must match exact diagonalisation to 1e-8 at S >= 4 (measured 1.1e-9 at S = 4)."""
 import numpy as np
 import pytest
 
@@ -26,8 +30,12 @@ def _rand(n, seed):
     return rng.standard_normal(n) + 1j * rng.standard_normal(n)
 
 
-def _tol(slices, kmax):
-    return 40.0 * 2.0 ** (-7 * slices) * np.sqrt(kmax)
+# 10x the largest measured c of the error model, per slice count
+TOL_C = {2: 100.0, 3: 130.0, 4: 140.0, 5: 220.0, 6: 200.0}
+
+
+def _tol(slices):
+    return TOL_C[slices] * 2.0 ** (-7 * slices)
 
 
 @pytest.mark.parametrize("slices", [3, 4, 5, 6])
@@ -46,8 +54,7 @@ def test_ozaki_hpsi(lib, slices, L, m, nb, seed):
             lib.tdmrg_apply_h(ctx, Q, dev(x), out)
             ref = superblock.apply_h(sb, HL, HR, conns, Q, x)
             err = rel_err(host(out), ref)
-            kmax = 5 * max(ss.ldim) * (1 + 2 * nb)
-            assert err < _tol(slices, kmax), (slices, err)
+            assert err < _tol(slices), (slices, err)
     finally:
         lib.tdmrg_destroy(ctx)
 
@@ -76,7 +83,7 @@ def test_ozaki_schedules_bit_identical(lib, L, m, nb, seed):
         for o in outs[1:]:
             assert np.array_equal(o.view(np.float64), outs[0].view(np.float64))
         ref = superblock.apply_h(sb, HL, HR, conns, ss.Q1, x)
-        assert rel_err(outs[0], ref) < _tol(4, 5 * max(ss.ldim) * (1 + 2 * nb))
+        assert rel_err(outs[0], ref) < _tol(4)
         with pytest.raises(lib.TdmrgError):
             lib.tdmrg_set_schedule(ctx, 2)
     finally:
@@ -125,9 +132,10 @@ def test_ozaki_switch_precision_and_fp64_parity(lib):
         lib.tdmrg_destroy(ctx)
 
 
-@pytest.mark.parametrize("slices", [5, 6])
+@pytest.mark.parametrize("slices", [4, 5, 6])
 def test_ozaki_trajectory_against_ed(lib, c1_problem, c1_ground, slices):
-    """L=8 chain, U=4, c^dag_{4 up}: 20 Krylov steps of tau=0.1 on the tensor path; n_i(t) vs ED <= 1e-8."""
+    """L=8 chain, U=4, c^dag_{4 up}: 20 Krylov steps of tau=0.1 on the tensor path; n_i(t) vs ED <= 1e-8
+    (measured 1.1e-9 at S = 4, 9e-12 at S = 5)."""
     p = c1_problem
     e, psi = c1_ground
     Q1 = (5, 4)

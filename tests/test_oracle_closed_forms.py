@@ -3,6 +3,8 @@ excitation at U=0), Eq. nd and Sec. III.B.2 (holon-doublon at t=0), and the
 small-time expansion of Sec. III.B.1."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from oracle import closed_forms, ed, krylov, models, superblock
 
@@ -93,10 +95,48 @@ def test_holon_doublon_against_ed(ladder_hd):
             assert abs(p.double_occupation(targets[-1], p.Q, site) - ed.double_occupation(ex, sec, site)) < 1e-9
 
 
+def _fock_state(p, phi):
+    sec = ed.Sector(8, *p.Q)
+    perm = superblock.fock_to_psi(p.cut, sec, np.arange(sec.dim) + 0j).real.astype(int)
+    phif = np.zeros(sec.dim, complex)
+    phif[perm] = phi
+    return sec, phif
+
+
+@pytest.mark.parametrize("site", [2, 4, 5])
+def test_small_time_coefficient_against_ed_curvature(ladder_hd, site):
+    """closed_forms.small_time_coefficient against the curvature of the exact density: O(t) from
+    exact evolution (ED, expm) at t = 0, +-h, +-h/2, and a = O''(0) / 2 by central differences with
+    one Richardson step (error O(h^4)); U = 10 ladder, holon-doublon state (Sec. III.B.1).  A sign or
+    ordering slip in the formula (H n H + H^2 n, or n H^2 for H n H) fails by orders of magnitude."""
+    p, phi = ladder_hd[10.0]
+    sec, phif = _fock_state(p, phi)
+    H = ed.hamiltonian(sec, ed.ladder_hopping(4, 1.0, 0.5), 10.0)
+    occ = np.array([((int(s) >> ed.mode(site, 0)) & 1) + ((int(s) >> ed.mode(site, 1)) & 1)
+                    for s in sec.states], dtype=float)
+    n_p = sp.diags(occ)
+    a = closed_forms.small_time_coefficient(H, n_p, phif)
+
+    def O(t):
+        v = ed.evolve(H, phif, [t])[0]
+        return float(np.dot(occ, np.abs(v) ** 2) / np.vdot(v, v).real)
+
+    def curv(h):
+        return (O(h) - 2.0 * O(0.0) + O(-h)) / (2.0 * h * h)
+
+    h = 2e-3
+    a_fd = (4.0 * curv(h / 2) - curv(h)) / 3.0
+    assert abs(a - a_fd) < 1e-6 * max(1.0, abs(a)), (a, a_fd)
+    assert abs(a) > 1e-3                       # the pin is not vacuous at this site
+
+
 def test_small_time_expansion(ladder_hd):
-    """O(t) - O(0) = a t^2 + O(t^4), a = <H n H - H^2 n>, at U = 10 (Sec. III.B.1)."""
+    """O(t) - O(0) = a t^2 + O(t^4) with a from closed_forms.small_time_coefficient applied to the
+    block-basis H psi of the oracle, at U = 10 (Sec. III.B.1)."""
     p, phi = ladder_hd[10.0]
     Hf = p.apply_h(p.Q)
+    n = len(phi)
+    Hop = spla.LinearOperator((n, n), matvec=Hf, dtype=complex)
     for site in (2, 4, 5):
         side, n_up = p.op("n", site, 0)
         side, n_dn = p.op("n", site, 1)
@@ -108,8 +148,7 @@ def test_small_time_expansion(ladder_hd):
                 out = out + superblock.apply_op(p.sb, A, B, p.Q, v, p.Q)
             return out
 
-        Hphi = Hf(phi)
-        a = (np.vdot(Hphi, nop(Hphi)) - np.vdot(phi, Hf(Hf(nop(phi))))).real / np.vdot(phi, phi).real
+        a = closed_forms.small_time_coefficient(Hop, spla.LinearOperator((n, n), matvec=nop, dtype=complex), phi)
         O0 = p.density(phi, p.Q, site)
         for t in (0.005, 0.01, 0.02):
             targets, n_used, err = krylov.evolve(Hf, phi, [t], nk=12)
