@@ -28,6 +28,7 @@ namespace {
 
 constexpr int JT = 1024;  // threads of the FP32 Jacobi CTA (warps over rotation pairs, lanes over rows)
 constexpr int kSmemMaxN = 112;   // A and V as float2 in shared memory: 2 * 112 * 113 * 8 B = 198 KB
+constexpr int kSmemMaxA = 158;   // A alone in shared memory (158 * 159 * 8 B = 196 KB), V in global memory
 constexpr int kJacSmemCap = 225 * 1024;   // dynamic shared memory of the Jacobi CTA at most
 constexpr int kMaxEigN = 512;    // largest sector dimension
 constexpr int kKChunk = 16;      // K chunk of the refinement GEMMs
@@ -88,8 +89,17 @@ __device__ __forceinline__ float2 rot_r(float c, float2 s, float2 x, float2 y) {
 
 constexpr int JA = 512;   // threads that rotate A (warps 0-15); the other 16 warps accumulate V
 
+// Where a sector's Jacobi keeps its matrices: A and V in shared memory (n <= kSmemMaxN); A in shared
+// memory and V in global memory, stored transposed so that the V warps' accesses along a column are
+// contiguous (n <= kSmemMaxA); both in global memory (larger n).
+enum JacMode { JAC_SMEM = 0, JAC_SMEM_A = 1, JAC_GLOBAL = 2 };
+__host__ __device__ inline int jac_mode(int n) { return n <= kSmemMaxN ? JAC_SMEM : n <= kSmemMaxA ? JAC_SMEM_A : JAC_GLOBAL; }
+
 // Rounds of the rotation record that fit in `smem` bytes beside A and V (two buffers of float4 per pair).
-__host__ __device__ inline int jac_base_bytes(int n) { return n <= kSmemMaxN ? 16 * n * (n | 1) : 0; }
+__host__ __device__ inline int jac_base_bytes(int n) {
+    const int m = jac_mode(n);
+    return m == JAC_SMEM ? 16 * n * (n | 1) : m == JAC_SMEM_A ? ((8 * n * (n | 1) + 15) & ~15) : 0;
+}
 __host__ __device__ inline int jac_chunk(int n, int smem) {
     const int P = n + (n & 1), R = P - 1, npair = P / 2;
     if (npair == 0) return 1;
@@ -99,7 +109,9 @@ __host__ __device__ inline int jac_chunk(int n, int smem) {
 
 // V <- V J_r for the recorded rounds r0 .. r0 + nr - 1 (V group: warps over pairs, lanes over rows, so a
 // warp's accesses to a column of V fall in distinct banks; a V-group barrier separates the rounds).
-__device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int ld, const float4* rec, int nr, int r0) {
+// Element (k, p) of V is at V[k * rs + p * cs]: row-major in shared memory (rs = ld, cs = 1), transposed
+// in global memory (rs = 1, cs = ld), where a warp's accesses along a column are then contiguous.
+__device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int rs, int cs, const float4* rec, int nr, int r0) {
     const int P = n + (n & 1), npair = P / 2;
     const int lane = threadIdx.x & 31, vw = (threadIdx.x - JA) >> 5;
     constexpr int NVW = (JT - JA) / 32;
@@ -110,10 +122,12 @@ __device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int ld, const f
             const int p = __float_as_int(ro.w) & 0xffff, q = __float_as_int(ro.w) >> 16;
             const float c = ro.x;
             const float2 s = make_float2(ro.y, ro.z), sc = conjf2(s);
+            float2* Vp = V + p * cs;
+            float2* Vq = V + q * cs;
             for (int k = lane; k < n; k += 32) {
-                const float2 vp = V[k * ld + p], vq = V[k * ld + q];
-                V[k * ld + p] = rot_l(c, sc, vp, vq);
-                V[k * ld + q] = rot_r(c, s, vp, vq);
+                const float2 vp = Vp[k * rs], vq = Vq[k * rs];
+                Vp[k * rs] = rot_l(c, sc, vp, vq);
+                Vq[k * rs] = rot_r(c, s, vp, vq);
             }
         }
         asm volatile("bar.sync 2, %0;" ::"r"(JT - JA) : "memory");
@@ -134,7 +148,8 @@ __device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int ld, const f
 __device__ __forceinline__ float jac_lim(bool rel, float thr2, float a, float d) {
     return rel ? fmaxf(kReseedTol * kReseedTol * fabsf(a * d), thr2) : thr2;
 }
-__device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, float thr, bool rel, float4* rec, int C) {
+__device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, int vrs, int vcs, float thr, bool rel,
+                                              float4* rec, int C) {
     const int tid = threadIdx.x;
     const bool agroup = tid < JA;
     const float thr2 = thr * thr;
@@ -220,14 +235,14 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                     }
                 }
             } else if (pend) {
-                jacobi_apply_v(V, n, ld, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
+                jacobi_apply_v(V, n, vrs, vcs, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
             }
             const int any = __syncthreads_or(above);
             pend = nr; pend_r0 = r0; buf ^= 1;
             if (last && !any) done = true;
         }
     }
-    if (!agroup && pend) jacobi_apply_v(V, n, ld, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
+    if (!agroup && pend) jacobi_apply_v(V, n, vrs, vcs, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
     __syncthreads();
 }
 
@@ -246,16 +261,19 @@ __device__ __forceinline__ float jacobi_fro2(const float2* A, int n, int ld) {
     return f;
 }
 
-// W = V^H - dsub I: row j is the conjugate of eigenvector j (dsub = 1 stores the re-seed as a correction)
-__device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, int ld, double dsub) {
+// W = V^H - dsub I: row j is the conjugate of eigenvector j (dsub = 1 stores the re-seed as a correction);
+// element (k, j) of V at V[k * rs + j * cs]
+__device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, int rs, int cs, double dsub) {
     for (int e = threadIdx.x; e < n * n; e += JT) {
-        const float2 v = V[(e % n) * ld + e / n];
-        Ws[e] = make_double2((double)v.x - (e % n == e / n ? dsub : 0.0), -v.y);
+        const int j = e / n, k = e % n;
+        const float2 v = V[k * rs + j * cs];
+        Ws[e] = make_double2((double)v.x - (k == j ? dsub : 0.0), -v.y);
     }
 }
 
-// FP32 Jacobi per sector.  Dynamic shared memory (`smem` bytes): A and V of sectors with n <= kSmemMaxN,
-// then the rotation record; larger sectors keep A and V in `gwork`.
+// FP32 Jacobi per sector.  Dynamic shared memory (`smem` bytes): A and V of sectors with n <= kSmemMaxN
+// (A alone for n <= kSmemMaxA, V then in `gwork`, transposed), then the rotation record; larger sectors
+// keep A and V in `gwork`.
 //  - seed (rel = false): src = rho; writes W0 = X0^H (X0: unsorted eigenvector columns), ||rho||_F, the
 //    initial iteration count, and clears the sector's re-seed flag;
 //  - re-seed (rel = true) in refinement iteration `it`, for sectors whose flag is set: src = S = X^H rho X
@@ -273,9 +291,9 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     if (rel && (it >= *n_iter || flags[sct] == 0)) return;   // iteration skipped, or nothing to re-seed
     const int64_t off = tb.off[sct];
     const int ld = n | 1;   // odd row stride: column accesses of a warp hit distinct banks
-    const bool in_smem = n <= kSmemMaxN;
+    const int mode = jac_mode(n);
     float2* gA = gwork + 4 * off;
-    float2* gV = gA + (int64_t)n * ld;
+    float2* gV = gA + (int64_t)n * ld;   // transposed: element (k, p) at gV[p * ld + k]
     float4* rec = fsm4 + jac_base_bytes(n) / 16;
     const int C = jac_chunk(n, smem);
     __shared__ float red[JT / 32];
@@ -283,7 +301,9 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     const double scale = rel ? 1.0 / rho_fro[sct] : 1.0;
     if (!rel && sct == 0 && tid == 0) *n_iter = kRefine;
     float fro;
-    if (in_smem) { jacobi_load(src + off, scale, fsm, fsm + n * ld, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
+    // V starts as the identity, the same in either layout
+    if (mode == JAC_SMEM) { jacobi_load(src + off, scale, fsm, fsm + n * ld, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
+    else if (mode == JAC_SMEM_A) { jacobi_load(src + off, scale, fsm, gV, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
     else { jacobi_load(src + off, scale, gA, gV, n, ld); __syncthreads(); fro = jacobi_fro2(gA, n, ld); }
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     if ((tid & 31) == 0) red[tid >> 5] = fro;
@@ -303,12 +323,15 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     }
     __syncthreads();
     const float thr = thr_s;
-    if (in_smem) {
-        jacobi_sweeps(fsm, fsm + n * ld, n, ld, thr, rel, rec, C);
-        jacobi_store(fsm + n * ld, dst + off, n, ld, rel ? 1.0 : 0.0);
+    if (mode == JAC_SMEM) {
+        jacobi_sweeps(fsm, fsm + n * ld, n, ld, ld, 1, thr, rel, rec, C);
+        jacobi_store(fsm + n * ld, dst + off, n, ld, 1, rel ? 1.0 : 0.0);
+    } else if (mode == JAC_SMEM_A) {
+        jacobi_sweeps(fsm, gV, n, ld, 1, ld, thr, rel, rec, C);
+        jacobi_store(gV, dst + off, n, 1, ld, rel ? 1.0 : 0.0);
     } else {
-        jacobi_sweeps(gA, gV, n, ld, thr, rel, rec, C);
-        jacobi_store(gV, dst + off, n, ld, rel ? 1.0 : 0.0);
+        jacobi_sweeps(gA, gV, n, ld, 1, ld, thr, rel, rec, C);
+        jacobi_store(gV, dst + off, n, 1, ld, rel ? 1.0 : 0.0);
     }
 }
 
