@@ -28,6 +28,18 @@ int tdmrg_hpsi_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
  * tiles, slice pairs and K chunks, padding included); 0 when the context runs FP64. */
 int tdmrg_hpsi_tensor_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
 
+/* FP64 flops (8 per complex multiply-add) of the thin sector-pair products of one H psi in sector Q,
+ * i.e. those the tensor path computes on the FP64 warps of its persistent kernel; 0 on an FP64 context. */
+int tdmrg_hpsi_thin_flops(tdmrg_ctx* ctx, int n_up, int n_dn, double* flops);
+
+/* Tensor path: sector-pair products whose output block has fewer than `dim` rows or columns run on FP64
+ * warps of the persistent tensor kernel instead of tensor tiles (plans built from now on; existing plans
+ * are rebuilt on their next use).  Only products whose K over all segments is at most 32 qualify (an
+ * FP64 block must not outlast the tensor stage).  dim = 0 puts every product on the tensor tiles.
+ * Default 12 (fastest measured at the L=32 m=400, 2x16 m=800 and L=48 m=1000 workloads).
+ * Errors: EINVAL (dim outside 0..64). */
+int tdmrg_set_thin_dim(tdmrg_ctx* ctx, int dim);
+
 /* Tile schedule of the persistent tensor-core kernel for plans built from now on (existing plans are
  * dropped and rebuilt on their next use): -1 chosen per GEMM stage by timing when the plan is built
  * (the default), 0 static (CTA b takes tiles b, b + grid, ... of the longest-first list), 1 a device

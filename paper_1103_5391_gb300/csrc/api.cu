@@ -506,6 +506,16 @@ int tdmrg_set_schedule(tdmrg_ctx* c, int mode) {
     return TDMRG_OK;
 }
 
+int tdmrg_set_thin_dim(tdmrg_ctx* c, int dim) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (dim < 0 || dim > 64) return fail(c, TDMRG_EINVAL, "set_thin_dim: dim must be in 0..64");
+    DeviceGuard g(c->opts.device);
+    cudaStreamSynchronize(c->stream);
+    c->thin_dim = dim;
+    drop_plans(c);   // plans are rebuilt with the new split on their next use
+    return TDMRG_OK;
+}
+
 int tdmrg_expect(tdmrg_ctx* c, int opL, int opR, int a, int b, const tdmrg_c64* psi, tdmrg_c64* out) {
     if (check_ctx(c)) return TDMRG_EINVAL;
     if (!psi || !out) return fail(c, TDMRG_EINVAL, "expect: null pointer");

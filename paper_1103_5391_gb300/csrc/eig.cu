@@ -43,8 +43,13 @@ constexpr double kTolE = 1e-7;   // |E| above this: the next error (~|E|^2) may 
 struct EigTables {
     const int64_t* off;   // per sector: offset of its n x n block
     const int64_t* eoff;  // per sector: offset of its eigenvalues
+    const int64_t* roff;  // per sector: offset of its global rotation record (sectors beyond kSmemMaxN)
     const int* dims;
+    const int* big;       // the sectors beyond kSmemMaxN, in table order
 };
+constexpr int kMaxSweeps = 12;     // Jacobi sweeps at most (the record holds this many)
+constexpr int kReplayRows = 8;     // rows of V per CTA of the record replay
+constexpr int kReplayThreads = 512;
 
 __device__ __forceinline__ float2 cmf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
@@ -148,10 +153,15 @@ __device__ __forceinline__ void jacobi_apply_v(float2* V, int n, int rs, int cs,
 __device__ __forceinline__ float jac_lim(bool rel, float thr2, float a, float d) {
     return rel ? fmaxf(kReseedTol * kReseedTol * fabsf(a * d), thr2) : thr2;
 }
+//
+// Record mode (grec != nullptr, used when V does not fit in shared memory): every thread rotates A
+// (ja = JT), each rotation is also written to the global record grec (round-major, npair per round) and
+// *nrec receives the number of rounds; V is formed afterwards from the record by k_jacobi_replay.
 __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, int vrs, int vcs, float thr, bool rel,
-                                              float4* rec, int C) {
+                                              float4* rec, int C, int ja, float4* __restrict__ grec, int* nrec) {
     const int tid = threadIdx.x;
-    const bool agroup = tid < JA;
+    const bool agroup = tid < ja;
+    int total = 0;   // rounds recorded before the current chunk
     const float thr2 = thr * thr;
     const int P = n + (n & 1), npair = P / 2, R = P - 1;
     const int warp = tid >> 5, lane = tid & 31;
@@ -167,7 +177,7 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                 for (int r = 0; r < nr; ++r) {
                     const int round = r0 + r;
                     float4* rr = cur + r * npair;
-                    for (int i = tid; i < npair; i += JA) {
+                    for (int i = tid; i < npair; i += ja) {
                         int p, q;
                         rr_pair(round, i, P, p, q);
                         float c = 1.f;
@@ -182,12 +192,14 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                                 rotation32(ap, aq, b, c, s);
                             }
                         }
-                        rr[i] = make_float4(c, s.x, s.y, __int_as_float(p | (q << 16)));
+                        const float4 ro = make_float4(c, s.x, s.y, __int_as_float(p | (q << 16)));
+                        rr[i] = ro;
+                        if (grec != nullptr) grec[(size_t)(total + r) * npair + i] = ro;
                     }
-                    asm volatile("bar.sync 1, %0;" ::"r"(JA) : "memory");
+                    asm volatile("bar.sync 1, %0;" ::"r"(ja) : "memory");
                     // warp task j: block row a = j (blocks b = 0 .. a) followed by block row npair - 1 - j
                     // (blocks 0 .. npair - 1 - j): npair + 1 blocks, lanes over them
-                    for (int j = warp; j < (npair + 1) / 2; j += JA / 32) {
+                    for (int j = warp; j < (npair + 1) / 2; j += ja / 32) {
                         for (int l = lane; l < npair + 1; l += 32) {
                             int a = j, b = l;
                             if (l > j) { a = npair - 1 - j; b = l - j - 1; }
@@ -223,10 +235,10 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
                             }
                         }
                     }
-                    asm volatile("bar.sync 1, %0;" ::"r"(JA) : "memory");
+                    asm volatile("bar.sync 1, %0;" ::"r"(ja) : "memory");
                 }
                 if (last) {   // the next sweep rotates only pairs above the threshold: stop when there are none
-                    for (int e = tid; e < n * n; e += JA) {
+                    for (int e = tid; e < n * n; e += ja) {
                         const int r = e / n, cc = e % n;
                         if (r > cc) {
                             const float2 b = A[r * ld + cc];
@@ -239,10 +251,12 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
             }
             const int any = __syncthreads_or(above);
             pend = nr; pend_r0 = r0; buf ^= 1;
+            total += nr;
             if (last && !any) done = true;
         }
     }
     if (!agroup && pend) jacobi_apply_v(V, n, vrs, vcs, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
+    if (grec != nullptr && tid == 0) *nrec = total;
     __syncthreads();
 }
 
@@ -251,7 +265,7 @@ __device__ __forceinline__ void jacobi_load(const cplx* R, double scale, float2*
         const int r = e / n, cc = e % n;
         const double2 v = R[e];
         A[r * ld + cc] = make_float2((float)(v.x * scale), (float)(v.y * scale));
-        V[r * ld + cc] = make_float2(r == cc ? 1.f : 0.f, 0.f);
+        if (V != nullptr) V[r * ld + cc] = make_float2(r == cc ? 1.f : 0.f, 0.f);
     }
 }
 
@@ -283,17 +297,22 @@ __device__ __forceinline__ void jacobi_store(const float2* V, cplx* Ws, int n, i
 __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, cplx* __restrict__ dst,
                                                  double* __restrict__ rho_fro, int* __restrict__ n_iter,
                                                  int* __restrict__ flags, EigTables tb, float2* __restrict__ gwork,
+                                                 float4* __restrict__ grec, int* __restrict__ nrec,
                                                  int smem, bool rel, int it) {
     pdl_enter();
     extern __shared__ float4 fsm4[];
     float2* fsm = reinterpret_cast<float2*>(fsm4);
     const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
-    if (rel && (it >= *n_iter || flags[sct] == 0)) return;   // iteration skipped, or nothing to re-seed
+    const int mode = jac_mode(n);
+    if (rel && (it >= *n_iter || flags[sct] == 0)) {   // iteration skipped, or nothing to re-seed
+        if (mode != JAC_SMEM && tid == 0) nrec[sct] = -1;   // nor is there anything to replay
+        return;
+    }
     const int64_t off = tb.off[sct];
     const int ld = n | 1;   // odd row stride: column accesses of a warp hit distinct banks
-    const int mode = jac_mode(n);
     float2* gA = gwork + 4 * off;
     float2* gV = gA + (int64_t)n * ld;   // transposed: element (k, p) at gV[p * ld + k]
+    (void)gV;
     float4* rec = fsm4 + jac_base_bytes(n) / 16;
     const int C = jac_chunk(n, smem);
     __shared__ float red[JT / 32];
@@ -301,10 +320,10 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     const double scale = rel ? 1.0 / rho_fro[sct] : 1.0;
     if (!rel && sct == 0 && tid == 0) *n_iter = kRefine;
     float fro;
-    // V starts as the identity, the same in either layout
+    // V starts as the identity (record modes form V afterwards, in k_jacobi_replay)
     if (mode == JAC_SMEM) { jacobi_load(src + off, scale, fsm, fsm + n * ld, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
-    else if (mode == JAC_SMEM_A) { jacobi_load(src + off, scale, fsm, gV, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
-    else { jacobi_load(src + off, scale, gA, gV, n, ld); __syncthreads(); fro = jacobi_fro2(gA, n, ld); }
+    else if (mode == JAC_SMEM_A) { jacobi_load(src + off, scale, fsm, nullptr, n, ld); __syncthreads(); fro = jacobi_fro2(fsm, n, ld); }
+    else { jacobi_load(src + off, scale, gA, nullptr, n, ld); __syncthreads(); fro = jacobi_fro2(gA, n, ld); }
     for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
     if ((tid & 31) == 0) red[tid >> 5] = fro;
     __syncthreads();
@@ -324,14 +343,63 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     __syncthreads();
     const float thr = thr_s;
     if (mode == JAC_SMEM) {
-        jacobi_sweeps(fsm, fsm + n * ld, n, ld, ld, 1, thr, rel, rec, C);
+        jacobi_sweeps(fsm, fsm + n * ld, n, ld, ld, 1, thr, rel, rec, C, JA, nullptr, nullptr);
         jacobi_store(fsm + n * ld, dst + off, n, ld, 1, rel ? 1.0 : 0.0);
-    } else if (mode == JAC_SMEM_A) {
-        jacobi_sweeps(fsm, gV, n, ld, 1, ld, thr, rel, rec, C);
-        jacobi_store(gV, dst + off, n, 1, ld, rel ? 1.0 : 0.0);
+    } else if (mode == JAC_SMEM_A) {   // dst is written by k_jacobi_replay
+        jacobi_sweeps(fsm, nullptr, n, ld, 1, ld, thr, rel, rec, C, JT, grec + tb.roff[sct], nrec + sct);
     } else {
-        jacobi_sweeps(gA, gV, n, ld, 1, ld, thr, rel, rec, C);
-        jacobi_store(gV, dst + off, n, 1, ld, rel ? 1.0 : 0.0);
+        jacobi_sweeps(gA, nullptr, n, ld, 1, ld, thr, rel, rec, C, JT, grec + tb.roff[sct], nrec + sct);
+    }
+}
+
+// V of the sectors beyond kSmemMaxN from their rotation record: V starts as the identity and every
+// recorded rotation J_r acts on columns (p, q) of every row, so rows are independent: CTA (b, y) holds
+// rows 8y .. 8y + 7 of V of big sector b in shared memory and replays all rounds on them, the record
+// staged through shared memory a batch of rounds at a time.  Writes W = V^H - dsub I like jacobi_store
+// (dsub = 1 for a re-seed).  Runs after each k_jacobi32 launch; nrec < 0 marks a skipped sector.
+__global__ void __launch_bounds__(kReplayThreads) k_jacobi_replay(const float4* __restrict__ grec, const int* __restrict__ nrec,
+                                                                  cplx* __restrict__ dst, EigTables tb, int batch, bool rel) {
+    pdl_enter();
+    const int sct = tb.big[blockIdx.x], n = tb.dims[sct];
+    const int nr = nrec[sct];
+    const int k0 = blockIdx.y * kReplayRows;
+    if (nr < 0 || k0 >= n) return;
+    const int rows = min(kReplayRows, n - k0), ld = n | 1;
+    const int P = n + (n & 1), npair = P / 2;
+    extern __shared__ float4 rsm4[];
+    float4* rb = rsm4;                                        // batch rounds x npair records
+    float2* vs = reinterpret_cast<float2*>(rsm4 + (size_t)batch * npair);   // rows x ld
+    const int tid = threadIdx.x;
+    for (int e = tid; e < rows * n; e += blockDim.x) vs[(e / n) * ld + e % n] = make_float2(k0 + e / n == e % n ? 1.f : 0.f, 0.f);
+    const float4* rec = grec + tb.roff[sct];
+    for (int b0 = 0; b0 < nr; b0 += batch) {
+        const int nb = min(batch, nr - b0);
+        __syncthreads();
+        for (int e = tid; e < nb * npair; e += blockDim.x) rb[e] = rec[(size_t)b0 * npair + e];
+        __syncthreads();
+        for (int r = 0; r < nb; ++r) {
+            // lanes over rows within a pair: the rows' accesses to one column hit distinct banks (odd ld)
+            for (int x = tid; x < npair * rows; x += blockDim.x) {
+                const int i = x / rows, k = x % rows;
+                const float4 ro = rb[r * npair + i];
+                if (ro.y == 0.f && ro.z == 0.f) continue;   // identity
+                const int p = __float_as_int(ro.w) & 0xffff, q = __float_as_int(ro.w) >> 16;
+                const float2 s = make_float2(ro.y, ro.z), sc = conjf2(s);
+                float2* row = vs + k * ld;
+                const float2 vp = row[p], vq = row[q];
+                row[p] = rot_l(ro.x, sc, vp, vq);
+                row[q] = rot_r(ro.x, s, vp, vq);
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    const double dsub = rel ? 1.0 : 0.0;
+    cplx* W = dst + tb.off[sct];
+    for (int e = tid; e < rows * n; e += blockDim.x) {   // W[j][k0 + k] = conj(V[k0 + k][j]) - dsub delta
+        const int k = e % rows, j = e / rows;
+        const float2 v = vs[k * ld + j];
+        W[(int64_t)j * n + k0 + k] = make_double2((double)v.x - (j == k0 + k ? dsub : 0.0), -v.y);
     }
 }
 
@@ -503,18 +571,46 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         }
         if (maxn > kMaxEigN) return fail(c, TDMRG_EINVAL, "rho_eig: sector dimension above 512");
         w.nrho = r; w.nev = e; w.maxn = maxn; w.ns = ns;
-        int rc = dev_alloc(c, (void**)&w.tables, (size_t)ns * (2 * sizeof(int64_t) + sizeof(int)), "eig tables");
+        // sectors beyond kSmemMaxN: rotation records of up to kMaxSweeps sweeps, V from k_jacobi_replay
+        std::vector<int64_t> roff(ns, 0);
+        std::vector<int> big;
+        int64_t nrec_total = 0;
+        int maxn_big = 0;
+        for (int k = 0; k < ns; ++k) {
+            const int n = L.dim[k], P = n + (n & 1);
+            if (jac_mode(n) == JAC_SMEM) continue;
+            roff[k] = nrec_total;
+            nrec_total += (int64_t)kMaxSweeps * (P - 1) * (P / 2);
+            big.push_back(k);
+            maxn_big = std::max(maxn_big, n);
+        }
+        w.nbig = (int)big.size();
+        w.maxn_big = maxn_big;
+        w.grec_entries = nrec_total;
+        w.tables_bytes = (size_t)ns * (3 * sizeof(int64_t) + sizeof(int)) + big.size() * sizeof(int);
+        int rc = dev_alloc(c, (void**)&w.tables, w.tables_bytes, "eig tables");
         if (!rc) rc = dev_alloc(c, (void**)&w.buf, (size_t)6 * r * sizeof(cplx), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.lam, (size_t)e * sizeof(double), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double), "eig workspace");
-        if (!rc && maxn > kSmemMaxN) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
+        if (!rc && maxn > kSmemMaxA) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
+        if (!rc && nrec_total) rc = dev_alloc(c, (void**)&w.grec, (size_t)nrec_total * sizeof(float4), "eig rotation record");
+        if (!rc) rc = dev_alloc(c, (void**)&w.nrec, (size_t)ns * sizeof(int), "eig rotation record");
         if (rc) return rc;
-        std::vector<unsigned char> host((size_t)ns * (2 * sizeof(int64_t) + sizeof(int)));
-        memcpy(host.data(), off.data(), ns * sizeof(int64_t));
-        memcpy(host.data() + ns * sizeof(int64_t), eoff.data(), ns * sizeof(int64_t));
-        memcpy(host.data() + 2 * ns * sizeof(int64_t), L.dim.data(), ns * sizeof(int));
+        std::vector<unsigned char> host(w.tables_bytes);
+        unsigned char* h = host.data();
+        memcpy(h, off.data(), ns * sizeof(int64_t));
+        memcpy(h + ns * sizeof(int64_t), eoff.data(), ns * sizeof(int64_t));
+        memcpy(h + 2 * ns * sizeof(int64_t), roff.data(), ns * sizeof(int64_t));
+        memcpy(h + 3 * ns * sizeof(int64_t), L.dim.data(), ns * sizeof(int));
+        if (!big.empty()) memcpy(h + 3 * ns * sizeof(int64_t) + ns * sizeof(int), big.data(), big.size() * sizeof(int));
         rc = cuda_check(c, cudaMemcpy(w.tables, host.data(), host.size(), cudaMemcpyHostToDevice), "eig tables");
         if (rc) return rc;
+        if (w.nbig) {   // replay: 8 rows of V and as many rounds of the record as fit in 48 KB of shared memory
+            const int P = maxn_big + (maxn_big & 1);
+            const int slab = kReplayRows * (maxn_big | 1) * (int)sizeof(float2);
+            w.replay_batch = std::max(1, (48 * 1024 - slab) / ((P / 2) * (int)sizeof(float4)));
+            w.replay_smem = w.replay_batch * (P / 2) * (int)sizeof(float4) + slab;
+        }
         // task lists: AX = rho W^H; S = W AX and G = W W^H; W' = E1h W
         struct Prod { int cbuf, abuf, bbuf; int8_t opb, herm; };
         auto one = [&](TaskList& tl, std::initializer_list<Prod> prods) {
@@ -564,7 +660,16 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         if (rc) return rc;
         w.ready = true;
     }
-    EigTables tb{(const int64_t*)w.tables, (const int64_t*)w.tables + ns, (const int*)((const int64_t*)w.tables + 2 * ns)};
+    const int64_t* t64 = (const int64_t*)w.tables;
+    const int* dims = (const int*)(t64 + 3 * ns);
+    EigTables tb{t64, t64 + ns, t64 + 2 * ns, dims, dims + ns};
+    // V of the record-mode sectors after each Jacobi launch (seed or re-seed)
+    auto replay = [&](cplx* dst, bool rel) {
+        if (!w.nbig) return;
+        const dim3 grid(w.nbig, (w.maxn_big + kReplayRows - 1) / kReplayRows);
+        launch_pdl(k_jacobi_replay, grid, kReplayThreads, w.replay_smem, s, w.grec, w.nrec, dst, tb, w.replay_batch, rel);
+        c->launches++;
+    };
     cplx* W = w.buf;
     cplx* Wn = w.buf + w.nrho;
     cplx* AX = w.buf + 2 * w.nrho;
@@ -573,8 +678,10 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     cplx* E1h = w.buf + 5 * w.nrho;
     double* part = w.fro + ns;
     int* n_iter = reinterpret_cast<int*>(part + 2 * (size_t)ns * kRowChunks);
-    launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, false, 0);
+    launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec, w.jac_smem,
+               false, 0);
     c->launches += 1;
+    replay(W, false);
     GemmArgs a{};
     a.dscale = c->dscale;
     a.bufs[EB_RHO] = const_cast<cplx*>(rho);
@@ -598,8 +705,10 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
         launch_pdl(k_oa_norms, chunks, 256, 0, s, S, G, w.lam, part, n_iter, it, tb);
         launch_pdl(k_oa_update, chunks, 256, 0, s, S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
         if (reseed_iter(it)) {
-            launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.jac_smem, true, it);
+            launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec,
+                       w.jac_smem, true, it);
             c->launches++;
+            replay(E1h, true);
         }
         if (e == cudaSuccess) e = gemm(w.tl_y, true);
         c->launches += 2;
@@ -617,7 +726,9 @@ void release_eig(tdmrg_ctx* c) {
     EigWork& w = c->eig;
     release(c, w.tl_ax); release(c, w.tl_sg); release(c, w.tl_y);
     const int ns = w.ns;
-    dev_free(c, w.tables, (size_t)ns * (2 * sizeof(int64_t) + sizeof(int)));
+    dev_free(c, w.tables, w.tables_bytes);
+    dev_free(c, w.grec, (size_t)w.grec_entries * sizeof(float4));
+    dev_free(c, w.nrec, (size_t)ns * sizeof(int));
     dev_free(c, w.buf, (size_t)6 * w.nrho * sizeof(cplx));
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
     dev_free(c, w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double));

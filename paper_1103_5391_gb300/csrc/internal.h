@@ -110,6 +110,9 @@ struct OzTask {            // one complex GEMM C (+)= A op(B), all of its segmen
     int8_t c_buf, beta, trans, pad1;
 };
 struct OzTile { int32_t task, m0, n0, cost; };
+// An 8 x 8 output block of a thin sector-pair product (min(M, N) below the thin threshold), computed in
+// FP64 by the thin warps of the persistent tensor kernel; task indexes the stage's FP64 thin tasks.
+struct ThinItem { int32_t task, m0, n0, cost; };
 struct OzSliceJob {        // slices the rows of A' (role 0) or columns of B' (role 1) of one operand
     int32_t role, nvec, seg_begin, seg_end, row0, exp0, ktot, use_scale, vec_prefix;
 };
@@ -130,6 +133,10 @@ struct OzGemmArgs {
     int rowsA, rowsB;
     int* status;
     unsigned* sched;   // work queue of the persistent kernel: [0] next tile, [1] finished CTAs (zero between launches)
+    const Task* ttasks;       // thin tasks (FP64 warps): tasks, segments, items grouped by CTA
+    const Seg* tsegs;
+    const ThinItem* titems;
+    const int* tcta;          // items of CTA b: titems[tcta[b] .. tcta[b + 1]) (null: none)
 };
 struct OzStage {
     std::vector<OzTask> tasks;
@@ -153,6 +160,17 @@ struct OzStage {
     int rowsA = 0, rowsB = 0, kpad = 0, ncolsB = 0;
     unsigned* d_sched = nullptr;
     int queue = 0;   // tile schedule of the persistent kernel: 0 static, 1 work queue (chosen by timing)
+    int grid = 0;    // CTAs of the persistent kernel
+    // thin sector-pair products on the FP64 warps of the persistent kernel
+    std::vector<Task> ttasks;
+    std::vector<Seg> tsegs;
+    std::vector<ThinItem> titems;
+    std::vector<int> tcta;
+    Task* d_ttasks = nullptr;
+    Seg* d_tsegs = nullptr;
+    ThinItem* d_titems = nullptr;
+    int* d_tcta = nullptr;
+    double thin_flops = 0.0;   // algorithmic flops of the thin products (8 per complex MAC)
     CUtensorMap mapA, mapB;
     OzSliceArgs sliceA{}, sliceB{};
     OzGemmArgs args{};
@@ -223,6 +241,11 @@ struct EigWork {
     float2* gwork = nullptr;    // FP32 Jacobi storage for sectors too large for shared memory
     int jac_smem = 0;           // dynamic shared memory of the Jacobi launch
     int* flags = nullptr;       // per sector: re-seed requested by the refinement
+    size_t tables_bytes = 0;
+    float4* grec = nullptr;     // Jacobi rotation records of the sectors too large for V in shared memory
+    int64_t grec_entries = 0;
+    int* nrec = nullptr;        // per sector: rounds recorded by the last Jacobi launch (-1: skipped)
+    int nbig = 0, maxn_big = 0, replay_batch = 0, replay_smem = 0;
     TaskList tl_ax, tl_sg, tl_y;
 };
 
@@ -270,6 +293,7 @@ struct tdmrg_ctx {
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
     int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue
+    int thin_dim = 12;             // tensor path: sector products with min(M, N) below this run on FP64 warps
     int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
     tdmrg::EigWork eig;
 };

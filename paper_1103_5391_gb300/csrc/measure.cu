@@ -86,6 +86,16 @@ int tdmrg_hpsi_tensor_flops(tdmrg_ctx* c, int a, int b, double* flops) {
     return TDMRG_OK;
 }
 
+int tdmrg_hpsi_thin_flops(tdmrg_ctx* c, int a, int b, double* flops) {
+    if (!c || !flops) return tdmrg::fail(c, TDMRG_EINVAL, "hpsi_thin_flops: null argument");
+    if (!c->ham_set) return tdmrg::fail(c, TDMRG_ESTATE, "hpsi_thin_flops: Hamiltonian not set");
+    tdmrg::Plan* p = nullptr;
+    int rc = tdmrg::get_ham_plan(c, a, b, &p);
+    if (rc) return rc;
+    *flops = p->oz.ready ? p->oz.st[0].thin_flops + p->oz.st[1].thin_flops : 0.0;
+    return TDMRG_OK;
+}
+
 int tdmrg_fp64_peak(int device, double* dmma, double* dfma) {
     if (!dmma || !dfma) return tdmrg::fail(nullptr, TDMRG_EINVAL, "fp64_peak: null output");
     int prev = 0;

@@ -430,7 +430,9 @@ constexpr int TMW = 64;                    // MMA M of this variant: sector bloc
 constexpr int ABOXW = TMW * KCH * 2;       // bytes of one A slice box (8 KB)
 constexpr int NST = 3;                     // shared-memory stages of S x (8 + 8) KB
 constexpr int EPIW = 16;                   // epilogue warps: four per TMEM lane quarter, 16 accumulator columns each
-constexpr int WS_THREADS = 64 + 32 * EPIW;
+constexpr int THINW = 2;                   // FP64 warps for the thin sector-pair products
+constexpr int kThinMaxKsteps = 8;          // a thin block's m8n8k4 steps at most (K <= 32 over all its segments)
+constexpr int WS_THREADS = 64 + 32 * EPIW + 32 * THINW;
 constexpr int RT = 4;                      // tile-index ring between the producer and the consumers
 constexpr long kWaitWS = 1L << 22;
 
@@ -444,6 +446,64 @@ __device__ __forceinline__ bool mbar_wait_ws(uint32_t bar, uint32_t parity, vola
     }
     *failed = 1;
     return false;
+}
+
+// ---- thin sector-pair products (K3): FP64 on the warps the tensor pipeline leaves idle ---------------
+// A product whose output block has fewer than thin_dim rows or columns fills a small part of a 64-row
+// tensor tile, so it would cost a whole tile (TMA boxes, S(S+1)/2 MMAs per k-step, TMEM readout) for
+// little work.  Such products run instead on THINW extra warps of the persistent kernel, in FP64 with
+// the FP64 tensor MMA (mma.sync m8n8k4), straight from the FP64 operands (no slicing): the FP64 pipe is
+// otherwise idle during the tensor pipeline, and these operands need neither slices nor TMA boxes.
+// One warp computes one 8 x 8 output block over all segments of its task; items are assigned to CTAs
+// at plan build, longest first onto the least loaded CTA.
+__device__ __forceinline__ void dmma_f64(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1) : "d"(a), "d"(b));
+}
+__device__ __forceinline__ double neg_f64(double x) { return __longlong_as_double(__double_as_longlong(x) ^ (1ll << 63)); }
+
+__device__ __forceinline__ void thin_block(const ThinItem& it, const Task& tk, const Seg* __restrict__ segs,
+                                           const GemmArgs& g, int lane) {
+    const int gid = lane >> 2, tig = lane & 3;   // fragment layout of m8n8k4: A[gid][tig], B[tig][gid]
+    const int r = it.m0 + gid, cb = it.n0 + gid;
+    const bool rv = r < tk.M, cv = cb < tk.N;
+    double cre0 = 0.0, cre1 = 0.0, cim0 = 0.0, cim1 = 0.0;
+    for (int si = tk.seg_begin; si < tk.seg_end; ++si) {
+        const Seg sg = segs[si];
+        const cplx* __restrict__ A = g.bufs[sg.a_buf] + sg.a_off + (int64_t)r * sg.lda;
+        const cplx* __restrict__ B = g.bufs[sg.b_buf] + sg.b_off;
+        const bool bn = sg.opb == OPB_N, bc = sg.opb == OPB_C;
+        const cplx* __restrict__ Bc = bn ? B + cb : B + (int64_t)cb * sg.ldb;   // column cb of op(B)
+        const int64_t bk = bn ? sg.ldb : 1;                                         // its step along k
+        double pre0 = 0.0, pre1 = 0.0, pim0 = 0.0, pim1 = 0.0;
+#pragma unroll 2
+        for (int k0 = 0; k0 < sg.K; k0 += 4) {
+            const int k = k0 + tig;
+            double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+            if (rv && k < sg.K) a = A[k];
+            if (cv && k < sg.K) b = Bc[(int64_t)k * bk];
+            if (bc) b.y = neg_f64(b.y);
+            dmma_f64(pre0, pre1, a.x, b.x);           // Re += Re a Re b - Im a Im b
+            dmma_f64(pre0, pre1, neg_f64(a.y), b.y);
+            dmma_f64(pim0, pim1, a.x, b.y);           // Im += Re a Im b + Im a Re b
+            dmma_f64(pim0, pim1, a.y, b.x);
+        }
+        const double sr = sg.scale.x, si2 = sg.scale.y;   // segment factor on the block's partial product
+        cre0 += sr * pre0 - si2 * pim0; cim0 += sr * pim0 + si2 * pre0;
+        cre1 += sr * pre1 - si2 * pim1; cim1 += sr * pim1 + si2 * pre1;
+    }
+    if (!rv) return;
+    cplx* __restrict__ C = g.bufs[tk.c_buf] + tk.c_off;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int n = it.n0 + 2 * tig + e;
+        if (n < tk.N) {
+            cplx* p = tk.trans ? C + (int64_t)n * tk.ldc + r : C + (int64_t)r * tk.ldc + n;
+            double2 v = e ? make_double2(cre1, cim1) : make_double2(cre0, cim0);
+            if (tk.beta) { const double2 o = *p; v.x += o.x; v.y += o.y; }
+            *p = v;
+        }
+    }
 }
 
 // i-th tile of this CTA under static scheduling: blockIdx.x + i gridDim.x over the longest-first list
@@ -586,6 +646,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 }
             }
         }
+    } else if (warp >= 2 + EPIW) {   // ----------------------------------------------------------- thin FP64 warps
+        if (oa.tcta != nullptr) {
+            const int i1 = oa.tcta[blockIdx.x + 1];
+            for (int i = oa.tcta[blockIdx.x] + (warp - 2 - EPIW); i < i1; i += THINW) {
+                const ThinItem it = oa.titems[i];
+                thin_block(it, oa.ttasks[it.task], oa.tsegs, g, lane);
+            }
+        }
     } else {   // ------------------------------------------------------------------------ epilogue warps 2..17
         const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31 (16 of them hold rows)
         const int part = (warp - 2) >> 2;     // accumulator columns 16 * part .. 16 * part + 15
@@ -726,9 +794,8 @@ cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, co
     if constexpr (S <= 4) {
         const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
         const int ntiles = (int)st.tiles.size();
-        const int grid = std::max(1, std::min(ntiles, g_num_sms));
-        launch_pdl(k_ozaki_gemm_ws<S>, grid, WS_THREADS, smem, s, st.mapA, st.mapB, st.args, g, ntiles, st.queue, skip_flag,
-                                                           skip_step);
+        launch_pdl(k_ozaki_gemm_ws<S>, std::max(1, st.grid), WS_THREADS, smem, s, st.mapA, st.mapB, st.args, g, ntiles,
+                   st.queue, skip_flag, skip_step);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
@@ -776,6 +843,10 @@ void release_oz(tdmrg_ctx* c, OzPlan& oz) {
         dev_free(c, st.expA, st.exp_bytes_a);
         dev_free(c, st.expB, st.exp_bytes_b);
         dev_free(c, st.d_sched, 2 * sizeof(unsigned));
+        dev_free(c, st.d_ttasks, st.ttasks.size() * sizeof(Task));
+        dev_free(c, st.d_tsegs, st.tsegs.size() * sizeof(Seg));
+        dev_free(c, st.d_titems, st.titems.size() * sizeof(ThinItem));
+        dev_free(c, st.d_tcta, st.tcta.size() * sizeof(int));
         st = OzStage();
     }
     oz.status = nullptr;   // owned by the context
@@ -858,7 +929,27 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             const Task& tk = tl.tasks[t];
             const int nseg = tk.seg_end - tk.seg_begin;
             int ktot = 0;
-            for (int s = tk.seg_begin; s < tk.seg_end; ++s) ktot += tl.segs[s].K;
+            bool dev_scale = false;
+            for (int s = tk.seg_begin; s < tk.seg_end; ++s) { ktot += tl.segs[s].K; dev_scale |= tl.segs[s].dscale >= 0; }
+            // thin product: on the FP64 warps of the persistent kernel (S <= 4), in 8 x 8 output blocks, if one
+            // block's FP64 chain is short (GB300 runs an m8n8k4 FP64 MMA in ~640 cycles of a sub-partition)
+            int ksteps_all = 0;
+            for (int s = tk.seg_begin; s < tk.seg_end; ++s) ksteps_all += (tl.segs[s].K + 3) / 4;
+            if (S <= 4 && c->thin_dim > 0 && nseg > 0 && !dev_scale && std::min(tk.M, tk.N) < c->thin_dim &&
+                ksteps_all <= kThinMaxKsteps) {
+                Task nt = tk;
+                nt.seg_begin = (int)st.tsegs.size();
+                for (int s = tk.seg_begin; s < tk.seg_end; ++s) st.tsegs.push_back(tl.segs[s]);
+                nt.seg_end = (int)st.tsegs.size();
+                const int ti = (int)st.ttasks.size();
+                st.ttasks.push_back(nt);
+                int ksteps = 0;   // m8n8k4 steps of one block over all segments
+                for (int s = tk.seg_begin; s < tk.seg_end; ++s) ksteps += (tl.segs[s].K + 3) / 4;
+                for (int m0 = 0; m0 < tk.M; m0 += 8)
+                    for (int n0 = 0; n0 < tk.N; n0 += 8) st.titems.push_back({ti, m0, n0, std::max(ksteps, 1)});
+                st.thin_flops += 8.0 * tk.M * tk.N * (double)ktot;
+                continue;
+            }
             const bool ok = nseg > 0 && (stg == 1 || nseg == 1) && 2 * ktot <= 4096;
             if (!ok) {   // FP64 kernel
                 Task nt = tk;
@@ -919,6 +1010,25 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
                 for (int n0 = 0; n0 < tk.N; n0 += TNC) st.tiles.push_back({ti, m0, n0, (int)(std::min(tm, tk.M - m0) * std::min(TNC, tk.N - n0)) * ot.kchunks});
         }
         std::stable_sort(st.tiles.begin(), st.tiles.end(), [](const OzTile& a, const OzTile& b) { return a.cost > b.cost; });
+        // persistent grid: one CTA per SM when thin items exist (their warps ride along), else one per tile
+        st.grid = st.titems.empty() ? std::max(1, std::min((int)st.tiles.size(), c->num_sms)) : c->num_sms;
+        if (!st.titems.empty()) {   // thin items: longest first onto the least loaded CTA, grouped by CTA
+            std::stable_sort(st.titems.begin(), st.titems.end(),
+                             [](const ThinItem& a, const ThinItem& b) { return a.cost > b.cost; });
+            std::vector<int64_t> load(st.grid, 0);
+            std::vector<std::vector<ThinItem>> per(st.grid);
+            for (const ThinItem& it : st.titems) {
+                const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[b] += it.cost;
+                per[b].push_back(it);
+            }
+            st.titems.clear();
+            st.tcta.assign(1, 0);
+            for (const auto& v : per) {
+                st.titems.insert(st.titems.end(), v.begin(), v.end());
+                st.tcta.push_back((int)st.titems.size());
+            }
+        }
         // panels: rows padded so that every TMA box (tm rows for A, 64 for B) stays inside the plane
         st.rowsA = rowsA + tm;
         st.rowsB = rowsB + 2 * TNC;
@@ -936,6 +1046,21 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             st.bjobs[j].vec_prefix = (int)pre; pre += st.bjobs[j].nvec;
             st.bvjob.insert(st.bvjob.end(), st.bjobs[j].nvec, (int)j);
         }
+        if (!st.titems.empty()) {
+            rc = upload_vec(c, st.ttasks, &st.d_ttasks, "thin tasks");
+            if (!rc) rc = upload_vec(c, st.tsegs, &st.d_tsegs, "thin segments");
+            if (!rc) rc = upload_vec(c, st.titems, &st.d_titems, "thin items");
+            if (!rc) rc = upload_vec(c, st.tcta, &st.d_tcta, "thin items");
+            if (rc) return rc;
+        }
+        st.args.ttasks = st.d_ttasks; st.args.tsegs = st.d_tsegs; st.args.titems = st.d_titems; st.args.tcta = st.d_tcta;
+        st.args.status = oz.status;
+        if (!st.tasks.empty() || !st.titems.empty()) {   // work-queue counters (also for a stage of thin items only)
+            rc = dev_alloc(c, (void**)&st.d_sched, 2 * sizeof(unsigned), "ozaki work queue");
+            if (!rc) rc = cuda_check(c, cudaMemset(st.d_sched, 0, 2 * sizeof(unsigned)), "ozaki work queue");
+            if (rc) return rc;
+            st.args.sched = st.d_sched;
+        }
         if (!st.tasks.empty()) {
             rc = dev_alloc(c, (void**)&st.panelA, st.panel_bytes_a, "ozaki panels");
             if (!rc) rc = dev_alloc(c, (void**)&st.panelB, st.panel_bytes_b, "ozaki panels");
@@ -949,8 +1074,6 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (!rc) rc = upload_vec(c, st.bjobs, &st.d_bjobs, "ozaki slice jobs");
             if (!rc && !st.avjob.empty()) rc = upload_vec(c, st.avjob, &st.d_avjob, "ozaki slice jobs");
             if (!rc && !st.bvjob.empty()) rc = upload_vec(c, st.bvjob, &st.d_bvjob, "ozaki slice jobs");
-            if (!rc) rc = dev_alloc(c, (void**)&st.d_sched, 2 * sizeof(unsigned), "ozaki work queue");
-            if (!rc) rc = cuda_check(c, cudaMemset(st.d_sched, 0, 2 * sizeof(unsigned)), "ozaki work queue");
             if (!rc) rc = upload_vec(c, st.asegs, &st.d_asegs, "ozaki slice segments");
             if (!rc) rc = upload_vec(c, st.bsegs, &st.d_bsegs, "ozaki slice segments");
             if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, tm);
@@ -958,8 +1081,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (rc) return rc;
             st.args.tasks = st.d_tasks; st.args.tiles = st.d_tiles;
             st.args.expA = st.expA; st.args.expB = st.expB;
-            st.args.rowsA = st.rowsA; st.args.rowsB = st.rowsB; st.args.status = oz.status;
-            st.args.sched = st.d_sched;
+            st.args.rowsA = st.rowsA; st.args.rowsB = st.rowsB;
             auto mk = [&](OzSliceArgs& sa, const std::vector<OzSliceJob>& jobs, OzSliceJob* dj, const int* dv, Seg* ds,
                           __nv_bfloat16* panel, int* exps, int rows) {
                 sa.jobs = dj; sa.vjob = dv; sa.njobs = (int)jobs.size(); sa.segs = ds; sa.panel = panel; sa.exps = exps;
@@ -1012,9 +1134,11 @@ int run_oz(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* sk
     for (int stg = 0; stg < 2; ++stg) {
         const OzStage& st = oz.st[stg];
         cudaError_t e = cudaSuccess;
-        if (!st.tasks.empty()) {
-            e = slice_launch(stg == 0 ? st.sliceA : st.sliceB, g, s, skip_flag, skip_step);
-            c->launches++;
+        if (!st.tasks.empty() || !st.titems.empty()) {
+            if (!st.tasks.empty()) {
+                e = slice_launch(stg == 0 ? st.sliceA : st.sliceB, g, s, skip_flag, skip_step);
+                c->launches++;
+            }
             if (e == cudaSuccess) {
                 switch (oz.S) {
                     case 2: e = gemm_launch<2>(st, g, s, skip_flag, skip_step); break;

@@ -22,7 +22,7 @@ EXPORTED = [
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect", "tdmrg_overlap_op",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
-    "tdmrg_set_schedule", "tdmrg_probe_wait",
+    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
@@ -85,6 +85,8 @@ def load(path=LIB_PATH):
         "tdmrg_launch_count": (I, [P, PI64]),
         "tdmrg_alloc_count": (I, [P, PI64, PI64]),
         "tdmrg_set_schedule": (I, [P, I]),
+        "tdmrg_set_thin_dim": (I, [P, I]),
+        "tdmrg_hpsi_thin_flops": (I, [P, I, I, PD]),
         "tdmrg_probe_wait": (I, [P, I64]),
         "tdmrg_hpsi_flops": (I, [P, I, I, PD]),
         "tdmrg_hpsi_tensor_flops": (I, [P, I, I, PD]),
@@ -266,6 +268,16 @@ def tdmrg_probe_wait(ctx, spins):
 
 def tdmrg_set_schedule(ctx, mode):
     return _check(ctx, load().tdmrg_set_schedule(ctx, mode))
+
+
+def tdmrg_set_thin_dim(ctx, dim):
+    return _check(ctx, load().tdmrg_set_thin_dim(ctx, dim))
+
+
+def tdmrg_hpsi_thin_flops(ctx, Q):
+    f = ctypes.c_double()
+    _check(ctx, load().tdmrg_hpsi_thin_flops(ctx, Q[0], Q[1], ctypes.byref(f)))
+    return f.value
 
 
 def tdmrg_launch_count(ctx):

@@ -191,3 +191,32 @@ def test_ozaki_synthetic_evolve(lib):
             assert rel_err(host(tg[x]), ref[x]) < 1e-8
     finally:
         lib.tdmrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("thin_dim", [0, 8, 16, 64])
+@pytest.mark.parametrize("L,m,nb,seed", [(8, 24, 2, 3), (32, 400, 1, S.SEED_BASE + 1)])
+def test_thin_split_parity(lib, thin_dim, L, m, nb, seed):
+    """The split of the sector products between tensor tiles and the FP64 thin warps (thin_dim 0: all on
+    tensor tiles; 64: every product with a short K on FP64) leaves H psi within the tensor-path bound
+    of the oracle, and the thin part's flops are reported."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(L, m, 4.0, nbonds=nb, seed=seed)
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=4)
+    try:
+        problem.load_synthetic(ctx, ss)
+        lib.tdmrg_set_thin_dim(ctx, thin_dim)
+        for Q in (ss.Q0, ss.Q1):
+            n = lib.tdmrg_sector_size(ctx, Q)
+            x = _rand(n, 9)
+            out = dev(np.full(n, np.nan + 0j))
+            lib.tdmrg_apply_h(ctx, Q, dev(x), out)
+            ref = superblock.apply_h(sb, HL, HR, conns, Q, x)
+            assert rel_err(host(out), ref) < _tol(4), thin_dim
+            thin = lib.tdmrg_hpsi_thin_flops(ctx, Q)
+            assert (thin == 0.0) == (thin_dim == 0)
+            assert thin <= lib.tdmrg_hpsi_flops(ctx, Q)
+        with pytest.raises(lib.TdmrgError):
+            lib.tdmrg_set_thin_dim(ctx, 65)
+    finally:
+        lib.tdmrg_destroy(ctx)
