@@ -15,6 +15,7 @@ Modules
   krylov        Lanczos tridiagonalisation and the Krylov exponential (Sec. II.A, II.C)
   density       target weights and the weighted reduced density matrix (Sec. II.B, II.C)
   closed_forms  U=0 results of App. A and App. B, small-time expansion (Sec. III)
+  dmrg          textbook two-site DMRG (infinite + finite) of the Hubbard chain: truncated blocks (Sec. I)
 
 Every function is plain FP64 NumPy; a library primitive (matmul, eigh) may be
 a step, but there is no blocking or fusion beyond the paper's definitions.

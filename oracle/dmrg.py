@@ -1,0 +1,267 @@
+"""Textbook two-site DMRG for the open Hubbard chain: infinite, then finite algorithm (oracle; test
+infrastructure only).
+
+Sec. I: a block keeps the m most probable states of its reduced density matrix, computed from the
+superblock's targeted state, and every block operator is carried into the kept basis, O -> U^dag O U.
+The superblock is (left block + one site) + (one site + right block); the two enlarged blocks are the
+L and R blocks of the superblock product (Sec. II.B: alpha in L, beta in R).
+
+Conventions (the same as the exact blocks of blocks.py and the superblock of superblock.py):
+  - chain sites 0..L-1 from the left; H = -t sum_<ij> sigma (c^dag c + h.c.) + U sum n_up n_dn;
+  - fermion order: left block string, then right block string; inside an enlarged block the sites in
+    lattice order, so an odd operator of a later factor picks up the parity of the earlier factor;
+  - a block basis is sorted by its quantum number (n_up, n_dn), lexicographically, stably;
+  - every block operator is a dense matrix over the block basis (plain Kronecker products, then the
+    sector permutation); sector blocks are cut from it for the superblock product.
+A block carries its Hamiltonian and c^dag_{edge, sigma} of the site that bonds to the rest of the chain
+(the last site of a left block, the first site of a right block).
+
+Truncation (the reading of the silent paper): the eigenvalues of rho of all sectors are sorted in
+descending order; the m largest are kept; eigenvalues within 1e-12 lambda_max of the m-th largest are
+ties, broken by (sector index ascending, eigen index ascending).  Within a sector the kept states are
+then always the leading eigenvectors.
+
+Algorithm:
+  infinite: blocks of l sites on both sides grow one site per step (superblock of 2l + 2 sites at half
+            filling) until the superblock has L sites;
+  finite:   sweeps left to right and back over the stored blocks at fixed L (half filling), each step
+            a ground state by Lanczos with restarts, then truncation of the growing side.
+"""
+import numpy as np
+
+from . import blocks, density, krylov, superblock
+
+# single-site basis in sector order (n_up, n_dn): |0>, |dn>, |up>, |up dn>; blocks.py uses
+# (|0>, |up>, |dn>, |up dn>), so the operators are permuted from there
+SITE_QN = [(0, 0), (0, 1), (1, 0), (1, 1)]
+_PERM = [0, 2, 1, 3]
+SITE_CDAG = [blocks.SITE_CDAG_UP[np.ix_(_PERM, _PERM)].astype(complex),
+             blocks.SITE_CDAG_DN[np.ix_(_PERM, _PERM)].astype(complex)]
+SITE_P = np.diag([1.0, -1.0, -1.0, 1.0]).astype(complex)
+SITE_NN = np.diag([0.0, 0.0, 0.0, 1.0]).astype(complex)
+TIE_REL = 1e-12
+
+
+class DBlock:
+    """A block: basis quantum numbers (sorted), dense H, c^dag of the edge site per spin, site count."""
+
+    def __init__(self, qn, H, cdag, nsites):
+        self.qn = [tuple(q) for q in qn]
+        self.H = H
+        self.cdag = cdag
+        self.nsites = nsites
+
+    @property
+    def dim(self):
+        return len(self.qn)
+
+    def parity(self):
+        return np.diag([(-1.0) ** (a + b) for a, b in self.qn]).astype(complex)
+
+    def sectors(self):
+        """(sector list, dims, start offsets) of the sorted basis."""
+        secs, dims, starts = [], [], []
+        for k, q in enumerate(self.qn):
+            if not secs or secs[-1] != q:
+                secs.append(q)
+                dims.append(0)
+                starts.append(k)
+            dims[-1] += 1
+        return secs, dims, starts
+
+    def blockop(self, M, odd):
+        """Nonzero sector blocks of a dense operator on this block."""
+        secs, dims, starts = self.sectors()
+        out = {}
+        for a, (sa, da) in enumerate(zip(starts, dims)):
+            for b, (sb, db) in enumerate(zip(starts, dims)):
+                blk = M[sa: sa + da, sb: sb + db]
+                if np.any(blk != 0):
+                    out[(a, b)] = blk.copy()
+        return blocks.BlockOp(out, odd)
+
+
+def site_block(U):
+    return DBlock(SITE_QN, U * SITE_NN, [c.copy() for c in SITE_CDAG], 1)
+
+
+def _sorted(qn, mats):
+    order = sorted(range(len(qn)), key=lambda k: qn[k])   # stable: ties keep Kronecker order
+    ix = np.ix_(order, order)
+    return [qn[k] for k in order], [m[ix] for m in mats]
+
+
+def enlarge(blk, side, t, U):
+    """Left block + site (side 'L') or site + right block (side 'R'), with the bond between the block's
+    edge site and the new site; the new site becomes the edge."""
+    s = site_block(U)
+    Ib, I4 = np.eye(blk.dim, dtype=complex), np.eye(4, dtype=complex)
+    if side == "L":     # block string first: an odd site operator picks up the block parity
+        Pb = blk.parity()
+        H = np.kron(blk.H, I4) + np.kron(Ib, s.H)
+        cd_new = []
+        for sig in range(2):
+            cb = np.kron(blk.cdag[sig], I4)
+            cs = np.kron(Pb, s.cdag[sig])
+            H = H - t * (cb @ cs.conj().T + cs @ cb.conj().T)
+            cd_new.append(cs)
+        qn = [(a + c, b + d) for (a, b) in blk.qn for (c, d) in SITE_QN]
+    else:               # site string first: an odd block operator picks up the site parity
+        H = np.kron(s.H, Ib) + np.kron(I4, blk.H)
+        cd_new = []
+        for sig in range(2):
+            cs = np.kron(s.cdag[sig], Ib)
+            cb = np.kron(SITE_P, blk.cdag[sig])
+            H = H - t * (cs @ cb.conj().T + cb @ cs.conj().T)
+            cd_new.append(cs)
+        qn = [(c + a, d + b) for (c, d) in SITE_QN for (a, b) in blk.qn]
+    qn, mats = _sorted(qn, [H] + cd_new)
+    return DBlock(qn, mats[0], mats[1:], blk.nsites + 1)
+
+
+def superblock_of(L, R, t):
+    """Superblock, H_L, H_R and the boundary terms -t (c^dag_L c_R + h.c.) as fermionic products (left
+    operator first): -t c^dag_L c_R and +t c_L c^dag_R."""
+    lsec, ldim, _ = L.sectors()
+    rsec, rdim, _ = R.sectors()
+    sb = superblock.Superblock(lsec, ldim, rsec, rdim)
+    HL, HR = L.blockop(L.H, False), R.blockop(R.H, False)
+    conns = []
+    for sig in range(2):
+        cdL, cdR = L.blockop(L.cdag[sig], True), R.blockop(R.cdag[sig], True)
+        conns.append((-t, cdL, cdR.dagger()))
+        conns.append((t, cdL.dagger(), cdR))
+    return sb, HL, HR, conns
+
+
+def ground_state(apply_h, n, seed=11035391, nk=120):
+    """Lowest eigenpair by Lanczos with restarts (full re-orthogonalisation), FP64."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(n) + 0j
+    v /= np.linalg.norm(v)
+    e_old = None
+    for _ in range(60):
+        V, alpha, beta, b0, bn = krylov.lanczos(apply_h, v, min(nk, n), tol=1e-14)
+        d, S = np.linalg.eigh(krylov.tridiagonal(alpha, beta))
+        v = sum(S[k, 0] * V[k] for k in range(len(V)))
+        v /= np.linalg.norm(v)
+        k = np.argmax(np.abs(v))
+        v *= abs(v[k]) / v[k]
+        if e_old is not None and abs(d[0] - e_old) < 1e-13 * max(1.0, abs(d[0])):
+            if np.linalg.norm(apply_h(v) - d[0] * v) < 1e-9:
+                return d[0], v
+        e_old = d[0]
+    return d[0], v
+
+
+def kept_counts(evals, m, tie_rel=TIE_REL):
+    """Number of kept states per sector: the m largest eigenvalues over all sectors (each sector's list
+    in descending order), ties within tie_rel * lambda_max of the m-th largest broken by (sector index,
+    eigen index) ascending."""
+    allv = [(lam, s, k) for s, ev in enumerate(evals) for k, lam in enumerate(ev)]
+    counts = [0] * len(evals)
+    if len(allv) <= m:
+        return [len(ev) for ev in evals]
+    srt = sorted(allv, key=lambda x: -x[0])
+    lam_m = srt[m - 1][0]
+    tol = tie_rel * max(srt[0][0], 0.0)
+    above = [x for x in allv if x[0] > lam_m + tol]
+    tied = sorted([x for x in allv if abs(x[0] - lam_m) <= tol], key=lambda x: (x[1], x[2]))
+    for lam, s, k in above + tied[: m - len(above)]:
+        counts[s] += 1
+    return counts
+
+
+def rho_right(sb, Q, psi):
+    """rho_R per right sector: sum over alpha of Psi[alpha, beta] conj(Psi[alpha, beta'])."""
+    rho = [np.zeros((d, d), dtype=complex) for d in sb.rdim]
+    for qi, ri, off, dl, dr in sb.pairs(Q):
+        X = psi[off: off + dl * dr].reshape(dl, dr)
+        rho[ri] += X.T @ X.conj()
+    return rho
+
+
+def eig_desc(rho):
+    """Per sector (eigenvalues descending, eigenvectors as columns)."""
+    return density.rho_eig(rho)
+
+
+def truncate(blk, rho, m):
+    """Kept basis of an enlarged block from its reduced density matrix (list per sector): the block with
+    every operator renormalised, O -> U^dag O U, plus (kept counts, eigenvalues, discarded weight)."""
+    eig = eig_desc(rho)
+    counts = kept_counts([lam for lam, _ in eig], m)
+    secs, dims, starts = blk.sectors()
+    cols = []
+    qn = []
+    for s, ((lam, Uq), k) in enumerate(zip(eig, counts)):
+        if k == 0:
+            continue
+        Ufull = np.zeros((blk.dim, k), dtype=complex)
+        Ufull[starts[s]: starts[s] + dims[s], :] = Uq[:, :k]
+        cols.append(Ufull)
+        qn.extend([secs[s]] * k)
+    U = np.concatenate(cols, axis=1)
+    ren = lambda M: U.conj().T @ M @ U
+    discarded = sum(float(np.sum(lam[k:])) for (lam, _), k in zip(eig, counts))
+    return DBlock(qn, ren(blk.H), [ren(c) for c in blk.cdag], blk.nsites), counts, [lam for lam, _ in eig], discarded
+
+
+class ChainDMRG:
+    """Infinite + finite two-site DMRG of the open Hubbard chain of L sites (L even) at half filling."""
+
+    def __init__(self, L, t, U, m):
+        assert L % 2 == 0 and L >= 4
+        self.L, self.t, self.U, self.m = L, t, U, m
+        self.left = {1: site_block(U)}
+        self.right = {1: site_block(U)}
+        self.energies = []
+
+    def _step(self, l, r, Q):
+        Lenl = enlarge(self.left[l], "L", self.t, self.U)
+        Renl = enlarge(self.right[r], "R", self.t, self.U)
+        sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t)
+        e, psi = ground_state(lambda v: superblock.apply_h(sb, HL, HR, conns, Q, v), sb.size(Q))
+        return Lenl, Renl, sb, e, psi
+
+    def infinite(self):
+        l = 1
+        while 2 * l + 2 <= self.L:
+            Q = (l + 1, l + 1)
+            Lenl, Renl, sb, e, psi = self._step(l, l, Q)
+            self.energies.append(("infinite", 2 * l + 2, e))
+            self.left[l + 1] = truncate(Lenl, density.rho_left(sb, [(Q, psi)], [1.0]), self.m)[0]
+            self.right[l + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)[0]
+            l += 1
+
+    def sweep(self):
+        """One finite sweep: left to right (new left blocks), right to left (new right blocks), then left
+        to right back to the centre.  At left-block size l the right block has L - 2 - l sites."""
+        L, h = self.L, self.L // 2
+        Q = (h, h)
+        rho_l = lambda sb, psi: density.rho_left(sb, [(Q, psi)], [1.0])
+        for l in range(h - 1, L - 2):
+            Lenl, Renl, sb, e, psi = self._step(l, L - 2 - l, Q)
+            self.energies.append(("sweep right", l, e))
+            if l + 1 <= L - 3:
+                self.left[l + 1] = truncate(Lenl, rho_l(sb, psi), self.m)[0]
+        for r in range(1, L - 2):
+            Lenl, Renl, sb, e, psi = self._step(L - 2 - r, r, Q)
+            self.energies.append(("sweep left", L - 2 - r, e))
+            if r + 1 <= L - 3:
+                self.right[r + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)[0]
+        for l in range(1, h - 1):
+            Lenl, Renl, sb, e, psi = self._step(l, L - 2 - l, Q)
+            self.energies.append(("sweep right", l, e))
+            self.left[l + 1] = truncate(Lenl, rho_l(sb, psi), self.m)[0]
+
+    def run(self, sweeps=2):
+        """Infinite algorithm, `sweeps` finite sweeps, then the superblock at the central cut: returns
+        (Lenl, Renl, sb, HL, HR, conns, energy, psi) with Q = (L/2, L/2)."""
+        self.infinite()
+        for _ in range(sweeps):
+            self.sweep()
+        h = self.L // 2
+        Lenl, Renl, sb, e, psi = self._step(h - 1, h - 1, (h, h))
+        sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t)
+        return Lenl, Renl, sb, HL, HR, conns, e, psi
