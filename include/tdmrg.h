@@ -172,6 +172,27 @@ int tdmrg_density_matrix(tdmrg_ctx* ctx, int ntargets, const int32_t* Q, const t
  * truncation of Sec. II.B.  Errors: EINVAL, ESTATE, ECUDA. */
 int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg_c64* evecs_d);
 
+/* Truncation of the left block to at most m states (Sec. I: a block keeps the m most probable states of
+ * its reduced density matrix).  evals_d: rho_L's eigenvalues in the packed layout of tdmrg_rho_eig (per
+ * left sector, descending).  Kept set: the m largest eigenvalues over all sectors; eigenvalues within
+ * 1e-12 lambda_max of the m-th largest are ties, broken by (sector index, eigen index) ascending, so
+ * every sector keeps its leading eigenvectors.  kept_d (device, one int per left sector) receives the
+ * states kept per sector (all of them when the block has at most m); discarded_d (device, one double,
+ * nullable) the sum of the dropped eigenvalues (the truncation error).  Synchronises the stream once to
+ * upload the sector tables.  Errors: EINVAL (m < 1, more than 1024 sectors), ESTATE, ECUDA. */
+int tdmrg_truncate(tdmrg_ctx* ctx, const double* evals_d, int m, int32_t* kept_d, double* discarded_d);
+
+/* Operator of one side renormalised into the kept basis (Sec. I): O' = U^dag O U sector block by sector
+ * block, O'[q_out <- q_in] = U(q_out)[:, :k(q_out)]^dag O[q_out <- q_in] U(q_in)[:, :k(q_in)].
+ * U_d: per sector of that side a dim x dim row-major matrix whose column k is the k-th eigenvector
+ * (the layout of tdmrg_rho_eig); kept (host, one int per sector of that side) the kept counts k(q).
+ * out_d (device) receives, for every block of the operator in the order it was set whose two kept
+ * counts are nonzero, the k(q_out) x k(q_in) block row-major, concatenated; *nblk_out (host, nullable)
+ * their number.  FP64 grouped products; allocates a scratch buffer and synchronises the stream.
+ * Errors: EINVAL (unknown op id, kept count outside 0..dim), ESTATE, ENOMEM, ECUDA. */
+int tdmrg_renormalize_op(tdmrg_ctx* ctx, int side, int op_id, const tdmrg_c64* U_d, const int32_t* kept,
+                         tdmrg_c64* out_d, int* nblk_out);
+
 /* out_d[0] = <psi| opL opR |psi> / <psi|psi> for a sector-preserving product (Eq. generalcorrelation
  * with a = 1 local operator per block, Eq. nholondoublon; -1 = identity on that block).  out_d is
  * one device tdmrg_c64.  Errors as apply_op. */

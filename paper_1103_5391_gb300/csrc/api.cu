@@ -213,6 +213,7 @@ int tdmrg_destroy(tdmrg_ctx* c) {
     dev_free(c, c->red, 2 * 64 * kRedBlocks * sizeof(double2));
     dev_free(c, c->dscale, 64 * sizeof(double));
     dev_free(c, c->dstatus, sizeof(int));
+    dev_free(c, c->trunc_tables, c->trunc_tables_bytes);
     delete c;
     return TDMRG_OK;
 }

@@ -96,12 +96,13 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     Ain[r][k] = neg(v.y);
                 }
             }
-            if (seg.opb == OPB_N) {                   // B[k][n] at B[k*ldb + n]: threads along n
+            if (seg.opb == OPB_N || seg.opb == OPB_CN) {   // B[k][n] at B[k*ldb + n] (conjugated for 'CN'): threads along n
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int e = tid + 128 * u, k = e / TS, n = e % TS;
                     double2 v = make_double2(0.0, 0.0);
                     if (k < kc && n < Nt) v = B[(int64_t)(k0 + k) * seg.ldb + n0 + n];
+                    if (seg.opb == OPB_CN) v.y = neg(v.y);
                     if constexpr (kCorr) {
                         fB[0][k][n] = (float)v.x;
                         fB[1][k][n] = (float)v.y;

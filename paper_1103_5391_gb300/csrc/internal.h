@@ -52,7 +52,7 @@ enum BufId : int8_t { BUF_OPS = 0, BUF_IN = 1, BUF_SCRATCH = 2, BUF_OUT = 3, BUF
 constexpr int kMaxBufs = 16;
 
 // op(B) of a segment: 'N' B[k][n] at b[k*ldb+n]; 'T' at b[n*ldb+k]; 'C' conj of 'T'.
-enum OpB : int8_t { OPB_N = 0, OPB_T = 1, OPB_C = 2 };
+enum OpB : int8_t { OPB_N = 0, OPB_T = 1, OPB_C = 2, OPB_CN = 3 };   // OPB_CN: conj of 'N', B[k][n] = conj(b[k*ldb+n])
 
 // One contribution  scale * dscale * A[M x K] * op(B)[K x N]  to a task's output.
 struct Seg {
@@ -293,6 +293,8 @@ struct tdmrg_ctx {
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
     int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue
+    void* trunc_tables = nullptr;  // sector tables of tdmrg_truncate
+    size_t trunc_tables_bytes = 0;
     int thin_dim = 12;             // tensor path: sector products with min(M, N) below this run on FP64 warps
     int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
     tdmrg::EigWork eig;

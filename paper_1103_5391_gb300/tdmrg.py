@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_expect", "tdmrg_overlap_op",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_expect", "tdmrg_overlap_op",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -80,6 +80,8 @@ def load(path=LIB_PATH):
         "tdmrg_rho_size": (I, [P, PI64, PI64]),
         "tdmrg_density_matrix": (I, [P, I, PI32, ctypes.POINTER(P), PD, P]),
         "tdmrg_rho_eig": (I, [P, P, P, P]),
+        "tdmrg_truncate": (I, [P, P, I, P, P]),
+        "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
         "tdmrg_launch_count": (I, [P, PI64]),
@@ -250,6 +252,21 @@ def tdmrg_density_matrix(ctx, states, weights, rho):
 
 def tdmrg_rho_eig(ctx, rho, evals, evecs):
     return _check(ctx, load().tdmrg_rho_eig(ctx, _ptr(rho), _ptr(evals), _ptr(evecs)))
+
+
+def tdmrg_truncate(ctx, evals, m, kept, discarded=None):
+    """kept (device int32, one per left sector) <- kept counts of the m-state truncation; discarded
+    (device float64, optional) <- the dropped weight."""
+    return _check(ctx, load().tdmrg_truncate(ctx, _ptr(evals), int(m), _ptr(kept), _ptr(discarded)))
+
+
+def tdmrg_renormalize_op(ctx, side, op_id, U, kept, out):
+    """out (device complex128) <- U^dag O U per kept block; kept: host sequence of kept counts of that
+    side's sectors.  Returns the number of blocks written."""
+    k, kp = _i32(kept)
+    nb = ctypes.c_int()
+    _check(ctx, load().tdmrg_renormalize_op(ctx, side, op_id, _ptr(U), kp, _ptr(out), ctypes.byref(nb)))
+    return nb.value
 
 
 def tdmrg_expect(ctx, opL, opR, Q, psi, out):

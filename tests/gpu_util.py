@@ -75,3 +75,33 @@ class ExactLoader:
 
 def rel_err(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+class DmrgLoader:
+    """Loads the central-cut superblock of an oracle DMRG run (oracle.dmrg enlarged blocks) into libtdmrg:
+    ids 0 = H, 10 + s = c^dag_{edge s}, 30 + s = its adjoint, 50 + s = n_{edge s} on both sides; the
+    Hamiltonian's boundary terms -t c^dag_L c_R + t c_L c^dag_R per spin."""
+
+    def __init__(self, ctx, Lenl, Renl, t):
+        from paper_1103_5391_gb300 import tdmrg as T
+        self.T, self.ctx = T, ctx
+        self.blk = (Lenl, Renl)
+        for side, b in enumerate(self.blk):
+            secs, dims, _ = b.sectors()
+            T.tdmrg_set_block(ctx, side, secs, dims)
+            self.add(side, 0, b.H, False)
+            for s in range(2):
+                self.add(side, 10 + s, b.cdag[s], True)
+                self.add(side, 30 + s, b.cdag[s].conj().T, True)
+                self.add(side, 50 + s, b.cdag[s] @ b.cdag[s].conj().T, False)
+        conns = []
+        for s in range(2):
+            conns += [(10 + s, 30 + s, -t), (30 + s, 10 + s, t)]
+        T.tdmrg_set_hamiltonian(ctx, 0, 0, conns)
+
+    def add(self, side, op_id, dense, odd):
+        b = self.blk[side]
+        secs, _, _ = b.sectors()
+        bo = b.blockop(dense, odd)
+        self.T.tdmrg_set_op(self.ctx, side, op_id, odd, [(secs[qo], secs[qi], blk) for (qo, qi), blk in bo.blocks.items()])
+        return bo
