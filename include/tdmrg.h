@@ -120,6 +120,20 @@ int tdmrg_set_op(tdmrg_ctx* ctx, int side, int op_id, int fermion_odd, int nblk,
 int tdmrg_set_hamiltonian(tdmrg_ctx* ctx, int opHL, int opHR, int nconn, const int32_t* opL,
                           const int32_t* opR, const tdmrg_c64* coeff);
 
+/* Time-dependent Hamiltonian inside a captured step (the time-dependent Hamiltonians of Sec. I, e.g. a
+ * quench or a Peierls-phased pulse on the boundary hopping): coeff_d is a device array of nconn
+ * tdmrg_c64 values, the coefficients of the connections in the order given to tdmrg_set_hamiltonian.
+ * From this call on, every superblock product of the Hamiltonian reads connection k's coefficient from
+ * coeff_d[k] when it runs, instead of the value given to tdmrg_set_hamiltonian, so the caller may change
+ * the array between steps (a copy or a kernel on the stream, also as nodes of a captured CUDA graph)
+ * without any rebuild; H_L and H_R keep coefficient 1.  The caller keeps the array valid while it is
+ * set; NULL returns to the static coefficients; tdmrg_set_hamiltonian also clears it.  Plans are
+ * rebuilt on their next use (the call synchronises the stream).  With values equal to the static
+ * coefficients the FP64 path gives the same bits; the tensor path then folds the coefficients into the
+ * per-product slices of the intermediates instead of the operator slices, equal within its slicing
+ * error.  Errors: ESTATE (no Hamiltonian). */
+int tdmrg_set_coefficients(tdmrg_ctx* ctx, const tdmrg_c64* coeff_d);
+
 /* Length of the sector-Q wave function (number of complex entries; 0 if Q has no pairs). */
 int tdmrg_sector_size(tdmrg_ctx* ctx, int n_up, int n_dn, int64_t* dim_out);
 
@@ -206,6 +220,19 @@ int tdmrg_expect(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdm
  * product uses a library-owned scratch vector and a fixed-order FP64 reduction.  Errors as apply_op. */
 int tdmrg_overlap_op(tdmrg_ctx* ctx, int opL, int opR, int n_up1, int n_dn1, const tdmrg_c64* phi1_d,
                      int n_up2, int n_dn2, const tdmrg_c64* phi2_d, tdmrg_c64* out_d);
+
+/* Correlation grid, the two-state form of Eq. generalcorrelation with one local operator per block,
+ * e.g. the Green's function G_ij(t) = <phi(t)| c_i c^dag_j |psi(t)> (Sec. I) on device-resident states:
+ *   out_d[i * nR + j] = <phi1| opL[i] opR[j] |phi2>   (not normalised), i < nL, j < nR,
+ * each product with the fermion sign of tdmrg_apply_op (-1 = identity on that block, not both in one
+ * product); phi2_d lives in sector Q2 = (n_up2, n_dn2) and every product must map it to Q1 =
+ * (n_up1, n_dn1), the sector of phi1_d.  out_d: nL * nR device tdmrg_c64.  The whole grid runs as two
+ * grouped FP64 launches into library-owned scratch (nL * nR vectors of sector Q1 plus the
+ * intermediates) and one fixed-order reduction per entry.  The plan and scratch are built by the first
+ * call for a given (operator lists, sectors), which allocates and synchronises; later calls do neither
+ * and may be captured in a CUDA graph.  Errors: EINVAL, ESTATE, ESECTOR, ENOMEM, ECUDA. */
+int tdmrg_correlation(tdmrg_ctx* ctx, int nL, const int32_t* opL, int nR, const int32_t* opR, int n_up1, int n_dn1,
+                      const tdmrg_c64* phi1_d, int n_up2, int n_dn2, const tdmrg_c64* phi2_d, tdmrg_c64* out_d);
 
 /* ---- serving: continuous batching of time-evolution jobs ----------------------------------------
  * A server drives many independent time evolutions (each the repeated time step of Sec. II.C:

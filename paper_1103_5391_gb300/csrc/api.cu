@@ -77,6 +77,7 @@ void drop_plans(tdmrg_ctx* c) {
     c->plans.clear();
     for (auto& kv : c->rho_plans) release(c, *kv.second);
     c->rho_plans.clear();
+    release_corr(c);
 }
 
 void drop_krylov(tdmrg_ctx* c) {
@@ -347,10 +348,13 @@ int tdmrg_set_hamiltonian(tdmrg_ctx* c, int hl, int hr, int nconn, const int32_t
     for (int k = 0; k < nconn; ++k) {
         if (opL[k] < 0 && opR[k] < 0) return fail(c, TDMRG_EINVAL, "set_hamiltonian: connection without operators");
         if (check_op(c, 0, opL[k]) || check_op(c, 1, opR[k])) return TDMRG_EINVAL;
-        terms.push_back({opL[k], opR[k], make_double2(coeff[k].re, coeff[k].im)});
+        Term tm{opL[k], opR[k], make_double2(coeff[k].re, coeff[k].im)};
+        tm.conn = k;
+        terms.push_back(tm);
     }
     c->ham = terms;
     c->ham_set = true;
+    c->dcoef = nullptr;   // a new Hamiltonian starts with its static coefficients
     c->ham_version++;
     drop_plans(c);
     return TDMRG_OK;
@@ -504,6 +508,16 @@ int tdmrg_set_schedule(tdmrg_ctx* c, int mode) {
     DeviceGuard g(c->opts.device);
     c->schedule = mode;
     drop_plans(c);   // plans are rebuilt with the new schedule on their next use
+    return TDMRG_OK;
+}
+
+int tdmrg_set_coefficients(tdmrg_ctx* c, const tdmrg_c64* coeff_d) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "set_coefficients: Hamiltonian not set");
+    DeviceGuard g(c->opts.device);
+    cudaStreamSynchronize(c->stream);
+    c->dcoef = (const cplx*)coeff_d;
+    drop_plans(c);   // plans are rebuilt with run-time coefficients on their next use
     return TDMRG_OK;
 }
 

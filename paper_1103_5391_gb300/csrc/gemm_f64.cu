@@ -77,6 +77,12 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
             const double d = args.dscale[seg.dscale];
             sr *= d; si *= d;
         }
+        if (seg.dcoef >= 0 && args.dcoef != nullptr) {   // run-time coefficient of a connection term
+            const cplx d = args.dcoef[seg.dcoef];
+            const double tr = sr * d.x - si * d.y;
+            si = sr * d.y + si * d.x;
+            sr = tr;
+        }
         const bool scaled = !(sr == 1.0 && si == 0.0);
         const bool conj = seg.opb == OPB_C;
         for (int k0 = 0; k0 < seg.K; k0 += KC) {

@@ -61,6 +61,7 @@ struct Seg {
     int8_t a_buf, b_buf, opb, pad0;
     int32_t dscale;           // index into the launch's device real scales, -1 = none
     cplx scale;               // static complex factor (1 = none)
+    int32_t dcoef = -1;       // index into the launch's device complex coefficients (connection terms), -1 = none
 };
 
 // C[M x N] (row stride ldc, buffer c_buf) = (beta ? C : 0) + sum of segments [seg_begin, seg_end).
@@ -193,6 +194,18 @@ struct Plan {
     TaskList thin[2];
 };
 
+// The correlation grid <phi1| A_i B_j |phi2>: every product of the grid compiled into one pair of task
+// lists (stage 1 into per-product scratch, stage 2 into per-product output vectors W_ij), then dots.
+struct CorrPlan {
+    TaskList s1, s2;
+    int npairs = 0;
+    int64_t n1 = 0, scratch = 0;
+    cplx* T = nullptr;          // stage-1 intermediates of all products
+    cplx* W = nullptr;          // npairs vectors of sector Q1
+    double2* part = nullptr;    // dot partials, npairs x kCorrChunks
+};
+constexpr int kCorrChunks = 32;
+
 struct BlockOp {
     int side = 0, odd = 0;
     // (out sector, in sector) -> element offset in the op pool; dims from the sector tables
@@ -213,6 +226,7 @@ struct Side {
 struct Term {           // coeff * (A P_L^{odd B}) (x) B; -1 = identity
     int opL, opR;
     cplx coeff;
+    int conn = -1;      // index of a Hamiltonian connection (its coefficient may live on the device), -1 = none
 };
 
 struct KrylovWork {     // device workspace of tdmrg_evolve for one (Q, nk)
@@ -259,6 +273,7 @@ struct GemmArgs {
     const double* dscale;
     cplx* partials;
     int* counters;
+    const cplx* dcoef = nullptr;   // device coefficients of the Hamiltonian connections (null: static)
 };
 
 }  // namespace tdmrg
@@ -277,6 +292,7 @@ struct tdmrg_ctx {
     int ham_version = 0;
     std::map<std::tuple<int, int, int, int, int, int, int>, std::unique_ptr<tdmrg::Plan>> plans;
     std::map<std::vector<int>, std::unique_ptr<tdmrg::TaskList>> rho_plans;   // keyed by the targets' sectors
+    std::map<std::vector<int>, std::unique_ptr<tdmrg::CorrPlan>> corr_plans;  // keyed by operator lists and sectors
     // generic workspace
     tdmrg::cplx* scratch = nullptr;
     int64_t scratch_cap = 0;
@@ -295,7 +311,8 @@ struct tdmrg_ctx {
     int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue
     void* trunc_tables = nullptr;  // sector tables of tdmrg_truncate
     size_t trunc_tables_bytes = 0;
-    int thin_dim = 12;             // tensor path: sector products with min(M, N) below this run on FP64 warps
+    int thin_dim = 12;
+    const tdmrg::cplx* dcoef = nullptr;   // caller's device array of connection coefficients (null: static)             // tensor path: sector products with min(M, N) below this run on FP64 warps
     int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
     tdmrg::EigWork eig;
 };
@@ -310,7 +327,7 @@ void dev_free(tdmrg_ctx* c, void* p, size_t bytes);
 
 // plan.cu
 int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qin0, int qin1, int qout0, int qout1,
-               Plan* out);
+               Plan* out, bool to_device = true);
 int64_t sector_size(const tdmrg_ctx* c, int n_up, int n_dn);
 void make_tiles(TaskList& tl, int tm, int tn, int ksplit);
 int upload(tdmrg_ctx* c, TaskList& tl);
@@ -345,6 +362,9 @@ constexpr int kRedBlocks = 304;   // 2 x 152 SMs: fixed, so reductions are deter
 
 // density.cu
 int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho);
+
+// correlation.cu
+void release_corr(tdmrg_ctx* c);
 
 // eig.cu
 int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs);

@@ -84,6 +84,7 @@ extern "C" int tdmrg_apply_h_static(tdmrg_ctx* c, int n_up, int n_dn, const tdmr
     a.bufs[BUF_SCRATCH] = (cplx*)base;
     a.bufs[BUF_OUT] = (cplx*)out;
     a.dscale = c->dscale;
+    a.dcoef = c->dcoef;
     for (int st = 0; st < 2 && !rc; ++st) {
         const TaskList& tl = st == 0 ? p.stage1 : p.stage2;
         if (tl.tiles.empty()) continue;

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, Gemm
             const Seg sg = sa.segs[job.seg_begin + w0 + lane];
             SegView w;
             w.scale = sg.scale;
+            if (sg.dcoef >= 0 && g.dcoef != nullptr) w.scale = scaled(g.dcoef[sg.dcoef], sg.scale);   // run-time coefficient
             w.conj = 0;
             if (job.role == 0) {
                 w.base = g.bufs[sg.a_buf] + sg.a_off + (int64_t)v * sg.lda;
@@ -488,7 +489,13 @@ __device__ __forceinline__ void thin_block(const ThinItem& it, const Task& tk, c
             dmma_f64(pim0, pim1, a.x, b.y);           // Im += Re a Im b + Im a Re b
             dmma_f64(pim0, pim1, a.y, b.x);
         }
-        const double sr = sg.scale.x, si2 = sg.scale.y;   // segment factor on the block's partial product
+        double sr = sg.scale.x, si2 = sg.scale.y;   // segment factor on the block's partial product
+        if (sg.dcoef >= 0 && g.dcoef != nullptr) {   // run-time coefficient of a connection term
+            const cplx d = g.dcoef[sg.dcoef];
+            const double tr = sr * d.x - si2 * d.y;
+            si2 = sr * d.y + si2 * d.x;
+            sr = tr;
+        }
         cre0 += sr * pre0 - si2 * pim0; cim0 += sr * pim0 + si2 * pre0;
         cre1 += sr * pre1 - si2 * pim1; cim1 += sr * pim1 + si2 * pre1;
     }
@@ -950,7 +957,11 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
                 st.thin_flops += 8.0 * tk.M * tk.N * (double)ktot;
                 continue;
             }
-            const bool ok = nseg > 0 && (stg == 1 || nseg == 1) && 2 * ktot <= 4096;
+            // a stage-1 segment with a run-time coefficient would need its static operator slices redone at
+            // every product: such tasks stay on the FP64 kernel
+            bool run_time = false;
+            for (int s = tk.seg_begin; s < tk.seg_end; ++s) run_time |= tl.segs[s].dcoef >= 0;
+            const bool ok = nseg > 0 && (stg == 1 || nseg == 1) && 2 * ktot <= 4096 && !(stg == 0 && run_time);
             if (!ok) {   // FP64 kernel
                 Task nt = tk;
                 nt.seg_begin = (int)thin.segs.size();
@@ -980,12 +991,13 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
                     rowsA += tk.M;
                 }
                 ot.arow0 = it->second; ot.aexp0 = it->second;
-            } else {          // A = [ops of all segments], coefficients folded in: static
+            } else {          // A = [ops of all segments]: static, sliced once, with the segment factors
+                              // folded in, unless the coefficients are read at run time (then on B)
                 OzSliceJob j{};
                 j.role = 0; j.nvec = tk.M; j.seg_begin = (int)st.asegs.size();
                 for (int s = tk.seg_begin; s < tk.seg_end; ++s) st.asegs.push_back(tl.segs[s]);
                 j.seg_end = (int)st.asegs.size();
-                j.row0 = rowsA; j.exp0 = rowsA; j.ktot = ktot; j.use_scale = 1;
+                j.row0 = rowsA; j.exp0 = rowsA; j.ktot = ktot; j.use_scale = c->dcoef == nullptr ? 1 : 0;
                 st.ajobs.push_back(j);
                 ot.arow0 = rowsA; ot.aexp0 = rowsA;
                 rowsA += tk.M;
@@ -997,7 +1009,10 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
                 for (int s = tk.seg_begin; s < tk.seg_end; ++s) st.bsegs.push_back(tl.segs[s]);
                 j.seg_end = (int)st.bsegs.size();
                 j.row0 = rowsB; j.exp0 = st.ncolsB; j.ktot = ktot;
-                j.use_scale = stg == 0 ? 1 : 0;   // stage 1: the segment scale goes on the static B
+                // the segment factor (coefficient and fermion sign) goes on the static operator: B of stage 1,
+                // A of stage 2; with run-time coefficients the stage-2 factors go on B, the intermediates
+                // sliced at every product, so that they may change between products
+                j.use_scale = (stg == 0 || c->dcoef != nullptr) ? 1 : 0;
                 st.bjobs.push_back(j);
                 ot.brow0 = rowsB; ot.bexp0 = st.ncolsB;
                 const int full = tk.N / TNC, rem = tk.N % TNC;
@@ -1130,6 +1145,7 @@ int run_oz(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* sk
     g.bufs[BUF_SCRATCH] = c->scratch;
     g.bufs[BUF_OUT] = out;
     g.dscale = c->dscale;
+    g.dcoef = c->dcoef;
     cudaStream_t s = c->stream;
     for (int stg = 0; stg < 2; ++stg) {
         const OzStage& st = oz.st[stg];

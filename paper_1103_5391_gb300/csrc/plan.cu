@@ -143,7 +143,7 @@ std::vector<PairInfo> pairs_of(const tdmrg_ctx* c, int a, int b) {
 
 }  // namespace
 
-int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int oa, int ob, Plan* p) {
+int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int oa, int ob, Plan* p, bool to_device) {
     const Side& L = c->side[0];
     p->qin[0] = qa; p->qin[1] = qb; p->qout[0] = oa; p->qout[1] = ob;
     std::vector<PairInfo> pin = pairs_of(c, qa, qb), pout = pairs_of(c, oa, ob);
@@ -164,7 +164,11 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
             const BlockOp* A = t.opL >= 0 ? &c->ops[0].at(t.opL) : nullptr;
             const BlockOp* B = t.opR >= 0 ? &c->ops[1].at(t.opR) : nullptr;
             double sgn = (B && B->odd && nparity) ? -1.0 : 1.0;
-            cplx sc = make_double2(sgn * t.coeff.x, sgn * t.coeff.y);
+            // a connection's coefficient is either folded into the segment or read at run time from the
+            // caller's device array (tdmrg_set_coefficients); the fermion sign stays static
+            const bool run_time = c->dcoef != nullptr && t.conn >= 0;
+            cplx sc = run_time ? make_double2(sgn, 0.0) : make_double2(sgn * t.coeff.x, sgn * t.coeff.y);
+            const int dcoef = run_time ? t.conn : -1;
             std::vector<std::pair<int, int64_t>> al, bl;
             if (!A) al.push_back({pi.qi, -1});
             else for (auto& blk : A->blocks) if (std::get<1>(blk) == pi.qi) al.push_back({std::get<0>(blk), std::get<2>(blk)});
@@ -181,13 +185,13 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
                         Seg s{};
                         s.a_off = pi.off; s.a_buf = BUF_IN; s.lda = pi.dr;
                         s.b_off = b.second; s.b_buf = BUF_OPS; s.ldb = pi.dr; s.opb = OPB_T;
-                        s.K = pi.dr; s.scale = sc; s.dscale = -1;
+                        s.K = pi.dr; s.scale = sc; s.dscale = -1; s.dcoef = dcoef;
                         direct[ko].push_back(s);
                     } else if (!B) {   // Psi'_q += sc * A Psi_{q'}
                         Seg s{};
                         s.a_off = a.second; s.a_buf = BUF_OPS; s.lda = pi.dl;
                         s.b_off = pi.off; s.b_buf = BUF_IN; s.ldb = pi.dr; s.opb = OPB_N;
-                        s.K = pi.dl; s.scale = sc; s.dscale = -1;
+                        s.K = pi.dl; s.scale = sc; s.dscale = -1; s.dcoef = dcoef;
                         left[ko].push_back(s);
                     } else {           // T = Psi_{q'} B^T (scratch, stored as T^T), then Psi'_q += sc * A T
                         // T^T rows are the columns of T: the stage-1 stores and the stage-2 operand
@@ -204,7 +208,7 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
                         Seg s2{};
                         s2.a_off = a.second; s2.a_buf = BUF_OPS; s2.lda = pi.dl;
                         s2.b_off = scr; s2.b_buf = BUF_SCRATCH; s2.ldb = pi.dl; s2.opb = OPB_T;
-                        s2.K = pi.dl; s2.scale = sc; s2.dscale = -1;
+                        s2.K = pi.dl; s2.scale = sc; s2.dscale = -1; s2.dcoef = dcoef;
                         left[ko].push_back(s2);
                         scr += (int64_t)pi.dl * po.dr;
                     }
@@ -250,6 +254,7 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
     make_tiles(s2, kTileF64, kTileF64, kSplitK);
     p->scratch = scr;
     p->flops = s1.flops + s2.flops;
+    if (!to_device) return TDMRG_OK;   // host task lists only (merged into a larger launch by the caller)
     int urc = upload(c, s1);
     if (!urc) urc = upload(c, s2);
     if (urc) return urc;
@@ -272,6 +277,7 @@ int run_plan(tdmrg_ctx* c, const Plan& p, const cplx* in, cplx* out, const int* 
     a.bufs[BUF_SCRATCH] = c->scratch;
     a.bufs[BUF_OUT] = out;
     a.dscale = c->dscale;
+    a.dcoef = c->dcoef;
     for (const TaskList* tl : {&p.stage1, &p.stage2}) {
         if (tl->tiles.empty()) continue;
         a.tasks = tl->d_tasks; a.segs = tl->d_segs; a.tiles = tl->d_tiles; a.ntiles = (int)tl->tiles.size();

@@ -18,9 +18,9 @@ TDMRG_FP64, TDMRG_OZAKI_BF16 = 0, 1
 
 EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
-    "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_sector_size",
+    "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_expect", "tdmrg_overlap_op",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -71,6 +71,7 @@ def load(path=LIB_PATH):
         "tdmrg_set_block": (I, [P, I, I, PI32, PI32]),
         "tdmrg_set_op": (I, [P, I, I, I, I, PI32, P, I]),
         "tdmrg_set_hamiltonian": (I, [P, I, I, I, PI32, PI32, P]),
+        "tdmrg_set_coefficients": (I, [P, P]),
         "tdmrg_sector_size": (I, [P, I, I, PI64]),
         "tdmrg_apply_h": (I, [P, I, I, P, P]),
         "tdmrg_apply_op": (I, [P, I, I, I, I, P, I, I, P]),
@@ -84,6 +85,7 @@ def load(path=LIB_PATH):
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
+        "tdmrg_correlation": (I, [P, I, PI32, I, PI32, I, I, P, I, I, P, P]),
         "tdmrg_launch_count": (I, [P, PI64]),
         "tdmrg_alloc_count": (I, [P, PI64, PI64]),
         "tdmrg_set_schedule": (I, [P, I]),
@@ -196,6 +198,11 @@ def tdmrg_set_hamiltonian(ctx, opHL, opHR, conns):
     return _check(ctx, load().tdmrg_set_hamiltonian(ctx, opHL, opHR, n, pL, pR, co.ctypes.data_as(ctypes.c_void_p)))
 
 
+def tdmrg_set_coefficients(ctx, coeff_d):
+    """Connection coefficients read at run time from the device array coeff_d (None: static)."""
+    return _check(ctx, load().tdmrg_set_coefficients(ctx, _ptr(coeff_d) if coeff_d is not None else None))
+
+
 def tdmrg_sector_size(ctx, Q):
     n = ctypes.c_int64()
     _check(ctx, load().tdmrg_sector_size(ctx, Q[0], Q[1], ctypes.byref(n)))
@@ -271,6 +278,14 @@ def tdmrg_renormalize_op(ctx, side, op_id, U, kept, out):
 
 def tdmrg_expect(ctx, opL, opR, Q, psi, out):
     return _check(ctx, load().tdmrg_expect(ctx, opL, opR, Q[0], Q[1], _ptr(psi), _ptr(out)))
+
+
+def tdmrg_correlation(ctx, opsL, opsR, Q1, phi1, Q2, phi2, out):
+    """out (device complex128, len(opsL) * len(opsR)) <- <phi1| opsL[i] opsR[j] |phi2>."""
+    a, ap = _i32(opsL)
+    b, bp = _i32(opsR)
+    return _check(ctx, load().tdmrg_correlation(ctx, len(a), ap, len(b), bp, Q1[0], Q1[1], _ptr(phi1), Q2[0], Q2[1],
+                                                _ptr(phi2), _ptr(out)))
 
 
 def tdmrg_overlap_op(ctx, opL, opR, Q1, phi1, Q2, phi2, out):
