@@ -178,6 +178,15 @@ int tdmrg_rho_size(tdmrg_ctx* ctx, int64_t* rho_entries, int64_t* n_evals);
 int tdmrg_density_matrix(tdmrg_ctx* ctx, int ntargets, const int32_t* Q, const tdmrg_c64* const* psi_d,
                          const double* w, tdmrg_c64* rho_d);
 
+/* Real-basis variant of time-step targeting (on = 1; 0 = off, the default): tdmrg_density_matrix then
+ * forms Re rho_L = sum_l w_l (Re Psi_l(q) Re Psi_l(q)^T + Im Psi_l(q) Im Psi_l(q)^T) / <psi_l|psi_l>,
+ * i.e. the real and imaginary parts of every target targeted apart with its weight (Eq. rdensitymatrix
+ * on real states; the paper is silent on complex targets).  Re rho_L is real symmetric, so its
+ * eigenvectors from tdmrg_rho_eig are real and block operators renormalised with them stay real; the
+ * library detects real operators (zero imaginary parts, tdmrg_set_op) and skips their imaginary
+ * products, half the work of a complex product.  Errors: EINVAL (null context). */
+int tdmrg_set_real_basis(tdmrg_ctx* ctx, int on);
+
 /* Eigendecomposition of a packed rho_L (as written by tdmrg_density_matrix) to FP64 accuracy per sector
  * (dL <= 512): FP32 Jacobi seed, FP64 iterative refinement (Ogita-Aishima) with re-seeding of coupled
  * clusters.

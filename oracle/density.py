@@ -26,14 +26,20 @@ def tst_weights(n_v):
     return 2 * omega, w
 
 
-def rho_left(sb, states, weights):
-    """rho_L per left sector (list indexed by left sector, dL x dL complex), states = [(Q, psi)]."""
+def rho_left(sb, states, weights, real_basis=False):
+    """rho_L per left sector (list indexed by left sector, dL x dL complex), states = [(Q, psi)].
+
+    real_basis: the real and imaginary parts of every target are targeted apart with its weight,
+    rho_L = sum_l w_l (Re X_l Re X_l^T + Im X_l Im X_l^T) / <psi_l|psi_l> (real symmetric)."""
     rho = [np.zeros((d, d), dtype=complex) for d in sb.ldim]
     for (Q, psi), w in zip(states, weights):
         nrm2 = np.vdot(psi, psi).real
         for qi, ri, off, dl, dr in sb.pairs(Q):
             X = psi[off: off + dl * dr].reshape(dl, dr)
-            rho[qi] += (w / nrm2) * (X @ X.conj().T)
+            if real_basis:
+                rho[qi] += (w / nrm2) * (X.real @ X.real.T + X.imag @ X.imag.T)
+            else:
+                rho[qi] += (w / nrm2) * (X @ X.conj().T)
     return rho
 
 

@@ -308,6 +308,20 @@ int tdmrg_set_op(tdmrg_ctx* c, int side, int id, int odd, int nblk, const int32_
         c->pool = np;
         c->pool_cap = cap;
     }
+    // real operator: every imaginary part is zero (checked on a host copy of device data)
+    {
+        std::vector<tdmrg_c64> hcopy;
+        const tdmrg_c64* h = data;
+        if (on_device && total) {
+            hcopy.resize(total);
+            int rc = cuda_check(c, cudaMemcpy(hcopy.data(), data, total * sizeof(tdmrg_c64), cudaMemcpyDeviceToHost),
+                                "set_op realness check");
+            if (rc) return rc;
+            h = hcopy.data();
+        }
+        op.real = 1;
+        for (int64_t k = 0; k < total && op.real; ++k) op.real = h[k].im == 0.0;
+    }
     int64_t off = c->pool_used;
     int64_t src = 0;
     for (int b = 0; b < nblk; ++b) {
@@ -518,6 +532,12 @@ int tdmrg_set_coefficients(tdmrg_ctx* c, const tdmrg_c64* coeff_d) {
     cudaStreamSynchronize(c->stream);
     c->dcoef = (const cplx*)coeff_d;
     drop_plans(c);   // plans are rebuilt with run-time coefficients on their next use
+    return TDMRG_OK;
+}
+
+int tdmrg_set_real_basis(tdmrg_ctx* c, int on) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    c->real_basis = on ? 1 : 0;
     return TDMRG_OK;
 }
 

@@ -29,6 +29,14 @@ __global__ void k_weight_scale(const double2* __restrict__ part, int nt, double*
     if (lane == 0) dscale[l] = s > 0.0 ? ws.w[l] / s : 0.0;
 }
 
+// Real-basis variant: Re rho_L = sum_l w_l (Re Psi_l Re Psi_l^T + Im Psi_l Im Psi_l^T) / <psi_l|psi_l>, the
+// real part of the Hermitian rho_L (each target's real and imaginary parts targeted apart).
+__global__ void k_real_part(cplx* __restrict__ rho, int64_t n) {
+    pdl_enter();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rho[i].y = 0.0;
+}
+
 }  // namespace
 
 int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho) {
@@ -92,6 +100,13 @@ int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* ps
     a.dscale = c->dscale;
     cudaError_t e = launch_gemm_f64(a, s, nullptr, 0);
     c->launches++;
+    if (e == cudaSuccess && c->real_basis) {
+        int64_t nr = 0;
+        for (int d : L.dim) nr += (int64_t)d * d;
+        launch_pdl(k_real_part, (int)std::min<int64_t>((nr + 255) / 256, 4L * c->num_sms), 256, 0, s, rho, nr);
+        c->launches++;
+        e = cudaGetLastError();
+    }
     return cuda_check(c, e, "density_matrix launch");
 }
 

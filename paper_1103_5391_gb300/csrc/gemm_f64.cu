@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
         }
         const bool scaled = !(sr == 1.0 && si == 0.0);
         const bool conj = seg.opb == OPB_C;
+        const bool a_real = (seg.rflags & 1) != 0, b_real = (seg.rflags & 2) != 0;   // skip zero imaginary products
         for (int k0 = 0; k0 < seg.K; k0 += KC) {
             const int kc = min(KC, seg.K - k0);
 #pragma unroll
@@ -147,14 +148,24 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
                     }
                 }
             } else if (active) {
-                for (int kk = 0; kk < kc; kk += 4) {   // zero-padded beyond kc
-                    const double ar = Are[8 * bi + gid][kk + tig], ai = Aim[8 * bi + gid][kk + tig];
-                    const double an = Ain[8 * bi + gid][kk + tig];
-                    const double br = Bre[kk + tig][8 * bj + gid], bm = Bim[kk + tig][8 * bj + gid];
-                    dmma(cre[0], cre[1], ar, br);
-                    dmma(cre[0], cre[1], an, bm);
-                    dmma(cim[0], cim[1], ar, bm);
-                    dmma(cim[0], cim[1], ai, br);
+                if (a_real || b_real) {   // one operand real: two real MMAs per complex k-step
+                    for (int kk = 0; kk < kc; kk += 4) {
+                        const double ar = Are[8 * bi + gid][kk + tig], ai = Aim[8 * bi + gid][kk + tig];
+                        const double br = Bre[kk + tig][8 * bj + gid], bm = Bim[kk + tig][8 * bj + gid];
+                        dmma(cre[0], cre[1], ar, br);
+                        if (a_real) dmma(cim[0], cim[1], ar, bm);
+                        else dmma(cim[0], cim[1], ai, br);
+                    }
+                } else {
+                    for (int kk = 0; kk < kc; kk += 4) {   // zero-padded beyond kc
+                        const double ar = Are[8 * bi + gid][kk + tig], ai = Aim[8 * bi + gid][kk + tig];
+                        const double an = Ain[8 * bi + gid][kk + tig];
+                        const double br = Bre[kk + tig][8 * bj + gid], bm = Bim[kk + tig][8 * bj + gid];
+                        dmma(cre[0], cre[1], ar, br);
+                        dmma(cre[0], cre[1], an, bm);
+                        dmma(cim[0], cim[1], ar, bm);
+                        dmma(cim[0], cim[1], ai, br);
+                    }
                 }
             }
             __syncthreads();

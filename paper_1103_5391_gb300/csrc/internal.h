@@ -58,7 +58,8 @@ enum OpB : int8_t { OPB_N = 0, OPB_T = 1, OPB_C = 2, OPB_CN = 3 };   // OPB_CN: 
 struct Seg {
     int64_t a_off, b_off;     // element offsets into buffers a_buf, b_buf
     int32_t lda, ldb, K;
-    int8_t a_buf, b_buf, opb, pad0;
+    int8_t a_buf, b_buf, opb;
+    int8_t rflags;            // bit 0: A (with the scale) real, bit 1: B real -- their imaginary products are skipped
     int32_t dscale;           // index into the launch's device real scales, -1 = none
     cplx scale;               // static complex factor (1 = none)
     int32_t dcoef = -1;       // index into the launch's device complex coefficients (connection terms), -1 = none
@@ -208,6 +209,7 @@ constexpr int kCorrChunks = 32;
 
 struct BlockOp {
     int side = 0, odd = 0;
+    int real = 0;             // every block has zero imaginary parts (the real-basis variant keeps operators real)
     // (out sector, in sector) -> element offset in the op pool; dims from the sector tables
     std::vector<std::tuple<int, int, int64_t>> blocks;
     int version = 0;
@@ -312,6 +314,7 @@ struct tdmrg_ctx {
     void* trunc_tables = nullptr;  // sector tables of tdmrg_truncate
     size_t trunc_tables_bytes = 0;
     int thin_dim = 12;
+    int real_basis = 0;            // tdmrg_density_matrix forms Re rho_L (targets' real and imaginary parts apart)
     const tdmrg::cplx* dcoef = nullptr;   // caller's device array of connection coefficients (null: static)             // tensor path: sector products with min(M, N) below this run on FP64 warps
     int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
     tdmrg::EigWork eig;

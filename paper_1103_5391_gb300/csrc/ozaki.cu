@@ -477,6 +477,7 @@ __device__ __forceinline__ void thin_block(const ThinItem& it, const Task& tk, c
         const cplx* __restrict__ Bc = bn ? B + cb : B + (int64_t)cb * sg.ldb;   // column cb of op(B)
         const int64_t bk = bn ? sg.ldb : 1;                                         // its step along k
         double pre0 = 0.0, pre1 = 0.0, pim0 = 0.0, pim1 = 0.0;
+        const bool a_real = (sg.rflags & 1) != 0, b_real = (sg.rflags & 2) != 0;   // zero imaginary products skipped
 #pragma unroll 2
         for (int k0 = 0; k0 < sg.K; k0 += 4) {
             const int k = k0 + tig;
@@ -485,9 +486,9 @@ __device__ __forceinline__ void thin_block(const ThinItem& it, const Task& tk, c
             if (cv && k < sg.K) b = Bc[(int64_t)k * bk];
             if (bc) b.y = neg_f64(b.y);
             dmma_f64(pre0, pre1, a.x, b.x);           // Re += Re a Re b - Im a Im b
-            dmma_f64(pre0, pre1, neg_f64(a.y), b.y);
-            dmma_f64(pim0, pim1, a.x, b.y);           // Im += Re a Im b + Im a Re b
-            dmma_f64(pim0, pim1, a.y, b.x);
+            if (!a_real && !b_real) dmma_f64(pre0, pre1, neg_f64(a.y), b.y);
+            if (!b_real) dmma_f64(pim0, pim1, a.x, b.y);   // Im += Re a Im b + Im a Re b
+            if (!a_real) dmma_f64(pim0, pim1, a.y, b.x);
         }
         double sr = sg.scale.x, si2 = sg.scale.y;   // segment factor on the block's partial product
         if (sg.dcoef >= 0 && g.dcoef != nullptr) {   // run-time coefficient of a connection term
@@ -973,7 +974,11 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             OzTask ot{};
             ot.c_off = tk.c_off; ot.c_buf = tk.c_buf; ot.ldc = tk.ldc; ot.M = tk.M; ot.N = tk.N; ot.beta = tk.beta;
             ot.trans = tk.trans;
-            ot.kchunks = (2 * ktot + KCH - 1) / KCH;
+            // every A segment real (stage 2, real operators with real factors): A' = [Re A | 0], and the first
+            // halves of the B' rows hold Re b and Im b, so only the first ktot of the real K are used
+            bool all_a_real = stg == 1;
+            for (int s = tk.seg_begin; s < tk.seg_end; ++s) all_a_real &= (tl.segs[s].rflags & 1) != 0;
+            ot.kchunks = ((all_a_real ? ktot : 2 * ktot) + KCH - 1) / KCH;
             kmax = std::max(kmax, 2 * ktot);
             // A operand
             if (stg == 0) {   // A = Psi_{q'}: one dynamic row-sliced panel per input pair, shared by its tasks

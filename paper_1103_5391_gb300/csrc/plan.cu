@@ -70,8 +70,11 @@ void make_tiles(TaskList& tl, int tm, int tn, int ksplit) {
     for (size_t t = 0; t < tl.tasks.size(); ++t) {
         const Task& k = tl.tasks[t];
         int64_t ksum = 0;
-        for (int s = k.seg_begin; s < k.seg_end; ++s) ksum += tl.segs[s].K;
-        tl.flops += 8.0 * (double)k.M * k.N * (double)ksum;
+        for (int s = k.seg_begin; s < k.seg_end; ++s) {
+            ksum += tl.segs[s].K;
+            // 8 real flops per complex multiply-add, 4 when one operand is real
+            tl.flops += (tl.segs[s].rflags ? 4.0 : 8.0) * (double)k.M * k.N * (double)tl.segs[s].K;
+        }
         // split long K along segment boundaries into parts of about ksplit
         std::vector<std::pair<int, int>> parts;
         const int nseg = k.seg_end - k.seg_begin;
@@ -169,6 +172,10 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
             const bool run_time = c->dcoef != nullptr && t.conn >= 0;
             cplx sc = run_time ? make_double2(sgn, 0.0) : make_double2(sgn * t.coeff.x, sgn * t.coeff.y);
             const int dcoef = run_time ? t.conn : -1;
+            // real operands skip their imaginary products: A (left operator) with a real static factor,
+            // B (right operator) always (its factor goes on A in the FP64 kernel)
+            const int8_t a_real = (A && A->real && sc.y == 0.0 && dcoef < 0) ? 1 : 0;
+            const int8_t b_real = (B && B->real) ? 2 : 0;
             std::vector<std::pair<int, int64_t>> al, bl;
             if (!A) al.push_back({pi.qi, -1});
             else for (auto& blk : A->blocks) if (std::get<1>(blk) == pi.qi) al.push_back({std::get<0>(blk), std::get<2>(blk)});
@@ -186,12 +193,14 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
                         s.a_off = pi.off; s.a_buf = BUF_IN; s.lda = pi.dr;
                         s.b_off = b.second; s.b_buf = BUF_OPS; s.ldb = pi.dr; s.opb = OPB_T;
                         s.K = pi.dr; s.scale = sc; s.dscale = -1; s.dcoef = dcoef;
+                        s.rflags = b_real;
                         direct[ko].push_back(s);
                     } else if (!B) {   // Psi'_q += sc * A Psi_{q'}
                         Seg s{};
                         s.a_off = a.second; s.a_buf = BUF_OPS; s.lda = pi.dl;
                         s.b_off = pi.off; s.b_buf = BUF_IN; s.ldb = pi.dr; s.opb = OPB_N;
                         s.K = pi.dl; s.scale = sc; s.dscale = -1; s.dcoef = dcoef;
+                        s.rflags = a_real;
                         left[ko].push_back(s);
                     } else {           // T = Psi_{q'} B^T (scratch, stored as T^T), then Psi'_q += sc * A T
                         // T^T rows are the columns of T: the stage-1 stores and the stage-2 operand
@@ -203,12 +212,14 @@ int build_plan(tdmrg_ctx* c, const std::vector<Term>& terms, int qa, int qb, int
                         s.a_off = pi.off; s.a_buf = BUF_IN; s.lda = pi.dr;
                         s.b_off = b.second; s.b_buf = BUF_OPS; s.ldb = pi.dr; s.opb = OPB_T;
                         s.K = pi.dr; s.scale = one; s.dscale = -1;
+                        s.rflags = b_real;
                         s1_inter.push_back(tk);
                         s1_inter_seg.push_back(s);
                         Seg s2{};
                         s2.a_off = a.second; s2.a_buf = BUF_OPS; s2.lda = pi.dl;
                         s2.b_off = scr; s2.b_buf = BUF_SCRATCH; s2.ldb = pi.dl; s2.opb = OPB_T;
                         s2.K = pi.dl; s2.scale = sc; s2.dscale = -1; s2.dcoef = dcoef;
+                        s2.rflags = a_real;
                         left[ko].push_back(s2);
                         scr += (int64_t)pi.dl * po.dr;
                     }

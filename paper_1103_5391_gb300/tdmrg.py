@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -81,6 +81,7 @@ def load(path=LIB_PATH):
         "tdmrg_rho_size": (I, [P, PI64, PI64]),
         "tdmrg_density_matrix": (I, [P, I, PI32, ctypes.POINTER(P), PD, P]),
         "tdmrg_rho_eig": (I, [P, P, P, P]),
+        "tdmrg_set_real_basis": (I, [P, I]),
         "tdmrg_truncate": (I, [P, P, I, P, P]),
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
@@ -255,6 +256,10 @@ def tdmrg_density_matrix(ctx, states, weights, rho):
     w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
     return _check(ctx, load().tdmrg_density_matrix(ctx, len(states), qp, arr,
                                                    w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
+
+
+def tdmrg_set_real_basis(ctx, on):
+    return _check(ctx, load().tdmrg_set_real_basis(ctx, 1 if on else 0))
 
 
 def tdmrg_rho_eig(ctx, rho, evals, evecs):

@@ -58,3 +58,25 @@ def test_mixed_sector_rho_properties():
     for (lam, U), r in zip(density.rho_eig(rho), rho):
         assert np.all(np.diff(lam) <= 1e-15)
         assert np.abs(U @ np.diag(lam) @ U.conj().T - r).max() < 1e-13
+
+
+def test_real_basis_rho_is_real_part():
+    """Targeting the real and imaginary parts apart gives Re rho_L (the real part of the Hermitian
+    rho_L): checked against np.real of the complex rho_L, which is computed by a different formula;
+    for real targets the two coincide; trace = sum of weights, positive semidefinite."""
+    from oracle import density, superblock
+    from workloads import sectors as S
+    ss = S.make_synthetic(10, 40, 4.0, nbonds=1, seed=S.SEED_BASE + 21)
+    sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
+    states = [(ss.Q0, ss.psi_gs), (ss.Q1, ss.phi)]
+    w = [0.75, 0.25]
+    rc = density.rho_left(sb, states, w)
+    rr = density.rho_left(sb, states, w, real_basis=True)
+    for a, b in zip(rc, rr):
+        assert np.abs(b.imag).max() == 0.0
+        assert np.abs(b - a.real).max() < 1e-15
+        assert np.linalg.eigvalsh(b).min() > -1e-14
+    assert abs(sum(np.trace(b).real for b in rr) - 1.0) < 1e-13
+    real_states = [(Q, v.real + 0j) for Q, v in states]
+    for a, b in zip(density.rho_left(sb, real_states, w), density.rho_left(sb, real_states, w, real_basis=True)):
+        assert np.abs(a - b).max() < 1e-15
