@@ -120,6 +120,8 @@ def parse():
     ap.add_argument("--gap-ms", type=float, default=20.0, help="serving: mean inter-arrival time")
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="only apply H psi N times on the workload (a short run for ncu captures)")
+    ap.add_argument("--thin-dim", type=int, default=None,
+                    help="profile mode: products with fewer rows or columns run on the FP64 thin warps (0 = none)")
     ap.add_argument("--precision-errors", action="store_true",
                     help="errors of the tensor path (S = 2..6 slices) against the FP64 path on the L=48 m=1000 chain")
     return ap.parse_args()
@@ -782,6 +784,8 @@ def run_profile_hpsi(args):
     ctx = T.tdmrg_create(device=0, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
     try:
         problem.load_synthetic(ctx, ss)
+        if args.thin_dim is not None:
+            T.tdmrg_set_thin_dim(ctx, args.thin_dim)
         n = T.tdmrg_sector_size(ctx, ss.Q1)
         x = torch.randn(n, dtype=torch.complex128, device="cuda")
         y = torch.zeros_like(x)
