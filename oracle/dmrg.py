@@ -88,7 +88,7 @@ def site_block(U):
 def _sorted(qn, mats):
     order = sorted(range(len(qn)), key=lambda k: qn[k])   # stable: ties keep Kronecker order
     ix = np.ix_(order, order)
-    return [qn[k] for k in order], [m[ix] for m in mats]
+    return [qn[k] for k in order], [m[ix] for m in mats], order
 
 
 def enlarge(blk, side, t, U):
@@ -115,8 +115,10 @@ def enlarge(blk, side, t, U):
             H = H - t * (cs @ cb.conj().T + cb @ cs.conj().T)
             cd_new.append(cs)
         qn = [(c + a, d + b) for (c, d) in SITE_QN for (a, b) in blk.qn]
-    qn, mats = _sorted(qn, [H] + cd_new)
-    return DBlock(qn, mats[0], mats[1:], blk.nsites + 1)
+    qn, mats, order = _sorted(qn, [H] + cd_new)
+    out = DBlock(qn, mats[0], mats[1:], blk.nsites + 1)
+    out.perm = order   # Kronecker index of each basis state: a * 4 + s (side 'L') or s * dim + a (side 'R')
+    return out
 
 
 def superblock_of(L, R, t):
@@ -188,7 +190,8 @@ def eig_desc(rho):
 
 def truncate(blk, rho, m):
     """Kept basis of an enlarged block from its reduced density matrix (list per sector): the block with
-    every operator renormalised, O -> U^dag O U, plus (kept counts, eigenvalues, discarded weight)."""
+    every operator renormalised, O -> U^dag O U, plus (kept counts, eigenvalues, discarded weight, U),
+    U (block dim x kept) holding the kept states in the enlarged block's basis, sector by sector."""
     eig = eig_desc(rho)
     counts = kept_counts([lam for lam, _ in eig], m)
     secs, dims, starts = blk.sectors()
@@ -204,7 +207,7 @@ def truncate(blk, rho, m):
     U = np.concatenate(cols, axis=1)
     ren = lambda M: U.conj().T @ M @ U
     discarded = sum(float(np.sum(lam[k:])) for (lam, _), k in zip(eig, counts))
-    return DBlock(qn, ren(blk.H), [ren(c) for c in blk.cdag], blk.nsites), counts, [lam for lam, _ in eig], discarded
+    return DBlock(qn, ren(blk.H), [ren(c) for c in blk.cdag], blk.nsites), counts, [lam for lam, _ in eig], discarded, U
 
 
 class ChainDMRG:
@@ -215,6 +218,7 @@ class ChainDMRG:
         self.L, self.t, self.U, self.m = L, t, U, m
         self.left = {1: site_block(U)}
         self.right = {1: site_block(U)}
+        self.right_U = {}   # right block of r sites as U^dag of the enlarged block of r - 1 sites (its kept basis)
         self.energies = []
 
     def _step(self, l, r, Q):
@@ -231,7 +235,7 @@ class ChainDMRG:
             Lenl, Renl, sb, e, psi = self._step(l, l, Q)
             self.energies.append(("infinite", 2 * l + 2, e))
             self.left[l + 1] = truncate(Lenl, density.rho_left(sb, [(Q, psi)], [1.0]), self.m)[0]
-            self.right[l + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)[0]
+            self.right[l + 1], *_, self.right_U[l + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)
             l += 1
 
     def sweep(self):
@@ -249,7 +253,7 @@ class ChainDMRG:
             Lenl, Renl, sb, e, psi = self._step(L - 2 - r, r, Q)
             self.energies.append(("sweep left", L - 2 - r, e))
             if r + 1 <= L - 3:
-                self.right[r + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)[0]
+                self.right[r + 1], *_, self.right_U[r + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)
         for l in range(1, h - 1):
             Lenl, Renl, sb, e, psi = self._step(l, L - 2 - l, Q)
             self.energies.append(("sweep right", l, e))
@@ -265,3 +269,45 @@ class ChainDMRG:
         Lenl, Renl, sb, e, psi = self._step(h - 1, h - 1, (h, h))
         sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t)
         return Lenl, Renl, sb, HL, HR, conns, e, psi
+
+
+def dense_psi(sb, Q, psi):
+    """The sector-blocked wave function as the dense matrix Psi[alpha, beta] over both block bases."""
+    loff = np.concatenate([[0], np.cumsum(sb.ldim)])
+    roff = np.concatenate([[0], np.cumsum(sb.rdim)])
+    M = np.zeros((loff[-1], roff[-1]), dtype=complex)
+    for qi, ri, off, dl, dr in sb.pairs(Q):
+        M[loff[qi]: loff[qi] + dl, roff[ri]: roff[ri] + dr] = psi[off: off + dl * dr].reshape(dl, dr)
+    return M
+
+
+def blocks_of_dense(sb, Q, M):
+    """Inverse of dense_psi: the sector-Q vector of a dense Psi."""
+    loff = np.concatenate([[0], np.cumsum(sb.ldim)])
+    roff = np.concatenate([[0], np.cumsum(sb.rdim)])
+    out = np.zeros(sb.size(Q), dtype=complex)
+    for qi, ri, off, dl, dr in sb.pairs(Q):
+        out[off: off + dl * dr] = M[loff[qi]: loff[qi] + dl, roff[ri]: roff[ri] + dr].ravel()
+    return out
+
+
+def wft_right(Lenl, Renl, Q, psi, U, Rblk, V, Lenl_next, Renl_next):
+    """Wave-function transformation (Sec. II.B) when the centre moves one site to the right: psi on
+    (Lenl, Renl) with Renl = site + Rblk, to (Lenl_next, Renl_next) with Lenl_next = kept(Lenl) + site and
+    Rblk the kept basis of Renl_next (|b> = sum_c V[c, b] |c>).  Left: projection on the kept states,
+    Psi1 = U^dag Psi; right: each right-block state expanded in Renl_next; the moved site changes block
+    but not its place in the lattice order of the fermions, so no sign arises."""
+    sbA = superblock.Superblock(*Lenl.sectors()[:2], *Renl.sectors()[:2])
+    sbB = superblock.Superblock(*Lenl_next.sectors()[:2], *Renl_next.sectors()[:2])
+    P1 = U.conj().T @ dense_psi(sbA, Q, psi)                     # (kept, Renl)
+    m, Db = P1.shape[0], Rblk.dim
+    T = np.zeros((m, 4, Db), dtype=complex)
+    for p, kidx in enumerate(Renl.perm):                         # Renl position p <- (site s, block b)
+        s, b = divmod(kidx, Db)
+        T[:, s, b] = P1[:, p]
+    T2 = np.einsum("asb,cb->asc", T, V)                           # right block state b -> states c of Renl_next
+    out = np.zeros((Lenl_next.dim, Renl_next.dim), dtype=complex)
+    for p, kidx in enumerate(Lenl_next.perm):                    # Lenl_next position p <- (kept a, site s)
+        a, s = divmod(kidx, 4)
+        out[p, :] = T2[a, s, :]
+    return blocks_of_dense(sbB, Q, out)

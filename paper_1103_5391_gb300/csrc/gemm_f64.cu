@@ -89,10 +89,13 @@ __global__ void __launch_bounds__(128) gemm_f64_kernel(GemmArgs args, const int*
         for (int k0 = 0; k0 < seg.K; k0 += KC) {
             const int kc = min(KC, seg.K - k0);
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {             // A chunk TS x KC: threads along k
-                const int e = tid + 128 * u, r = e / KC, k = e % KC;
+            for (int u = 0; u < 2; ++u) {             // A chunk TS x KC: threads along k (along m when transposed)
+                const int e = tid + 128 * u;
+                const int r = seg.opa ? e % TS : e / KC, k = seg.opa ? e / TS : e % KC;
                 double2 v = make_double2(0.0, 0.0);
-                if (r < Mt && k < kc) v = A[(int64_t)(m0 + r) * seg.lda + k0 + k];
+                if (r < Mt && k < kc)
+                    v = seg.opa ? A[(int64_t)(k0 + k) * seg.lda + m0 + r] : A[(int64_t)(m0 + r) * seg.lda + k0 + k];
+                if (seg.opa == 2) v.y = neg(v.y);
                 if (scaled) v = make_double2(sr * v.x - si * v.y, sr * v.y + si * v.x);
                 if constexpr (kCorr) {
                     fA[0][r][k] = (float)v.x;

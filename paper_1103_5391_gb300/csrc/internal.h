@@ -60,6 +60,7 @@ struct Seg {
     int32_t lda, ldb, K;
     int8_t a_buf, b_buf, opb;
     int8_t rflags;            // bit 0: A (with the scale) real, bit 1: B real -- their imaginary products are skipped
+    int8_t opa;               // op(A): 0 A[m][k] at a[m*lda+k]; 1 at a[k*lda+m] (transposed); 2 its conjugate (FP64 kernel only)
     int32_t dscale;           // index into the launch's device real scales, -1 = none
     cplx scale;               // static complex factor (1 = none)
     int32_t dcoef = -1;       // index into the launch's device complex coefficients (connection terms), -1 = none

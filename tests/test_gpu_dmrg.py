@@ -141,7 +141,7 @@ def test_renormalization_matches_oracle(lib, chain, device_rho):
         ref = np.concatenate([w.ravel() for w in want])
         assert np.abs(got - ref).max() < 1e-12 * max(1.0, np.abs(ref).max()), op_id
     # spectrum of the renormalised H_L per sector against the oracle's own truncation
-    blk_new, counts, lam, disc = dmrg.truncate(Lenl, rho_ref, M)
+    blk_new, counts, lam, disc, _ = dmrg.truncate(Lenl, rho_ref, M)
     assert counts == kept
     hb = Lenl.blockop(Lenl.H, False)
     want = [np.linalg.eigvalsh(Us[q][:, :k].conj().T @ hb.blocks[(q, q)] @ Us[q][:, :k]) for q, k in enumerate(kept) if k]

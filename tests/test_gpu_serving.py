@@ -118,3 +118,34 @@ def test_budget_cancel_and_errors():
     finally:
         for ss, ctx, psi, phi in jobs:
             T.tdmrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_server_job_against_oracle(prec):
+    """A server job's observables after every time step against the oracle's trajectory of the same job
+    (Krylov advance with 4 targets, n_K = 8, tau = 0.05), while a second job runs beside it.  Bounds:
+    FP64 path 1e-12; tensor path (4 slices) 1e-8, the observable accuracy target."""
+    torch = torch_cuda()
+    from oracle import krylov, superblock
+    from oracle import blocks as oblocks
+    from paper_1103_5391_gb300 import problem
+    from paper_1103_5391_gb300 import tdmrg as T
+    from tests.gpu_util import oracle_ops_of_synthetic
+    steps = 5
+    jobs = [_job(T, problem, torch, 16, 128, 1, 111, prec), _job(T, problem, torch, 20, 200, 2, 112, prec)]
+    ss = jobs[0][0]
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    phi0 = superblock.apply_op(sb, None, oblocks.BlockOp(ss.cdag_exc, True), ss.Q0, ss.psi_gs, ss.Q1)
+    traj = krylov.time_steps(lambda v: superblock.apply_h(sb, HL, HR, conns, ss.Q1, v), phi0, 0.05, steps, 4, 8)
+    nL, nR = oblocks.BlockOp(ss.nL, False), oblocks.BlockOp(ss.nR, False)
+    want = np.array([[superblock.expect(sb, nL, None, ss.Q1, tg[-1]), superblock.expect(sb, None, nR, ss.Q1, tg[-1])]
+                     for tg, _, _ in traj])
+    srv = T.tdmrg_server_create(0, 0, 2)
+    try:
+        res = _run(T, srv, jobs, steps, [0.0, 0.0], problem)
+    finally:
+        T.tdmrg_server_destroy(srv)
+        for jb in jobs:
+            T.tdmrg_destroy(jb[1])
+    got = res[0][1].reshape(steps, 2)
+    assert np.abs(got - want).max() < (1e-12 if prec == 0 else 1e-8)

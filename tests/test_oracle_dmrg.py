@@ -12,7 +12,7 @@ import itertools
 import numpy as np
 import pytest
 
-from oracle import dmrg, ed, krylov, superblock
+from oracle import density, dmrg, ed, krylov, superblock
 
 
 @pytest.fixture(scope="module")
@@ -114,3 +114,34 @@ def test_kept_counts_brute_force_small():
         assert valid == [counts], (m, valid, counts)
     assert dmrg.kept_counts(evals, 2) == [2, 0, 0]        # the 0.25 tie goes to the lowest sector first
     assert dmrg.kept_counts(evals, 3) == [2, 1, 0]
+
+
+def _position(d, l):
+    """Superblock pieces at left-block size l of a finished run: (Lenl, Renl, r) with r = L - 2 - l."""
+    r = d.L - 2 - l
+    return dmrg.enlarge(d.left[l], "L", d.t, d.U), dmrg.enlarge(d.right[r], "R", d.t, d.U), r
+
+
+def test_wft_exact_without_truncation():
+    """L=8 with m=256: no state is dropped, so the wave-function transformation is a change of basis --
+    the ground state at the centre, moved one site to the right, is the ground state of the next
+    superblock (H psi' = E psi' to 1e-10) with the same norm and central densities."""
+    d = dmrg.ChainDMRG(8, 1.0, 4.0, 256)
+    Lenl, Renl, sb, HL, HR, conns, e, psi = d.run(sweeps=1)
+    Q = (4, 4)
+    l = 3
+    Lc, Rc, r = _position(d, l)
+    assert Lc.dim == Lenl.dim and Rc.dim == Renl.dim
+    rho = density.rho_left(sb, [(Q, psi)], [1.0])
+    Lb, counts, lam, disc, U = dmrg.truncate(Lenl, rho, 256)
+    Ln = dmrg.enlarge(Lb, "L", 1.0, 4.0)
+    Rn = dmrg.enlarge(d.right[r - 1], "R", 1.0, 4.0)
+    psi2 = dmrg.wft_right(Lenl, Renl, Q, psi, U, d.right[r], d.right_U[r], Ln, Rn)
+    sb2, HL2, HR2, conns2 = dmrg.superblock_of(Ln, Rn, 1.0)
+    assert abs(np.linalg.norm(psi2) - 1.0) < 1e-12
+    res = superblock.apply_h(sb2, HL2, HR2, conns2, Q, psi2) - e * psi2
+    assert np.abs(res).max() < 1e-10
+    # the density of site 4 (right edge before, left edge after the move)
+    n_before = Renl.blockop(Renl.cdag[0] @ Renl.cdag[0].conj().T, False)
+    n_after = Ln.blockop(Ln.cdag[0] @ Ln.cdag[0].conj().T, False)
+    assert abs(superblock.expect(sb, None, n_before, Q, psi) - superblock.expect(sb2, n_after, None, Q, psi2)) < 1e-12
