@@ -216,6 +216,25 @@ int tdmrg_truncate(tdmrg_ctx* ctx, const double* evals_d, int m, int32_t* kept_d
 int tdmrg_renormalize_op(tdmrg_ctx* ctx, int side, int op_id, const tdmrg_c64* U_d, const int32_t* kept,
                          tdmrg_c64* out_d, int* nblk_out);
 
+/* Wave-function transformation of a target (Sec. II.B: transporting the targets from one superblock to
+ * the next during a sweep) when the centre moves one site to the right.  `from` holds the superblock
+ * (L_enl, R_enl) with R_enl = site + R_b; `to` holds (L_enl', R_enl') with L_enl' = K + site, K the kept
+ * states of L_enl, and R_b the kept basis of R_enl'.  Block bases are Kronecker products sorted stably by
+ * quantum number: inside a sector of R_enl the site states (0,0), (0,1), (1,0), (1,1) come in that order,
+ * each followed by the states of R_b in its order; a sector of L_enl' runs over the states of K in order.
+ *   psi_d: the target in `from`'s sector Q = (n_up, n_dn); out_d: the result in `to`'s sector Q (cleared
+ *          first); U_d: per left sector of `from`, the dim x dim matrix whose first kept[s] columns are the
+ *          kept states (the layout of tdmrg_rho_eig); kept: host, one count per left sector of `from`;
+ *   rb_nsec, rb_qn, rb_dim: the sector table of R_b (host); V_d: per sector q of R_b, the
+ *          dim_R_enl'(q) x dim_R_b(q) row-major matrix whose columns are R_b's states in the basis of R_enl',
+ *          concatenated in R_b's sector order.
+ * No fermion sign arises (the moved site keeps its place in the lattice order).  Two grouped FP64
+ * launches on `from`'s stream; allocates scratch and synchronises.  Errors: EINVAL, ESTATE, ESECTOR
+ * (the block tables are not site + R_b and K + site), ENOMEM, ECUDA. */
+int tdmrg_wft_right(tdmrg_ctx* from, int n_up, int n_dn, const tdmrg_c64* psi_d, const tdmrg_c64* U_d,
+                    const int32_t* kept, int rb_nsec, const int32_t* rb_qn, const int32_t* rb_dim,
+                    const tdmrg_c64* V_d, tdmrg_ctx* to, tdmrg_c64* out_d);
+
 /* out_d[0] = <psi| opL opR |psi> / <psi|psi> for a sector-preserving product (Eq. generalcorrelation
  * with a = 1 local operator per block, Eq. nholondoublon; -1 = identity on that block).  out_d is
  * one device tdmrg_c64.  Errors as apply_op. */

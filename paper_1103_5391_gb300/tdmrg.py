@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -83,6 +83,7 @@ def load(path=LIB_PATH):
         "tdmrg_rho_eig": (I, [P, P, P, P]),
         "tdmrg_set_real_basis": (I, [P, I]),
         "tdmrg_truncate": (I, [P, P, I, P, P]),
+        "tdmrg_wft_right": (I, [P, I, I, P, P, PI32, I, PI32, PI32, P, P, P]),
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
@@ -279,6 +280,15 @@ def tdmrg_renormalize_op(ctx, side, op_id, U, kept, out):
     nb = ctypes.c_int()
     _check(ctx, load().tdmrg_renormalize_op(ctx, side, op_id, _ptr(U), kp, _ptr(out), ctypes.byref(nb)))
     return nb.value
+
+
+def tdmrg_wft_right(ctx_from, Q, psi, U, kept, rb_qn, rb_dim, V, ctx_to, out):
+    """Transport psi (ctx_from, sector Q) to ctx_to's superblock when the centre moves one site right."""
+    k, kp = _i32(kept)
+    q, qp = _i32(np.asarray(rb_qn).reshape(-1))
+    d, dp = _i32(rb_dim)
+    return _check(ctx_from, load().tdmrg_wft_right(ctx_from, Q[0], Q[1], _ptr(psi), _ptr(U), kp, len(d), qp, dp, _ptr(V),
+                                                   ctx_to, _ptr(out)))
 
 
 def tdmrg_expect(ctx, opL, opR, Q, psi, out):

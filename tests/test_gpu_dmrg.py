@@ -149,3 +149,52 @@ def test_renormalization_matches_oracle(lib, chain, device_rho):
     mine = [np.linalg.eigvalsh(blk_new.H[s0: s0 + d, s0: s0 + d]) for s0, d in zip(new_starts, new_dims)]
     for a, b in zip(want, mine):
         assert np.abs(a - b).max() < 1e-10
+
+
+@pytest.fixture(scope="module")
+def run_object():
+    d = dmrg.ChainDMRG(L, T_HOP, U, M)
+    return d, d.run(sweeps=1)
+
+
+def _blocks_of_V(V, Rn, Rb):
+    """Per sector of Rb, the rows of Rn's sector and Rb's columns of V (V is block diagonal by sector)."""
+    rn_secs, rn_dims, rn_starts = Rn.sectors()
+    rb_secs, rb_dims, rb_starts = Rb.sectors()
+    out = []
+    for q, db, sb0 in zip(rb_secs, rb_dims, rb_starts):
+        k = rn_secs.index(q)
+        out.append(V[rn_starts[k]: rn_starts[k] + rn_dims[k], sb0: sb0 + db].ravel())
+    return np.concatenate(out)
+
+
+def test_wft_right_matches_oracle(lib, run_object):
+    """The ground state at the centre of the L=10 m=32 chain moved one site to the right (truncation to
+    m = 32 on the left, the right block expanded in the next right enlarged block) against the oracle's
+    wave-function transformation: 1e-13; its squared norm is 1 minus the discarded weight."""
+    d, (Lenl, Renl, sb, HL, HR, conns, e, psi) = run_object
+    Q = (L // 2, L // 2)
+    r = L // 2 - 1
+    rho = density.rho_left(sb, [(Q, psi)], [1.0])
+    Lb, counts, lam, disc, Uf = dmrg.truncate(Lenl, rho, M)
+    Ln = dmrg.enlarge(Lb, "L", T_HOP, U)
+    Rn = dmrg.enlarge(d.right[r - 1], "R", T_HOP, U)
+    want = dmrg.wft_right(Lenl, Renl, Q, psi, Uf, d.right[r], d.right_U[r], Ln, Rn)
+    # the same U in the device layout: per left sector its eigenvector matrix (kept columns first)
+    Us = np.concatenate([Uq.ravel() for _, Uq in density.rho_eig(rho)])
+    ca, cb = new_ctx(), new_ctx()
+    try:
+        DmrgLoader(ca, Lenl, Renl, T_HOP)
+        DmrgLoader(cb, Ln, Rn, T_HOP)
+        n2 = lib.tdmrg_sector_size(cb, Q)
+        assert n2 == len(want)
+        out = dev(np.full(n2, np.nan + 0j))
+        rb_secs, rb_dims, _ = d.right[r].sectors()
+        lib.tdmrg_wft_right(ca, Q, dev(psi), dev(Us), counts, rb_secs, rb_dims,
+                            dev(_blocks_of_V(d.right_U[r], Rn, d.right[r])), cb, out)
+        assert np.abs(host(out) - want).max() < 1e-13
+        # the projection keeps exactly the kept weight and the right expansion is an isometry
+        assert abs(np.linalg.norm(host(out)) ** 2 - (1.0 - disc)) < 1e-12
+    finally:
+        lib.tdmrg_destroy(ca)
+        lib.tdmrg_destroy(cb)
