@@ -157,6 +157,15 @@ int tdmrg_apply_op(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const t
 int tdmrg_evolve(tdmrg_ctx* ctx, int n_up, int n_dn, const tdmrg_c64* phi_d, int n_v, const double* t_x,
                  int nk, tdmrg_c64* const* targets_d);
 
+/* Ground state in sector Q (the ground-state targeting of Sec. II.B, needed at every DMRG step):
+ * `restarts` times, nk Lanczos steps started at psi_d (full re-orthogonalisation, FP64), the lowest
+ * eigenvector of the tridiagonal (bisection on its Sturm count, then inverse iteration, FP64) combined
+ * in place into psi_d, normalised.  psi_d (device, sector Q) is the start vector on entry and the ground
+ * state on return; *energy (host, nullable) receives the lowest Ritz value of the last restart.  The
+ * call synchronises the stream once at the end.  Errors: EINVAL (nk outside 2..nk_max, restarts < 1),
+ * ESTATE, ENOMEM, ECUDA, ETIMEOUT. */
+int tdmrg_ground_state(tdmrg_ctx* ctx, int n_up, int n_dn, tdmrg_c64* psi_d, int nk, int restarts, double* energy);
+
 /* Results of the last tdmrg_evolve: Krylov dimension used, a-posteriori error estimate
  * ||phi|| beta_n |[e^{-i T t_{n_v-1}}]_{n-1,0}| (Saad), and optionally alpha[0..n-1], beta[0..n-1]
  * (beta[j] couples v_j and v_{j+1}; beta[n-1] is the residual).  Synchronises the stream. */
@@ -215,6 +224,48 @@ int tdmrg_truncate(tdmrg_ctx* ctx, const double* evals_d, int m, int32_t* kept_d
  * Errors: EINVAL (unknown op id, kept count outside 0..dim), ESTATE, ENOMEM, ECUDA. */
 int tdmrg_renormalize_op(tdmrg_ctx* ctx, int side, int op_id, const tdmrg_c64* U_d, const int32_t* kept,
                          tdmrg_c64* out_d, int* nblk_out);
+
+/* A block operator given as sector blocks: nblk blocks, blk_qn[4*b..4*b+3] = (out n_up, out n_dn, in n_up,
+ * in n_dn), data_d (device) the blocks row-major, concatenated in that order (the layout of tdmrg_set_op). */
+typedef struct {
+    int nblk;
+    const int32_t* blk_qn;
+    const tdmrg_c64* data_d;
+} tdmrg_blocks;
+
+/* Sector table of the block K enlarged by one Hubbard site (Sec. I: blocks grow by one site per step;
+ * Sec. II.B: the superblock is (block + site) + (site + block)).  side 0: K + site (K's sites first),
+ * side 1: site + K.  K: nsec sectors qn[2s], qn[2s+1] ascending, dims dim[s] >= 1 (host).  Writes (host,
+ * each nullable) the number of enlarged sectors, their quantum numbers and dimensions (capacity cap
+ * sectors), the number of blocks of the new edge operators c^dag'_up, c^dag'_dn, and the complex entries of
+ * the three outputs of tdmrg_enlarge (H', c^dag'_up, c^dag'_dn).  No device work.
+ * Errors: EINVAL (side, capacity), ESECTOR (table not ascending, dim < 1). */
+int tdmrg_enlarge_size(int side, int nsec, const int32_t* qn, const int32_t* dim, int cap, int* nsec_out,
+                       int32_t* qn_out, int32_t* dim_out, int32_t* nblk_cdag, int64_t* entries);
+
+/* Operators of the enlarged block (Hubbard site: U n_up n_dn, bond -t to K's edge site):
+ *   side 0 (K + site): H' = H_K x 1 + 1 x U n_up n_dn - t sum_s [(c^dag_K,s P_K) x c_s + (P_K c_K,s) x c^dag_s],
+ *                      c^dag'_s = P_K x c^dag_s;
+ *   side 1 (site + K): H' = U n_up n_dn x 1 + 1 x H_K - t sum_s [(c^dag_s P) x c_K,s + (P c_s) x c^dag_K,s],
+ *                      c^dag'_s = c^dag_s x 1,
+ * with P_K, P the parities of K and of the site, the site states |0>, |dn>, |up>, |up dn> created as
+ * c^dag_up c^dag_dn |0>, and the enlarged basis the Kronecker basis sorted stably by quantum number (the
+ * table of tdmrg_enlarge_size).  H (H_K, sector-diagonal blocks) and cdag[2] (K's edge c^dag_up, c^dag_dn)
+ * are device blocks of K.  H_out (device) receives every enlarged sector's dim x dim block in table order;
+ * cdag_out[s] (device) the blocks of c^dag'_s, one per enlarged sector Q that it maps out of, in table
+ * order of Q, each dim(Q + e_s) x dim(Q); cdag_qn_out[s] (host, 4 ints per block, nullable) their quantum
+ * numbers in tdmrg_set_op's layout.  One placement launch into the zeroed outputs; synchronises the stream.
+ * Errors: EINVAL, ESECTOR (a block of H off the diagonal, a c^dag block that does not raise n_s by one),
+ * ENOMEM, ECUDA. */
+int tdmrg_enlarge(tdmrg_ctx* ctx, int side, int nsec, const int32_t* qn, const int32_t* dim, const tdmrg_blocks* H,
+                  const tdmrg_blocks* cdag, double t, double U, tdmrg_c64* H_out, tdmrg_c64* const* cdag_out,
+                  int32_t* const* cdag_qn_out);
+
+/* Operator op_id of one side defined as the adjoint of operator src_id of the same side (block (q_in, q_out)
+ * = the conjugate transpose of block (q_out, q_in); same fermion parity): e.g. c from c^dag for the
+ * Hamiltonian's boundary terms.  Synchronises the stream.  Errors: EINVAL (unknown src_id, op_id < 0 or equal
+ * to src_id), ENOMEM, ECUDA. */
+int tdmrg_set_op_adjoint(tdmrg_ctx* ctx, int side, int op_id, int src_id);
 
 /* Wave-function transformation of a target (Sec. II.B: transporting the targets from one superblock to
  * the next during a sweep) when the centre moves one site to the right.  `from` holds the superblock

@@ -53,19 +53,6 @@ void dev_free(tdmrg_ctx* c, void* p, size_t bytes) {
 
 namespace {
 
-struct DeviceGuard {   // makes the context's device current for the duration of a call
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 void drop_plans(tdmrg_ctx* c) {
     for (auto& kv : c->plans) {
         release(c, kv.second->stage1);
@@ -314,8 +301,10 @@ int tdmrg_set_op(tdmrg_ctx* c, int side, int id, int odd, int nblk, const int32_
         const tdmrg_c64* h = data;
         if (on_device && total) {
             hcopy.resize(total);
-            int rc = cuda_check(c, cudaMemcpy(hcopy.data(), data, total * sizeof(tdmrg_c64), cudaMemcpyDeviceToHost),
-                                "set_op realness check");
+            // on the context's stream: device data the caller produced there is complete before it is read
+            int rc = cuda_check(c, cudaMemcpyAsync(hcopy.data(), data, total * sizeof(tdmrg_c64), cudaMemcpyDeviceToHost,
+                                                   c->stream), "set_op realness check");
+            if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "set_op realness check");
             if (rc) return rc;
             h = hcopy.data();
         }
@@ -423,6 +412,15 @@ int tdmrg_evolve(tdmrg_ctx* c, int a, int b, const tdmrg_c64* phi, int n_v, cons
     }
     DeviceGuard g(c->opts.device);
     return evolve(c, a, b, (const cplx*)phi, n_v, t_x, nk, (cplx* const*)targets);
+}
+
+int tdmrg_ground_state(tdmrg_ctx* c, int a, int b, tdmrg_c64* psi, int nk, int restarts, double* energy) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "ground_state: Hamiltonian not set");
+    if (!psi || nk < 2 || nk > c->opts.nk_max || restarts < 1)
+        return fail(c, TDMRG_EINVAL, "ground_state: bad argument (nk in 2..nk_max, restarts >= 1)");
+    DeviceGuard g(c->opts.device);
+    return ground_state(c, a, b, (cplx*)psi, nk, restarts, energy);
 }
 
 int tdmrg_evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta) {

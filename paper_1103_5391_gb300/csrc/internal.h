@@ -324,6 +324,19 @@ struct tdmrg_ctx {
 namespace tdmrg {
 
 // error helpers (api.cu)
+struct DeviceGuard {   // makes the context's device current for the duration of a call
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 int fail(tdmrg_ctx* c, int code, const std::string& msg);
 int cuda_check(tdmrg_ctx* c, cudaError_t e, const char* what);
 int dev_alloc(tdmrg_ctx* c, void** p, size_t bytes, const char* what);
@@ -359,6 +372,7 @@ int oz_status(tdmrg_ctx* c, const Plan& p, int* status);
 int evolve(tdmrg_ctx* c, int n_up, int n_dn, const cplx* phi, int n_v, const double* t_x, int nk,
            cplx* const* targets);
 int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta);
+int ground_state(tdmrg_ctx* c, int n_up, int n_dn, cplx* psi, int nk, int restarts, double* energy);
 cudaError_t launch_norm2(const cplx* x, int64_t n, double2* partials, int nblk, cudaStream_t s);
 cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* partials, int nblk,
                              cplx* out, int normalise, cudaStream_t s);

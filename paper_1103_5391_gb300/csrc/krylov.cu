@@ -20,7 +20,7 @@ namespace {
 
 constexpr int NB = kRedBlocks;   // reduction blocks
 constexpr int NT = 256;          // threads per reduction block
-enum { T_ALPHA = 0, T_BETA = 32, T_BETA0 = 64, T_RESID = 65, T_ERR = 66 };
+enum { T_ALPHA = 0, T_BETA = 32, T_BETA0 = 64, T_RESID = 65, T_ERR = 66, T_EMIN = 67 };
 
 __device__ __forceinline__ void chunk_of(int64_t n, int64_t& lo, int64_t& hi) {
     const int64_t ch = (n + NB - 1) / NB;
@@ -396,6 +396,67 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, co
     }
 }
 
+// Lowest eigenpair of the Lanczos tridiagonal T (ground-state targeting, Sec. II.B): one thread, FP64.
+// The eigenvalue by bisection on the Sturm count (number of eigenvalues below x from the signs of the
+// LDL^T pivots of T - x), then the eigenvector by inverse iteration (three tridiagonal solves with the
+// shifted matrix, pivots kept away from zero); coef[0][k] = x_k (normalised, real), tri[T_EMIN] = lambda.
+__global__ void __launch_bounds__(32) k_tridiag_min(double* __restrict__ tri, const int* __restrict__ flags,
+                                                     cplx* __restrict__ coef) {
+    pdl_enter();
+    if (threadIdx.x != 0) return;
+    const int n = flags[0];
+    for (int k = 0; k < 32; ++k) coef[k] = make_double2(0.0, 0.0);
+    if (n <= 0) { tri[T_EMIN] = 0.0; return; }
+    const double* al = tri + T_ALPHA;
+    const double* be = tri + T_BETA;   // be[k] couples k and k + 1
+    double lo = 1e300, hi = -1e300;
+    for (int k = 0; k < n; ++k) {
+        const double r = (k > 0 ? fabs(be[k - 1]) : 0.0) + (k + 1 < n ? fabs(be[k]) : 0.0);
+        lo = fmin(lo, al[k] - r);
+        hi = fmax(hi, al[k] + r);
+    }
+    const double tiny = 1e-300;
+    for (int it = 0; it < 200 && hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300; ++it) {
+        const double x = 0.5 * (lo + hi);
+        int cnt = 0;
+        double q = al[0] - x;
+        cnt += q < 0.0;
+        for (int k = 1; k < n; ++k) {
+            if (q == 0.0) q = tiny;
+            q = al[k] - x - be[k - 1] * be[k - 1] / q;
+            cnt += q < 0.0;
+        }
+        if (cnt >= 1) hi = x;
+        else lo = x;
+    }
+    const double lam = 0.5 * (lo + hi);
+    // a pivot that vanishes (lam an exact eigenvalue, e.g. n = 1 when the start vector is already an
+    // eigenvector) is replaced by eps ||T||; each solve is rescaled by its largest entry before the norm
+    const double pmin = 2.2e-16 * fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
+    double v[32], dg[32], up[32];
+    for (int k = 0; k < n; ++k) v[k] = 1.0;
+    for (int r = 0; r < 3; ++r) {   // (T - lam) y = v by elimination down the band, then back substitution
+        for (int k = 0; k < n; ++k) { dg[k] = al[k] - lam; up[k] = k + 1 < n ? be[k] : 0.0; }
+        for (int k = 1; k < n; ++k) {
+            if (fabs(dg[k - 1]) < pmin) dg[k - 1] = dg[k - 1] < 0.0 ? -pmin : pmin;
+            const double m = be[k - 1] / dg[k - 1];
+            dg[k] -= m * up[k - 1];
+            v[k] -= m * v[k - 1];
+        }
+        if (fabs(dg[n - 1]) < pmin) dg[n - 1] = dg[n - 1] < 0.0 ? -pmin : pmin;
+        v[n - 1] /= dg[n - 1];
+        for (int k = n - 2; k >= 0; --k) v[k] = (v[k] - up[k] * v[k + 1]) / dg[k];
+        double mx = 0.0;
+        for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(v[k]));
+        double nn = 0.0;
+        for (int k = 0; k < n; ++k) { v[k] /= mx; nn += v[k] * v[k]; }
+        const double inv = 1.0 / sqrt(nn);
+        for (int k = 0; k < n; ++k) v[k] *= inv;
+    }
+    for (int k = 0; k < n; ++k) coef[k] = make_double2(v[k], 0.0);
+    tri[T_EMIN] = lam;
+}
+
 struct TargetPtrs { cplx* p[16]; };
 
 // targets[x][i] = sum_k coef[x][k] v_k[i] for x in [x0, x0 + NX): one pass over V.  NX is exact (no
@@ -530,18 +591,19 @@ cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* p
     return cudaGetLastError();
 }
 
-int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t_x, int nk, cplx* const* targets) {
+// The Lanczos recursion of n_K steps started at phi (Sec. II.A): V, the tridiagonal and the flags in the
+// Krylov workspace of (Q, nk).
+int lanczos_build(tdmrg_ctx* c, int a, int b, const cplx* phi, int nk, KrylovWork** out) {
     int64_t n = sector_size(c, a, b);
-    if (n == 0) return fail(c, TDMRG_ESECTOR, "evolve: empty sector");
+    if (n == 0) return fail(c, TDMRG_ESECTOR, "Lanczos: empty sector");
     Plan* p = nullptr;
     int rc = get_ham_plan(c, a, b, &p);
     if (rc) return rc;
     KrylovWork* k = nullptr;
     rc = ensure_work(c, a, b, nk, n, &k);
     if (rc) return rc;
+    *out = k;
     cudaStream_t s = c->stream;
-    Times tt{};
-    for (int x = 0; x < n_v; ++x) tt.t[x] = t_x[x];
     launch_pdl(k_norm2, NB, NT, 0, s, phi, n, k->partA);
     launch_pdl(k_init_v0, NB, NT, 0, s, phi, n, k->partA, k->V, k->tri, k->flags, nk);
     c->launches += 2;
@@ -566,6 +628,17 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
         if (le != cudaSuccess) return cuda_check(c, le, "Lanczos orthogonalisation launch");
         c->launches += 1;
     }
+    return TDMRG_OK;
+}
+
+int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t_x, int nk, cplx* const* targets) {
+    KrylovWork* k = nullptr;
+    int rc = lanczos_build(c, a, b, phi, nk, &k);
+    if (rc) return rc;
+    const int64_t n = k->n;
+    cudaStream_t s = c->stream;
+    Times tt{};
+    for (int x = 0; x < n_v; ++x) tt.t[x] = t_x[x];
     launch_pdl(k_tridiag_exp, 1, 32, 0, s, k->tri, k->flags, tt, n_v, k->coef);
     TargetPtrs tg{};
     for (int x = 0; x < n_v; ++x) tg.p[x] = targets[x];
@@ -574,6 +647,31 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
     c->launches += 1 + (n_v + 7) / 8;
     c->last_krylov = k;
     return cuda_check(c, cudaGetLastError(), "evolve launch");
+}
+
+// Ground state in sector Q (ground-state targeting, Sec. II.B): `restarts` times, Lanczos with nk steps from
+// psi, the lowest eigenvector of T combined in place into psi.
+int ground_state(tdmrg_ctx* c, int a, int b, cplx* psi, int nk, int restarts, double* energy) {
+    KrylovWork* k = nullptr;
+    for (int r = 0; r < restarts; ++r) {
+        int rc = lanczos_build(c, a, b, psi, nk, &k);
+        if (rc) return rc;
+        launch_pdl(k_tridiag_min, 1, 32, 0, c->stream, k->tri, k->flags, k->coef);
+        TargetPtrs tg{};
+        tg.p[0] = psi;
+        const int grid = (int)std::min<int64_t>((k->n + 255) / 256, 4L * c->num_sms);
+        launch_combine(k->V, k->n, k->flags, k->coef, 1, tg, grid, c->stream);
+        c->launches += 2;
+        rc = cuda_check(c, cudaGetLastError(), "ground-state launch");
+        if (rc) return rc;
+    }
+    c->last_krylov = k;
+    double tri[128];
+    int rc = cuda_check(c, cudaMemcpyAsync(tri, k->tri, sizeof(tri), cudaMemcpyDeviceToHost, c->stream), "ground state");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "ground state");
+    if (!rc) rc = check_device_status(c);
+    if (!rc && energy) *energy = tri[T_EMIN];
+    return rc;
 }
 
 int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta) {

@@ -19,8 +19,8 @@ TDMRG_FP64, TDMRG_OZAKI_BF16 = 0, 1
 EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
-    "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
+    "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_tst_weights",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -77,6 +77,7 @@ def load(path=LIB_PATH):
         "tdmrg_apply_op": (I, [P, I, I, I, I, P, I, I, P]),
         "tdmrg_evolve": (I, [P, I, I, P, I, PD, I, ctypes.POINTER(P)]),
         "tdmrg_evolve_info": (I, [P, ctypes.POINTER(I), PD, PD, PD]),
+        "tdmrg_ground_state": (I, [P, I, I, P, I, I, PD]),
         "tdmrg_tst_weights": (I, [I, PD, PD]),
         "tdmrg_rho_size": (I, [P, PI64, PI64]),
         "tdmrg_density_matrix": (I, [P, I, PI32, ctypes.POINTER(P), PD, P]),
@@ -85,6 +86,9 @@ def load(path=LIB_PATH):
         "tdmrg_truncate": (I, [P, P, I, P, P]),
         "tdmrg_wft_right": (I, [P, I, I, P, P, PI32, I, PI32, PI32, P, P, P]),
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
+        "tdmrg_enlarge_size": (I, [I, I, PI32, PI32, I, ctypes.POINTER(I), PI32, PI32, PI32, ctypes.POINTER(ctypes.c_int64)]),
+        "tdmrg_enlarge": (I, [P, I, I, PI32, PI32, P, P, ctypes.c_double, ctypes.c_double, P, P, P]),
+        "tdmrg_set_op_adjoint": (I, [P, I, I, I]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
         "tdmrg_correlation": (I, [P, I, PI32, I, PI32, I, I, P, I, I, P, P]),
@@ -191,6 +195,13 @@ def tdmrg_set_op(ctx, side, op_id, odd, blocks):
                                            data.ctypes.data_as(ctypes.c_void_p), 0))
 
 
+def tdmrg_set_op_device(ctx, side, op_id, odd, blk_qn, data_d):
+    """Operator from device data: blk_qn a list of (out_up, out_dn, in_up, in_dn), data_d the blocks
+    row-major, concatenated in that order (e.g. the outputs of tdmrg_enlarge or tdmrg_renormalize_op)."""
+    q, qp = _i32(np.asarray(blk_qn, dtype=np.int32).reshape(-1) if len(blk_qn) else [0])
+    return _check(ctx, load().tdmrg_set_op(ctx, side, op_id, int(odd), len(blk_qn), qp, _ptr(data_d), 1))
+
+
 def tdmrg_set_hamiltonian(ctx, opHL, opHR, conns):
     """conns: list of (opL, opR, complex coeff)."""
     n = len(conns)
@@ -224,6 +235,13 @@ def tdmrg_evolve(ctx, Q, phi, times, nk, targets):
     arr = (ctypes.c_void_p * len(targets))(*[_ptr(x) for x in targets])
     return _check(ctx, load().tdmrg_evolve(ctx, Q[0], Q[1], _ptr(phi), len(t),
                                            t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nk, arr))
+
+
+def tdmrg_ground_state(ctx, Q, psi, nk=16, restarts=20):
+    """psi (device, sector Q): start vector in, ground state out; returns the energy."""
+    e = ctypes.c_double()
+    _check(ctx, load().tdmrg_ground_state(ctx, Q[0], Q[1], _ptr(psi), nk, restarts, ctypes.byref(e)))
+    return e.value
 
 
 def tdmrg_evolve_info(ctx, nk_max=32):
@@ -289,6 +307,64 @@ def tdmrg_wft_right(ctx_from, Q, psi, U, kept, rb_qn, rb_dim, V, ctx_to, out):
     d, dp = _i32(rb_dim)
     return _check(ctx_from, load().tdmrg_wft_right(ctx_from, Q[0], Q[1], _ptr(psi), _ptr(U), kp, len(d), qp, dp, _ptr(V),
                                                    ctx_to, _ptr(out)))
+
+
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+
+
+class _Blocks(ctypes.Structure):
+    _fields_ = [("nblk", ctypes.c_int), ("blk_qn", ctypes.c_void_p), ("data_d", ctypes.c_void_p)]
+
+
+def _blocks(qns, data):
+    """tdmrg_blocks of a list of (out n_up, out n_dn, in n_up, in n_dn) and the device data."""
+    q = np.ascontiguousarray(np.asarray(qns, dtype=np.int32).reshape(-1))
+    b = _Blocks(len(q) // 4, q.ctypes.data_as(ctypes.c_void_p) if len(q) else None, _ptr(data))
+    return b, q
+
+
+def tdmrg_enlarge_size(side, qn, dim):
+    """(sector quantum numbers, dims, blocks of c^dag'_up / c^dag'_dn, entries of H', c^dag'_up, c^dag'_dn)
+    of the block (qn, dim) enlarged by one site on `side`."""
+    q, qp = _i32(np.asarray(qn).reshape(-1))
+    d, dp = _i32(dim)
+    cap = 4 * len(d) + 4
+    n = ctypes.c_int()
+    qo = np.zeros(2 * cap, np.int32)
+    do = np.zeros(cap, np.int32)
+    nb = np.zeros(2, np.int32)
+    ent = np.zeros(3, np.int64)
+    _check(None, load().tdmrg_enlarge_size(side, len(d), qp, dp, cap, ctypes.byref(n),
+                                           qo.ctypes.data_as(_PI32), do.ctypes.data_as(_PI32), nb.ctypes.data_as(_PI32),
+                                           ent.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    k = n.value
+    return [tuple(x) for x in qo[:2 * k].reshape(k, 2)], list(do[:k]), list(nb), list(ent)
+
+
+def tdmrg_enlarge(ctx, side, qn, dim, H, cdag, t, U, H_out, cdag_out):
+    """H = (block quantum numbers, device data) of H_K; cdag = [(qns, data) for up, down] of K's edge
+    c^dag; H_out, cdag_out[2] device outputs sized by tdmrg_enlarge_size.  Returns the block quantum
+    numbers of c^dag'_up and c^dag'_dn."""
+    q, qp = _i32(np.asarray(qn).reshape(-1))
+    d, dp = _i32(dim)
+    _, _, nb, _ = tdmrg_enlarge_size(side, qn, dim)
+    hb, hq = _blocks(*H)
+    cb = (_Blocks * 2)()
+    keep = []
+    for s in range(2):
+        b, bq = _blocks(*cdag[s])
+        cb[s] = b
+        keep.append(bq)
+    outs = (ctypes.c_void_p * 2)(_ptr(cdag_out[0]), _ptr(cdag_out[1]))
+    qouts = [np.zeros(4 * max(int(nb[s]), 1), np.int32) for s in range(2)]
+    qptr = (ctypes.c_void_p * 2)(*[x.ctypes.data_as(ctypes.c_void_p) for x in qouts])
+    _check(ctx, load().tdmrg_enlarge(ctx, side, len(d), qp, dp, ctypes.byref(hb), cb, float(t), float(U), _ptr(H_out),
+                                     outs, qptr))
+    return [[tuple(x) for x in qouts[s][:4 * int(nb[s])].reshape(-1, 4)] for s in range(2)]
+
+
+def tdmrg_set_op_adjoint(ctx, side, op_id, src_id):
+    return _check(ctx, load().tdmrg_set_op_adjoint(ctx, side, op_id, src_id))
 
 
 def tdmrg_expect(ctx, opL, opR, Q, psi, out):
