@@ -196,6 +196,14 @@ int tdmrg_density_matrix(tdmrg_ctx* ctx, int ntargets, const int32_t* Q, const t
  * products, half the work of a complex product.  Errors: EINVAL (null context). */
 int tdmrg_set_real_basis(tdmrg_ctx* ctx, int on);
 
+/* The same for either block (side 0: rho_L as above; side 1: the right block's matrix, needed when a
+ * sweep moves left, rho_R(r) = sum_l w[l] sum_{q: Q_l - q = r} Psi_l(q)^T conj(Psi_l(q)) / <psi_l|psi_l>,
+ * i.e. rho_R[b, b'] = sum_a Psi[a, b] conj(Psi[a, b']), packed per right sector).  tdmrg_rho_size_side
+ * gives its sizes.  Errors as above, EINVAL for a side other than 0 or 1. */
+int tdmrg_density_matrix_side(tdmrg_ctx* ctx, int side, int ntargets, const int32_t* Q,
+                              const tdmrg_c64* const* psi_d, const double* w, tdmrg_c64* rho_d);
+int tdmrg_rho_size_side(tdmrg_ctx* ctx, int side, int64_t* rho_entries, int64_t* n_evals);
+
 /* Eigendecomposition of a packed rho_L (as written by tdmrg_density_matrix) to FP64 accuracy per sector
  * (dL <= 512): FP32 Jacobi seed, FP64 iterative refinement (Ogita-Aishima) with re-seeding of coupled
  * clusters.
@@ -203,6 +211,9 @@ int tdmrg_set_real_basis(tdmrg_ctx* ctx, int on);
  * rho) gets U with rho(q) = U diag(evals) U^dag, column k of U the k-th eigenvector.  This feeds the
  * truncation of Sec. II.B.  Errors: EINVAL, ESTATE, ECUDA. */
 int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg_c64* evecs_d);
+
+/* tdmrg_rho_eig for the matrix of either block (packed over that side's sectors). */
+int tdmrg_rho_eig_side(tdmrg_ctx* ctx, int side, const tdmrg_c64* rho_d, double* evals_d, tdmrg_c64* evecs_d);
 
 /* Truncation of the left block to at most m states (Sec. I: a block keeps the m most probable states of
  * its reduced density matrix).  evals_d: rho_L's eigenvalues in the packed layout of tdmrg_rho_eig (per
@@ -213,6 +224,9 @@ int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg
  * nullable) the sum of the dropped eigenvalues (the truncation error).  Synchronises the stream once to
  * upload the sector tables.  Errors: EINVAL (m < 1, more than 1024 sectors), ESTATE, ECUDA. */
 int tdmrg_truncate(tdmrg_ctx* ctx, const double* evals_d, int m, int32_t* kept_d, double* discarded_d);
+
+/* tdmrg_truncate for either block (evals_d and kept_d over that side's sectors). */
+int tdmrg_truncate_side(tdmrg_ctx* ctx, int side, const double* evals_d, int m, int32_t* kept_d, double* discarded_d);
 
 /* Operator of one side renormalised into the kept basis (Sec. I): O' = U^dag O U sector block by sector
  * block, O'[q_out <- q_in] = U(q_out)[:, :k(q_out)]^dag O[q_out <- q_in] U(q_in)[:, :k(q_in)].
@@ -254,12 +268,14 @@ int tdmrg_enlarge_size(int side, int nsec, const int32_t* qn, const int32_t* dim
  * are device blocks of K.  H_out (device) receives every enlarged sector's dim x dim block in table order;
  * cdag_out[s] (device) the blocks of c^dag'_s, one per enlarged sector Q that it maps out of, in table
  * order of Q, each dim(Q + e_s) x dim(Q); cdag_qn_out[s] (host, 4 ints per block, nullable) their quantum
- * numbers in tdmrg_set_op's layout.  One placement launch into the zeroed outputs; synchronises the stream.
+ * numbers in tdmrg_set_op's layout; n_out[s] (device, nullable, each nullable) the density n_s of the new
+ * site (1 x n_s or n_s x 1), laid out like H_out.  One placement launch into the zeroed outputs;
+ * synchronises the stream.
  * Errors: EINVAL, ESECTOR (a block of H off the diagonal, a c^dag block that does not raise n_s by one),
  * ENOMEM, ECUDA. */
 int tdmrg_enlarge(tdmrg_ctx* ctx, int side, int nsec, const int32_t* qn, const int32_t* dim, const tdmrg_blocks* H,
                   const tdmrg_blocks* cdag, double t, double U, tdmrg_c64* H_out, tdmrg_c64* const* cdag_out,
-                  int32_t* const* cdag_qn_out);
+                  int32_t* const* cdag_qn_out, tdmrg_c64* const* n_out);
 
 /* Operator op_id of one side defined as the adjoint of operator src_id of the same side (block (q_in, q_out)
  * = the conjugate transpose of block (q_out, q_in); same fermion parity): e.g. c from c^dag for the
@@ -268,23 +284,33 @@ int tdmrg_enlarge(tdmrg_ctx* ctx, int side, int nsec, const int32_t* qn, const i
 int tdmrg_set_op_adjoint(tdmrg_ctx* ctx, int side, int op_id, int src_id);
 
 /* Wave-function transformation of a target (Sec. II.B: transporting the targets from one superblock to
- * the next during a sweep) when the centre moves one site to the right.  `from` holds the superblock
- * (L_enl, R_enl) with R_enl = site + R_b; `to` holds (L_enl', R_enl') with L_enl' = K + site, K the kept
- * states of L_enl, and R_b the kept basis of R_enl'.  Block bases are Kronecker products sorted stably by
- * quantum number: inside a sector of R_enl the site states (0,0), (0,1), (1,0), (1,1) come in that order,
- * each followed by the states of R_b in its order; a sector of L_enl' runs over the states of K in order.
- *   psi_d: the target in `from`'s sector Q = (n_up, n_dn); out_d: the result in `to`'s sector Q (cleared
- *          first); U_d: per left sector of `from`, the dim x dim matrix whose first kept[s] columns are the
- *          kept states (the layout of tdmrg_rho_eig); kept: host, one count per left sector of `from`;
- *   rb_nsec, rb_qn, rb_dim: the sector table of R_b (host); V_d: per sector q of R_b, the
- *          dim_R_enl'(q) x dim_R_b(q) row-major matrix whose columns are R_b's states in the basis of R_enl',
- *          concatenated in R_b's sector order.
- * No fermion sign arises (the moved site keeps its place in the lattice order).  Two grouped FP64
- * launches on `from`'s stream; allocates scratch and synchronises.  Errors: EINVAL, ESTATE, ESECTOR
- * (the block tables are not site + R_b and K + site), ENOMEM, ECUDA. */
+ * the next during a finite sweep).  Block bases are Kronecker products sorted stably by quantum number:
+ * a sector of an enlarged left block K + site runs over K's sectors in order, a sector of an enlarged
+ * right block site + K over the site states (0,0), (0,1), (1,0), (1,1) in order, each followed by the
+ * states of K's matching sector.  U_d and V_d are in the layout of tdmrg_rho_eig: per sector of the
+ * block they belong to, in table order, a dim x dim row-major matrix whose first columns are the kept
+ * states (kept[s], kept_next[s] of them; host arrays, one count per sector).
+ *
+ * tdmrg_wft_right, the centre moves one site to the right: `from` holds (L_enl, R_enl) with
+ * R_enl = site + R_b, `to` holds (L_enl', R_enl') with L_enl' = K + site.  U_d: rho_L's eigenvectors of
+ * `from`'s left block, kept the kept counts there (K); V_d: over `to`'s right block R_enl', whose first
+ * kept_next columns per sector are R_b (the truncation that made R_b).  Psi' = (U^dag Psi) re-indexed,
+ * with R_b's states expanded in R_enl'.
+ * tdmrg_wft_left, the centre moves one site to the left: `from` holds (L_enl = L_b + site, R_enl), `to`
+ * holds (L_enl', R_enl' = site + K).  U_d: rho_R's eigenvectors of `from`'s right block (tdmrg_rho_eig_side
+ * with side 1), kept there (K); V_d: over `to`'s left block L_enl', whose first kept_next columns per
+ * sector are L_b.  Psi' = (Psi conj(U)) re-indexed, with L_b's states expanded in L_enl'.
+ *
+ * psi_d: the target in `from`'s sector Q = (n_up, n_dn); out_d: the result in `to`'s sector Q (cleared
+ * first).  No fermion sign arises (the moved site keeps its place in the lattice order).  Two grouped FP64
+ * launches on `from`'s stream; allocates scratch and synchronises.  Errors: EINVAL (null, kept counts
+ * outside 0..dim), ESTATE, ESECTOR (the block tables do not match the move), ENOMEM, ECUDA. */
 int tdmrg_wft_right(tdmrg_ctx* from, int n_up, int n_dn, const tdmrg_c64* psi_d, const tdmrg_c64* U_d,
-                    const int32_t* kept, int rb_nsec, const int32_t* rb_qn, const int32_t* rb_dim,
-                    const tdmrg_c64* V_d, tdmrg_ctx* to, tdmrg_c64* out_d);
+                    const int32_t* kept, const tdmrg_c64* V_d, const int32_t* kept_next, tdmrg_ctx* to,
+                    tdmrg_c64* out_d);
+int tdmrg_wft_left(tdmrg_ctx* from, int n_up, int n_dn, const tdmrg_c64* psi_d, const tdmrg_c64* U_d,
+                   const int32_t* kept, const tdmrg_c64* V_d, const int32_t* kept_next, tdmrg_ctx* to,
+                   tdmrg_c64* out_d);
 
 /* out_d[0] = <psi| opL opR |psi> / <psi|psi> for a sector-preserving product (Eq. generalcorrelation
  * with a = 1 local operator per block, Eq. nholondoublon; -1 = identity on that block).  out_d is
@@ -296,7 +322,8 @@ int tdmrg_expect(tdmrg_ctx* ctx, int opL, int opR, int n_up, int n_dn, const tdm
  * one local operator per block (-1 = identity on that block), e.g. one entry of a Green's function
  * <phi(t)| c_i c^dag_j |psi(t)> (Sec. I).  phi2_d lives in sector Q2 = (n_up2, n_dn2); opL opR (with
  * the fermion sign of tdmrg_apply_op) maps it to Q1 = (n_up1, n_dn1), the sector of phi1_d.  The
- * product uses a library-owned scratch vector and a fixed-order FP64 reduction.  Errors as apply_op. */
+ * product uses a library-owned scratch vector and a fixed-order FP64 reduction; with both ids -1 it is
+ * the plain overlap <phi1|phi2> (Q1 = Q2).  Errors as apply_op. */
 int tdmrg_overlap_op(tdmrg_ctx* ctx, int opL, int opR, int n_up1, int n_dn1, const tdmrg_c64* phi1_d,
                      int n_up2, int n_dn2, const tdmrg_c64* phi2_d, tdmrg_c64* out_d);
 

@@ -43,6 +43,21 @@ def rho_left(sb, states, weights, real_basis=False):
     return rho
 
 
+def rho_right(sb, states, weights, real_basis=False):
+    """rho_R per right sector (the block truncated when a sweep moves left): rho_R[b, b'] =
+    sum_l w_l sum_a Psi_l[a, b] conj(Psi_l[a, b']) / <psi_l|psi_l>; real_basis as in rho_left."""
+    rho = [np.zeros((d, d), dtype=complex) for d in sb.rdim]
+    for (Q, psi), w in zip(states, weights):
+        nrm2 = np.vdot(psi, psi).real
+        for qi, ri, off, dl, dr in sb.pairs(Q):
+            X = psi[off: off + dl * dr].reshape(dl, dr)
+            if real_basis:
+                rho[ri] += (w / nrm2) * (X.real.T @ X.real + X.imag.T @ X.imag)
+            else:
+                rho[ri] += (w / nrm2) * (X.T @ X.conj())
+    return rho
+
+
 def rho_eig(rho):
     """Eigenpairs per sector, eigenvalues descending; columns of U are eigenvectors."""
     out = []

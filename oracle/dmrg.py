@@ -136,8 +136,9 @@ def superblock_of(L, R, t):
     return sb, HL, HR, conns
 
 
-def ground_state(apply_h, n, seed=11035391, nk=120):
-    """Lowest eigenpair by Lanczos with restarts (full re-orthogonalisation), FP64."""
+def ground_state(apply_h, n, seed=11035391, nk=120, resid_tol=1e-9):
+    """Lowest eigenpair by Lanczos with restarts (full re-orthogonalisation), FP64: stops when the energy
+    is stationary to 1e-13 and ||H v - E v|| < resid_tol."""
     rng = np.random.default_rng(seed)
     v = rng.standard_normal(n) + 0j
     v /= np.linalg.norm(v)
@@ -150,7 +151,7 @@ def ground_state(apply_h, n, seed=11035391, nk=120):
         k = np.argmax(np.abs(v))
         v *= abs(v[k]) / v[k]
         if e_old is not None and abs(d[0] - e_old) < 1e-13 * max(1.0, abs(d[0])):
-            if np.linalg.norm(apply_h(v) - d[0] * v) < 1e-9:
+            if np.linalg.norm(apply_h(v) - d[0] * v) < resid_tol:
                 return d[0], v
         e_old = d[0]
     return d[0], v
@@ -218,7 +219,8 @@ class ChainDMRG:
         self.L, self.t, self.U, self.m = L, t, U, m
         self.left = {1: site_block(U)}
         self.right = {1: site_block(U)}
-        self.right_U = {}   # right block of r sites as U^dag of the enlarged block of r - 1 sites (its kept basis)
+        self.right_U = {}   # right block of r sites: its kept states (columns) in the enlarged block of r - 1 sites
+        self.left_U = {}    # the same for the left blocks
         self.energies = []
 
     def _step(self, l, r, Q):
@@ -234,7 +236,7 @@ class ChainDMRG:
             Q = (l + 1, l + 1)
             Lenl, Renl, sb, e, psi = self._step(l, l, Q)
             self.energies.append(("infinite", 2 * l + 2, e))
-            self.left[l + 1] = truncate(Lenl, density.rho_left(sb, [(Q, psi)], [1.0]), self.m)[0]
+            self.left[l + 1], *_, self.left_U[l + 1] = truncate(Lenl, density.rho_left(sb, [(Q, psi)], [1.0]), self.m)
             self.right[l + 1], *_, self.right_U[l + 1] = truncate(Renl, rho_right(sb, Q, psi), self.m)
             l += 1
 
@@ -248,7 +250,7 @@ class ChainDMRG:
             Lenl, Renl, sb, e, psi = self._step(l, L - 2 - l, Q)
             self.energies.append(("sweep right", l, e))
             if l + 1 <= L - 3:
-                self.left[l + 1] = truncate(Lenl, rho_l(sb, psi), self.m)[0]
+                self.left[l + 1], *_, self.left_U[l + 1] = truncate(Lenl, rho_l(sb, psi), self.m)
         for r in range(1, L - 2):
             Lenl, Renl, sb, e, psi = self._step(L - 2 - r, r, Q)
             self.energies.append(("sweep left", L - 2 - r, e))
@@ -257,7 +259,7 @@ class ChainDMRG:
         for l in range(1, h - 1):
             Lenl, Renl, sb, e, psi = self._step(l, L - 2 - l, Q)
             self.energies.append(("sweep right", l, e))
-            self.left[l + 1] = truncate(Lenl, rho_l(sb, psi), self.m)[0]
+            self.left[l + 1], *_, self.left_U[l + 1] = truncate(Lenl, rho_l(sb, psi), self.m)
 
     def run(self, sweeps=2):
         """Infinite algorithm, `sweeps` finite sweeps, then the superblock at the central cut: returns
@@ -310,4 +312,26 @@ def wft_right(Lenl, Renl, Q, psi, U, Rblk, V, Lenl_next, Renl_next):
     for p, kidx in enumerate(Lenl_next.perm):                    # Lenl_next position p <- (kept a, site s)
         a, s = divmod(kidx, 4)
         out[p, :] = T2[a, s, :]
+    return blocks_of_dense(sbB, Q, out)
+
+
+def wft_left(Lenl, Renl, Q, psi, U, Lblk, V, Lenl_next, Renl_next):
+    """Wave-function transformation (Sec. II.B) when the centre moves one site to the left: psi on
+    (Lenl, Renl) with Lenl = Lblk + site, to (Lenl_next, Renl_next) with Renl_next = site + kept(Renl) and
+    Lblk the kept basis of Lenl_next (|a> = sum_c V[c, a] |c>).  Right: projection on the kept states
+    |u_k> = sum_b U[b, k] |b>, Psi1 = Psi conj(U); left: each left-block state expanded in Lenl_next; no
+    sign (the moved site keeps its place in the lattice order)."""
+    sbA = superblock.Superblock(*Lenl.sectors()[:2], *Renl.sectors()[:2])
+    sbB = superblock.Superblock(*Lenl_next.sectors()[:2], *Renl_next.sectors()[:2])
+    P1 = dense_psi(sbA, Q, psi) @ U.conj()                        # (Lenl, kept)
+    Da, k = Lblk.dim, P1.shape[1]
+    T = np.zeros((Da, 4, k), dtype=complex)
+    for p, kidx in enumerate(Lenl.perm):                          # Lenl position p <- (block a, site s)
+        a, s = divmod(kidx, 4)
+        T[a, s, :] = P1[p, :]
+    T2 = np.einsum("ca,ask->csk", V, T)                           # left block state a -> states c of Lenl_next
+    out = np.zeros((Lenl_next.dim, Renl_next.dim), dtype=complex)
+    for p, kidx in enumerate(Renl_next.perm):                     # Renl_next position p <- (site s, kept k)
+        s, kk = divmod(kidx, k)
+        out[:, p] = T2[:, s, kk]
     return blocks_of_dense(sbB, Q, out)

@@ -194,7 +194,8 @@ int tdmrg_destroy(tdmrg_ctx* c) {
     cudaStreamSynchronize(c->stream);
     drop_plans(c);
     drop_krylov(c);
-    release_eig(c);
+    release_eig(c, 0);
+    release_eig(c, 1);
     dev_free(c, c->pool, c->pool_cap * sizeof(cplx));
     dev_free(c, c->scratch, c->scratch_cap * sizeof(cplx));
     dev_free(c, c->tmp, c->tmp_cap * sizeof(cplx));
@@ -245,7 +246,7 @@ int tdmrg_set_block(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const i
     s.set = true;
     DeviceGuard g(c->opts.device);
     cudaStreamSynchronize(c->stream);
-    if (side == 0) release_eig(c);
+    release_eig(c, side);
     c->side[side] = s;
     c->ops[side].clear();
     c->ham_set = false;
@@ -440,34 +441,49 @@ int tdmrg_tst_weights(int n_v, double* w_gs, double* w) {
     return TDMRG_OK;
 }
 
-int tdmrg_rho_size(tdmrg_ctx* c, int64_t* rho_entries, int64_t* n_evals) {
+int tdmrg_rho_size_side(tdmrg_ctx* c, int side, int64_t* rho_entries, int64_t* n_evals) {
     if (check_ctx(c)) return TDMRG_EINVAL;
-    if (!c->side[0].set) return fail(c, TDMRG_ESTATE, "rho_size: left block not set");
+    if (side != 0 && side != 1) return fail(c, TDMRG_EINVAL, "rho_size: side must be 0 or 1");
+    if (!c->side[side].set) return fail(c, TDMRG_ESTATE, "rho_size: block not set");
     int64_t r = 0, e = 0;
-    for (int d : c->side[0].dim) { r += (int64_t)d * d; e += d; }
+    for (int d : c->side[side].dim) { r += (int64_t)d * d; e += d; }
     if (rho_entries) *rho_entries = r;
     if (n_evals) *n_evals = e;
     return TDMRG_OK;
 }
 
-int tdmrg_density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const tdmrg_c64* const* psi, const double* w,
-                         tdmrg_c64* rho) {
+int tdmrg_rho_size(tdmrg_ctx* c, int64_t* rho_entries, int64_t* n_evals) {
+    return tdmrg_rho_size_side(c, 0, rho_entries, n_evals);
+}
+
+int tdmrg_density_matrix_side(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const tdmrg_c64* const* psi,
+                              const double* w, tdmrg_c64* rho) {
     if (check_ctx(c)) return TDMRG_EINVAL;
     if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "density_matrix: blocks not set");
-    if (nt < 1 || nt > kMaxBufs - BUF_EXTRA0 || !Q || !psi || !w || !rho)
-        return fail(c, TDMRG_EINVAL, "density_matrix: bad argument (1..12 targets)");
+    if ((side != 0 && side != 1) || nt < 1 || nt > kMaxBufs - BUF_EXTRA0 || !Q || !psi || !w || !rho)
+        return fail(c, TDMRG_EINVAL, "density_matrix: bad argument (side 0 or 1, 1..12 targets)");
     for (int l = 0; l < nt; ++l)
         if (!psi[l] || !(w[l] >= 0.0)) return fail(c, TDMRG_EINVAL, "density_matrix: null state or negative weight");
     DeviceGuard g(c->opts.device);
-    return density_matrix(c, nt, Q, (const cplx* const*)psi, w, (cplx*)rho);
+    return density_matrix(c, side, nt, Q, (const cplx* const*)psi, w, (cplx*)rho);
+}
+
+int tdmrg_density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const tdmrg_c64* const* psi, const double* w,
+                         tdmrg_c64* rho) {
+    return tdmrg_density_matrix_side(c, 0, nt, Q, psi, w, rho);
+}
+
+int tdmrg_rho_eig_side(tdmrg_ctx* c, int side, const tdmrg_c64* rho, double* evals, tdmrg_c64* evecs) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (side != 0 && side != 1) return fail(c, TDMRG_EINVAL, "rho_eig: side must be 0 or 1");
+    if (!c->side[side].set) return fail(c, TDMRG_ESTATE, "rho_eig: block not set");
+    if (!rho || !evals || !evecs) return fail(c, TDMRG_EINVAL, "rho_eig: null pointer");
+    DeviceGuard g(c->opts.device);
+    return rho_eig(c, side, (const cplx*)rho, evals, (cplx*)evecs);
 }
 
 int tdmrg_rho_eig(tdmrg_ctx* c, const tdmrg_c64* rho, double* evals, tdmrg_c64* evecs) {
-    if (check_ctx(c)) return TDMRG_EINVAL;
-    if (!c->side[0].set) return fail(c, TDMRG_ESTATE, "rho_eig: left block not set");
-    if (!rho || !evals || !evecs) return fail(c, TDMRG_EINVAL, "rho_eig: null pointer");
-    DeviceGuard g(c->opts.device);
-    return rho_eig(c, (const cplx*)rho, evals, (cplx*)evecs);
+    return tdmrg_rho_eig_side(c, 0, rho, evals, evecs);
 }
 
 int tdmrg_hpsi_flops(tdmrg_ctx* c, int a, int b, double* flops) {
@@ -573,6 +589,12 @@ int tdmrg_overlap_op(tdmrg_ctx* c, int opL, int opR, int a1, int b1, const tdmrg
     const int64_t n1 = sector_size(c, a1, b1);
     if (n1 == 0 || sector_size(c, a2, b2) == 0) return fail(c, TDMRG_ESECTOR, "overlap_op: empty sector");
     DeviceGuard g(c->opts.device);
+    if (opL < 0 && opR < 0) {   // both identities: the plain overlap <phi1|phi2>
+        if (a1 != a2 || b1 != b2) return fail(c, TDMRG_ESECTOR, "overlap_op: identity between different sectors");
+        c->launches += 1;
+        return cuda_check(c, launch_dot_final((const cplx*)phi1, (const cplx*)phi2, n1, c->red, kRedBlocks, (cplx*)out, 0,
+                                              c->stream), "overlap_op reduction");
+    }
     int rc = ensure_tmp(c, n1);
     if (rc) return rc;
     rc = tdmrg_apply_op(c, opL, opR, a2, b2, phi2, a1, b1, (tdmrg_c64*)c->tmp);   // opL opR phi2, in Q1

@@ -554,10 +554,10 @@ __global__ void __launch_bounds__(256) k_eig_sort(const cplx* __restrict__ W_eve
 // Buffer ids of the refinement GEMMs (all packed like rho).
 enum { EB_RHO = BUF_EXTRA0, EB_W, EB_AX, EB_S, EB_G, EB_E, EB_WN };
 
-int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
-    const Side& L = c->side[0];
+int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs) {
+    const Side& L = c->side[side];
     const int ns = (int)L.dim.size();
-    EigWork& w = c->eig;
+    EigWork& w = c->eig[side];
     cudaStream_t s = c->stream;
     if (!w.ready) {
         std::vector<int64_t> off(ns), eoff(ns);
@@ -722,8 +722,8 @@ int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs) {
     return cuda_check(c, e, "rho_eig launch");
 }
 
-void release_eig(tdmrg_ctx* c) {
-    EigWork& w = c->eig;
+void release_eig(tdmrg_ctx* c, int side) {
+    EigWork& w = c->eig[side];
     release(c, w.tl_ax); release(c, w.tl_sg); release(c, w.tl_y);
     const int ns = w.ns;
     dev_free(c, w.tables, w.tables_bytes);

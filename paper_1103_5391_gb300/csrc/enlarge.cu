@@ -46,7 +46,7 @@ struct Place {
     double diag;            // added on the diagonal (MODE_COPY, MODE_ADJ)
 };
 struct PlaceTile { int item, r0, c0; };
-struct PlaceBufs { cplx* d[3]; const cplx* s[3]; };
+struct PlaceBufs { cplx* d[5]; const cplx* s[3]; };
 
 // One CTA of 32 x 8 threads per 32 x 32 destination tile; a transposed source goes through shared memory
 // so that both the read and the write are coalesced.
@@ -193,7 +193,7 @@ extern "C" int tdmrg_enlarge_size(int side, int nsec, const int32_t* qn, const i
 
 extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const int32_t* dim,
                              const tdmrg_blocks* H, const tdmrg_blocks* cdag, double t, double U, tdmrg_c64* H_out,
-                             tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out) {
+                             tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out, tdmrg_c64* const* n_out) {
     if (!c) return fail(nullptr, TDMRG_EINVAL, "null context");
     if ((side != 0 && side != 1) || !H || !cdag || !H_out || !cdag_out || !cdag_out[0] || !cdag_out[1])
         return fail(c, TDMRG_EINVAL, "enlarge: bad argument");
@@ -298,14 +298,32 @@ extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn
                 b[2] = L.qn[L.cblk[sg][k].second].first; b[3] = L.qn[L.cblk[sg][k].second].second;
             }
     }
+    // densities of the new site: identity runs where the site state holds a particle of that spin
+    for (int sg = 0; sg < 2; ++sg) {
+        if (!n_out || !n_out[sg]) continue;
+        for (int q = 0; q < nsec; ++q)
+            for (int s = 0; s < 4; ++s) {
+                if (!kSq[s][sg == 0 ? 0 : 1]) continue;
+                const int o = hsec(q, s), r = L.roff[q][s];
+                Place p{};
+                p.mode = MODE_EYE; p.scale = make_double2(1.0, 0.0);
+                p.dst = L.hoff[o] + (int64_t)r * L.dim[o] + r; p.ldd = L.dim[o]; p.rows = p.cols = dim[q];
+                p.dbuf = (int8_t)(3 + sg);
+                items.push_back(p);
+            }
+    }
     DeviceGuard g(c->opts.device);
     rc = cuda_check(c, cudaMemsetAsync(H_out, 0, (size_t)L.nH * sizeof(cplx), c->stream), "enlarge clear");
+    for (int sg = 0; sg < 2 && !rc; ++sg)
+        if (n_out && n_out[sg])
+            rc = cuda_check(c, cudaMemsetAsync(n_out[sg], 0, (size_t)L.nH * sizeof(cplx), c->stream), "enlarge clear");
     for (int sg = 0; sg < 2 && !rc; ++sg)
         if (L.nC[sg]) rc = cuda_check(c, cudaMemsetAsync(cdag_out[sg], 0, (size_t)L.nC[sg] * sizeof(cplx), c->stream),
                                       "enlarge clear");
     if (rc) return rc;
     PlaceBufs pb{};
     pb.d[0] = (cplx*)H_out; pb.d[1] = (cplx*)cdag_out[0]; pb.d[2] = (cplx*)cdag_out[1];
+    pb.d[3] = n_out ? (cplx*)n_out[0] : nullptr; pb.d[4] = n_out ? (cplx*)n_out[1] : nullptr;
     pb.s[0] = (const cplx*)H->data_d; pb.s[1] = (const cplx*)cdag[0].data_d; pb.s[2] = (const cplx*)cdag[1].data_d;
     return launch_places(c, items, pb);
 }

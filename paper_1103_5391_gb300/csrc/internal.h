@@ -318,7 +318,7 @@ struct tdmrg_ctx {
     int real_basis = 0;            // tdmrg_density_matrix forms Re rho_L (targets' real and imaginary parts apart)
     const tdmrg::cplx* dcoef = nullptr;   // caller's device array of connection coefficients (null: static)             // tensor path: sector products with min(M, N) below this run on FP64 warps
     int* dstatus = nullptr;        // device word: bit 0 set when a bounded device wait ran out
-    tdmrg::EigWork eig;
+    tdmrg::EigWork eig[2];         // per side (rho_L, rho_R)
 };
 
 namespace tdmrg {
@@ -379,13 +379,13 @@ cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* p
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs: fixed, so reductions are deterministic
 
 // density.cu
-int density_matrix(tdmrg_ctx* c, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho);
+int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho);
 
 // correlation.cu
 void release_corr(tdmrg_ctx* c);
 
 // eig.cu
-int rho_eig(tdmrg_ctx* c, const cplx* rho, double* evals, cplx* evecs);
-void release_eig(tdmrg_ctx* c);
+int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs);
+void release_eig(tdmrg_ctx* c, int side);
 
 }  // namespace tdmrg

@@ -154,13 +154,14 @@ __global__ void __launch_bounds__(TT) k_truncate(const double* __restrict__ eval
 
 using namespace tdmrg;
 
-extern "C" int tdmrg_truncate(tdmrg_ctx* c, const double* evals, int m, int32_t* kept, double* discarded) {
+extern "C" int tdmrg_truncate_side(tdmrg_ctx* c, int side, const double* evals, int m, int32_t* kept, double* discarded) {
     if (!c) return fail(nullptr, TDMRG_EINVAL, "null context");
-    if (!evals || !kept || m < 1) return fail(c, TDMRG_EINVAL, "truncate: null pointer or m < 1");
-    const Side& L = c->side[0];
-    if (!L.set) return fail(c, TDMRG_ESTATE, "truncate: left block not set");
+    if ((side != 0 && side != 1) || !evals || !kept || m < 1)
+        return fail(c, TDMRG_EINVAL, "truncate: side not 0 or 1, null pointer or m < 1");
+    const Side& L = c->side[side];
+    if (!L.set) return fail(c, TDMRG_ESTATE, "truncate: block not set");
     const int ns = (int)L.dim.size();
-    if (ns > 1024) return fail(c, TDMRG_EINVAL, "truncate: more than 1024 left sectors");
+    if (ns > 1024) return fail(c, TDMRG_EINVAL, "truncate: more than 1024 sectors");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != c->opts.device) cudaSetDevice(c->opts.device);
@@ -192,6 +193,10 @@ extern "C" int tdmrg_truncate(tdmrg_ctx* c, const double* evals, int m, int32_t*
     }
     if (prev >= 0 && prev != c->opts.device) cudaSetDevice(prev);
     return rc;
+}
+
+extern "C" int tdmrg_truncate(tdmrg_ctx* c, const double* evals, int m, int32_t* kept, double* discarded) {
+    return tdmrg_truncate_side(c, 0, evals, m, kept, discarded);
 }
 
 extern "C" int tdmrg_renormalize_op(tdmrg_ctx* c, int side, int op_id, const tdmrg_c64* U, const int32_t* kept,

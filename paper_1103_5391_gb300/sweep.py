@@ -1,0 +1,228 @@
+"""Finite DMRG sweeps with time-step targeting on the device (Sec. I; Sec. II.B-II.D), driven through
+the C ABI of libtdmrg.  Every arithmetic step (ground state, excitation, Krylov advance, reduced density
+matrix, its eigendecomposition, truncation, renormalisation, enlargement, wave-function transformation,
+observables) runs in the library's kernels; this module keeps the block tables (host) and the blocks'
+device buffers (torch tensors) and calls the entry points in the order of the method.
+
+A kept block K (Block) holds its sector table, H_K and the edge-site c^dag_s as device sector blocks,
+and -- when it was cut from an enlarged block -- its states in that block's basis (V, the layout of
+tdmrg_rho_eig) with the kept counts, which the wave-function transformation needs.  Enlarged blocks
+(Enlarged) add the new site's densities.  Operator ids inside a superblock context: 0 = H, 10 + s =
+c^dag_{edge s}, 30 + s = its adjoint, 50 + s = n_{edge s}; the boundary terms are -t c^dag_L c_R and
++t c_L c^dag_R per spin.
+
+Schedule of one sweep with time-step targeting (the paper leaves it open): from the centre of the chain
+move right to the right end (right block of one site), left to the left end, and right back to the
+centre; the excitation c^dag_{up} on the first site of the right enlarged block is applied at the first
+step, and the targets advance by tau at every `advance_every`-th step after it (Sec. II.C: the targets
+are wave-function transformed at every other step).
+"""
+import numpy as np
+import torch
+
+from . import tdmrg as T
+
+H_ID, CDAG_ID, C_ID, N_ID = 0, 10, 30, 50
+
+
+def _zeros(n, dev):
+    return torch.zeros(max(int(n), 1), dtype=torch.complex128, device=dev)
+
+
+class Block:
+    """A kept block on the device."""
+
+    def __init__(self, qn, dim, H, cdag, V=None, kept_V=None):
+        self.qn = [tuple(int(x) for x in q) for q in qn]
+        self.dim = [int(x) for x in dim]
+        self.H = H            # (block quantum numbers, device data)
+        self.cdag = cdag      # [(qns, data), (qns, data)] for up, down
+        self.V = V            # its states in the enlarged block it was cut from (tdmrg_rho_eig layout), or None
+        self.kept_V = kept_V  # kept counts per sector of that enlarged block
+
+
+class Enlarged:
+    """K + site or site + K on the device, with the new site's densities."""
+
+    def __init__(self, qn, dim, H, cdag, n):
+        self.qn, self.dim, self.H, self.cdag, self.n = qn, dim, H, cdag, n
+
+
+def enlarge(ctx, blk, side, t, U, dev):
+    qn, dim, nb, ent = T.tdmrg_enlarge_size(side, blk.qn, blk.dim)
+    qn = [tuple(int(x) for x in q) for q in qn]
+    dim = [int(x) for x in dim]
+    H = _zeros(ent[0], dev)
+    cd = [_zeros(ent[1 + s], dev) for s in range(2)]
+    n = [_zeros(ent[0], dev) for _ in range(2)]
+    cq = T.tdmrg_enlarge(ctx, side, blk.qn, blk.dim, blk.H, blk.cdag, t, U, H, cd, n)
+    hq = [q + q for q in qn]
+    return Enlarged(qn, dim, (hq, H), [(cq[s], cd[s]) for s in range(2)], [(hq, n[s]) for s in range(2)])
+
+
+def load(ctx, Lenl, Renl, t):
+    """The superblock (Lenl, Renl) with the Hubbard bond between the two edge sites."""
+    for side, b in enumerate((Lenl, Renl)):
+        T.tdmrg_set_block(ctx, side, b.qn, b.dim)
+    for side, b in enumerate((Lenl, Renl)):
+        T.tdmrg_set_op_device(ctx, side, H_ID, 0, *b.H)
+        for s in range(2):
+            T.tdmrg_set_op_device(ctx, side, CDAG_ID + s, 1, *b.cdag[s])
+            T.tdmrg_set_op_adjoint(ctx, side, C_ID + s, CDAG_ID + s)
+            T.tdmrg_set_op_device(ctx, side, N_ID + s, 0, *b.n[s])
+    conns = [(CDAG_ID + s, C_ID + s, -t) for s in range(2)] + [(C_ID + s, CDAG_ID + s, t) for s in range(2)]
+    T.tdmrg_set_hamiltonian(ctx, H_ID, H_ID, conns)
+
+
+def _kept_blocks(qns, kept_of):
+    """Blocks of an operator that survive the truncation (both sectors kept), in the order they were set."""
+    return [q for q in qns if kept_of.get(tuple(q[:2]), 0) > 0 and kept_of.get(tuple(q[2:]), 0) > 0]
+
+
+def truncate_block(ctx, side, enl, states, weights, m, real_basis, dev):
+    """Reduced density matrix of one block of the superblock in ctx from the weighted targets, its
+    eigendecomposition and the m-state truncation, then H and the edge c^dag renormalised into the kept
+    basis.  Returns (Block K, host record {kept, evals, discarded}, U)."""
+    nr, ne = T.tdmrg_rho_size(ctx, side)
+    rho = _zeros(nr, dev)
+    T.tdmrg_set_real_basis(ctx, real_basis)
+    T.tdmrg_density_matrix(ctx, states, weights, rho, side=side)
+    evals = torch.zeros(ne, dtype=torch.float64, device=dev)
+    U = _zeros(nr, dev)
+    T.tdmrg_rho_eig(ctx, rho, evals, U, side=side)
+    kept_d = torch.zeros(len(enl.dim), dtype=torch.int32, device=dev)
+    disc = torch.zeros(1, dtype=torch.float64, device=dev)
+    T.tdmrg_truncate(ctx, evals, m, kept_d, disc, side=side)
+    kept = [int(x) for x in kept_d.cpu().numpy()]
+    kept_of = dict(zip(enl.qn, kept))
+    kq = [q for q, k in zip(enl.qn, kept) if k > 0]
+    kd = [k for k in kept if k > 0]
+    ops = []
+    for op_id, qns in [(H_ID, enl.H[0]), (CDAG_ID, enl.cdag[0][0]), (CDAG_ID + 1, enl.cdag[1][0])]:
+        out = _zeros(sum(enl.dim[enl.qn.index(tuple(q[:2]))] * enl.dim[enl.qn.index(tuple(q[2:]))] for q in qns), dev)
+        nb = T.tdmrg_renormalize_op(ctx, side, op_id, U, kept, out)
+        kb = _kept_blocks(qns, kept_of)
+        assert nb == len(kb)
+        ops.append((kb, out))
+    K = Block(kq, kd, ops[0], ops[1:], V=U, kept_V=kept)
+    ev = evals.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(enl.dim)])
+    rec = {"kept": kept, "evals": [ev[off[i]: off[i + 1]] for i in range(len(enl.dim))],
+           "discarded": float(disc.cpu().numpy()[0])}
+    return K, rec, U
+
+
+class TSTSweep:
+    """One finite sweep of the L-site Hubbard chain (half filling) with time-step targeting, on the device.
+
+    left, right: dicts {number of sites: Block} of the stored blocks the sweep starts from (each block of
+    two or more sites with its V and kept counts); they are replaced by the blocks the sweep makes."""
+
+    def __init__(self, L, t, U, m, left, right, n_v=4, tau=0.1, nk=12, advance_every=2, gs_nk=32, gs_restarts=40,
+                 real_basis=False, device=None):
+        self.L, self.t, self.U, self.m = L, t, U, m
+        self.left, self.right = dict(left), dict(right)
+        self.n_v, self.tau, self.nk, self.advance_every = n_v, tau, nk, advance_every
+        self.gs_nk, self.gs_restarts = gs_nk, gs_restarts
+        self.real_basis = real_basis
+        self.dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.times = [x * tau / (n_v - 1) for x in range(n_v)]
+        self.w_gs, self.w = T.tdmrg_tst_weights(n_v)
+
+    def path(self):
+        h, L = self.L // 2 - 1, self.L
+        p = [(l, "R") for l in range(h, L - 3)] + [(l, "L") for l in range(L - 3, 1, -1)] + [(l, "R") for l in range(1, h)]
+        return p + [(h, None)]
+
+    def _ctx(self):
+        return T.tdmrg_create(device=self.dev.index, stream=torch.cuda.current_stream(self.dev).cuda_stream,
+                              nk_max=max(32, self.nk, self.gs_nk))
+
+    def _observe(self, ctx, Q, x):
+        n = T.tdmrg_sector_size(ctx, Q)
+        out = _zeros(5, self.dev)
+        hx = _zeros(n, self.dev)
+        T.tdmrg_overlap_op(ctx, -1, -1, Q, x, Q, x, out[0:1])
+        T.tdmrg_apply_h(ctx, Q, x, hx)
+        T.tdmrg_overlap_op(ctx, -1, -1, Q, x, Q, hx, out[1:2])
+        T.tdmrg_expect(ctx, N_ID, -1, Q, x, out[2:3])
+        T.tdmrg_expect(ctx, -1, N_ID, Q, x, out[3:4])
+        T.tdmrg_expect(ctx, CDAG_ID, C_ID, Q, x, out[4:5])
+        o = out.cpu().numpy()
+        return {"norm2": o[0].real, "energy": o[1].real / o[0].real, "n_left": o[2], "n_right": o[3], "bond": o[4]}
+
+    def run(self, psi0=None):
+        """Runs the sweep; returns the per-step records (host)."""
+        L, h = self.L, self.L // 2
+        Q0, Q1 = (h, h), (h + 1, h)
+        work, cur, nxt = self._ctx(), self._ctx(), self._ctx()
+        records = []
+        psi, targets, t_now = None, None, 0.0
+        try:
+            path = self.path()
+            l0 = path[0][0]
+            Lenl = enlarge(work, self.left[l0], 0, self.t, self.U, self.dev)
+            Renl = enlarge(work, self.right[L - 2 - l0], 1, self.t, self.U, self.dev)
+            load(cur, Lenl, Renl, self.t)
+            if psi0 is None:
+                n0 = T.tdmrg_sector_size(cur, Q0)
+                g = torch.Generator().manual_seed(11035391)
+                psi = torch.complex(torch.randn(n0, generator=g, dtype=torch.float64),
+                                    torch.randn(n0, generator=g, dtype=torch.float64)).to(self.dev)
+            else:
+                psi = psi0
+            for step, (l, move) in enumerate(path):
+                r = L - 2 - l
+                e = T.tdmrg_ground_state(cur, Q0, psi, self.gs_nk, self.gs_restarts)
+                action = "keep"
+                if step == 0:
+                    phi = _zeros(T.tdmrg_sector_size(cur, Q1), self.dev)
+                    T.tdmrg_apply_op(cur, -1, CDAG_ID, Q0, psi, Q1, phi)
+                    targets = [torch.empty_like(phi) for _ in range(self.n_v)]
+                    T.tdmrg_evolve(cur, Q1, phi, self.times, self.nk, targets)
+                    action = "excite"
+                elif step % self.advance_every == 0:
+                    new = [torch.empty_like(targets[0]) for _ in range(self.n_v)]
+                    T.tdmrg_evolve(cur, Q1, targets[-1], self.times, self.nk, new)
+                    targets = new
+                    t_now += self.tau
+                    action = "advance"
+                rec = {"l": l, "move": move, "action": action, "t": t_now, "energy": e,
+                       "targets": [self._observe(cur, Q1, x) for x in targets]}
+                if move is not None:
+                    states = [(Q0, psi)] + [(Q1, x) for x in targets]
+                    weights = [self.w_gs] + list(self.w)
+                    side = 0 if move == "R" else 1
+                    K, trec, Uk = truncate_block(cur, side, Lenl if side == 0 else Renl, states, weights, self.m,
+                                                 self.real_basis, self.dev)
+                    rec.update(trec)
+                    if move == "R":
+                        nL = enlarge(work, K, 0, self.t, self.U, self.dev)
+                        nR = enlarge(work, self.right[r - 1], 1, self.t, self.U, self.dev)
+                        load(nxt, nL, nR, self.t)
+                        Rb = self.right[r]
+                        moved = []
+                        for Q, v in states:
+                            o = _zeros(T.tdmrg_sector_size(nxt, Q), self.dev)
+                            T.tdmrg_wft_right(cur, Q, v, Uk, trec["kept"], Rb.V, Rb.kept_V, nxt, o)
+                            moved.append(o)
+                        self.left[l + 1] = K
+                    else:
+                        nL = enlarge(work, self.left[l - 1], 0, self.t, self.U, self.dev)
+                        nR = enlarge(work, K, 1, self.t, self.U, self.dev)
+                        load(nxt, nL, nR, self.t)
+                        Lb = self.left[l]
+                        moved = []
+                        for Q, v in states:
+                            o = _zeros(T.tdmrg_sector_size(nxt, Q), self.dev)
+                            T.tdmrg_wft_left(cur, Q, v, Uk, trec["kept"], Lb.V, Lb.kept_V, nxt, o)
+                            moved.append(o)
+                        self.right[r + 1] = K
+                    psi, targets = moved[0], moved[1:]
+                    Lenl, Renl = nL, nR
+                    cur, nxt = nxt, cur
+                records.append(rec)
+        finally:
+            for c in (work, cur, nxt):
+                T.tdmrg_destroy(c)
+        return records

@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
@@ -84,10 +84,15 @@ def load(path=LIB_PATH):
         "tdmrg_rho_eig": (I, [P, P, P, P]),
         "tdmrg_set_real_basis": (I, [P, I]),
         "tdmrg_truncate": (I, [P, P, I, P, P]),
-        "tdmrg_wft_right": (I, [P, I, I, P, P, PI32, I, PI32, PI32, P, P, P]),
+        "tdmrg_wft_right": (I, [P, I, I, P, P, PI32, P, PI32, P, P]),
+        "tdmrg_wft_left": (I, [P, I, I, P, P, PI32, P, PI32, P, P]),
+        "tdmrg_density_matrix_side": (I, [P, I, I, PI32, P, PD, P]),
+        "tdmrg_rho_size_side": (I, [P, I, PI64, PI64]),
+        "tdmrg_rho_eig_side": (I, [P, I, P, P, P]),
+        "tdmrg_truncate_side": (I, [P, I, P, I, P, P]),
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_enlarge_size": (I, [I, I, PI32, PI32, I, ctypes.POINTER(I), PI32, PI32, PI32, ctypes.POINTER(ctypes.c_int64)]),
-        "tdmrg_enlarge": (I, [P, I, I, PI32, PI32, P, P, ctypes.c_double, ctypes.c_double, P, P, P]),
+        "tdmrg_enlarge": (I, [P, I, I, PI32, PI32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
         "tdmrg_set_op_adjoint": (I, [P, I, I, I]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
@@ -262,33 +267,40 @@ def tdmrg_tst_weights(n_v):
     return wgs.value, w[:n_v].tolist()
 
 
-def tdmrg_rho_size(ctx):
+def tdmrg_rho_size(ctx, side=0):
     r, e = ctypes.c_int64(), ctypes.c_int64()
-    _check(ctx, load().tdmrg_rho_size(ctx, ctypes.byref(r), ctypes.byref(e)))
+    _check(ctx, load().tdmrg_rho_size_side(ctx, side, ctypes.byref(r), ctypes.byref(e)))
     return r.value, e.value
 
 
-def tdmrg_density_matrix(ctx, states, weights, rho):
-    """states: list of (Q, tensor)."""
+def tdmrg_density_matrix(ctx, states, weights, rho, side=0):
+    """states: list of (Q, tensor); side 0: rho_L, side 1: rho_R."""
     q, qp = _i32([x for Q, _ in states for x in Q])
     arr = (ctypes.c_void_p * len(states))(*[_ptr(v) for _, v in states])
     w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
-    return _check(ctx, load().tdmrg_density_matrix(ctx, len(states), qp, arr,
-                                                   w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
+    if side == 0:
+        return _check(ctx, load().tdmrg_density_matrix(ctx, len(states), qp, arr,
+                                                       w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
+    return _check(ctx, load().tdmrg_density_matrix_side(ctx, side, len(states), qp, arr,
+                                                        w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
 
 
 def tdmrg_set_real_basis(ctx, on):
     return _check(ctx, load().tdmrg_set_real_basis(ctx, 1 if on else 0))
 
 
-def tdmrg_rho_eig(ctx, rho, evals, evecs):
-    return _check(ctx, load().tdmrg_rho_eig(ctx, _ptr(rho), _ptr(evals), _ptr(evecs)))
+def tdmrg_rho_eig(ctx, rho, evals, evecs, side=0):
+    if side == 0:
+        return _check(ctx, load().tdmrg_rho_eig(ctx, _ptr(rho), _ptr(evals), _ptr(evecs)))
+    return _check(ctx, load().tdmrg_rho_eig_side(ctx, side, _ptr(rho), _ptr(evals), _ptr(evecs)))
 
 
-def tdmrg_truncate(ctx, evals, m, kept, discarded=None):
-    """kept (device int32, one per left sector) <- kept counts of the m-state truncation; discarded
+def tdmrg_truncate(ctx, evals, m, kept, discarded=None, side=0):
+    """kept (device int32, one per sector of the side) <- kept counts of the m-state truncation; discarded
     (device float64, optional) <- the dropped weight."""
-    return _check(ctx, load().tdmrg_truncate(ctx, _ptr(evals), int(m), _ptr(kept), _ptr(discarded)))
+    if side == 0:
+        return _check(ctx, load().tdmrg_truncate(ctx, _ptr(evals), int(m), _ptr(kept), _ptr(discarded)))
+    return _check(ctx, load().tdmrg_truncate_side(ctx, side, _ptr(evals), int(m), _ptr(kept), _ptr(discarded)))
 
 
 def tdmrg_renormalize_op(ctx, side, op_id, U, kept, out):
@@ -300,13 +312,20 @@ def tdmrg_renormalize_op(ctx, side, op_id, U, kept, out):
     return nb.value
 
 
-def tdmrg_wft_right(ctx_from, Q, psi, U, kept, rb_qn, rb_dim, V, ctx_to, out):
+def tdmrg_wft_right(ctx_from, Q, psi, U, kept, V, kept_next, ctx_to, out):
     """Transport psi (ctx_from, sector Q) to ctx_to's superblock when the centre moves one site right."""
     k, kp = _i32(kept)
-    q, qp = _i32(np.asarray(rb_qn).reshape(-1))
-    d, dp = _i32(rb_dim)
-    return _check(ctx_from, load().tdmrg_wft_right(ctx_from, Q[0], Q[1], _ptr(psi), _ptr(U), kp, len(d), qp, dp, _ptr(V),
+    kn, knp = _i32(kept_next)
+    return _check(ctx_from, load().tdmrg_wft_right(ctx_from, Q[0], Q[1], _ptr(psi), _ptr(U), kp, _ptr(V), knp,
                                                    ctx_to, _ptr(out)))
+
+
+def tdmrg_wft_left(ctx_from, Q, psi, U, kept, V, kept_next, ctx_to, out):
+    """Transport psi (ctx_from, sector Q) to ctx_to's superblock when the centre moves one site left."""
+    k, kp = _i32(kept)
+    kn, knp = _i32(kept_next)
+    return _check(ctx_from, load().tdmrg_wft_left(ctx_from, Q[0], Q[1], _ptr(psi), _ptr(U), kp, _ptr(V), knp,
+                                                  ctx_to, _ptr(out)))
 
 
 _PI32 = ctypes.POINTER(ctypes.c_int32)
@@ -341,10 +360,11 @@ def tdmrg_enlarge_size(side, qn, dim):
     return [tuple(x) for x in qo[:2 * k].reshape(k, 2)], list(do[:k]), list(nb), list(ent)
 
 
-def tdmrg_enlarge(ctx, side, qn, dim, H, cdag, t, U, H_out, cdag_out):
+def tdmrg_enlarge(ctx, side, qn, dim, H, cdag, t, U, H_out, cdag_out, n_out=None):
     """H = (block quantum numbers, device data) of H_K; cdag = [(qns, data) for up, down] of K's edge
-    c^dag; H_out, cdag_out[2] device outputs sized by tdmrg_enlarge_size.  Returns the block quantum
-    numbers of c^dag'_up and c^dag'_dn."""
+    c^dag; H_out, cdag_out[2] (and optionally n_out[2], the new site's densities, laid out like H_out)
+    device outputs sized by tdmrg_enlarge_size.  Returns the block quantum numbers of c^dag'_up and
+    c^dag'_dn."""
     q, qp = _i32(np.asarray(qn).reshape(-1))
     d, dp = _i32(dim)
     _, _, nb, _ = tdmrg_enlarge_size(side, qn, dim)
@@ -358,8 +378,9 @@ def tdmrg_enlarge(ctx, side, qn, dim, H, cdag, t, U, H_out, cdag_out):
     outs = (ctypes.c_void_p * 2)(_ptr(cdag_out[0]), _ptr(cdag_out[1]))
     qouts = [np.zeros(4 * max(int(nb[s]), 1), np.int32) for s in range(2)]
     qptr = (ctypes.c_void_p * 2)(*[x.ctypes.data_as(ctypes.c_void_p) for x in qouts])
+    nptr = (ctypes.c_void_p * 2)(_ptr(n_out[0]), _ptr(n_out[1])) if n_out is not None else None
     _check(ctx, load().tdmrg_enlarge(ctx, side, len(d), qp, dp, ctypes.byref(hb), cb, float(t), float(U), _ptr(H_out),
-                                     outs, qptr))
+                                     outs, qptr, nptr))
     return [[tuple(x) for x in qouts[s][:4 * int(nb[s])].reshape(-1, 4)] for s in range(2)]
 
 

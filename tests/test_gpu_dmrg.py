@@ -157,15 +157,22 @@ def run_object():
     return d, d.run(sweeps=1)
 
 
-def _blocks_of_V(V, Rn, Rb):
-    """Per sector of Rb, the rows of Rn's sector and Rb's columns of V (V is block diagonal by sector)."""
+def _eig_layout_of_V(V, Rn, Rb):
+    """Rb's states (columns of V over Rn, grouped by Rb's sectors) in the layout of tdmrg_rho_eig: per
+    sector of Rn a dim x dim matrix whose first columns are Rb's states; with the counts per sector."""
     rn_secs, rn_dims, rn_starts = Rn.sectors()
     rb_secs, rb_dims, rb_starts = Rb.sectors()
-    out = []
-    for q, db, sb0 in zip(rb_secs, rb_dims, rb_starts):
-        k = rn_secs.index(q)
-        out.append(V[rn_starts[k]: rn_starts[k] + rn_dims[k], sb0: sb0 + db].ravel())
-    return np.concatenate(out)
+    parts, kept = [], []
+    for q, dq, s0 in zip(rn_secs, rn_dims, rn_starts):
+        M_ = np.zeros((dq, dq), complex)
+        k = 0
+        if q in rb_secs:
+            j = rb_secs.index(q)
+            k = rb_dims[j]
+            M_[:, :k] = V[s0: s0 + dq, rb_starts[j]: rb_starts[j] + k]
+        parts.append(M_.ravel())
+        kept.append(k)
+    return np.concatenate(parts), kept
 
 
 def test_wft_right_matches_oracle(lib, run_object):
@@ -189,12 +196,68 @@ def test_wft_right_matches_oracle(lib, run_object):
         n2 = lib.tdmrg_sector_size(cb, Q)
         assert n2 == len(want)
         out = dev(np.full(n2, np.nan + 0j))
-        rb_secs, rb_dims, _ = d.right[r].sectors()
-        lib.tdmrg_wft_right(ca, Q, dev(psi), dev(Us), counts, rb_secs, rb_dims,
-                            dev(_blocks_of_V(d.right_U[r], Rn, d.right[r])), cb, out)
+        Vh, kept_next = _eig_layout_of_V(d.right_U[r], Rn, d.right[r])
+        lib.tdmrg_wft_right(ca, Q, dev(psi), dev(Us), counts, dev(Vh), kept_next, cb, out)
         assert np.abs(host(out) - want).max() < 1e-13
         # the projection keeps exactly the kept weight and the right expansion is an isometry
         assert abs(np.linalg.norm(host(out)) ** 2 - (1.0 - disc)) < 1e-12
     finally:
         lib.tdmrg_destroy(ca)
         lib.tdmrg_destroy(cb)
+
+
+def test_wft_left_matches_oracle(lib, run_object):
+    """The centre ground state moved one site to the left (rho_R truncation to m = 32 on the right, the
+    left block expanded in the next left enlarged block) against the oracle's transformation: 1e-13;
+    squared norm 1 - discarded weight."""
+    d, (Lenl, Renl, sb, HL, HR, conns, e, psi) = run_object
+    Q = (L // 2, L // 2)
+    l = L // 2 - 1
+    rho = density.rho_right(sb, [(Q, psi)], [1.0])
+    K, counts, lam, disc, Uf = dmrg.truncate(Renl, rho, M)
+    Ln = dmrg.enlarge(d.left[l - 1], "L", T_HOP, U)
+    Rn = dmrg.enlarge(K, "R", T_HOP, U)
+    want = dmrg.wft_left(Lenl, Renl, Q, psi, Uf, d.left[l], d.left_U[l], Ln, Rn)
+    Us = np.concatenate([Uq.ravel() for _, Uq in density.rho_eig(rho)])
+    Vh, kept_next = _eig_layout_of_V(d.left_U[l], Ln, d.left[l])
+    ca, cb = new_ctx(), new_ctx()
+    try:
+        DmrgLoader(ca, Lenl, Renl, T_HOP)
+        DmrgLoader(cb, Ln, Rn, T_HOP)
+        n2 = lib.tdmrg_sector_size(cb, Q)
+        assert n2 == len(want)
+        out = dev(np.full(n2, np.nan + 0j))
+        lib.tdmrg_wft_left(ca, Q, dev(psi), dev(Us), counts, dev(Vh), kept_next, cb, out)
+        assert np.abs(host(out) - want).max() < 1e-13
+        assert abs(np.linalg.norm(host(out)) ** 2 - (1.0 - disc)) < 1e-12
+    finally:
+        lib.tdmrg_destroy(ca)
+        lib.tdmrg_destroy(cb)
+
+
+def test_rho_right_matches_oracle(lib, run_object):
+    """rho_R of the ground state and three random targets in another sector (weights of time-step
+    targeting) against the oracle's, 1e-14; its device eigenvalues against numpy's, 1e-14."""
+    d, (Lenl, Renl, sb, HL, HR, conns, e, psi) = run_object
+    Q0, Q1 = (L // 2, L // 2), (L // 2 + 1, L // 2)
+    rng = np.random.default_rng(9)
+    n1 = sb.size(Q1)
+    xs = [rng.standard_normal(n1) + 1j * rng.standard_normal(n1) for _ in range(3)]
+    w = [0.25, 0.25, 0.25, 0.25]
+    want = density.rho_right(sb, [(Q0, psi)] + [(Q1, x) for x in xs], w)
+    ctx = new_ctx()
+    try:
+        DmrgLoader(ctx, Lenl, Renl, T_HOP)
+        nr, ne = lib.tdmrg_rho_size(ctx, 1)
+        rho = dev(np.zeros(nr))
+        lib.tdmrg_density_matrix(ctx, [(Q0, dev(psi))] + [(Q1, dev(x)) for x in xs], w, rho, side=1)
+        got = host(rho)
+        assert np.abs(got - np.concatenate([r.ravel() for r in want])).max() < 1e-14
+        torch = torch_cuda()
+        ev = torch.zeros(ne, dtype=torch.float64, device="cuda")
+        U = dev(np.zeros(nr))
+        lib.tdmrg_rho_eig(ctx, rho, ev, U, side=1)
+        ref = np.concatenate([lam for lam, _ in density.rho_eig(want)])
+        assert np.abs(ev.cpu().numpy() - ref).max() < 1e-14
+    finally:
+        lib.tdmrg_destroy(ctx)

@@ -1,0 +1,104 @@
+"""One finite sweep with time-step targeting on the GPU (Sec. II.B-II.D) against the oracle's sweep, step
+by step, on the FP64 path.
+
+L=10 Hubbard chain (U=4, half filling), m=24, n_v=4 targets, tau=0.1, n_K=10, advance at every second
+step; both sweeps start from the same stored blocks (the oracle's ground-state DMRG).  The device runs
+every step through the C ABI: ground state by restarted Lanczos, the excitation c^dag_{5 up}, Krylov
+advance, rho_L or rho_R, its eigendecomposition, truncation, renormalisation, enlargement of both blocks
+and the wave-function transformation of all five targets, left and right.  Compared per step (quantities
+that do not depend on eigenvector phases): the ground-state energy (1e-10), the kept counts (equal), all
+eigenvalues of rho and the discarded weight (1e-12), and for every target its norm, <H>, the densities of
+the two central sites and the bond <c^dag_l c_{l+1}> (1e-10).  m=24 is chosen so that no cut of the sweep
+falls inside a cluster of eigenvalues closer than 1e-6 lambda_max (checked on the oracle's records)."""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import dmrg, tst
+from tests.gpu_util import dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+L, U, T_HOP, M = 10, 4.0, 1.0, 24
+
+
+def _blockops(blk, dense, odd):
+    secs, _, _ = blk.sectors()
+    bo = blk.blockop(dense, odd)
+    qns = [tuple(secs[qo]) + tuple(secs[qi]) for (qo, qi) in bo.blocks]
+    data = np.concatenate([b.ravel() for b in bo.blocks.values()])
+    return qns, data
+
+
+def _eig_layout(Ufull, enl, K):
+    """The oracle's kept states (columns of Ufull over the enlarged block enl, grouped by K's sectors) in
+    the layout of tdmrg_rho_eig: per sector of enl a dim x dim matrix whose first columns are K's states."""
+    esecs, edims, estarts = enl.sectors()
+    ksecs, kdims, kstarts = K.sectors()
+    parts, kept = [], []
+    for q, dq, s0 in zip(esecs, edims, estarts):
+        M_ = np.zeros((dq, dq), complex)
+        if q in ksecs:
+            j = ksecs.index(q)
+            M_[:, :kdims[j]] = Ufull[s0: s0 + dq, kstarts[j]: kstarts[j] + kdims[j]]
+            kept.append(kdims[j])
+        else:
+            kept.append(0)
+        parts.append(M_.ravel())
+    return np.concatenate(parts), kept
+
+
+def _device_blocks(d, sweep_mod):
+    left, right = {}, {}
+    for store, ustore, side, out in ((d.left, d.left_U, "L", left), (d.right, d.right_U, "R", right)):
+        for n, blk in store.items():
+            secs, dims, _ = blk.sectors()
+            hq, hd = _blockops(blk, blk.H, False)
+            cd = [_blockops(blk, blk.cdag[s], True) for s in range(2)]
+            V = kept = None
+            if n in ustore:   # (a block older than its smaller neighbour has no usable V; the sweep remakes it first)
+                enl = dmrg.enlarge(store[n - 1], side, d.t, d.U)
+                if ustore[n].shape[0] == enl.dim:
+                    Vh, kept = _eig_layout(ustore[n], enl, blk)
+                    V = dev(Vh)
+            out[n] = sweep_mod.Block(secs, dims, (hq, dev(hd)), [(q, dev(x)) for q, x in cd], V, kept)
+    return left, right
+
+
+@pytest.fixture(scope="module")
+def sweeps():
+    torch_cuda()
+    from paper_1103_5391_gb300 import sweep as S
+    d = dmrg.ChainDMRG(L, T_HOP, U, M)
+    d.run(sweeps=1)
+    left, right = _device_blocks(d, S)
+    want = tst.TSTSweep(copy.deepcopy(d), M, n_v=4, tau=0.1, nk=10, advance_every=2).run()
+    got = S.TSTSweep(L, T_HOP, U, M, left, right, n_v=4, tau=0.1, nk=10, advance_every=2).run()
+    return want, got
+
+
+def test_sweep_cuts_are_clean(sweeps):
+    want, _ = sweeps
+    for r in want:
+        if r["move"] is None:
+            continue
+        lam = np.sort(np.concatenate(r["evals"]))[::-1]
+        if len(lam) > M:
+            assert lam[M - 1] - lam[M] > 1e-6 * lam[0]
+
+
+def test_sweep_matches_oracle_step_by_step(sweeps):
+    want, got = sweeps
+    assert len(want) == len(got) == len(tst.sweep_path(L))
+    for w, g in zip(want, got):
+        assert (g["l"], g["move"], g["action"]) == (w["l"], w["move"], w["action"])
+        assert abs(g["t"] - w["t"]) < 1e-15
+        assert abs(g["energy"] - w["energy"]) < 1e-10, (w["l"], w["move"])
+        if w["move"] is not None:
+            assert g["kept"] == list(w["kept"])
+            assert abs(g["discarded"] - w["discarded"]) < 1e-12
+            for a, b in zip(g["evals"], w["evals"]):
+                assert np.abs(a - b).max() < 1e-12
+        for a, b in zip(g["targets"], w["targets"]):
+            for key in ("norm2", "energy", "n_left", "n_right", "bond"):
+                assert abs(a[key] - b[key]) < 1e-10, (w["l"], w["move"], key, a[key], b[key])
