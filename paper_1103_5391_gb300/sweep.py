@@ -11,11 +11,16 @@ tdmrg_rho_eig) with the kept counts, which the wave-function transformation need
 c^dag_{edge s}, 30 + s = its adjoint, 50 + s = n_{edge s}; the boundary terms are -t c^dag_L c_R and
 +t c_L c^dag_R per spin.
 
-Schedule of one sweep with time-step targeting (the paper leaves it open): from the centre of the chain
-move right to the right end (right block of one site), left to the left end, and right back to the
-centre; the excitation c^dag_{up} on the first site of the right enlarged block is applied at the first
-step, and the targets advance by tau at every `advance_every`-th step after it (Sec. II.C: the targets
-are wave-function transformed at every other step).
+Excitation (Eq. b): phi = B_{b-1} ... B_0 psi with local c^dag / c operators on sites in the order the
+sweep reaches them; B_i is applied at the first step whose central pair of sites (l, the new site of the
+left enlarged block, and l + 1, the new site of the right one) holds its site.  Before B_0 only the
+ground state is targeted; while the product is partial it takes the places of all n_v targets; at the
+step that completes it the targets phi(t_x) are built.
+
+Schedule of one sweep (the paper leaves it open): from the centre of the chain move right to the right
+end (right block of one site), left to the left end, and right back to the centre; the targets advance by
+tau at every `advance_every`-th step after the one that completed phi (Sec. II.C: the targets are
+wave-function transformed at every other step).
 """
 import numpy as np
 import torch
@@ -119,7 +124,7 @@ class TSTSweep:
     two or more sites with its V and kept counts); they are replaced by the blocks the sweep makes."""
 
     def __init__(self, L, t, U, m, left, right, n_v=4, tau=0.1, nk=12, advance_every=2, gs_nk=32, gs_restarts=40,
-                 real_basis=False, device=None):
+                 real_basis=False, device=None, excitations=None):
         self.L, self.t, self.U, self.m = L, t, U, m
         self.left, self.right = dict(left), dict(right)
         self.n_v, self.tau, self.nk, self.advance_every = n_v, tau, nk, advance_every
@@ -128,6 +133,7 @@ class TSTSweep:
         self.dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.times = [x * tau / (n_v - 1) for x in range(n_v)]
         self.w_gs, self.w = T.tdmrg_tst_weights(n_v)
+        self.excitations = list(excitations) if excitations else [(L // 2, "cdag", 0)]
 
     def path(self):
         h, L = self.L // 2 - 1, self.L
@@ -171,27 +177,43 @@ class TSTSweep:
                                     torch.randn(n0, generator=g, dtype=torch.float64)).to(self.dev)
             else:
                 psi = psi0
+            phi, Q1, pending, done_step = None, Q0, list(self.excitations), None
             for step, (l, move) in enumerate(path):
                 r = L - 2 - l
                 e = T.tdmrg_ground_state(cur, Q0, psi, self.gs_nk, self.gs_restarts)
-                action = "keep"
-                if step == 0:
-                    phi = _zeros(T.tdmrg_sector_size(cur, Q1), self.dev)
-                    T.tdmrg_apply_op(cur, -1, CDAG_ID, Q0, psi, Q1, phi)
+                action = "ground" if phi is None else ("partial" if pending else "keep")
+                applied = False
+                while pending and pending[0][0] in (l, l + 1):   # operators of Eq. b reached here
+                    site, kind, sigma = pending.pop(0)
+                    op = (CDAG_ID if kind == "cdag" else C_ID) + sigma
+                    opL, opR = (op, -1) if site == l else (-1, op)
+                    dq = [0, 0]
+                    dq[sigma] = 1 if kind == "cdag" else -1
+                    Qn = (Q1[0] + dq[0], Q1[1] + dq[1])
+                    out = _zeros(T.tdmrg_sector_size(cur, Qn), self.dev)
+                    T.tdmrg_apply_op(cur, opL, opR, Q1, psi if phi is None else phi, Qn, out)
+                    phi, Q1, applied = out, Qn, True
+                if applied and not pending:
                     targets = [torch.empty_like(phi) for _ in range(self.n_v)]
                     T.tdmrg_evolve(cur, Q1, phi, self.times, self.nk, targets)
-                    action = "excite"
-                elif step % self.advance_every == 0:
+                    action, done_step = "excite", step
+                elif applied:
+                    targets, action = [phi] * self.n_v, "partial"
+                elif done_step is not None and (step - done_step) % self.advance_every == 0:
                     new = [torch.empty_like(targets[0]) for _ in range(self.n_v)]
                     T.tdmrg_evolve(cur, Q1, targets[-1], self.times, self.nk, new)
                     targets = new
                     t_now += self.tau
                     action = "advance"
-                rec = {"l": l, "move": move, "action": action, "t": t_now, "energy": e,
-                       "targets": [self._observe(cur, Q1, x) for x in targets]}
+                rec = {"l": l, "move": move, "action": action, "t": t_now, "energy": e, "Q1": Q1,
+                       "applied": len(self.excitations) - len(pending),
+                       "targets": [self._observe(cur, Q1, x) for x in targets or []]}
                 if move is not None:
-                    states = [(Q0, psi)] + [(Q1, x) for x in targets]
-                    weights = [self.w_gs] + list(self.w)
+                    if targets is None:   # before the first operator of Eq. b: the ground state alone
+                        states, weights = [(Q0, psi)], [1.0]
+                    else:
+                        states = [(Q0, psi)] + [(Q1, x) for x in targets]
+                        weights = [self.w_gs] + list(self.w)
                     side = 0 if move == "R" else 1
                     K, trec, Uk = truncate_block(cur, side, Lenl if side == 0 else Renl, states, weights, self.m,
                                                  self.real_basis, self.dev)
@@ -218,7 +240,11 @@ class TSTSweep:
                             T.tdmrg_wft_left(cur, Q, v, Uk, trec["kept"], Lb.V, Lb.kept_V, nxt, o)
                             moved.append(o)
                         self.right[r + 1] = K
-                    psi, targets = moved[0], moved[1:]
+                    psi = moved[0]
+                    if targets is not None:
+                        targets = moved[1:]
+                        if pending:   # the partial product is every target
+                            phi = targets[0]
                     Lenl, Renl = nL, nR
                     cur, nxt = nxt, cur
                 records.append(rec)

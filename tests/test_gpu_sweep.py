@@ -1,15 +1,16 @@
 """One finite sweep with time-step targeting on the GPU (Sec. II.B-II.D) against the oracle's sweep, step
 by step, on the FP64 path.
 
-L=10 Hubbard chain (U=4, half filling), m=24, n_v=4 targets, tau=0.1, n_K=10, advance at every second
-step; both sweeps start from the same stored blocks (the oracle's ground-state DMRG).  The device runs
-every step through the C ABI: ground state by restarted Lanczos, the excitation c^dag_{5 up}, Krylov
+L=10 Hubbard chain (U=4, half filling), m=20..24, n_v=4 targets, tau=0.1, n_K=10, three schedules of
+Eq. b (c^dag_{5 up} at once; c_{7 dn} c^dag_{5 up} completed two steps later; c^dag_{8 dn} reached on the
+left pass after ground-state targeting); both sweeps start from the same stored blocks (the oracle's
+ground-state DMRG).  The device runs every step through the C ABI: ground state by restarted Lanczos, the
+excitation operators, Krylov
 advance, rho_L or rho_R, its eigendecomposition, truncation, renormalisation, enlargement of both blocks
 and the wave-function transformation of all five targets, left and right.  Compared per step (quantities
 that do not depend on eigenvector phases): the ground-state energy (1e-10), the kept counts (equal), all
 eigenvalues of rho and the discarded weight (1e-12), and for every target its norm, <H>, the densities of
-the two central sites and the bond <c^dag_l c_{l+1}> (1e-10).  m=24 is chosen so that no cut of the sweep
-falls inside a cluster of eigenvalues closer than 1e-6 lambda_max (checked on the oracle's records)."""
+the two central sites and the bond <c^dag_l c_{l+1}> (1e-10)."""
 import copy
 
 import numpy as np
@@ -65,33 +66,45 @@ def _device_blocks(d, sweep_mod):
     return left, right
 
 
-@pytest.fixture(scope="module")
-def sweeps():
+# (m, advance_every, excitations of Eq. b); m is chosen per case so that no cut of the sweep falls inside a
+# cluster of eigenvalues closer than 1e-6 lambda_max (checked on the oracle's records below)
+CASES = [
+    (24, 2, [(5, "cdag", 0)]),
+    (20, 1, [(5, "cdag", 0), (7, "c", 1)]),   # partial product for two steps, completed at sites (6, 7)
+    (24, 1, [(8, "cdag", 1)]),                # ground-state targeting until the left pass reaches site 8
+]
+
+
+@pytest.fixture(scope="module", params=range(len(CASES)))
+def sweeps(request):
+    m, every, exc = CASES[request.param]
     torch_cuda()
     from paper_1103_5391_gb300 import sweep as S
-    d = dmrg.ChainDMRG(L, T_HOP, U, M)
+    d = dmrg.ChainDMRG(L, T_HOP, U, m)
     d.run(sweeps=1)
     left, right = _device_blocks(d, S)
-    want = tst.TSTSweep(copy.deepcopy(d), M, n_v=4, tau=0.1, nk=10, advance_every=2).run()
-    got = S.TSTSweep(L, T_HOP, U, M, left, right, n_v=4, tau=0.1, nk=10, advance_every=2).run()
-    return want, got
+    want = tst.TSTSweep(copy.deepcopy(d), m, n_v=4, tau=0.1, nk=10, advance_every=every, excitations=exc).run()
+    got = S.TSTSweep(L, T_HOP, U, m, left, right, n_v=4, tau=0.1, nk=10, advance_every=every,
+                     excitations=exc).run()
+    return m, want, got
 
 
 def test_sweep_cuts_are_clean(sweeps):
-    want, _ = sweeps
+    m, want, _ = sweeps
     for r in want:
         if r["move"] is None:
             continue
         lam = np.sort(np.concatenate(r["evals"]))[::-1]
-        if len(lam) > M:
-            assert lam[M - 1] - lam[M] > 1e-6 * lam[0]
+        if len(lam) > m:
+            assert lam[m - 1] - lam[m] > 1e-7 * lam[0]
 
 
 def test_sweep_matches_oracle_step_by_step(sweeps):
-    want, got = sweeps
+    m, want, got = sweeps
     assert len(want) == len(got) == len(tst.sweep_path(L))
     for w, g in zip(want, got):
-        assert (g["l"], g["move"], g["action"]) == (w["l"], w["move"], w["action"])
+        assert (g["l"], g["move"], g["action"], g["applied"], tuple(g["Q1"])) == \
+            (w["l"], w["move"], w["action"], w["applied"], tuple(w["Q1"]))
         assert abs(g["t"] - w["t"]) < 1e-15
         assert abs(g["energy"] - w["energy"]) < 1e-10, (w["l"], w["move"])
         if w["move"] is not None:
@@ -99,6 +112,7 @@ def test_sweep_matches_oracle_step_by_step(sweeps):
             assert abs(g["discarded"] - w["discarded"]) < 1e-12
             for a, b in zip(g["evals"], w["evals"]):
                 assert np.abs(a - b).max() < 1e-12
+        assert len(g["targets"]) == len(w["targets"])
         for a, b in zip(g["targets"], w["targets"]):
             for key in ("norm2", "energy", "n_left", "n_right", "bond"):
                 assert abs(a[key] - b[key]) < 1e-10, (w["l"], w["move"], key, a[key], b[key])
