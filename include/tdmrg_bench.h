@@ -59,6 +59,11 @@ int tdmrg_fp64_peak(int device, double* dmma_tflops, double* dfma_tflops);
  * Errors: EINVAL (spins outside 1..2^26), ENOMEM, ECUDA. */
 int tdmrg_probe_wait(tdmrg_ctx* ctx, int64_t spins);
 
+/* Per sector of one block (side 0: left, 1: right), from the last tdmrg_rho_eig[_side] there: the
+ * number of sweeps of the FP32 Jacobi seed and the SM cycles its CTA took (host arrays of the side's
+ * sector count).  Synchronises the stream.  Errors: EINVAL, ESTATE (no eigendecomposition yet). */
+int tdmrg_eig_stats(tdmrg_ctx* ctx, int side, int32_t* sweeps, int64_t* cycles);
+
 #ifdef __cplusplus
 }
 #endif

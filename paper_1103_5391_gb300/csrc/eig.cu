@@ -100,6 +100,9 @@ constexpr int JA = 512;   // threads that rotate A (warps 0-15); the other 16 wa
 enum JacMode { JAC_SMEM = 0, JAC_SMEM_A = 1, JAC_GLOBAL = 2 };
 __host__ __device__ inline int jac_mode(int n) { return n <= kSmemMaxN ? JAC_SMEM : n <= kSmemMaxA ? JAC_SMEM_A : JAC_GLOBAL; }
 
+// Sectors whose V is formed afterwards from a global rotation record (V not in shared memory).
+__host__ __device__ inline bool jac_recorded(int n) { return n > kSmemMaxN; }
+
 // Rounds of the rotation record that fit in `smem` bytes beside A and V (two buffers of float4 per pair).
 __host__ __device__ inline int jac_base_bytes(int n) {
     const int m = jac_mode(n);
@@ -157,8 +160,8 @@ __device__ __forceinline__ float jac_lim(bool rel, float thr2, float a, float d)
 // Record mode (grec != nullptr, used when V does not fit in shared memory): every thread rotates A
 // (ja = JT), each rotation is also written to the global record grec (round-major, npair per round) and
 // *nrec receives the number of rounds; V is formed afterwards from the record by k_jacobi_replay.
-__device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int ld, int vrs, int vcs, float thr, bool rel,
-                                              float4* rec, int C, int ja, float4* __restrict__ grec, int* nrec) {
+__device__ __forceinline__ int jacobi_sweeps(float2* A, float2* V, int n, int ld, int vrs, int vcs, float thr, bool rel,
+                                             float4* rec, int C, int ja, float4* __restrict__ grec, int* nrec) {
     const int tid = threadIdx.x;
     const bool agroup = tid < ja;
     int total = 0;   // rounds recorded before the current chunk
@@ -167,7 +170,8 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
     const int warp = tid >> 5, lane = tid & 31;
     int pend = 0, pend_r0 = 0, buf = 0;
     bool done = n <= 1;
-    for (int sweep = 0; sweep < 12 && !done; ++sweep) {
+    int sweep = 0;
+    for (; sweep < 12 && !done; ++sweep) {
         for (int r0 = 0; r0 < R; r0 += C) {
             const int nr = min(C, R - r0);
             const bool last = r0 + nr >= R;
@@ -258,6 +262,7 @@ __device__ __forceinline__ void jacobi_sweeps(float2* A, float2* V, int n, int l
     if (!agroup && pend) jacobi_apply_v(V, n, vrs, vcs, rec + (size_t)(buf ^ 1) * C * npair, pend, pend_r0);
     if (grec != nullptr && tid == 0) *nrec = total;
     __syncthreads();
+    return sweep;
 }
 
 __device__ __forceinline__ void jacobi_load(const cplx* R, double scale, float2* A, float2* V, int n, int ld) {
@@ -298,14 +303,15 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
                                                  double* __restrict__ rho_fro, int* __restrict__ n_iter,
                                                  int* __restrict__ flags, EigTables tb, float2* __restrict__ gwork,
                                                  float4* __restrict__ grec, int* __restrict__ nrec,
-                                                 int smem, bool rel, int it) {
+                                                 int smem, bool rel, int it, int2* __restrict__ stats) {
     pdl_enter();
+    const long long t_start = clock64();
     extern __shared__ float4 fsm4[];
     float2* fsm = reinterpret_cast<float2*>(fsm4);
     const int sct = blockIdx.x, n = tb.dims[sct], tid = threadIdx.x;
     const int mode = jac_mode(n);
     if (rel && (it >= *n_iter || flags[sct] == 0)) {   // iteration skipped, or nothing to re-seed
-        if (mode != JAC_SMEM && tid == 0) nrec[sct] = -1;   // nor is there anything to replay
+        if (jac_recorded(n) && tid == 0) nrec[sct] = -1;   // nor is there anything to replay
         return;
     }
     const int64_t off = tb.off[sct];
@@ -342,14 +348,17 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
     }
     __syncthreads();
     const float thr = thr_s;
+    int sweeps;
     if (mode == JAC_SMEM) {
-        jacobi_sweeps(fsm, fsm + n * ld, n, ld, ld, 1, thr, rel, rec, C, JA, nullptr, nullptr);
+        sweeps = jacobi_sweeps(fsm, fsm + n * ld, n, ld, ld, 1, thr, rel, rec, C, JA, nullptr, nullptr);
         jacobi_store(fsm + n * ld, dst + off, n, ld, 1, rel ? 1.0 : 0.0);
     } else if (mode == JAC_SMEM_A) {   // dst is written by k_jacobi_replay
-        jacobi_sweeps(fsm, nullptr, n, ld, 1, ld, thr, rel, rec, C, JT, grec + tb.roff[sct], nrec + sct);
+        sweeps = jacobi_sweeps(fsm, nullptr, n, ld, 1, ld, thr, rel, rec, C, JT, grec + tb.roff[sct], nrec + sct);
     } else {
-        jacobi_sweeps(gA, nullptr, n, ld, 1, ld, thr, rel, rec, C, JT, grec + tb.roff[sct], nrec + sct);
+        sweeps = jacobi_sweeps(gA, nullptr, n, ld, 1, ld, thr, rel, rec, C, JT, grec + tb.roff[sct], nrec + sct);
     }
+    // per sector of the last launch: sweeps and SM cycles (a measurement aid; tdmrg_eig_stats)
+    if (tid == 0 && !rel) stats[sct] = make_int2(sweeps, (int)min(clock64() - t_start, (long long)INT_MAX));
 }
 
 // V of the sectors beyond kSmemMaxN from their rotation record: V starts as the identity and every
@@ -578,7 +587,7 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         int maxn_big = 0;
         for (int k = 0; k < ns; ++k) {
             const int n = L.dim[k], P = n + (n & 1);
-            if (jac_mode(n) == JAC_SMEM) continue;
+            if (!jac_recorded(n)) continue;
             roff[k] = nrec_total;
             nrec_total += (int64_t)kMaxSweeps * (P - 1) * (P / 2);
             big.push_back(k);
@@ -595,6 +604,7 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         if (!rc && maxn > kSmemMaxA) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
         if (!rc && nrec_total) rc = dev_alloc(c, (void**)&w.grec, (size_t)nrec_total * sizeof(float4), "eig rotation record");
         if (!rc) rc = dev_alloc(c, (void**)&w.nrec, (size_t)ns * sizeof(int), "eig rotation record");
+        if (!rc) rc = dev_alloc(c, (void**)&w.stats, (size_t)ns * sizeof(int2), "eig statistics");
         if (rc) return rc;
         std::vector<unsigned char> host(w.tables_bytes);
         unsigned char* h = host.data();
@@ -679,7 +689,7 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
     double* part = w.fro + ns;
     int* n_iter = reinterpret_cast<int*>(part + 2 * (size_t)ns * kRowChunks);
     launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec, w.jac_smem,
-               false, 0);
+               false, 0, w.stats);
     c->launches += 1;
     replay(W, false);
     GemmArgs a{};
@@ -706,7 +716,7 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         launch_pdl(k_oa_update, chunks, 256, 0, s, S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
         if (reseed_iter(it)) {
             launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec,
-                       w.jac_smem, true, it);
+                       w.jac_smem, true, it, w.stats);
             c->launches++;
             replay(E1h, true);
         }
@@ -729,6 +739,7 @@ void release_eig(tdmrg_ctx* c, int side) {
     dev_free(c, w.tables, w.tables_bytes);
     dev_free(c, w.grec, (size_t)w.grec_entries * sizeof(float4));
     dev_free(c, w.nrec, (size_t)ns * sizeof(int));
+    dev_free(c, w.stats, (size_t)ns * sizeof(int2));
     dev_free(c, w.buf, (size_t)6 * w.nrho * sizeof(cplx));
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
     dev_free(c, w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double));
@@ -738,3 +749,22 @@ void release_eig(tdmrg_ctx* c, int side) {
 }
 
 }  // namespace tdmrg
+
+using namespace tdmrg;
+
+extern "C" int tdmrg_eig_stats(tdmrg_ctx* c, int side, int32_t* sweeps, int64_t* cycles) {
+    if (!c) return fail(nullptr, TDMRG_EINVAL, "null context");
+    if (side != 0 && side != 1) return fail(c, TDMRG_EINVAL, "eig_stats: side must be 0 or 1");
+    const EigWork& w = c->eig[side];
+    if (!w.ready || !w.stats) return fail(c, TDMRG_ESTATE, "eig_stats: no eigendecomposition on this side yet");
+    std::vector<int2> h(w.ns);
+    DeviceGuard g(c->opts.device);
+    int rc = cuda_check(c, cudaMemcpyAsync(h.data(), w.stats, w.ns * sizeof(int2), cudaMemcpyDeviceToHost, c->stream),
+                        "eig_stats");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "eig_stats");
+    for (int k = 0; k < w.ns && !rc; ++k) {
+        if (sweeps) sweeps[k] = h[k].x;
+        if (cycles) cycles[k] = h[k].y;
+    }
+    return rc;
+}

@@ -262,6 +262,7 @@ struct EigWork {
     float4* grec = nullptr;     // Jacobi rotation records of the sectors too large for V in shared memory
     int64_t grec_entries = 0;
     int* nrec = nullptr;        // per sector: rounds recorded by the last Jacobi launch (-1: skipped)
+    int2* stats = nullptr;      // per sector: sweeps and SM cycles of the last seed Jacobi
     int nbig = 0, maxn_big = 0, replay_batch = 0, replay_smem = 0;
     TaskList tl_ax, tl_sg, tl_y;
 };

@@ -22,7 +22,7 @@ EXPORTED = [
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
-    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim",
+    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
@@ -94,6 +94,7 @@ def load(path=LIB_PATH):
         "tdmrg_enlarge_size": (I, [I, I, PI32, PI32, I, ctypes.POINTER(I), PI32, PI32, PI32, ctypes.POINTER(ctypes.c_int64)]),
         "tdmrg_enlarge": (I, [P, I, I, PI32, PI32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
         "tdmrg_set_op_adjoint": (I, [P, I, I, I]),
+        "tdmrg_eig_stats": (I, [P, I, PI32, PI64]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
         "tdmrg_correlation": (I, [P, I, PI32, I, PI32, I, I, P, I, I, P, P]),
@@ -404,6 +405,15 @@ def tdmrg_overlap_op(ctx, opL, opR, Q1, phi1, Q2, phi2, out):
     """out[0] = <phi1| opL opR |phi2> (phi2 in sector Q2, phi1 in the sector Q1 the operators lead to)."""
     return _check(ctx, load().tdmrg_overlap_op(ctx, opL, opR, Q1[0], Q1[1], _ptr(phi1), Q2[0], Q2[1], _ptr(phi2),
                                                _ptr(out)))
+
+
+def tdmrg_eig_stats(ctx, nsec, side=0):
+    """(sweeps, SM cycles) per sector (nsec sectors) of the last Jacobi seed of rho_eig on that side."""
+    sw = np.zeros(nsec, np.int32)
+    cy = np.zeros(nsec, np.int64)
+    _check(ctx, load().tdmrg_eig_stats(ctx, side, sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       cy.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return sw, cy
 
 
 def tdmrg_probe_wait(ctx, spins):
