@@ -166,6 +166,32 @@ int tdmrg_evolve(tdmrg_ctx* ctx, int n_up, int n_dn, const tdmrg_c64* phi_d, int
  * ESTATE, ENOMEM, ECUDA, ETIMEOUT. */
 int tdmrg_ground_state(tdmrg_ctx* ctx, int n_up, int n_dn, tdmrg_c64* psi_d, int nk, int restarts, double* energy);
 
+/* Batching of independent problems (several superblocks, e.g. the time evolutions of different jobs):
+ * tdmrg_direct_sum loads into ctx the direct sum of the superblocks of nsrc source contexts, each with
+ * its sector Q_k = (Q[2k], Q[2k+1]) (host): the sectors of source k are shifted apart (left n_up by
+ * 4096 k, the right sectors so that Q_k lands on the common sector Qsum = (4096 nsrc, 4096)), so no
+ * product of the sum pairs blocks of different sources, and source k's operator id becomes 2^20 k + id.
+ * The vector of ctx in Qsum is the concatenation of the sources' vectors in their sectors Q_k, in source
+ * order: seg_off (host, nsrc + 1, nullable) receives their offsets, Qsum (host, 2, nullable) the common
+ * sector.  One H psi of ctx is then one grouped product over all sources (Sec. IV).  Sources keep their
+ * own data (ctx holds copies); their quantum numbers must lie in 0..2047 and their coefficients be
+ * static.  Synchronises the streams.  Errors: EINVAL, ESTATE (a source without Hamiltonian), ESECTOR,
+ * ENOMEM, ECUDA. */
+int tdmrg_direct_sum(tdmrg_ctx* ctx, int nsrc, tdmrg_ctx* const* src, const int32_t* Q, int32_t* Qsum, int64_t* seg_off);
+
+/* tdmrg_evolve for nseg independent problems side by side in one vector of sector Q (e.g. a direct sum):
+ * segment s is elements [off_s, off_s + seg_len[s]) (host lengths, adding up to the sector size); each
+ * segment gets its own Lanczos recursion (norm, alpha, beta, breakdown, re-orthogonalisation), its own
+ * tridiagonal exponential and targets, exactly as tdmrg_evolve would give it alone up to the order of
+ * the FP64 reductions, while every H psi is one product over all segments.  targets_d[x] are full-length
+ * vectors (segment s of target x is the evolution of segment s of phi_d).  nseg is at most the number of
+ * co-resident blocks of the orthogonalisation (one per SM).  Errors: as tdmrg_evolve. */
+int tdmrg_evolve_segments(tdmrg_ctx* ctx, int n_up, int n_dn, const tdmrg_c64* phi_d, int nseg, const int64_t* seg_len,
+                          int n_v, const double* t_x, int nk, tdmrg_c64* const* targets_d);
+/* Per segment of the last tdmrg_evolve_segments with these (Q, nk, nseg): Krylov vectors used and the
+ * error estimate (host arrays of nseg, nullable).  Synchronises.  Errors: ESTATE, ECUDA, ETIMEOUT. */
+int tdmrg_evolve_segments_info(tdmrg_ctx* ctx, int n_up, int n_dn, int nk, int nseg, int* nk_used, double* err);
+
 /* Results of the last tdmrg_evolve: Krylov dimension used, a-posteriori error estimate
  * ||phi|| beta_n |[e^{-i T t_{n_v-1}}]_{n-1,0}| (Saad), and optionally alpha[0..n-1], beta[0..n-1]
  * (beta[j] couples v_j and v_{j+1}; beta[n-1] is the residual).  Synchronises the stream. */

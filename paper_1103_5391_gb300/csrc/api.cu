@@ -4,6 +4,8 @@
 #include <cstring>
 #include <new>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "tdmrg_bench.h"
 
@@ -79,6 +81,7 @@ void drop_krylov(tdmrg_ctx* c) {
         dev_free(c, k.flags, 4 * sizeof(int));
         dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
         dev_free(c, k.bar, 2 * sizeof(unsigned));
+        dev_free(c, k.segmem, k.segmem_bytes);
     }
     c->krylov.clear();
     c->last_krylov = nullptr;
@@ -422,6 +425,129 @@ int tdmrg_ground_state(tdmrg_ctx* c, int a, int b, tdmrg_c64* psi, int nk, int r
         return fail(c, TDMRG_EINVAL, "ground_state: bad argument (nk in 2..nk_max, restarts >= 1)");
     DeviceGuard g(c->opts.device);
     return ground_state(c, a, b, (cplx*)psi, nk, restarts, energy);
+}
+
+int tdmrg_evolve_segments(tdmrg_ctx* c, int a, int b, const tdmrg_c64* phi, int nseg, const int64_t* seg_len, int n_v,
+                          const double* t_x, int nk, tdmrg_c64* const* targets) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "evolve_segments: Hamiltonian not set");
+    if (!phi || !seg_len || !t_x || !targets || nseg < 1 || n_v < 1 || n_v > 16 || nk < 1 || nk > c->opts.nk_max)
+        return fail(c, TDMRG_EINVAL, "evolve_segments: bad argument (n_v in 1..16, nk in 1..nk_max)");
+    for (int x = 0; x < n_v; ++x)
+        if (!targets[x] || !(t_x[x] >= 0.0)) return fail(c, TDMRG_EINVAL, "evolve_segments: null target or negative time");
+    DeviceGuard g(c->opts.device);
+    return evolve_segments(c, a, b, (const cplx*)phi, nseg, seg_len, n_v, t_x, nk, (cplx* const*)targets);
+}
+
+int tdmrg_evolve_segments_info(tdmrg_ctx* c, int a, int b, int nk, int nseg, int* nk_used, double* err) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    DeviceGuard g(c->opts.device);
+    return segments_info(c, a, b, nk, nseg, nk_used, err);
+}
+
+// Direct sum of superblocks: the sectors of source k are moved apart (left n_up + 4096 k; right shifted so
+// that source k's sector Q_k lands on Qsum = (4096 nsrc, 4096)), so that the products of the sum never
+// pair blocks of different sources; operator ids become 2^20 k + id.
+int tdmrg_direct_sum(tdmrg_ctx* dst, int nsrc, tdmrg_ctx* const* src, const int32_t* Q, int32_t* Qsum, int64_t* seg_off) {
+    if (check_ctx(dst)) return TDMRG_EINVAL;
+    if (nsrc < 1 || nsrc > 512 || !src || !Q) return fail(dst, TDMRG_EINVAL, "direct_sum: bad argument (1..512 sources)");
+    constexpr int kShift = 4096, kIdStride = 1 << 20;
+    for (int k = 0; k < nsrc; ++k) {
+        const tdmrg_ctx* c = src[k];
+        if (!c || c == dst) return fail(dst, TDMRG_EINVAL, "direct_sum: null source or the destination itself");
+        if (!c->ham_set) return fail(dst, TDMRG_ESTATE, "direct_sum: a source has no Hamiltonian");
+        if (c->dcoef) return fail(dst, TDMRG_EINVAL, "direct_sum: a source reads its coefficients at run time");
+        if (c->opts.device != dst->opts.device) return fail(dst, TDMRG_EINVAL, "direct_sum: sources on another device");
+        if (Q[2 * k] < 0 || Q[2 * k] >= kShift / 2 || Q[2 * k + 1] < 0 || Q[2 * k + 1] >= kShift / 2)
+            return fail(dst, TDMRG_ESECTOR, "direct_sum: sector quantum numbers outside 0..2047");
+        for (int sd = 0; sd < 2; ++sd)
+            for (size_t q = 0; q < c->side[sd].dim.size(); ++q)
+                if (c->side[sd].nup[q] < 0 || c->side[sd].nup[q] >= kShift / 2 || c->side[sd].ndn[q] < 0 ||
+                    c->side[sd].ndn[q] >= kShift / 2)
+                    return fail(dst, TDMRG_ESECTOR, "direct_sum: block quantum numbers outside 0..2047");
+        for (const auto& kv : c->ops[0]) if (kv.first >= kIdStride) return fail(dst, TDMRG_EINVAL, "direct_sum: op id >= 2^20");
+        for (const auto& kv : c->ops[1]) if (kv.first >= kIdStride) return fail(dst, TDMRG_EINVAL, "direct_sum: op id >= 2^20");
+    }
+    const int Bu = kShift * nsrc, Bd = kShift;
+    auto shL = [&](int k) { return std::make_pair(kShift * k, 0); };
+    auto shR = [&](int k) { return std::make_pair(Bu - Q[2 * k] - kShift * k, Bd - Q[2 * k + 1]); };
+    // sector tables
+    std::vector<int32_t> lq, ld;
+    std::vector<std::pair<std::pair<int, int>, int>> rs;
+    for (int k = 0; k < nsrc; ++k) {
+        const Side& L = src[k]->side[0];
+        const Side& R = src[k]->side[1];
+        for (size_t q = 0; q < L.dim.size(); ++q) {
+            lq.push_back(L.nup[q] + shL(k).first); lq.push_back(L.ndn[q] + shL(k).second); ld.push_back(L.dim[q]);
+        }
+        for (size_t q = 0; q < R.dim.size(); ++q) rs.push_back({{R.nup[q] + shR(k).first, R.ndn[q] + shR(k).second}, R.dim[q]});
+    }
+    std::sort(rs.begin(), rs.end());
+    std::vector<int32_t> rq, rd;
+    for (auto& e : rs) { rq.push_back(e.first.first); rq.push_back(e.first.second); rd.push_back(e.second); }
+    int rc = tdmrg_set_block(dst, 0, (int)ld.size(), lq.data(), ld.data());
+    if (!rc) rc = tdmrg_set_block(dst, 1, (int)rd.size(), rq.data(), rd.data());
+    if (rc) return rc;
+    DeviceGuard g(dst->opts.device);
+    // operators: the blocks of every source operator, gathered from the source pool
+    for (int k = 0; k < nsrc && !rc; ++k) {
+        const tdmrg_ctx* c = src[k];
+        cudaStreamSynchronize(c->stream);
+        for (int sd = 0; sd < 2 && !rc; ++sd) {
+            const Side& S = c->side[sd];
+            const std::pair<int, int> sh = sd == 0 ? shL(k) : shR(k);
+            for (const auto& kv : c->ops[sd]) {
+                const BlockOp& op = kv.second;
+                std::vector<int32_t> bq;
+                int64_t tot = 0;
+                for (const auto& blk : op.blocks) {
+                    const int qo = std::get<0>(blk), qi = std::get<1>(blk);
+                    bq.insert(bq.end(), {S.nup[qo] + sh.first, S.ndn[qo] + sh.second, S.nup[qi] + sh.first, S.ndn[qi] + sh.second});
+                    tot += (int64_t)S.dim[qo] * S.dim[qi];
+                }
+                cplx* tmp = nullptr;
+                rc = dev_alloc(dst, (void**)&tmp, (size_t)std::max<int64_t>(tot, 1) * sizeof(cplx), "direct sum gather");
+                if (rc) break;
+                int64_t o = 0;
+                for (const auto& blk : op.blocks) {
+                    const int64_t nb = (int64_t)S.dim[std::get<0>(blk)] * S.dim[std::get<1>(blk)];
+                    if (!rc) rc = cuda_check(dst, cudaMemcpyAsync(tmp + o, c->pool + std::get<2>(blk), nb * sizeof(cplx),
+                                                                  cudaMemcpyDeviceToDevice, dst->stream), "direct sum gather");
+                    o += nb;
+                }
+                if (!rc) rc = tdmrg_set_op(dst, sd, kIdStride * k + kv.first, op.odd, (int)op.blocks.size(), bq.data(),
+                                           (const tdmrg_c64*)tmp, 1);
+                cudaStreamSynchronize(dst->stream);
+                dev_free(dst, tmp, (size_t)std::max<int64_t>(tot, 1) * sizeof(cplx));
+                if (rc) break;
+            }
+        }
+    }
+    if (rc) return rc;
+    // Hamiltonian: every source's terms with its operator ids
+    std::vector<Term> terms;
+    for (int k = 0; k < nsrc; ++k)
+        for (const Term& t : src[k]->ham) {
+            Term u = t;
+            u.opL = t.opL >= 0 ? kIdStride * k + t.opL : -1;
+            u.opR = t.opR >= 0 ? kIdStride * k + t.opR : -1;
+            u.conn = -1;
+            terms.push_back(u);
+        }
+    dst->ham = terms;
+    dst->ham_set = true;
+    dst->dcoef = nullptr;
+    dst->ham_version++;
+    drop_plans(dst);
+    if (Qsum) { Qsum[0] = Bu; Qsum[1] = Bd; }
+    int64_t off = 0;
+    for (int k = 0; k < nsrc; ++k) {
+        if (seg_off) seg_off[k] = off;
+        off += sector_size(src[k], Q[2 * k], Q[2 * k + 1]);
+    }
+    if (seg_off) seg_off[nsrc] = off;
+    if (sector_size(dst, Bu, Bd) != off) return fail(dst, TDMRG_ESECTOR, "direct_sum: the summed sector does not add up");
+    return TDMRG_OK;
 }
 
 int tdmrg_evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta) {

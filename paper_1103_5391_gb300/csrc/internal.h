@@ -244,6 +244,12 @@ struct KrylovWork {     // device workspace of tdmrg_evolve for one (Q, nk)
     cplx* coef = nullptr;       // [x][k] Krylov coefficients
     unsigned* bar = nullptr;    // grid barrier of the fused orthogonalisation
     int orth_grid = 0;
+    // segmented mode (independent problems side by side in one vector): per-segment tridiagonals, flags
+    // and coefficients, and the CTA partition of the vector, in one device allocation
+    int nseg = 0;
+    std::vector<int64_t> seg_len;
+    void* segmem = nullptr;
+    size_t segmem_bytes = 0;
 };
 
 // Workspace of the rho_L eigensolver (eig.cu), built once per left block.
@@ -374,6 +380,9 @@ int evolve(tdmrg_ctx* c, int n_up, int n_dn, const cplx* phi, int n_v, const dou
            cplx* const* targets);
 int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta);
 int ground_state(tdmrg_ctx* c, int n_up, int n_dn, cplx* psi, int nk, int restarts, double* energy);
+int evolve_segments(tdmrg_ctx* c, int n_up, int n_dn, const cplx* phi, int nseg, const int64_t* seg_len, int n_v,
+                    const double* t_x, int nk, cplx* const* targets);
+int segments_info(tdmrg_ctx* c, int n_up, int n_dn, int nk, int nseg, int* nk_used, double* err);
 cudaError_t launch_norm2(const cplx* x, int64_t n, double2* partials, int nblk, cudaStream_t s);
 cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* partials, int nblk,
                              cplx* out, int normalise, cudaStream_t s);

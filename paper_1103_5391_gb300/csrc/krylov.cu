@@ -12,6 +12,8 @@
 // a fixed summation order, so results do not depend on scheduling.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -113,6 +115,18 @@ __global__ void __launch_bounds__(NT) k_init_v0(const cplx* __restrict__ phi, in
 constexpr int OB = 256;   // threads per block of the fused kernel
 constexpr long kBarrierSpin = 1L << 24;
 
+// Segmented mode: the vector holds independent problems side by side (a direct sum of superblocks);
+// CTA b works on elements [lo_b, hi_b) of segment seg_b, and each segment has its own partial sums,
+// tridiagonal (kTriStride doubles), flags (kFlagStride ints) and coefficients (kCoefStride).
+constexpr int kTriStride = 128, kFlagStride = 4, kCoefStride = 16 * 32;
+struct SegTab {
+    const int* cta_seg;
+    const int64_t* cta_lo;
+    const int64_t* cta_hi;
+    const int* seg_cta0;   // first CTA of each segment; seg_cta0[nseg] = the grid
+    int nseg;
+};
+
 struct OrthArgs {
     const cplx* V;
     cplx* w;
@@ -125,6 +139,7 @@ struct OrthArgs {
     int* flags;
     unsigned* bar;     // [0] arrivals, [1] generation
     int* status;
+    SegTab seg;        // seg.nseg == 0: one problem over the whole vector
 };
 
 __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
@@ -199,12 +214,13 @@ __device__ double block_sum1(double x, double* sh) {
     return s;
 }
 
-// partials[k * gridDim + b] for k < nv  ->  every block's h[k] (same order everywhere)
-__device__ void sum_partials(const double2* __restrict__ part, int nv, double2* h) {
+// partials[k * gridDim + b] for k < nv and b in [b0, b1)  ->  every block's h[k] (same order everywhere)
+__device__ void sum_partials(const double2* __restrict__ part, int nv, double2* h, int b0 = 0, int b1 = -1) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (b1 < 0) b1 = (int)gridDim.x;
     for (int k = w; k < nv; k += OB / 32) {
         double2 s = make_double2(0.0, 0.0);
-        for (int b = l; b < (int)gridDim.x; b += 32) { s.x += part[(int64_t)k * gridDim.x + b].x; s.y += part[(int64_t)k * gridDim.x + b].y; }
+        for (int b = b0 + l; b < b1; b += 32) { s.x += part[(int64_t)k * gridDim.x + b].x; s.y += part[(int64_t)k * gridDim.x + b].y; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
@@ -264,44 +280,65 @@ __device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, i
     }
 }
 
-__global__ void __launch_bounds__(OB) k_lanczos_orth(OrthArgs a) {
+template <bool SEG>
+__global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
     pdl_enter();
-    if (a.j >= a.flags[0]) return;   // uniform: the flag only changes after the last barrier
+    // one problem: the whole grid stops together.  Segments: a stopped segment's blocks stay for the grid
+    // barriers and do nothing else.
+    int sg = 0, b0 = 0, b1 = (int)gridDim.x;
+    int64_t lo, hi;
+    if (SEG) {
+        sg = a.seg.cta_seg[blockIdx.x];
+        b0 = a.seg.seg_cta0[sg];
+        b1 = a.seg.seg_cta0[sg + 1];
+        lo = a.seg.cta_lo[blockIdx.x];
+        hi = a.seg.cta_hi[blockIdx.x];
+    } else {
+        const int64_t ch = (a.n + gridDim.x - 1) / gridDim.x;
+        lo = min(a.n, (int64_t)blockIdx.x * ch);
+        hi = min(a.n, lo + ch);
+    }
+    double* tri = a.tri + (SEG ? (int64_t)sg * kTriStride : 0);
+    int* flags = a.flags + (SEG ? sg * kFlagStride : 0);
+    const bool active = a.j < flags[0];   // uniform per segment: the flag only changes after the last barrier
+    if (!SEG && !active) return;
     __shared__ double sh[(OB / 32) * 16];
     __shared__ double2 red8[8];
     __shared__ double2 h[33];
-    const int64_t ch = (a.n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = min(a.n, (int64_t)blockIdx.x * ch), hi = min(a.n, lo + ch);
     // (A) first-pass dots
-    for (int k0 = 0; k0 < a.nv; k0 += 8) chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, nullptr, a.partA, sh, red8);
+    if (active)
+        for (int k0 = 0; k0 < a.nv; k0 += 8) chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, nullptr, a.partA, sh, red8);
     grid_barrier(a.bar, a.status);
     // (B) w' = w - sum h1_k v_k, second-pass dots, ||w'||^2
-    sum_partials(a.partA, a.nv, h);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.tri[T_ALPHA + a.j] = h[a.j].x;
     double nn = 0.0;
-    for (int k0 = 0; k0 < a.nv; k0 += 8) {
-        nn += chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, h, a.partB, sh, red8);
-        __syncthreads();   // h is read by every thread of the first group
+    if (active) {
+        sum_partials(a.partA, a.nv, h, b0, b1);
+        if (blockIdx.x == b0 && threadIdx.x == 0) tri[T_ALPHA + a.j] = h[a.j].x;
+        for (int k0 = 0; k0 < a.nv; k0 += 8) {
+            nn += chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, h, a.partB, sh, red8);
+            __syncthreads();   // h is read by every thread of the first group
+        }
+        nn = block_sum1(nn, sh);
+        if (threadIdx.x == 0) a.partB[(int64_t)a.nv * gridDim.x + blockIdx.x] = make_double2(nn, 0.0);
     }
-    nn = block_sum1(nn, sh);
-    if (threadIdx.x == 0) a.partB[(int64_t)a.nv * gridDim.x + blockIdx.x] = make_double2(nn, 0.0);
     grid_barrier(a.bar, a.status);
+    if (!active) return;
     // (C) beta, stop test, v_{j+1} = (w' - sum h2_k v_k) / beta
-    sum_partials(a.partB, a.nv + 1, h);
+    sum_partials(a.partB, a.nv + 1, h, b0, b1);
     double b2 = h[a.nv].x;
     for (int k = 0; k < a.nv; ++k) b2 -= h[k].x * h[k].x + h[k].y * h[k].y;
     const double beta = sqrt(fmax(b2, 0.0));
-    const double alpha = a.tri[T_ALPHA + a.j];
+    const double alpha = tri[T_ALPHA + a.j];
     const bool stop = (a.j == a.nk - 1) || (beta <= a.tol * fmax(1.0, fabs(alpha)));
     if (stop) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            a.tri[T_BETA + a.j] = beta;
-            a.tri[T_RESID] = beta;
-            a.flags[0] = a.j + 1;   // read by later kernels only (every block is past its check)
+        if (blockIdx.x == b0 && threadIdx.x == 0) {
+            tri[T_BETA + a.j] = beta;
+            tri[T_RESID] = beta;
+            flags[0] = a.j + 1;   // read by later kernels only (every block is past its check)
         }
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.tri[T_BETA + a.j] = beta;
+    if (blockIdx.x == b0 && threadIdx.x == 0) tri[T_BETA + a.j] = beta;
     const double inv = 1.0 / beta;
     cplx* vnext = const_cast<cplx*>(a.V) + (int64_t)(a.j + 1) * a.n;
     for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
@@ -338,6 +375,10 @@ __constant__ double kInvK[25] = {0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 
 __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, const int* __restrict__ flags,
                                                      Times times, int n_v, cplx* __restrict__ coef) {
     pdl_enter();
+    // one block per segment in segmented mode (a single block otherwise)
+    tri += (int64_t)blockIdx.x * kTriStride;
+    flags += blockIdx.x * kFlagStride;
+    coef += (int64_t)blockIdx.x * kCoefStride;
     __shared__ int order[16];
     const int l = threadIdx.x;
     const int n = flags[0];
@@ -506,6 +547,90 @@ cudaError_t launch_combine(const cplx* V, int64_t n, const int* flags, const cpl
     return cudaGetLastError();
 }
 
+// ---- segmented mode: the start vector's norm, v_0 and the targets per segment --------------------
+__global__ void __launch_bounds__(NT) k_norm2_seg(const cplx* __restrict__ x, SegTab tb, double2* __restrict__ part) {
+    pdl_enter();
+    const int64_t lo = tb.cta_lo[blockIdx.x], hi = tb.cta_hi[blockIdx.x];
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = x[i]; s += v.x * v.x + v.y * v.y; }
+    const double2 t = block_sum(make_double2(s, 0.0));
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_init_v0_seg(const cplx* __restrict__ phi, SegTab tb, const double2* __restrict__ part,
+                                                    cplx* __restrict__ v0, double* __restrict__ tri, int* __restrict__ flags,
+                                                    int nk) {
+    pdl_enter();
+    __shared__ double b0s;
+    const int sg = tb.cta_seg[blockIdx.x], c0 = tb.seg_cta0[sg], c1 = tb.seg_cta0[sg + 1];
+    if (threadIdx.x < 32) {   // the segment's partials in a fixed order
+        double t = 0.0;
+        for (int b = c0 + (int)threadIdx.x; b < c1; b += 32) t += part[b].x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) b0s = sqrt(t);
+    }
+    __syncthreads();
+    const double b0 = b0s, inv = b0 > 0.0 ? 1.0 / b0 : 0.0;
+    const int64_t lo = tb.cta_lo[blockIdx.x], hi = tb.cta_hi[blockIdx.x];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NT) { const double2 v = phi[i]; v0[i] = make_double2(v.x * inv, v.y * inv); }
+    if ((int)blockIdx.x == c0 && threadIdx.x == 0) {
+        tri[(int64_t)sg * kTriStride + T_BETA0] = b0;
+        tri[(int64_t)sg * kTriStride + T_RESID] = 0.0;
+        flags[sg * kFlagStride] = b0 > 0.0 ? nk : 0;
+    }
+}
+
+// targets[x] over each block's range with its segment's coefficients (one pass over V)
+template <int NX>
+__global__ void __launch_bounds__(256) k_combine_seg(const cplx* __restrict__ V, int64_t n, SegTab tb,
+                                                     const int* __restrict__ flags, const cplx* __restrict__ coef, int x0,
+                                                     TargetPtrs tg) {
+    pdl_enter();
+    __shared__ double2 cf[NX][32];
+    const int sg = tb.cta_seg[blockIdx.x];
+    const int nu = flags[sg * kFlagStride];
+    const cplx* cs = coef + (int64_t)sg * kCoefStride;
+    for (int e = threadIdx.x; e < NX * 32; e += blockDim.x) cf[e / 32][e % 32] = cs[(x0 + e / 32) * 32 + e % 32];
+    __syncthreads();
+    const int64_t lo = tb.cta_lo[blockIdx.x], hi = tb.cta_hi[blockIdx.x];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        double2 acc[NX];
+#pragma unroll
+        for (int x = 0; x < NX; ++x) acc[x] = make_double2(0.0, 0.0);
+        for (int k = 0; k < nu; ++k) {
+            const double2 v = V[(int64_t)k * n + i];
+#pragma unroll
+            for (int x = 0; x < NX; ++x) {
+                const double2 c = cf[x][k];
+                acc[x].x = fma(c.x, v.x, fma(-c.y, v.y, acc[x].x));
+                acc[x].y = fma(c.x, v.y, fma(c.y, v.x, acc[x].y));
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < NX; ++x) tg.p[x][i] = acc[x];
+    }
+}
+
+cudaError_t launch_combine_seg(const cplx* V, int64_t n, const SegTab& tb, int grid, const int* flags, const cplx* coef,
+                               int n_v, const TargetPtrs& tg, cudaStream_t s) {
+    for (int x0 = 0; x0 < n_v; x0 += 8) {
+        TargetPtrs t{};
+        for (int x = x0; x < n_v; ++x) t.p[x - x0] = tg.p[x];
+        switch (std::min(8, n_v - x0)) {
+            case 1: launch_pdl(k_combine_seg<1>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            case 2: launch_pdl(k_combine_seg<2>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            case 3: launch_pdl(k_combine_seg<3>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            case 4: launch_pdl(k_combine_seg<4>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            case 5: launch_pdl(k_combine_seg<5>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            case 6: launch_pdl(k_combine_seg<6>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            case 7: launch_pdl(k_combine_seg<7>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+            default: launch_pdl(k_combine_seg<8>, grid, 256, 0, s, V, n, tb, flags, coef, x0, t); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(NT) k_dot2(const cplx* __restrict__ x, const cplx* __restrict__ y, int64_t n,
                                               double2* __restrict__ part) {
     pdl_enter();
@@ -556,7 +681,7 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
     if (!rc) rc = cuda_check(c, cudaMemset(k.bar, 0, 2 * sizeof(unsigned)), "Krylov grid barrier");
     if (!rc) {   // co-resident grid of the fused orthogonalisation: at most one block per SM, at most NB
         int per_sm = 0;
-        rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_orth, OB, 0), "occupancy");
+        rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_orth_t<true>, OB, 0), "occupancy");
         k.orth_grid = std::max(1, std::min({c->num_sms * std::max(per_sm, 1), c->num_sms, NB}));
     }
     if (rc) {
@@ -624,7 +749,7 @@ int lanczos_build(tdmrg_ctx* c, int a, int b, const cplx* phi, int nk, KrylovWor
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t le = cudaLaunchKernelExC(&cfg, (const void*)k_lanczos_orth, params);
+        cudaError_t le = cudaLaunchKernelExC(&cfg, (const void*)k_lanczos_orth_t<false>, params);
         if (le != cudaSuccess) return cuda_check(c, le, "Lanczos orthogonalisation launch");
         c->launches += 1;
     }
@@ -672,6 +797,164 @@ int ground_state(tdmrg_ctx* c, int a, int b, cplx* psi, int nk, int restarts, do
     if (!rc) rc = check_device_status(c);
     if (!rc && energy) *energy = tri[T_EMIN];
     return rc;
+}
+
+// Device tables of the segmented mode: the CTA partition (each segment gets CTAs in proportion to its
+// length, at least one) and the per-segment Krylov state, allocated with the Krylov workspace.
+static int ensure_segments(tdmrg_ctx* c, KrylovWork* k, int nseg, const int64_t* seg_len, SegTab* tb, double** tri,
+                           int** flags, cplx** coef, int* grid) {
+    const int G = k->orth_grid;
+    if (nseg < 1 || nseg > G) return fail(c, TDMRG_EINVAL, "evolve_segments: more segments than co-resident blocks");
+    const bool same = k->nseg == nseg && std::equal(k->seg_len.begin(), k->seg_len.end(), seg_len) &&
+                      (int)k->seg_len.size() == nseg;
+    const size_t b_tri = (size_t)nseg * kTriStride * sizeof(double), b_fl = (size_t)nseg * kFlagStride * sizeof(int);
+    const size_t b_co = (size_t)nseg * kCoefStride * sizeof(cplx), b_cs = (size_t)G * sizeof(int);
+    const size_t b_lo = (size_t)G * sizeof(int64_t), b_c0 = (size_t)(nseg + 1) * sizeof(int);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t bytes = al(b_tri) + al(b_fl) + al(b_co) + al(b_cs) + 2 * al(b_lo) + al(b_c0);
+    unsigned char* m = (unsigned char*)k->segmem;
+    if (!same) {
+        // partition: CTAs in proportion to the lengths, at least one per segment
+        int64_t n = 0;
+        for (int s = 0; s < nseg; ++s) n += seg_len[s];
+        std::vector<int> cnt(nseg, 1);
+        int left = G - nseg;
+        for (int s = 0; s < nseg && n > 0; ++s) {
+            const int extra = (int)((double)left * (double)seg_len[s] / (double)n);
+            cnt[s] += extra;
+        }
+        int used = 0;
+        for (int s = 0; s < nseg; ++s) used += cnt[s];
+        for (int s = 0; used < G; s = (s + 1) % nseg) { ++cnt[s]; ++used; }
+        std::vector<int> cta_seg, c0(nseg + 1, 0);
+        std::vector<int64_t> lo, hi;
+        int64_t off = 0;
+        for (int s = 0; s < nseg; ++s) {
+            c0[s] = (int)cta_seg.size();
+            const int64_t ch = (seg_len[s] + cnt[s] - 1) / cnt[s];
+            for (int b = 0; b < cnt[s]; ++b) {
+                cta_seg.push_back(s);
+                lo.push_back(off + std::min(seg_len[s], (int64_t)b * ch));
+                hi.push_back(off + std::min(seg_len[s], (int64_t)(b + 1) * ch));
+            }
+            off += seg_len[s];
+        }
+        c0[nseg] = (int)cta_seg.size();
+        if (k->segmem_bytes < bytes) {
+            dev_free(c, k->segmem, k->segmem_bytes);
+            k->segmem = nullptr;
+            k->segmem_bytes = 0;
+            int rc = dev_alloc(c, &k->segmem, bytes, "Krylov segments");
+            if (rc) return rc;
+            k->segmem_bytes = bytes;
+        }
+        m = (unsigned char*)k->segmem;
+        std::vector<unsigned char> h(al(b_cs) + 2 * al(b_lo) + al(b_c0), 0);
+        memcpy(h.data(), cta_seg.data(), b_cs);
+        memcpy(h.data() + al(b_cs), lo.data(), b_lo);
+        memcpy(h.data() + al(b_cs) + al(b_lo), hi.data(), b_lo);
+        memcpy(h.data() + al(b_cs) + 2 * al(b_lo), c0.data(), b_c0);
+        int rc = cuda_check(c, cudaMemcpyAsync(m + al(b_tri) + al(b_fl) + al(b_co), h.data(), h.size(), cudaMemcpyHostToDevice,
+                                               c->stream), "Krylov segments");
+        if (!rc) rc = cuda_check(c, cudaMemsetAsync(m, 0, al(b_tri) + al(b_fl) + al(b_co), c->stream), "Krylov segments");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "Krylov segments");
+        if (rc) return rc;
+        k->nseg = nseg;
+        k->seg_len.assign(seg_len, seg_len + nseg);
+    }
+    *tri = (double*)m;
+    *flags = (int*)(m + al(b_tri));
+    *coef = (cplx*)(m + al(b_tri) + al(b_fl));
+    unsigned char* t = m + al(b_tri) + al(b_fl) + al(b_co);
+    tb->cta_seg = (const int*)t;
+    tb->cta_lo = (const int64_t*)(t + al(b_cs));
+    tb->cta_hi = (const int64_t*)(t + al(b_cs) + al(b_lo));
+    tb->seg_cta0 = (const int*)(t + al(b_cs) + 2 * al(b_lo));
+    tb->nseg = nseg;
+    *grid = G;
+    return TDMRG_OK;
+}
+
+// Independent Krylov advances side by side (Sec. II.A, Eq. lanczosevolution for each segment): one H psi
+// over the whole vector per Lanczos step (the superblock is a direct sum, so its products never mix
+// segments), orthogonalisation, tridiagonal exponentials and targets per segment.
+int evolve_segments(tdmrg_ctx* c, int a, int b, const cplx* phi, int nseg, const int64_t* seg_len, int n_v,
+                    const double* t_x, int nk, cplx* const* targets) {
+    const int64_t n = sector_size(c, a, b);
+    if (n == 0) return fail(c, TDMRG_ESECTOR, "evolve_segments: empty sector");
+    int64_t tot = 0;
+    for (int s = 0; s < nseg; ++s) {
+        if (seg_len[s] < 1) return fail(c, TDMRG_EINVAL, "evolve_segments: empty segment");
+        tot += seg_len[s];
+    }
+    if (tot != n) return fail(c, TDMRG_EINVAL, "evolve_segments: the segment lengths do not add up to the sector size");
+    Plan* p = nullptr;
+    int rc = get_ham_plan(c, a, b, &p);
+    if (rc) return rc;
+    KrylovWork* k = nullptr;
+    rc = ensure_work(c, a, b, nk, n, &k);
+    if (rc) return rc;
+    SegTab tb{};
+    double* tri = nullptr;
+    int* flags = nullptr;
+    cplx* coef = nullptr;
+    int G = 0;
+    rc = ensure_segments(c, k, nseg, seg_len, &tb, &tri, &flags, &coef, &G);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    launch_pdl(k_norm2_seg, G, NT, 0, s, phi, tb, k->partA);
+    launch_pdl(k_init_v0_seg, G, NT, 0, s, phi, tb, k->partA, k->V, tri, flags, nk);
+    c->launches += 2;
+    for (int j = 0; j < nk; ++j) {
+        cplx* vj = k->V + (int64_t)j * n;
+        rc = run_plan(c, *p, vj, k->w, nullptr, 0);   // every segment's product (a stopped one's is ignored)
+        if (rc) return rc;
+        OrthArgs oa{k->V, k->w, n, j + 1, j, nk, c->opts.breakdown_tol, k->partA, k->partB, tri, flags, k->bar,
+                    c->dstatus, tb};
+        void* params[] = {&oa};
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(G);
+        cfg.blockDim = dim3(OB);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t le = cudaLaunchKernelExC(&cfg, (const void*)k_lanczos_orth_t<true>, params);
+        if (le != cudaSuccess) return cuda_check(c, le, "segmented Lanczos launch");
+        c->launches += 1;
+    }
+    Times tt{};
+    for (int x = 0; x < n_v; ++x) tt.t[x] = t_x[x];
+    launch_pdl(k_tridiag_exp, nseg, 32, 0, s, tri, flags, tt, n_v, coef);
+    TargetPtrs tg{};
+    for (int x = 0; x < n_v; ++x) tg.p[x] = targets[x];
+    launch_combine_seg(k->V, n, tb, G, flags, coef, n_v, tg, s);
+    c->launches += 1 + (n_v + 7) / 8;
+    return cuda_check(c, cudaGetLastError(), "evolve_segments launch");
+}
+
+// Krylov dimension used and error estimate of each segment of the last evolve_segments on (Q, nk).
+int segments_info(tdmrg_ctx* c, int a, int b, int nk, int nseg, int* nk_used, double* err) {
+    auto it = c->krylov.find(std::make_pair(a * 4096 + b, nk));
+    if (it == c->krylov.end() || it->second.nseg != nseg || !it->second.segmem)
+        return fail(c, TDMRG_ESTATE, "evolve_segments_info: no segmented evolve with these arguments");
+    std::vector<double> tri((size_t)nseg * kTriStride);
+    std::vector<int> fl((size_t)nseg * kFlagStride);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const unsigned char* m = (const unsigned char*)it->second.segmem;
+    int rc = cuda_check(c, cudaMemcpyAsync(tri.data(), m, tri.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "info");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(fl.data(), m + al(tri.size() * sizeof(double)), fl.size() * sizeof(int),
+                                                cudaMemcpyDeviceToHost, c->stream), "info");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "info");
+    if (!rc) rc = check_device_status(c);
+    if (rc) return rc;
+    for (int s = 0; s < nseg; ++s) {
+        if (nk_used) nk_used[s] = fl[(size_t)s * kFlagStride];
+        if (err) err[s] = tri[(size_t)s * kTriStride + T_ERR];
+    }
+    return TDMRG_OK;
 }
 
 int evolve_info(tdmrg_ctx* c, int* nk_used, double* err, double* alpha, double* beta) {

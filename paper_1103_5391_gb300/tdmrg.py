@@ -19,7 +19,7 @@ TDMRG_FP64, TDMRG_OZAKI_BF16 = 0, 1
 EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
-    "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_tst_weights",
+    "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_direct_sum", "tdmrg_evolve_segments", "tdmrg_evolve_segments_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats",
@@ -78,6 +78,9 @@ def load(path=LIB_PATH):
         "tdmrg_evolve": (I, [P, I, I, P, I, PD, I, ctypes.POINTER(P)]),
         "tdmrg_evolve_info": (I, [P, ctypes.POINTER(I), PD, PD, PD]),
         "tdmrg_ground_state": (I, [P, I, I, P, I, I, PD]),
+        "tdmrg_direct_sum": (I, [P, I, P, PI32, PI32, PI64]),
+        "tdmrg_evolve_segments": (I, [P, I, I, P, I, PI64, I, PD, I, P]),
+        "tdmrg_evolve_segments_info": (I, [P, I, I, I, I, ctypes.POINTER(I), PD]),
         "tdmrg_tst_weights": (I, [I, PD, PD]),
         "tdmrg_rho_size": (I, [P, PI64, PI64]),
         "tdmrg_density_matrix": (I, [P, I, PI32, ctypes.POINTER(P), PD, P]),
@@ -248,6 +251,34 @@ def tdmrg_ground_state(ctx, Q, psi, nk=16, restarts=20):
     e = ctypes.c_double()
     _check(ctx, load().tdmrg_ground_state(ctx, Q[0], Q[1], _ptr(psi), nk, restarts, ctypes.byref(e)))
     return e.value
+
+
+def tdmrg_direct_sum(ctx, srcs, Qs):
+    """Loads the direct sum of the sources' superblocks into ctx; returns (Qsum, segment offsets)."""
+    arr = (ctypes.c_void_p * len(srcs))(*[x.value if hasattr(x, "value") else x for x in srcs])
+    q, qp = _i32(np.asarray(Qs).reshape(-1))
+    qs = np.zeros(2, np.int32)
+    off = np.zeros(len(srcs) + 1, np.int64)
+    _check(ctx, load().tdmrg_direct_sum(ctx, len(srcs), arr, qp, qs.ctypes.data_as(_PI32),
+                                        off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return (int(qs[0]), int(qs[1])), [int(x) for x in off]
+
+
+def tdmrg_evolve_segments(ctx, Q, phi, seg_len, times, nk, targets):
+    t = np.ascontiguousarray(np.asarray(times, dtype=np.float64))
+    sl = np.ascontiguousarray(np.asarray(seg_len, dtype=np.int64))
+    arr = (ctypes.c_void_p * len(targets))(*[_ptr(x) for x in targets])
+    return _check(ctx, load().tdmrg_evolve_segments(ctx, Q[0], Q[1], _ptr(phi), len(sl),
+                                                    sl.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(t),
+                                                    t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nk, arr))
+
+
+def tdmrg_evolve_segments_info(ctx, Q, nk, nseg):
+    n = np.zeros(nseg, np.int32)
+    e = np.zeros(nseg, np.float64)
+    _check(ctx, load().tdmrg_evolve_segments_info(ctx, Q[0], Q[1], nk, nseg, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                  e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return n, e
 
 
 def tdmrg_evolve_info(ctx, nk_max=32):
