@@ -107,6 +107,7 @@ def parse():
     ap.add_argument("--config", choices=sorted(CONFIGS), default="C2",
                     help="workload of the headline line (C2 by default; C3 and C4 are also measured beside C2)")
     ap.add_argument("--no-other-configs", action="store_true", help="measure the headline workload only")
+    ap.add_argument("--batch-jobs", type=int, default=24, help="jobs of the batched-mix measurement (0: skip)")
     ap.add_argument("--oracle-rate", metavar="CONFIG", default=None,
                     help="(internal) time the oracle's step on CONFIG in this process and print one JSON line")
     ap.add_argument("--prec", choices=["ozaki", "fp64"], default="ozaki")
@@ -578,6 +579,121 @@ def measure_config(args, torch, T, problem, key, dev, stream, flush, barrier, st
     return res
 
 
+def measure_batched(args, torch, T, problem, dev, stream, flush, barrier, njobs, steps=5, warmup=2):
+    """Aggregate Krylov steps/s of a mix of independent jobs (chains and two-leg ladders, L in [16, 48],
+    m log-uniform in [128, 512], U in {2, 4, 8}; seeded): a full time step per job (Krylov advance, rho_L
+    of the ground state and the targets, its eigendecomposition, two observables), (a) each job on its own
+    stream, (b) the advances of all jobs as one segmented advance over their direct sum (one grouped
+    product per Lanczos step for every job), the rest per job on its stream."""
+    from workloads import sectors as S
+    prec = T.TDMRG_OZAKI_BF16 if args.prec == "ozaki" else T.TDMRG_FP64
+    rng = np.random.default_rng(1103)
+    jobs = []
+    for k in range(njobs):
+        L = int(rng.choice([16, 24, 32, 40, 48]))
+        m = int(np.exp(rng.uniform(np.log(128), np.log(512))))
+        nb = 1 if rng.random() < 0.7 else 2
+        ss = S.make_synthetic(L, m, float(rng.choice([2.0, 4.0, 8.0])), nbonds=nb, seed=2000 + k)
+        ctx = T.tdmrg_create(device=dev.index, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
+        problem.load_synthetic(ctx, ss)
+        jobs.append(Runner(T, problem, ctx, ss, dev, stream, WL))
+    nv, nk, times = WL["n_v"], WL["nk"], jobs[0].times
+    streams = [torch.cuda.Stream(device=dev) for _ in jobs]
+
+    def tail(r, st, targets):   # rho_L, its eigendecomposition and the observables of one job on its stream
+        T.tdmrg_set_stream(r.ctx, st.cuda_stream)
+        T.tdmrg_density_matrix(r.ctx, [(r.Q0, r.psi_gs)] + [(r.Q1, t) for t in targets], [r.wgs] + r.w, r.rho)
+        T.tdmrg_rho_eig(r.ctx, r.rho, r.evals, r.evecs)
+        T.tdmrg_expect(r.ctx, problem.OP_N, -1, r.Q1, targets[-1], r.obs[0:1])
+        T.tdmrg_expect(r.ctx, -1, problem.OP_N, r.Q1, targets[-1], r.obs[1:2])
+        T.tdmrg_set_stream(r.ctx, stream.cuda_stream)
+
+    def step_streams():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for r, st in zip(jobs, streams):
+            st.wait_event(ev)
+            T.tdmrg_set_stream(r.ctx, st.cuda_stream)
+            T.tdmrg_evolve(r.ctx, r.Q1, r.phi, r.times, nk, r.targets)
+            tail(r, st, r.targets)
+        for st in streams:
+            stream.wait_stream(st)
+
+    big = T.tdmrg_create(device=dev.index, stream=stream.cuda_stream, prec=prec, ozaki_slices=args.slices)
+    Qs, off = T.tdmrg_direct_sum(big, [r.ctx for r in jobs], [r.Q1 for r in jobs])
+    bphi = torch.cat([r.phi0 for r in jobs])
+    bphi0 = bphi.clone()
+    btg = [torch.zeros_like(bphi) for _ in range(nv - 1)] + [bphi]   # advance in place, like the single job
+    seg = [off[k + 1] - off[k] for k in range(njobs)]
+
+    Q0s = (Qs[0] - 1, Qs[1])   # the ground states' sector of the sum (every job's excitation is c^dag_up)
+    bpsi = torch.cat([r.psi_gs for r in jobs])
+    nr, ne = T.tdmrg_rho_size(big)
+    brho = torch.zeros(nr, dtype=torch.complex128, device=dev)
+    bev = torch.zeros(ne, dtype=torch.float64, device=dev)
+    bU = torch.zeros_like(brho)
+
+    def step_batched():
+        # one segmented advance, one grouped rho_L (every job normalised apart) and one eigendecomposition over
+        # every job's sectors; the observables per job on its own stream beside the eigendecomposition
+        T.tdmrg_evolve_segments(big, Qs, bphi, seg, times, nk, btg)
+        T.tdmrg_density_matrix(big, [(Q0s, bpsi)] + [(Qs, t) for t in btg], [jobs[0].wgs] + jobs[0].w, brho)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for k, (r, st) in enumerate(zip(jobs, streams)):
+            st.wait_event(ev)
+            T.tdmrg_set_stream(r.ctx, st.cuda_stream)
+            last = btg[-1][off[k]: off[k + 1]]
+            T.tdmrg_expect(r.ctx, problem.OP_N, -1, r.Q1, last, r.obs[0:1])
+            T.tdmrg_expect(r.ctx, -1, problem.OP_N, r.Q1, last, r.obs[1:2])
+            T.tdmrg_set_stream(r.ctx, stream.cuda_stream)
+        T.tdmrg_rho_eig(big, brho, bev, bU)
+        for st in streams:
+            stream.wait_stream(st)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            barrier()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    for r in jobs:
+        r.reset()
+    t_streams = timed(step_streams)
+    bphi.copy_(bphi0)
+    t_batch = timed(step_batched)
+    # the same first step both ways: every job's targets agree
+    for r in jobs:
+        r.reset()
+    bphi.copy_(bphi0)
+    step_streams()
+    step_batched()
+    barrier()
+    diff = max(float((btg[x][off[k]: off[k + 1]] - jobs[k].targets[x]).abs().max() /
+                     jobs[k].targets[x].abs().max()) for k in range(njobs) for x in range(nv))
+    ev_diff = float((bev - torch.cat([r.evals for r in jobs])).abs().max())
+    T.tdmrg_destroy(big)
+    for r in jobs:
+        T.tdmrg_destroy(r.ctx)
+    return {"jobs": njobs, "D_total": int(off[-1]), "unit": UNIT,
+            "value": njobs * nk / (t_batch * 1e-3), "ms_per_step": t_batch,
+            "value_streams": njobs * nk / (t_streams * 1e-3), "ms_per_step_streams": t_streams,
+            "speedup_vs_streams": t_streams / t_batch, "max_rel_diff_vs_streams": diff,
+            "max_eigenvalue_diff_vs_streams": ev_diff,
+            "mode": "the jobs' superblocks as one direct sum: one segmented Krylov advance (one grouped product "
+                    "per Lanczos step for every job), one grouped rho_L and one eigendecomposition over every "
+                    "job's sectors, observables per job; compared with every job's whole step on its own stream"}
+
+
 def roofline_of(res, mixed, peaks, peak_src, dmma_peak, dfma_peak, traffic=None, traffic_note=None):
     """Roofline of H psi: algorithmic FP64-equivalent flops (cheaper association per term, 8 per complex
     MAC) per H psi over its measured time, against the measured bf16 dense peak (tensor path) or the
@@ -667,6 +783,10 @@ def run_ours(args):
             r2.pop("step_ms")
             others[k2] = r2
 
+    batched = None
+    if rank == 0 and args.batch_jobs > 0:
+        batched = measure_batched(args, torch, T, problem, dev, stream, flush, barrier, args.batch_jobs)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(workload(wl), key)
@@ -691,6 +811,7 @@ def run_ours(args):
             "step_mode": "CUDA graph replay of one time step (captured from the direct C-ABI calls; the observables on a second stream beside the eigendecomposition)",
             "clocks": res.get("clocks"),
             "other_configs": others or None,
+            "batched_jobs": batched,
             "precision_note": "the tensor path is Ozaki integer slicing (exact bf16 slice products, int64 "
                               "recombination); split-FP32 / 3xTF32 and BF16x3 with FP32 accumulation are not "
                               "built: their FP32 accumulation bounds the error near 1e-7, above the 1e-8 target",

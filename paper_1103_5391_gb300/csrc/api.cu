@@ -203,6 +203,7 @@ int tdmrg_destroy(tdmrg_ctx* c) {
     dev_free(c, c->scratch, c->scratch_cap * sizeof(cplx));
     dev_free(c, c->tmp, c->tmp_cap * sizeof(cplx));
     dev_free(c, c->red, 2 * 64 * kRedBlocks * sizeof(double2));
+    dev_free(c, c->dsum_dscale, c->dsum_dscale_bytes);
     dev_free(c, c->dscale, 64 * sizeof(double));
     dev_free(c, c->dstatus, sizeof(int));
     dev_free(c, c->trunc_tables, c->trunc_tables_bytes);
@@ -252,6 +253,9 @@ int tdmrg_set_block(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const i
     release_eig(c, side);
     c->side[side] = s;
     c->ops[side].clear();
+    c->dsum_src[0].clear();
+    c->dsum_src[1].clear();
+    c->dsum_nsrc = 0;
     c->ham_set = false;
     c->ham.clear();
     drop_plans(c);
@@ -539,6 +543,16 @@ int tdmrg_direct_sum(tdmrg_ctx* dst, int nsrc, tdmrg_ctx* const* src, const int3
     dst->dcoef = nullptr;
     dst->ham_version++;
     drop_plans(dst);
+    // source of every sector (left sectors come in source order; right ones were sorted)
+    dst->dsum_src[0].clear();
+    for (int k = 0; k < nsrc; ++k) dst->dsum_src[0].insert(dst->dsum_src[0].end(), src[k]->side[0].dim.size(), k);
+    dst->dsum_src[1].assign(dst->side[1].dim.size(), -1);
+    for (int k = 0; k < nsrc; ++k) {
+        const Side& R = src[k]->side[1];
+        for (size_t q = 0; q < R.dim.size(); ++q)
+            dst->dsum_src[1][dst->side[1].find(R.nup[q] + shR(k).first, R.ndn[q] + shR(k).second)] = k;
+    }
+    dst->dsum_nsrc = nsrc;
     if (Qsum) { Qsum[0] = Bu; Qsum[1] = Bd; }
     int64_t off = 0;
     for (int k = 0; k < nsrc; ++k) {

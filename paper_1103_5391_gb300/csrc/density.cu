@@ -40,28 +40,90 @@ __global__ void k_real_part(cplx* __restrict__ rho, int64_t n) {
         rho[i].y = 0.0;
 }
 
+// Direct sum of superblocks: each target is normalised per source, dscale[l * nsrc + k] = w_l / ||psi_l^(k)||^2
+// with psi_l^(k) the elements of source k (one block per (target, source), fixed-order block sum).
+struct SegNorm { const cplx* x; int64_t lo, hi; int l, k; };
+__global__ void __launch_bounds__(256) k_seg_weight(const SegNorm* __restrict__ segs, Weights ws, int nsrc,
+                                                    double* __restrict__ dscale) {
+    pdl_enter();
+    __shared__ double sh[8];
+    const SegNorm sg = segs[blockIdx.x];
+    double s = 0.0;
+    for (int64_t i = sg.lo + threadIdx.x; i < sg.hi; i += 256) { const double2 v = sg.x[i]; s += v.x * v.x + v.y * v.y; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += sh[k];
+        dscale[sg.l * nsrc + sg.k] = t > 0.0 ? ws.w[sg.l] / t : 0.0;
+    }
+}
+
 }  // namespace
 
 int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho) {
     const Side& L = c->side[0];
     const Side& R = c->side[1];
     cudaStream_t s = c->stream;
-    // norms of the targets -> dscale[l] = w_l / ||psi_l||^2
-    std::vector<int64_t> nl(nt);
-    for (int l = 0; l < nt; ++l) {
-        nl[l] = sector_size(c, Q[2 * l], Q[2 * l + 1]);
-        if (nl[l] == 0) return fail(c, TDMRG_ESECTOR, "density_matrix: target in an empty sector");
-        cudaError_t e = launch_norm2(psi[l], nl[l], c->red + (int64_t)l * NB, NB, s);
-        c->launches++;
-        if (e != cudaSuccess) return cuda_check(c, e, "density_matrix norms");
-    }
     Weights wl{};
     for (int l = 0; l < nt; ++l) wl.w[l] = w[l];
-    launch_pdl(k_weight_scale, 1, 32 * 12, 0, s, c->red, nt, c->dscale, wl);
-    c->launches++;
+    const int nsrc = c->dsum_nsrc;   // > 0: a direct sum, normalised per source
+    double* dscale = c->dscale;
+    if (nsrc > 0) {
+        const size_t need = (size_t)nt * nsrc * sizeof(double);
+        if (c->dsum_dscale_bytes < need) {
+            dev_free(c, c->dsum_dscale, c->dsum_dscale_bytes);
+            c->dsum_dscale = nullptr;
+            c->dsum_dscale_bytes = 0;
+            int rc = dev_alloc(c, (void**)&c->dsum_dscale, need, "direct sum scales");
+            if (rc) return rc;
+            c->dsum_dscale_bytes = need;
+        }
+        dscale = c->dsum_dscale;
+        std::vector<SegNorm> segs;
+        for (int l = 0; l < nt; ++l) {   // pairs come by left sector, and the left sectors by source
+            std::vector<int64_t> lo(nsrc, -1), hi(nsrc, -1);
+            int64_t off = 0;
+            for (size_t qi = 0; qi < L.dim.size(); ++qi) {
+                const int ri = R.find(Q[2 * l] - L.nup[qi], Q[2 * l + 1] - L.ndn[qi]);
+                if (ri < 0) continue;
+                const int k = c->dsum_src[0][qi];
+                if (lo[k] < 0) lo[k] = off;
+                off += (int64_t)L.dim[qi] * R.dim[ri];
+                hi[k] = off;
+            }
+            if (off == 0) return fail(c, TDMRG_ESECTOR, "density_matrix: target in an empty sector");
+            for (int k = 0; k < nsrc; ++k)
+                segs.push_back({psi[l], lo[k] < 0 ? 0 : lo[k], lo[k] < 0 ? 0 : hi[k], l, k});
+        }
+        SegNorm* d = nullptr;
+        int rc = dev_alloc(c, (void**)&d, segs.size() * sizeof(SegNorm), "direct sum norms");
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(d, segs.data(), segs.size() * sizeof(SegNorm), cudaMemcpyHostToDevice, s),
+                                 "direct sum norms");
+        if (!rc) rc = cuda_check(c, launch_pdl(k_seg_weight, (int)segs.size(), 256, 0, s, (const SegNorm*)d, wl, nsrc, dscale),
+                                 "direct sum norms");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "direct sum norms");
+        dev_free(c, d, segs.size() * sizeof(SegNorm));
+        c->launches++;
+        if (rc) return rc;
+    } else {
+        // norms of the targets -> dscale[l] = w_l / ||psi_l||^2
+        for (int l = 0; l < nt; ++l) {
+            const int64_t nl = sector_size(c, Q[2 * l], Q[2 * l + 1]);
+            if (nl == 0) return fail(c, TDMRG_ESECTOR, "density_matrix: target in an empty sector");
+            cudaError_t e = launch_norm2(psi[l], nl, c->red + (int64_t)l * NB, NB, s);
+            c->launches++;
+            if (e != cudaSuccess) return cuda_check(c, e, "density_matrix norms");
+        }
+        launch_pdl(k_weight_scale, 1, 32 * 12, 0, s, c->red, nt, c->dscale, wl);
+        c->launches++;
+    }
     // task list: one task per sector of the side, compiled once per (side, set of target sectors)
     std::vector<int> key(Q, Q + 2 * nt);
     key.push_back(side);
+    key.push_back(nsrc);
     auto it = c->rho_plans.find(key);
     if (it == c->rho_plans.end() && side == 1) {
         std::unique_ptr<TaskList> tl(new TaskList());
@@ -74,7 +136,8 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
                 Seg sg{};
                 sg.a_off = po; sg.a_buf = (int8_t)(BUF_EXTRA0 + l); sg.lda = R.dim[ri]; sg.opa = 1;   // Psi^T
                 sg.b_off = po; sg.b_buf = (int8_t)(BUF_EXTRA0 + l); sg.ldb = R.dim[ri]; sg.opb = OPB_CN;
-                sg.K = L.dim[qi]; sg.scale = make_double2(1.0, 0.0); sg.dscale = l;
+                sg.K = L.dim[qi]; sg.scale = make_double2(1.0, 0.0);
+                sg.dscale = nsrc > 0 ? l * nsrc + c->dsum_src[0][qi] : l;
                 segs[ri].push_back(sg);
                 po += (int64_t)L.dim[qi] * R.dim[ri];
             }
@@ -114,7 +177,8 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
                 Seg sg{};
                 sg.a_off = po; sg.a_buf = (int8_t)(BUF_EXTRA0 + l); sg.lda = R.dim[ri];
                 sg.b_off = po; sg.b_buf = (int8_t)(BUF_EXTRA0 + l); sg.ldb = R.dim[ri]; sg.opb = OPB_C;
-                sg.K = R.dim[ri]; sg.scale = make_double2(1.0, 0.0); sg.dscale = l;
+                sg.K = R.dim[ri]; sg.scale = make_double2(1.0, 0.0);
+                sg.dscale = nsrc > 0 ? l * nsrc + c->dsum_src[0][qi] : l;
                 tl->segs.push_back(sg);
             }
             tk.seg_end = (int)tl->segs.size();
@@ -133,7 +197,7 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
     a.bufs[BUF_OPS] = c->pool;
     a.bufs[BUF_OUT] = rho;
     for (int l = 0; l < nt; ++l) a.bufs[BUF_EXTRA0 + l] = const_cast<cplx*>(psi[l]);
-    a.dscale = c->dscale;
+    a.dscale = dscale;
     cudaError_t e = launch_gemm_f64(a, s, nullptr, 0);
     c->launches++;
     if (e == cudaSuccess && c->real_basis) {

@@ -310,6 +310,12 @@ struct tdmrg_ctx {
     tdmrg::KrylovWork* last_krylov = nullptr;
     // reduction / misc device buffers
     double2* red = nullptr;        // partials for norms and dots
+    // direct sum of superblocks (tdmrg_direct_sum): source of every left / right sector (empty otherwise),
+    // and the per-(target, source) scales of the density matrix
+    std::vector<int> dsum_src[2];
+    int dsum_nsrc = 0;
+    double* dsum_dscale = nullptr;
+    size_t dsum_dscale_bytes = 0;
     double* dscale = nullptr;      // device real scales (rho weights)
     tdmrg::cplx* tmp = nullptr;    // apply_op temporary for expect
     int64_t tmp_cap = 0;

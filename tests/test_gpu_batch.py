@@ -121,3 +121,46 @@ def test_inactive_segment(lib):
         lib.tdmrg_destroy(big)
         for _, c, _ in all_jobs:
             lib.tdmrg_destroy(c)
+
+
+def test_direct_sum_rho_and_eig(lib):
+    """rho_L of the direct sum (ground states in the sum's sector Q0, targets in Q1, weights of Sec. II.C,
+    every target normalised per job) = every job's own rho_L, packed in job order (1e-14); the
+    eigendecomposition over all jobs' sectors in one call = each job's (eigenvalues 1e-13)."""
+    torch = torch_cuda()
+    jobs = _jobs(lib, lib.TDMRG_FP64)
+    big = new_ctx()
+    try:
+        Qsum, off = lib.tdmrg_direct_sum(big, [c for _, c, _ in jobs], [ss.Q1 for ss, _, _ in jobs])
+        Q0sum = (Qsum[0] - 1, Qsum[1])
+        rng = np.random.default_rng(4)
+        psis, tgts = [], []
+        for ss, ctx, p in jobs:
+            psis.append(torch.as_tensor(ss.psi_gs).cuda())
+            tgts.append([p] + [p * complex(rng.standard_normal(), rng.standard_normal()) +
+                               torch.roll(p, x + 1) for x in range(3)])
+        wgs, w = lib.tdmrg_tst_weights(4)
+        big_states = [(Q0sum, torch.cat(psis))] + [(Qsum, torch.cat([t[x] for t in tgts])) for x in range(4)]
+        assert lib.tdmrg_sector_size(big, Q0sum) == sum(int(q.numel()) for q in psis)
+        nr, ne = lib.tdmrg_rho_size(big)
+        rho = torch.zeros(nr, dtype=torch.complex128, device="cuda")
+        lib.tdmrg_density_matrix(big, big_states, [wgs] + w, rho)
+        ev = torch.zeros(ne, dtype=torch.float64, device="cuda")
+        U = torch.zeros_like(rho)
+        lib.tdmrg_rho_eig(big, rho, ev, U)
+        ro = eo = 0
+        for (ss, ctx, p), q, t in zip(jobs, psis, tgts):
+            nrk, nek = lib.tdmrg_rho_size(ctx)
+            rk = torch.zeros(nrk, dtype=torch.complex128, device="cuda")
+            lib.tdmrg_density_matrix(ctx, [(ss.Q0, q)] + [(ss.Q1, x) for x in t], [wgs] + w, rk)
+            assert float((rho[ro: ro + nrk] - rk).abs().max()) < 1e-14
+            evk = torch.zeros(nek, dtype=torch.float64, device="cuda")
+            lib.tdmrg_rho_eig(ctx, rk, evk, torch.zeros_like(rk))
+            assert float((ev[eo: eo + nek] - evk).abs().max()) < 1e-13
+            ro += nrk
+            eo += nek
+        assert ro == nr and eo == ne
+    finally:
+        lib.tdmrg_destroy(big)
+        for _, c, _ in jobs:
+            lib.tdmrg_destroy(c)
