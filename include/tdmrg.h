@@ -374,7 +374,8 @@ int tdmrg_correlation(tdmrg_ctx* ctx, int nL, const int32_t* opL, int nR, const 
  * and fewer than max_active run; every running job owns a stream, so the steps of different jobs
  * overlap on the device; a job's first step runs directly and the following steps replay a CUDA
  * graph captured from it.  Results are bit-for-bit those of the same job run alone (every kernel is
- * deterministic and a job's work never reads another job's memory). */
+ * deterministic and a job's work never reads another job's memory), unless batching groups jobs
+ * (tdmrg_server_set_batching). */
 typedef struct tdmrg_server tdmrg_server;
 
 enum tdmrg_job_status { TDMRG_JOB_QUEUED = 0, TDMRG_JOB_RUNNING = 1, TDMRG_JOB_DONE = 2, TDMRG_JOB_CANCELLED = 3,
@@ -395,6 +396,18 @@ typedef struct {
 /* Create a server on `device`: hbm_budget bytes for the footprint of running jobs (0 = no limit),
  * at most max_active jobs at once.  Starts the server thread.  Errors: EINVAL, ECUDA. */
 int tdmrg_server_create(tdmrg_server** out, int device, size_t hbm_budget, int max_active);
+/* Batching of admitted jobs (north star pattern 2 across jobs): with max_group > 1, the queued jobs that
+ * can share a time step (same precision, tau, n_v, n_K, steps and excitation sector shift, static
+ * coefficients, distinct contexts) are admitted together, up to max_group, and run as one group on the
+ * direct sum of their superblocks (tdmrg_direct_sum): per time step one segmented Krylov advance with
+ * one grouped product per Lanczos step for all members, one grouped rho_L and one eigendecomposition
+ * over all members' sectors, then each member's observables.  Members finish together; a member's
+ * results equal the job alone up to the order of the FP64 reductions.  A job at the front of the queue
+ * without a partner waits up to window_us microseconds for one (while slots are free) before it runs
+ * alone.  max_group = 1 (the default) runs every job on its own stream.  Errors: EINVAL. */
+int tdmrg_server_set_batching(tdmrg_server* srv, int max_group, int window_us);
+/* Groups formed so far and the jobs they ran. */
+int tdmrg_server_batch_stats(tdmrg_server* srv, int* groups, int64_t* grouped_jobs);
 /* Queue a job (non-blocking); *job_id identifies it.  Errors: EINVAL (bad description). */
 int tdmrg_server_submit(tdmrg_server* srv, const tdmrg_job* job, int64_t* job_id);
 /* Non-blocking state of a job.  obs (host, steps * nobs entries, nullable) receives the observables of

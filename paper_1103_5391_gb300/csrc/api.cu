@@ -66,6 +66,8 @@ void drop_plans(tdmrg_ctx* c) {
     c->plans.clear();
     for (auto& kv : c->rho_plans) release(c, *kv.second);
     c->rho_plans.clear();
+    for (auto& kv : c->dsum_norms) dev_free(c, kv.second.d, kv.second.bytes);
+    c->dsum_norms.clear();
     release_corr(c);
 }
 

@@ -42,14 +42,16 @@ __global__ void k_real_part(cplx* __restrict__ rho, int64_t n) {
 
 // Direct sum of superblocks: each target is normalised per source, dscale[l * nsrc + k] = w_l / ||psi_l^(k)||^2
 // with psi_l^(k) the elements of source k (one block per (target, source), fixed-order block sum).
-struct SegNorm { const cplx* x; int64_t lo, hi; int l, k; };
-__global__ void __launch_bounds__(256) k_seg_weight(const SegNorm* __restrict__ segs, Weights ws, int nsrc,
+struct SegNorm { int64_t lo, hi; int l, k; };
+struct TargetList { const cplx* p[12]; };
+__global__ void __launch_bounds__(256) k_seg_weight(const SegNorm* __restrict__ segs, TargetList tl, Weights ws, int nsrc,
                                                     double* __restrict__ dscale) {
     pdl_enter();
     __shared__ double sh[8];
     const SegNorm sg = segs[blockIdx.x];
+    const cplx* x = tl.p[sg.l];
     double s = 0.0;
-    for (int64_t i = sg.lo + threadIdx.x; i < sg.hi; i += 256) { const double2 v = sg.x[i]; s += v.x * v.x + v.y * v.y; }
+    for (int64_t i = sg.lo + threadIdx.x; i < sg.hi; i += 256) { const double2 v = x[i]; s += v.x * v.x + v.y * v.y; }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -82,31 +84,40 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
             c->dsum_dscale_bytes = need;
         }
         dscale = c->dsum_dscale;
-        std::vector<SegNorm> segs;
-        for (int l = 0; l < nt; ++l) {   // pairs come by left sector, and the left sectors by source
-            std::vector<int64_t> lo(nsrc, -1), hi(nsrc, -1);
-            int64_t off = 0;
-            for (size_t qi = 0; qi < L.dim.size(); ++qi) {
-                const int ri = R.find(Q[2 * l] - L.nup[qi], Q[2 * l + 1] - L.ndn[qi]);
-                if (ri < 0) continue;
-                const int k = c->dsum_src[0][qi];
-                if (lo[k] < 0) lo[k] = off;
-                off += (int64_t)L.dim[qi] * R.dim[ri];
-                hi[k] = off;
+        // the ranges of every (target, source) pair, built once per set of target sectors (outside any
+        // stream capture: the first call of a captured step runs directly)
+        std::vector<int> nkey(Q, Q + 2 * nt);
+        auto nit = c->dsum_norms.find(nkey);
+        if (nit == c->dsum_norms.end()) {
+            std::vector<SegNorm> segs;
+            for (int l = 0; l < nt; ++l) {   // pairs come by left sector, and the left sectors by source
+                std::vector<int64_t> lo(nsrc, -1), hi(nsrc, -1);
+                int64_t off = 0;
+                for (size_t qi = 0; qi < L.dim.size(); ++qi) {
+                    const int ri = R.find(Q[2 * l] - L.nup[qi], Q[2 * l + 1] - L.ndn[qi]);
+                    if (ri < 0) continue;
+                    const int k = c->dsum_src[0][qi];
+                    if (lo[k] < 0) lo[k] = off;
+                    off += (int64_t)L.dim[qi] * R.dim[ri];
+                    hi[k] = off;
+                }
+                if (off == 0) return fail(c, TDMRG_ESECTOR, "density_matrix: target in an empty sector");
+                for (int k = 0; k < nsrc; ++k) segs.push_back({lo[k] < 0 ? 0 : lo[k], lo[k] < 0 ? 0 : hi[k], l, k});
             }
-            if (off == 0) return fail(c, TDMRG_ESECTOR, "density_matrix: target in an empty sector");
-            for (int k = 0; k < nsrc; ++k)
-                segs.push_back({psi[l], lo[k] < 0 ? 0 : lo[k], lo[k] < 0 ? 0 : hi[k], l, k});
+            tdmrg_ctx::DsumNorms dn;
+            dn.bytes = segs.size() * sizeof(SegNorm);
+            dn.count = (int)segs.size();
+            int rc = dev_alloc(c, &dn.d, dn.bytes, "direct sum norms");
+            if (!rc) rc = cuda_check(c, cudaMemcpyAsync(dn.d, segs.data(), dn.bytes, cudaMemcpyHostToDevice, s), "direct sum norms");
+            if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "direct sum norms");
+            if (rc) { dev_free(c, dn.d, dn.bytes); return rc; }
+            nit = c->dsum_norms.emplace(nkey, dn).first;
         }
-        SegNorm* d = nullptr;
-        int rc = dev_alloc(c, (void**)&d, segs.size() * sizeof(SegNorm), "direct sum norms");
-        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(d, segs.data(), segs.size() * sizeof(SegNorm), cudaMemcpyHostToDevice, s),
-                                 "direct sum norms");
-        if (!rc) rc = cuda_check(c, launch_pdl(k_seg_weight, (int)segs.size(), 256, 0, s, (const SegNorm*)d, wl, nsrc, dscale),
-                                 "direct sum norms");
-        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(s), "direct sum norms");
-        dev_free(c, d, segs.size() * sizeof(SegNorm));
+        TargetList tl{};
+        for (int l = 0; l < nt; ++l) tl.p[l] = psi[l];
         c->launches++;
+        int rc = cuda_check(c, launch_pdl(k_seg_weight, nit->second.count, 256, 0, s, (const SegNorm*)nit->second.d, tl, wl,
+                                          nsrc, dscale), "direct sum norms");
         if (rc) return rc;
     } else {
         // norms of the targets -> dscale[l] = w_l / ||psi_l||^2

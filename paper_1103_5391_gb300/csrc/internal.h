@@ -316,6 +316,8 @@ struct tdmrg_ctx {
     int dsum_nsrc = 0;
     double* dsum_dscale = nullptr;
     size_t dsum_dscale_bytes = 0;
+    struct DsumNorms { void* d = nullptr; size_t bytes = 0; int count = 0; };
+    std::map<std::vector<int>, DsumNorms> dsum_norms;   // per-(target, source) ranges, keyed like rho_plans
     double* dscale = nullptr;      // device real scales (rho weights)
     tdmrg::cplx* tmp = nullptr;    // apply_op temporary for expect
     int64_t tmp_cap = 0;

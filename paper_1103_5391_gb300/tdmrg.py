@@ -23,7 +23,7 @@ EXPORTED = [
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats",
-    "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats",
+    "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats", "tdmrg_server_set_batching", "tdmrg_server_batch_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
 TDMRG_JOB_QUEUED, TDMRG_JOB_RUNNING, TDMRG_JOB_DONE, TDMRG_JOB_CANCELLED, TDMRG_JOB_FAILED = 0, 1, 2, 3, 4
@@ -115,6 +115,8 @@ def load(path=LIB_PATH):
         "tdmrg_server_submit": (I, [P, ctypes.POINTER(tdmrg_job), PI64]),
         "tdmrg_server_poll": (I, [P, ctypes.c_int64, ctypes.POINTER(I), ctypes.POINTER(I), P, P]),
         "tdmrg_server_cancel": (I, [P, ctypes.c_int64]),
+        "tdmrg_server_set_batching": (I, [P, I, I]),
+        "tdmrg_server_batch_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_int64)]),
         "tdmrg_server_stats": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
                                    ctypes.POINTER(ctypes.c_size_t)]),
         "tdmrg_server_destroy": (I, [P]),
@@ -552,6 +554,16 @@ def tdmrg_server_stats(srv):
     q, r, f, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
     _scheck(srv, load().tdmrg_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f), ctypes.byref(b)))
     return q.value, r.value, f.value, b.value
+
+
+def tdmrg_server_set_batching(srv, max_group, window_us=2000):
+    return _scheck(srv, load().tdmrg_server_set_batching(srv, max_group, window_us))
+
+
+def tdmrg_server_batch_stats(srv):
+    g, n = ctypes.c_int(), ctypes.c_int64()
+    _scheck(srv, load().tdmrg_server_batch_stats(srv, ctypes.byref(g), ctypes.byref(n)))
+    return g.value, n.value
 
 
 def tdmrg_server_destroy(srv):

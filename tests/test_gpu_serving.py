@@ -149,3 +149,42 @@ def test_server_job_against_oracle(prec):
             T.tdmrg_destroy(jb[1])
     got = res[0][1].reshape(steps, 2)
     assert np.abs(got - want).max() < (1e-12 if prec == 0 else 1e-8)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_mix_equals_alone(prec):
+    """Batching on (groups of up to 4): jobs queued together run as groups on the direct sum of their
+    superblocks; every job's observables equal the job alone up to the order of the FP64 reductions
+    (1e-12 on the FP64 path, 1e-10 on the tensor path, both far below the 1e-8 target)."""
+    torch = torch_cuda()
+    from paper_1103_5391_gb300 import problem
+    from paper_1103_5391_gb300 import tdmrg as T
+    specs = [(16, 128, 1, 101), (20, 200, 2, 102), (24, 300, 1, 103), (16, 160, 2, 104), (28, 256, 1, 105)]
+    steps = 6
+    jobs = [_job(T, problem, torch, *sp, prec) for sp in specs]
+    try:
+        alone = []
+        for jb in jobs:
+            srv = T.tdmrg_server_create(0, 0, 1)
+            try:
+                alone.append(_run(T, srv, [jb], steps, [0.0], problem)[0])
+            finally:
+                T.tdmrg_server_destroy(srv)
+        srv = T.tdmrg_server_create(0, 0, 8)
+        T.tdmrg_server_set_batching(srv, 4, 200000)   # the front waits up to 0.2 s for partners
+        try:
+            mixed = _run(T, srv, jobs, steps, [0.0] * len(jobs), problem)
+            q, r, f, b = T.tdmrg_server_stats(srv)
+            assert (q, r, f) == (0, 0, len(jobs))
+            groups, grouped = T.tdmrg_server_batch_stats(srv)
+            assert groups >= 1 and grouped >= 2
+        finally:
+            T.tdmrg_server_destroy(srv)
+        tol = 1e-12 if prec == 0 else 1e-10
+        for (sa, oa, ma), (sm, om, mm) in zip(alone, mixed):
+            assert sa == sm == T.TDMRG_JOB_DONE
+            assert np.abs(oa - om).max() < tol
+            assert len(mm) == steps and (mm > 0).all()
+    finally:
+        for ss, ctx, psi, phi in jobs:
+            T.tdmrg_destroy(ctx)
