@@ -119,6 +119,8 @@ def parse():
     ap.add_argument("--job-lmax", type=int, default=48, help="serving: largest L of a job (even, >= 16)")
     ap.add_argument("--job-mmax", type=int, default=768, help="serving: largest m of a job (>= 128)")
     ap.add_argument("--gap-ms", type=float, default=20.0, help="serving: mean inter-arrival time")
+    ap.add_argument("--max-group", type=int, default=1, help="serving: batch up to this many jobs per group (1: off)")
+    ap.add_argument("--batch-window-us", type=int, default=2000, help="serving: how long a job waits for partners")
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="only apply H psi N times on the workload (a short run for ncu captures)")
     ap.add_argument("--thin-dim", type=int, default=None,
@@ -850,6 +852,8 @@ def run_serving(args):
     t_gen = time.perf_counter() - t_gen
     gaps = rng.exponential(args.gap_ms * 1e-3, args.jobs)
     srv = T.tdmrg_server_create(0, 0, args.max_active)
+    if args.max_group > 1:
+        T.tdmrg_server_set_batching(srv, args.max_group, args.batch_window_us)
     nk, steps = WL["nk"], args.job_steps
     ids, peak_running = [], 0
     t0 = time.perf_counter()
@@ -872,6 +876,7 @@ def run_serving(args):
                     done[jid] = (st, ms)
         time.sleep(0.001)
     makespan = time.perf_counter() - t0
+    groups, grouped = T.tdmrg_server_batch_stats(srv)
     T.tdmrg_server_destroy(srv)
     ms = np.concatenate([done[j][1] for j in ids])
     ok = sum(1 for j in ids if done[j][0] == T.TDMRG_JOB_DONE)
@@ -883,7 +888,9 @@ def run_serving(args):
                                    f"2-leg ladders L in [16, {args.job_lmax}], U in {{2, 4, 8}}, m log-uniform in "
                                    f"[128, {args.job_mmax}], tau=0.05, "
                                    f"n_v=4, n_K=10, {steps} time steps each, ozaki-bf16 x{args.slices}",
-                       "max_active": args.max_active},
+                       "max_active": args.max_active, "max_group": args.max_group,
+                       "batch_window_us": args.batch_window_us if args.max_group > 1 else None},
+            "groups": groups, "grouped_jobs": grouped,
             "jobs_done": ok, "makespan_s": makespan, "peak_running": peak_running,
             "step_latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                                 "mean": float(ms.mean())},

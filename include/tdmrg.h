@@ -398,7 +398,8 @@ typedef struct {
 int tdmrg_server_create(tdmrg_server** out, int device, size_t hbm_budget, int max_active);
 /* Batching of admitted jobs (north star pattern 2 across jobs): with max_group > 1, the queued jobs that
  * can share a time step (same precision, tau, n_v, n_K, steps and excitation sector shift, static
- * coefficients, distinct contexts) are admitted together, up to max_group, and run as one group on the
+ * coefficients, distinct contexts, vector lengths within a factor of two) are admitted together, up to
+ * max_group, and run as one group on the
  * direct sum of their superblocks (tdmrg_direct_sum): per time step one segmented Krylov advance with
  * one grouped product per Lanczos step for all members, one grouped rho_L and one eigendecomposition
  * over all members' sectors, then each member's observables.  Members finish together; a member's

@@ -11,7 +11,7 @@
 //
 // Batching (tdmrg_server_set_batching, max_group > 1): when jobs are admitted, the queued jobs that can
 // share a time step (same precision, tau, n_v, n_K, number of steps and excitation sector shift; static
-// coefficients) are admitted together, up to max_group, as one group.  A group runs on the direct sum
+// coefficients; vector lengths within a factor of two) are admitted together, up to max_group, as one group.  A group runs on the direct sum
 // of its members' superblocks: per time step one segmented Krylov advance (one grouped product per
 // Lanczos step for every member), one grouped rho_L (every member normalised apart) and one
 // eigendecomposition over every member's sectors, then each member's observables on its own context.
@@ -242,7 +242,9 @@ bool compatible(const Job& a, const Job& b) {
     return x->opts.prec == y->opts.prec && x->opts.ozaki_slices == y->opts.ozaki_slices && a.d.tau == b.d.tau &&
            a.d.n_v == b.d.n_v && a.d.nk == b.d.nk && a.d.steps == b.d.steps && !x->dcoef && !y->dcoef &&
            a.d.q[0] - a.d.q_gs[0] == b.d.q[0] - b.d.q_gs[0] && a.d.q[1] - a.d.q_gs[1] == b.d.q[1] - b.d.q_gs[1] &&
-           x->opts.nk_max >= b.d.nk && x != y;
+           x->opts.nk_max >= b.d.nk && x != y &&
+           // similar sizes: a group's step lasts as long as its largest member's
+           std::max(a.n, b.n) <= 2 * std::min(a.n, b.n);
 }
 
 void release_group(tdmrg_server* s, Group& g) {
