@@ -549,6 +549,8 @@ def measure_config(args, torch, T, problem, key, dev, stream, flush, barrier, st
         res["hpsi"] = {"ms": h_ms, "alg_tflops": alg / (h_ms * 1e-3) / 1e12, "alg_bytes": alg_bytes}
         if mixed:
             res["hpsi"]["work"] = work_decomposition(T, ctx, ss, Q1, args.slices, alg)
+            res["hpsi"]["tuning"] = {"stage%d" % (k + 1): {"tile_m": m, "schedule": "queue" if q == 1 else "static"}
+                                     for k, (m, q) in enumerate(T.tdmrg_hpsi_tuning(ctx, Q1))}
         if headline:
             res["run"] = run
             res["ctx"] = ctx

@@ -59,6 +59,14 @@ int tdmrg_fp64_peak(int device, double* dmma_tflops, double* dfma_tflops);
  * Errors: EINVAL (spins outside 1..2^26), ENOMEM, ECUDA. */
 int tdmrg_probe_wait(tdmrg_ctx* ctx, int64_t spins);
 
+/* Tile M of the persistent tensor kernel: 0 (the default) lets the autotuner time M = 64 and M = 128
+ * with both schedules per GEMM stage when a plan is built; 64 or 128 fixes it (plans are rebuilt on
+ * their next use).  Every choice gives bit-identical products.  Errors: EINVAL. */
+int tdmrg_set_tile_m(tdmrg_ctx* ctx, int m);
+/* The choices of the H psi plan of sector Q: out[0..3] = tile M and schedule (0 static, 1 queue) of
+ * stage 1, then of stage 2 (0 / -1 on the FP64 path).  Builds the plan if needed.  Errors: EINVAL, ESTATE. */
+int tdmrg_hpsi_tuning(tdmrg_ctx* ctx, int n_up, int n_dn, int32_t* out);
+
 /* Per sector of one block (side 0: left, 1: right), from the last tdmrg_rho_eig[_side] there: the
  * number of sweeps of the FP32 Jacobi seed and the SM cycles its CTA took (host arrays of the side's
  * sector count).  Synchronises the stream.  Errors: EINVAL, ESTATE (no eigendecomposition yet). */

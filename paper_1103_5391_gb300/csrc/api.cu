@@ -672,6 +672,30 @@ int tdmrg_probe_wait(tdmrg_ctx* c, int64_t spins) {
     return rc ? rc : check_device_status(c);
 }
 
+int tdmrg_set_tile_m(tdmrg_ctx* c, int m) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (m != 0 && m != 64 && m != 128) return fail(c, TDMRG_EINVAL, "set_tile_m: m must be 0, 64 or 128");
+    DeviceGuard g(c->opts.device);
+    c->tile_m = m;
+    drop_plans(c);   // plans are rebuilt with the new tile shape on their next use
+    return TDMRG_OK;
+}
+
+int tdmrg_hpsi_tuning(tdmrg_ctx* c, int a, int b, int32_t* out) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!out) return fail(c, TDMRG_EINVAL, "hpsi_tuning: null output");
+    if (!c->ham_set) return fail(c, TDMRG_ESTATE, "hpsi_tuning: Hamiltonian not set");
+    DeviceGuard g(c->opts.device);
+    Plan* p = nullptr;
+    int rc = get_plan(c, 0, -1, -1, a, b, a, b, &p);
+    if (rc) return rc;
+    for (int s = 0; s < 2; ++s) {
+        out[2 * s] = p->oz.ready ? p->oz.st[s].tmw : 0;
+        out[2 * s + 1] = p->oz.ready ? p->oz.st[s].queue : -1;
+    }
+    return TDMRG_OK;
+}
+
 int tdmrg_set_schedule(tdmrg_ctx* c, int mode) {
     if (check_ctx(c)) return TDMRG_EINVAL;
     if (mode < -1 || mode > 1) return fail(c, TDMRG_EINVAL, "set_schedule: mode must be -1, 0 or 1");

@@ -143,7 +143,10 @@ struct OzGemmArgs {
 };
 struct OzStage {
     std::vector<OzTask> tasks;
-    std::vector<OzTile> tiles;
+    std::vector<OzTile> tiles;      // M = 64 tiles (the M of the kernel for S > 4 when that kernel runs)
+    std::vector<OzTile> tiles128;   // M = 128 tiles of the persistent kernel (S <= 4)
+    OzTile* d_tiles128 = nullptr;
+    int tmw = 64;                   // tile M of the persistent kernel, chosen by the autotuner
     std::vector<OzSliceJob> ajobs, bjobs;
     std::vector<Seg> asegs, bsegs;
     std::vector<int> avjob, bvjob;   // job index of every vector
@@ -174,7 +177,7 @@ struct OzStage {
     ThinItem* d_titems = nullptr;
     int* d_tcta = nullptr;
     double thin_flops = 0.0;   // algorithmic flops of the thin products (8 per complex MAC)
-    CUtensorMap mapA, mapB;
+    CUtensorMap mapA, mapB, mapA128;
     OzSliceArgs sliceA{}, sliceB{};
     OzGemmArgs args{};
 };
@@ -327,6 +330,7 @@ struct tdmrg_ctx {
     int num_sms = 0;
     int64_t launches = 0;          // kernels launched by this context
     int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue
+    int tile_m = 0;                // tile M of the persistent tensor kernel: 0 autotuned, 64, 128
     void* trunc_tables = nullptr;  // sector tables of tdmrg_truncate
     size_t trunc_tables_bytes = 0;
     int thin_dim = 12;

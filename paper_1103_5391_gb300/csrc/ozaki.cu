@@ -427,9 +427,12 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
 // buffers, so the epilogue of one block overlaps the MMAs of the next.  Hand-offs:
 //   full[st]  (TMA -> MMA, transaction bytes)     empty[st] (MMA completion -> TMA)
 //   tfull[b]  (MMA completion -> epilogue)         tempty[b] (epilogue warps -> MMA)
-constexpr int TMW = 64;                    // MMA M of this variant: sector blocks are mostly <= 64 rows
-constexpr int ABOXW = TMW * KCH * 2;       // bytes of one A slice box (8 KB)
-constexpr int NST = 3;                     // shared-memory stages of S x (8 + 8) KB
+// Tile M is a template parameter (64 or 128), chosen per stage by the autotuner: M = 64 wastes less on
+// the small sector blocks, M = 128 halves the tiles (and the B reads) of blocks with more than 64 rows.
+// With M = 128 every TMEM lane of a quarter holds a row (row i in lane i); three stages of
+// S x (8 + 8) KB (M = 64) or two of S x (16 + 8) KB (M = 128) fit the shared memory.
+template <int TMW> __host__ __device__ constexpr int ws_aboxw() { return TMW * KCH * 2; }   // bytes of one A slice box
+template <int TMW> __host__ __device__ constexpr int ws_nst() { return TMW == 128 ? 2 : 3; }  // shared-memory stages
 constexpr int EPIW = 16;                   // epilogue warps: four per TMEM lane quarter, 16 accumulator columns each
 constexpr int THINW = 2;                   // FP64 warps for the thin sector-pair products
 constexpr int kThinMaxKsteps = 8;          // a thin block's m8n8k4 steps at most (K <= 32 over all its segments)
@@ -520,7 +523,7 @@ __device__ __forceinline__ int static_tile(uint32_t i, int ntiles, volatile int&
     return (t < ntiles && !failed) ? (int)t : -1;
 }
 
-template <int S>
+template <int S, int TMW>
 __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, OzGemmArgs oa,
                                                           GemmArgs g, int ntiles, int queue, const int* skip_flag,
@@ -528,7 +531,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
     pdl_enter();
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
     static_assert(S <= 4, "two TMEM buffers of S x 64 columns must fit in 512");
+    static_assert(TMW == 64 || TMW == 128, "MMA M of the persistent kernel");
     constexpr uint32_t NCOLS = 512;
+    constexpr int ABOXW = ws_aboxw<TMW>(), NST = ws_nst<TMW>();
     constexpr uint32_t STAGE = S * (ABOXW + BBOX);
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -663,9 +668,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
             }
         }
     } else {   // ------------------------------------------------------------------------ epilogue warps 2..17
-        const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31 (16 of them hold rows)
+        const int quad = warp & 3;            // TMEM lanes 32 * quad .. 32 * quad + 31 (M = 64: 16 of them hold rows)
         const int part = (warp - 2) >> 2;     // accumulator columns 16 * part .. 16 * part + 15
-        const int row = 16 * quad + lane;     // valid for lane < 16
+        const int row = (TMW == 128 ? 32 : 16) * quad + lane;
+        const bool row_lane = TMW == 128 || lane < 16;   // this lane holds a row of the tile
         uint32_t b = 0;
         for (uint32_t i = 0;; ++i) {
             int t;
@@ -721,7 +727,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 if (lane < 16) sExp[warp - 2][lane] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
             }
             __syncwarp();
-            if (lane < 16 && tile.m0 + row < task.M) {
+            if (row_lane && tile.m0 + row < task.M) {
                 const int Ei = oa.expA[task.aexp0 + tile.m0 + row] - 7 * (S + 1);
                 const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
                 double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
@@ -787,8 +793,12 @@ int encode_map(tdmrg_ctx* c, CUtensorMap* m, void* base, int64_t rows, int kpad,
 template <int S>
 cudaError_t gemm_attr() {
     if constexpr (S <= 4) {
-        const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
-        return cudaFuncSetAttribute(k_ozaki_gemm_ws<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t s64 = (size_t)ws_nst<64>() * S * (ws_aboxw<64>() + BBOX) + 1024;
+        const size_t s128 = (size_t)ws_nst<128>() * S * (ws_aboxw<128>() + BBOX) + 1024;
+        cudaError_t e = cudaFuncSetAttribute(k_ozaki_gemm_ws<S, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ozaki_gemm_ws<S, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s128);
+        return e;
     } else {
         const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
         return cudaFuncSetAttribute(k_ozaki_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -800,10 +810,17 @@ int g_num_sms = 0;
 template <int S>
 cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
     if constexpr (S <= 4) {
-        const size_t smem = (size_t)NST * S * (ABOXW + BBOX) + 1024;
-        const int ntiles = (int)st.tiles.size();
-        launch_pdl(k_ozaki_gemm_ws<S>, std::max(1, st.grid), WS_THREADS, smem, s, st.mapA, st.mapB, st.args, g, ntiles,
-                   st.queue, skip_flag, skip_step);
+        OzGemmArgs a = st.args;
+        if (st.tmw == 128) {
+            const size_t smem = (size_t)ws_nst<128>() * S * (ws_aboxw<128>() + BBOX) + 1024;
+            a.tiles = st.d_tiles128;
+            launch_pdl(k_ozaki_gemm_ws<S, 128>, std::max(1, st.grid), WS_THREADS, smem, s, st.mapA128, st.mapB, a, g,
+                       (int)st.tiles128.size(), st.queue, skip_flag, skip_step);
+        } else {
+            const size_t smem = (size_t)ws_nst<64>() * S * (ws_aboxw<64>() + BBOX) + 1024;
+            launch_pdl(k_ozaki_gemm_ws<S, 64>, std::max(1, st.grid), WS_THREADS, smem, s, st.mapA, st.mapB, a, g,
+                       (int)st.tiles.size(), st.queue, skip_flag, skip_step);
+        }
         return cudaGetLastError();
     }
     const size_t smem = (size_t)S * (ABOX + BBOX) + 1024;
@@ -840,6 +857,7 @@ void release_oz(tdmrg_ctx* c, OzPlan& oz) {
     for (OzStage& st : oz.st) {
         dev_free(c, st.d_tasks, st.tasks.size() * sizeof(OzTask));
         dev_free(c, st.d_tiles, st.tiles.size() * sizeof(OzTile));
+        dev_free(c, st.d_tiles128, st.tiles128.size() * sizeof(OzTile));
         dev_free(c, st.d_ajobs, st.ajobs.size() * sizeof(OzSliceJob));
         dev_free(c, st.d_bjobs, st.bjobs.size() * sizeof(OzSliceJob));
         dev_free(c, st.d_avjob, st.avjob.size() * sizeof(int));
@@ -867,11 +885,13 @@ void release_oz(tdmrg_ctx* c, OzPlan& oz) {
 // schedule computes the same exact integer sums, so the choice never changes a result.
 static int autotune_oz(tdmrg_ctx* c, Plan* p) {
     OzPlan& oz = p->oz;
-    if (oz.S > 4) return TDMRG_OK;   // only the persistent kernel has schedules
-    if (c->schedule >= 0) {          // fixed by tdmrg_set_schedule
-        for (OzStage& st : oz.st) st.queue = c->schedule;
-        return TDMRG_OK;
+    if (oz.S > 4) return TDMRG_OK;   // only the persistent kernel has schedules and tile shapes
+    const bool fix_q = c->schedule >= 0, fix_m = c->tile_m > 0;   // fixed by tdmrg_set_schedule / tdmrg_set_tile_m
+    for (OzStage& st : oz.st) {
+        st.queue = fix_q ? c->schedule : 0;
+        st.tmw = (fix_m && c->tile_m == 128 && !st.tiles128.empty()) ? 128 : 64;
     }
+    if (fix_q && fix_m) return TDMRG_OK;
     cplx *tin = nullptr, *tout = nullptr;
     const size_t bin = (size_t)std::max<int64_t>(p->n_in, 1) * sizeof(cplx), bout = (size_t)std::max<int64_t>(p->n_out, 1) * sizeof(cplx);
     int rc = dev_alloc(c, (void**)&tin, bin, "autotuning buffers");
@@ -892,21 +912,37 @@ static int autotune_oz(tdmrg_ctx* c, Plan* p) {
             default: return gemm_launch<4>(st, g, c->stream, nullptr, 0);
         }
     };
+    // per stage: every allowed (tile M, schedule) timed; the default (M = 64, static) is kept unless
+    // another is at least 3 % faster.  Every choice computes the same exact integer sums.
     for (int stg = 0; stg < 2 && !rc; ++stg) {
         OzStage& st = oz.st[stg];
         if (st.tasks.empty()) continue;
-        float ms[2] = {0.f, 0.f};
-        for (int q = 0; q < 2 && !rc; ++q) {
-            st.queue = q;
+        std::vector<std::pair<int, int>> cand;
+        for (int m : {64, 128}) {
+            if (m == 128 && st.tiles128.empty()) continue;
+            if (fix_m && m != st.tmw) continue;
+            for (int q : {0, 1}) {
+                if (fix_q && q != c->schedule) continue;
+                cand.push_back({m, q});
+            }
+        }
+        float best = 0.f;
+        std::pair<int, int> pick = cand.front();
+        for (size_t k = 0; k < cand.size() && !rc; ++k) {
+            st.tmw = cand[k].first;
+            st.queue = cand[k].second;
+            float ms = 0.f;
             cudaError_t e = launch(st);   // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch(st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[q], e0, e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             rc = cuda_check(c, e, "autotuning");
+            if (k == 0 || ms < 0.97f * best) { best = ms; pick = cand[k]; }
         }
-        st.queue = (!rc && ms[1] < 0.97f * ms[0]) ? 1 : 0;
+        st.tmw = pick.first;
+        st.queue = pick.second;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -923,7 +959,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
     release_oz(c, oz);
     oz.S = S;
     oz.status = c->dstatus;
-    const int tm = S <= 4 ? TMW : TM;   // MMA M of the kernel that runs this precision
+    const int tm = S <= 4 ? 64 : TM;   // MMA M of the kernel that runs this precision (S <= 4: also an M = 128 list)
     int rc = TDMRG_OK;
     for (int stg = 0; stg < 2; ++stg) {
         const TaskList& tl = stg == 0 ? p->stage1 : p->stage2;
@@ -1028,8 +1064,13 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             st.tasks.push_back(ot);
             for (int m0 = 0; m0 < tk.M; m0 += tm)
                 for (int n0 = 0; n0 < tk.N; n0 += TNC) st.tiles.push_back({ti, m0, n0, (int)(std::min(tm, tk.M - m0) * std::min(TNC, tk.N - n0)) * ot.kchunks});
+            if (S <= 4)
+                for (int m0 = 0; m0 < tk.M; m0 += 128)
+                    for (int n0 = 0; n0 < tk.N; n0 += TNC)
+                        st.tiles128.push_back({ti, m0, n0, (int)(std::min(128, tk.M - m0) * std::min(TNC, tk.N - n0)) * ot.kchunks});
         }
         std::stable_sort(st.tiles.begin(), st.tiles.end(), [](const OzTile& a, const OzTile& b) { return a.cost > b.cost; });
+        std::stable_sort(st.tiles128.begin(), st.tiles128.end(), [](const OzTile& a, const OzTile& b) { return a.cost > b.cost; });
         // persistent grid: one CTA per SM when thin items exist (their warps ride along), else one per tile
         st.grid = st.titems.empty() ? std::max(1, std::min((int)st.tiles.size(), c->num_sms)) : c->num_sms;
         if (!st.titems.empty()) {   // thin items: longest first onto the least loaded CTA, grouped by CTA
@@ -1050,7 +1091,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             }
         }
         // panels: rows padded so that every TMA box (tm rows for A, 64 for B) stays inside the plane
-        st.rowsA = rowsA + tm;
+        st.rowsA = rowsA + (S <= 4 ? 128 : tm);
         st.rowsB = rowsB + 2 * TNC;
         st.kpad = std::max(KCH, (kmax + KCH - 1) / KCH * KCH);
         st.panel_bytes_a = (size_t)S * st.rowsA * st.kpad * 2;
@@ -1090,6 +1131,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (!rc) rc = cuda_check(c, cudaMemset(st.panelB, 0, st.panel_bytes_b), "ozaki panels");
             if (!rc) rc = upload_vec(c, st.tasks, &st.d_tasks, "ozaki tasks");
             if (!rc) rc = upload_vec(c, st.tiles, &st.d_tiles, "ozaki tiles");
+            if (!rc && !st.tiles128.empty()) rc = upload_vec(c, st.tiles128, &st.d_tiles128, "ozaki tiles");
             if (!rc) rc = upload_vec(c, st.ajobs, &st.d_ajobs, "ozaki slice jobs");
             if (!rc) rc = upload_vec(c, st.bjobs, &st.d_bjobs, "ozaki slice jobs");
             if (!rc && !st.avjob.empty()) rc = upload_vec(c, st.avjob, &st.d_avjob, "ozaki slice jobs");
@@ -1097,6 +1139,7 @@ int build_oz(tdmrg_ctx* c, Plan* p, int S) {
             if (!rc) rc = upload_vec(c, st.asegs, &st.d_asegs, "ozaki slice segments");
             if (!rc) rc = upload_vec(c, st.bsegs, &st.d_bsegs, "ozaki slice segments");
             if (!rc) rc = encode_map(c, &st.mapA, st.panelA, (int64_t)S * st.rowsA, st.kpad, tm);
+            if (!rc && S <= 4) rc = encode_map(c, &st.mapA128, st.panelA, (int64_t)S * st.rowsA, st.kpad, 128);
             if (!rc) rc = encode_map(c, &st.mapB, st.panelB, (int64_t)S * st.rowsB, st.kpad, 2 * TNC);
             if (rc) return rc;
             st.args.tasks = st.d_tasks; st.args.tiles = st.d_tiles;

@@ -22,7 +22,7 @@ EXPORTED = [
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_direct_sum", "tdmrg_evolve_segments", "tdmrg_evolve_segments_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
-    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats",
+    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats", "tdmrg_set_tile_m", "tdmrg_hpsi_tuning",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats", "tdmrg_server_set_batching", "tdmrg_server_batch_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
@@ -98,6 +98,8 @@ def load(path=LIB_PATH):
         "tdmrg_enlarge": (I, [P, I, I, PI32, PI32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
         "tdmrg_set_op_adjoint": (I, [P, I, I, I]),
         "tdmrg_eig_stats": (I, [P, I, PI32, PI64]),
+        "tdmrg_set_tile_m": (I, [P, I]),
+        "tdmrg_hpsi_tuning": (I, [P, I, I, PI32]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
         "tdmrg_correlation": (I, [P, I, PI32, I, PI32, I, I, P, I, I, P, P]),
@@ -447,6 +449,17 @@ def tdmrg_eig_stats(ctx, nsec, side=0):
     _check(ctx, load().tdmrg_eig_stats(ctx, side, sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                        cy.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
     return sw, cy
+
+
+def tdmrg_set_tile_m(ctx, m):
+    return _check(ctx, load().tdmrg_set_tile_m(ctx, m))
+
+
+def tdmrg_hpsi_tuning(ctx, Q):
+    """(tile M, schedule) of stage 1 and of stage 2 of the H psi plan of sector Q."""
+    o = np.zeros(4, np.int32)
+    _check(ctx, load().tdmrg_hpsi_tuning(ctx, Q[0], Q[1], o.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return [(int(o[0]), int(o[1])), (int(o[2]), int(o[3]))]
 
 
 def tdmrg_probe_wait(ctx, spins):

@@ -220,3 +220,39 @@ def test_thin_split_parity(lib, thin_dim, L, m, nb, seed):
             lib.tdmrg_set_thin_dim(ctx, 65)
     finally:
         lib.tdmrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("slices", [2, 4])
+def test_tile_shapes_bit_identical(lib, slices):
+    """Tile M = 64 and M = 128 of the persistent kernel (each with both schedules) and the autotuned
+    choice give bit-identical H psi (the accumulation is exact integer arithmetic) on a superblock with
+    sector blocks above 64 rows (L=24, m=700: left sectors up to ~90), within the slicing bound of the
+    oracle; the tuning query reports the fixed choices."""
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(24, 700, 4.0, nbonds=1, seed=23)
+    assert max(ss.ldim) > 64
+    sb, HL, HR, conns = oracle_ops_of_synthetic(ss)
+    ctx = new_ctx(prec=lib.TDMRG_OZAKI_BF16, ozaki_slices=slices)
+    try:
+        problem.load_synthetic(ctx, ss)
+        n = lib.tdmrg_sector_size(ctx, ss.Q1)
+        x = _rand(n, 8)
+        xd = dev(x)
+        outs = []
+        for m in (64, 128, 0):
+            for mode in ((0, 1) if m else (-1,)):
+                lib.tdmrg_set_tile_m(ctx, m)
+                lib.tdmrg_set_schedule(ctx, mode)
+                out = dev(np.full(n, np.nan + 0j))
+                lib.tdmrg_apply_h(ctx, ss.Q1, xd, out)
+                outs.append(host(out))
+                if m:
+                    tun = lib.tdmrg_hpsi_tuning(ctx, ss.Q1)
+                    assert all(t[0] == m and t[1] == mode for t in tun), tun
+        for o in outs[1:]:
+            assert np.array_equal(o.view(np.float64), outs[0].view(np.float64))
+        assert rel_err(outs[0], superblock.apply_h(sb, HL, HR, conns, ss.Q1, x)) < _tol(slices)
+        with pytest.raises(lib.TdmrgError):
+            lib.tdmrg_set_tile_m(ctx, 96)
+    finally:
+        lib.tdmrg_destroy(ctx)
