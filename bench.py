@@ -123,6 +123,8 @@ def parse():
     ap.add_argument("--batch-window-us", type=int, default=2000, help="serving: how long a job waits for partners")
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="only apply H psi N times on the workload (a short run for ncu captures)")
+    ap.add_argument("--tile-m", type=int, default=0, choices=[0, 64, 128],
+                    help="--profile-hpsi: fix the tile M of the tensor kernel (0: autotuned)")
     ap.add_argument("--thin-dim", type=int, default=None,
                     help="profile mode: products with fewer rows or columns run on the FP64 thin warps (0 = none)")
     ap.add_argument("--precision-errors", action="store_true",
@@ -902,9 +904,9 @@ def run_serving(args):
 
 
 def run_profile_hpsi(args):
-    """N applications of H psi on the bench workload, nothing else: after the plan build (which times
-    both tile schedules of each stage) every application is slice rows, stage-1 GEMM, slice columns,
-    stage-2 GEMM."""
+    """N applications of H psi on the bench workload, nothing else: after the plan build (two static
+    slicing launches, then 4 timed launches of each tile shape x schedule choice per stage: 4 choices,
+    or 2 with --tile-m) every application is slice rows, stage-1 GEMM, slice columns, stage-2 GEMM."""
     import torch
     from paper_1103_5391_gb300 import problem, tdmrg as T
     torch.cuda.set_device(0)
@@ -916,6 +918,8 @@ def run_profile_hpsi(args):
         problem.load_synthetic(ctx, ss)
         if args.thin_dim is not None:
             T.tdmrg_set_thin_dim(ctx, args.thin_dim)
+        if args.tile_m:
+            T.tdmrg_set_tile_m(ctx, args.tile_m)
         n = T.tdmrg_sector_size(ctx, ss.Q1)
         x = torch.randn(n, dtype=torch.complex128, device="cuda")
         y = torch.zeros_like(x)
