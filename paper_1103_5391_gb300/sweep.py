@@ -124,8 +124,12 @@ class TSTSweep:
     two or more sites with its V and kept counts); they are replaced by the blocks the sweep makes."""
 
     def __init__(self, L, t, U, m, left, right, n_v=4, tau=0.1, nk=12, advance_every=2, gs_nk=32, gs_restarts=40,
-                 real_basis=False, device=None, excitations=None):
+                 real_basis=False, device=None, excitations=None, prec=None, ozaki_slices=4):
+        """prec: arithmetic of the superblock products (T.TDMRG_FP64, the default, or T.TDMRG_OZAKI_BF16
+        with ozaki_slices slices); everything else stays FP64."""
         self.L, self.t, self.U, self.m = L, t, U, m
+        self.prec = T.TDMRG_FP64 if prec is None else prec
+        self.ozaki_slices = ozaki_slices
         self.left, self.right = dict(left), dict(right)
         self.n_v, self.tau, self.nk, self.advance_every = n_v, tau, nk, advance_every
         self.gs_nk, self.gs_restarts = gs_nk, gs_restarts
@@ -142,7 +146,7 @@ class TSTSweep:
 
     def _ctx(self):
         return T.tdmrg_create(device=self.dev.index, stream=torch.cuda.current_stream(self.dev).cuda_stream,
-                              nk_max=max(32, self.nk, self.gs_nk))
+                              nk_max=max(32, self.nk, self.gs_nk), prec=self.prec, ozaki_slices=self.ozaki_slices)
 
     def _observe(self, ctx, Q, x):
         n = T.tdmrg_sector_size(ctx, Q)

@@ -116,3 +116,37 @@ def test_sweep_matches_oracle_step_by_step(sweeps):
         for a, b in zip(g["targets"], w["targets"]):
             for key in ("norm2", "energy", "n_left", "n_right", "bond"):
                 assert abs(a[key] - b[key]) < 1e-10, (w["l"], w["move"], key, a[key], b[key])
+
+
+def test_sweep_on_the_tensor_path():
+    """The same sweep (first schedule) with every superblock product on the tensor cores (4 bf16 slices;
+    Lanczos, rho, eigendecomposition and transformations in FP64) against the oracle's FP64 sweep: the
+    kept counts equal; the eigenvalues of rho, the discarded weight and every target's norm, densities and
+    bond within 1e-8, the observable accuracy target of the mixed-precision path (measured 6e-9, 1e-11,
+    5e-9); energies (the ground state's and every target's <H>, which carry the product's own error to
+    first order) within the H psi slicing bound 140 2^-28 relative (measured 1.4e-8)."""
+    torch_cuda()
+    from paper_1103_5391_gb300 import sweep as S
+    from paper_1103_5391_gb300 import tdmrg as T
+    m, every, exc = CASES[0]
+    d = dmrg.ChainDMRG(L, T_HOP, U, m)
+    d.run(sweeps=1)
+    left, right = _device_blocks(d, S)
+    want = tst.TSTSweep(copy.deepcopy(d), m, n_v=4, tau=0.1, nk=10, advance_every=every, excitations=exc).run()
+    got = S.TSTSweep(L, T_HOP, U, m, left, right, n_v=4, tau=0.1, nk=10, advance_every=every, excitations=exc,
+                     prec=T.TDMRG_OZAKI_BF16, ozaki_slices=4).run()
+    worst = {"energy_rel": 0.0, "evals": 0.0, "discarded": 0.0, "observables": 0.0}
+    for w, g in zip(want, got):
+        assert (g["l"], g["move"], g["action"]) == (w["l"], w["move"], w["action"])
+        worst["energy_rel"] = max(worst["energy_rel"], abs(g["energy"] - w["energy"]) / abs(w["energy"]))
+        if w["move"] is not None:
+            assert g["kept"] == list(w["kept"])
+            worst["discarded"] = max(worst["discarded"], abs(g["discarded"] - w["discarded"]))
+            for a, b in zip(g["evals"], w["evals"]):
+                worst["evals"] = max(worst["evals"], float(np.abs(a - b).max()))
+        for a, b in zip(g["targets"], w["targets"]):
+            worst["energy_rel"] = max(worst["energy_rel"], abs(a["energy"] - b["energy"]) / abs(b["energy"]))
+            for key in ("norm2", "n_left", "n_right", "bond"):
+                worst["observables"] = max(worst["observables"], abs(a[key] - b[key]))
+    assert worst["energy_rel"] < 140.0 * 2.0 ** -28, worst
+    assert max(worst["evals"], worst["discarded"], worst["observables"]) < 1e-8, worst
