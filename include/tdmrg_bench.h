@@ -63,6 +63,9 @@ int tdmrg_probe_wait(tdmrg_ctx* ctx, int64_t spins);
  * with both schedules per GEMM stage when a plan is built; 64 or 128 fixes it (plans are rebuilt on
  * their next use).  Every choice gives bit-identical products.  Errors: EINVAL. */
 int tdmrg_set_tile_m(tdmrg_ctx* ctx, int m);
+/* Blocks per SM of the cooperative Lanczos orthogonalisation (1..8, capped by co-residency and by 304
+ * blocks; 0 = the default).  Drops the Krylov workspaces.  Errors: EINVAL. */
+int tdmrg_set_orth_per_sm(tdmrg_ctx* ctx, int k);
 /* The choices of the H psi plan of sector Q: out[0..3] = tile M and schedule (0 static, 1 queue) of
  * stage 1, then of stage 2 (0 / -1 on the FP64 path).  Builds the plan if needed.  Errors: EINVAL, ESTATE. */
 int tdmrg_hpsi_tuning(tdmrg_ctx* ctx, int n_up, int n_dn, int32_t* out);

@@ -672,6 +672,16 @@ int tdmrg_probe_wait(tdmrg_ctx* c, int64_t spins) {
     return rc ? rc : check_device_status(c);
 }
 
+int tdmrg_set_orth_per_sm(tdmrg_ctx* c, int k) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (k < 0 || k > 8) return fail(c, TDMRG_EINVAL, "set_orth_per_sm: 0..8 blocks per SM");
+    DeviceGuard g(c->opts.device);
+    cudaStreamSynchronize(c->stream);
+    c->orth_per_sm = k;
+    drop_krylov(c);   // the Krylov workspaces are rebuilt with the new grid on their next use
+    return TDMRG_OK;
+}
+
 int tdmrg_set_tile_m(tdmrg_ctx* c, int m) {
     if (check_ctx(c)) return TDMRG_EINVAL;
     if (m != 0 && m != 64 && m != 128) return fail(c, TDMRG_EINVAL, "set_tile_m: m must be 0, 64 or 128");

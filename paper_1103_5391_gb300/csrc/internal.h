@@ -331,6 +331,7 @@ struct tdmrg_ctx {
     int64_t launches = 0;          // kernels launched by this context
     int schedule = -1;             // tile schedule of the persistent tensor kernel: -1 autotuned, 0 static, 1 queue
     int tile_m = 0;                // tile M of the persistent tensor kernel: 0 autotuned, 64, 128
+    int orth_per_sm = 0;           // blocks per SM of the cooperative orthogonalisation (0: the default)
     void* trunc_tables = nullptr;  // sector tables of tdmrg_truncate
     size_t trunc_tables_bytes = 0;
     int thin_dim = 12;

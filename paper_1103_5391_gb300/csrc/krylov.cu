@@ -682,7 +682,8 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
     if (!rc) {   // co-resident grid of the fused orthogonalisation: at most one block per SM, at most NB
         int per_sm = 0;
         rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_orth_t<true>, OB, 0), "occupancy");
-        k.orth_grid = std::max(1, std::min({c->num_sms * std::max(per_sm, 1), c->num_sms, NB}));
+        const int want = c->orth_per_sm > 0 ? c->orth_per_sm : 1;   // blocks per SM of the fused orthogonalisation
+        k.orth_grid = std::max(1, std::min({c->num_sms * std::max(per_sm, 1), c->num_sms * want, NB}));
     }
     if (rc) {
         dev_free(c, k.V, (size_t)(nk + 1) * n * sizeof(cplx));

@@ -22,7 +22,7 @@ EXPORTED = [
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_direct_sum", "tdmrg_evolve_segments", "tdmrg_evolve_segments_info", "tdmrg_tst_weights",
     "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
-    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats", "tdmrg_set_tile_m", "tdmrg_hpsi_tuning",
+    "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats", "tdmrg_set_tile_m", "tdmrg_hpsi_tuning", "tdmrg_set_orth_per_sm",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats", "tdmrg_server_set_batching", "tdmrg_server_batch_stats",
     "tdmrg_server_destroy", "tdmrg_server_last_error",
 ]
@@ -99,6 +99,7 @@ def load(path=LIB_PATH):
         "tdmrg_set_op_adjoint": (I, [P, I, I, I]),
         "tdmrg_eig_stats": (I, [P, I, PI32, PI64]),
         "tdmrg_set_tile_m": (I, [P, I]),
+        "tdmrg_set_orth_per_sm": (I, [P, I]),
         "tdmrg_hpsi_tuning": (I, [P, I, I, PI32]),
         "tdmrg_expect": (I, [P, I, I, I, I, P, P]),
         "tdmrg_overlap_op": (I, [P, I, I, I, I, P, I, I, P, P]),
@@ -449,6 +450,10 @@ def tdmrg_eig_stats(ctx, nsec, side=0):
     _check(ctx, load().tdmrg_eig_stats(ctx, side, sw.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                        cy.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
     return sw, cy
+
+
+def tdmrg_set_orth_per_sm(ctx, k):
+    return _check(ctx, load().tdmrg_set_orth_per_sm(ctx, k))
 
 
 def tdmrg_set_tile_m(ctx, m):
