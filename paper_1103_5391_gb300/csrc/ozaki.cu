@@ -69,14 +69,44 @@ __device__ __forceinline__ double2 scaled(double2 v, cplx s) {
     return make_double2(s.x * v.x - s.y * v.y, s.x * v.y + s.y * v.x);
 }
 
-// One warp per vector (row of A' or complex column of B'); two passes over the task's segments
-// (exponent, then digits).  The segments are flattened into one element index (their views cached in
-// shared memory, kSegCache at a time) and each lane issues kSliceU independent loads per batch, so a
-// vector costs a few memory latencies instead of one per segment and pass; a vector of at most
-// 32 kSliceU elements keeps its values in registers between the passes.
-constexpr int kSliceU = 8;
+// For S <= 4 the fixed-point value fits 32 bits (|N| <= 2^28), so the rounding and the digits run in
+// 32-bit integer arithmetic: with k = -sh >= 25, (m + 2^{k-1}) >> k = ((m >> (k - 1)) + 1) >> 1, whose
+// operand is below 2^29.  Same values as fixed_point + digits.
+template <int S>
+__device__ __forceinline__ void slice_digits(double v, int E, int* d) {
+    if constexpr (7 * S <= 28) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const int ex = (int)((b >> 52) & 0x7FF);
+        int N = 0;
+        if (ex != 0) {
+            const int k = E - (ex - 1075) - 7 * S;   // >= 25 as |v| < 2^E
+            if (k <= 62) {
+                const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+                N = (int)(((unsigned)(m >> (k - 1)) + 1u) >> 1);
+                if (b >> 63) N = -N;
+            }
+        }
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+            const int w = 7 * (S - s);
+            const int q = (N + (1 << (w - 1))) >> w;
+            N -= q << w;
+            d[s - 1] = q;
+        }
+        d[S - 1] = N;
+    } else {
+        digits<S>(fixed_point(v, E, 7 * S), d);
+    }
+}
+
+// One CTA of kSliceCT threads per vector (row of A' or complex column of B'); two passes over the task's
+// segments (exponent, then digits).  The segments are flattened into one element index (their views
+// cached in shared memory, kSegCache at a time) and each thread loads kSliceCU elements per batch, so a
+// vector costs a few memory latencies, its elements spread over four warps; a vector of at most
+// kSliceCT kSliceCU elements keeps its values in registers between the passes.
+constexpr int kSliceCT = 128;
+constexpr int kSliceCU = 4;
 constexpr int kSegCache = 16;
-constexpr int kSliceWarps = 8;
 
 struct SegView {          // element k of the vector at base[k * sk], conjugated and scaled as asked
     const double2* base;
@@ -93,82 +123,89 @@ __device__ __forceinline__ double2 view_load(const SegView& w, int k, bool use_s
 }
 
 template <int S>
-__global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, GemmArgs g, const int* skip_flag, int skip_step) {
+__global__ void __launch_bounds__(kSliceCT) k_slice(OzSliceArgs sa, GemmArgs g, const int* skip_flag, int skip_step) {
     pdl_enter();
     if (skip_flag != nullptr && skip_step >= *skip_flag) return;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    if (gw >= sa.nvec_total) return;   // warp-uniform
-    const OzSliceJob job = sa.jobs[sa.vjob[gw]];
-    const int v = gw - job.vec_prefix;
-    constexpr int S7 = 7 * S;
-    __shared__ SegView sv[kSliceWarps][kSegCache];
-    __shared__ int spre[kSliceWarps][kSegCache + 1];
+    const int gv = blockIdx.x;   // the vector; block-uniform
+    if (gv >= sa.nvec_total) return;
+    const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5;
+    const OzSliceJob job = sa.jobs[sa.vjob[gv]];
+    const int v = gv - job.vec_prefix;
+    __shared__ SegView sv[kSegCache];
+    __shared__ int spre[kSegCache + 1];
+    __shared__ int red[kSliceCT / 32];
     const int nseg = job.seg_end - job.seg_begin;
     const bool use_scale = job.use_scale != 0;
-    // views of segments [w0, w0 + nw) for this vector; prefix offsets of their K in spre
-    auto build = [&](int w0, int nw) {
-        __syncwarp();
-        if (lane < nw) {
-            const Seg sg = sa.segs[job.seg_begin + w0 + lane];
-            SegView w;
-            w.scale = sg.scale;
-            if (sg.dcoef >= 0 && g.dcoef != nullptr) w.scale = scaled(g.dcoef[sg.dcoef], sg.scale);   // run-time coefficient
-            w.conj = 0;
-            if (job.role == 0) {
-                w.base = g.bufs[sg.a_buf] + sg.a_off + (int64_t)v * sg.lda;
-                w.sk = 1;
-            } else {
-                const cplx* B = g.bufs[sg.b_buf] + sg.b_off;
-                if (sg.opb == OPB_N) { w.base = B + v; w.sk = sg.ldb; }
-                else { w.base = B + (int64_t)v * sg.ldb; w.sk = 1; w.conj = sg.opb == OPB_C; }
+    // views of segments [w0, w0 + nw) for this vector and the prefix offsets of their K (warp 0, one scan)
+    auto build = [&](int w0, int nw, bool again) {
+        if (again) __syncthreads();   // the previous window's views are no longer read
+        if (wi == 0) {
+            int k = 0;
+            if (lane < nw) {
+                const Seg sg = sa.segs[job.seg_begin + w0 + lane];
+                SegView w;
+                w.scale = sg.scale;
+                if (sg.dcoef >= 0 && g.dcoef != nullptr) w.scale = scaled(g.dcoef[sg.dcoef], sg.scale);   // run-time coefficient
+                w.conj = 0;
+                if (job.role == 0) {
+                    w.base = g.bufs[sg.a_buf] + sg.a_off + (int64_t)v * sg.lda;
+                    w.sk = 1;
+                } else {
+                    const cplx* B = g.bufs[sg.b_buf] + sg.b_off;
+                    if (sg.opb == OPB_N) { w.base = B + v; w.sk = sg.ldb; }
+                    else { w.base = B + (int64_t)v * sg.ldb; w.sk = 1; w.conj = sg.opb == OPB_C; }
+                }
+                sv[lane] = w;
+                k = sg.K;
             }
-            sv[wi][lane] = w;
-            spre[wi][lane + 1] = sg.K;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {   // inclusive prefix sum over the lanes
+                const int t = __shfl_up_sync(0xffffffffu, k, o);
+                if (lane >= o) k += t;
+            }
+            if (lane < nw) spre[lane + 1] = k;
+            if (lane == 0) spre[0] = 0;
         }
-        __syncwarp();
-        if (lane == 0) {
-            spre[wi][0] = 0;
-            for (int i = 0; i < nw; ++i) spre[wi][i + 1] += spre[wi][i];
-        }
-        __syncwarp();
-        return spre[wi][nw];
+        __syncthreads();
+        return spre[nw];
     };
     auto seg_of = [&](int e, int nw) {
         int sgi = 0;
-        while (sgi + 1 < nw && e >= spre[wi][sgi + 1]) ++sgi;
+        while (sgi + 1 < nw && e >= spre[sgi + 1]) ++sgi;
         return sgi;
     };
-    // the first batch of a vector (up to 32 kSliceU elements) is kept in shared memory between the
-    // passes; each lane reads back only what it wrote, so no barrier is needed
-    __shared__ double2 scache[kSliceWarps][32 * kSliceU];
-    double2* cache = scache[wi];
-    const bool one_batch = nseg <= kSegCache;
+    const bool one_window = nseg <= kSegCache;
+    double2 xr[kSliceCU];
     int emax = 0, kw_first = 0;
     for (int w0 = 0; w0 < nseg; w0 += kSegCache) {   // pass 1: largest exponent
         const int nw = min(kSegCache, nseg - w0);
-        const int kw = build(w0, nw);
+        const int kw = build(w0, nw, w0 > 0);
         if (w0 == 0) kw_first = kw;
-        for (int e0 = 0; e0 < kw; e0 += 32 * kSliceU) {
-            double2 x[kSliceU];
+        for (int e0 = 0; e0 < kw; e0 += kSliceCT * kSliceCU) {
+            double2 x[kSliceCU];
 #pragma unroll
-            for (int u = 0; u < kSliceU; ++u) {
-                const int e = e0 + lane + 32 * u;
+            for (int u = 0; u < kSliceCU; ++u) {
+                const int e = e0 + tid + kSliceCT * u;
                 x[u] = make_double2(0.0, 0.0);
                 if (e < kw) {
                     const int sgi = seg_of(e, nw);
-                    x[u] = view_load(sv[wi][sgi], e - spre[wi][sgi], use_scale);
+                    x[u] = view_load(sv[sgi], e - spre[sgi], use_scale);
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kSliceU; ++u) {
+            for (int u = 0; u < kSliceCU; ++u) {
                 emax = max(emax, max(biased_exp(x[u].x), biased_exp(x[u].y)));
-                if (w0 == 0 && e0 == 0) cache[lane + 32 * u] = x[u];
+                if (w0 == 0 && e0 == 0) xr[u] = x[u];
             }
         }
     }
-    const bool cached = one_batch && kw_first <= 32 * kSliceU;
+    const bool cached = one_window && kw_first <= kSliceCT * kSliceCU;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if (lane == 0) red[wi] = emax;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSliceCT / 32; ++k) emax = max(emax, red[k]);
     const int E = emax == 0 ? 0 : emax - 1023 + 1;   // every |value| < 2^E
     int r_re, r_im;                                   // destination panel rows
     if (job.role == 0) {
@@ -180,43 +217,44 @@ __global__ void __launch_bounds__(32 * kSliceWarps) k_slice(OzSliceArgs sa, Gemm
         r_re = job.row0 + 2 * TNC * nt + c;
         r_im = r_re + n_t;
     }
-    if (lane == 0) sa.exps[job.exp0 + v] = E;
+    if (tid == 0) sa.exps[job.exp0 + v] = E;
     const int64_t plane = (int64_t)sa.rows * sa.kpad;
     __nv_bfloat16* const row_re = sa.panel + (int64_t)r_re * sa.kpad;   // plane 0 rows; plane t at + t plane
     __nv_bfloat16* const row_im = sa.panel + (int64_t)r_im * sa.kpad;
     const bool role0 = job.role == 0;
+    const int q = job.ktot;   // the imaginary half of a row starts at ktot
     int kbase = 0;
     for (int w0 = 0; w0 < nseg; w0 += kSegCache) {   // pass 2: digits
         const int nw = min(kSegCache, nseg - w0);
-        const int kw = (w0 == 0 && one_batch) ? kw_first : build(w0, nw);
-        for (int e0 = 0; e0 < kw; e0 += 32 * kSliceU) {
-#pragma unroll 1
-            for (int u = 0; u < kSliceU; ++u) {
-                const int e = e0 + lane + 32 * u;
-                if (e >= kw) break;   // e grows with u
-                double2 x;
-                if (cached) {
-                    x = cache[lane + 32 * u];
-                } else {
-                    const int sgi = seg_of(e, nw);
-                    x = view_load(sv[wi][sgi], e - spre[wi][sgi], use_scale);
-                }
-                int dr[S], di[S];
-                digits<S>(fixed_point(x.x, E, S7), dr);
-                digits<S>(fixed_point(x.y, E, S7), di);
-                __nv_bfloat16* pr = row_re + kbase + e;
-                __nv_bfloat16* pi = row_im + kbase + e;
-                const int q = job.ktot;   // the imaginary half of a row starts at ktot
+        const int kw = one_window ? kw_first : build(w0, nw, true);
+        for (int e0 = 0; e0 < kw; e0 += kSliceCT * kSliceCU) {
 #pragma unroll
-                for (int t = 0; t < S; ++t) {
-                    if (role0) {
-                        pr[t * plane] = __float2bfloat16_rn((float)dr[t]);
-                        pr[t * plane + q] = __float2bfloat16_rn((float)di[t]);
+            for (int u = 0; u < kSliceCU; ++u) {
+                const int e = e0 + tid + kSliceCT * u;
+                if (e < kw) {
+                    double2 x;
+                    if (cached) {
+                        x = xr[u];
                     } else {
-                        pr[t * plane] = __float2bfloat16_rn((float)dr[t]);
-                        pr[t * plane + q] = __float2bfloat16_rn((float)(-di[t]));
-                        pi[t * plane] = __float2bfloat16_rn((float)di[t]);
-                        pi[t * plane + q] = __float2bfloat16_rn((float)dr[t]);
+                        const int sgi = seg_of(e, nw);
+                        x = view_load(sv[sgi], e - spre[sgi], use_scale);
+                    }
+                    int dr[S], di[S];
+                    slice_digits<S>(x.x, E, dr);
+                    slice_digits<S>(x.y, E, di);
+                    __nv_bfloat16* pr = row_re + kbase + e;
+                    __nv_bfloat16* pi = row_im + kbase + e;
+#pragma unroll
+                    for (int t = 0; t < S; ++t) {
+                        if (role0) {
+                            pr[t * plane] = __float2bfloat16_rn((float)dr[t]);
+                            pr[t * plane + q] = __float2bfloat16_rn((float)di[t]);
+                        } else {
+                            pr[t * plane] = __float2bfloat16_rn((float)dr[t]);
+                            pr[t * plane + q] = __float2bfloat16_rn((float)(-di[t]));
+                            pi[t * plane] = __float2bfloat16_rn((float)di[t]);
+                            pi[t * plane + q] = __float2bfloat16_rn((float)dr[t]);
+                        }
                     }
                 }
             }
@@ -830,13 +868,13 @@ cudaError_t gemm_launch(const OzStage& st, const GemmArgs& g, cudaStream_t s, co
 
 cudaError_t slice_launch(const OzSliceArgs& sa, const GemmArgs& g, cudaStream_t s, const int* skip_flag, int skip_step) {
     if (sa.nvec_total <= 0) return cudaSuccess;
-    const int warps = kSliceWarps, grid = (sa.nvec_total + warps - 1) / warps;
+    const int grid = sa.nvec_total;   // one CTA per vector
     switch (sa.S) {
-        case 2: launch_pdl(k_slice<2>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
-        case 3: launch_pdl(k_slice<3>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
-        case 4: launch_pdl(k_slice<4>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
-        case 5: launch_pdl(k_slice<5>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
-        case 6: launch_pdl(k_slice<6>, grid, 32 * warps, 0, s, sa, g, skip_flag, skip_step); break;
+        case 2: launch_pdl(k_slice<2>, grid, kSliceCT, 0, s, sa, g, skip_flag, skip_step); break;
+        case 3: launch_pdl(k_slice<3>, grid, kSliceCT, 0, s, sa, g, skip_flag, skip_step); break;
+        case 4: launch_pdl(k_slice<4>, grid, kSliceCT, 0, s, sa, g, skip_flag, skip_step); break;
+        case 5: launch_pdl(k_slice<5>, grid, kSliceCT, 0, s, sa, g, skip_flag, skip_step); break;
+        case 6: launch_pdl(k_slice<6>, grid, kSliceCT, 0, s, sa, g, skip_flag, skip_step); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
