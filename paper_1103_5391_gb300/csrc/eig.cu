@@ -425,95 +425,120 @@ __device__ __forceinline__ void chunk_rows(int n, int ch, int& r0, int& r1) {
     r1 = min(n, r0 + rows);
 }
 
-__device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[8]) {
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
+// Work items of the element-wise refinement kernels: kOaElems consecutive elements of one sector's
+// n x n block (row-major), the items of a sector contiguous; one CTA of kOaThreads threads per item, each
+// thread with kOaElems / kOaThreads elements whose loads are issued together.  Small CTAs with equal
+// work: FP64 instructions of empty warps would still occupy the slow FP64 pipe.
+constexpr int kOaThreads = 64;
+constexpr int kOaElems = 256;
+constexpr int kOaPer = kOaElems / kOaThreads;
+struct OaTables {
+    const int4* items;   // (sector, e0, e1, -)
+    const int* first;    // per sector: its first item; first[ns] = number of items
+    double* part;        // per item: partial squared norms (||S - diag(lambda)||^2, ||I - G||^2)
+    double* delta;       // per sector: the cluster threshold of this iteration
+    int* count;          // per sector: items done (reset by the last one)
+};
+
+// lambda_i = Re S_ii / Re G_ii for the item's diagonal elements and the item's partial squared Frobenius
+// norms of S - diag(lambda) and R = I - G; the last item of a sector to finish sums the sector's
+// partials in item order and writes delta = 2 (||S - diag(lambda)||_F + ||rho||_F ||R||_F).
+__global__ void __launch_bounds__(kOaThreads) k_oa_norms(const cplx* __restrict__ S, const cplx* __restrict__ G,
+                                                         double* __restrict__ lam, const double* __restrict__ rho_fro,
+                                                         OaTables oa, const int* __restrict__ n_iter, int it, EigTables tb) {
+    pdl_enter();
+    if (it >= *n_iter) return;   // refinement already converged
+    const int4 item = oa.items[blockIdx.x];
+    const int sct = item.x, n = tb.dims[sct];
+    const int64_t off = tb.off[sct], eo = tb.eoff[sct];
+    __shared__ double red[2][kOaThreads / 32];
+    double2 sv[kOaPer], g[kOaPer];
+#pragma unroll
+    for (int u = 0; u < kOaPer; ++u) {
+        const int e = item.y + threadIdx.x + kOaThreads * u;
+        if (e < item.z) { sv[u] = S[off + e]; g[u] = G[off + e]; }
     }
-    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = a; red[1][threadIdx.x >> 5] = b; }
+    double offS = 0.0, rr = 0.0;
+#pragma unroll
+    for (int u = 0; u < kOaPer; ++u) {
+        const int e = item.y + threadIdx.x + kOaThreads * u;
+        if (e < item.z) {
+            const int i = e / n, j = e - i * n;
+            if (i == j) {
+                const double l = sv[u].x / g[u].x;
+                lam[eo + i] = l;
+                sv[u].x -= l;
+            }
+            offS += sv[u].x * sv[u].x + sv[u].y * sv[u].y;
+            const double rx = (i == j ? 1.0 : 0.0) - g[u].x, ry = -g[u].y;
+            rr += rx * rx + ry * ry;
+        }
+    }
+    const int w = threadIdx.x >> 5;
+    if (item.y + w * 32 < item.z) {   // warps without elements skip the FP64 shuffle tree
+        for (int o = 16; o > 0; o >>= 1) {
+            offS += __shfl_xor_sync(0xffffffffu, offS, o);
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][w] = offS; red[1][w] = rr; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        a = 0.0; b = 0.0;
-        for (int k = 0; k < (int)(blockDim.x / 32); ++k) { a += red[0][k]; b += red[1][k]; }
-    }
-}
-
-// lambda_i = Re S_ii / Re G_ii for the chunk's rows; partial squared Frobenius norms of S - diag(lambda)
-// and R = I - G over the chunk's rows into part[(sector, chunk)].
-__global__ void __launch_bounds__(256) k_oa_norms(const cplx* __restrict__ S, const cplx* __restrict__ G,
-                                                  double* __restrict__ lam, double* __restrict__ part,
-                                                  const int* __restrict__ n_iter, int it, EigTables tb) {
-    pdl_enter();
-    if (it >= *n_iter) return;   // refinement already converged
-    const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
-    const int64_t off = tb.off[sct], eo = tb.eoff[sct];
-    __shared__ double red[2][8];
-    int r0, r1;
-    chunk_rows(n, ch, r0, r1);
-    double offS = 0.0, rr = 0.0;
-    for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
-        const int i = r0 + e / n, j = e % n;
-        double2 sv = S[off + (int64_t)i * n + j];
-        const double2 g = G[off + (int64_t)i * n + j];
-        if (i == j) {
-            const double l = sv.x / g.x;
-            lam[eo + i] = l;
-            sv.x -= l;
+        double a = red[0][0], b = red[1][0];
+        for (int k = 1; k < kOaThreads / 32; ++k) { a += red[0][k]; b += red[1][k]; }
+        oa.part[2 * blockIdx.x] = a;
+        oa.part[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        const int i0 = oa.first[sct], i1 = oa.first[sct + 1];
+        if (atomicAdd(oa.count + sct, 1) == i1 - i0 - 1) {
+            __threadfence();
+            a = 0.0; b = 0.0;
+            for (int k = i0; k < i1; ++k) { a += __ldcg(oa.part + 2 * k); b += __ldcg(oa.part + 2 * k + 1); }
+            oa.delta[sct] = 2.0 * (sqrt(a) + rho_fro[sct] * sqrt(b));
+            oa.count[sct] = 0;   // every item of the sector has arrived: ready for the next iteration
         }
-        offS += sv.x * sv.x + sv.y * sv.y;
-        const double rx = (i == j ? 1.0 : 0.0) - g.x, ry = -g.y;
-        rr += rx * rx + ry * ry;
-    }
-    block_sum2(offS, rr, red);
-    if (threadIdx.x == 0) {
-        part[2 * ((int64_t)sct * kRowChunks + ch)] = offS;
-        part[2 * ((int64_t)sct * kRowChunks + ch) + 1] = rr;
     }
 }
 
-// Rows of E^H for the chunk (the update adds the identity).  With S and R = I - G Hermitian and lambda real, the
-// conjugate of E_ji = (S_ji + lambda_i R_ji) / (lambda_i - lambda_j) is
+// The item's elements of E^H (the update adds the identity).  With S and R = I - G Hermitian and lambda real,
+// the conjugate of E_ji = (S_ji + lambda_i R_ji) / (lambda_i - lambda_j) is
 // (S_ij + lambda_i R_ij) / (lambda_i - lambda_j), and that of the cluster value R_ji / 2 is R_ij / 2.
-// delta = 2 (||S - diag(lambda)||_F + ||rho||_F ||R||_F), partial sums added in a fixed order.
-__global__ void __launch_bounds__(256) k_oa_update(const cplx* __restrict__ S, const cplx* __restrict__ G,
-                                                   const double* __restrict__ lam, const double* __restrict__ part,
-                                                   const double* __restrict__ rho_fro, cplx* __restrict__ E1h,
-                                                   int* __restrict__ n_iter, int* __restrict__ flags, int it, EigTables tb) {
+__global__ void __launch_bounds__(kOaThreads) k_oa_update(const cplx* __restrict__ S, const cplx* __restrict__ G,
+                                                          const double* __restrict__ lam, OaTables oa,
+                                                          const double* __restrict__ rho_fro, cplx* __restrict__ E1h,
+                                                          int* __restrict__ n_iter, int* __restrict__ flags, int it, EigTables tb) {
     pdl_enter();
     if (it >= *n_iter) return;   // refinement already converged
-    const int sct = blockIdx.x, ch = blockIdx.y, n = tb.dims[sct];
+    const int4 item = oa.items[blockIdx.x];
+    const int sct = item.x, n = tb.dims[sct];
     const int64_t off = tb.off[sct], eo = tb.eoff[sct];
-    int r0, r1;
-    chunk_rows(n, ch, r0, r1);
-    if (r0 >= r1) return;
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < kRowChunks; ++k) {
-        a += part[2 * ((int64_t)sct * kRowChunks + k)];
-        b += part[2 * ((int64_t)sct * kRowChunks + k) + 1];
+    const double delta = oa.delta[sct], floor_s = (double)kReseedFloor * rho_fro[sct];
+    double2 sv[kOaPer], g[kOaPer];
+#pragma unroll
+    for (int u = 0; u < kOaPer; ++u) {
+        const int e = item.y + threadIdx.x + kOaThreads * u;
+        if (e < item.z) { sv[u] = S[off + e]; g[u] = G[off + e]; }
     }
-    const double delta = 2.0 * (sqrt(a) + rho_fro[sct] * sqrt(b));
     bool big = false, clus = false;
-    const double floor_s = (double)kReseedFloor * rho_fro[sct];
-    for (int e = threadIdx.x; e < (r1 - r0) * n; e += blockDim.x) {
-        const int i = r0 + e / n, j = e % n;
-        const int64_t x = off + (int64_t)i * n + j;
-        const double2 g = G[x];
-        const double2 r = make_double2((i == j ? 1.0 : 0.0) - g.x, -g.y);
-        double2 ev;
-        const double li = lam[eo + i], lj = lam[eo + j];
-        if (i != j && fabs(li - lj) > delta) {
-            const double2 sv = S[x];
-            const double inv = 1.0 / (li - lj);
-            ev = make_double2((sv.x + li * r.x) * inv, (sv.y + li * r.y) * inv);
-        } else {
-            ev = make_double2(0.5 * r.x, 0.5 * r.y);
-            if (i != j) {   // clustered pair still coupled: the cluster is not diagonalised by this update
-                const double2 sv = S[x];
-                clus |= fmax(fabs(sv.x), fabs(sv.y)) > floor_s;
+#pragma unroll
+    for (int u = 0; u < kOaPer; ++u) {
+        const int e = item.y + threadIdx.x + kOaThreads * u;
+        if (e < item.z) {
+            const int i = e / n, j = e - i * n;
+            const double2 r = make_double2((i == j ? 1.0 : 0.0) - g[u].x, -g[u].y);
+            double2 ev;
+            const double li = lam[eo + i], lj = lam[eo + j];
+            if (i != j && fabs(li - lj) > delta) {
+                const double inv = 1.0 / (li - lj);
+                ev = make_double2((sv[u].x + li * r.x) * inv, (sv[u].y + li * r.y) * inv);
+            } else {
+                ev = make_double2(0.5 * r.x, 0.5 * r.y);
+                // clustered pair still coupled: the cluster is not diagonalised by this update
+                if (i != j) clus |= fmax(fabs(sv[u].x), fabs(sv[u].y)) > floor_s;
             }
+            big |= fmax(fabs(ev.x), fabs(ev.y)) > kTolE;
+            E1h[off + e] = ev;   // the update adds the identity: W' = (I + E1h) W
         }
-        big |= fmax(fabs(ev.x), fabs(ev.y)) > kTolE;
-        E1h[x] = ev;   // the update adds the identity: W' = (I + E1h) W
     }
     // from the last iteration that always runs on, a correction still above kTolE asks for one more
     if (it >= kRefine - 1 && it + 1 < kMaxRefine && __syncthreads_or(big) && threadIdx.x == 0) atomicMax(n_iter, it + 2);
@@ -560,6 +585,21 @@ __global__ void __launch_bounds__(256) k_eig_sort(const cplx* __restrict__ W_eve
 
 }  // namespace
 
+// Layout of the work-item buffer: items, first (padded to 16 B), per-item partials, per-sector delta and
+// per-sector counters.
+OaTables oa_tables(const EigWork& w) {
+    unsigned char* b = static_cast<unsigned char*>(w.oa);
+    const size_t b_items = (size_t)w.noa * sizeof(int4), b_first = ((size_t)(w.ns + 1) * sizeof(int) + 15) & ~(size_t)15;
+    double* part = reinterpret_cast<double*>(b + b_items + b_first);
+    double* delta = part + 2 * (size_t)w.noa;
+    return OaTables{reinterpret_cast<const int4*>(b), reinterpret_cast<const int*>(b + b_items), part, delta,
+                    reinterpret_cast<int*>(delta + w.ns)};
+}
+size_t oa_bytes(int noa, int ns) {
+    return (size_t)noa * sizeof(int4) + (((size_t)(ns + 1) * sizeof(int) + 15) & ~(size_t)15) +
+           2 * (size_t)noa * sizeof(double) + (size_t)ns * sizeof(double) + (size_t)ns * sizeof(int);
+}
+
 // Buffer ids of the refinement GEMMs (all packed like rho).
 enum { EB_RHO = BUF_EXTRA0, EB_W, EB_AX, EB_S, EB_G, EB_E, EB_WN };
 
@@ -600,7 +640,7 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         int rc = dev_alloc(c, (void**)&w.tables, w.tables_bytes, "eig tables");
         if (!rc) rc = dev_alloc(c, (void**)&w.buf, (size_t)6 * r * sizeof(cplx), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.lam, (size_t)e * sizeof(double), "eig workspace");
-        if (!rc) rc = dev_alloc(c, (void**)&w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double), "eig workspace");
+        if (!rc) rc = dev_alloc(c, (void**)&w.fro, ((size_t)ns + 1) * sizeof(double), "eig workspace");
         if (!rc && maxn > kSmemMaxA) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
         if (!rc && nrec_total) rc = dev_alloc(c, (void**)&w.grec, (size_t)nrec_total * sizeof(float4), "eig rotation record");
         if (!rc) rc = dev_alloc(c, (void**)&w.nrec, (size_t)ns * sizeof(int), "eig rotation record");
@@ -615,6 +655,25 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         if (!big.empty()) memcpy(h + 3 * ns * sizeof(int64_t) + ns * sizeof(int), big.data(), big.size() * sizeof(int));
         rc = cuda_check(c, cudaMemcpy(w.tables, host.data(), host.size(), cudaMemcpyHostToDevice), "eig tables");
         if (rc) return rc;
+        {   // work items of the element-wise refinement kernels (counters start at zero)
+            std::vector<int4> items;
+            std::vector<int> first(ns + 1);
+            for (int k = 0; k < ns; ++k) {
+                first[k] = (int)items.size();
+                const int nn = L.dim[k] * L.dim[k];
+                for (int e0 = 0; e0 < nn; e0 += kOaElems) items.push_back(make_int4(k, e0, std::min(nn, e0 + kOaElems), 0));
+            }
+            first[ns] = (int)items.size();
+            w.noa = (int)items.size();
+            const size_t bytes = oa_bytes(w.noa, ns);
+            rc = dev_alloc(c, &w.oa, bytes, "eig work items");
+            if (rc) return rc;
+            std::vector<unsigned char> ho(bytes, 0);
+            memcpy(ho.data(), items.data(), items.size() * sizeof(int4));
+            memcpy(ho.data() + items.size() * sizeof(int4), first.data(), first.size() * sizeof(int));
+            rc = cuda_check(c, cudaMemcpy(w.oa, ho.data(), bytes, cudaMemcpyHostToDevice), "eig work items");
+            if (rc) return rc;
+        }
         if (w.nbig) {   // replay: 8 rows of V and as many rounds of the record as fit in 48 KB of shared memory
             const int P = maxn_big + (maxn_big & 1);
             const int slab = kReplayRows * (maxn_big | 1) * (int)sizeof(float2);
@@ -686,8 +745,8 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
     cplx* S = w.buf + 3 * w.nrho;
     cplx* G = w.buf + 4 * w.nrho;
     cplx* E1h = w.buf + 5 * w.nrho;
-    double* part = w.fro + ns;
-    int* n_iter = reinterpret_cast<int*>(part + 2 * (size_t)ns * kRowChunks);
+    int* n_iter = reinterpret_cast<int*>(w.fro + ns);
+    const OaTables oat = oa_tables(w);
     launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec, w.jac_smem,
                false, 0, w.stats);
     c->launches += 1;
@@ -712,8 +771,11 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
         e = gemm(w.tl_ax, false);
         if (e == cudaSuccess) e = gemm(w.tl_sg, false);
-        launch_pdl(k_oa_norms, chunks, 256, 0, s, S, G, w.lam, part, n_iter, it, tb);
-        launch_pdl(k_oa_update, chunks, 256, 0, s, S, G, w.lam, part, w.fro, E1h, n_iter, w.flags, it, tb);
+        if (w.noa) {
+            launch_pdl(k_oa_norms, w.noa, kOaThreads, 0, s, S, G, w.lam, (const double*)w.fro, oat, n_iter, it, tb);
+            launch_pdl(k_oa_update, w.noa, kOaThreads, 0, s, S, G, w.lam, oat, (const double*)w.fro, E1h, n_iter, w.flags,
+                       it, tb);
+        }
         if (reseed_iter(it)) {
             launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec,
                        w.jac_smem, true, it, w.stats);
@@ -742,7 +804,8 @@ void release_eig(tdmrg_ctx* c, int side) {
     dev_free(c, w.stats, (size_t)ns * sizeof(int2));
     dev_free(c, w.buf, (size_t)6 * w.nrho * sizeof(cplx));
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
-    dev_free(c, w.fro, ((size_t)ns * (1 + 2 * kRowChunks) + 1) * sizeof(double));
+    dev_free(c, w.fro, ((size_t)ns + 1) * sizeof(double));
+    dev_free(c, w.oa, oa_bytes(w.noa, ns));
     dev_free(c, w.gwork, (size_t)4 * w.nrho * sizeof(float2));
     dev_free(c, w.flags, (size_t)ns * sizeof(int));
     w = EigWork();

@@ -273,6 +273,8 @@ struct EigWork {
     int* nrec = nullptr;        // per sector: rounds recorded by the last Jacobi launch (-1: skipped)
     int2* stats = nullptr;      // per sector: sweeps and SM cycles of the last seed Jacobi
     int nbig = 0, maxn_big = 0, replay_batch = 0, replay_smem = 0;
+    void* oa = nullptr;         // work items of the element-wise refinement kernels, their partials and counters
+    int noa = 0;
     TaskList tl_ax, tl_sg, tl_y;
 };
 
