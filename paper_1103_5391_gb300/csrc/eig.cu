@@ -585,15 +585,15 @@ __global__ void __launch_bounds__(256) k_eig_sort(const cplx* __restrict__ W_eve
 
 }  // namespace
 
-// Layout of the work-item buffer: items, first (padded to 16 B), per-item partials, per-sector delta and
-// per-sector counters.
-OaTables oa_tables(const EigWork& w) {
-    unsigned char* b = static_cast<unsigned char*>(w.oa);
-    const size_t b_items = (size_t)w.noa * sizeof(int4), b_first = ((size_t)(w.ns + 1) * sizeof(int) + 15) & ~(size_t)15;
+// Layout of a group's work-item buffer: items, first (padded to 16 B), per-item partials, per-sector delta
+// and per-sector counters.
+OaTables oa_tables(const EigGroup& g) {
+    unsigned char* b = static_cast<unsigned char*>(g.oa);
+    const size_t b_items = (size_t)g.noa * sizeof(int4), b_first = ((size_t)(g.ns + 1) * sizeof(int) + 15) & ~(size_t)15;
     double* part = reinterpret_cast<double*>(b + b_items + b_first);
-    double* delta = part + 2 * (size_t)w.noa;
+    double* delta = part + 2 * (size_t)g.noa;
     return OaTables{reinterpret_cast<const int4*>(b), reinterpret_cast<const int*>(b + b_items), part, delta,
-                    reinterpret_cast<int*>(delta + w.ns)};
+                    reinterpret_cast<int*>(delta + g.ns)};
 }
 size_t oa_bytes(int noa, int ns) {
     return (size_t)noa * sizeof(int4) + (((size_t)(ns + 1) * sizeof(int) + 15) & ~(size_t)15) +
@@ -602,6 +602,217 @@ size_t oa_bytes(int noa, int ns) {
 
 // Buffer ids of the refinement GEMMs (all packed like rho).
 enum { EB_RHO = BUF_EXTRA0, EB_W, EB_AX, EB_S, EB_G, EB_E, EB_WN };
+
+// Cost model of the split into two groups, in SM cycles: the Jacobi seed of one sector (about 7 sweeps of
+// n - 1 rounds; a round costs ~1300 + 12 n cycles with A and V in shared memory, ~40 n beyond) and the
+// refinement of a sector spread over the GPU (3 iterations of 2 m^3 complex FP64 MACs at ~140 FMA per
+// cycle chip-wide, m = n rounded up to the 16 x 16 x 16 tiles of the grouped GEMM).  Fitted to graph-replay
+// timings of the split sizes on the L=32 m=400 and L=48 m=1000 blocks; it only decides the scheduling.
+double jacobi_cost(int n) { return 7.0 * std::max(n - 1, 0) * (n <= kSmemMaxN ? 1300.0 + 12.0 * n : 40.0 * n); }
+double refine_cost(int n) {
+    const double m = 16.0 * ((n + 15) / 16);
+    return 0.35 * m * m * m;
+}
+
+// Sectors of the first group (run on the second stream): the k with the longest Jacobi seeds, k chosen to
+// minimise max(J_1 + R(first k), J_{k+1} + R(rest)) (J_i the i-th longest seed); empty when one group is
+// predicted within 10 % of the best split.
+std::vector<int> long_sectors(const std::vector<int>& dim) {
+    const int ns = (int)dim.size();
+    std::vector<int> order(ns);
+    for (int k = 0; k < ns; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dim[a] > dim[b]; });
+    double rall = 0.0;
+    for (int k = 0; k < ns; ++k) rall += refine_cost(dim[k]);
+    if (ns < 2) return {};
+    const double one = jacobi_cost(dim[order[0]]) + rall;
+    double best = one, rl = 0.0;
+    int bestk = 0;
+    for (int k = 1; k < ns; ++k) {
+        rl += refine_cost(dim[order[k - 1]]);
+        const double t = std::max(jacobi_cost(dim[order[0]]) + rl, jacobi_cost(dim[order[k]]) + rall - rl);
+        if (t < best) { best = t; bestk = k; }
+    }
+    if (bestk == 0 || best > 0.9 * one) return {};
+    std::vector<int> sel(order.begin(), order.begin() + bestk);
+    std::sort(sel.begin(), sel.end());
+    return sel;
+}
+
+int setup_group(tdmrg_ctx* c, const Side& L, const std::vector<int64_t>& goff, const std::vector<int64_t>& geoff,
+                EigGroup& G) {
+    const int ns = (int)G.sel.size();
+    G.ns = ns;
+    std::vector<int64_t> off(ns), eoff(ns), roff(ns, 0);
+    std::vector<int> dim(ns), big;
+    int64_t nrec_total = 0;
+    int maxn_big = 0;
+    for (int k = 0; k < ns; ++k) {
+        const int q = G.sel[k], n = L.dim[q], P = n + (n & 1);
+        off[k] = goff[q]; eoff[k] = geoff[q]; dim[k] = n;
+        if (!jac_recorded(n)) continue;   // beyond kSmemMaxN: records of up to kMaxSweeps sweeps, V replayed
+        roff[k] = nrec_total;
+        nrec_total += (int64_t)kMaxSweeps * (P - 1) * (P / 2);
+        big.push_back(k);
+        maxn_big = std::max(maxn_big, n);
+    }
+    G.nbig = (int)big.size();
+    G.maxn_big = maxn_big;
+    G.grec_entries = nrec_total;
+    G.tables_bytes = (size_t)ns * (3 * sizeof(int64_t) + sizeof(int)) + big.size() * sizeof(int);
+    int rc = dev_alloc(c, (void**)&G.tables, G.tables_bytes, "eig tables");
+    if (!rc) rc = dev_alloc(c, (void**)&G.fro, ((size_t)ns + 1) * sizeof(double), "eig workspace");
+    if (!rc && nrec_total) rc = dev_alloc(c, (void**)&G.grec, (size_t)nrec_total * sizeof(float4), "eig rotation record");
+    if (!rc) rc = dev_alloc(c, (void**)&G.nrec, (size_t)ns * sizeof(int), "eig rotation record");
+    if (!rc) rc = dev_alloc(c, (void**)&G.stats, (size_t)ns * sizeof(int2), "eig statistics");
+    if (!rc) rc = dev_alloc(c, (void**)&G.flags, (size_t)ns * sizeof(int), "eig workspace");
+    if (rc) return rc;
+    std::vector<unsigned char> host(G.tables_bytes);
+    unsigned char* h = host.data();
+    memcpy(h, off.data(), ns * sizeof(int64_t));
+    memcpy(h + ns * sizeof(int64_t), eoff.data(), ns * sizeof(int64_t));
+    memcpy(h + 2 * ns * sizeof(int64_t), roff.data(), ns * sizeof(int64_t));
+    memcpy(h + 3 * ns * sizeof(int64_t), dim.data(), ns * sizeof(int));
+    if (!big.empty()) memcpy(h + 3 * ns * sizeof(int64_t) + ns * sizeof(int), big.data(), big.size() * sizeof(int));
+    rc = cuda_check(c, cudaMemcpy(G.tables, host.data(), host.size(), cudaMemcpyHostToDevice), "eig tables");
+    if (rc) return rc;
+    {   // work items of the element-wise refinement kernels (counters start at zero)
+        std::vector<int4> items;
+        std::vector<int> first(ns + 1);
+        for (int k = 0; k < ns; ++k) {
+            first[k] = (int)items.size();
+            const int nn = dim[k] * dim[k];
+            for (int e0 = 0; e0 < nn; e0 += kOaElems) items.push_back(make_int4(k, e0, std::min(nn, e0 + kOaElems), 0));
+        }
+        first[ns] = (int)items.size();
+        G.noa = (int)items.size();
+        const size_t bytes = oa_bytes(G.noa, ns);
+        rc = dev_alloc(c, &G.oa, bytes, "eig work items");
+        if (rc) return rc;
+        std::vector<unsigned char> ho(bytes, 0);
+        memcpy(ho.data(), items.data(), items.size() * sizeof(int4));
+        memcpy(ho.data() + items.size() * sizeof(int4), first.data(), first.size() * sizeof(int));
+        rc = cuda_check(c, cudaMemcpy(G.oa, ho.data(), bytes, cudaMemcpyHostToDevice), "eig work items");
+        if (rc) return rc;
+    }
+    if (G.nbig) {   // replay: 8 rows of V and as many rounds of the record as fit in 48 KB of shared memory
+        const int P = maxn_big + (maxn_big & 1);
+        const int slab = kReplayRows * (maxn_big | 1) * (int)sizeof(float2);
+        G.replay_batch = std::max(1, (48 * 1024 - slab) / ((P / 2) * (int)sizeof(float4)));
+        G.replay_smem = G.replay_batch * (P / 2) * (int)sizeof(float4) + slab;
+    }
+    // task lists: AX = rho W^H; S = W AX and G = W W^H; W' = E1h W
+    struct Prod { int cbuf, abuf, bbuf; int8_t opb, herm; };
+    auto one = [&](TaskList& tl, std::initializer_list<Prod> prods) {
+        tl.tasks.clear(); tl.segs.clear();
+        for (int k = 0; k < ns; ++k) {
+            const int n = dim[k];
+            for (const Prod& pr : prods) {
+                Task t{};
+                t.c_off = off[k]; t.c_buf = (int8_t)pr.cbuf; t.ldc = n; t.M = n; t.N = n; t.beta = 0;
+                t.herm = pr.herm;
+                t.seg_begin = (int)tl.segs.size();
+                // K in chunks of kKChunk: split-K over the chunks spreads a sector's FP64 work over
+                // several SMs (the per-SM FP64 rate is the limit, not the tile count)
+                for (int k0 = 0; k0 < n; k0 += kKChunk) {
+                    Seg sg{};
+                    sg.a_off = off[k] + k0; sg.a_buf = (int8_t)pr.abuf; sg.lda = n;
+                    sg.b_off = off[k] + (pr.opb == OPB_N ? (int64_t)k0 * n : (int64_t)k0);
+                    sg.b_buf = (int8_t)pr.bbuf; sg.ldb = n; sg.opb = pr.opb;
+                    sg.K = std::min(kKChunk, n - k0); sg.scale = make_double2(1.0, 0.0); sg.dscale = -1;
+                    tl.segs.push_back(sg);
+                }
+                t.seg_end = (int)tl.segs.size();
+                tl.tasks.push_back(t);
+            }
+        }
+        make_tiles(tl, kTileF64, kTileF64, kKChunk);
+        return upload(c, tl);
+    };
+    // shared memory of the Jacobi launch: the most any sector asks for (A, V and a whole sweep of
+    // rotation records), capped; every sector then holds at least one round of records
+    int smem = 0;
+    for (int k = 0; k < ns; ++k) {
+        const int n = dim[k], P = n + (n & 1);
+        smem = std::max(smem, jac_base_bytes(n) + 32 * (P / 2) * (P - 1));
+    }
+    G.jac_smem = std::min(smem, kJacSmemCap);
+    for (int k = 0; k < ns && !rc; ++k)
+        if (dim[k] > 1 && jac_chunk(dim[k], G.jac_smem) < 1) rc = fail(c, TDMRG_EINVAL, "rho_eig: Jacobi shared memory");
+    // S = W rho W^H and G = W W^H are Hermitian: lower tiles plus mirror
+    if (!rc) rc = one(G.tl_ax, {{EB_AX, EB_RHO, EB_W, OPB_C, 0}});
+    if (!rc) rc = one(G.tl_sg, {{EB_S, EB_W, EB_AX, OPB_N, 1}, {EB_G, EB_W, EB_W, OPB_C, 1}});
+    if (!rc) rc = one(G.tl_y, {{EB_WN, EB_E, EB_W, OPB_N, 0}});
+    return rc;
+}
+
+// Seed, refinement and sort of one group's sectors on stream s.
+cudaError_t launch_group(tdmrg_ctx* c, EigWork& w, EigGroup& G, const cplx* rho, double* evals, cplx* evecs, cudaStream_t s) {
+    const int ns = G.ns;
+    const int64_t* t64 = (const int64_t*)G.tables;
+    const int* dims = (const int*)(t64 + 3 * ns);
+    EigTables tb{t64, t64 + ns, t64 + 2 * ns, dims, dims + ns};
+    // V of the record-mode sectors after each Jacobi launch (seed or re-seed)
+    auto replay = [&](cplx* dst, bool rel) {
+        if (!G.nbig) return;
+        const dim3 grid(G.nbig, (G.maxn_big + kReplayRows - 1) / kReplayRows);
+        launch_pdl(k_jacobi_replay, grid, kReplayThreads, G.replay_smem, s, G.grec, G.nrec, dst, tb, G.replay_batch, rel);
+        c->launches++;
+    };
+    cplx* W = w.buf;
+    cplx* Wn = w.buf + w.nrho;
+    cplx* AX = w.buf + 2 * w.nrho;
+    cplx* S = w.buf + 3 * w.nrho;
+    cplx* Gm = w.buf + 4 * w.nrho;
+    cplx* E1h = w.buf + 5 * w.nrho;
+    int* n_iter = reinterpret_cast<int*>(G.fro + ns);
+    const OaTables oat = oa_tables(G);
+    launch_pdl(k_jacobi32, ns, JT, G.jac_smem, s, rho, W, G.fro, n_iter, G.flags, tb, w.gwork, G.grec, G.nrec, G.jac_smem,
+               false, 0, G.stats);
+    c->launches += 1;
+    replay(W, false);
+    GemmArgs a{};
+    a.dscale = c->dscale;
+    a.bufs[EB_RHO] = const_cast<cplx*>(rho);
+    a.bufs[EB_AX] = AX; a.bufs[EB_S] = S; a.bufs[EB_G] = Gm; a.bufs[EB_E] = E1h;
+    const cplx* W_even = W;
+    const cplx* W_odd = Wn;
+    int it = 0;
+    // iterations past kRefine run on the device only when the previous correction asked for them
+    auto gemm = [&](TaskList& tl, bool corr) {
+        a.tasks = tl.d_tasks; a.segs = tl.d_segs; a.tiles = tl.d_tiles; a.ntiles = (int)tl.tiles.size();
+        a.partials = tl.d_partials; a.counters = tl.d_counters;
+        c->launches++;
+        return launch_gemm_f64(a, s, it < kRefine ? nullptr : n_iter, it, corr);
+    };
+    const dim3 chunks(ns, kRowChunks);
+    cudaError_t e = cudaGetLastError();
+    for (; it < kMaxRefine && e == cudaSuccess; ++it) {
+        a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
+        e = gemm(G.tl_ax, false);
+        if (e == cudaSuccess) e = gemm(G.tl_sg, false);
+        if (G.noa) {
+            launch_pdl(k_oa_norms, G.noa, kOaThreads, 0, s, S, Gm, w.lam, (const double*)G.fro, oat, n_iter, it, tb);
+            launch_pdl(k_oa_update, G.noa, kOaThreads, 0, s, S, Gm, w.lam, oat, (const double*)G.fro, E1h, n_iter, G.flags,
+                       it, tb);
+        }
+        if (reseed_iter(it)) {
+            launch_pdl(k_jacobi32, ns, JT, G.jac_smem, s, S, E1h, G.fro, n_iter, G.flags, tb, w.gwork, G.grec, G.nrec,
+                       G.jac_smem, true, it, G.stats);
+            c->launches++;
+            replay(E1h, true);
+        }
+        if (e == cudaSuccess) e = gemm(G.tl_y, true);
+        c->launches += 2;
+        std::swap(W, Wn);
+    }
+    if (e == cudaSuccess) {
+        launch_pdl(k_eig_sort, chunks, 256, 0, s, W_even, W_odd, n_iter, w.lam, evecs, evals, tb);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    return e;
+}
 
 int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs) {
     const Side& L = c->side[side];
@@ -620,194 +831,66 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         }
         if (maxn > kMaxEigN) return fail(c, TDMRG_EINVAL, "rho_eig: sector dimension above 512");
         w.nrho = r; w.nev = e; w.maxn = maxn; w.ns = ns;
-        // sectors beyond kSmemMaxN: rotation records of up to kMaxSweeps sweeps, V from k_jacobi_replay
-        std::vector<int64_t> roff(ns, 0);
-        std::vector<int> big;
-        int64_t nrec_total = 0;
-        int maxn_big = 0;
-        for (int k = 0; k < ns; ++k) {
-            const int n = L.dim[k], P = n + (n & 1);
-            if (!jac_recorded(n)) continue;
-            roff[k] = nrec_total;
-            nrec_total += (int64_t)kMaxSweeps * (P - 1) * (P / 2);
-            big.push_back(k);
-            maxn_big = std::max(maxn_big, n);
-        }
-        w.nbig = (int)big.size();
-        w.maxn_big = maxn_big;
-        w.grec_entries = nrec_total;
-        w.tables_bytes = (size_t)ns * (3 * sizeof(int64_t) + sizeof(int)) + big.size() * sizeof(int);
-        int rc = dev_alloc(c, (void**)&w.tables, w.tables_bytes, "eig tables");
-        if (!rc) rc = dev_alloc(c, (void**)&w.buf, (size_t)6 * r * sizeof(cplx), "eig workspace");
+        int rc = dev_alloc(c, (void**)&w.buf, (size_t)6 * r * sizeof(cplx), "eig workspace");
         if (!rc) rc = dev_alloc(c, (void**)&w.lam, (size_t)e * sizeof(double), "eig workspace");
-        if (!rc) rc = dev_alloc(c, (void**)&w.fro, ((size_t)ns + 1) * sizeof(double), "eig workspace");
         if (!rc && maxn > kSmemMaxA) rc = dev_alloc(c, (void**)&w.gwork, (size_t)4 * r * sizeof(float2), "eig workspace");
-        if (!rc && nrec_total) rc = dev_alloc(c, (void**)&w.grec, (size_t)nrec_total * sizeof(float4), "eig rotation record");
-        if (!rc) rc = dev_alloc(c, (void**)&w.nrec, (size_t)ns * sizeof(int), "eig rotation record");
-        if (!rc) rc = dev_alloc(c, (void**)&w.stats, (size_t)ns * sizeof(int2), "eig statistics");
-        if (rc) return rc;
-        std::vector<unsigned char> host(w.tables_bytes);
-        unsigned char* h = host.data();
-        memcpy(h, off.data(), ns * sizeof(int64_t));
-        memcpy(h + ns * sizeof(int64_t), eoff.data(), ns * sizeof(int64_t));
-        memcpy(h + 2 * ns * sizeof(int64_t), roff.data(), ns * sizeof(int64_t));
-        memcpy(h + 3 * ns * sizeof(int64_t), L.dim.data(), ns * sizeof(int));
-        if (!big.empty()) memcpy(h + 3 * ns * sizeof(int64_t) + ns * sizeof(int), big.data(), big.size() * sizeof(int));
-        rc = cuda_check(c, cudaMemcpy(w.tables, host.data(), host.size(), cudaMemcpyHostToDevice), "eig tables");
-        if (rc) return rc;
-        {   // work items of the element-wise refinement kernels (counters start at zero)
-            std::vector<int4> items;
-            std::vector<int> first(ns + 1);
-            for (int k = 0; k < ns; ++k) {
-                first[k] = (int)items.size();
-                const int nn = L.dim[k] * L.dim[k];
-                for (int e0 = 0; e0 < nn; e0 += kOaElems) items.push_back(make_int4(k, e0, std::min(nn, e0 + kOaElems), 0));
-            }
-            first[ns] = (int)items.size();
-            w.noa = (int)items.size();
-            const size_t bytes = oa_bytes(w.noa, ns);
-            rc = dev_alloc(c, &w.oa, bytes, "eig work items");
-            if (rc) return rc;
-            std::vector<unsigned char> ho(bytes, 0);
-            memcpy(ho.data(), items.data(), items.size() * sizeof(int4));
-            memcpy(ho.data() + items.size() * sizeof(int4), first.data(), first.size() * sizeof(int));
-            rc = cuda_check(c, cudaMemcpy(w.oa, ho.data(), bytes, cudaMemcpyHostToDevice), "eig work items");
-            if (rc) return rc;
-        }
-        if (w.nbig) {   // replay: 8 rows of V and as many rounds of the record as fit in 48 KB of shared memory
-            const int P = maxn_big + (maxn_big & 1);
-            const int slab = kReplayRows * (maxn_big | 1) * (int)sizeof(float2);
-            w.replay_batch = std::max(1, (48 * 1024 - slab) / ((P / 2) * (int)sizeof(float4)));
-            w.replay_smem = w.replay_batch * (P / 2) * (int)sizeof(float4) + slab;
-        }
-        // task lists: AX = rho W^H; S = W AX and G = W W^H; W' = E1h W
-        struct Prod { int cbuf, abuf, bbuf; int8_t opb, herm; };
-        auto one = [&](TaskList& tl, std::initializer_list<Prod> prods) {
-            tl.tasks.clear(); tl.segs.clear();
-            for (int k = 0; k < ns; ++k) {
-                const int n = L.dim[k];
-                for (const Prod& pr : prods) {
-                    Task t{};
-                    t.c_off = off[k]; t.c_buf = (int8_t)pr.cbuf; t.ldc = n; t.M = n; t.N = n; t.beta = 0;
-                    t.herm = pr.herm;
-                    t.seg_begin = (int)tl.segs.size();
-                    // K in chunks of kKChunk: split-K over the chunks spreads a sector's FP64 work over
-                    // several SMs (the per-SM FP64 rate is the limit, not the tile count)
-                    for (int k0 = 0; k0 < n; k0 += kKChunk) {
-                        Seg sg{};
-                        sg.a_off = off[k] + k0; sg.a_buf = (int8_t)pr.abuf; sg.lda = n;
-                        sg.b_off = off[k] + (pr.opb == OPB_N ? (int64_t)k0 * n : (int64_t)k0);
-                        sg.b_buf = (int8_t)pr.bbuf; sg.ldb = n; sg.opb = pr.opb;
-                        sg.K = std::min(kKChunk, n - k0); sg.scale = make_double2(1.0, 0.0); sg.dscale = -1;
-                        tl.segs.push_back(sg);
-                    }
-                    t.seg_end = (int)tl.segs.size();
-                    tl.tasks.push_back(t);
-                }
-            }
-            make_tiles(tl, kTileF64, kTileF64, kKChunk);
-            return upload(c, tl);
-        };
         // the opt-in is a property of the kernel on the device, shared by every context: always the maximum
-        if (!rc) rc = dev_alloc(c, (void**)&w.flags, (size_t)ns * sizeof(int), "eig workspace");
         if (!rc) rc = cuda_check(c, cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacSmemCap),
                                  "eig smem");
-        // shared memory of the Jacobi launch: the most any sector asks for (A, V and a whole sweep of
-        // rotation records), capped; every sector then holds at least one round of records
-        int smem = 0;
-        for (int k = 0; k < ns; ++k) {
-            const int n = L.dim[k], P = n + (n & 1);
-            smem = std::max(smem, jac_base_bytes(n) + 32 * (P / 2) * (P - 1));
+        if (rc) return rc;
+        // the longest Jacobi seeds on a second stream, beside the other sectors' seeds and refinement
+        const std::vector<int> lng = long_sectors(L.dim);
+        std::vector<char> in_long(ns, 0);
+        for (int q : lng) in_long[q] = 1;
+        w.ngroups = lng.empty() ? 1 : 2;
+        w.grp[0].sel.clear();
+        w.grp[1].sel.clear();
+        for (int k = 0; k < ns; ++k) w.grp[w.ngroups == 2 && !in_long[k] ? 1 : 0].sel.push_back(k);
+        for (int g = 0; g < w.ngroups && !rc; ++g) rc = setup_group(c, L, off, eoff, w.grp[g]);
+        if (!rc && w.ngroups == 2) {
+            rc = cuda_check(c, cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking), "eig stream");
+            if (!rc) rc = cuda_check(c, cudaEventCreateWithFlags(&w.fork, cudaEventDisableTiming), "eig stream");
+            if (!rc) rc = cuda_check(c, cudaEventCreateWithFlags(&w.join, cudaEventDisableTiming), "eig stream");
         }
-        w.jac_smem = std::min(smem, kJacSmemCap);
-        for (int k = 0; k < ns && !rc; ++k)
-            if (L.dim[k] > 1 && jac_chunk(L.dim[k], w.jac_smem) < 1) rc = fail(c, TDMRG_EINVAL, "rho_eig: Jacobi shared memory");
-        // S = W rho W^H and G = W W^H are Hermitian: lower tiles plus mirror
-        if (!rc) rc = one(w.tl_ax, {{EB_AX, EB_RHO, EB_W, OPB_C, 0}});
-        if (!rc) rc = one(w.tl_sg, {{EB_S, EB_W, EB_AX, OPB_N, 1}, {EB_G, EB_W, EB_W, OPB_C, 1}});
-        if (!rc) rc = one(w.tl_y, {{EB_WN, EB_E, EB_W, OPB_N, 0}});
         if (rc) return rc;
         w.ready = true;
     }
-    const int64_t* t64 = (const int64_t*)w.tables;
-    const int* dims = (const int*)(t64 + 3 * ns);
-    EigTables tb{t64, t64 + ns, t64 + 2 * ns, dims, dims + ns};
-    // V of the record-mode sectors after each Jacobi launch (seed or re-seed)
-    auto replay = [&](cplx* dst, bool rel) {
-        if (!w.nbig) return;
-        const dim3 grid(w.nbig, (w.maxn_big + kReplayRows - 1) / kReplayRows);
-        launch_pdl(k_jacobi_replay, grid, kReplayThreads, w.replay_smem, s, w.grec, w.nrec, dst, tb, w.replay_batch, rel);
-        c->launches++;
-    };
-    cplx* W = w.buf;
-    cplx* Wn = w.buf + w.nrho;
-    cplx* AX = w.buf + 2 * w.nrho;
-    cplx* S = w.buf + 3 * w.nrho;
-    cplx* G = w.buf + 4 * w.nrho;
-    cplx* E1h = w.buf + 5 * w.nrho;
-    int* n_iter = reinterpret_cast<int*>(w.fro + ns);
-    const OaTables oat = oa_tables(w);
-    launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, rho, W, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec, w.jac_smem,
-               false, 0, w.stats);
-    c->launches += 1;
-    replay(W, false);
-    GemmArgs a{};
-    a.dscale = c->dscale;
-    a.bufs[EB_RHO] = const_cast<cplx*>(rho);
-    a.bufs[EB_AX] = AX; a.bufs[EB_S] = S; a.bufs[EB_G] = G; a.bufs[EB_E] = E1h;
-    const cplx* W_even = W;
-    const cplx* W_odd = Wn;
-    int it = 0;
-    // iterations past kRefine run on the device only when the previous correction asked for them
-    auto gemm = [&](TaskList& tl, bool corr) {
-        a.tasks = tl.d_tasks; a.segs = tl.d_segs; a.tiles = tl.d_tiles; a.ntiles = (int)tl.tiles.size();
-        a.partials = tl.d_partials; a.counters = tl.d_counters;
-        c->launches++;
-        return launch_gemm_f64(a, s, it < kRefine ? nullptr : n_iter, it, corr);
-    };
-    const dim3 chunks(ns, kRowChunks);
-    cudaError_t e = cudaGetLastError();
-    for (; it < kMaxRefine && e == cudaSuccess; ++it) {
-        a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
-        e = gemm(w.tl_ax, false);
-        if (e == cudaSuccess) e = gemm(w.tl_sg, false);
-        if (w.noa) {
-            launch_pdl(k_oa_norms, w.noa, kOaThreads, 0, s, S, G, w.lam, (const double*)w.fro, oat, n_iter, it, tb);
-            launch_pdl(k_oa_update, w.noa, kOaThreads, 0, s, S, G, w.lam, oat, (const double*)w.fro, E1h, n_iter, w.flags,
-                       it, tb);
-        }
-        if (reseed_iter(it)) {
-            launch_pdl(k_jacobi32, ns, JT, w.jac_smem, s, S, E1h, w.fro, n_iter, w.flags, tb, w.gwork, w.grec, w.nrec,
-                       w.jac_smem, true, it, w.stats);
-            c->launches++;
-            replay(E1h, true);
-        }
-        if (e == cudaSuccess) e = gemm(w.tl_y, true);
-        c->launches += 2;
-        std::swap(W, Wn);
-    }
-    if (e == cudaSuccess) {
-        launch_pdl(k_eig_sort, chunks, 256, 0, s, W_even, W_odd, n_iter, w.lam, evecs, evals, tb);
-        c->launches++;
-        e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (w.ngroups == 1) {
+        e = launch_group(c, w, w.grp[0], rho, evals, evecs, s);
+    } else {   // fork and join by events (kept as dependencies when the caller's stream is being captured)
+        e = cudaEventRecord(w.fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.fork, 0);
+        if (e == cudaSuccess) e = launch_group(c, w, w.grp[0], rho, evals, evecs, w.side);
+        if (e == cudaSuccess) e = launch_group(c, w, w.grp[1], rho, evals, evecs, s);
+        if (e == cudaSuccess) e = cudaEventRecord(w.join, w.side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
     }
     return cuda_check(c, e, "rho_eig launch");
 }
 
 void release_eig(tdmrg_ctx* c, int side) {
     EigWork& w = c->eig[side];
-    release(c, w.tl_ax); release(c, w.tl_sg); release(c, w.tl_y);
-    const int ns = w.ns;
-    dev_free(c, w.tables, w.tables_bytes);
-    dev_free(c, w.grec, (size_t)w.grec_entries * sizeof(float4));
-    dev_free(c, w.nrec, (size_t)ns * sizeof(int));
-    dev_free(c, w.stats, (size_t)ns * sizeof(int2));
+    for (int g = 0; g < 2; ++g) {
+        EigGroup& G = w.grp[g];
+        release(c, G.tl_ax); release(c, G.tl_sg); release(c, G.tl_y);
+        dev_free(c, G.tables, G.tables_bytes);
+        dev_free(c, G.grec, (size_t)G.grec_entries * sizeof(float4));
+        dev_free(c, G.nrec, (size_t)G.ns * sizeof(int));
+        dev_free(c, G.stats, (size_t)G.ns * sizeof(int2));
+        dev_free(c, G.fro, ((size_t)G.ns + 1) * sizeof(double));
+        dev_free(c, G.flags, (size_t)G.ns * sizeof(int));
+        dev_free(c, G.oa, oa_bytes(G.noa, G.ns));
+    }
     dev_free(c, w.buf, (size_t)6 * w.nrho * sizeof(cplx));
     dev_free(c, w.lam, (size_t)w.nev * sizeof(double));
-    dev_free(c, w.fro, ((size_t)ns + 1) * sizeof(double));
-    dev_free(c, w.oa, oa_bytes(w.noa, ns));
     dev_free(c, w.gwork, (size_t)4 * w.nrho * sizeof(float2));
-    dev_free(c, w.flags, (size_t)ns * sizeof(int));
+    if (w.side) {   // work queued on the second stream ends before it is destroyed
+        cudaStreamSynchronize(w.side);
+        cudaStreamDestroy(w.side);
+    }
+    if (w.fork) cudaEventDestroy(w.fork);
+    if (w.join) cudaEventDestroy(w.join);
     w = EigWork();
 }
 
@@ -819,15 +902,18 @@ extern "C" int tdmrg_eig_stats(tdmrg_ctx* c, int side, int32_t* sweeps, int64_t*
     if (!c) return fail(nullptr, TDMRG_EINVAL, "null context");
     if (side != 0 && side != 1) return fail(c, TDMRG_EINVAL, "eig_stats: side must be 0 or 1");
     const EigWork& w = c->eig[side];
-    if (!w.ready || !w.stats) return fail(c, TDMRG_ESTATE, "eig_stats: no eigendecomposition on this side yet");
-    std::vector<int2> h(w.ns);
+    if (!w.ready) return fail(c, TDMRG_ESTATE, "eig_stats: no eigendecomposition on this side yet");
     DeviceGuard g(c->opts.device);
-    int rc = cuda_check(c, cudaMemcpyAsync(h.data(), w.stats, w.ns * sizeof(int2), cudaMemcpyDeviceToHost, c->stream),
-                        "eig_stats");
-    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "eig_stats");
-    for (int k = 0; k < w.ns && !rc; ++k) {
-        if (sweeps) sweeps[k] = h[k].x;
-        if (cycles) cycles[k] = h[k].y;
+    int rc = TDMRG_OK;
+    for (int gi = 0; gi < w.ngroups && !rc; ++gi) {
+        const EigGroup& G = w.grp[gi];
+        std::vector<int2> h(G.ns);
+        rc = cuda_check(c, cudaMemcpyAsync(h.data(), G.stats, G.ns * sizeof(int2), cudaMemcpyDeviceToHost, c->stream), "eig_stats");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "eig_stats");
+        for (int k = 0; k < G.ns && !rc; ++k) {
+            if (sweeps) sweeps[G.sel[k]] = h[k].x;
+            if (cycles) cycles[G.sel[k]] = h[k].y;
+        }
     }
     return rc;
 }

@@ -255,19 +255,16 @@ struct KrylovWork {     // device workspace of tdmrg_evolve for one (Q, nk)
     size_t segmem_bytes = 0;
 };
 
-// Workspace of the rho_L eigensolver (eig.cu), built once per left block.
-struct EigWork {
-    bool ready = false;
-    int64_t nrho = 0, nev = 0;
-    int maxn = 0, ns = 0;
-    void* tables = nullptr;     // per-sector offsets and dims
-    cplx* buf = nullptr;        // 6 packed matrices: X, AX, Xh, S, G, E1
-    double* lam = nullptr;
-    double* fro = nullptr;
-    float2* gwork = nullptr;    // FP32 Jacobi storage for sectors too large for shared memory
+// One group of sectors of the rho eigensolver (eig.cu): its own tables, Jacobi records, refinement task
+// lists and device-side iteration count, so that two groups run independently on two streams.
+struct EigGroup {
+    std::vector<int> sel;       // the group's sectors (indices into the side's sector list)
+    int ns = 0;
+    void* tables = nullptr;     // per-sector offsets (into the side's packed rho) and dims
+    size_t tables_bytes = 0;
+    double* fro = nullptr;      // per sector ||rho||_F, then the iteration count (int)
     int jac_smem = 0;           // dynamic shared memory of the Jacobi launch
     int* flags = nullptr;       // per sector: re-seed requested by the refinement
-    size_t tables_bytes = 0;
     float4* grec = nullptr;     // Jacobi rotation records of the sectors too large for V in shared memory
     int64_t grec_entries = 0;
     int* nrec = nullptr;        // per sector: rounds recorded by the last Jacobi launch (-1: skipped)
@@ -276,6 +273,21 @@ struct EigWork {
     void* oa = nullptr;         // work items of the element-wise refinement kernels, their partials and counters
     int noa = 0;
     TaskList tl_ax, tl_sg, tl_y;
+};
+
+// Workspace of the rho eigensolver (eig.cu), built once per block.  The sectors form one group, or two
+// (the few largest, whose Jacobi seed is the longest, on a second stream, beside the others).
+struct EigWork {
+    bool ready = false;
+    int64_t nrho = 0, nev = 0;
+    int maxn = 0, ns = 0;
+    cplx* buf = nullptr;        // 6 packed matrices: X, AX, Xh, S, G, E1
+    double* lam = nullptr;
+    float2* gwork = nullptr;    // FP32 Jacobi storage for sectors too large for shared memory
+    int ngroups = 0;
+    EigGroup grp[2];
+    cudaStream_t side = nullptr;            // stream of the first group when there are two
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // Launch of a grouped complex GEMM (gemm_f64.cu / gemm_ozaki.cu).
