@@ -323,13 +323,22 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
     }
     grid_barrier(a.bar, a.status);
     if (!active) return;
-    // (C) beta, stop test, v_{j+1} = (w' - sum h2_k v_k) / beta
+    // (C) beta, stop test, v_{j+1} = (w' - sum h2_k v_k) / beta; the scalars by one thread (FP64
+    // instructions of the other warps would only repeat them on the slow FP64 pipe)
     sum_partials(a.partB, a.nv + 1, h, b0, b1);
-    double b2 = h[a.nv].x;
-    for (int k = 0; k < a.nv; ++k) b2 -= h[k].x * h[k].x + h[k].y * h[k].y;
-    const double beta = sqrt(fmax(b2, 0.0));
-    const double alpha = tri[T_ALPHA + a.j];
-    const bool stop = (a.j == a.nk - 1) || (beta <= a.tol * fmax(1.0, fabs(alpha)));
+    __shared__ double sc[2];
+    if (threadIdx.x == 0) {
+        double b2 = h[a.nv].x;
+        for (int k = 0; k < a.nv; ++k) b2 -= h[k].x * h[k].x + h[k].y * h[k].y;
+        const double bt = sqrt(fmax(b2, 0.0));
+        const double alpha = tri[T_ALPHA + a.j];
+        const bool st = (a.j == a.nk - 1) || (bt <= a.tol * fmax(1.0, fabs(alpha)));
+        sc[0] = bt;
+        sc[1] = st ? 0.0 : 1.0 / bt;
+    }
+    __syncthreads();
+    const double beta = sc[0];
+    const bool stop = sc[1] == 0.0;
     if (stop) {
         if (blockIdx.x == b0 && threadIdx.x == 0) {
             tri[T_BETA + a.j] = beta;
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
         return;
     }
     if (blockIdx.x == b0 && threadIdx.x == 0) tri[T_BETA + a.j] = beta;
-    const double inv = 1.0 / beta;
+    const double inv = sc[1];
     cplx* vnext = const_cast<cplx*>(a.V) + (int64_t)(a.j + 1) * a.n;
     for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
         double2 x = a.w[i];
