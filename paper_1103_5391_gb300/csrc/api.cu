@@ -81,8 +81,8 @@ void drop_krylov(tdmrg_ctx* c) {
         dev_free(c, k.partB, 64 * kRedBlocks * sizeof(double2));
         dev_free(c, k.tri, 128 * sizeof(double));
         dev_free(c, k.flags, 4 * sizeof(int));
-        dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
-        dev_free(c, k.bar, 2 * sizeof(unsigned));
+        dev_free(c, k.coef, (16 + 32) * 32 * sizeof(cplx));
+        dev_free(c, k.bar, 4 * sizeof(unsigned));
         dev_free(c, k.segmem, k.segmem_bytes);
     }
     c->krylov.clear();

@@ -21,6 +21,8 @@ namespace tdmrg {
 namespace {
 
 constexpr int NB = kRedBlocks;   // reduction blocks
+constexpr int kCoefWords = (16 + 32) * 32;   // Krylov coefficients of 16 targets + step exponential columns
+constexpr int kBarWords = 4;                  // grid barrier count and generation, exponential ticket
 constexpr int NT = 256;          // threads per reduction block
 enum { T_ALPHA = 0, T_BETA = 32, T_BETA0 = 64, T_RESID = 65, T_ERR = 66, T_EMIN = 67 };
 
@@ -446,6 +448,82 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, co
     }
 }
 
+// Targets at equally spaced times m dt (m = 0 .. n_v - 1, target order[m] at m dt): the same c_x as
+// k_tridiag_exp, with the chain of dependent Taylor terms one time step long instead of n_v - 1.  Block c
+// forms column c of the step exponential E = e^{-i T dt} (the Taylor substeps of k_tridiag_exp from e_c,
+// lane l = row l); the last block to finish (ticket) takes u_0 = e_0, u_m = E u_{m-1}.
+struct StepTimes { double dt; int n_v, xmax; int order[16]; };
+__global__ void __launch_bounds__(32) k_tridiag_exp_eq(double* __restrict__ tri, const int* __restrict__ flags,
+                                                        StepTimes st, cplx* __restrict__ coef, cplx* __restrict__ mexp,
+                                                        unsigned* __restrict__ ticket) {
+    pdl_enter();
+    const int l = threadIdx.x, c = blockIdx.x;
+    const int n = flags[0];
+    if (c < n) {
+        const double al = l < n ? tri[T_ALPHA + l] : 0.0;
+        const double bl = l < n - 1 ? tri[T_BETA + l] : 0.0;   // couples l and l + 1
+        double bm = __shfl_up_sync(0xffffffffu, bl, 1);        // couples l - 1 and l
+        if (l == 0) bm = 0.0;
+        double nu = fabs(al) + fabs(bl) + fabs(bm);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nu = fmax(nu, __shfl_xor_sync(0xffffffffu, nu, o));
+        double2 u0 = make_double2(l == c ? 1.0 : 0.0, 0.0);
+        const double span = nu * st.dt;
+        const int S = span > 0.0 ? (int)ceil(0.5 * span) : 0;
+        if (S > 0) {
+            const double h = st.dt / S, xs = nu * h;
+            const int K = xs <= 0.25 ? 12 : xs <= 0.5 ? 15 : xs <= 1.0 ? 18 : 24;
+            for (int sb = 0; sb < S; ++sb) {
+                double2 u = u0, sum = u0;
+                for (int k = 1; k <= K; ++k) {
+                    const double lx = __shfl_up_sync(0xffffffffu, u.x, 1), ly = __shfl_up_sync(0xffffffffu, u.y, 1);
+                    const double rx = __shfl_down_sync(0xffffffffu, u.x, 1), ry = __shfl_down_sync(0xffffffffu, u.y, 1);
+                    const double tx = fma(bl, rx, fma(bm, lx, al * u.x));
+                    const double ty = fma(bl, ry, fma(bm, ly, al * u.y));
+                    const double f = h * kInvK[k];
+                    u = make_double2(f * ty, -f * tx);                      // (-i h / k) T u
+                    sum.x += u.x; sum.y += u.y;
+                }
+                u0 = sum;
+            }
+        }
+        mexp[c * 32 + l] = u0;
+    }
+    __threadfence();
+    unsigned tk = 0;
+    if (l == 0) tk = atomicAdd(ticket, 1u);
+    tk = __shfl_sync(0xffffffffu, tk, 0);
+    if (tk != gridDim.x - 1) return;   // not the last block
+    __threadfence();
+    if (l == 0) *ticket = 0u;          // every block has taken its ticket: ready for the next launch
+    const double b0 = tri[T_BETA0];
+    for (int x = 0; x < st.n_v; ++x) coef[x * 32 + l] = make_double2(0.0, 0.0);
+    if (n <= 0) {
+        if (l == 0) tri[T_ERR] = 0.0;
+        return;
+    }
+    double2 u = make_double2(l == 0 ? 1.0 : 0.0, 0.0);
+    for (int m = 0; m < st.n_v; ++m) {
+        if (m > 0) {   // u <- E u, two partial sums
+            double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+            for (int cc = 0; cc < n; cc += 2) {   // lanes >= n hold u = 0, so column n (if n is odd) adds 0
+                const double ux = __shfl_sync(0xffffffffu, u.x, cc), uy = __shfl_sync(0xffffffffu, u.y, cc);
+                const double vx = __shfl_sync(0xffffffffu, u.x, cc + 1), vy = __shfl_sync(0xffffffffu, u.y, cc + 1);
+                const double2 e = __ldcg(mexp + cc * 32 + l);
+                const double2 f = cc + 1 < n ? __ldcg(mexp + (cc + 1) * 32 + l) : make_double2(0.0, 0.0);
+                a0.x = fma(e.x, ux, fma(-e.y, uy, a0.x));
+                a0.y = fma(e.x, uy, fma(e.y, ux, a0.y));
+                a1.x = fma(f.x, vx, fma(-f.y, vy, a1.x));
+                a1.y = fma(f.x, vy, fma(f.y, vx, a1.y));
+            }
+            u = make_double2(a0.x + a1.x, a0.y + a1.y);
+        }
+        const int x = st.order[m];
+        if (l < n) coef[x * 32 + l] = make_double2(b0 * u.x, b0 * u.y);
+        if (x == st.xmax && l == n - 1) tri[T_ERR] = tri[T_RESID] * b0 * sqrt(u.x * u.x + u.y * u.y);
+    }
+}
+
 // Lowest eigenpair of the Lanczos tridiagonal T (ground-state targeting, Sec. II.B): one thread, FP64.
 // The eigenvalue by bisection on the Sturm count (number of eigenvalues below x from the signs of the
 // LDL^T pivots of T - x), then the eigenvector by inverse iteration (three tridiagonal solves with the
@@ -508,16 +586,17 @@ __global__ void __launch_bounds__(32) k_tridiag_min(double* __restrict__ tri, co
 }
 
 struct TargetPtrs { cplx* p[16]; };
+struct CombineList { cplx* p[8]; int row[8]; };   // targets of one combine launch and their coefficient rows
 
-// targets[x][i] = sum_k coef[x][k] v_k[i] for x in [x0, x0 + NX): one pass over V.  NX is exact (no
+// targets p[x][i] = sum_k coef[row[x]][k] v_k[i] for x < NX: one pass over V.  NX is exact (no
 // predicated FP64 work for absent targets).
 template <int NX>
 __global__ void __launch_bounds__(256) k_combine(const cplx* __restrict__ V, int64_t n, const int* __restrict__ flags,
-                                                  const cplx* __restrict__ coef, int x0, TargetPtrs tg) {
+                                                  const cplx* __restrict__ coef, CombineList tg) {
     pdl_enter();
     __shared__ double2 cf[NX][32];
     const int nu = flags[0];
-    for (int e = threadIdx.x; e < NX * 32; e += blockDim.x) cf[e / 32][e % 32] = coef[(x0 + e / 32) * 32 + e % 32];
+    for (int e = threadIdx.x; e < NX * 32; e += blockDim.x) cf[e / 32][e % 32] = coef[tg.row[e / 32] * 32 + e % 32];
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double2 acc[NX];
@@ -533,27 +612,31 @@ __global__ void __launch_bounds__(256) k_combine(const cplx* __restrict__ V, int
             }
         }
 #pragma unroll
-        for (int x = 0; x < NX; ++x) tg.p[x][i] = acc[x];   // tg holds the pointers from target x0 on
+        for (int x = 0; x < NX; ++x) tg.p[x][i] = acc[x];
     }
 }
 
-cudaError_t launch_combine(const cplx* V, int64_t n, const int* flags, const cplx* coef, int n_v, const TargetPtrs& tg,
-                           int grid, cudaStream_t s) {
-    for (int x0 = 0; x0 < n_v; x0 += 8) {
-        TargetPtrs t{};
-        for (int x = x0; x < n_v; ++x) t.p[x - x0] = tg.p[x];
-        switch (std::min(8, n_v - x0)) {
-            case 1: launch_pdl(k_combine<1>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            case 2: launch_pdl(k_combine<2>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            case 3: launch_pdl(k_combine<3>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            case 4: launch_pdl(k_combine<4>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            case 5: launch_pdl(k_combine<5>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            case 6: launch_pdl(k_combine<6>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            case 7: launch_pdl(k_combine<7>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
-            default: launch_pdl(k_combine<8>, grid, 256, 0, s, V, n, flags, coef, x0, t); break;
+// The targets listed in rows (coefficient row of each), eight per launch; returns the launch count.
+int launch_combine(const cplx* V, int64_t n, const int* flags, const cplx* coef, const std::vector<int>& rows,
+                   const TargetPtrs& tg, int grid, cudaStream_t s) {
+    const int cnt = (int)rows.size();
+    int launches = 0;
+    for (int x0 = 0; x0 < cnt; x0 += 8) {
+        CombineList t{};
+        for (int x = x0; x < std::min(cnt, x0 + 8); ++x) { t.p[x - x0] = tg.p[rows[x]]; t.row[x - x0] = rows[x]; }
+        switch (std::min(8, cnt - x0)) {
+            case 1: launch_pdl(k_combine<1>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            case 2: launch_pdl(k_combine<2>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            case 3: launch_pdl(k_combine<3>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            case 4: launch_pdl(k_combine<4>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            case 5: launch_pdl(k_combine<5>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            case 6: launch_pdl(k_combine<6>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            case 7: launch_pdl(k_combine<7>, grid, 256, 0, s, V, n, flags, coef, t); break;
+            default: launch_pdl(k_combine<8>, grid, 256, 0, s, V, n, flags, coef, t); break;
         }
+        ++launches;
     }
-    return cudaGetLastError();
+    return launches;
 }
 
 // ---- segmented mode: the start vector's norm, v_0 and the targets per segment --------------------
@@ -685,9 +768,11 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
     if (!rc) rc = dev_alloc(c, (void**)&k.partB, 64 * kRedBlocks * sizeof(double2), "Krylov partials");
     if (!rc) rc = dev_alloc(c, (void**)&k.tri, 128 * sizeof(double), "Krylov tridiagonal");
     if (!rc) rc = dev_alloc(c, (void**)&k.flags, 4 * sizeof(int), "Krylov flags");
-    if (!rc) rc = dev_alloc(c, (void**)&k.coef, 16 * 32 * sizeof(cplx), "Krylov coefficients");
-    if (!rc) rc = dev_alloc(c, (void**)&k.bar, 2 * sizeof(unsigned), "Krylov grid barrier");
-    if (!rc) rc = cuda_check(c, cudaMemset(k.bar, 0, 2 * sizeof(unsigned)), "Krylov grid barrier");
+    // coefficients [x][k] of 16 targets, then the columns of the step exponential (32 x 32)
+    if (!rc) rc = dev_alloc(c, (void**)&k.coef, kCoefWords * sizeof(cplx), "Krylov coefficients");
+    // grid barrier (count, generation), then the ticket of k_tridiag_exp_eq
+    if (!rc) rc = dev_alloc(c, (void**)&k.bar, kBarWords * sizeof(unsigned), "Krylov grid barrier");
+    if (!rc) rc = cuda_check(c, cudaMemset(k.bar, 0, kBarWords * sizeof(unsigned)), "Krylov grid barrier");
     if (!rc) {   // co-resident grid of the fused orthogonalisation: at most one block per SM, at most NB
         int per_sm = 0;
         rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lanczos_orth_t<true>, OB, 0), "occupancy");
@@ -701,8 +786,8 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
         dev_free(c, k.partB, 64 * kRedBlocks * sizeof(double2));
         dev_free(c, k.tri, 128 * sizeof(double));
         dev_free(c, k.flags, 4 * sizeof(int));
-        dev_free(c, k.coef, 16 * 32 * sizeof(cplx));
-        dev_free(c, k.bar, 2 * sizeof(unsigned));
+        dev_free(c, k.coef, kCoefWords * sizeof(cplx));
+        dev_free(c, k.bar, kBarWords * sizeof(unsigned));
         return rc;
     }
     c->krylov[key] = k;
@@ -774,12 +859,36 @@ int evolve(tdmrg_ctx* c, int a, int b, const cplx* phi, int n_v, const double* t
     cudaStream_t s = c->stream;
     Times tt{};
     for (int x = 0; x < n_v; ++x) tt.t[x] = t_x[x];
-    launch_pdl(k_tridiag_exp, 1, 32, 0, s, k->tri, k->flags, tt, n_v, k->coef);
+    // equally spaced targets from t = 0 (the TST schedule): one time step's Taylor chain, columns in parallel
+    std::vector<int> ord(n_v);
+    for (int x = 0; x < n_v; ++x) ord[x] = x;
+    std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) { return t_x[p] < t_x[q]; });
+    const double tmax = t_x[ord[n_v - 1]];
+    bool eq = n_v >= 2 && n_v <= 16 && t_x[ord[0]] == 0.0 && t_x[ord[1]] > 0.0;
+    const double dt = eq ? t_x[ord[1]] : 0.0;
+    for (int m = 2; m < n_v && eq; ++m) eq = std::fabs(t_x[ord[m]] - m * dt) <= 8.0 * 2.220446049250313e-16 * tmax;
+    if (eq) {
+        StepTimes st{};
+        st.dt = dt; st.n_v = n_v; st.xmax = ord[n_v - 1];
+        for (int m = 0; m < n_v; ++m) st.order[m] = ord[m];
+        launch_pdl(k_tridiag_exp_eq, k->nk, 32, 0, s, k->tri, k->flags, st, k->coef, k->coef + 16 * 32, k->bar + 2);
+    } else {
+        launch_pdl(k_tridiag_exp, 1, 32, 0, s, k->tri, k->flags, tt, n_v, k->coef);
+    }
+    // a target at t = 0 is phi itself: copied (before any target that aliases phi is written), not combined
+    std::vector<int> rows;
+    for (int x = 0; x < n_v; ++x) {
+        if (t_x[x] != 0.0) { rows.push_back(x); continue; }
+        if (targets[x] != phi) {
+            int rc2 = cuda_check(c, cudaMemcpyAsync(targets[x], phi, (size_t)n * sizeof(cplx), cudaMemcpyDeviceToDevice, s),
+                                 "evolve copy");
+            if (rc2) return rc2;
+        }
+    }
     TargetPtrs tg{};
     for (int x = 0; x < n_v; ++x) tg.p[x] = targets[x];
     int grid = (int)std::min<int64_t>((n + 255) / 256, 4L * c->num_sms);
-    launch_combine(k->V, n, k->flags, k->coef, n_v, tg, grid, s);
-    c->launches += 1 + (n_v + 7) / 8;
+    c->launches += 1 + launch_combine(k->V, n, k->flags, k->coef, rows, tg, grid, s);
     c->last_krylov = k;
     return cuda_check(c, cudaGetLastError(), "evolve launch");
 }
@@ -795,7 +904,7 @@ int ground_state(tdmrg_ctx* c, int a, int b, cplx* psi, int nk, int restarts, do
         TargetPtrs tg{};
         tg.p[0] = psi;
         const int grid = (int)std::min<int64_t>((k->n + 255) / 256, 4L * c->num_sms);
-        launch_combine(k->V, k->n, k->flags, k->coef, 1, tg, grid, c->stream);
+        launch_combine(k->V, k->n, k->flags, k->coef, std::vector<int>{0}, tg, grid, c->stream);
         c->launches += 2;
         rc = cuda_check(c, cudaGetLastError(), "ground-state launch");
         if (rc) return rc;
