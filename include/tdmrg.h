@@ -241,6 +241,14 @@ int tdmrg_rho_eig(tdmrg_ctx* ctx, const tdmrg_c64* rho_d, double* evals_d, tdmrg
 /* tdmrg_rho_eig for the matrix of either block (packed over that side's sectors). */
 int tdmrg_rho_eig_side(tdmrg_ctx* ctx, int side, const tdmrg_c64* rho_d, double* evals_d, tdmrg_c64* evecs_d);
 
+/* tdmrg_density_matrix_side followed by tdmrg_rho_eig_side in one call, with the same results (Eq.
+ * rdensitymatrix, then the truncation input of Sec. II.B): when the eigensolver runs its sectors in two
+ * groups (the sectors with the longest Jacobi seeds on a second stream), the rho blocks of that group are
+ * formed on its stream too, so that its seeds start before the other sectors' blocks are done.
+ * Arguments as the two calls; rho_d is written and then decomposed.  Errors as the two calls. */
+int tdmrg_density_eig(tdmrg_ctx* ctx, int side, int ntargets, const int32_t* Q, const tdmrg_c64* const* psi_d,
+                      const double* w, tdmrg_c64* rho_d, double* evals_d, tdmrg_c64* evecs_d);
+
 /* Truncation of the left block to at most m states (Sec. I: a block keeps the m most probable states of
  * its reduced density matrix).  evals_d: rho_L's eigenvalues in the packed layout of tdmrg_rho_eig (per
  * left sector, descending).  Kept set: the m largest eigenvalues over all sectors; eigenvalues within

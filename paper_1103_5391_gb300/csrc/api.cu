@@ -628,6 +628,23 @@ int tdmrg_rho_eig(tdmrg_ctx* c, const tdmrg_c64* rho, double* evals, tdmrg_c64* 
     return tdmrg_rho_eig_side(c, 0, rho, evals, evecs);
 }
 
+int tdmrg_density_eig(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const tdmrg_c64* const* psi, const double* w,
+                      tdmrg_c64* rho, double* evals, tdmrg_c64* evecs) {
+    if (check_ctx(c)) return TDMRG_EINVAL;
+    if (!c->side[0].set || !c->side[1].set) return fail(c, TDMRG_ESTATE, "density_eig: blocks not set");
+    if ((side != 0 && side != 1) || nt < 1 || nt > kMaxBufs - BUF_EXTRA0 || !Q || !psi || !w || !rho || !evals || !evecs)
+        return fail(c, TDMRG_EINVAL, "density_eig: bad argument (side 0 or 1, 1..12 targets, non-null outputs)");
+    for (int l = 0; l < nt; ++l)
+        if (!psi[l] || !(w[l] >= 0.0)) return fail(c, TDMRG_EINVAL, "density_eig: null state or negative weight");
+    DeviceGuard g(c->opts.device);
+    int rc = eig_prepare(c, side);
+    // the real-basis variant's Re rho pass runs over all of rho after the product: no split there
+    const bool grouped = !c->real_basis;
+    if (!rc) rc = density_matrix(c, side, nt, Q, (const cplx* const*)psi, w, (cplx*)rho, grouped);
+    if (!rc) rc = eig_launch(c, side, (const cplx*)rho, evals, (cplx*)evecs, grouped && c->eig[side].ngroups == 2);
+    return rc;
+}
+
 int tdmrg_hpsi_flops(tdmrg_ctx* c, int a, int b, double* flops) {
     if (check_ctx(c)) return TDMRG_EINVAL;
     if (!flops) return fail(c, TDMRG_EINVAL, "hpsi_flops: null output");

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(256) k_seg_weight(const SegNorm* __restrict__ 
 
 }  // namespace
 
-int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho) {
+int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho,
+                   bool grouped) {
     const Side& L = c->side[0];
     const Side& R = c->side[1];
     cudaStream_t s = c->stream;
@@ -120,21 +121,36 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
                                           nsrc, dscale), "direct sum norms");
         if (rc) return rc;
     } else {
-        // norms of the targets -> dscale[l] = w_l / ||psi_l||^2
+        // norms of the targets -> dscale[l] = w_l / ||psi_l||^2; partials in the upper half of the reduction
+        // workspace, apart from those of tdmrg_expect / tdmrg_overlap_op (which may run beside on another stream)
+        double2* nred = c->red + 64 * (int64_t)NB;
         for (int l = 0; l < nt; ++l) {
             const int64_t nl = sector_size(c, Q[2 * l], Q[2 * l + 1]);
             if (nl == 0) return fail(c, TDMRG_ESECTOR, "density_matrix: target in an empty sector");
-            cudaError_t e = launch_norm2(psi[l], nl, c->red + (int64_t)l * NB, NB, s);
+            cudaError_t e = launch_norm2(psi[l], nl, nred + (int64_t)l * NB, NB, s);
             c->launches++;
             if (e != cudaSuccess) return cuda_check(c, e, "density_matrix norms");
         }
-        launch_pdl(k_weight_scale, 1, 32 * 12, 0, s, c->red, nt, c->dscale, wl);
+        launch_pdl(k_weight_scale, 1, 32 * 12, 0, s, nred, nt, c->dscale, wl);
         c->launches++;
     }
-    // task list: one task per sector of the side, compiled once per (side, set of target sectors)
+    // task list: one task per sector of the side, compiled once per (side, set of target sectors, order);
+    // grouped: the eigensolver's first group's sectors first, so that their tiles form one launch
+    const EigWork& ew = c->eig[side];
+    grouped = grouped && ew.ready && ew.ngroups == 2;
+    const int nsec = (int)c->side[side].dim.size();
+    std::vector<int> order;
+    if (grouped) {
+        order = ew.grp[0].sel;
+        order.insert(order.end(), ew.grp[1].sel.begin(), ew.grp[1].sel.end());
+    } else {
+        for (int q = 0; q < nsec; ++q) order.push_back(q);
+    }
+    const int nfirst = grouped ? (int)ew.grp[0].sel.size() : 0;
     std::vector<int> key(Q, Q + 2 * nt);
     key.push_back(side);
     key.push_back(nsrc);
+    key.push_back(grouped ? 1 : 0);
     auto it = c->rho_plans.find(key);
     if (it == c->rho_plans.end() && side == 1) {
         std::unique_ptr<TaskList> tl(new TaskList());
@@ -153,28 +169,30 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
                 po += (int64_t)L.dim[qi] * R.dim[ri];
             }
         }
-        int64_t off = 0;
-        for (size_t ri = 0; ri < R.dim.size(); ++ri) {
+        std::vector<int64_t> roff(R.dim.size() + 1, 0);
+        for (size_t ri = 0; ri < R.dim.size(); ++ri) roff[ri + 1] = roff[ri] + (int64_t)R.dim[ri] * R.dim[ri];
+        for (int ri : order) {
             Task tk{};
-            tk.c_off = off; tk.c_buf = BUF_OUT; tk.ldc = R.dim[ri]; tk.M = R.dim[ri]; tk.N = R.dim[ri]; tk.beta = 0;
+            tk.c_off = roff[ri]; tk.c_buf = BUF_OUT; tk.ldc = R.dim[ri]; tk.M = R.dim[ri]; tk.N = R.dim[ri]; tk.beta = 0;
             tk.herm = 1;
             tk.seg_begin = (int)tl->segs.size();
             tl->segs.insert(tl->segs.end(), segs[ri].begin(), segs[ri].end());
             tk.seg_end = (int)tl->segs.size();
             tl->tasks.push_back(tk);
-            off += (int64_t)R.dim[ri] * R.dim[ri];
         }
         make_tiles(*tl, kTileF64, kTileF64, kSplitK);
+        for (const Tile& t : tl->tiles) tl->ntiles_first += t.task < nfirst ? 1 : 0;
         int rc = upload(c, *tl);
         if (rc) { release(c, *tl); return rc; }
         it = c->rho_plans.emplace(key, std::move(tl)).first;
     }
     if (it == c->rho_plans.end()) {
         std::unique_ptr<TaskList> tl(new TaskList());
-        int64_t off = 0;
-        for (size_t qi = 0; qi < L.dim.size(); ++qi) {
+        std::vector<int64_t> loff(L.dim.size() + 1, 0);
+        for (size_t qi = 0; qi < L.dim.size(); ++qi) loff[qi + 1] = loff[qi] + (int64_t)L.dim[qi] * L.dim[qi];
+        for (int qi : order) {
             Task tk{};
-            tk.c_off = off; tk.c_buf = BUF_OUT; tk.ldc = L.dim[qi]; tk.M = L.dim[qi]; tk.N = L.dim[qi]; tk.beta = 0;
+            tk.c_off = loff[qi]; tk.c_buf = BUF_OUT; tk.ldc = L.dim[qi]; tk.M = L.dim[qi]; tk.N = L.dim[qi]; tk.beta = 0;
             tk.herm = 1;   // rho_L(q) is Hermitian: lower tiles plus mirror (a batched HERK)
             tk.seg_begin = (int)tl->segs.size();
             for (int l = 0; l < nt; ++l) {
@@ -194,9 +212,9 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
             }
             tk.seg_end = (int)tl->segs.size();
             tl->tasks.push_back(tk);
-            off += (int64_t)L.dim[qi] * L.dim[qi];
         }
         make_tiles(*tl, kTileF64, kTileF64, kSplitK);
+        for (const Tile& t : tl->tiles) tl->ntiles_first += t.task < nfirst ? 1 : 0;
         int rc = upload(c, *tl);
         if (rc) { release(c, *tl); return rc; }
         it = c->rho_plans.emplace(key, std::move(tl)).first;
@@ -209,7 +227,18 @@ int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx*
     a.bufs[BUF_OUT] = rho;
     for (int l = 0; l < nt; ++l) a.bufs[BUF_EXTRA0 + l] = const_cast<cplx*>(psi[l]);
     a.dscale = dscale;
-    cudaError_t e = launch_gemm_f64(a, s, nullptr, 0);
+    cudaError_t e = cudaSuccess;
+    if (grouped) {   // the first group's blocks on its stream, forked after the norms and weights
+        e = cudaEventRecord(ew.fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ew.side, ew.fork, 0);
+        GemmArgs a1 = a;
+        a1.ntiles = tl.ntiles_first;
+        if (e == cudaSuccess) e = launch_gemm_f64(a1, ew.side, nullptr, 0);
+        a.tiles = tl.d_tiles + tl.ntiles_first;
+        a.ntiles = (int)tl.tiles.size() - tl.ntiles_first;
+        c->launches++;
+    }
+    if (e == cudaSuccess) e = launch_gemm_f64(a, s, nullptr, 0);
     c->launches++;
     if (e == cudaSuccess && c->real_basis) {
         int64_t nr = 0;

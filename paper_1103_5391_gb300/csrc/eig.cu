@@ -814,11 +814,10 @@ cudaError_t launch_group(tdmrg_ctx* c, EigWork& w, EigGroup& G, const cplx* rho,
     return e;
 }
 
-int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs) {
+int eig_prepare(tdmrg_ctx* c, int side) {
     const Side& L = c->side[side];
     const int ns = (int)L.dim.size();
     EigWork& w = c->eig[side];
-    cudaStream_t s = c->stream;
     if (!w.ready) {
         std::vector<int64_t> off(ns), eoff(ns);
         int64_t r = 0, e = 0;
@@ -855,18 +854,32 @@ int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs)
         if (rc) return rc;
         w.ready = true;
     }
+    return TDMRG_OK;
+}
+
+// `forked`: the second stream already follows the caller's stream (density_matrix with grouped = true).
+int eig_launch(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs, bool forked) {
+    EigWork& w = c->eig[side];
+    cudaStream_t s = c->stream;
     cudaError_t e = cudaSuccess;
     if (w.ngroups == 1) {
         e = launch_group(c, w, w.grp[0], rho, evals, evecs, s);
     } else {   // fork and join by events (kept as dependencies when the caller's stream is being captured)
-        e = cudaEventRecord(w.fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.fork, 0);
+        if (!forked) {
+            e = cudaEventRecord(w.fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(w.side, w.fork, 0);
+        }
         if (e == cudaSuccess) e = launch_group(c, w, w.grp[0], rho, evals, evecs, w.side);
         if (e == cudaSuccess) e = launch_group(c, w, w.grp[1], rho, evals, evecs, s);
         if (e == cudaSuccess) e = cudaEventRecord(w.join, w.side);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, w.join, 0);
     }
     return cuda_check(c, e, "rho_eig launch");
+}
+
+int rho_eig(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs) {
+    const int rc = eig_prepare(c, side);
+    return rc ? rc : eig_launch(c, side, rho, evals, evecs, false);
 }
 
 void release_eig(tdmrg_ctx* c, int side) {

@@ -101,6 +101,7 @@ struct TaskList {
     int nsplit = 0, npartial = 0;
     cplx* d_partials = nullptr;   // split-K partial tiles
     int* d_counters = nullptr;    // split-K tickets (zero between launches)
+    int ntiles_first = 0;         // rho task lists ordered by eigensolver groups: tiles of the first group
 };
 
 // ---- tensor-core (Ozaki-sliced) form of a plan's stages, ozaki.cu
@@ -416,7 +417,13 @@ cudaError_t launch_dot_final(const cplx* x, const cplx* y, int64_t n, double2* p
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs: fixed, so reductions are deterministic
 
 // density.cu
-int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho);
+// With `grouped` (a side whose eigensolver runs two sector groups, eig_prepare done), the rho blocks of the
+// first group's sectors are formed on that group's stream (forked after the target norms) and the others
+// on the context stream; eig_launch(..., true) then continues each group on its stream.
+int density_matrix(tdmrg_ctx* c, int side, int nt, const int32_t* Q, const cplx* const* psi, const double* w, cplx* rho,
+                   bool grouped = false);
+int eig_prepare(tdmrg_ctx* c, int side);
+int eig_launch(tdmrg_ctx* c, int side, const cplx* rho, double* evals, cplx* evecs, bool forked);
 
 // correlation.cu
 void release_corr(tdmrg_ctx* c);

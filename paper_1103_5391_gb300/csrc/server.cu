@@ -4,8 +4,8 @@
 // fits the HBM budget and a slot is free; for every running job whose step in flight has finished,
 // record its observables and device time and enqueue the next step on the job's own stream; release
 // finished and cancelled jobs.  A step is the time step of Sec. II.C: tdmrg_evolve (Krylov advance
-// with n_v targets, the last target overwriting phi), tdmrg_density_matrix (ground state + targets,
-// weights of Sec. II.C), tdmrg_rho_eig and one tdmrg_expect per observable.  The first step runs
+// with n_v targets, the last target overwriting phi), tdmrg_density_eig (rho_L of the ground state + targets,
+// weights of Sec. II.C, and its eigendecomposition) and one tdmrg_expect per observable.  The first step runs
 // directly (it compiles the plans and allocates the workspace); the next steps replay a CUDA graph
 // captured from one step.
 //
@@ -141,9 +141,8 @@ int enqueue_step(Job& j) {
         ps.push_back((const tdmrg_c64*)j.targets[x]);
         ws.push_back(j.w[x]);
     }
-    rc = tdmrg_density_matrix(c, (int)ps.size(), Q.data(), ps.data(), ws.data(), (tdmrg_c64*)j.rho);
-    if (rc) return rc;
-    rc = tdmrg_rho_eig(c, (const tdmrg_c64*)j.rho, j.evals, (tdmrg_c64*)j.evecs);
+    rc = tdmrg_density_eig(c, 0, (int)ps.size(), Q.data(), ps.data(), ws.data(), (tdmrg_c64*)j.rho, j.evals,
+                           (tdmrg_c64*)j.evecs);
     if (rc) return rc;
     for (int k = 0; k < j.d.nobs; ++k) {
         rc = tdmrg_expect(c, j.d.obs_opL[k], j.d.obs_opR[k], j.d.q[0], j.d.q[1], (const tdmrg_c64*)j.phi,
@@ -355,9 +354,8 @@ int enqueue_group_step(tdmrg_server* s, Group& g) {
         ps.push_back((const tdmrg_c64*)g.targets[x]);
         ws.push_back(g.w[x]);
     }
-    rc = tdmrg_density_matrix(g.big, (int)ps.size(), Q.data(), ps.data(), ws.data(), (tdmrg_c64*)g.rho);
-    if (rc) return rc;
-    rc = tdmrg_rho_eig(g.big, (const tdmrg_c64*)g.rho, g.evals, (tdmrg_c64*)g.evecs);
+    rc = tdmrg_density_eig(g.big, 0, (int)ps.size(), Q.data(), ps.data(), ws.data(), (tdmrg_c64*)g.rho, g.evals,
+                           (tdmrg_c64*)g.evecs);
     if (rc) return rc;
     for (size_t k = 0; k < g.members.size(); ++k) {
         Job& j = *s->jobs[g.members[k]];

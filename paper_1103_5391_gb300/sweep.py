@@ -91,10 +91,9 @@ def truncate_block(ctx, side, enl, states, weights, m, real_basis, dev):
     nr, ne = T.tdmrg_rho_size(ctx, side)
     rho = _zeros(nr, dev)
     T.tdmrg_set_real_basis(ctx, real_basis)
-    T.tdmrg_density_matrix(ctx, states, weights, rho, side=side)
     evals = torch.zeros(ne, dtype=torch.float64, device=dev)
     U = _zeros(nr, dev)
-    T.tdmrg_rho_eig(ctx, rho, evals, U, side=side)
+    T.tdmrg_density_eig(ctx, states, weights, rho, evals, U, side=side)
     kept_d = torch.zeros(len(enl.dim), dtype=torch.int32, device=dev)
     disc = torch.zeros(1, dtype=torch.float64, device=dev)
     T.tdmrg_truncate(ctx, evals, m, kept_d, disc, side=side)

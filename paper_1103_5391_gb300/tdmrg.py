@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_direct_sum", "tdmrg_evolve_segments", "tdmrg_evolve_segments_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_density_eig", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats", "tdmrg_set_tile_m", "tdmrg_hpsi_tuning", "tdmrg_set_orth_per_sm",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats", "tdmrg_server_set_batching", "tdmrg_server_batch_stats",
@@ -92,6 +92,7 @@ def load(path=LIB_PATH):
         "tdmrg_density_matrix_side": (I, [P, I, I, PI32, P, PD, P]),
         "tdmrg_rho_size_side": (I, [P, I, PI64, PI64]),
         "tdmrg_rho_eig_side": (I, [P, I, P, P, P]),
+        "tdmrg_density_eig": (I, [P, I, I, PI32, P, PD, P, P, P]),
         "tdmrg_truncate_side": (I, [P, I, P, I, P, P]),
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_enlarge_size": (I, [I, I, PI32, PI32, I, ctypes.POINTER(I), PI32, PI32, PI32, ctypes.POINTER(ctypes.c_int64)]),
@@ -320,6 +321,16 @@ def tdmrg_density_matrix(ctx, states, weights, rho, side=0):
                                                        w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
     return _check(ctx, load().tdmrg_density_matrix_side(ctx, side, len(states), qp, arr,
                                                         w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho)))
+
+
+def tdmrg_density_eig(ctx, states, weights, rho, evals, evecs, side=0):
+    """tdmrg_density_matrix and tdmrg_rho_eig in one call (states: list of (Q, tensor))."""
+    q, qp = _i32([x for Q, _ in states for x in Q])
+    arr = (ctypes.c_void_p * len(states))(*[_ptr(v) for _, v in states])
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    return _check(ctx, load().tdmrg_density_eig(ctx, side, len(states), qp, arr,
+                                                w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(rho),
+                                                _ptr(evals), _ptr(evecs)))
 
 
 def tdmrg_set_real_basis(ctx, on):

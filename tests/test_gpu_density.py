@@ -172,3 +172,35 @@ def test_overlap_op(lib):
             lib.tdmrg_overlap_op(ctx, 123, -1, ss.Q1, dev(phi_q1), ss.Q0, dev(ss.psi_gs), out)
     finally:
         lib.tdmrg_destroy(ctx)
+
+
+@pytest.mark.parametrize("L,m,side", [(8, 24, 0), (32, 400, 0), (32, 400, 1), (48, 1000, 0)])
+def test_density_eig_equals_the_two_calls(lib, L, m, side):
+    """tdmrg_density_eig (rho of the first eigensolver group formed on that group's stream) = the two calls:
+    rho, eigenvalues and eigenvectors bit-equal, on layouts with one group (L=8) and two (L=32, 48)."""
+    torch = pytest.importorskip("torch")
+    from paper_1103_5391_gb300 import problem
+    ss = S.make_synthetic(L, m, 4.0, nbonds=1, seed=S.SEED_BASE + 21)
+    sts = [(Q, dev(v)) for Q, v in _states(ss, 4, 5)]
+    wgs, w = lib.tdmrg_tst_weights(4)
+    out = []
+    for fused in (False, True):
+        ctx = new_ctx()
+        try:
+            problem.load_synthetic(ctx, ss)
+            nr, ne = lib.tdmrg_rho_size(ctx, side=side)
+            rho = torch.zeros(nr, dtype=torch.complex128, device="cuda")
+            ev = torch.zeros(ne, dtype=torch.float64, device="cuda")
+            U = torch.zeros_like(rho)
+            for _ in range(2):   # the second call reuses the compiled plans and workspaces
+                if fused:
+                    lib.tdmrg_density_eig(ctx, sts, [wgs] + w, rho, ev, U, side=side)
+                else:
+                    lib.tdmrg_density_matrix(ctx, sts, [wgs] + w, rho, side=side)
+                    lib.tdmrg_rho_eig(ctx, rho, ev, U, side=side)
+            torch.cuda.synchronize()
+            out.append((rho.clone(), ev.clone(), U.clone()))
+        finally:
+            lib.tdmrg_destroy(ctx)
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
