@@ -22,7 +22,7 @@ namespace {
 
 constexpr int NB = kRedBlocks;   // reduction blocks
 constexpr int kCoefWords = (16 + 32) * 32;   // Krylov coefficients of 16 targets + step exponential columns
-constexpr int kBarWords = 4;                  // grid barrier count and generation, exponential ticket
+constexpr int kBarWords = 4;                  // grid barrier counter, exponential ticket
 constexpr int NT = 256;          // threads per reduction block
 enum { T_ALPHA = 0, T_BETA = 32, T_BETA0 = 64, T_RESID = 65, T_ERR = 66, T_EMIN = 67 };
 
@@ -139,26 +139,29 @@ struct OrthArgs {
     double2* partB;
     double* tri;
     int* flags;
-    unsigned* bar;     // [0] arrivals, [1] generation
+    unsigned* bar;     // [0] grid barrier counter (top bit flips at each barrier)
     int* status;
     SegTab seg;        // seg.nseg == 0: one problem over the whole vector
 };
 
+// Grid barrier of the co-resident (cooperative) grid on one counter word whose low 31 bits stay zero:
+// block 0 adds 2^31 - (G - 1), every other block 1, so the top bit flips exactly when the last block
+// arrives, and each block waits until the top bit differs from the value it saw at its own arrival.  The
+// last arrival releases everyone directly (no reset, no second word).  Bounded wait: status bit 2.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g0 = *gen;
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
         __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long it = 0;
-            while (*gen == g0) {
-                if (++it > kBarrierSpin) { atomicOr(status, 2); break; }
-            }
+        const unsigned old = atomicAdd(bar, add);
+        long it = 0;
+        while (((old ^ ld_acquire_u32(bar)) & 0x80000000u) == 0u) {
+            if (++it > kBarrierSpin) { atomicOr(status, 2); break; }
         }
         __threadfence();
     }
@@ -770,7 +773,7 @@ int ensure_work(tdmrg_ctx* c, int a, int b, int nk, int64_t n, KrylovWork** out)
     if (!rc) rc = dev_alloc(c, (void**)&k.flags, 4 * sizeof(int), "Krylov flags");
     // coefficients [x][k] of 16 targets, then the columns of the step exponential (32 x 32)
     if (!rc) rc = dev_alloc(c, (void**)&k.coef, kCoefWords * sizeof(cplx), "Krylov coefficients");
-    // grid barrier (count, generation), then the ticket of k_tridiag_exp_eq
+    // grid barrier counter (word 0), then the ticket of k_tridiag_exp_eq (word 2)
     if (!rc) rc = dev_alloc(c, (void**)&k.bar, kBarWords * sizeof(unsigned), "Krylov grid barrier");
     if (!rc) rc = cuda_check(c, cudaMemset(k.bar, 0, kBarWords * sizeof(unsigned)), "Krylov grid barrier");
     if (!rc) {   // co-resident grid of the fused orthogonalisation: at most one block per SM, at most NB
