@@ -271,6 +271,57 @@ __device__ double chunk_dots_n(const cplx* __restrict__ V, cplx* __restrict__ w,
     return nn;
 }
 
+// FP32 value of a double by truncating its mantissa to 23 bits, on the integer pipe (conversions and FP64
+// arithmetic share this GPU's narrow FP64 pipe); |x| below 2^-126 gives 0.  Relative error <= 2^-23.
+__device__ __forceinline__ float f32_trunc(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), ex = (hi >> 20) & 0x7FFu;
+    const unsigned mant = ((hi & 0xFFFFFu) << 3) | ((unsigned)b >> 29);
+    return ex <= 896u ? 0.f : __uint_as_float((hi & 0x80000000u) | ((ex - 896u) << 23) | mant);
+}
+
+// First-pass dots <v_k|w> over this block's chunk in FP32 (k in [k0, k0 + NK)), written as FP64
+// partials.  The second pass (FP64, chunk_dots_n with h) removes what this pass leaves along V to FP64
+// accuracy, and alpha is the sum of both passes' coefficients, so only the first pass's FP64 work goes.
+template <int NK>
+__device__ void chunk_dots_f32_n(const cplx* __restrict__ V, const cplx* __restrict__ w, int64_t n, int k0, int64_t lo,
+                                 int64_t hi, double2* part, double* sh, double2* red8) {
+    float2 fa[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) fa[k] = make_float2(0.f, 0.f);
+    const cplx* __restrict__ Vk = V + (int64_t)k0 * n;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
+        const double2 x = w[i];
+        const float xr = f32_trunc(x.x), xi = f32_trunc(x.y);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const double2 v = Vk[(int64_t)k * n + i];   // acc += conj(v) x
+            const float vr = f32_trunc(v.x), vi = f32_trunc(v.y);
+            fa[k].x = fmaf(vr, xr, fmaf(vi, xi, fa[k].x));
+            fa[k].y = fmaf(vr, xi, fmaf(-vi, xr, fa[k].y));
+        }
+    }
+    double2 acc[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) acc[k] = make_double2((double)fa[k].x, (double)fa[k].y);
+    block_sum<NK>(acc, sh, red8);
+    if (threadIdx.x < NK) part[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = red8[threadIdx.x];
+}
+
+__device__ void chunk_dots_f32(const cplx* __restrict__ V, const cplx* __restrict__ w, int64_t n, int nv, int k0,
+                               int64_t lo, int64_t hi, double2* part, double* sh, double2* red8) {
+    switch (min(8, nv - k0)) {
+        case 1: return chunk_dots_f32_n<1>(V, w, n, k0, lo, hi, part, sh, red8);
+        case 2: return chunk_dots_f32_n<2>(V, w, n, k0, lo, hi, part, sh, red8);
+        case 3: return chunk_dots_f32_n<3>(V, w, n, k0, lo, hi, part, sh, red8);
+        case 4: return chunk_dots_f32_n<4>(V, w, n, k0, lo, hi, part, sh, red8);
+        case 5: return chunk_dots_f32_n<5>(V, w, n, k0, lo, hi, part, sh, red8);
+        case 6: return chunk_dots_f32_n<6>(V, w, n, k0, lo, hi, part, sh, red8);
+        case 7: return chunk_dots_f32_n<7>(V, w, n, k0, lo, hi, part, sh, red8);
+        default: return chunk_dots_f32_n<8>(V, w, n, k0, lo, hi, part, sh, red8);
+    }
+}
+
 __device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
                              int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
     switch (min(8, nv - k0)) {
@@ -310,15 +361,16 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
     __shared__ double sh[(OB / 32) * 16];
     __shared__ double2 red8[8];
     __shared__ double2 h[33];
-    // (A) first-pass dots
+    __shared__ double alpha1;   // the first pass's coefficient of v_j (alpha = pass 1 + pass 2)
+    // (A) first-pass dots (FP32)
     if (active)
-        for (int k0 = 0; k0 < a.nv; k0 += 8) chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, nullptr, a.partA, sh, red8);
+        for (int k0 = 0; k0 < a.nv; k0 += 8) chunk_dots_f32(a.V, a.w, a.n, a.nv, k0, lo, hi, a.partA, sh, red8);
     grid_barrier(a.bar, a.status);
     // (B) w' = w - sum h1_k v_k, second-pass dots, ||w'||^2
     double nn = 0.0;
     if (active) {
         sum_partials(a.partA, a.nv, h, b0, b1);
-        if (blockIdx.x == b0 && threadIdx.x == 0) tri[T_ALPHA + a.j] = h[a.j].x;
+        if (threadIdx.x == 0) alpha1 = h[a.j].x;
         for (int k0 = 0; k0 < a.nv; k0 += 8) {
             nn += chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, h, a.partB, sh, red8);
             __syncthreads();   // h is read by every thread of the first group
@@ -336,7 +388,8 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
         double b2 = h[a.nv].x;
         for (int k = 0; k < a.nv; ++k) b2 -= h[k].x * h[k].x + h[k].y * h[k].y;
         const double bt = sqrt(fmax(b2, 0.0));
-        const double alpha = tri[T_ALPHA + a.j];
+        const double alpha = alpha1 + h[a.j].x;
+        if (blockIdx.x == b0) tri[T_ALPHA + a.j] = alpha;
         const bool st = (a.j == a.nk - 1) || (bt <= a.tol * fmax(1.0, fabs(alpha)));
         sc[0] = bt;
         sc[1] = st ? 0.0 : 1.0 / bt;
