@@ -419,6 +419,13 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
     }
 }
 
+// Taylor terms for a substep with ||T h|| <= xs <= 2: the smallest K (per bucket of xs) whose remainder
+// bound xs^{K+1} / (K+1)! is below 1e-17.
+__device__ __forceinline__ int taylor_terms(double xs) {
+    return xs <= 0.25 ? 12 : xs <= 0.5 ? 15 : xs <= 0.75 ? 17 : xs <= 1.0 ? 18 : xs <= 1.25 ? 20 : xs <= 1.5 ? 21
+         : xs <= 1.75 ? 23 : 24;
+}
+
 struct Times { double t[16]; };
 
 // Order key of a time t >= 0: unsigned comparison of the bits is numeric comparison (-0 taken as +0).
@@ -483,7 +490,7 @@ __global__ void __launch_bounds__(32) k_tridiag_exp(double* __restrict__ tri, co
         const int S = span > 0.0 ? (int)ceil(0.5 * span) : 0;
         if (S > 0) {
             const double h = dt / S, xs = nu * h;
-            const int K = xs <= 0.25 ? 12 : xs <= 0.5 ? 15 : xs <= 1.0 ? 18 : 24;
+            const int K = taylor_terms(xs);
             for (int st = 0; st < S; ++st) {
                 double2 u = u0, sum = u0;
                 for (int k = 1; k <= K; ++k) {
@@ -528,7 +535,7 @@ __global__ void __launch_bounds__(32) k_tridiag_exp_eq(double* __restrict__ tri,
         const int S = span > 0.0 ? (int)ceil(0.5 * span) : 0;
         if (S > 0) {
             const double h = st.dt / S, xs = nu * h;
-            const int K = xs <= 0.25 ? 12 : xs <= 0.5 ? 15 : xs <= 1.0 ? 18 : 24;
+            const int K = taylor_terms(xs);
             for (int sb = 0; sb < S; ++sb) {
                 double2 u = u0, sum = u0;
                 for (int k = 1; k <= K; ++k) {
