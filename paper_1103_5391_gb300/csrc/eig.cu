@@ -17,6 +17,10 @@
 //      on S with a relative criterion, k_jacobi32).  The iterate is kept as W = X^H, so every product
 //      is a plain or conjugate-transposed GEMM operand;
 //   3. sort each sector's eigenpairs by descending eigenvalue.
+// The sectors run in one group, or in two on two streams: the few with the longest Jacobi seeds (the
+// seed of a sector runs on one SM, so its cost grows with n, not with the total work) seed and refine on
+// a second stream while the others' seeds and refinement fill the rest of the GPU; a cost model picks the
+// split (long_sectors).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -3,13 +3,15 @@
 //
 // Lanczos is started from phi itself: v_0 = phi / ||phi||.  Step j: w = H v_j (grouped superblock
 // product), alpha_j = Re <v_j|w>, then two classical Gram-Schmidt passes against v_0..v_j
-// (the first pass also removes the alpha_j v_j and beta_j v_{j-1} components), beta_{j+1} = ||w||,
-// v_{j+1} = w / beta_{j+1}, all in one cooperative launch per step with two grid barriers; the recursion stops at n_K
-// vectors or when beta_{j+1} <= tol * max(1, |alpha_j|).  Then the coefficients
-// c_x = ||phi|| e^{-i T t_x} e_0 (= ||phi|| [S^dag e^{-i D t_x} S]_{.,0} with T = S^dag D S) are
-// computed on the tridiagonal itself (Taylor series on short substeps, FP64) and the targets
-// phi(t_x) = sum_k v_k c_x[k] are formed in one pass over V.  Everything is FP64 and stays on the device; reductions use a fixed grid and
-// a fixed summation order, so results do not depend on scheduling.
+// (the first pass also removes the alpha_j v_j and beta_j v_{j-1} components; its dots in FP32, the second
+// pass in FP64 removes what they leave, and alpha_j is the sum of both passes' coefficients),
+// beta_{j+1} = ||w||, v_{j+1} = w / beta_{j+1}, all in one cooperative launch per step with two grid
+// barriers; the recursion stops at n_K vectors or when beta_{j+1} <= tol * max(1, |alpha_j|).  Then the
+// coefficients c_x = ||phi|| e^{-i T t_x} e_0 (= ||phi|| [S^dag e^{-i D t_x} S]_{.,0} with T = S^dag D S)
+// are computed on the tridiagonal itself (Taylor series on short substeps, FP64; for equally spaced
+// times by powers of the step exponential) and the targets phi(t_x) = sum_k v_k c_x[k] are formed in
+// one pass over V.  The vectors, alpha and beta are FP64-accurate and stay on the device; reductions use
+// a fixed grid and a fixed summation order, so results do not depend on scheduling.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
