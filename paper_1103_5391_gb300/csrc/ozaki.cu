@@ -211,11 +211,11 @@ __global__ void __launch_bounds__(kSliceCT) k_slice(OzSliceArgs sa, GemmArgs g, 
     if (job.role == 0) {
         r_re = r_im = job.row0 + v;
     } else {
+        // column c of a column tile: rows 2c (Re) and 2c + 1 (Im) of the tile's 2 n_t rows, so the two
+        // accumulator columns of one complex output are adjacent (one 16-byte store in the epilogue)
         const int nt = v / TNC, c = v % TNC;
-        const int nrem = job.nvec - TNC * nt;
-        const int n_t = ((nrem < TNC ? nrem : TNC) + 7) & ~7;
-        r_re = job.row0 + 2 * TNC * nt + c;
-        r_im = r_re + n_t;
+        r_re = job.row0 + 2 * TNC * nt + 2 * c;
+        r_im = r_re + 1;
     }
     if (tid == 0) sa.exps[job.exp0 + v] = E;
     const int64_t plane = (int64_t)sa.rows * sa.kpad;
@@ -426,25 +426,17 @@ __global__ void __launch_bounds__(128) k_ozaki_gemm(const __grid_constant__ CUte
         const int Ei = oa.expA[task.aexp0 + tile.m0 + row];
         const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
         double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
-        int eB[64];   // loads ahead of the stores (see the warp-specialised kernel)
+        int eB[32];   // loads ahead of the stores (see the warp-specialised kernel)
 #pragma unroll
-        for (int jj = 0; jj < 64; ++jj) {
-            const bool im = jj >= n_t;
-            const int j = im ? jj - n_t : jj;
-            eB[jj] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
-        }
+        for (int j = 0; j < 32; ++j) eB[j] = j < nval ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
 #pragma unroll
-        for (int jj = 0; jj < 64; ++jj) {       // accumulator column jj: Re of column jj, or Im of column jj - n_t
-            if (jj < 2 * n_t) {
-                const bool im = jj >= n_t;
-                const int j = im ? jj - n_t : jj;
-                if (j < nval) {
-                    const int e = Ei + eB[jj] - 7 * (S + 1);
-                    double v = scaled_int(acc[jj], e);
-                    double* pc = C + 2 * (int64_t)j * cs + (im ? 1 : 0);
-                    if (task.beta) v += *pc;
-                    *pc = v;
-                }
+        for (int j = 0; j < 32; ++j) {          // accumulator columns 2j, 2j + 1: Re and Im of column j
+            if (j < nval) {
+                const int e = Ei + eB[j] - 7 * (S + 1);
+                double2 v = make_double2(scaled_int(acc[2 * j], e), scaled_int(acc[2 * j + 1], e));
+                double2* pc = reinterpret_cast<double2*>(C + 2 * (int64_t)j * cs);
+                if (task.beta) { const double2 o = *pc; v.x += o.x; v.y += o.y; }
+                *pc = v;
             }
         }
     }
@@ -758,11 +750,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
             // loads ahead of the stores (a load behind a store to C may not be reordered above it, so
             // loads inside the store loop would cost one memory latency each): the column exponents
             // through a per-warp row of shared memory, the beta operands eight at a time
-            {
-                const int jj = 16 * part + lane;
-                const bool im = jj >= n_t;
-                const int j = im ? jj - n_t : jj;
-                if (lane < 16) sExp[warp - 2][lane] = (jj < 2 * n_t && j < nval) ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
+            {   // accumulator columns 2j, 2j + 1 hold Re and Im of output column j: this warp's 16 columns
+                // are output columns 8 part .. 8 part + 7
+                const int j = 8 * part + (lane >> 1);
+                if (lane < 16) sExp[warp - 2][lane] = j < nval ? oa.expB[task.bexp0 + tile.n0 + j] : 0;
             }
             __syncwarp();
             if (row_lane && tile.m0 + row < task.M) {
@@ -770,28 +761,30 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_ozaki_gemm_ws(const __grid_co
                 const int64_t rs = task.trans ? 1 : task.ldc, cs = task.trans ? task.ldc : 1;   // row / column strides
                 double* C = (double*)(g.bufs[task.c_buf] + task.c_off + (int64_t)(tile.m0 + row) * rs + (int64_t)tile.n0 * cs);
 #pragma unroll
-                for (int c8 = 0; c8 < 16; c8 += 8) {
-                    double old[8];
+                for (int c4 = 0; c4 < 8; c4 += 4) {   // the beta operands four at a time, ahead of their stores
+                    double2 old[4];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int jj = 16 * part + c8 + u;
-                        const bool im = jj >= n_t;
-                        const int j = im ? jj - n_t : jj;
-                        old[u] = (task.beta && jj < 2 * n_t && j < nval) ? C[2 * (int64_t)j * cs + (im ? 1 : 0)] : 0.0;
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = 8 * part + c4 + u;
+                        old[u] = (task.beta && j < nval) ? *reinterpret_cast<const double2*>(C + 2 * (int64_t)j * cs)
+                                                         : make_double2(0.0, 0.0);
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int jj = 16 * part + c8 + u;
-                        const bool im = jj >= n_t;
-                        const int j = im ? jj - n_t : jj;
-                        if (jj < 2 * n_t && j < nval)
-                            C[2 * (int64_t)j * cs + (im ? 1 : 0)] = scaled_int(acc[c8 + u], Ei + sExp[warp - 2][c8 + u]) + old[u];
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = 8 * part + c4 + u;
+                        if (j < nval) {
+                            const int e = Ei + sExp[warp - 2][2 * (c4 + u)];
+                            *reinterpret_cast<double2*>(C + 2 * (int64_t)j * cs) =
+                                make_double2(scaled_int(acc[2 * (c4 + u)], e) + old[u].x,
+                                             scaled_int(acc[2 * (c4 + u) + 1], e) + old[u].y);
+                        }
                     }
                 }
             }
             __syncwarp();   // sExp is rewritten for the next tile
         }
     }
+    __syncwarp();   // the producer and MMA threads rejoin their warps: the barrier below waits for every thread
     __syncthreads();
     if (failed && tid == 0) atomicOr(oa.status, 1);
     if (queue && tid == 0 && atomicAdd(oa.sched + 1, 1u) == gridDim.x - 1) {   // every CTA has stopped claiming tiles
