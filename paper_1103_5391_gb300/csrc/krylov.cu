@@ -239,11 +239,11 @@ __device__ void sum_partials(const double2* __restrict__ part, int nv, double2* 
 }
 
 // Dots <v_k|x> over this block's chunk for k in [k0, k0 + NK), written as partials.  With
-// h != nullptr the chunk is first updated in place, x <- x - sum_k h_k v_k over all nv vectors, and
+// h != nullptr the chunk is first updated in place, x <- x - sum_u h_u v_{ju + u} over u < nu, and
 // ||x||^2 of the updated chunk is returned (this happens in the group k0 = 0 only).  NK is the exact
 // count: predicated-off FP64 instructions would still take issue slots of the slow FP64 pipe.
 template <int NK>
-__device__ double chunk_dots_n(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
+__device__ double chunk_dots_n(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int ju, int nu, int k0,
                                int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
     double2 acc[NK];
 #pragma unroll
@@ -253,8 +253,8 @@ __device__ double chunk_dots_n(const cplx* __restrict__ V, cplx* __restrict__ w,
     for (int64_t i = lo + threadIdx.x; i < hi; i += OB) {
         double2 x = w[i];
         if (h != nullptr && k0 == 0) {
-            for (int k = 0; k < nv; ++k) {
-                const double2 v = V[(int64_t)k * n + i];
+            for (int k = 0; k < nu; ++k) {
+                const double2 v = V[(int64_t)(ju + k) * n + i];
                 x.x = fma(-h[k].x, v.x, fma(h[k].y, v.y, x.x));
                 x.y = fma(-h[k].x, v.y, fma(-h[k].y, v.x, x.y));
             }
@@ -324,17 +324,17 @@ __device__ void chunk_dots_f32(const cplx* __restrict__ V, const cplx* __restric
     }
 }
 
-__device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int k0,
+__device__ double chunk_dots(const cplx* __restrict__ V, cplx* __restrict__ w, int64_t n, int nv, int ju, int nu, int k0,
                              int64_t lo, int64_t hi, const double2* h, double2* part, double* sh, double2* red8) {
     switch (min(8, nv - k0)) {
-        case 1: return chunk_dots_n<1>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        case 2: return chunk_dots_n<2>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        case 3: return chunk_dots_n<3>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        case 4: return chunk_dots_n<4>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        case 5: return chunk_dots_n<5>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        case 6: return chunk_dots_n<6>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        case 7: return chunk_dots_n<7>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
-        default: return chunk_dots_n<8>(V, w, n, nv, k0, lo, hi, h, part, sh, red8);
+        case 1: return chunk_dots_n<1>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        case 2: return chunk_dots_n<2>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        case 3: return chunk_dots_n<3>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        case 4: return chunk_dots_n<4>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        case 5: return chunk_dots_n<5>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        case 6: return chunk_dots_n<6>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        case 7: return chunk_dots_n<7>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
+        default: return chunk_dots_n<8>(V, w, n, ju, nu, k0, lo, hi, h, part, sh, red8);
     }
 }
 
@@ -364,17 +364,18 @@ __global__ void __launch_bounds__(OB) k_lanczos_orth_t(OrthArgs a) {
     __shared__ double2 red8[8];
     __shared__ double2 h[33];
     __shared__ double alpha1;   // the first pass's coefficient of v_j (alpha = pass 1 + pass 2)
-    // (A) first-pass dots (FP32)
-    if (active)
-        for (int k0 = 0; k0 < a.nv; k0 += 8) chunk_dots_f32(a.V, a.w, a.n, a.nv, k0, lo, hi, a.partA, sh, red8);
+    // (A) first-pass dots (FP32) with v_{j-1} and v_j only: H v_j has components above rounding along
+    // these two alone (the three-term recurrence), so the first pass skips the older vectors
+    const int j0 = a.j > 0 ? a.j - 1 : 0, na = a.j - j0 + 1;
+    if (active) chunk_dots_f32(a.V + (int64_t)j0 * a.n, a.w, a.n, na, 0, lo, hi, a.partA, sh, red8);
     grid_barrier(a.bar, a.status);
-    // (B) w' = w - sum h1_k v_k, second-pass dots, ||w'||^2
+    // (B) w' = w - h1_{j-1} v_{j-1} - h1_j v_j, second-pass dots with every v_k (FP64), ||w'||^2
     double nn = 0.0;
     if (active) {
-        sum_partials(a.partA, a.nv, h, b0, b1);
-        if (threadIdx.x == 0) alpha1 = h[a.j].x;
+        sum_partials(a.partA, na, h, b0, b1);
+        if (threadIdx.x == 0) alpha1 = h[na - 1].x;
         for (int k0 = 0; k0 < a.nv; k0 += 8) {
-            nn += chunk_dots(a.V, a.w, a.n, a.nv, k0, lo, hi, h, a.partB, sh, red8);
+            nn += chunk_dots(a.V, a.w, a.n, a.nv, j0, na, k0, lo, hi, h, a.partB, sh, red8);
             __syncthreads();   // h is read by every thread of the first group
         }
         nn = block_sum1(nn, sh);
