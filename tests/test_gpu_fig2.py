@@ -1,0 +1,72 @@
+"""Sec. III.A, Fig. 2(b): the one-site hole excitation of the tight-binding chain, reproduced by a finite
+sweep with time-step targeting on the GPU and compared with the exact result of App. A.
+
+16-site chain, H_0 = -sum_<ij> sigma (c^dag c + h.c.) (U = 0), half filling, m = 200 (the paper's value for
+the chain).  The stored blocks are the oracle's ground-state DMRG (infinite algorithm and one finite
+sweep).  The hole is created by c_{8 up} on the ground state (i = 8: b = 1, B = c_up in Eq. b) at the
+sweep's first step, whose central sites are 7 and 8; n_v = 4 targets, tau = 0.1, n_K = 12, the targets
+advanced at every other step (Sec. II.C).  At every step the device measures <n_{l up}> and <n_{l+1 up}>
+of every target (l, l + 1: the new sites of the two enlarged blocks), normalised, so for target x at time
+t = t_step + x tau / 3
+    X_{8j}(t) = <phi|phi> <n_{j up}>(t),   <phi|phi> = <psi|n_{8 up}|psi> = R_8,
+and the closed form X_ij(t) = R_i R_j - |T_ij(t)|^2 (oracle.closed_forms.hole_x, pinned against ED)
+gives the expected density X_{8j}(t) / R_8.
+
+The arithmetic is FP64 throughout, so the deviations are the method's truncation error, bounded by the
+sweep's total discarded weight W = sum_k eps_k (eps_k the discarded weight of the weighted rho of step k
+as the sweep reports it) and the targeting weights w (ground state 1/4, targets 1/4, 1/8, 1/8, 1/4):
+eps_k = sum_x w_x ||(1 - P_k) phi_x||^2, so a cut removes at most eps_k / w_x of target x's squared norm
+and these losses add up.  Hence every target's norm lies within W / min w of R_8; the ground-state
+energy, variational, lies above the exact free-fermion energy by at most (W / w_gs) |E_0|; and a
+density, not variational, errs at most at the order of the amplitude error sqrt(W / min w).  Measured
+at m = 200: W = 2.3e-6; energy 1.1e-5 above (bound 1.8e-4), norm 1.1e-6 (bound 1.9e-5), densities
+6.7e-4 over 200 points up to t = 1.2 (bound 4.3e-3)."""
+import numpy as np
+import pytest
+
+from oracle import closed_forms, dmrg
+from tests.gpu_util import torch_cuda
+from tests.test_gpu_sweep import _device_blocks
+
+pytestmark = pytest.mark.gpu
+L, M, I_SITE, TAU, N_V = 16, 200, 8, 0.1, 4
+HOP = -np.eye(L, k=1) - np.eye(L, k=-1)
+
+
+@pytest.fixture(scope="module")
+def records():
+    torch_cuda()
+    from paper_1103_5391_gb300 import sweep as S
+    d = dmrg.ChainDMRG(L, 1.0, 0.0, M)
+    d.run(sweeps=1)
+    left, right = _device_blocks(d, S)
+    return S.TSTSweep(L, 1.0, 0.0, M, left, right, n_v=N_V, tau=TAU, nk=12, advance_every=2,
+                      excitations=[(I_SITE, "c", 0)]).run()
+
+
+def test_hole_excitation_matches_app_a(records):
+    from paper_1103_5391_gb300 import tdmrg as T
+    e_exact = 2.0 * np.linalg.eigvalsh(HOP)[: L // 2].sum()
+    r8 = closed_forms.ground_density(HOP, L // 2)[I_SITE]
+    assert records[0]["action"] == "excite"
+    worst = {"energy": 0.0, "norm": 0.0, "density": 0.0}
+    npoints = 0
+    for rec in records:
+        worst["energy"] = max(worst["energy"], abs(rec["energy"] - e_exact))
+        l = rec["l"]
+        for x, tg in enumerate(rec["targets"]):
+            t = rec["t"] + x * TAU / (N_V - 1)
+            worst["norm"] = max(worst["norm"], abs(tg["norm2"] - r8))
+            for site, key in ((l, "n_left"), (l + 1, "n_right")):
+                want = closed_forms.hole_x(HOP, L // 2, I_SITE, site, t) / r8
+                worst["density"] = max(worst["density"], abs(tg[key].real - want))
+                npoints += 1
+    W = sum(rec.get("discarded", 0.0) for rec in records)
+    w_gs, w = T.tdmrg_tst_weights(N_V)
+    print("fig2 chain:", npoints, "points, t up to %.2f, W = %.2e," % (records[-1]["t"], W), worst)
+    assert npoints > 150 and records[-1]["t"] >= 1.0
+    assert 0.0 < W < 1e-5, W   # m = 200 resolves the targets, so the bounds below are tight
+    assert min(rec["energy"] for rec in records) > e_exact - 1e-9   # variational
+    assert worst["energy"] < W / w_gs * abs(e_exact), (W, worst)
+    assert worst["norm"] < W / min(w), (W, worst)
+    assert worst["density"] < np.sqrt(W / min(w)), (W, worst)

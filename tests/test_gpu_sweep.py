@@ -27,7 +27,7 @@ def _blockops(blk, dense, odd):
     secs, _, _ = blk.sectors()
     bo = blk.blockop(dense, odd)
     qns = [tuple(secs[qo]) + tuple(secs[qi]) for (qo, qi) in bo.blocks]
-    data = np.concatenate([b.ravel() for b in bo.blocks.values()])
+    data = np.concatenate([b.ravel() for b in bo.blocks.values()]) if bo.blocks else np.zeros(0, complex)   # H = 0: one site at U = 0
     return qns, data
 
 
