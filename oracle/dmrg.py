@@ -1,5 +1,5 @@
-"""Textbook two-site DMRG for the open Hubbard chain: infinite, then finite algorithm (oracle; test
-infrastructure only).
+"""Textbook two-site DMRG for the open Hubbard chain and two-leg ladder: infinite, then finite algorithm
+(oracle; test infrastructure only).
 
 Sec. I: a block keeps the m most probable states of its reduced density matrix, computed from the
 superblock's targeted state, and every block operator is carried into the kept basis, O -> U^dag O U.
@@ -15,6 +15,12 @@ Conventions (the same as the exact blocks of blocks.py and the superblock of sup
     sector permutation); sector blocks are cut from it for the superblock product.
 A block carries its Hamiltonian and c^dag_{edge, sigma} of the site that bonds to the rest of the chain
 (the last site of a left block, the first site of a right block).
+
+Ladder (Sec. III: 8 x 2 and 2 x 4 ladders): sites i = 2x + y in rung-first order, so site i bonds to
+i - 1 across a rung when i is odd and to i - 2 along a leg; a ladder block also carries c^dag of its
+second site from the edge (cdag2), since a new site bonds to both.  The ladder with an even number of
+sites is symmetric under reflection i -> N - 1 - i (which exchanges the legs), so a right block of r sites
+has the bonds of a left block of r sites and the same rule (Geometry) builds both.
 
 Truncation (the reading of the silent paper): the eigenvalues of rho of all sectors are sorted in
 descending order; the m largest are kept; eigenvalues within 1e-12 lambda_max of the m-th largest are
@@ -42,13 +48,47 @@ SITE_NN = np.diag([0.0, 0.0, 0.0, 1.0]).astype(complex)
 TIE_REL = 1e-12
 
 
-class DBlock:
-    """A block: basis quantum numbers (sorted), dense H, c^dag of the edge site per spin, site count."""
+class Geometry:
+    """Bonds of the open chain (legs = 1, hopping t_leg) or of the two-leg ladder (legs = 2) with
+    rung-first labels, H_0 = -sum_bonds t (c^dag c + h.c.)."""
 
-    def __init__(self, qn, H, cdag, nsites):
+    def __init__(self, legs=1, t_leg=1.0, t_rung=1.0):
+        assert legs in (1, 2)
+        self.legs, self.t_leg, self.t_rung = legs, t_leg, t_rung
+
+    def new_site_bonds(self, k):
+        """Hopping of a new site with k sites between it and the block's open end to the block's edge
+        (the site k - 1 from that end) and to the second site from the edge (k - 2)."""
+        if self.legs == 1:
+            return (self.t_leg if k >= 1 else 0.0), 0.0
+        return (self.t_rung if k % 2 == 1 else 0.0), (self.t_leg if k >= 2 else 0.0)
+
+    def cut_bonds(self, l):
+        """Bonds between the left enlarged block (sites 0..l) and the right one (sites l + 1 ...), as
+        (left edge index, right edge index, t); edge 0 is the site at the cut, edge 1 the next one."""
+        if self.legs == 1:
+            return [(0, 0, self.t_leg)]
+        return ([(0, 0, self.t_rung)] if l % 2 == 0 else []) + [(1, 0, self.t_leg), (0, 1, self.t_leg)]
+
+    def hopping(self, nsites):
+        """The matrix h of H_0 = sum_ij h_ij c^dag_i c_j (h_ij = -t on bonds)."""
+        h = np.zeros((nsites, nsites))
+        for j in range(nsites):
+            for d, tb in zip((1, 2), self.new_site_bonds(j)):
+                if tb != 0.0 and j - d >= 0:
+                    h[j - d, j] = h[j, j - d] = -tb
+        return h
+
+
+class DBlock:
+    """A block: basis quantum numbers (sorted), dense H, c^dag of the edge site per spin, site count, and
+    on a ladder c^dag of the second site from the edge per spin (cdag2; None on a chain)."""
+
+    def __init__(self, qn, H, cdag, nsites, cdag2=None):
         self.qn = [tuple(q) for q in qn]
         self.H = H
         self.cdag = cdag
+        self.cdag2 = cdag2
         self.nsites = nsites
 
     @property
@@ -91,48 +131,66 @@ def _sorted(qn, mats):
     return [qn[k] for k in order], [m[ix] for m in mats], order
 
 
-def enlarge(blk, side, t, U):
+def enlarge(blk, side, t, U, geom=None):
     """Left block + site (side 'L') or site + right block (side 'R'), with the bond between the block's
-    edge site and the new site; the new site becomes the edge."""
+    edge site and the new site (hopping t); the new site becomes the edge.  With a geometry, the new
+    site's bonds to the edge and to the second site from the edge come from it, and on a ladder the old
+    edge is carried as the new block's second site from the edge."""
+    t0, t1 = (t, 0.0) if geom is None else geom.new_site_bonds(blk.nsites)
+    keep = geom is not None and geom.legs == 2
     s = site_block(U)
     Ib, I4 = np.eye(blk.dim, dtype=complex), np.eye(4, dtype=complex)
+    edges = [(blk.cdag, t0), (blk.cdag2, t1)]
     if side == "L":     # block string first: an odd site operator picks up the block parity
         Pb = blk.parity()
         H = np.kron(blk.H, I4) + np.kron(Ib, s.H)
-        cd_new = []
+        cd_new, carried = [], []
         for sig in range(2):
-            cb = np.kron(blk.cdag[sig], I4)
             cs = np.kron(Pb, s.cdag[sig])
-            H = H - t * (cb @ cs.conj().T + cs @ cb.conj().T)
+            for cdK, tb in edges:
+                if cdK is not None and tb != 0.0:
+                    cb = np.kron(cdK[sig], I4)
+                    H = H - tb * (cb @ cs.conj().T + cs @ cb.conj().T)
             cd_new.append(cs)
+            carried.append(np.kron(blk.cdag[sig], I4))
         qn = [(a + c, b + d) for (a, b) in blk.qn for (c, d) in SITE_QN]
     else:               # site string first: an odd block operator picks up the site parity
         H = np.kron(s.H, Ib) + np.kron(I4, blk.H)
-        cd_new = []
+        cd_new, carried = [], []
         for sig in range(2):
             cs = np.kron(s.cdag[sig], Ib)
-            cb = np.kron(SITE_P, blk.cdag[sig])
-            H = H - t * (cs @ cb.conj().T + cb @ cs.conj().T)
+            for cdK, tb in edges:
+                if cdK is not None and tb != 0.0:
+                    cb = np.kron(SITE_P, cdK[sig])
+                    H = H - tb * (cs @ cb.conj().T + cb @ cs.conj().T)
             cd_new.append(cs)
+            carried.append(np.kron(SITE_P, blk.cdag[sig]))
         qn = [(c + a, d + b) for (c, d) in SITE_QN for (a, b) in blk.qn]
-    qn, mats, order = _sorted(qn, [H] + cd_new)
-    out = DBlock(qn, mats[0], mats[1:], blk.nsites + 1)
+    qn, mats, order = _sorted(qn, [H] + cd_new + (carried if keep else []))
+    out = DBlock(qn, mats[0], mats[1:3], blk.nsites + 1, cdag2=mats[3:5] if keep else None)
     out.perm = order   # Kronecker index of each basis state: a * 4 + s (side 'L') or s * dim + a (side 'R')
     return out
 
 
-def superblock_of(L, R, t):
-    """Superblock, H_L, H_R and the boundary terms -t (c^dag_L c_R + h.c.) as fermionic products (left
-    operator first): -t c^dag_L c_R and +t c_L c^dag_R."""
+def superblock_of(L, R, t, geom=None):
+    """Superblock, H_L, H_R and the boundary terms -t (c^dag_L c_R + h.c.) of every bond across the cut as
+    fermionic products (left operator first): -t c^dag_L c_R and +t c_L c^dag_R.  Without a geometry the
+    one bond of the chain (hopping t) between the two edges."""
     lsec, ldim, _ = L.sectors()
     rsec, rdim, _ = R.sectors()
     sb = superblock.Superblock(lsec, ldim, rsec, rdim)
     HL, HR = L.blockop(L.H, False), R.blockop(R.H, False)
     conns = []
-    for sig in range(2):
-        cdL, cdR = L.blockop(L.cdag[sig], True), R.blockop(R.cdag[sig], True)
-        conns.append((-t, cdL, cdR.dagger()))
-        conns.append((t, cdL.dagger(), cdR))
+    bonds = [(0, 0, t)] if geom is None else geom.cut_bonds(L.nsites - 1)
+    for eL, eR, tb in bonds:
+        if tb == 0.0:
+            continue
+        opL = L.cdag if eL == 0 else L.cdag2
+        opR = R.cdag if eR == 0 else R.cdag2
+        for sig in range(2):
+            cdL, cdR = L.blockop(opL[sig], True), R.blockop(opR[sig], True)
+            conns.append((-tb, cdL, cdR.dagger()))
+            conns.append((tb, cdL.dagger(), cdR))
     return sb, HL, HR, conns
 
 
@@ -208,15 +266,19 @@ def truncate(blk, rho, m):
     U = np.concatenate(cols, axis=1)
     ren = lambda M: U.conj().T @ M @ U
     discarded = sum(float(np.sum(lam[k:])) for (lam, _), k in zip(eig, counts))
-    return DBlock(qn, ren(blk.H), [ren(c) for c in blk.cdag], blk.nsites), counts, [lam for lam, _ in eig], discarded, U
+    cdag2 = None if blk.cdag2 is None else [ren(c) for c in blk.cdag2]
+    return (DBlock(qn, ren(blk.H), [ren(c) for c in blk.cdag], blk.nsites, cdag2=cdag2), counts,
+            [lam for lam, _ in eig], discarded, U)
 
 
 class ChainDMRG:
-    """Infinite + finite two-site DMRG of the open Hubbard chain of L sites (L even) at half filling."""
+    """Infinite + finite two-site DMRG of the open Hubbard chain of L sites (L even) at half filling, or
+    of the two-leg ladder of L sites (geom = Geometry(2, t_leg, t_rung); the superblocks of the infinite
+    algorithm are ladders of 2l + 2 sites)."""
 
-    def __init__(self, L, t, U, m):
+    def __init__(self, L, t, U, m, geom=None):
         assert L % 2 == 0 and L >= 4
-        self.L, self.t, self.U, self.m = L, t, U, m
+        self.L, self.t, self.U, self.m, self.geom = L, t, U, m, geom
         self.left = {1: site_block(U)}
         self.right = {1: site_block(U)}
         self.right_U = {}   # right block of r sites: its kept states (columns) in the enlarged block of r - 1 sites
@@ -224,9 +286,9 @@ class ChainDMRG:
         self.energies = []
 
     def _step(self, l, r, Q):
-        Lenl = enlarge(self.left[l], "L", self.t, self.U)
-        Renl = enlarge(self.right[r], "R", self.t, self.U)
-        sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t)
+        Lenl = enlarge(self.left[l], "L", self.t, self.U, self.geom)
+        Renl = enlarge(self.right[r], "R", self.t, self.U, self.geom)
+        sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t, self.geom)
         e, psi = ground_state(lambda v: superblock.apply_h(sb, HL, HR, conns, Q, v), sb.size(Q))
         return Lenl, Renl, sb, e, psi
 
@@ -269,7 +331,7 @@ class ChainDMRG:
             self.sweep()
         h = self.L // 2
         Lenl, Renl, sb, e, psi = self._step(h - 1, h - 1, (h, h))
-        sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t)
+        sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t, self.geom)
         return Lenl, Renl, sb, HL, HR, conns, e, psi
 
 

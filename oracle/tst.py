@@ -66,8 +66,8 @@ class TSTSweep:
     def _blocks(self, l):
         d = self.d
         r = d.L - 2 - l
-        Lenl = dmrg.enlarge(d.left[l], "L", d.t, d.U)
-        Renl = dmrg.enlarge(d.right[r], "R", d.t, d.U)
+        Lenl = dmrg.enlarge(d.left[l], "L", d.t, d.U, d.geom)
+        Renl = dmrg.enlarge(d.right[r], "R", d.t, d.U, d.geom)
         return Lenl, Renl, r
 
     @staticmethod
@@ -87,7 +87,7 @@ class TSTSweep:
         phi, Q1, pending, done_step = None, Q0, list(self.excitations), None
         for step, (l, move) in enumerate(sweep_path(d.L)):
             Lenl, Renl, r = self._blocks(l)
-            sb, HL, HR, conns = dmrg.superblock_of(Lenl, Renl, d.t)
+            sb, HL, HR, conns = dmrg.superblock_of(Lenl, Renl, d.t, d.geom)
             hq = lambda Q: (lambda v: superblock.apply_h(sb, HL, HR, conns, Q, v))
             e, psi = dmrg.ground_state(hq(Q0), sb.size(Q0), resid_tol=self.gs_resid)
             # the evolve call: apply the operators of Eq. b reached here, then excite, advance or keep
@@ -123,16 +123,16 @@ class TSTSweep:
                 if move == "R":
                     rho = density.rho_left(sb, states, weights, self.real_basis)
                     K, counts, lams, disc, U = dmrg.truncate(Lenl, rho, self.m)
-                    Ln = dmrg.enlarge(K, "L", d.t, d.U)
-                    Rn = dmrg.enlarge(d.right[r - 1], "R", d.t, d.U)
+                    Ln = dmrg.enlarge(K, "L", d.t, d.U, d.geom)
+                    Rn = dmrg.enlarge(d.right[r - 1], "R", d.t, d.U, d.geom)
                     moved = [dmrg.wft_right(Lenl, Renl, Q, v, U, d.right[r], d.right_U[r], Ln, Rn)
                              for Q, v in states]
                     d.left[l + 1], d.left_U[l + 1] = K, U
                 else:
                     rho = density.rho_right(sb, states, weights, self.real_basis)
                     K, counts, lams, disc, U = dmrg.truncate(Renl, rho, self.m)
-                    Ln = dmrg.enlarge(d.left[l - 1], "L", d.t, d.U)
-                    Rn = dmrg.enlarge(K, "R", d.t, d.U)
+                    Ln = dmrg.enlarge(d.left[l - 1], "L", d.t, d.U, d.geom)
+                    Rn = dmrg.enlarge(K, "R", d.t, d.U, d.geom)
                     moved = [dmrg.wft_left(Lenl, Renl, Q, v, U, d.left[l], d.left_U[l], Ln, Rn)
                              for Q, v in states]
                     d.right[r + 1], d.right_U[r + 1] = K, U
