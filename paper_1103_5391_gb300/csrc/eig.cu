@@ -12,7 +12,11 @@
 //         X <- X (I + E);
 //      convergence is quadratic: from the FP32 seed (error ~1e-5) two iterations reach rounding level;
 //      up to four more run (decided on the device, launched regardless) while the last correction is
-//      above 1e-7, as for near-degenerate pairs that the first iteration treats as a cluster.  At
+//      above 1e-7, as for near-degenerate pairs that the first iteration treats as a cluster.  If the
+//      sixth is still above it (density matrices of DMRG blocks whose spectra span the whole FP64 range in
+//      large degenerate multiplets), two last steps only orthonormalise W (E = R / 2 for every pair, a
+//      Newton-Schulz step: orthogonality error eps -> ~eps^2 -> rounding), so that the kept states always
+//      form an orthonormal basis and the renormalised operators are projections.  At
 //      iterations 1 and 3 a sector whose clustered pairs stay coupled is re-seeded instead (FP32 Jacobi
 //      on S with a relative criterion, k_jacobi32).  The iterate is kept as W = X^H, so every product
 //      is a plain or conjugate-transposed GEMM operand;
@@ -37,7 +41,8 @@ constexpr int kJacSmemCap = 225 * 1024;   // dynamic shared memory of the Jacobi
 constexpr int kMaxEigN = 512;    // largest sector dimension
 constexpr int kKChunk = 16;      // K chunk of the refinement GEMMs
 constexpr int kRefine = 2;       // refinement iterations always run
-constexpr int kMaxRefine = 6;    // more, each only when the previous correction was not yet small
+constexpr int kOaIters = 6;      // more, each only when the previous correction was not yet small
+constexpr int kMaxRefine = 8;    // then, if the last one was still not small, two steps that only orthonormalise W
 constexpr float kReseedTol = 1e-7f;    // re-seed rotates (p, q) while |S_pq| > kReseedTol sqrt|S_pp S_qq| ...
 constexpr float kReseedFloor = 1e-14f; // ... and |S_pq| > kReseedFloor ||rho||_F
 // Refinement iterations that may re-seed a sector instead of updating it.
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(JT) k_jacobi32(const cplx* __restrict__ src, c
         if (rel) {
             thr_s = kReseedFloor;          // S is in units of ||rho||_F
             flags[sct] = 0;
-            atomicMax(n_iter, min(kMaxRefine, it + 3));
+            atomicMax(n_iter, min(kOaIters, it + 3));
         } else {
             thr_s = 4.8e-7f * sqrtf(f);    // 4 eps_fp32 ||A||_F: above FP32 rounding noise, so sweeps terminate
             rho_fro[sct] = sqrtf(f);       // ||rho||_F for the refinement's cluster threshold
@@ -524,6 +529,7 @@ __global__ void __launch_bounds__(kOaThreads) k_oa_update(const cplx* __restrict
         if (e < item.z) { sv[u] = S[off + e]; g[u] = G[off + e]; }
     }
     bool big = false, clus = false;
+    const bool orth_only = it >= kOaIters;   // E = R / 2: W <- (I + R / 2) W, a Newton-Schulz step
 #pragma unroll
     for (int u = 0; u < kOaPer; ++u) {
         const int e = item.y + threadIdx.x + kOaThreads * u;
@@ -532,20 +538,23 @@ __global__ void __launch_bounds__(kOaThreads) k_oa_update(const cplx* __restrict
             const double2 r = make_double2((i == j ? 1.0 : 0.0) - g[u].x, -g[u].y);
             double2 ev;
             const double li = lam[eo + i], lj = lam[eo + j];
-            if (i != j && fabs(li - lj) > delta) {
+            if (!orth_only && i != j && fabs(li - lj) > delta) {
                 const double inv = 1.0 / (li - lj);
                 ev = make_double2((sv[u].x + li * r.x) * inv, (sv[u].y + li * r.y) * inv);
             } else {
                 ev = make_double2(0.5 * r.x, 0.5 * r.y);
                 // clustered pair still coupled: the cluster is not diagonalised by this update
-                if (i != j) clus |= fmax(fabs(sv[u].x), fabs(sv[u].y)) > floor_s;
+                if (i != j && !orth_only) clus |= fmax(fabs(sv[u].x), fabs(sv[u].y)) > floor_s;
             }
             big |= fmax(fabs(ev.x), fabs(ev.y)) > kTolE;
             E1h[off + e] = ev;   // the update adds the identity: W' = (I + E1h) W
         }
     }
-    // from the last iteration that always runs on, a correction still above kTolE asks for one more
-    if (it >= kRefine - 1 && it + 1 < kMaxRefine && __syncthreads_or(big) && threadIdx.x == 0) atomicMax(n_iter, it + 2);
+    // from the last iteration that always runs on, a correction still above kTolE asks for one more; after
+    // the last such iteration it asks for both orthonormalisation steps (an orthogonality error eps of W
+    // becomes ~eps^2, then rounding), so that the eigenvectors always span an orthonormal basis
+    if (it >= kRefine - 1 && it < kOaIters && __syncthreads_or(big) && threadIdx.x == 0)
+        atomicMax(n_iter, it + 1 < kOaIters ? it + 2 : kMaxRefine);
     // at a re-seed iteration, a cluster with coupling above the floor sends the sector to the re-seed
     if (reseed_iter(it) && __syncthreads_or(clus) && threadIdx.x == 0) flags[sct] = 1;
 }
@@ -793,10 +802,13 @@ cudaError_t launch_group(tdmrg_ctx* c, EigWork& w, EigGroup& G, const cplx* rho,
     cudaError_t e = cudaGetLastError();
     for (; it < kMaxRefine && e == cudaSuccess; ++it) {
         a.bufs[EB_W] = W; a.bufs[EB_WN] = Wn;
-        e = gemm(G.tl_ax, false);
+        // the orthonormalisation steps need G = W W^H only (S is formed but not read, lambda stays)
+        const bool orth_only = it >= kOaIters;
+        if (!orth_only) e = gemm(G.tl_ax, false);
         if (e == cudaSuccess) e = gemm(G.tl_sg, false);
         if (G.noa) {
-            launch_pdl(k_oa_norms, G.noa, kOaThreads, 0, s, S, Gm, w.lam, (const double*)G.fro, oat, n_iter, it, tb);
+            if (!orth_only)
+                launch_pdl(k_oa_norms, G.noa, kOaThreads, 0, s, S, Gm, w.lam, (const double*)G.fro, oat, n_iter, it, tb);
             launch_pdl(k_oa_update, G.noa, kOaThreads, 0, s, S, Gm, w.lam, oat, (const double*)G.fro, E1h, n_iter, G.flags,
                        it, tb);
         }
@@ -807,7 +819,7 @@ cudaError_t launch_group(tdmrg_ctx* c, EigWork& w, EigGroup& G, const cplx* rho,
             replay(E1h, true);
         }
         if (e == cudaSuccess) e = gemm(G.tl_y, true);
-        c->launches += 2;
+        if (G.noa) c->launches += orth_only ? 1 : 2;
         std::swap(W, Wn);
     }
     if (e == cudaSuccess) {
