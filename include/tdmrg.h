@@ -311,6 +311,22 @@ int tdmrg_enlarge(tdmrg_ctx* ctx, int side, int nsec, const int32_t* qn, const i
                   const tdmrg_blocks* cdag, double t, double U, tdmrg_c64* H_out, tdmrg_c64* const* cdag_out,
                   int32_t* const* cdag_qn_out, tdmrg_c64* const* n_out);
 
+/* Enlargement on the two-leg ladder (Sec. III.A Fig. 2: 8 x 2 ladder; Sec. III.B: 2 x 4 ladders), where a
+ * new site bonds to two sites of K: as tdmrg_enlarge, with nedge (1 or 2) bonds of the new site, to K's edge
+ * site (c^dag in cdag[0], cdag[1], hopping t[0]) and to the second site from the edge (cdag[2], cdag[3],
+ * t[1]); a zero t[e] leaves that bond out (cdag[2e], cdag[2e+1] must still be valid block lists, possibly
+ * empty).  With carry_out (device, nullable; each entry non-null) K's edge is carried into the enlarged
+ * block as its second site from the edge: carry_out[s] receives c^dag_{K edge, s} x 1 (side 0) or
+ * P x c^dag_{K edge, s} (side 1, P the site parity) with the block list and layout of cdag_out[s]
+ * (tdmrg_enlarge_size's entries[1 + s]).  nedge = 1 without carry_out is tdmrg_enlarge.  The second
+ * bond's terms fall on the sub-blocks of the first's and are added by a second placement launch, the
+ * carried edge by a third; synchronises the stream.
+ * Errors: as tdmrg_enlarge; EINVAL also for nedge outside 1..2, t NULL or a NULL carry_out entry. */
+int tdmrg_enlarge_bonds(tdmrg_ctx* ctx, int side, int nsec, const int32_t* qn, const int32_t* dim,
+                        const tdmrg_blocks* H, int nedge, const tdmrg_blocks* cdag, const double* t, double U,
+                        tdmrg_c64* H_out, tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out,
+                        tdmrg_c64* const* n_out, tdmrg_c64* const* carry_out);
+
 /* Operator op_id of one side defined as the adjoint of operator src_id of the same side (block (q_in, q_out)
  * = the conjugate transpose of block (q_out, q_in); same fermion parity): e.g. c from c^dag for the
  * Hamiltonian's boundary terms.  Synchronises the stream.  Errors: EINVAL (unknown src_id, op_id < 0 or equal

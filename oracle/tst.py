@@ -54,14 +54,15 @@ class TSTSweep:
         """d: a ChainDMRG that has run (its blocks and their kept bases are the sweep's start); m: states
         kept per block during the sweep; gs_resid: the ground state's residual bound (the excitation and
         the ground-state target inherit its error to first order); excitations: [(site, 'cdag' | 'c',
-        sigma)] in the order the sweep reaches them (default: c^dag_{L/2, up}, reached at once)."""
+        sigma)] in the order the sweep reaches them ([]: the ground state alone, a finite DMRG sweep; default
+        c^dag_{L/2, up}, reached at once)."""
         self.gs_resid = gs_resid
         self.d, self.m, self.n_v, self.tau, self.nk = d, m, n_v, tau, nk
         self.advance_every = advance_every
         self.real_basis = real_basis
         self.times = krylov.target_times(tau, n_v)
         self.w_gs, self.w = density.tst_weights(n_v)
-        self.excitations = list(excitations) if excitations else [(d.L // 2, "cdag", 0)]
+        self.excitations = list(excitations) if excitations is not None else [(d.L // 2, "cdag", 0)]
 
     def _blocks(self, l):
         d = self.d

@@ -18,6 +18,11 @@
 // of disjoint sub-blocks ("runs" pairs), each a scaled copy, scaled adjoint or scaled identity of a block
 // of K, so one launch places all of them into zeroed outputs (no sub-block is written twice: the U term
 // rides on the H_K copy's diagonal).
+//
+// Ladders (Sec. III): the new site also bonds to the second site from K's edge (a leg when the edge bond is
+// a rung or absent), whose bond terms fall on the same sub-blocks of H' as the edge's, so they are added by
+// a second launch; and K's edge becomes the enlarged block's second site from the edge, carried as
+// c^dag_K x 1 (left) or P_site x c^dag_K (right) with the block layout of the new edge's c^dag'.
 #include <algorithm>
 #include <array>
 #include <map>
@@ -42,6 +47,7 @@ struct Place {
     int ldd, lds;
     int rows, cols;         // destination extent
     int8_t dbuf, sbuf, mode;
+    int8_t acc;             // add to the destination instead of writing it
     double2 scale;
     double diag;            // added on the diagonal (MODE_COPY, MODE_ADJ)
 };
@@ -80,6 +86,7 @@ __global__ void __launch_bounds__(256) k_place(const Place* __restrict__ items, 
         }
         cplx y = make_double2(it.scale.x * x.x - it.scale.y * x.y, it.scale.x * x.y + it.scale.y * x.x);
         if (i == j && it.mode != MODE_EYE) y.x += it.diag;
+        if (it.acc) { const cplx o = dst[(int64_t)i * it.ldd + j]; y.x += o.x; y.y += o.y; }
         dst[(int64_t)i * it.ldd + j] = y;
     }
 }
@@ -191,11 +198,18 @@ extern "C" int tdmrg_enlarge_size(int side, int nsec, const int32_t* qn, const i
     return TDMRG_OK;
 }
 
-extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const int32_t* dim,
-                             const tdmrg_blocks* H, const tdmrg_blocks* cdag, double t, double U, tdmrg_c64* H_out,
-                             tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out, tdmrg_c64* const* n_out) {
+namespace tdmrg {
+namespace {
+
+// The enlargement with nedge (1 or 2) bonds of the new site: edge e of K with c^dag cdag[2e + s] and
+// hopping t[e]; carry_out (nullable): K's edge carried as the enlarged block's second site from the edge.
+int enlarge_impl(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const int32_t* dim, const tdmrg_blocks* H,
+                 int nedge, const tdmrg_blocks* cdag, const double* t, double U, tdmrg_c64* H_out,
+                 tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out, tdmrg_c64* const* n_out,
+                 tdmrg_c64* const* carry_out) {
     if (!c) return fail(nullptr, TDMRG_EINVAL, "null context");
-    if ((side != 0 && side != 1) || !H || !cdag || !H_out || !cdag_out || !cdag_out[0] || !cdag_out[1])
+    if ((side != 0 && side != 1) || !H || !cdag || !t || nedge < 1 || nedge > 2 || !H_out || !cdag_out ||
+        !cdag_out[0] || !cdag_out[1] || (carry_out && (!carry_out[0] || !carry_out[1])))
         return fail(c, TDMRG_EINVAL, "enlarge: bad argument");
     int rc = check_block_table(nsec, qn, dim);
     if (rc) return fail(c, rc, "enlarge: bad sector table (ascending, dims >= 1)");
@@ -237,10 +251,20 @@ extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn
             }
             items.push_back(p);
         }
+    // bond terms of edge e (first bonded edge: into the first launch; the other: added by a second one)
+    std::vector<Place> bond_items[2];
+    int first_bond = -1;
+    for (int e = 0; e < nedge; ++e)
+        if (t[e] != 0.0 && first_bond < 0) first_bond = e;
+    for (int e = 0; e < nedge; ++e)
     for (int sg = 0; sg < 2; ++sg) {
-        const tdmrg_blocks& C = cdag[sg];
+        const tdmrg_blocks& C = cdag[2 * e + sg];
         if (C.nblk < 0 || (C.nblk > 0 && (!C.blk_qn || !C.data_d)))
             return fail(c, TDMRG_EINVAL, "enlarge: c^dag blocks without data");
+        if (t[e] == 0.0) continue;
+        std::vector<Place>& dst_items = e == first_bond ? items : bond_items[e];
+        const double te = t[e];
+        const int8_t acc = e == first_bond ? 0 : 1;
         int64_t so = 0;
         for (int k = 0; k < C.nblk; ++k) {
             const int32_t* b = C.blk_qn + 4 * k;
@@ -253,12 +277,13 @@ extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn
                 // K-raising, site-lowering: (q, to) -> (q + e, from); K-lowering, site-raising: (q + e, from) -> (q, to)
                 Place a{}, d{};
                 if (side == 0) {   // -t (c^dag_K P_K) x c_site and -t (P_K c_K) x c^dag_site, P_K on sector q
-                    a.scale = make_double2(-t * pk * h.v, 0.0);
+                    a.scale = make_double2(-te * pk * h.v, 0.0);
                     d.scale = a.scale;
                 } else {           // -t (P_site c_site) x c^dag_K and -t (c^dag_site P_site) x c_K, p(from)
-                    a.scale = make_double2(-t * kParity[h.from] * h.v, 0.0);
+                    a.scale = make_double2(-te * kParity[h.from] * h.v, 0.0);
                     d.scale = a.scale;
                 }
+                a.acc = d.acc = acc;
                 const int oa = hsec(qo, h.from), ob = hsec(qi, h.to);
                 if (oa != ob) return fail(c, TDMRG_ESECTOR, "enlarge: inconsistent sectors");
                 a.mode = MODE_COPY; a.sbuf = (int8_t)(1 + sg); a.src = so; a.lds = dim[qi];
@@ -267,12 +292,39 @@ extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn
                 d.mode = MODE_ADJ; d.sbuf = (int8_t)(1 + sg); d.src = so; d.lds = dim[qi];
                 d.dst = L.hoff[oa] + (int64_t)L.roff[qi][h.to] * L.dim[oa] + L.roff[qo][h.from];
                 d.ldd = L.dim[oa]; d.rows = dim[qi]; d.cols = dim[qo]; d.dbuf = OH;
-                items.push_back(a);
-                items.push_back(d);
+                dst_items.push_back(a);
+                dst_items.push_back(d);
             }
             so += (int64_t)dim[qo] * dim[qi];
         }
     }
+    // K's edge carried: its blocks (q_o, q_i) copied to the runs (q_o, s) x (q_i, s) of every site state s,
+    // scaled by the site parity on the right (the site's fermion comes first)
+    std::vector<Place> carry_items;
+    if (carry_out)
+        for (int sg = 0; sg < 2; ++sg) {
+            std::map<int, size_t> blk_of_in;
+            for (size_t k = 0; k < L.cblk[sg].size(); ++k) blk_of_in[L.cblk[sg][k].second] = k;
+            const tdmrg_blocks& C = cdag[sg];
+            int64_t so = 0;
+            for (int k = 0; k < C.nblk; ++k) {
+                const int32_t* b = C.blk_qn + 4 * k;
+                const int qo = kfind(b[0], b[1]), qi = kfind(b[2], b[3]);
+                for (int st = 0; st < 4; ++st) {
+                    const int oi = hsec(qi, st), oo = hsec(qo, st);
+                    const auto it = blk_of_in.find(oi);
+                    if (it == blk_of_in.end() || L.cblk[sg][it->second].first != oo)
+                        return fail(c, TDMRG_ESECTOR, "enlarge: inconsistent carried edge sectors");
+                    Place p{};
+                    p.mode = MODE_COPY; p.sbuf = (int8_t)(1 + sg); p.src = so; p.lds = dim[qi];
+                    p.scale = make_double2(side == 0 ? 1.0 : (double)kParity[st], 0.0);
+                    p.dst = L.coff[sg][it->second] + (int64_t)L.roff[qo][st] * L.dim[oi] + L.roff[qi][st];
+                    p.ldd = L.dim[oi]; p.rows = dim[qo]; p.cols = dim[qi]; p.dbuf = (int8_t)sg;
+                    carry_items.push_back(p);
+                }
+                so += (int64_t)dim[qo] * dim[qi];
+            }
+        }
     // the new edge operators: scaled identities between the runs (q, from) and (q, to)
     for (int sg = 0; sg < 2; ++sg) {
         std::map<int, size_t> blk_of_in;
@@ -320,12 +372,47 @@ extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn
     for (int sg = 0; sg < 2 && !rc; ++sg)
         if (L.nC[sg]) rc = cuda_check(c, cudaMemsetAsync(cdag_out[sg], 0, (size_t)L.nC[sg] * sizeof(cplx), c->stream),
                                       "enlarge clear");
+    for (int sg = 0; sg < 2 && !rc && carry_out; ++sg)
+        if (L.nC[sg]) rc = cuda_check(c, cudaMemsetAsync(carry_out[sg], 0, (size_t)L.nC[sg] * sizeof(cplx), c->stream),
+                                      "enlarge clear");
     if (rc) return rc;
+    const int e0 = first_bond < 0 ? 0 : first_bond;
     PlaceBufs pb{};
     pb.d[0] = (cplx*)H_out; pb.d[1] = (cplx*)cdag_out[0]; pb.d[2] = (cplx*)cdag_out[1];
     pb.d[3] = n_out ? (cplx*)n_out[0] : nullptr; pb.d[4] = n_out ? (cplx*)n_out[1] : nullptr;
-    pb.s[0] = (const cplx*)H->data_d; pb.s[1] = (const cplx*)cdag[0].data_d; pb.s[2] = (const cplx*)cdag[1].data_d;
-    return launch_places(c, items, pb);
+    pb.s[0] = (const cplx*)H->data_d;
+    pb.s[1] = (const cplx*)cdag[2 * e0].data_d; pb.s[2] = (const cplx*)cdag[2 * e0 + 1].data_d;
+    rc = launch_places(c, items, pb);
+    for (int e = 0; e < nedge && !rc; ++e) {
+        if (bond_items[e].empty()) continue;
+        PlaceBufs pe{};
+        pe.d[0] = (cplx*)H_out;
+        pe.s[1] = (const cplx*)cdag[2 * e].data_d; pe.s[2] = (const cplx*)cdag[2 * e + 1].data_d;
+        rc = launch_places(c, bond_items[e], pe);
+    }
+    if (!rc && !carry_items.empty()) {
+        PlaceBufs pc{};
+        pc.d[0] = (cplx*)carry_out[0]; pc.d[1] = (cplx*)carry_out[1];
+        pc.s[1] = (const cplx*)cdag[0].data_d; pc.s[2] = (const cplx*)cdag[1].data_d;
+        rc = launch_places(c, carry_items, pc);
+    }
+    return rc;
+}
+
+}  // namespace
+}  // namespace tdmrg
+
+extern "C" int tdmrg_enlarge(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const int32_t* dim,
+                             const tdmrg_blocks* H, const tdmrg_blocks* cdag, double t, double U, tdmrg_c64* H_out,
+                             tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out, tdmrg_c64* const* n_out) {
+    return enlarge_impl(c, side, nsec, qn, dim, H, 1, cdag, &t, U, H_out, cdag_out, cdag_qn_out, n_out, nullptr);
+}
+
+extern "C" int tdmrg_enlarge_bonds(tdmrg_ctx* c, int side, int nsec, const int32_t* qn, const int32_t* dim,
+                                   const tdmrg_blocks* H, int nedge, const tdmrg_blocks* cdag, const double* t, double U,
+                                   tdmrg_c64* H_out, tdmrg_c64* const* cdag_out, int32_t* const* cdag_qn_out,
+                                   tdmrg_c64* const* n_out, tdmrg_c64* const* carry_out) {
+    return enlarge_impl(c, side, nsec, qn, dim, H, nedge, cdag, t, U, H_out, cdag_out, cdag_qn_out, n_out, carry_out);
 }
 
 extern "C" int tdmrg_set_op_adjoint(tdmrg_ctx* c, int side, int op_id, int src_id) {

@@ -9,7 +9,13 @@ and -- when it was cut from an enlarged block -- its states in that block's basi
 tdmrg_rho_eig) with the kept counts, which the wave-function transformation needs.  Enlarged blocks
 (Enlarged) add the new site's densities.  Operator ids inside a superblock context: 0 = H, 10 + s =
 c^dag_{edge s}, 30 + s = its adjoint, 50 + s = n_{edge s}; the boundary terms are -t c^dag_L c_R and
-+t c_L c^dag_R per spin.
++t c_L c^dag_R per spin and bond.
+
+Ladders (Sec. III: the 8 x 2 ladder of Fig. 2, the 2 x 4 ladders of Figs. 3-4; Lattice): sites i = 2x + y
+in rung-first order, site i bonds to i - 1 across a rung when i is odd and to i - 2 along a leg, so a block
+also carries c^dag of its second site from the edge (20 + s, adjoint 40 + s), the enlargement bonds the
+new site to both (tdmrg_enlarge_bonds) and the central cut is crossed by two legs and, when the left
+enlarged block ends on the first site of a rung, by that rung.
 
 Excitation (Eq. b): phi = B_{b-1} ... B_0 psi with local c^dag / c operators on sites in the order the
 sweep reaches them; B_i is applied at the first step whose central pair of sites (l, the new site of the
@@ -27,46 +33,91 @@ import torch
 
 from . import tdmrg as T
 
-H_ID, CDAG_ID, C_ID, N_ID = 0, 10, 30, 50
+H_ID, CDAG_ID, CDAG2_ID, C_ID, C2_ID, N_ID = 0, 10, 20, 30, 40, 50
 
 
 def _zeros(n, dev):
     return torch.zeros(max(int(n), 1), dtype=torch.complex128, device=dev)
 
 
+class Lattice:
+    """Bonds of the lattice (host tables): the open chain (legs = 1, hopping t_leg between neighbours) or
+    the two-leg ladder with rung-first labels (legs = 2).  An even number of sites makes the ladder
+    symmetric under reflection i -> N - 1 - i (which exchanges the legs), so a right block of r sites bonds
+    like a left block of r sites."""
+
+    def __init__(self, legs=1, t_leg=1.0, t_rung=1.0):
+        if legs not in (1, 2):
+            raise ValueError("Lattice: legs must be 1 (chain) or 2 (ladder)")
+        self.legs, self.t_leg, self.t_rung = legs, float(t_leg), float(t_rung)
+
+    def new_site_bonds(self, k):
+        """Hoppings of a new site with k sites between it and the block's open end to the block's edge
+        site and to its second site from the edge."""
+        if self.legs == 1:
+            return (self.t_leg if k >= 1 else 0.0), 0.0
+        return (self.t_rung if k % 2 == 1 else 0.0), (self.t_leg if k >= 2 else 0.0)
+
+    def cut_bonds(self, l):
+        """(left edge index, right edge index, hopping) of the bonds between the left enlarged block (sites
+        0..l) and the right one; edge 0 is the site at the cut, edge 1 the next one."""
+        if self.legs == 1:
+            return [(0, 0, self.t_leg)]
+        return ([(0, 0, self.t_rung)] if l % 2 == 0 else []) + [(1, 0, self.t_leg), (0, 1, self.t_leg)]
+
+
 class Block:
     """A kept block on the device."""
 
-    def __init__(self, qn, dim, H, cdag, V=None, kept_V=None):
+    def __init__(self, qn, dim, H, cdag, V=None, kept_V=None, nsites=None, cdag2=None):
         self.qn = [tuple(int(x) for x in q) for q in qn]
         self.dim = [int(x) for x in dim]
         self.H = H            # (block quantum numbers, device data)
         self.cdag = cdag      # [(qns, data), (qns, data)] for up, down
         self.V = V            # its states in the enlarged block it was cut from (tdmrg_rho_eig layout), or None
         self.kept_V = kept_V  # kept counts per sector of that enlarged block
+        self.nsites = nsites  # sites in the block (needed on a ladder)
+        self.cdag2 = cdag2    # ladder: c^dag of the second site from the edge, like cdag; None on a chain
 
 
 class Enlarged:
     """K + site or site + K on the device, with the new site's densities."""
 
-    def __init__(self, qn, dim, H, cdag, n):
+    def __init__(self, qn, dim, H, cdag, n, nsites=None, cdag2=None):
         self.qn, self.dim, self.H, self.cdag, self.n = qn, dim, H, cdag, n
+        self.nsites, self.cdag2 = nsites, cdag2
 
 
-def enlarge(ctx, blk, side, t, U, dev):
+def enlarge(ctx, blk, side, t, U, dev, lattice=None):
+    """blk + site (side 0) or site + blk (side 1).  Chain: the bond -t between blk's edge and the new site.
+    lattice: the new site's bonds from it; on a ladder blk's edge is carried as the second site from the
+    enlarged block's edge."""
     qn, dim, nb, ent = T.tdmrg_enlarge_size(side, blk.qn, blk.dim)
     qn = [tuple(int(x) for x in q) for q in qn]
     dim = [int(x) for x in dim]
     H = _zeros(ent[0], dev)
     cd = [_zeros(ent[1 + s], dev) for s in range(2)]
     n = [_zeros(ent[0], dev) for _ in range(2)]
-    cq = T.tdmrg_enlarge(ctx, side, blk.qn, blk.dim, blk.H, blk.cdag, t, U, H, cd, n)
     hq = [q + q for q in qn]
-    return Enlarged(qn, dim, (hq, H), [(cq[s], cd[s]) for s in range(2)], [(hq, n[s]) for s in range(2)])
+    nsites = None if blk.nsites is None else blk.nsites + 1
+    if lattice is None or lattice.legs == 1:
+        tb = t if lattice is None else lattice.new_site_bonds(blk.nsites if blk.nsites is not None else 1)[0]
+        cq = T.tdmrg_enlarge(ctx, side, blk.qn, blk.dim, blk.H, blk.cdag, tb, U, H, cd, n)
+        return Enlarged(qn, dim, (hq, H), [(cq[s], cd[s]) for s in range(2)], [(hq, n[s]) for s in range(2)], nsites)
+    t0, t1 = lattice.new_site_bonds(blk.nsites)
+    edges, ts = [blk.cdag], [t0]
+    if blk.cdag2 is not None:
+        edges.append(blk.cdag2)
+        ts.append(t1)
+    carry = [_zeros(ent[1 + s], dev) for s in range(2)]
+    cq = T.tdmrg_enlarge_bonds(ctx, side, blk.qn, blk.dim, blk.H, edges, ts, U, H, cd, n, carry)
+    return Enlarged(qn, dim, (hq, H), [(cq[s], cd[s]) for s in range(2)], [(hq, n[s]) for s in range(2)], nsites,
+                    [(cq[s], carry[s]) for s in range(2)])
 
 
-def load(ctx, Lenl, Renl, t):
-    """The superblock (Lenl, Renl) with the Hubbard bond between the two edge sites."""
+def load(ctx, Lenl, Renl, t, lattice=None, l=None):
+    """The superblock (Lenl, Renl) with the Hubbard bonds across the cut: the one between the two edge sites
+    (hopping t) without a lattice, else the lattice's bonds at the cut after site l."""
     for side, b in enumerate((Lenl, Renl)):
         T.tdmrg_set_block(ctx, side, b.qn, b.dim)
     for side, b in enumerate((Lenl, Renl)):
@@ -75,7 +126,14 @@ def load(ctx, Lenl, Renl, t):
             T.tdmrg_set_op_device(ctx, side, CDAG_ID + s, 1, *b.cdag[s])
             T.tdmrg_set_op_adjoint(ctx, side, C_ID + s, CDAG_ID + s)
             T.tdmrg_set_op_device(ctx, side, N_ID + s, 0, *b.n[s])
-    conns = [(CDAG_ID + s, C_ID + s, -t) for s in range(2)] + [(C_ID + s, CDAG_ID + s, t) for s in range(2)]
+            if b.cdag2 is not None:
+                T.tdmrg_set_op_device(ctx, side, CDAG2_ID + s, 1, *b.cdag2[s])
+                T.tdmrg_set_op_adjoint(ctx, side, C2_ID + s, CDAG2_ID + s)
+    bonds = [(0, 0, t)] if lattice is None else [x for x in lattice.cut_bonds(l) if x[2] != 0.0]
+    cd_id = lambda e: CDAG_ID if e == 0 else CDAG2_ID
+    c_id = lambda e: C_ID if e == 0 else C2_ID
+    conns = [(cd_id(eL) + s, c_id(eR) + s, -tb) for eL, eR, tb in bonds for s in range(2)]
+    conns += [(c_id(eL) + s, cd_id(eR) + s, tb) for eL, eR, tb in bonds for s in range(2)]
     T.tdmrg_set_hamiltonian(ctx, H_ID, H_ID, conns)
 
 
@@ -102,13 +160,17 @@ def truncate_block(ctx, side, enl, states, weights, m, real_basis, dev):
     kq = [q for q, k in zip(enl.qn, kept) if k > 0]
     kd = [k for k in kept if k > 0]
     ops = []
-    for op_id, qns in [(H_ID, enl.H[0]), (CDAG_ID, enl.cdag[0][0]), (CDAG_ID + 1, enl.cdag[1][0])]:
+    todo = [(H_ID, enl.H[0]), (CDAG_ID, enl.cdag[0][0]), (CDAG_ID + 1, enl.cdag[1][0])]
+    if enl.cdag2 is not None:
+        todo += [(CDAG2_ID, enl.cdag2[0][0]), (CDAG2_ID + 1, enl.cdag2[1][0])]
+    for op_id, qns in todo:
         out = _zeros(sum(enl.dim[enl.qn.index(tuple(q[:2]))] * enl.dim[enl.qn.index(tuple(q[2:]))] for q in qns), dev)
         nb = T.tdmrg_renormalize_op(ctx, side, op_id, U, kept, out)
         kb = _kept_blocks(qns, kept_of)
         assert nb == len(kb)
         ops.append((kb, out))
-    K = Block(kq, kd, ops[0], ops[1:], V=U, kept_V=kept)
+    K = Block(kq, kd, ops[0], ops[1:3], V=U, kept_V=kept, nsites=enl.nsites,
+              cdag2=ops[3:5] if enl.cdag2 is not None else None)
     ev = evals.cpu().numpy()
     off = np.concatenate([[0], np.cumsum(enl.dim)])
     rec = {"kept": kept, "evals": [ev[off[i]: off[i + 1]] for i in range(len(enl.dim))],
@@ -117,16 +179,19 @@ def truncate_block(ctx, side, enl, states, weights, m, real_basis, dev):
 
 
 class TSTSweep:
-    """One finite sweep of the L-site Hubbard chain (half filling) with time-step targeting, on the device.
+    """One finite sweep of the L-site Hubbard chain or two-leg ladder (half filling) with time-step
+    targeting, on the device.
 
     left, right: dicts {number of sites: Block} of the stored blocks the sweep starts from (each block of
     two or more sites with its V and kept counts); they are replaced by the blocks the sweep makes."""
 
     def __init__(self, L, t, U, m, left, right, n_v=4, tau=0.1, nk=12, advance_every=2, gs_nk=32, gs_restarts=40,
-                 real_basis=False, device=None, excitations=None, prec=None, ozaki_slices=4):
+                 real_basis=False, device=None, excitations=None, prec=None, ozaki_slices=4, lattice=None):
         """prec: arithmetic of the superblock products (T.TDMRG_FP64, the default, or T.TDMRG_OZAKI_BF16
-        with ozaki_slices slices); everything else stays FP64."""
+        with ozaki_slices slices); everything else stays FP64.  lattice: a Lattice (default: the chain with
+        hopping t); on a ladder every stored block carries its nsites and cdag2."""
         self.L, self.t, self.U, self.m = L, t, U, m
+        self.lattice = lattice
         self.prec = T.TDMRG_FP64 if prec is None else prec
         self.ozaki_slices = ozaki_slices
         self.left, self.right = dict(left), dict(right)
@@ -136,7 +201,9 @@ class TSTSweep:
         self.dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.times = [x * tau / (n_v - 1) for x in range(n_v)]
         self.w_gs, self.w = T.tdmrg_tst_weights(n_v)
-        self.excitations = list(excitations) if excitations else [(L // 2, "cdag", 0)]
+        # excitations: [(site, 'cdag' | 'c', sigma)] in sweep order; [] targets the ground state alone (a
+        # finite DMRG sweep); None: c^dag_{L/2, up}
+        self.excitations = list(excitations) if excitations is not None else [(L // 2, "cdag", 0)]
 
     def path(self):
         h, L = self.L // 2 - 1, self.L
@@ -170,9 +237,9 @@ class TSTSweep:
         try:
             path = self.path()
             l0 = path[0][0]
-            Lenl = enlarge(work, self.left[l0], 0, self.t, self.U, self.dev)
-            Renl = enlarge(work, self.right[L - 2 - l0], 1, self.t, self.U, self.dev)
-            load(cur, Lenl, Renl, self.t)
+            Lenl = enlarge(work, self.left[l0], 0, self.t, self.U, self.dev, self.lattice)
+            Renl = enlarge(work, self.right[L - 2 - l0], 1, self.t, self.U, self.dev, self.lattice)
+            load(cur, Lenl, Renl, self.t, self.lattice, l0)
             if psi0 is None:
                 n0 = T.tdmrg_sector_size(cur, Q0)
                 g = torch.Generator().manual_seed(11035391)
@@ -222,9 +289,9 @@ class TSTSweep:
                                                  self.real_basis, self.dev)
                     rec.update(trec)
                     if move == "R":
-                        nL = enlarge(work, K, 0, self.t, self.U, self.dev)
-                        nR = enlarge(work, self.right[r - 1], 1, self.t, self.U, self.dev)
-                        load(nxt, nL, nR, self.t)
+                        nL = enlarge(work, K, 0, self.t, self.U, self.dev, self.lattice)
+                        nR = enlarge(work, self.right[r - 1], 1, self.t, self.U, self.dev, self.lattice)
+                        load(nxt, nL, nR, self.t, self.lattice, l + 1)
                         Rb = self.right[r]
                         moved = []
                         for Q, v in states:
@@ -233,9 +300,9 @@ class TSTSweep:
                             moved.append(o)
                         self.left[l + 1] = K
                     else:
-                        nL = enlarge(work, self.left[l - 1], 0, self.t, self.U, self.dev)
-                        nR = enlarge(work, K, 1, self.t, self.U, self.dev)
-                        load(nxt, nL, nR, self.t)
+                        nL = enlarge(work, self.left[l - 1], 0, self.t, self.U, self.dev, self.lattice)
+                        nR = enlarge(work, K, 1, self.t, self.U, self.dev, self.lattice)
+                        load(nxt, nL, nR, self.t, self.lattice, l - 1)
                         Lb = self.left[l]
                         moved = []
                         for Q, v in states:

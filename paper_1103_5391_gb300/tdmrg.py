@@ -20,7 +20,7 @@ EXPORTED = [
     "tdmrg_default_opts", "tdmrg_create", "tdmrg_destroy", "tdmrg_set_stream", "tdmrg_set_precision",
     "tdmrg_last_error", "tdmrg_set_block", "tdmrg_set_op", "tdmrg_set_hamiltonian", "tdmrg_set_coefficients", "tdmrg_sector_size",
     "tdmrg_apply_h", "tdmrg_apply_op", "tdmrg_evolve", "tdmrg_evolve_info", "tdmrg_ground_state", "tdmrg_direct_sum", "tdmrg_evolve_segments", "tdmrg_evolve_segments_info", "tdmrg_tst_weights",
-    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_density_eig", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
+    "tdmrg_rho_size", "tdmrg_density_matrix", "tdmrg_set_real_basis", "tdmrg_rho_eig", "tdmrg_truncate", "tdmrg_renormalize_op", "tdmrg_wft_right", "tdmrg_wft_left", "tdmrg_density_matrix_side", "tdmrg_rho_size_side", "tdmrg_rho_eig_side", "tdmrg_density_eig", "tdmrg_truncate_side", "tdmrg_enlarge_size", "tdmrg_enlarge", "tdmrg_enlarge_bonds", "tdmrg_set_op_adjoint", "tdmrg_expect", "tdmrg_overlap_op", "tdmrg_correlation",
     "tdmrg_launch_count", "tdmrg_alloc_count", "tdmrg_hpsi_flops", "tdmrg_hpsi_tensor_flops", "tdmrg_fp64_peak", "tdmrg_apply_h_static",
     "tdmrg_set_schedule", "tdmrg_probe_wait", "tdmrg_hpsi_thin_flops", "tdmrg_set_thin_dim", "tdmrg_eig_stats", "tdmrg_set_tile_m", "tdmrg_hpsi_tuning", "tdmrg_set_orth_per_sm",
     "tdmrg_server_create", "tdmrg_server_submit", "tdmrg_server_poll", "tdmrg_server_cancel", "tdmrg_server_stats", "tdmrg_server_set_batching", "tdmrg_server_batch_stats",
@@ -97,6 +97,7 @@ def load(path=LIB_PATH):
         "tdmrg_renormalize_op": (I, [P, I, I, P, PI32, P, ctypes.POINTER(I)]),
         "tdmrg_enlarge_size": (I, [I, I, PI32, PI32, I, ctypes.POINTER(I), PI32, PI32, PI32, ctypes.POINTER(ctypes.c_int64)]),
         "tdmrg_enlarge": (I, [P, I, I, PI32, PI32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
+        "tdmrg_enlarge_bonds": (I, [P, I, I, PI32, PI32, P, I, P, P, ctypes.c_double, P, P, P, P, P]),
         "tdmrg_set_op_adjoint": (I, [P, I, I, I]),
         "tdmrg_eig_stats": (I, [P, I, PI32, PI64]),
         "tdmrg_set_tile_m": (I, [P, I]),
@@ -429,6 +430,34 @@ def tdmrg_enlarge(ctx, side, qn, dim, H, cdag, t, U, H_out, cdag_out, n_out=None
     nptr = (ctypes.c_void_p * 2)(_ptr(n_out[0]), _ptr(n_out[1])) if n_out is not None else None
     _check(ctx, load().tdmrg_enlarge(ctx, side, len(d), qp, dp, ctypes.byref(hb), cb, float(t), float(U), _ptr(H_out),
                                      outs, qptr, nptr))
+    return [[tuple(x) for x in qouts[s][:4 * int(nb[s])].reshape(-1, 4)] for s in range(2)]
+
+
+def tdmrg_enlarge_bonds(ctx, side, qn, dim, H, edges, ts, U, H_out, cdag_out, n_out=None, carry_out=None):
+    """As tdmrg_enlarge with the new site bonded to K's edge and to the second site from it: edges =
+    [[(qns, data) up, (qns, data) dn] per bonded site of K], ts their hoppings; carry_out[2] (device, sized
+    like cdag_out) receives K's edge as the enlarged block's second site from the edge.  Returns the block
+    quantum numbers of c^dag'_up and c^dag'_dn (also those of the carried operators)."""
+    q, qp = _i32(np.asarray(qn).reshape(-1))
+    d, dp = _i32(dim)
+    _, _, nb, _ = tdmrg_enlarge_size(side, qn, dim)
+    hb, hq = _blocks(*H)
+    cb = (_Blocks * (2 * len(edges)))()
+    keep = []
+    for e, ops in enumerate(edges):
+        for s in range(2):
+            b, bq = _blocks(*ops[s])
+            cb[2 * e + s] = b
+            keep.append(bq)
+    tv = np.ascontiguousarray(ts, dtype=np.float64)
+    outs = (ctypes.c_void_p * 2)(_ptr(cdag_out[0]), _ptr(cdag_out[1]))
+    qouts = [np.zeros(4 * max(int(nb[s]), 1), np.int32) for s in range(2)]
+    qptr = (ctypes.c_void_p * 2)(*[x.ctypes.data_as(ctypes.c_void_p) for x in qouts])
+    nptr = (ctypes.c_void_p * 2)(_ptr(n_out[0]), _ptr(n_out[1])) if n_out is not None else None
+    cptr = (ctypes.c_void_p * 2)(_ptr(carry_out[0]), _ptr(carry_out[1])) if carry_out is not None else None
+    _check(ctx, load().tdmrg_enlarge_bonds(ctx, side, len(d), qp, dp, ctypes.byref(hb), len(edges), cb,
+                                           tv.ctypes.data_as(ctypes.c_void_p), float(U), _ptr(H_out), outs, qptr,
+                                           nptr, cptr))
     return [[tuple(x) for x in qouts[s][:4 * int(nb[s])].reshape(-1, 4)] for s in range(2)]
 
 

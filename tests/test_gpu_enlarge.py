@@ -3,6 +3,8 @@ the adjoint of a block operator, against the oracle DMRG's enlargement of the sa
 
   - the enlarged sector table, H' and the new edge c^dag'_s of left and right blocks of 1, 3 and 4 sites
     of the L=10 m=32 run: every block equal to the oracle's (scaled copies: 1e-15);
+  - the same on the 2 x 5 ladder (blocks of 1 to 4 sites) with the two bonds of the new site and K's edge
+    carried as the second site from the edge (tdmrg_enlarge_bonds);
   - the adjoint c = (c^dag)^dag defined on the device against the explicitly loaded adjoint (bit-equal
     products);
   - a superblock assembled only from device outputs (enlarged blocks, their edge operators and adjoints)
@@ -86,6 +88,63 @@ def test_enlarge_matches_oracle(lib, run, side, nsites):
             assert set(got_c) == set(want_c)
             for k, m in want_c.items():
                 assert np.array_equal(got_c[k], m)
+    finally:
+        lib.tdmrg_destroy(ctx)
+
+
+LADDER = dmrg.Geometry(2, 1.0, 0.5)
+
+
+@pytest.fixture(scope="module")
+def ladder_run():
+    d = dmrg.ChainDMRG(L, T_HOP, U, M, geom=LADDER)
+    d.run(sweeps=1)
+    return d
+
+
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("nsites", [1, 2, 3, 4])
+def test_ladder_enlarge_matches_oracle(lib, ladder_run, side, nsites):
+    """2 x 5 ladder blocks (Sec. III): the new site bonded to K's edge (a rung when K has an odd number of
+    sites) and to the second site from the edge (a leg, K of two or more sites), the second bond added by
+    the accumulating launch; K's edge carried as the enlarged block's second site from the edge.  H' to
+    1e-15, the new and the carried c^dag bit-equal to the oracle's."""
+    blk = (ladder_run.left if side == 0 else ladder_run.right)[nsites]
+    want = dmrg.enlarge(blk, "L" if side == 0 else "R", T_HOP, U, LADDER)
+    wsecs, wdims, _ = want.sectors()
+    secs, dims, _ = blk.sectors()
+    qn_o, dim_o, nb, ent = lib.tdmrg_enlarge_size(side, secs, dims)
+    qn_o = [tuple(int(x) for x in q) for q in qn_o]
+    dim_o = [int(x) for x in dim_o]
+    hq, hd = _blocks(blk, blk.H, False)
+    edges = [[(q, dev(x)) for q, x in (_blocks(blk, blk.cdag[s], True) for s in range(2))]]
+    t0, t1 = LADDER.new_site_bonds(nsites)
+    ts = [t0]
+    if blk.cdag2 is not None:
+        edges.append([(q, dev(x)) for q, x in (_blocks(blk, blk.cdag2[s], True) for s in range(2))])
+        ts.append(t1)
+    assert (blk.cdag2 is None) == (nsites == 1)
+    ctx = new_ctx()
+    try:
+        H_out = dev(np.zeros(int(ent[0])))
+        c_out = [dev(np.zeros(max(int(ent[1 + s]), 1))) for s in range(2)]
+        k_out = [dev(np.zeros(max(int(ent[1 + s]), 1))) for s in range(2)]
+        cq = lib.tdmrg_enlarge_bonds(ctx, side, secs, dims, (hq, dev(hd)), edges, ts, U, H_out, c_out, None, k_out)
+        assert qn_o == [tuple(q) for q in wsecs] and dim_o == list(wdims)
+        got_h = _unpack(qn_o, dim_o, host(H_out), [q + q for q in qn_o])
+        want_h = want.blockop(want.H, False).blocks
+        for (a, b), blkw in want_h.items():
+            assert np.abs(got_h[(wsecs[a], wsecs[a])] - blkw).max() <= 1e-15
+        for q, g in got_h.items():
+            if (wsecs.index(q[0]), wsecs.index(q[0])) not in want_h:
+                assert not np.any(g)
+        for s in range(2):
+            for out, op in ((c_out[s], want.cdag[s]), (k_out[s], want.cdag2[s])):
+                got_c = _unpack(qn_o, dim_o, host(out), [tuple(int(x) for x in b) for b in cq[s]])
+                want_c = {(wsecs[a], wsecs[b]): m for (a, b), m in want.blockop(op, True).blocks.items()}
+                assert set(want_c) <= set(got_c)
+                for k, m in got_c.items():
+                    assert np.array_equal(m, want_c[k]) if k in want_c else not np.any(m)
     finally:
         lib.tdmrg_destroy(ctx)
 

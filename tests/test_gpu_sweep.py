@@ -3,8 +3,9 @@ by step, on the FP64 path.
 
 L=10 Hubbard chain (U=4, half filling), m=20..24, n_v=4 targets, tau=0.1, n_K=10, three schedules of
 Eq. b (c^dag_{5 up} at once; c_{7 dn} c^dag_{5 up} completed two steps later; c^dag_{8 dn} reached on the
-left pass after ground-state targeting); both sweeps start from the same stored blocks (the oracle's
-ground-state DMRG).  The device runs every step through the C ABI: ground state by restarted Lanczos, the
+left pass after ground-state targeting); the 2 x 5 ladder (t_leg = 1, t_rung = 0.5, U=4; Sec. III), m=28
+and 32, two schedules, whose blocks carry their two edge sites and whose cuts are crossed by two or three
+bonds; both sweeps start from the same stored blocks (the oracle's ground-state DMRG).  The device runs every step through the C ABI: ground state by restarted Lanczos, the
 excitation operators, Krylov
 advance, rho_L or rho_R, its eigendecomposition, truncation, renormalisation, enlargement of both blocks
 and the wave-function transformation of all five targets, left and right.  Compared per step (quantities
@@ -56,36 +57,43 @@ def _device_blocks(d, sweep_mod):
             secs, dims, _ = blk.sectors()
             hq, hd = _blockops(blk, blk.H, False)
             cd = [_blockops(blk, blk.cdag[s], True) for s in range(2)]
+            cd2 = None
+            if blk.cdag2 is not None:
+                cd2 = [(q, dev(x)) for q, x in (_blockops(blk, blk.cdag2[s], True) for s in range(2))]
             V = kept = None
             if n in ustore:   # (a block older than its smaller neighbour has no usable V; the sweep remakes it first)
-                enl = dmrg.enlarge(store[n - 1], side, d.t, d.U)
+                enl = dmrg.enlarge(store[n - 1], side, d.t, d.U, d.geom)
                 if ustore[n].shape[0] == enl.dim:
                     Vh, kept = _eig_layout(ustore[n], enl, blk)
                     V = dev(Vh)
-            out[n] = sweep_mod.Block(secs, dims, (hq, dev(hd)), [(q, dev(x)) for q, x in cd], V, kept)
+            out[n] = sweep_mod.Block(secs, dims, (hq, dev(hd)), [(q, dev(x)) for q, x in cd], V, kept,
+                                     nsites=blk.nsites, cdag2=cd2)
     return left, right
 
 
-# (m, advance_every, excitations of Eq. b); m is chosen per case so that no cut of the sweep falls inside a
-# cluster of eigenvalues closer than 1e-6 lambda_max (checked on the oracle's records below)
+# (m, advance_every, excitations of Eq. b, ladder); m is chosen per case so that no cut of the sweep falls
+# inside a cluster of eigenvalues closer than 1e-7 lambda_max (checked on the oracle's records below)
 CASES = [
-    (24, 2, [(5, "cdag", 0)]),
-    (20, 1, [(5, "cdag", 0), (7, "c", 1)]),   # partial product for two steps, completed at sites (6, 7)
-    (24, 1, [(8, "cdag", 1)]),                # ground-state targeting until the left pass reaches site 8
+    (24, 2, [(5, "cdag", 0)], False),
+    (20, 1, [(5, "cdag", 0), (7, "c", 1)], False),   # partial product for two steps, completed at sites (6, 7)
+    (24, 1, [(8, "cdag", 1)], False),                # ground-state targeting until the left pass reaches site 8
+    (32, 2, [(5, "cdag", 0)], True),                 # 2 x 5 ladder: cuts after odd sites cross a rung
+    (28, 1, [(4, "c", 1)], True),
 ]
+T_RUNG = 0.5
 
 
 @pytest.fixture(scope="module", params=range(len(CASES)))
 def sweeps(request):
-    m, every, exc = CASES[request.param]
+    m, every, exc, ladder = CASES[request.param]
     torch_cuda()
     from paper_1103_5391_gb300 import sweep as S
-    d = dmrg.ChainDMRG(L, T_HOP, U, m)
+    d = dmrg.ChainDMRG(L, T_HOP, U, m, geom=dmrg.Geometry(2, T_HOP, T_RUNG) if ladder else None)
     d.run(sweeps=1)
     left, right = _device_blocks(d, S)
     want = tst.TSTSweep(copy.deepcopy(d), m, n_v=4, tau=0.1, nk=10, advance_every=every, excitations=exc).run()
-    got = S.TSTSweep(L, T_HOP, U, m, left, right, n_v=4, tau=0.1, nk=10, advance_every=every,
-                     excitations=exc).run()
+    got = S.TSTSweep(L, T_HOP, U, m, left, right, n_v=4, tau=0.1, nk=10, advance_every=every, excitations=exc,
+                     lattice=S.Lattice(2, T_HOP, T_RUNG) if ladder else None).run()
     return m, want, got
 
 
@@ -130,7 +138,7 @@ def test_sweep_on_the_tensor_path():
     torch_cuda()
     from paper_1103_5391_gb300 import sweep as S
     from paper_1103_5391_gb300 import tdmrg as T
-    m, every, exc = CASES[0]
+    m, every, exc, _ = CASES[0]
     d = dmrg.ChainDMRG(L, T_HOP, U, m)
     d.run(sweeps=1)
     left, right = _device_blocks(d, S)
