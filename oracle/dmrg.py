@@ -276,9 +276,10 @@ class ChainDMRG:
     of the two-leg ladder of L sites (geom = Geometry(2, t_leg, t_rung); the superblocks of the infinite
     algorithm are ladders of 2l + 2 sites)."""
 
-    def __init__(self, L, t, U, m, geom=None):
+    def __init__(self, L, t, U, m, geom=None, gs_resid=1e-9):
         assert L % 2 == 0 and L >= 4
         self.L, self.t, self.U, self.m, self.geom = L, t, U, m, geom
+        self.gs_resid = gs_resid   # residual bound of every step's ground state
         self.left = {1: site_block(U)}
         self.right = {1: site_block(U)}
         self.right_U = {}   # right block of r sites: its kept states (columns) in the enlarged block of r - 1 sites
@@ -289,7 +290,8 @@ class ChainDMRG:
         Lenl = enlarge(self.left[l], "L", self.t, self.U, self.geom)
         Renl = enlarge(self.right[r], "R", self.t, self.U, self.geom)
         sb, HL, HR, conns = superblock_of(Lenl, Renl, self.t, self.geom)
-        e, psi = ground_state(lambda v: superblock.apply_h(sb, HL, HR, conns, Q, v), sb.size(Q))
+        e, psi = ground_state(lambda v: superblock.apply_h(sb, HL, HR, conns, Q, v), sb.size(Q),
+                              resid_tol=self.gs_resid)
         return Lenl, Renl, sb, e, psi
 
     def infinite(self):

@@ -23,6 +23,8 @@ left enlarged block, and l + 1, the new site of the right one) holds its site.  
 ground state is targeted; while the product is partial it takes the places of all n_v targets; at the
 step that completes it the targets phi(t_x) are built.
 
+Start: the stored blocks of an infinite-system DMRG, on the device (`infinite`) or from elsewhere.
+
 Schedule of one sweep (the paper leaves it open): from the centre of the chain move right to the right
 end (right block of one site), left to the left end, and right back to the centre; the targets advance by
 tau at every `advance_every`-th step after the one that completed phi (Sec. II.C: the targets are
@@ -176,6 +178,50 @@ def truncate_block(ctx, side, enl, states, weights, m, real_basis, dev):
     rec = {"kept": kept, "evals": [ev[off[i]: off[i + 1]] for i in range(len(enl.dim))],
            "discarded": float(disc.cpu().numpy()[0])}
     return K, rec, U
+
+
+def site_block(ctx, U, dev, lattice=None):
+    """One Hubbard site as a Block, made on the device: the one-state vacuum block (sector (0, 0), H = 0,
+    no c^dag blocks) enlarged by a site, so H = U n_up n_dn and c^dag_s are the site's (on a ladder with a
+    zero second edge)."""
+    vac = Block([(0, 0)], [1], ([], _zeros(1, dev)), [([], _zeros(1, dev)), ([], _zeros(1, dev))], nsites=0)
+    e = enlarge(ctx, vac, 0, 0.0, U, dev, lattice)
+    return Block(e.qn, e.dim, e.H, e.cdag, nsites=1, cdag2=e.cdag2)
+
+
+def infinite(L, t, U, m, lattice=None, device=None, gs_nk=32, gs_restarts=40):
+    """Infinite-system DMRG on the device (Sec. I): both blocks grow by one site per step; the superblock
+    of 2l + 2 sites (l sites per block, the lattice's bonds at the cut after site l) at half filling, its
+    ground state by restarted Lanczos from a seeded vector, and both enlarged blocks cut to their m most
+    probable states (rho_L and rho_R of the ground state alone).  On a ladder the rung-first labels make
+    every intermediate superblock a ladder of l + 1 rungs and the right block the reflection of the left
+    one.  Returns ({sites: left Block}, {sites: right Block}, [(superblock sites, energy)]); the blocks of
+    two or more sites carry their states in the enlarged block they were cut from, as TSTSweep needs."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    mk = lambda: T.tdmrg_create(device=dev.index, stream=torch.cuda.current_stream(dev).cuda_stream,
+                                nk_max=max(32, gs_nk), prec=T.TDMRG_FP64)
+    work, cur = mk(), mk()
+    try:
+        site = site_block(work, U, dev, lattice)
+        left, right, energies = {1: site}, {1: site}, []
+        l = 1
+        while 2 * l + 2 <= L:
+            Lenl = enlarge(work, left[l], 0, t, U, dev, lattice)
+            Renl = enlarge(work, right[l], 1, t, U, dev, lattice)
+            load(cur, Lenl, Renl, t, lattice, l)
+            Q = (l + 1, l + 1)
+            n = T.tdmrg_sector_size(cur, Q)
+            g = torch.Generator().manual_seed(11035391 + l)
+            psi = torch.complex(torch.randn(n, generator=g, dtype=torch.float64),
+                                torch.randn(n, generator=g, dtype=torch.float64)).to(dev)
+            energies.append((2 * l + 2, T.tdmrg_ground_state(cur, Q, psi, gs_nk, gs_restarts)))
+            left[l + 1], _, _ = truncate_block(cur, 0, Lenl, [(Q, psi)], [1.0], m, False, dev)
+            right[l + 1], _, _ = truncate_block(cur, 1, Renl, [(Q, psi)], [1.0], m, False, dev)
+            l += 1
+        return left, right, energies
+    finally:
+        for c in (work, cur):
+            T.tdmrg_destroy(c)
 
 
 class TSTSweep:
