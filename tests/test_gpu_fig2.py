@@ -3,8 +3,9 @@ reproduced by a finite sweep with time-step targeting on the GPU and compared wi
 App. A.
 
 16-site chain, H_0 = -sum_<ij> sigma (c^dag c + h.c.) (U = 0), half filling, m = 200 (the paper's value for
-the chain).  The stored blocks are the oracle's ground-state DMRG (infinite algorithm and one finite
-sweep).  The hole is created by c_{8 up} on the ground state (i = 8: b = 1, B = c_up in Eq. b) at the
+the chain).  Everything runs on the device: the infinite algorithm, one finite ground-state sweep (W_gs,
+its discarded weight, enters the energy bound), then the sweep with time-step targeting.  The hole is
+created by c_{8 up} on the ground state (i = 8: b = 1, B = c_up in Eq. b) at the
 sweep's first step, whose central sites are 7 and 8; n_v = 4 targets, tau = 0.1, n_K = 12, the targets
 advanced at every other step (Sec. II.C).  At every step the device measures <n_{l up}> and <n_{l+1 up}>
 of every target (l, l + 1: the new sites of the two enlarged blocks), normalised, so for target x at time
@@ -27,17 +28,15 @@ Ladder, Fig. 2(a): 8 x 2 sites (rung-first labels, site 8 = leg 0 of rung 4), m 
 for the ladder), the same excitation and schedule.  The paper does not give the rung hopping of this
 figure; with t_rung = t_leg the half-filled U=0 ladder has two levels at the Fermi energy, a degenerate
 ground state for which App. A's X_ij is not defined, so t_rung = 0.5 (the value of Sec. III.B) is used,
-which leaves a gap of 0.31.  The oracle runs the infinite algorithm only; two ground-state sweeps on the
-device (tdmrg sweep without excitation) converge the blocks, and W_gs, the last one's discarded weight,
-enters the energy bound.  Measured: W = 6.8e-4; energy 5.7e-3 above (bound 5.3e-2), densities 7.9e-3
+which leaves a gap of 0.31.  The device runs the infinite algorithm and two ground-state sweeps (W_gs: the
+last one's discarded weight).  Measured: W = 6.8e-4; energy 5.7e-3 above (bound 5.3e-2), densities 7.9e-3
 (bound 7.4e-2): a ladder needs far more states than a chain for the same accuracy, as its cut crosses
 two legs."""
 import numpy as np
 import pytest
 
-from oracle import closed_forms, dmrg, ed
+from oracle import closed_forms, ed
 from tests.gpu_util import torch_cuda
-from tests.test_gpu_sweep import _device_blocks
 
 pytestmark = pytest.mark.gpu
 L, M, M_LADDER, I_SITE, TAU, N_V, T_RUNG = 16, 200, 400, 8, 0.1, 4, 0.5
@@ -73,31 +72,28 @@ def _check(records, hop, nsites, w_gs_sweep=0.0):
     return W, worst
 
 
-def test_chain_hole_excitation_matches_app_a():
+def _device_run(lattice, m, gs_sweeps):
+    """Infinite algorithm, ground-state sweeps and the sweep with the hole c_{8 up}, all on the device."""
     torch_cuda()
     from paper_1103_5391_gb300 import sweep as S
-    d = dmrg.ChainDMRG(L, 1.0, 0.0, M)
-    d.run(sweeps=1)
-    left, right = _device_blocks(d, S)
-    records = S.TSTSweep(L, 1.0, 0.0, M, left, right, n_v=N_V, tau=TAU, nk=12, advance_every=2,
-                         excitations=[(I_SITE, "c", 0)]).run()
-    W, _ = _check(records, HOP, L)
+    lat = None if lattice is None else S.Lattice(*lattice)
+    left, right, _ = S.infinite(L, 1.0, 0.0, m, lattice=lat)
+    w_gs_sweep = 0.0
+    for _ in range(gs_sweeps):
+        gs = S.TSTSweep(L, 1.0, 0.0, m, left, right, excitations=[], lattice=lat)
+        w_gs_sweep = sum(r.get("discarded", 0.0) for r in gs.run())
+        left, right = gs.left, gs.right
+    records = S.TSTSweep(L, 1.0, 0.0, m, left, right, n_v=N_V, tau=TAU, nk=12, advance_every=2,
+                         excitations=[(I_SITE, "c", 0)], lattice=lat).run()
+    return records, w_gs_sweep
+
+
+def test_chain_hole_excitation_matches_app_a():
+    records, w_gs_sweep = _device_run(None, M, 1)
+    W, _ = _check(records, HOP, L, w_gs_sweep)
     assert W < 1e-5   # m = 200 resolves the chain's targets: the bounds are tight
 
 
 def test_ladder_hole_excitation_matches_app_a():
-    torch_cuda()
-    from paper_1103_5391_gb300 import sweep as S
-    hop = ed.ladder_hopping(L // 2, 1.0, T_RUNG)
-    d = dmrg.ChainDMRG(L, 1.0, 0.0, M_LADDER, geom=dmrg.Geometry(2, 1.0, T_RUNG))
-    d.infinite()
-    left, right = _device_blocks(d, S)
-    lattice = S.Lattice(2, 1.0, T_RUNG)
-    for _ in range(2):   # ground-state sweeps on the device
-        gs = S.TSTSweep(L, 1.0, 0.0, M_LADDER, left, right, excitations=[], lattice=lattice)
-        recs = gs.run()
-        left, right = gs.left, gs.right
-    w_gs_sweep = sum(r.get("discarded", 0.0) for r in recs)
-    records = S.TSTSweep(L, 1.0, 0.0, M_LADDER, left, right, n_v=N_V, tau=TAU, nk=12, advance_every=2,
-                         excitations=[(I_SITE, "c", 0)], lattice=lattice).run()
-    _check(records, hop, L, w_gs_sweep)
+    records, w_gs_sweep = _device_run((2, 1.0, T_RUNG), M_LADDER, 2)
+    _check(records, ed.ladder_hopping(L // 2, 1.0, T_RUNG), L, w_gs_sweep)
