@@ -420,7 +420,7 @@ typedef struct {
 /* Create a server on `device`: hbm_budget bytes for the footprint of running jobs (0 = no limit),
  * at most max_active jobs at once.  Starts the server thread.  Errors: EINVAL, ECUDA. */
 int tdmrg_server_create(tdmrg_server** out, int device, size_t hbm_budget, int max_active);
-/* Batching of admitted jobs (north star pattern 2 across jobs): with max_group > 1, the queued jobs that
+/* Batching of admitted jobs (one grouped launch across jobs): with max_group > 1, the queued jobs that
  * can share a time step (same precision, tau, n_v, n_K, steps and excitation sector shift, static
  * coefficients, distinct contexts, vector lengths within a factor of two) are admitted together, up to
  * max_group, and run as one group on the
