@@ -80,3 +80,51 @@ def test_real_basis_rho_is_real_part():
     real_states = [(Q, v.real + 0j) for Q, v in states]
     for a, b in zip(density.rho_left(sb, real_states, w), density.rho_left(sb, real_states, w, real_basis=True)):
         assert np.abs(a - b).max() < 1e-15
+
+
+def test_rho_right_is_the_partial_trace():
+    """rho_R (Eq. rdensitymatrix for the right block, Sec. II.B) against the definition of the reduced
+    density matrix: the partial trace over the left block of the full density matrix |psi><psi| (einsum on
+    the DL x DR x DL x DR tensor), for the weighted rho_R of the sweep and the one-state rho_R of the DMRG;
+    and against an independent route: Tr(rho_R O_R) = <psi| 1 x O_R |psi> / <psi|psi> (and the same for
+    rho_L) with the complex Hermitian block Hamiltonians as O, through the sector-pair product.  A complex
+    conjugated (transposed) rho_R fails the trace against a complex O."""
+    from oracle import dmrg
+    ss = S.make_synthetic(6, 8, 4.0, seed=S.SEED_BASE + 31)
+    sb = superblock.Superblock(ss.lsec, ss.ldim, ss.rsec, ss.rdim)
+    states = [(ss.Q0, ss.psi_gs), (ss.Q1, ss.phi * (0.3 - 0.8j))]
+    weights = [0.6, 0.4]
+    roffs = np.concatenate([[0], np.cumsum(sb.rdim)])
+    loffs = np.concatenate([[0], np.cumsum(sb.ldim)])
+    full_r = 0
+    for (Q, v), w in zip(states, weights):
+        M = _full_matrix(sb, Q, v)
+        D = np.einsum("ab,cd->abcd", M, M.conj()) / np.vdot(v, v).real    # <a b|psi><psi|c d>
+        full_r = full_r + w * np.einsum("abad->bd", D)
+    rr = density.rho_right(sb, states, weights)
+    for ri, r in enumerate(rr):
+        blk = full_r[roffs[ri]:roffs[ri + 1], roffs[ri]:roffs[ri + 1]]
+        assert np.abs(r - blk).max() < 1e-14
+    # nothing outside the sector blocks (rho_R commutes with the right block's quantum numbers)
+    mask = np.zeros_like(full_r, dtype=bool)
+    for ri in range(len(rr)):
+        mask[roffs[ri]:roffs[ri + 1], roffs[ri]:roffs[ri + 1]] = True
+    assert np.abs(full_r[~mask]).max() < 1e-14
+    # the DMRG's one-state rho_R (unnormalised psi, weight 1)
+    v = 1.7 * ss.psi_gs
+    M = _full_matrix(sb, ss.Q0, v)
+    pt = np.einsum("ab,ad->bd", M, M.conj())
+    for ri, r in enumerate(dmrg.rho_right(sb, ss.Q0, v)):
+        assert np.abs(r - pt[roffs[ri]:roffs[ri + 1], roffs[ri]:roffs[ri + 1]]).max() < 1e-13
+    # expectation values of complex Hermitian block operators through H psi's product route
+    from oracle import blocks
+    OL, OR = blocks.BlockOp(ss.HL, False), blocks.BlockOp(ss.HR, False)
+    rl = density.rho_left(sb, states, weights)
+    want_l = sum(w * superblock.expect(sb, OL, None, Q, x).real for (Q, x), w in zip(states, weights))
+    want_r = sum(w * superblock.expect(sb, None, OR, Q, x).real for (Q, x), w in zip(states, weights))
+    got_l = sum(np.trace(rl[k] @ ss.HL[(k, k)]).real for k in range(len(rl)) if (k, k) in ss.HL)
+    got_r = sum(np.trace(rr[k] @ ss.HR[(k, k)]).real for k in range(len(rr)) if (k, k) in ss.HR)
+    assert abs(got_l - want_l) < 1e-12 and abs(got_r - want_r) < 1e-12
+    # the check is not vacuous: the conjugated matrix gives a different trace against the complex O
+    bad_r = sum(np.trace(rr[k].conj() @ ss.HR[(k, k)]).real for k in range(len(rr)) if (k, k) in ss.HR)
+    assert abs(bad_r - want_r) > 1e-3
