@@ -182,6 +182,27 @@ def _half_u(orig):
     return lambda sector, hop, U: orig(sector, hop, 0.5 * U)
 
 
+def _density_spin(orig):
+    """The density of the other spin species."""
+    return lambda vec, sector, i, sigma: orig(vec, sector, i, 1 - sigma)
+
+
+# ---------------------------------------------------------------- exact blocks
+def _block_half_u(orig):
+    """U/2 in an exact block's Hamiltonian."""
+    return lambda self, hop, U: orig(self, hop, 0.5 * U)
+
+
+def _no_string(orig):
+    """A block's c^dag / c without the Jordan-Wigner string of the sites before it."""
+    from oracle import blocks
+
+    def f(self, i, sigma, dagger):
+        cd = blocks.SITE_CDAG_UP if sigma == 0 else blocks.SITE_CDAG_DN
+        return self.kron_op([np.eye(4)] * i + [cd if dagger else cd.T] + [np.eye(4)] * (self.nsites - i - 1))
+    return f
+
+
 # ---------------------------------------------------------------- DMRG (Sec. I) and the sweep (Sec. II.B-II.D)
 def _kept_smallest(orig):
     """The m smallest eigenvalues kept."""
@@ -198,6 +219,14 @@ def _superblock_bond_halved(orig):
     def f(*a, **k):
         sb, HL, HR, conns = orig(*a, **k)
         return sb, HL, HR, [(0.5 * c, A, B) for c, A, B in conns]
+    return f
+
+
+def _discarded_kept(orig):
+    """The discarded weight reported as the kept weight."""
+    def f(*a, **k):
+        K, counts, lams, disc, U = orig(*a, **k)
+        return K, counts, lams, float(sum(np.sum(x) for x in lams)) - disc, U
     return f
 
 
@@ -264,6 +293,11 @@ MUTANTS = {
     "ed_no_jordan_wigner": ([("oracle.ed", "apply_c"), ("oracle.ed", "apply_cdag")], _no_jw,
                             [C + "test_hole_formula_against_ed", C + "test_c1_u0_trajectory_against_closed_form"]),
     "ed_half_u": ([("oracle.ed", "hamiltonian")], _half_u, [H + "test_exact_cut_hpsi_equals_ed"]),
+    "ed_density_spin": ([("oracle.ed", "density")], _density_spin, [G + "test_dmrg_superblock_dynamics_match_ed"]),
+    "block_half_u": ([("oracle.blocks", "Block.hubbard_h")], _block_half_u, [H + "test_exact_cut_hpsi_equals_ed"]),
+    "block_no_jw_string": ([("oracle.blocks", "Block.site_fermion")], _no_string,
+                           [H + "test_local_operators_equal_ed"]),
+    "discarded_weight": ([("oracle.dmrg", "truncate")], _discarded_kept, [T + "test_truncated_sweep_invariants"]),
     "kept_smallest": ([("oracle.dmrg", "kept_counts")], _kept_smallest,
                       [G + "test_kept_counts_brute_force_small"]),
     "dmrg_eig_ascending": ([("oracle.dmrg", "eig_desc")], _eig_ascending,
