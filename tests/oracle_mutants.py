@@ -230,6 +230,16 @@ def _discarded_kept(orig):
     return f
 
 
+def _wft_u_conj(orig):
+    """The kept states' projection with U^T (no conjugation) in a wave-function transformation."""
+    return lambda Lenl, Renl, Q, psi, U, *rest: orig(Lenl, Renl, Q, psi, U.conj(), *rest)
+
+
+def _wft_v_conj(orig):
+    """The expansion of the other block's states with conj(V)."""
+    return lambda Lenl, Renl, Q, psi, U, blk, V, *rest: orig(Lenl, Renl, Q, psi, U, blk, V.conj(), *rest)
+
+
 def _ladder_bonds_swapped(orig):
     """A new ladder site bonded to the second site with the rung amplitude and to the edge with the leg's."""
     def f(self, k):
@@ -305,6 +315,14 @@ MUTANTS = {
     "enlarge_half_u": ([("oracle.dmrg", "enlarge")], _enlarge_half_u, [G + "test_dmrg_exact_blocks_match_ed"]),
     "superblock_bond_halved": ([("oracle.dmrg", "superblock_of")], _superblock_bond_halved,
                            [G + "test_dmrg_exact_blocks_match_ed"]),
+    "wft_right_projection_conj": ([("oracle.dmrg", "wft_right")], _wft_u_conj,
+                                  [T + "test_exact_sweep_is_exact_time_evolution"]),
+    "wft_left_projection_conj": ([("oracle.dmrg", "wft_left")], _wft_u_conj,
+                                 [T + "test_exact_sweep_is_exact_time_evolution"]),
+    "wft_right_expansion_conj": ([("oracle.dmrg", "wft_right")], _wft_v_conj,
+                                 [T + "test_exact_sweep_is_exact_time_evolution"]),
+    "wft_left_expansion_conj": ([("oracle.dmrg", "wft_left")], _wft_v_conj,
+                                [T + "test_exact_sweep_is_exact_time_evolution"]),
     "ladder_bonds_swapped": ([("oracle.dmrg", "Geometry.new_site_bonds")], _ladder_bonds_swapped,
                              [LAD + "test_geometry_is_the_lattice"]),
     "ladder_rung_dropped": ([("oracle.dmrg", "Geometry.cut_bonds")], _ladder_rung_dropped,
