@@ -52,6 +52,11 @@ def _norm_dropped(orig):
     return f
 
 
+def _no_breakdown(orig):
+    """The breakdown test never fires: the recursion runs on from a vector at rounding level."""
+    return lambda apply_h, phi, nk, tol=1e-12: orig(apply_h, phi, nk, -1.0)
+
+
 def _err_first_component(orig):
     """Saad's estimate with the first component of e^{-iTt} e_0 in place of the last."""
     from oracle import krylov
@@ -268,6 +273,8 @@ MUTANTS = {
                           [K + "test_lanczos_relation_and_orthonormality", K + "test_full_krylov_space_is_exact_expm"]),
     "lanczos_norm_dropped": ([("oracle.krylov", "lanczos")], _norm_dropped,
                              [K + "test_full_krylov_space_is_exact_expm"]),
+    "lanczos_no_breakdown": ([("oracle.krylov", "lanczos")], _no_breakdown,
+                             [K + "test_breakdown_on_invariant_subspace"]),
     "error_estimate_component": ([("oracle.krylov", "error_estimate")], _err_first_component,
                                  [K + "test_error_estimate_bounds_the_true_error"]),
     "error_estimate_beta": ([("oracle.krylov", "error_estimate")], _err_no_beta,
