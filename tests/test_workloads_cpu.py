@@ -1,5 +1,5 @@
 """The seeded synthetic superblocks the bench times (Gaussian sector model of a truncated DMRG superblock
-at the central cut): their sizes are the ones the design notes and the bench's roofline quote, their
+at the central cut): their sizes are the ones quoted for them and used by the bench's roofline, their
 operators have the structure the model states, and a seed gives the same arrays every time."""
 import numpy as np
 import pytest
